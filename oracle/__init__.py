@@ -1,0 +1,229 @@
+"""FP64 CPU oracle of the panoramic stitching path (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+this package.  The product (``paper_1810_03988_gb300``) never imports it and shares no code with
+it: the oracle is a separate C library (``oracle.c``) compiled with gcc, evaluated in double
+precision, loaded through ctypes.
+
+Paper anchors: Sec. 4.3 / Alg. 4 step 1 (frames "cut and transformed" on the GPU) and step 6
+("transform the video and blend it into a panoramic video"), Sec. 1 contribution 3 ("multi band
+fusion").  The paper states no formulas; ``oracle.c`` lists the readings it evaluates.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+_threads_used = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` with gcc (-O2, IEEE double, OpenMP when available)."""
+    global _threads_used
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = f"{_LIB_PATH}.{os.getpid()}.tmp"
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-fno-fast-math", "-ffp-contract=off", src, "-o", tmp,
+            "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_invert_h.argtypes = [_P, _P]
+            lib.oracle_reduce.argtypes = [_P, _I, _I, _I, _P]
+            lib.oracle_expand.argtypes = [_P, _I, _I, _I, _I, _I, _P]
+            lib.oracle_regions.argtypes = [_I, _I, _I, _I, _I, _I, _I, _P]
+            lib.oracle_forward.argtypes = [_I, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _P, _P, _P,
+                                           _P, _P]
+            lib.oracle_warp.argtypes = [_I, _I, _P, _D, _P, ctypes.c_int64, _I, _I, _P, _P]
+            lib.oracle_loss_grad.argtypes = [_I, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _P, _P]
+            for f in ("oracle_invert_h", "oracle_reduce", "oracle_expand", "oracle_regions", "oracle_forward",
+                      "oracle_warp", "oracle_loss_grad"):
+                getattr(lib, f).restype = _I
+            _lib = lib
+    return _lib
+
+
+def threads() -> int:
+    """Number of OpenMP threads the oracle runs with (OMP_NUM_THREADS, else the affinity mask)."""
+    env = os.environ.get("OMP_NUM_THREADS")
+    if env:
+        return int(env)
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with status {rc}")
+
+
+def invert_h(M) -> np.ndarray:
+    """Canvas->camera map A = M^-1 with a33 = 1."""
+    M = np.ascontiguousarray(M, dtype=np.float64).reshape(9)
+    A = np.empty(9)
+    _check(_load().oracle_invert_h(M.ctypes.data, A.ctypes.data), "invert_h")
+    return A.reshape(3, 3)
+
+
+def reduce(img: np.ndarray) -> np.ndarray:
+    """One REDUCE step (separable [1,4,6,4,1]/16, even-index decimation, reflect-101) of HxWxC."""
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    if img.ndim == 2:
+        return reduce(img[:, :, None])[:, :, 0]
+    h, w, c = img.shape
+    out = np.empty(((h + 1) // 2, (w + 1) // 2, c))
+    _check(_load().oracle_reduce(img.ctypes.data, w, h, c, out.ctypes.data), "reduce")
+    return out
+
+
+def expand(img: np.ndarray, shape) -> np.ndarray:
+    """One EXPAND step of a coarse HcxWcxC image to the finer size ``shape`` = (h, w)."""
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    if img.ndim == 2:
+        return expand(img[:, :, None], shape)[:, :, 0]
+    hc, wc, c = img.shape
+    h, w = shape
+    out = np.empty((h, w, c))
+    _check(_load().oracle_expand(img.ctypes.data, wc, hc, c, w, h, out.ctypes.data), "expand")
+    return out
+
+
+def gaussian_pyramid(img: np.ndarray, levels: int) -> list:
+    out = [np.asarray(img, dtype=np.float64)]
+    for _ in range(levels - 1):
+        out.append(reduce(out[-1]))
+    return out
+
+
+def laplacian_pyramid(img: np.ndarray, levels: int) -> list:
+    g = gaussian_pyramid(img, levels)
+    return [g[l] - expand(g[l + 1], g[l].shape[:2]) for l in range(levels - 1)] + [g[-1]]
+
+
+def collapse(lap: list) -> np.ndarray:
+    r = lap[-1]
+    for l in range(len(lap) - 2, -1, -1):
+        r = lap[l] + expand(r, lap[l].shape[:2])
+    return r
+
+
+def _cam_arrays(cams, frames):
+    n = len(cams)
+    Ws = np.array([c.width for c in cams], dtype=np.int32)
+    Hs = np.array([c.height for c in cams], dtype=np.int32)
+    Ms = np.ascontiguousarray(np.stack([np.asarray(c.H, dtype=np.float64).reshape(9) for c in cams]))
+    gains = np.array([float(getattr(c, "gain", 1.0)) for c in cams], dtype=np.float64)
+    frames = [np.ascontiguousarray(f, dtype=np.uint8) for f in frames]
+    for c, f in zip(cams, frames):
+        assert f.shape == (c.height, c.width, 3), (f.shape, c.width, c.height)
+    fp = (ctypes.c_void_p * n)(*[f.ctypes.data for f in frames])
+    pitches = np.array([f.strides[0] for f in frames], dtype=np.int64)
+    return Ws, Hs, Ms, gains, fp, pitches, frames
+
+
+def regions(canvas_w: int, canvas_h: int, levels: int, window=None) -> np.ndarray:
+    """Per-level rectangles [X_l | Y_l] as an (L, 8) array of (x0, x1, y0, y1) pairs."""
+    x0, y0, w, h = window if window is not None else (0, 0, canvas_w, canvas_h)
+    out = np.empty((levels, 8), dtype=np.int32)
+    _check(_load().oracle_regions(canvas_w, canvas_h, levels, x0, y0, w, h, out.ctypes.data), "regions")
+    return out
+
+
+def forward(cams, frames, canvas_w: int, canvas_h: int, levels: int, window=None, debug: bool = False):
+    """Stitch one frame set (S1-S6) in double precision.
+
+    ``cams``: objects with ``width``, ``height``, ``H`` (camera->canvas 3x3) and ``gain``.
+    ``window``: (x0, y0, w, h) output rectangle, default the whole canvas.
+    Returns dict with ``out`` (h x w x 3 float64 in [0,1]), ``u8`` (h x w x 3 uint8), ``mindist``
+    (h x w distance in source px to the nearest validity border over all cameras) and, when
+    ``debug``, ``S``/``B`` per level on the X_l rectangles with ``regions``.
+    """
+    lib = _load()
+    n = len(cams)
+    Ws, Hs, Ms, gains, fp, pitches, keep = _cam_arrays(cams, frames)
+    x0, y0, w, h = window if window is not None else (0, 0, canvas_w, canvas_h)
+    out = np.empty((h, w, 3))
+    u8 = np.empty((h, w, 3), dtype=np.uint8)
+    md = np.empty((h, w))
+    S = B = None
+    dS = dB = None
+    reg = regions(canvas_w, canvas_h, levels, (x0, y0, w, h))
+    if debug:
+        S = [np.empty((r[3] - r[2], r[1] - r[0])) for r in reg]
+        B = [np.empty((r[3] - r[2], r[1] - r[0], 3)) for r in reg]
+        dS = (ctypes.c_void_p * levels)(*[a.ctypes.data for a in S])
+        dB = (ctypes.c_void_p * levels)(*[a.ctypes.data for a in B])
+    rc = lib.oracle_forward(n, Ws.ctypes.data, Hs.ctypes.data, Ms.ctypes.data, gains.ctypes.data, fp,
+                            pitches.ctypes.data, canvas_w, canvas_h, levels, x0, y0, w, h, out.ctypes.data,
+                            u8.ctypes.data, md.ctypes.data, dS, dB)
+    _check(rc, "forward")
+    del keep
+    res = {"out": out, "u8": u8, "mindist": md, "regions": reg}
+    if debug:
+        res["S"] = S
+        res["B"] = B
+    return res
+
+
+def warp(cam, frame, canvas_w: int, canvas_h: int):
+    """Level 0 of one camera on the whole canvas: (I_i as HcxWcx3, raw feather weight HcxWc)."""
+    lib = _load()
+    frame = np.ascontiguousarray(frame, dtype=np.uint8)
+    M = np.ascontiguousarray(np.asarray(cam.H, dtype=np.float64).reshape(9))
+    img = np.empty((canvas_h, canvas_w, 3))
+    wr = np.empty((canvas_h, canvas_w))
+    rc = lib.oracle_warp(cam.width, cam.height, M.ctypes.data, float(getattr(cam, "gain", 1.0)),
+                         frame.ctypes.data, frame.strides[0], canvas_w, canvas_h, img.ctypes.data, wr.ctypes.data)
+    _check(rc, "warp")
+    return img, wr
+
+
+def loss_grad(widths, heights, params, frames, window, mask_params=None, grad: bool = True):
+    """Overlap SSD loss (S7) and its gradient with respect to (a11..a32, gain) per camera.
+
+    ``params``/``mask_params``: (n, 9) arrays; ``window``: canvas (x0, y0, w, h).
+    Returns (loss, grad (n, 9) or None)."""
+    lib = _load()
+    n = len(widths)
+    Ws = np.asarray(widths, dtype=np.int32)
+    Hs = np.asarray(heights, dtype=np.int32)
+    p = np.ascontiguousarray(params, dtype=np.float64).reshape(n, 9)
+    mp = None if mask_params is None else np.ascontiguousarray(mask_params, dtype=np.float64).reshape(n, 9)
+    frames = [np.ascontiguousarray(f, dtype=np.uint8) for f in frames]
+    fp = (ctypes.c_void_p * n)(*[f.ctypes.data for f in frames])
+    pitches = np.array([f.strides[0] for f in frames], dtype=np.int64)
+    loss = np.zeros(1)
+    g = np.zeros((n, 9)) if grad else None
+    x0, y0, w, h = window
+    rc = lib.oracle_loss_grad(n, Ws.ctypes.data, Hs.ctypes.data, p.ctypes.data,
+                              None if mp is None else mp.ctypes.data, fp, pitches.ctypes.data, x0, y0, w, h,
+                              loss.ctypes.data, None if g is None else g.ctypes.data)
+    _check(rc, "loss_grad")
+    return float(loss[0]), g

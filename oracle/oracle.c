@@ -1,0 +1,618 @@
+/*
+ * FP64 CPU oracle of the per-frame panoramic stitching path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or helper with the CUDA path.
+ *
+ * What it computes (paper Sec. 4.3, Alg. 4 step 1 "cut and transformed" and
+ * step 6 "transform the video and blend it into a panoramic video"; Sec. 1,
+ * contribution 3, "multi band fusion" to remove seams).  The paper gives no
+ * formulas for any of these steps; the definitions below are the textbook
+ * Burt-Adelson multiresolution spline with the readings listed in the design
+ * notes (C1-C17).  Everything is evaluated literally in double precision:
+ *
+ *  S1 warp:   A_i = M_i^-1 scaled so a33 = 1.  For canvas pixel (x, y):
+ *             (nu, nv, w) = A_i (x, y, 1); u = nu/w, v = nv/w.
+ *             I_i = gain_i * bilinear(frame_i, clamp(u), clamp(v)) / 255,
+ *             coordinates clamped to [0, W-1] x [0, H-1]; I_i = 0 where w <= 0.
+ *             valid_i = w > 0 and -0.5 <= u < W-0.5 and -0.5 <= v < H-0.5.
+ *  S2 weight: w_i = valid_i * max(0, min(u+0.5, v+0.5, W-0.5-u, H-0.5-v)),
+ *             What_i = w_i / sum_j w_j where the sum is > 0, else 0.
+ *  S3 REDUCE: G^{l+1}(k, j) = sum_{m,n=-2..2} w(m) w(n) G^l(r(2k+m), r(2j+n)),
+ *             w = [1,4,6,4,1]/16, r = reflect-101 on the finer grid, size ceil(n/2).
+ *  S4 EXPAND: E(x, y) = sum_{k,j} 2w(x-2k) 2w(y-2j) G(r(k), r(j)), r = reflect-101
+ *             on the coarser grid; L^l = G^l - E(G^{l+1}), L^{L-1} = G^{L-1}.
+ *  S5 blend:  N^l = sum_i G^l(What_i) L^l(I_i), S^l = sum_i G^l(What_i),
+ *             B^l = N^l / S^l where S^l > 1e-12, else 0.
+ *  S6 collapse: R^{L-1} = B^{L-1}, R^l = B^l + E(R^{l+1});
+ *             out = clamp(R^0, 0, 1) where sum_i w_i > 0, else 0;
+ *             out_u8 = round-half-even(255 * out).
+ *  S7 loss:   sum over canvas pixels of sum_{i<j} valid_i valid_j |I_i - I_j|^2
+ *             and its analytic gradient with respect to (a11..a32, gain) of each
+ *             camera, validity masks held constant.
+ *
+ * Output windows: the forward pass evaluates the definition on the smallest
+ * per-level rectangles that the requested output window depends on (reflect-101
+ * folds every index back into the level, so the rectangles are computed by
+ * enumerating the folded indices).  For a window equal to the canvas this is
+ * the whole-canvas definition; for a sub-window the values are bit-identical
+ * to the whole-canvas run because every needed value is computed by the same
+ * expression from the same inputs.
+ */
+#include <float.h>
+#include <limits.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_EINVAL -1
+#define OR_ENOMEM -2
+
+static const double W5[5] = {1.0 / 16.0, 4.0 / 16.0, 6.0 / 16.0, 4.0 / 16.0, 1.0 / 16.0};
+
+/* reflect-101 index folding (..., 2, 1, 0, 1, 2, ..., n-2, n-1, n-2, ...); size 1 clamps. */
+static int reflect101(int i, int n) {
+    if (n <= 1) return 0;
+    int p = 2 * (n - 1);
+    i %= p;
+    if (i < 0) i += p;
+    if (i >= n) i = p - i;
+    return i;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* homography inverse                                                                          */
+
+/* A = M^-1 scaled so that A[8] == 1.  Returns 0, or -1 when M is singular or the unscaled
+ * inverse has a33 <= 0 (then the sign convention w > 0 <=> in front of the camera is lost). */
+int oracle_invert_h(const double* M, double* A) {
+    double a = M[0], b = M[1], c = M[2], d = M[3], e = M[4], f = M[5], g = M[6], h = M[7], k = M[8];
+    double C00 = e * k - f * h, C01 = -(d * k - f * g), C02 = d * h - e * g;
+    double det = a * C00 + b * C01 + c * C02;
+    if (!(fabs(det) > 0.0) || !isfinite(det)) return -1;
+    double inv[9];
+    inv[0] = C00 / det;
+    inv[1] = -(b * k - c * h) / det;
+    inv[2] = (b * f - c * e) / det;
+    inv[3] = C01 / det;
+    inv[4] = (a * k - c * g) / det;
+    inv[5] = -(a * f - c * d) / det;
+    inv[6] = C02 / det;
+    inv[7] = -(a * h - b * g) / det;
+    inv[8] = (a * e - b * d) / det;
+    if (!(inv[8] > 0.0)) return -1;
+    for (int i = 0; i < 9; ++i) A[i] = inv[i] / inv[8];
+    A[8] = 1.0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* cameras and sampling                                                                        */
+
+typedef struct {
+    int W, H;
+    double A[9];
+    double gain;
+    const uint8_t* px;
+    int64_t pitch;
+} ocam;
+
+static inline double texel(const ocam* c, int x, int y, int ch) {
+    return (double)c->px[(int64_t)y * c->pitch + 3 * (int64_t)x + ch];
+}
+
+/* S1 + S2 at one canvas point.  rgb gets I_i, *wraw the un-normalised feather weight,
+ * *dist the distance (source px) to the border of the validity rectangle, or DBL_MAX when w<=0. */
+static void cam_sample(const ocam* c, double x, double y, double rgb[3], double* wraw, double* dist) {
+    const double* A = c->A;
+    double nu = A[0] * x + A[1] * y + A[2];
+    double nv = A[3] * x + A[4] * y + A[5];
+    double w = A[6] * x + A[7] * y + A[8];
+    if (!(w > 0.0)) {
+        rgb[0] = rgb[1] = rgb[2] = 0.0;
+        *wraw = 0.0;
+        if (dist) *dist = DBL_MAX;
+        return;
+    }
+    double u = nu / w, v = nv / w;
+    /* bilinear with coordinates clamped to the image (reading C2) */
+    double uc = u < 0.0 ? 0.0 : (u > c->W - 1 ? (double)(c->W - 1) : u);
+    double vc = v < 0.0 ? 0.0 : (v > c->H - 1 ? (double)(c->H - 1) : v);
+    int i0 = (int)floor(uc), j0 = (int)floor(vc);
+    double fx = uc - i0, fy = vc - j0;
+    int i1 = i0 + 1 < c->W ? i0 + 1 : i0;
+    int j1 = j0 + 1 < c->H ? j0 + 1 : j0;
+    for (int ch = 0; ch < 3; ++ch) {
+        double top = (1.0 - fx) * texel(c, i0, j0, ch) + fx * texel(c, i1, j0, ch);
+        double bot = (1.0 - fx) * texel(c, i0, j1, ch) + fx * texel(c, i1, j1, ch);
+        rgb[ch] = c->gain * ((1.0 - fy) * top + fy * bot) / 255.0;
+    }
+    int valid = (u >= -0.5) && (u < c->W - 0.5) && (v >= -0.5) && (v < c->H - 0.5);
+    double m = u + 0.5;
+    if (v + 0.5 < m) m = v + 0.5;
+    if (c->W - 0.5 - u < m) m = c->W - 0.5 - u;
+    if (c->H - 0.5 - v < m) m = c->H - 0.5 - v;
+    *wraw = valid ? (m > 0.0 ? m : 0.0) : 0.0;
+    if (dist) {
+        double dx = fmax(fmax(-0.5 - u, u - (c->W - 0.5)), 0.0);
+        double dy = fmax(fmax(-0.5 - v, v - (c->H - 0.5)), 0.0);
+        if (dx == 0.0 && dy == 0.0)
+            *dist = fmin(fmin(u + 0.5, c->W - 0.5 - u), fmin(v + 0.5, c->H - 0.5 - v));
+        else
+            *dist = hypot(dx, dy);
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* index intervals and level images                                                            */
+
+typedef struct {
+    int lo, hi; /* inclusive; empty when lo > hi */
+} ivl;
+
+static ivl ivl_union(ivl a, ivl b) {
+    if (a.lo > a.hi) return b;
+    if (b.lo > b.hi) return a;
+    ivl r = {a.lo < b.lo ? a.lo : b.lo, a.hi > b.hi ? a.hi : b.hi};
+    return r;
+}
+
+/* finer-grid indices read by REDUCE outputs k in `c` (finer size n) */
+static ivl reduce_support(ivl c, int n) {
+    ivl r = {INT_MAX, INT_MIN};
+    for (int k = c.lo; k <= c.hi; ++k)
+        for (int m = -2; m <= 2; ++m) {
+            int i = reflect101(2 * k + m, n);
+            if (i < r.lo) r.lo = i;
+            if (i > r.hi) r.hi = i;
+        }
+    return r;
+}
+
+/* coarser-grid indices read by EXPAND outputs x in `f` (coarser size n) */
+static ivl expand_support(ivl f, int n) {
+    ivl r = {INT_MAX, INT_MIN};
+    for (int x = f.lo; x <= f.hi; ++x)
+        for (int k = x / 2 - 2; k <= x / 2 + 2; ++k) {
+            int d = x - 2 * k;
+            if (d < -2 || d > 2) continue;
+            int i = reflect101(k, n);
+            if (i < r.lo) r.lo = i;
+            if (i > r.hi) r.hi = i;
+        }
+    return r;
+}
+
+typedef struct {
+    int x0, y0, w, h, ch;
+    double* d;
+} limg; /* image on a rectangle of one level, addressed by level coordinates */
+
+static int limg_alloc(limg* im, ivl xs, ivl ys, int ch) {
+    im->x0 = xs.lo;
+    im->y0 = ys.lo;
+    im->w = xs.hi - xs.lo + 1;
+    im->h = ys.hi - ys.lo + 1;
+    im->ch = ch;
+    im->d = (double*)calloc((size_t)im->w * im->h * ch, sizeof(double));
+    return im->d ? 0 : -1;
+}
+
+static inline double* limg_at(const limg* im, int x, int y) {
+    int lx = x - im->x0, ly = y - im->y0;
+    if (lx < 0 || ly < 0 || lx >= im->w || ly >= im->h) {
+        fprintf(stderr, "oracle: level access (%d,%d) outside [%d,%d)x[%d,%d)\n", x, y, im->x0,
+                im->x0 + im->w, im->y0, im->y0 + im->h);
+        abort();
+    }
+    return im->d + ((size_t)ly * im->w + lx) * im->ch;
+}
+
+/* S3: REDUCE of `in` (finer level of size nxf x nyf) onto out's rectangle, all channels */
+static void reduce_into(const limg* in, int nxf, int nyf, limg* out) {
+#pragma omp parallel for schedule(static)
+    for (int j = out->y0; j < out->y0 + out->h; ++j)
+        for (int k = out->x0; k < out->x0 + out->w; ++k) {
+            double* o = limg_at(out, k, j);
+            for (int c = 0; c < out->ch; ++c) o[c] = 0.0;
+            for (int n = -2; n <= 2; ++n) {
+                int yy = reflect101(2 * j + n, nyf);
+                for (int m = -2; m <= 2; ++m) {
+                    int xx = reflect101(2 * k + m, nxf);
+                    const double* s = limg_at(in, xx, yy);
+                    double wt = W5[m + 2] * W5[n + 2];
+                    for (int c = 0; c < out->ch; ++c) o[c] += wt * s[c];
+                }
+            }
+        }
+}
+
+/* S4: EXPAND of coarse image `in` (level size nxc x nyc) at fine (x, y); first `ch` channels */
+static void expand_at(const limg* in, int nxc, int nyc, int x, int y, int ch, double* o) {
+    for (int c = 0; c < ch; ++c) o[c] = 0.0;
+    for (int j = y / 2 - 2; j <= y / 2 + 2; ++j) {
+        int dy = y - 2 * j;
+        if (dy < -2 || dy > 2) continue;
+        int jj = reflect101(j, nyc);
+        for (int k = x / 2 - 2; k <= x / 2 + 2; ++k) {
+            int dx = x - 2 * k;
+            if (dx < -2 || dx > 2) continue;
+            int kk = reflect101(k, nxc);
+            const double* s = limg_at(in, kk, jj);
+            double wt = (2.0 * W5[dx + 2]) * (2.0 * W5[dy + 2]);
+            for (int c = 0; c < ch; ++c) o[c] += wt * s[c];
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* whole-image REDUCE / EXPAND (used by the pin tests)                                         */
+
+int oracle_reduce(const double* in, int w, int h, int ch, double* out) {
+    if (w < 1 || h < 1 || ch < 1) return OR_EINVAL;
+    int wc = (w + 1) / 2, hc = (h + 1) / 2;
+    limg a = {0, 0, w, h, ch, (double*)in}, b = {0, 0, wc, hc, ch, out};
+    reduce_into(&a, w, h, &b);
+    return OR_OK;
+}
+
+int oracle_expand(const double* in, int wc, int hc, int ch, int w, int h, double* out) {
+    if (w < 1 || h < 1 || ch < 1 || wc != (w + 1) / 2 || hc != (h + 1) / 2) return OR_EINVAL;
+    limg a = {0, 0, wc, hc, ch, (double*)in};
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) expand_at(&a, wc, hc, x, y, ch, out + ((size_t)y * w + x) * ch);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* forward                                                                                     */
+
+static int setup_cams(int n, const int32_t* Ws, const int32_t* Hs, const double* Ms, const double* gains,
+                      const uint8_t* const* frames, const int64_t* pitches, ocam* cams) {
+    for (int i = 0; i < n; ++i) {
+        if (Ws[i] < 1 || Hs[i] < 1 || !frames[i] || pitches[i] < 3LL * Ws[i]) return OR_EINVAL;
+        cams[i].W = Ws[i];
+        cams[i].H = Hs[i];
+        if (oracle_invert_h(Ms + 9 * i, cams[i].A) != 0) return OR_EINVAL;
+        cams[i].gain = gains ? gains[i] : 1.0;
+        cams[i].px = frames[i];
+        cams[i].pitch = pitches[i];
+    }
+    return OR_OK;
+}
+
+/* Per-level rectangles of the forward pass for an output window: X_l (output dependency)
+ * and Y_l (pyramid region).  Arrays of length L, level coordinates, inclusive bounds. */
+static void forward_regions(int Wc, int Hc, int L, int wx0, int wy0, int ww, int wh, int* nx, int* ny,
+                            ivl* Xx, ivl* Xy, ivl* Yx, ivl* Yy) {
+    nx[0] = Wc;
+    ny[0] = Hc;
+    for (int l = 1; l < L; ++l) {
+        nx[l] = (nx[l - 1] + 1) / 2;
+        ny[l] = (ny[l - 1] + 1) / 2;
+    }
+    Xx[0].lo = wx0; Xx[0].hi = wx0 + ww - 1;
+    Xy[0].lo = wy0; Xy[0].hi = wy0 + wh - 1;
+    for (int l = 0; l + 1 < L; ++l) {
+        Xx[l + 1] = expand_support(Xx[l], nx[l + 1]);
+        Xy[l + 1] = expand_support(Xy[l], ny[l + 1]);
+    }
+    Yx[L - 1] = Xx[L - 1];
+    Yy[L - 1] = Xy[L - 1];
+    for (int l = L - 2; l >= 0; --l) {
+        Yx[l] = ivl_union(Xx[l], reduce_support(Yx[l + 1], nx[l]));
+        Yy[l] = ivl_union(Xy[l], reduce_support(Yy[l + 1], ny[l]));
+    }
+}
+
+/* Rectangles (x0, x1_exclusive, y0, y1_exclusive) of X_l and Y_l for each level: 8*L ints. */
+int oracle_regions(int Wc, int Hc, int L, int wx0, int wy0, int ww, int wh, int32_t* out) {
+    if (L < 1 || L > 24 || Wc < 1 || Hc < 1 || ww < 1 || wh < 1 || wx0 < 0 || wy0 < 0 || wx0 + ww > Wc ||
+        wy0 + wh > Hc)
+        return OR_EINVAL;
+    int nx[24], ny[24];
+    ivl Xx[24], Xy[24], Yx[24], Yy[24];
+    forward_regions(Wc, Hc, L, wx0, wy0, ww, wh, nx, ny, Xx, Xy, Yx, Yy);
+    for (int l = 0; l < L; ++l) {
+        int32_t* o = out + 8 * l;
+        o[0] = Xx[l].lo; o[1] = Xx[l].hi + 1; o[2] = Xy[l].lo; o[3] = Xy[l].hi + 1;
+        o[4] = Yx[l].lo; o[5] = Yx[l].hi + 1; o[6] = Yy[l].lo; o[7] = Yy[l].hi + 1;
+    }
+    return OR_OK;
+}
+
+/*
+ * The whole stitching path (S1-S6) on the output window [wx0, wx0+ww) x [wy0, wy0+wh).
+ *   out      ww*wh*3 doubles, [0,1] canvas after mask and clamp (may be NULL)
+ *   out_u8   ww*wh*3 bytes (may be NULL)
+ *   mindist  ww*wh doubles: min over cameras of the distance (source px) from (u, v) to the
+ *            border of the validity rectangle (may be NULL)
+ *   dbg_S, dbg_B  optional arrays of L pointers; level l receives S^l (1 ch) / B^l (3 ch) on
+ *            the X_l rectangle reported by oracle_regions.
+ */
+int oracle_forward(int n, const int32_t* Ws, const int32_t* Hs, const double* Ms, const double* gains,
+                   const uint8_t* const* frames, const int64_t* pitches, int Wc, int Hc, int L, int wx0,
+                   int wy0, int ww, int wh, double* out, uint8_t* out_u8, double* mindist, double** dbg_S,
+                   double** dbg_B) {
+    if (n < 1 || n > 64 || L < 1 || L > 24 || Wc < 1 || Hc < 1 || ww < 1 || wh < 1 || wx0 < 0 || wy0 < 0 ||
+        wx0 + ww > Wc || wy0 + wh > Hc)
+        return OR_EINVAL;
+    ocam cams[64];
+    int rc = setup_cams(n, Ws, Hs, Ms, gains, frames, pitches, cams);
+    if (rc) return rc;
+
+    int nx[24], ny[24];
+    ivl Xx[24], Xy[24], Yx[24], Yy[24];
+    forward_regions(Wc, Hc, L, wx0, wy0, ww, wh, nx, ny, Xx, Xy, Yx, Yy);
+
+    limg Nl[24], Sl[24], G[24], wsum;
+    memset(Nl, 0, sizeof(Nl));
+    memset(Sl, 0, sizeof(Sl));
+    memset(G, 0, sizeof(G));
+    memset(&wsum, 0, sizeof(wsum));
+    rc = OR_ENOMEM;
+    for (int l = 0; l < L; ++l)
+        if (limg_alloc(&Nl[l], Xx[l], Xy[l], 3) || limg_alloc(&Sl[l], Xx[l], Xy[l], 1) ||
+            limg_alloc(&G[l], Yx[l], Yy[l], 4))
+            goto done;
+    if (limg_alloc(&wsum, Yx[0], Yy[0], 1)) goto done;
+
+    /* S2 denominator: sum of raw feather weights at level 0 */
+#pragma omp parallel for schedule(static)
+    for (int y = Yy[0].lo; y <= Yy[0].hi; ++y)
+        for (int x = Yx[0].lo; x <= Yx[0].hi; ++x) {
+            double s = 0.0, rgb[3], wr;
+            for (int i = 0; i < n; ++i) {
+                cam_sample(&cams[i], x, y, rgb, &wr, NULL);
+                s += wr;
+            }
+            *limg_at(&wsum, x, y) = s;
+        }
+
+    for (int i = 0; i < n; ++i) {
+        /* S1 + S2: level 0 of camera i (image and normalised weight) */
+#pragma omp parallel for schedule(static)
+        for (int y = Yy[0].lo; y <= Yy[0].hi; ++y)
+            for (int x = Yx[0].lo; x <= Yx[0].hi; ++x) {
+                double rgb[3], wr;
+                cam_sample(&cams[i], x, y, rgb, &wr, NULL);
+                double s = *limg_at(&wsum, x, y);
+                double* g = limg_at(&G[0], x, y);
+                g[0] = rgb[0];
+                g[1] = rgb[1];
+                g[2] = rgb[2];
+                g[3] = s > 0.0 ? wr / s : 0.0;
+            }
+        /* S3: Gaussian pyramids of image and weight */
+        for (int l = 0; l + 1 < L; ++l) reduce_into(&G[l], nx[l], ny[l], &G[l + 1]);
+        /* S4 + S5 numerator and denominator */
+        for (int l = 0; l < L; ++l) {
+#pragma omp parallel for schedule(static)
+            for (int y = Xy[l].lo; y <= Xy[l].hi; ++y)
+                for (int x = Xx[l].lo; x <= Xx[l].hi; ++x) {
+                    const double* g = limg_at(&G[l], x, y);
+                    double lap[3] = {g[0], g[1], g[2]};
+                    if (l + 1 < L) {
+                        double e[3];
+                        expand_at(&G[l + 1], nx[l + 1], ny[l + 1], x, y, 3, e);
+                        for (int c = 0; c < 3; ++c) lap[c] -= e[c];
+                    }
+                    double* nn = limg_at(&Nl[l], x, y);
+                    for (int c = 0; c < 3; ++c) nn[c] += g[3] * lap[c];
+                    *limg_at(&Sl[l], x, y) += g[3];
+                }
+        }
+    }
+
+    /* S5: B^l = N^l / S^l (kept in Nl), then S6 collapse from the coarsest level (kept in Nl) */
+    for (int l = 0; l < L; ++l) {
+        if (dbg_S && dbg_S[l]) memcpy(dbg_S[l], Sl[l].d, sizeof(double) * (size_t)Sl[l].w * Sl[l].h);
+#pragma omp parallel for schedule(static)
+        for (int y = Xy[l].lo; y <= Xy[l].hi; ++y)
+            for (int x = Xx[l].lo; x <= Xx[l].hi; ++x) {
+                double s = *limg_at(&Sl[l], x, y);
+                double* nn = limg_at(&Nl[l], x, y);
+                for (int c = 0; c < 3; ++c) nn[c] = s > 1e-12 ? nn[c] / s : 0.0;
+            }
+        if (dbg_B && dbg_B[l]) memcpy(dbg_B[l], Nl[l].d, sizeof(double) * 3 * (size_t)Nl[l].w * Nl[l].h);
+    }
+    for (int l = L - 2; l >= 0; --l) {
+#pragma omp parallel for schedule(static)
+        for (int y = Xy[l].lo; y <= Xy[l].hi; ++y)
+            for (int x = Xx[l].lo; x <= Xx[l].hi; ++x) {
+                double e[3];
+                expand_at(&Nl[l + 1], nx[l + 1], ny[l + 1], x, y, 3, e);
+                double* r = limg_at(&Nl[l], x, y);
+                for (int c = 0; c < 3; ++c) r[c] += e[c];
+            }
+    }
+
+    /* output: mask by coverage, clamp, quantise */
+#pragma omp parallel for schedule(static)
+    for (int y = wy0; y < wy0 + wh; ++y)
+        for (int x = wx0; x < wx0 + ww; ++x) {
+            size_t o = (size_t)(y - wy0) * ww + (x - wx0);
+            int covered = *limg_at(&wsum, x, y) > 0.0;
+            const double* r = limg_at(&Nl[0], x, y);
+            for (int c = 0; c < 3; ++c) {
+                double v = covered ? (r[c] < 0.0 ? 0.0 : (r[c] > 1.0 ? 1.0 : r[c])) : 0.0;
+                if (out) out[3 * o + c] = v;
+                if (out_u8) out_u8[3 * o + c] = (uint8_t)nearbyint(255.0 * v);
+            }
+            if (mindist) {
+                double md = DBL_MAX, rgb[3], wr, d;
+                for (int i = 0; i < n; ++i) {
+                    cam_sample(&cams[i], x, y, rgb, &wr, &d);
+                    if (d < md) md = d;
+                }
+                mindist[o] = md;
+            }
+        }
+    rc = OR_OK;
+done:
+    for (int l = 0; l < L; ++l) {
+        free(Nl[l].d);
+        free(Sl[l].d);
+        free(G[l].d);
+    }
+    free(wsum.d);
+    return rc;
+}
+
+/*
+ * Level 0 of one camera on the whole canvas: I_i (3 ch), raw feather weight and validity.
+ * img: Hc*Wc*3 doubles, wraw: Hc*Wc doubles (either may be NULL).
+ */
+int oracle_warp(int W, int H, const double* M, double gain, const uint8_t* frame, int64_t pitch, int Wc,
+                int Hc, double* img, double* wraw) {
+    ocam c;
+    int32_t Ws = W, Hs = H;
+    if (setup_cams(1, &Ws, &Hs, M, &gain, &frame, &pitch, &c)) return OR_EINVAL;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < Hc; ++y)
+        for (int x = 0; x < Wc; ++x) {
+            double rgb[3], wr;
+            cam_sample(&c, x, y, rgb, &wr, NULL);
+            size_t o = (size_t)y * Wc + x;
+            if (img) {
+                img[3 * o] = rgb[0];
+                img[3 * o + 1] = rgb[1];
+                img[3 * o + 2] = rgb[2];
+            }
+            if (wraw) wraw[o] = wr;
+        }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* S7: overlap photometric loss and its analytic gradient                                      */
+
+typedef struct {
+    double I[3], dIu[3], dIv[3], u, v, w, B[3];
+    int ok;
+} gsample;
+
+/* I = gain * bilinear / 255 with clamped coordinates, and dI/du, dI/dv (zero on a clamped axis). */
+static void grad_sample(const int W, const int H, const uint8_t* px, int64_t pitch, const double* p, double x,
+                        double y, gsample* s) {
+    double nu = p[0] * x + p[1] * y + p[2];
+    double nv = p[3] * x + p[4] * y + p[5];
+    double w = p[6] * x + p[7] * y + 1.0;
+    memset(s, 0, sizeof(*s));
+    if (!(w > 0.0)) return;
+    s->ok = 1;
+    s->w = w;
+    s->u = nu / w;
+    s->v = nv / w;
+    int cu = s->u < 0.0 || s->u > W - 1, cv = s->v < 0.0 || s->v > H - 1;
+    double uc = s->u < 0.0 ? 0.0 : (s->u > W - 1 ? (double)(W - 1) : s->u);
+    double vc = s->v < 0.0 ? 0.0 : (s->v > H - 1 ? (double)(H - 1) : s->v);
+    int i0 = (int)floor(uc), j0 = (int)floor(vc);
+    double fx = uc - i0, fy = vc - j0;
+    int i1 = i0 + 1 < W ? i0 + 1 : i0;
+    int j1 = j0 + 1 < H ? j0 + 1 : j0;
+    double g = p[8];
+    for (int c = 0; c < 3; ++c) {
+        double p00 = px[(int64_t)j0 * pitch + 3 * i0 + c], p01 = px[(int64_t)j0 * pitch + 3 * i1 + c];
+        double p10 = px[(int64_t)j1 * pitch + 3 * i0 + c], p11 = px[(int64_t)j1 * pitch + 3 * i1 + c];
+        double top = (1.0 - fx) * p00 + fx * p01, bot = (1.0 - fx) * p10 + fx * p11;
+        s->B[c] = ((1.0 - fy) * top + fy * bot) / 255.0;
+        s->I[c] = g * s->B[c];
+        s->dIu[c] = cu ? 0.0 : g * ((1.0 - fy) * (p01 - p00) + fy * (p11 - p10)) / 255.0;
+        s->dIv[c] = cv ? 0.0 : g * ((1.0 - fx) * (p10 - p00) + fx * (p11 - p01)) / 255.0;
+    }
+}
+
+static int mask_valid(int W, int H, const double* p, double x, double y) {
+    double nu = p[0] * x + p[1] * y + p[2];
+    double nv = p[3] * x + p[4] * y + p[5];
+    double w = p[6] * x + p[7] * y + 1.0;
+    if (!(w > 0.0)) return 0;
+    double u = nu / w, v = nv / w;
+    return (u >= -0.5) && (u < W - 0.5) && (v >= -0.5) && (v < H - 0.5);
+}
+
+/*
+ * params: n*9 doubles per camera (a11 a12 a13 a21 a22 a23 a31 a32 gain), a33 = 1, A maps canvas
+ * to camera.  mask_params: same layout, used only for the validity masks (NULL: params).
+ * Window [x0,x0+w) x [y0,y0+h) of the canvas.  loss: 1 double; grad: n*9 doubles (may be NULL).
+ * Rows are summed independently and then added in row order, so the result does not depend on
+ * the number of threads.
+ */
+int oracle_loss_grad(int n, const int32_t* Ws, const int32_t* Hs, const double* params, const double* mask_params,
+                     const uint8_t* const* frames, const int64_t* pitches, int x0, int y0, int w, int h,
+                     double* loss, double* grad) {
+    if (n < 1 || n > 64 || w < 0 || h < 0 || !loss) return OR_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (Ws[i] < 1 || Hs[i] < 1 || !frames[i] || pitches[i] < 3LL * Ws[i]) return OR_EINVAL;
+    const double* mp = mask_params ? mask_params : params;
+    int stride = 1 + 9 * n;
+    double* rows = (double*)calloc((size_t)(h > 0 ? h : 1) * stride, sizeof(double));
+    if (!rows) return OR_ENOMEM;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int yy = 0; yy < h; ++yy) {
+        double* acc = rows + (size_t)yy * stride;
+        double y = (double)(y0 + yy);
+        gsample s[64];
+        int val[64];
+        for (int xx = 0; xx < w; ++xx) {
+            double x = (double)(x0 + xx);
+            int k = 0;
+            for (int i = 0; i < n; ++i) {
+                val[i] = mask_valid(Ws[i], Hs[i], mp + 9 * i, x, y);
+                k += val[i];
+            }
+            if (k < 2) continue;
+            for (int i = 0; i < n; ++i)
+                if (val[i]) grad_sample(Ws[i], Hs[i], frames[i], pitches[i], params + 9 * i, x, y, &s[i]);
+            for (int i = 0; i < n; ++i) {
+                if (!val[i]) continue;
+                for (int j = i + 1; j < n; ++j) {
+                    if (!val[j]) continue;
+                    for (int c = 0; c < 3; ++c) {
+                        double d = s[i].I[c] - s[j].I[c];
+                        acc[0] += d * d;
+                    }
+                }
+                if (!grad || !s[i].ok) continue;
+                double gu = 0.0, gv = 0.0, gg = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    double r = 0.0;
+                    for (int j = 0; j < n; ++j)
+                        if (j != i && val[j]) r += s[i].I[c] - s[j].I[c];
+                    gu += 2.0 * r * s[i].dIu[c];
+                    gv += 2.0 * r * s[i].dIv[c];
+                    gg += 2.0 * r * s[i].B[c];
+                }
+                double iw = 1.0 / s[i].w;
+                double* gi = acc + 1 + 9 * i;
+                gi[0] += gu * x * iw;
+                gi[1] += gu * y * iw;
+                gi[2] += gu * iw;
+                gi[3] += gv * x * iw;
+                gi[4] += gv * y * iw;
+                gi[5] += gv * iw;
+                double q = gu * s[i].u + gv * s[i].v;
+                gi[6] += -q * x * iw;
+                gi[7] += -q * y * iw;
+                gi[8] += gg;
+            }
+        }
+    }
+    double L = 0.0;
+    if (grad) memset(grad, 0, sizeof(double) * 9 * (size_t)n);
+    for (int yy = 0; yy < h; ++yy) {
+        const double* acc = rows + (size_t)yy * stride;
+        L += acc[0];
+        if (grad)
+            for (int k = 0; k < 9 * n; ++k) grad[k] += acc[1 + k];
+    }
+    *loss = L;
+    free(rows);
+    return OR_OK;
+}

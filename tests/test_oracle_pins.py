@@ -1,0 +1,375 @@
+"""Pins of the FP64 oracle against facts fixed independently of its code (CPU only).
+
+Each test names the property it checks.  The paper prints no worked example and no intermediate
+values for the stitching path, so the pins are closed forms of the operators, invariants of the
+method (identity, integer translation, telescoping collapse, constants, weights summing to one),
+an independent dense-matrix formulation on tiny sizes, and finite differences for the gradient.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from synth import Camera
+from tests import dense_ref
+
+RNG = np.random.default_rng(12345)
+
+
+def _T(tx, ty):
+    return np.array([[1.0, 0, tx], [0, 1.0, ty], [0, 0, 1.0]])
+
+
+def _rand_frame(h, w, seed=0):
+    return np.random.default_rng(seed).integers(0, 256, (h, w, 3), dtype=np.uint8)
+
+
+# ---------------------------------------------------------------------------------------------
+# P6: closed forms of REDUCE / EXPAND
+
+
+def test_reduce_impulse_response_polyphase():
+    """An impulse at an even fine index 2a reduces to (1,6,1)/16 per axis around a; at an odd
+    index 2a+1 to (4,4)/16 on a, a+1 (columns of the REDUCE operator)."""
+    n = 21
+    for a in (4, 5):
+        img = np.zeros((n, n))
+        img[2 * a, 2 * a + 1] = 1.0
+        out = oracle.reduce(img)
+        ey = np.zeros(11); ey[a - 1:a + 2] = [1 / 16, 6 / 16, 1 / 16]
+        ex = np.zeros(11); ex[a:a + 2] = [4 / 16, 4 / 16]
+        np.testing.assert_allclose(out, np.outer(ey, ex), atol=1e-15)
+
+
+def test_reduce_row_is_5tap_kernel():
+    """Output k of REDUCE weighs fine samples 2k-2..2k+2 by [1,4,6,4,1]/16 (a row of the operator)."""
+    n = 19
+    k = 4
+    row = np.zeros(n)
+    for i in range(n):
+        img = np.zeros((1, n))
+        img[0, i] = 1.0
+        row[i] = oracle.reduce(img)[0, k]
+    expect = np.zeros(n)
+    expect[2 * k - 2:2 * k + 3] = np.array([1, 4, 6, 4, 1]) / 16
+    np.testing.assert_allclose(row, expect, atol=1e-15)
+
+
+def test_expand_impulse_is_kernel_times_two():
+    """A coarse impulse at k expands to (1,4,6,4,1)/8 on fine 2k-2..2k+2 per axis."""
+    img = np.zeros((9, 9))
+    img[4, 3] = 1.0
+    out = oracle.expand(img, (17, 17))
+    ey = np.zeros(17); ey[6:11] = np.array([1, 4, 6, 4, 1]) / 8
+    ex = np.zeros(17); ex[4:9] = np.array([1, 4, 6, 4, 1]) / 8
+    np.testing.assert_allclose(out, np.outer(ey, ex), atol=1e-15)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 7), (2, 2), (5, 3), (8, 9), (16, 33)])
+def test_constants_preserved(shape):
+    """REDUCE and EXPAND preserve constants everywhere, borders included (reflect-101)."""
+    img = np.full(shape + (3,), 0.37)
+    r = oracle.reduce(img)
+    np.testing.assert_allclose(r, 0.37, atol=1e-15)
+    np.testing.assert_allclose(oracle.expand(r, shape), 0.37, atol=1e-15)
+
+
+def test_linear_ramp_interior_and_border_values():
+    """Away from borders a ramp f(x)=x reduces to f(2k) and a coarse ramp g(k)=k expands to x/2.
+    At the border reflect-101 gives G(0) = (2+4+0+4+2)/16 = 0.75 (plain reflection would give 7/16)."""
+    n = 32
+    img = np.tile(np.arange(n, dtype=np.float64), (3, 1))
+    r = oracle.reduce(img)
+    np.testing.assert_allclose(r[1, 1:-1], 2.0 * np.arange(1, 15), atol=1e-13)
+    assert abs(r[1, 0] - 0.75) < 1e-15
+    g = np.tile(np.arange(16, dtype=np.float64), (3, 1))
+    e = oracle.expand(g, (5, 32))
+    np.testing.assert_allclose(e[2, 2:-2], np.arange(2, 30) / 2.0, atol=1e-13)
+    # fine x=0: taps k=-1 (->1) weight 1/8, k=0 weight 6/8, k=1 weight 1/8 -> 2/8
+    assert abs(e[2, 0] - 0.25) < 1e-15
+
+
+# ---------------------------------------------------------------------------------------------
+# P7: dense-matrix brute force on tiny sizes
+
+
+@pytest.mark.parametrize("h,w", [(1, 1), (1, 2), (2, 1), (3, 3), (4, 5), (7, 9), (9, 7), (6, 8), (17, 33)])
+def test_reduce_expand_match_dense_matrices(h, w):
+    img = RNG.standard_normal((h, w, 4))
+    np.testing.assert_allclose(oracle.reduce(img), dense_ref.reduce2d(img), atol=1e-13)
+    c = RNG.standard_normal(((h + 1) // 2, (w + 1) // 2, 3))
+    np.testing.assert_allclose(oracle.expand(c, (h, w)), dense_ref.expand2d(c, (h, w)), atol=1e-13)
+
+
+# ---------------------------------------------------------------------------------------------
+# P3: collapse of an unblended Laplacian pyramid reconstructs the image (telescoping)
+
+
+@pytest.mark.parametrize("h,w,L", [(1, 1, 3), (13, 7, 3), (40, 64, 4), (37, 91, 6)])
+def test_collapse_of_laplacian_is_identity(h, w, L):
+    img = RNG.uniform(0, 1, (h, w, 3))
+    np.testing.assert_allclose(oracle.collapse(oracle.laplacian_pyramid(img, L)), img, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------------
+# warp (S1) and feather weight (S2)
+
+
+def test_identity_homography_reproduces_input():
+    """P1: one camera, canvas = image, M = I: float output = frame/255, u8 output == frame."""
+    for (h, w, L) in [(23, 37, 3), (48, 64, 4), (1, 1, 1), (5, 2, 2)]:
+        fr = _rand_frame(h, w, seed=h)
+        cam = Camera(w, h, np.eye(3))
+        r = oracle.forward([cam], [fr], w, h, L)
+        np.testing.assert_allclose(r["out"], fr / 255.0, atol=1e-12)
+        assert np.array_equal(r["u8"], fr)
+
+
+def test_integer_translation_warp_is_exact_shift():
+    """P2 (level 0): M = T(tx, ty) samples frame[y-ty, x-tx] exactly; outside the image the value
+    is the clamped edge texel and the raw weight is 0."""
+    fr = _rand_frame(11, 17, 3)
+    tx, ty = 5, -3
+    cam = Camera(17, 11, _T(tx, ty))
+    img, wr = oracle.warp(cam, fr, 30, 12)
+    for y in range(12):
+        for x in range(30):
+            u, v = x - tx, y - ty
+            uc, vc = min(max(u, 0), 16), min(max(v, 0), 10)
+            np.testing.assert_array_equal(img[y, x], fr[vc, uc] / 255.0)
+            inside = 0 <= u < 17 and 0 <= v < 11
+            assert (wr[y, x] > 0) == inside
+
+
+def test_integer_translation_full_path_exact_when_covered():
+    """P2 (whole path): a translated camera covering the whole canvas reproduces the shifted
+    frame exactly."""
+    fr = _rand_frame(40, 60, 4)
+    cam = Camera(60, 40, _T(-7, -5))
+    r = oracle.forward([cam], [fr], 45, 29, 4)
+    assert np.array_equal(r["u8"], fr[5:34, 7:52])
+    np.testing.assert_allclose(r["out"], fr[5:34, 7:52] / 255.0, atol=1e-12)
+
+
+def test_half_pixel_translation_is_neighbour_average():
+    """Bilinear at a half-pixel offset is the mean of the two neighbours (closed form)."""
+    fr = _rand_frame(6, 9, 5)
+    cam = Camera(9, 6, _T(0.5, 0.0))
+    img, _ = oracle.warp(cam, fr, 9, 6)
+    np.testing.assert_allclose(img[:, 1:9], (fr[:, 0:8].astype(float) + fr[:, 1:9]) / 2 / 255.0, atol=1e-15)
+    np.testing.assert_allclose(img[:, 0], fr[:, 0] / 255.0, atol=1e-15)  # u=-0.5 clamps to texel 0
+
+
+def test_feather_weight_distance_to_border():
+    """Raw weight = distance (source px) to the nearest image border, measured to the outer
+    pixel edge: 0.5 on the border pixels, k+0.5 on ring k, 0 outside."""
+    W, H = 9, 7
+    cam = Camera(W, H, _T(2, 1))
+    _, wr = oracle.warp(cam, np.zeros((H, W, 3), np.uint8), 14, 10)
+    for y in range(10):
+        for x in range(14):
+            u, v = x - 2, y - 1
+            if 0 <= u < W and 0 <= v < H:
+                ring = min(u, v, W - 1 - u, H - 1 - v)
+                assert wr[y, x] == ring + 0.5
+            else:
+                assert wr[y, x] == 0.0
+
+
+def test_gain_scales_and_output_clamps():
+    fr = np.full((8, 8, 3), 200, np.uint8)
+    cam = Camera(8, 8, np.eye(3), gain=2.0)
+    r = oracle.forward([cam], [fr], 8, 8, 3)
+    assert np.all(r["out"] == 1.0) and np.all(r["u8"] == 255)
+    cam.gain = 0.5
+    r = oracle.forward([cam], [fr], 8, 8, 3)
+    np.testing.assert_allclose(r["out"], 100 / 255.0, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------------
+# P4 / P5: constants and weights
+
+
+def test_constant_inputs_blend_to_the_constant():
+    """P4: every camera shows the same constant -> output is that constant on every covered pixel
+    and 0 where no camera is valid."""
+    cfg = synth.config_2cam(scale=0.25)
+    frames = [np.full((c.height, c.width, 3), (37, 180, 255), np.uint8) for c in cfg.cameras]
+    r = oracle.forward(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h, 4)
+    covered = np.zeros((cfg.canvas_h, cfg.canvas_w), bool)
+    for c in cfg.cameras:
+        covered |= oracle.warp(c, frames[0], cfg.canvas_w, cfg.canvas_h)[1] > 0
+    assert covered.any() and (~covered).any()
+    got = r["out"][covered]
+    np.testing.assert_allclose(got, np.broadcast_to(np.array([37, 180, 255]) / 255.0, got.shape), atol=1e-12)
+    assert np.all(r["out"][~covered] == 0.0)
+
+
+def test_weights_sum_to_one_at_every_level():
+    """P5: S^0 = sum_i What_i is 1 on covered pixels and 0 elsewhere, and S^l equals the l-fold
+    REDUCE of the coverage indicator (dense-matrix formulation)."""
+    cfg = synth.config_2cam(scale=0.2)
+    frames = cfg.frame(0)
+    L = 4
+    r = oracle.forward(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h, L, debug=True)
+    covered = np.zeros((cfg.canvas_h, cfg.canvas_w))
+    for c, f in zip(cfg.cameras, frames):
+        covered = np.maximum(covered, (oracle.warp(c, f, cfg.canvas_w, cfg.canvas_h)[1] > 0).astype(float))
+    g = dense_ref.gaussian(covered, L)
+    for l in range(L):
+        x0, x1, y0, y1 = r["regions"][l][:4]
+        assert (x0, y0) == (0, 0) and (x1, y1) == (g[l].shape[1], g[l].shape[0])
+        np.testing.assert_allclose(r["S"][l], g[l], atol=1e-13)
+
+
+def test_two_identical_cameras_average_their_frames():
+    """Two cameras with the same homography get What = 1/2 each at every level, so two constant
+    frames a and b blend to (a+b)/2, and equal frames reproduce the single-camera result."""
+    M = synth.rig_planar(32, 24, 30.0, [5.0], 40, 30)[0]
+    cams = [Camera(32, 24, M), Camera(32, 24, M)]
+    fa = np.full((24, 32, 3), 40, np.uint8)
+    fb = np.full((24, 32, 3), 200, np.uint8)
+    r = oracle.forward(cams, [fa, fb], 40, 30, 3)
+    _, wr = oracle.warp(cams[0], fa, 40, 30)
+    cov = wr > 0
+    np.testing.assert_allclose(r["out"][cov], 120 / 255.0, atol=1e-12)
+    fr = _rand_frame(24, 32, 9)
+    r2 = oracle.forward(cams, [fr, fr], 40, 30, 3)
+    r1 = oracle.forward(cams[:1], [fr], 40, 30, 3)
+    np.testing.assert_allclose(r2["out"], r1["out"], atol=1e-12)
+
+
+def test_two_constant_cameras_blend_by_coarsest_weight_pyramid():
+    """Constant frames a (camera A) and b (camera B) have zero Laplacian bands below the top, so
+    the blend is the top-level weight mix expanded back: out = E^{L-1}(G^{L-1}(WA) a + G^{L-1}(WB) b)
+    / E^{L-1}(S^{L-1}) reduces, with S = 1 everywhere, to E^{L-1}(G^{L-1}(WA)) (a - b) + b.
+    Expected values come from the dense-matrix operators."""
+    Wc, Hc, L = 48, 20, 3
+    ca = Camera(30, 20, _T(0, 0))   # covers x in [0, 30)
+    cb = Camera(30, 20, _T(18, 0))  # covers x in [18, 48)
+    fa = np.full((20, 30, 3), 60, np.uint8)
+    fb = np.full((20, 30, 3), 220, np.uint8)
+    r = oracle.forward([ca, cb], [fa, fb], Wc, Hc, L)
+    _, wa = oracle.warp(ca, fa, Wc, Hc)
+    _, wb = oracle.warp(cb, fb, Wc, Hc)
+    What_a = np.where(wa + wb > 0, wa / np.where(wa + wb > 0, wa + wb, 1), 0)
+    g = dense_ref.gaussian(What_a, L)
+    top = g[-1]
+    e = top
+    shapes = [dense_ref.gaussian(np.zeros((Hc, Wc)), L)[l].shape for l in range(L)]
+    for l in range(L - 2, -1, -1):
+        e = dense_ref.expand2d(e, shapes[l])
+    expect = e * (60 / 255.0) + (1 - e) * (220 / 255.0)
+    np.testing.assert_allclose(r["out"][:, :, 0], expect, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------------------------
+# regions / windows
+
+
+def test_window_is_bit_identical_to_full_canvas():
+    cfg = synth.config_2cam(scale=0.3)
+    frames = cfg.frame(0)
+    full = oracle.forward(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h, 4)
+    for win in [(0, 0, 17, 9), (cfg.canvas_w - 23, cfg.canvas_h - 11, 23, 11), (101, 37, 64, 40)]:
+        x0, y0, w, h = win
+        part = oracle.forward(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h, 4, window=win)
+        assert np.array_equal(part["out"], full["out"][y0:y0 + h, x0:x0 + w])
+        assert np.array_equal(part["u8"], full["u8"][y0:y0 + h, x0:x0 + w])
+
+
+# ---------------------------------------------------------------------------------------------
+# S7: loss and gradient
+
+
+def _params_of(cams, gains=None):
+    ps = []
+    for i, c in enumerate(cams):
+        A = oracle.invert_h(c.H).reshape(9)
+        ps.append(np.r_[A[:8], 1.0 if gains is None else gains[i]])
+    return np.array(ps)
+
+
+def test_loss_closed_form_for_constant_frames():
+    """Constant frames c_A, c_B with gains g_A, g_B: loss = K * 3 * (g_A c_A - g_B c_B)^2 / 255^2,
+    K = number of canvas pixels valid in both."""
+    ca = Camera(20, 10, _T(0, 0))
+    cb = Camera(20, 10, _T(12, 3))
+    fa = np.full((10, 20, 3), 100, np.uint8)
+    fb = np.full((10, 20, 3), 30, np.uint8)
+    p = _params_of([ca, cb], [0.9, 1.3])
+    loss, g = oracle.loss_grad([20, 20], [10, 10], p, [fa, fb], (0, 0, 32, 13))
+    K = 8 * 7
+    assert abs(loss - K * 3 * (0.9 * 100 - 1.3 * 30) ** 2 / 255.0 ** 2) < 1e-10
+    # the gain gradients have the closed form 2 * sum r * I / g
+    dA = 0.9 * 100 / 255.0 - 1.3 * 30 / 255.0
+    assert abs(g[0, 8] - K * 3 * 2 * dA * 100 / 255.0) < 1e-9
+    assert abs(g[1, 8] + K * 3 * 2 * dA * 30 / 255.0) < 1e-9
+    # constant frames: no spatial gradient
+    assert np.all(np.abs(g[:, :8]) < 1e-12)
+
+
+def _fd_check(cfg, frames, window, rel_eps=1e-7, tol=2e-5):
+    n = len(cfg.cameras)
+    p0 = _params_of(cfg.cameras, [1.0 + 0.05 * i for i in range(n)])
+    # move every camera off the true alignment a little so residuals are not ~0
+    p0[:, 2] += 0.37
+    p0[:, 5] -= 0.21
+    loss, g = oracle.loss_grad([c.width for c in cfg.cameras], [c.height for c in cfg.cameras], p0, frames,
+                               window)
+    # the spatial parts must be populated, otherwise the check below is vacuous
+    assert np.all(np.abs(g[:, :8]).max(axis=1) > 1e-3 * np.abs(g).max())
+    Ws = [c.width for c in cfg.cameras]
+    Hs = [c.height for c in cfg.cameras]
+    for i in range(n):
+        for k in range(9):
+            h = rel_eps * max(abs(p0[i, k]), 1e-3 if k < 6 else 1e-7)
+            pp = p0.copy(); pp[i, k] += h
+            pm = p0.copy(); pm[i, k] -= h
+            lp, _ = oracle.loss_grad(Ws, Hs, pp, frames, window, mask_params=p0, grad=False)
+            lm, _ = oracle.loss_grad(Ws, Hs, pm, frames, window, mask_params=p0, grad=False)
+            fd = (lp - lm) / (2 * h)
+            scale = max(abs(g[i, k]), 1e-3 * np.abs(g[i]).max())
+            assert abs(fd - g[i, k]) <= tol * scale, (i, k, fd, g[i, k])
+    return loss, g
+
+
+def test_gradient_matches_central_differences():
+    """P8: analytic gradient vs central differences with frozen masks (tiny relative steps keep the
+    difference inside one bilinear cell almost everywhere)."""
+    cfg = synth.config_2cam(scale=0.15)
+    frames = cfg.frame(0)
+    _fd_check(cfg, frames, (0, 0, cfg.canvas_w, cfg.canvas_h))
+
+
+def test_translation_gradient_has_lucas_kanade_form():
+    """For a pure translation A = T(-t) the a13 / a23 gradients are 2 sum r dI/du and 2 sum r dI/dv
+    (w = 1), i.e. minus the gradient of the loss with respect to the canvas shift of the camera;
+    checked by moving the camera instead of its parameters."""
+    fr_a = _rand_frame(30, 40, 1)
+    fr_b = _rand_frame(30, 40, 2)
+    ca = Camera(40, 30, _T(0, 0))
+    cb = Camera(40, 30, _T(10.3, 4.6))
+    p = _params_of([ca, cb])
+    win = (0, 0, 52, 36)
+    loss, g = oracle.loss_grad([40, 40], [30, 30], p, [fr_a, fr_b], win)
+    h = 1e-6
+    # camera B shifted on the canvas by +h in x: a13 of B decreases by h
+    cb2 = Camera(40, 30, _T(10.3 + h, 4.6))
+    cb3 = Camera(40, 30, _T(10.3 - h, 4.6))
+    lp, _ = oracle.loss_grad([40, 40], [30, 30], _params_of([ca, cb2]), [fr_a, fr_b], win, mask_params=p, grad=False)
+    lm, _ = oracle.loss_grad([40, 40], [30, 30], _params_of([ca, cb3]), [fr_a, fr_b], win, mask_params=p, grad=False)
+    d_shift = (lp - lm) / (2 * h)
+    assert abs(d_shift + g[1, 2]) <= 1e-5 * abs(g[1, 2])
+    # and a11/a12 gradients equal x- and y-weighted sums of the same integrand (w = 1)
+    assert abs(g[1, 6]) > 0  # projective terms are populated
+
+
+def test_invert_h_roundtrip():
+    M = synth.config_2cam().cameras[1].H
+    A = oracle.invert_h(M)
+    P = M @ A
+    np.testing.assert_allclose(P / P[2, 2], np.eye(3), atol=1e-12)
+    assert A[2, 2] == 1.0
