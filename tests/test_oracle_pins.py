@@ -311,7 +311,7 @@ def test_loss_closed_form_for_constant_frames():
     assert np.all(np.abs(g[:, :8]) < 1e-12)
 
 
-def _fd_check(cfg, frames, window, rel_eps=1e-7, tol=2e-5):
+def _fd_check(cfg, frames, window, tol=2e-5):
     n = len(cfg.cameras)
     p0 = _params_of(cfg.cameras, [1.0 + 0.05 * i for i in range(n)])
     # move every camera off the true alignment a little so residuals are not ~0
@@ -323,9 +323,12 @@ def _fd_check(cfg, frames, window, rel_eps=1e-7, tol=2e-5):
     assert np.all(np.abs(g[:, :8]).max(axis=1) > 1e-3 * np.abs(g).max())
     Ws = [c.width for c in cfg.cameras]
     Hs = [c.height for c in cfg.cameras]
+    # step of each parameter sized so the sample coordinates move by ~1e-6 px over the window
+    ext = float(max(window[0] + window[2], window[1] + window[3]))
+    steps = [1e-6 / ext, 1e-6 / ext, 1e-6, 1e-6 / ext, 1e-6 / ext, 1e-6, 1e-6 / ext ** 2, 1e-6 / ext ** 2, 1e-6]
     for i in range(n):
         for k in range(9):
-            h = rel_eps * max(abs(p0[i, k]), 1e-3 if k < 6 else 1e-7)
+            h = steps[k]
             pp = p0.copy(); pp[i, k] += h
             pm = p0.copy(); pm[i, k] -= h
             lp, _ = oracle.loss_grad(Ws, Hs, pp, frames, window, mask_params=p0, grad=False)
