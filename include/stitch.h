@@ -1,0 +1,187 @@
+/*
+ * libstitch: GB300 (sm_103a) per-frame panoramic stitching path, C ABI.
+ *
+ * What the library computes.  The paper (Du et al., "GPU based Parallel Optimization for Real
+ * Time Panoramic Video Stitching") describes the per-frame work only in words: each camera
+ * frame is "cut and transformed" by the GPU according to pre-corrected parameters (Sec. 4.3,
+ * Alg. 4 step 1), and the GPU then transforms the video and blends it into the panorama
+ * (Alg. 4 step 6) with multi-band fusion to remove seams (Sec. 1, contribution 3).  Once
+ * registration has fixed one homography per camera (Alg. 4 step 5, "transformation matrix"),
+ * the library runs, for every frame:
+ *   S1 inverse-homography warp of each frame into the canvas with bilinear sampling
+ *      (coordinates clamped to the image; pixel centres at integer coordinates),
+ *   S2 feather weights: distance to the source-image border, normalised over cameras,
+ *   S3 Gaussian pyramids (separable 5-tap [1,4,6,4,1]/16, even-index decimation, reflect-101),
+ *   S4 Laplacian bands (EXPAND with weights 2w(x-2k), reflect-101),
+ *   S5 per-level blend of the bands by the weight pyramids, renormalised per level,
+ *   S6 collapse, coverage mask, clamp to [0,1] and round-half-even to uint8 (or float out).
+ * and, for alignment refinement, S7: the overlap photometric loss
+ *      sum_{pixels} sum_{i<j} valid_i valid_j |I_i - I_j|^2 with I = gain * bilinear / 255
+ *   and its gradient with respect to each camera's 8 canvas->camera homography entries and gain.
+ *
+ * Conventions common to every call:
+ *  - Every pointer documented "device" is CUDA device memory of the device the rig was created
+ *    on; "host" pointers are ordinary (preferably pinned) host memory.  The caller owns frames,
+ *    outputs, parameters, loss and gradient buffers.  The library owns all scratch memory: it is
+ *    allocated by stitch_rig_create / stitch_batch_create and released by the destroy calls;
+ *    stitch_frames, stitch_backward and stitch_batch_frames never allocate.
+ *  - Frames are RGB, 8 bits per channel, interleaved, rows `pitch` bytes apart (pitch >= 3*W).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  All compute calls are
+ *    asynchronous on that stream; no call synchronises the device except the create/destroy
+ *    calls and stitch_frames_host (which returns after its output copy has completed).
+ *  - Errors are reported only through the returned status; no call aborts or throws.  After a
+ *    non-OK status from a compute call the outputs are undefined, and the rig stays usable
+ *    unless the status is STITCH_ECUDA (a sticky CUDA error poisons the whole context).
+ *  - A rig is not thread-safe: use one rig from one host thread and one stream at a time.
+ */
+#ifndef STITCH_H
+#define STITCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    STITCH_OK = 0,
+    STITCH_EINVAL = 1,      /* bad argument, descriptor or geometry */
+    STITCH_ENOMEM = 2,      /* device or host allocation failed (create calls only) */
+    STITCH_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    STITCH_ETIMEOUT = 4,    /* a bounded device-side wait gave up (batched schedule) */
+    STITCH_EUNSUPPORTED = 5 /* valid request this build does not handle */
+} stitch_status;
+
+/* Limits of this build. */
+#define STITCH_MAX_CAMERAS 32
+#define STITCH_MAX_LEVELS 12
+
+/* Which implementation of the forward path a rig runs. */
+#define STITCH_PATH_FUSED 0 /* fused kernels, pyramid levels kept on chip where they fit */
+#define STITCH_PATH_PLAIN 1 /* one kernel per step, FP32 intermediates in HBM (comparison path) */
+
+typedef struct {
+    int32_t width, height; /* source frame size in pixels, >= 1 */
+    double H[9];           /* camera->canvas homography, row-major; scaled internally so that the
+                              canvas->camera inverse has a33 = 1 (its sign must make a33 > 0) */
+    float gain;            /* intensity gain applied to the sampled value (1 = unchanged) */
+} stitch_camera;
+
+typedef struct {
+    int32_t num_cameras;          /* 1 .. STITCH_MAX_CAMERAS */
+    const stitch_camera* cameras; /* host array of num_cameras entries (copied by create) */
+    int32_t canvas_w, canvas_h;   /* output canvas size, >= 1 */
+    int32_t levels;               /* pyramid levels counting level 0, 1 .. STITCH_MAX_LEVELS */
+    int32_t band_fp16;            /* 0: FP32 pyramid storage; 1: FP16 storage of pyramid data
+                                     between kernels (all filtering and blending still FP32) */
+    int32_t out_float;            /* 0: uint8 RGB output; 1: float RGB output in [0,1] */
+    int32_t path;                 /* STITCH_PATH_FUSED or STITCH_PATH_PLAIN */
+} stitch_rig_desc;
+
+typedef struct stitch_rig stitch_rig; /* opaque, owned by the library */
+
+/*
+ * Validate a rig, plan it and preallocate every buffer the per-frame path needs (the paper
+ * precomputes grid/block sizes and static/dynamic memory at start-up, Sec. 4.3.2; this is the
+ * counterpart).  Checks: each H is finite and invertible with a33 > 0 after inversion; each
+ * camera's footprint is bounded (w > 0 at the four corners of its image rectangle); w > 0 over
+ * every canvas region the camera's blend depends on.  `device` is the CUDA ordinal; create makes
+ * it current and leaves it current.  On success *out receives the rig; on failure *out is NULL.
+ * Status: OK, EINVAL, ENOMEM, ECUDA.
+ */
+stitch_status stitch_rig_create(const stitch_rig_desc* desc, int device, stitch_rig** out);
+
+/* Release a rig and all its device memory.  NULL-safe.  Synchronises the rig's device. */
+void stitch_rig_destroy(stitch_rig* rig);
+
+/*
+ * Stitch one frame set (S1-S6).
+ *   frames   host array of num_cameras DEVICE pointers, one RGB8 frame per camera
+ *   pitches  host array of num_cameras row pitches in bytes (>= 3 * width)
+ *   out      DEVICE canvas, canvas_h rows of canvas_w RGB pixels: uint8 (3 bytes per pixel) or
+ *            float (12 bytes per pixel) as chosen by desc.out_float
+ *   out_pitch  row pitch of `out` in bytes
+ * Uncovered canvas pixels are written as 0.  Status: OK, EINVAL, ECUDA.
+ */
+stitch_status stitch_frames(stitch_rig* rig, const uint8_t* const* frames, const int64_t* pitches, void* out,
+                            int64_t out_pitch, void* stream);
+
+/*
+ * Same as stitch_frames for HOST buffers: copies the frames host->device into rig-owned
+ * staging buffers, stitches, copies the canvas device->host, and returns once `out` is written.
+ * The staging buffers are allocated on the first call of this function for a rig (so this call,
+ * unlike stitch_frames, may return STITCH_ENOMEM).  Pinned host memory gives asynchronous copies.
+ */
+stitch_status stitch_frames_host(stitch_rig* rig, const uint8_t* const* host_frames, const int64_t* pitches,
+                                 void* host_out, int64_t out_pitch, void* stream);
+
+/*
+ * S7: overlap photometric loss and its gradient.
+ *   params  DEVICE, num_cameras x 9 doubles per camera: a11 a12 a13 a21 a22 a23 a31 a32 gain of
+ *           the canvas->camera map A (a33 = 1).  Validity masks are taken from these params.
+ *   loss    DEVICE, 1 double: sum over canvas pixels and camera pairs i<j valid at the pixel of
+ *           the squared RGB difference of the gained, bilinearly sampled [0,1] intensities
+ *   grad    DEVICE, num_cameras x 9 doubles: d loss / d params, masks held constant (may be NULL)
+ * Sampling coordinates are clamped to the image as in S1; the derivative along a clamped axis is 0.
+ * Pixels where w <= 0 for a camera count as invalid for it.  Status: OK, EINVAL, ECUDA.
+ */
+stitch_status stitch_backward(stitch_rig* rig, const uint8_t* const* frames, const int64_t* pitches,
+                              const double* params, double* loss, double* grad, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* stitch_status_string(stitch_status s);
+
+/* ------------------------------------------------------------------------------------------ */
+/* Introspection and profiling                                                                 */
+
+typedef struct {
+    int64_t scratch_bytes;   /* device memory owned by the rig */
+    int32_t num_kernels;     /* kernel launches per stitch_frames call */
+    int32_t path;            /* STITCH_PATH_* actually used */
+    int64_t roi_pixels;      /* sum over cameras of level-0 pixels the path evaluates */
+} stitch_rig_info;
+
+stitch_status stitch_rig_get_info(const stitch_rig* rig, stitch_rig_info* info);
+
+/*
+ * Per-kernel CUDA-event timing of stitch_frames (events recorded on the call's stream around
+ * every launch).  enable=1 starts accumulating; stitch_rig_kernel_times copies up to `cap`
+ * entries: names (static strings), accumulated milliseconds and launch counts, returns the number
+ * of distinct kernels in *count.  Reading synchronises the events.  enable=0 stops and resets.
+ */
+stitch_status stitch_rig_set_profiling(stitch_rig* rig, int enable);
+stitch_status stitch_rig_kernel_times(stitch_rig* rig, const char** names, double* ms, int64_t* launches,
+                                      int32_t cap, int32_t* count);
+
+/* ------------------------------------------------------------------------------------------ */
+/* Batching: several independent rigs stitched by one persistent launch                        */
+
+typedef struct stitch_batch stitch_batch; /* opaque */
+
+/*
+ * Group rigs (all created on the same device, all STITCH_PATH_FUSED) into one batch.  The batch
+ * builds a device work list over every rig's tiles, ordered so that each tile's inputs come from
+ * earlier items, and preallocates its schedule state.  The rigs must outlive the batch.
+ * Status: OK, EINVAL, ENOMEM, ECUDA, EUNSUPPORTED.
+ */
+stitch_status stitch_batch_create(stitch_rig* const* rigs, int32_t n, stitch_batch** out);
+
+/*
+ * Stitch one frame set for every rig of the batch in one persistent launch.
+ *   frames       host array of n host arrays of DEVICE frame pointers (one per camera)
+ *   pitches      host array of n host arrays of row pitches
+ *   outs         host array of n DEVICE output canvases; out_pitches their row pitches
+ * Device-side waits are bounded; a wait that gives up returns STITCH_ETIMEOUT (read back after
+ * the launch, so this call synchronises `stream`).  Status: OK, EINVAL, ECUDA, ETIMEOUT.
+ */
+stitch_status stitch_batch_frames(stitch_batch* batch, const uint8_t* const* const* frames,
+                                  const int64_t* const* pitches, void* const* outs, const int64_t* out_pitches,
+                                  void* stream);
+
+void stitch_batch_destroy(stitch_batch* batch);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STITCH_H */

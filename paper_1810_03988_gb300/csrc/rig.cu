@@ -1,0 +1,435 @@
+// libstitch host side: rig validation and planning, buffer ownership, C-ABI entry points,
+// host staging and per-kernel profiling.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "stitch_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------------------------------------
+// index-range planning on one axis
+
+struct Span {
+    int lo, hi;  // half-open [lo, hi); empty when lo >= hi
+    bool empty() const { return hi <= lo; }
+};
+
+Span span_union(Span a, Span b) {
+    if (a.empty()) return b;
+    if (b.empty()) return a;
+    return {std::min(a.lo, b.lo), std::max(a.hi, b.hi)};
+}
+
+// finer-level samples read by REDUCE outputs in `c` (finer level of size n)
+Span reduce_reads(Span c, int n) {
+    if (c.empty()) return {0, 0};
+    int lo = n, hi = -1;
+    for (int k = c.lo; k < c.hi; ++k)
+        for (int m = -2; m <= 2; ++m) {
+            const int i = fold101(2 * k + m, n);
+            lo = std::min(lo, i);
+            hi = std::max(hi, i);
+        }
+    return {lo, hi + 1};
+}
+
+// coarser-level samples read by EXPAND outputs in `f` (coarser level of size n)
+Span expand_reads(Span f, int n) {
+    if (f.empty()) return {0, 0};
+    int lo = n, hi = -1;
+    for (int x = f.lo; x < f.hi; ++x) {
+        const int k0 = (x % 2 == 0) ? x / 2 - 1 : (x - 1) / 2;
+        const int k1 = (x % 2 == 0) ? x / 2 + 1 : (x + 1) / 2;
+        for (int k = k0; k <= k1; ++k) {
+            const int i = fold101(k, n);
+            lo = std::min(lo, i);
+            hi = std::max(hi, i);
+        }
+    }
+    return {lo, hi + 1};
+}
+
+// coarser-level outputs (level size nc) whose REDUCE support meets the finer span `f` (size nf)
+Span reduce_touch(Span f, int nf, int nc) {
+    if (f.empty()) return {0, 0};
+    int lo = nc, hi = -1;
+    for (int k = 0; k < nc; ++k) {
+        bool hit = false;
+        for (int m = -2; m <= 2 && !hit; ++m) {
+            const int i = fold101(2 * k + m, nf);
+            hit = i >= f.lo && i < f.hi;
+        }
+        if (hit) {
+            lo = std::min(lo, k);
+            hi = std::max(hi, k);
+        }
+    }
+    return hi < lo ? Span{0, 0} : Span{lo, hi + 1};
+}
+
+Rect make_rect(Span x, Span y) {
+    if (x.empty() || y.empty()) return Rect{0, 0, 0, 0};
+    return Rect{x.lo, x.hi, y.lo, y.hi};
+}
+
+bool invert_normalised(const double* M, double* A) {
+    const double a = M[0], b = M[1], c = M[2], d = M[3], e = M[4], f = M[5], g = M[6], h = M[7], k = M[8];
+    const double c00 = e * k - f * h, c01 = f * g - d * k, c02 = d * h - e * g;
+    const double det = a * c00 + b * c01 + c * c02;
+    if (!(fabs(det) > 0.0) || !std::isfinite(det)) return false;
+    double inv[9] = {c00, c * h - b * k, b * f - c * e, c01, a * k - c * g, c * d - a * f, c02, b * g - a * h,
+                     a * e - b * d};
+    for (double& v : inv) v /= det;
+    if (!(inv[8] > 0.0)) return false;
+    for (int i = 0; i < 9; ++i) A[i] = inv[i] / inv[8];
+    A[8] = 1.0;
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(A[i])) return false;
+    return true;
+}
+
+stitch_status plan_camera(stitch_rig* r, int i) {
+    const stitch_camera& c = r->cams[i];
+    CamDev& d = r->hcam[i];
+    memset(&d, 0, sizeof(d));
+    const RigGeom& g = r->geom;
+    const int L = g.levels, Wc = g.nx[0], Hc = g.ny[0];
+    if (c.width < 1 || c.height < 1 || !std::isfinite(c.gain)) return STITCH_EINVAL;
+    for (double v : c.H)
+        if (!std::isfinite(v)) return STITCH_EINVAL;
+    if (!invert_normalised(c.H, d.A)) return STITCH_EINVAL;
+    d.W = c.width;
+    d.H = c.height;
+    d.gain = c.gain;
+
+    // footprint of the validity rectangle: image of its corners under H (must stay in front)
+    const double cu[4] = {-0.5, c.width - 0.5, -0.5, c.width - 0.5};
+    const double cv[4] = {-0.5, -0.5, c.height - 0.5, c.height - 0.5};
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int k = 0; k < 4; ++k) {
+        const double X = c.H[0] * cu[k] + c.H[1] * cv[k] + c.H[2];
+        const double Y = c.H[3] * cu[k] + c.H[4] * cv[k] + c.H[5];
+        const double Wh = c.H[6] * cu[k] + c.H[7] * cv[k] + c.H[8];
+        // the corner must be in front of the camera for the footprint to be a bounded quad
+        if (!(Wh > 0.0)) return STITCH_EINVAL;
+        xmin = std::min(xmin, X / Wh);
+        xmax = std::max(xmax, X / Wh);
+        ymin = std::min(ymin, Y / Wh);
+        ymax = std::max(ymax, Y / Wh);
+    }
+    // one pixel of margin beyond the footprint so single-precision evaluation near its edge is
+    // still inside the box (outside the box the camera's weight is exactly zero)
+    const double bx0 = std::max(0.0, floor(xmin) - 1.0), bx1 = std::min((double)Wc, ceil(xmax) + 2.0);
+    const double by0 = std::max(0.0, floor(ymin) - 1.0), by1 = std::min((double)Hc, ceil(ymax) + 2.0);
+    if (bx1 <= bx0 || by1 <= by0) {
+        d.visible = 0;
+        return STITCH_OK;
+    }
+    d.visible = 1;
+    Span zx[MAXL], zy[MAXL];
+    zx[0] = {(int)bx0, (int)bx1};
+    zy[0] = {(int)by0, (int)by1};
+    d.V = make_rect(zx[0], zy[0]);
+    for (int l = 0; l + 1 < L; ++l) {
+        zx[l + 1] = reduce_touch(zx[l], g.nx[l], g.nx[l + 1]);
+        zy[l + 1] = reduce_touch(zy[l], g.ny[l], g.ny[l + 1]);
+    }
+    // Omega: everything the bands on Z depend on
+    Span ox[MAXL], oy[MAXL];
+    for (int l = L - 1; l >= 0; --l) {
+        ox[l] = zx[l];
+        oy[l] = zy[l];
+        if (l >= 1) {
+            ox[l] = span_union(ox[l], expand_reads(zx[l - 1], g.nx[l]));
+            oy[l] = span_union(oy[l], expand_reads(zy[l - 1], g.ny[l]));
+        }
+        if (l + 1 < L) {
+            ox[l] = span_union(ox[l], reduce_reads(ox[l + 1], g.nx[l]));
+            oy[l] = span_union(oy[l], reduce_reads(oy[l + 1], g.ny[l]));
+        }
+    }
+    for (int l = 0; l < L; ++l) {
+        d.Z[l] = make_rect(zx[l], zy[l]);
+        d.Om[l] = make_rect(ox[l], oy[l]);
+    }
+    // the camera must be in front (w > 0) everywhere its level-0 values are evaluated
+    const Rect& o = d.Om[0];
+    const double qx[2] = {(double)o.x0, (double)(o.x1 - 1)}, qy[2] = {(double)o.y0, (double)(o.y1 - 1)};
+    for (double x : qx)
+        for (double y : qy)
+            if (!(d.A[6] * x + d.A[7] * y + 1.0 > 0.0)) return STITCH_EINVAL;
+    r->roi_pixels += o.area();
+    return STITCH_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+void free_all(stitch_rig* r) {
+    for (void* p : r->allocs) cudaFree(p);
+    r->allocs.clear();
+    for (int i = 0; i < MAXC; ++i)
+        if (r->stage_frames[i]) cudaFree(r->stage_frames[i]);
+    if (r->stage_out) cudaFree(r->stage_out);
+    for (cudaEvent_t e : r->ev_pool) cudaEventDestroy(e);
+    r->ev_pool.clear();
+}
+
+bool frames_ok(const stitch_rig* r, const uint8_t* const* frames, const int64_t* pitches, FramePtrs* fp) {
+    if (!frames || !pitches) return false;
+    memset(fp, 0, sizeof(*fp));
+    for (int i = 0; i < r->geom.ncam; ++i) {
+        if (!r->hcam[i].visible) continue;
+        if (!frames[i] || pitches[i] < 3LL * r->cams[i].width) return false;
+        fp->p[i] = frames[i];
+        fp->pitch[i] = pitches[i];
+    }
+    return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+
+void* rig_alloc(stitch_rig* r, size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    r->allocs.push_back(p);
+    r->scratch_bytes += (long long)bytes;
+    return p;
+}
+
+void prof_mark(stitch_rig* r, const char* name, cudaStream_t s) {
+    if (!r->prof) return;
+    if (r->ev_used == r->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            r->prof = false;
+            return;
+        }
+        r->ev_pool.push_back(e);
+    }
+    cudaEvent_t e = r->ev_pool[r->ev_used++];
+    cudaEventRecord(e, s);
+    r->marks.push_back({name, e});
+}
+
+extern "C" {
+
+const char* stitch_status_string(stitch_status s) {
+    switch (s) {
+        case STITCH_OK: return "STITCH_OK";
+        case STITCH_EINVAL: return "STITCH_EINVAL: invalid argument or geometry";
+        case STITCH_ENOMEM: return "STITCH_ENOMEM: allocation failed";
+        case STITCH_ECUDA: return "STITCH_ECUDA: CUDA error";
+        case STITCH_ETIMEOUT: return "STITCH_ETIMEOUT: bounded device wait gave up";
+        case STITCH_EUNSUPPORTED: return "STITCH_EUNSUPPORTED: not supported by this build";
+    }
+    return "unknown stitch_status";
+}
+
+stitch_status stitch_rig_create(const stitch_rig_desc* desc, int device, stitch_rig** out) {
+    if (!out) return STITCH_EINVAL;
+    *out = nullptr;
+    if (!desc || !desc->cameras || desc->num_cameras < 1 || desc->num_cameras > MAXC || desc->canvas_w < 1 ||
+        desc->canvas_h < 1 || desc->levels < 1 || desc->levels > MAXL || desc->canvas_w > (1 << 28) ||
+        desc->canvas_h > (1 << 28) || (desc->band_fp16 != 0 && desc->band_fp16 != 1) ||
+        (desc->out_float != 0 && desc->out_float != 1) ||
+        (desc->path != STITCH_PATH_FUSED && desc->path != STITCH_PATH_PLAIN))
+        return STITCH_EINVAL;
+    if ((long long)desc->canvas_w * desc->canvas_h > (1LL << 31)) return STITCH_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return STITCH_ECUDA;
+    }
+    if (device < 0 || device >= ndev) return STITCH_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return STITCH_ECUDA;
+
+    stitch_rig* r = new (std::nothrow) stitch_rig();
+    if (!r) return STITCH_ENOMEM;
+    r->device = device;
+    r->desc = *desc;
+    r->cams.assign(desc->cameras, desc->cameras + desc->num_cameras);
+    r->desc.cameras = nullptr;
+    RigGeom& g = r->geom;
+    g.ncam = desc->num_cameras;
+    g.levels = desc->levels;
+    g.nx[0] = desc->canvas_w;
+    g.ny[0] = desc->canvas_h;
+    for (int l = 1; l < g.levels; ++l) {
+        g.nx[l] = (g.nx[l - 1] + 1) / 2;
+        g.ny[l] = (g.ny[l - 1] + 1) / 2;
+    }
+    stitch_status st = STITCH_OK;
+    for (int i = 0; i < g.ncam && st == STITCH_OK; ++i) st = plan_camera(r, i);
+    if (st == STITCH_OK && desc->path == STITCH_PATH_PLAIN && desc->band_fp16) st = STITCH_EUNSUPPORTED;
+    if (st == STITCH_OK) st = desc->path == STITCH_PATH_PLAIN ? plain_plan(r) : fused_plan(r);
+    if (st == STITCH_OK) st = backward_plan(r);
+    if (st == STITCH_OK) {
+        r->dcam = (CamDev*)rig_alloc(r, sizeof(CamDev) * g.ncam);
+        if (!r->dcam) st = STITCH_ENOMEM;
+    }
+    if (st == STITCH_OK && cudaMemcpy(r->dcam, r->hcam, sizeof(CamDev) * g.ncam, cudaMemcpyHostToDevice) != cudaSuccess)
+        st = STITCH_ECUDA;
+    if (st != STITCH_OK) {
+        fused_release(r);
+        free_all(r);
+        delete r;
+        return st;
+    }
+    *out = r;
+    return STITCH_OK;
+}
+
+void stitch_rig_destroy(stitch_rig* r) {
+    if (!r) return;
+    DeviceGuard dg(r->device);
+    cudaDeviceSynchronize();
+    fused_release(r);
+    free_all(r);
+    delete r;
+}
+
+stitch_status stitch_rig_get_info(const stitch_rig* r, stitch_rig_info* info) {
+    if (!r || !info) return STITCH_EINVAL;
+    info->scratch_bytes = r->scratch_bytes;
+    info->num_kernels = r->kernels_per_frame;
+    info->path = r->desc.path;
+    info->roi_pixels = r->roi_pixels;
+    return STITCH_OK;
+}
+
+stitch_status stitch_frames(stitch_rig* r, const uint8_t* const* frames, const int64_t* pitches, void* out,
+                            int64_t out_pitch, void* stream) {
+    if (!r || !out) return STITCH_EINVAL;
+    const long long row = (long long)r->geom.nx[0] * (r->desc.out_float ? 12 : 3);
+    if (out_pitch < row) return STITCH_EINVAL;
+    FramePtrs fp;
+    if (!frames_ok(r, frames, pitches, &fp)) return STITCH_EINVAL;
+    DeviceGuard dg(r->device);
+    if (!dg.ok) return STITCH_ECUDA;
+    OutDesc od{out, out_pitch, r->desc.out_float};
+    cudaStream_t s = (cudaStream_t)stream;
+    stitch_status st = r->desc.path == STITCH_PATH_PLAIN ? plain_frames(r, fp, od, s) : fused_frames(r, fp, od, s);
+    prof_mark(r, nullptr, s);
+    return st;
+}
+
+stitch_status stitch_frames_host(stitch_rig* r, const uint8_t* const* host_frames, const int64_t* pitches,
+                                 void* host_out, int64_t out_pitch, void* stream) {
+    if (!r || !host_frames || !pitches || !host_out) return STITCH_EINVAL;
+    const int bpp = r->desc.out_float ? 12 : 3;
+    const long long row = (long long)r->geom.nx[0] * bpp;
+    if (out_pitch < row) return STITCH_EINVAL;
+    DeviceGuard dg(r->device);
+    if (!dg.ok) return STITCH_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint8_t* dframes[MAXC] = {};
+    int64_t dpitch[MAXC] = {};
+    for (int i = 0; i < r->geom.ncam; ++i) {
+        const stitch_camera& c = r->cams[i];
+        if (!r->hcam[i].visible) continue;
+        if (!host_frames[i] || pitches[i] < 3LL * c.width) return STITCH_EINVAL;
+        if (!r->stage_frames[i] &&
+            cudaMalloc((void**)&r->stage_frames[i], (size_t)c.width * c.height * 3) != cudaSuccess) {
+            cudaGetLastError();
+            r->stage_frames[i] = nullptr;
+            return STITCH_ENOMEM;
+        }
+        STITCH_CUDA_TRY(cudaMemcpy2DAsync(r->stage_frames[i], (size_t)c.width * 3, host_frames[i], (size_t)pitches[i],
+                                          (size_t)c.width * 3, c.height, cudaMemcpyHostToDevice, s));
+        dframes[i] = r->stage_frames[i];
+        dpitch[i] = (int64_t)c.width * 3;
+    }
+    if (!r->stage_out && cudaMalloc(&r->stage_out, (size_t)row * r->geom.ny[0]) != cudaSuccess) {
+        cudaGetLastError();
+        r->stage_out = nullptr;
+        return STITCH_ENOMEM;
+    }
+    stitch_status st = stitch_frames(r, dframes, dpitch, r->stage_out, row, stream);
+    if (st != STITCH_OK) return st;
+    STITCH_CUDA_TRY(cudaMemcpy2DAsync(host_out, (size_t)out_pitch, r->stage_out, (size_t)row, (size_t)row,
+                                      r->geom.ny[0], cudaMemcpyDeviceToHost, s));
+    STITCH_CUDA_TRY(cudaStreamSynchronize(s));
+    return STITCH_OK;
+}
+
+stitch_status stitch_backward(stitch_rig* r, const uint8_t* const* frames, const int64_t* pitches,
+                              const double* params, double* loss, double* grad, void* stream) {
+    if (!r || !params || !loss) return STITCH_EINVAL;
+    if (!frames || !pitches) return STITCH_EINVAL;
+    FramePtrs fp;
+    memset(&fp, 0, sizeof(fp));
+    for (int i = 0; i < r->geom.ncam; ++i) {
+        if (!frames[i] || pitches[i] < 3LL * r->cams[i].width) return STITCH_EINVAL;
+        fp.p[i] = frames[i];
+        fp.pitch[i] = pitches[i];
+    }
+    DeviceGuard dg(r->device);
+    if (!dg.ok) return STITCH_ECUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    stitch_status st = backward_run(r, fp, params, loss, grad, s);
+    prof_mark(r, nullptr, s);
+    return st;
+}
+
+stitch_status stitch_rig_set_profiling(stitch_rig* r, int enable) {
+    if (!r) return STITCH_EINVAL;
+    r->prof = enable != 0;
+    r->marks.clear();
+    r->ev_used = 0;
+    r->stats.clear();
+    return STITCH_OK;
+}
+
+stitch_status stitch_rig_kernel_times(stitch_rig* r, const char** names, double* ms, int64_t* launches, int32_t cap,
+                                      int32_t* count) {
+    if (!r || !count) return STITCH_EINVAL;
+    DeviceGuard dg(r->device);
+    if (!r->marks.empty()) STITCH_CUDA_TRY(cudaEventSynchronize(r->marks.back().ev));
+    for (size_t k = 0; k + 1 < r->marks.size(); ++k) {
+        const ProfMark& a = r->marks[k];
+        if (!a.name) continue;
+        float t = 0.0f;
+        STITCH_CUDA_TRY(cudaEventElapsedTime(&t, a.ev, r->marks[k + 1].ev));
+        auto it = std::find_if(r->stats.begin(), r->stats.end(),
+                               [&](const KernelStat& s) { return strcmp(s.name, a.name) == 0; });
+        if (it == r->stats.end()) {
+            r->stats.push_back({a.name, 0.0, 0});
+            it = r->stats.end() - 1;
+        }
+        it->ms += t;
+        it->launches += 1;
+    }
+    r->marks.clear();
+    r->ev_used = 0;
+    const int n = (int)r->stats.size();
+    for (int k = 0; k < n && k < cap; ++k) {
+        if (names) names[k] = r->stats[k].name;
+        if (ms) ms[k] = r->stats[k].ms;
+        if (launches) launches[k] = r->stats[k].launches;
+    }
+    *count = n;
+    return STITCH_OK;
+}
+
+}  // extern "C"

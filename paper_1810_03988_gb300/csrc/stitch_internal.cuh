@@ -1,0 +1,261 @@
+// Internal declarations shared by the libstitch translation units (device structs, planner
+// output, launch helpers).  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "stitch.h"
+
+#define MAXL STITCH_MAX_LEVELS
+#define MAXC STITCH_MAX_CAMERAS
+
+// Half-open rectangle of one pyramid level, in that level's canvas coordinates.
+struct Rect {
+    int x0, x1, y0, y1;
+    __host__ __device__ int w() const { return x1 - x0; }
+    __host__ __device__ int h() const { return y1 - y0; }
+    __host__ __device__ bool empty() const { return x1 <= x0 || y1 <= y0; }
+    __host__ __device__ bool contains(int x, int y) const { return x >= x0 && x < x1 && y >= y0 && y < y1; }
+    __host__ __device__ long long area() const { return empty() ? 0 : (long long)w() * h(); }
+};
+
+// Per-camera descriptor, resident in device memory for the life of a rig.
+struct CamDev {
+    double A[9];     // canvas -> camera homography, a33 = 1
+    int W, H;        // source frame size
+    float gain;
+    int visible;     // 0 when the camera's footprint misses the canvas
+    Rect V;          // level-0 bounding box of the validity region (empty when !visible)
+    Rect Om[MAXL];   // Omega^l: region on which the camera's pyramid is evaluated
+    Rect Z[MAXL];    // Z^l: region where the camera's weight pyramid can be non-zero
+    // plain path buffers
+    float4* G[MAXL];   // Gaussian pyramid (r, g, b, weight) on Om[l], row pitch Om[l].w()
+    float4* Lp[MAXL];  // (Laplacian r, g, b, weight) on Z[l] for l < L-1, row pitch Z[l].w()
+    // fused path buffers
+    void* FG[MAXL];    // Gaussian pyramid (r, g, b, weight) on Om[l] for l >= 1 (FP32 or FP16)
+};
+
+// Rig-wide sizes passed by value to kernels.
+struct RigGeom {
+    int ncam, levels;
+    int nx[MAXL], ny[MAXL];  // canvas size of every level (nx[l+1] = ceil(nx[l] / 2))
+};
+
+// Device frame pointers of one call, passed by value.
+struct FramePtrs {
+    const uint8_t* p[MAXC];
+    long long pitch[MAXC];
+};
+
+// Output descriptor of one call.
+struct OutDesc {
+    void* ptr;
+    long long pitch;  // bytes
+    int is_float;
+};
+
+// ------------------------------------------------------------------------------------------------
+// small device helpers
+
+// reflect-101 border folding on a grid of n samples: ... 2 1 | 0 1 2 ... n-1 | n-2 n-3 ...
+__host__ __device__ __forceinline__ int fold101(int i, int n) {
+    if (n == 1) return 0;
+    const int period = 2 * n - 2;
+    int r = i % period;
+    if (r < 0) r += period;
+    return r < n ? r : period - r;
+}
+
+// Accurate per-tile parameterisation of a homography.  With (X, Y) the tile anchor and
+// U0 = round(u(X, Y)), the offset u - U0 = (pu0 + pu1 dx + pu2 dy) / (q0 + q1 dx + q2 dy) is
+// small, so single precision keeps ~1e-5 px accuracy anywhere on a 24000-px canvas; the
+// coefficients are formed in double precision once per tile.
+struct TileMap {
+    int U0, V0;
+    float pu0, pu1, pu2, pv0, pv1, pv2, q0, q1, q2;
+};
+
+__device__ __forceinline__ TileMap make_tile_map(const double* A, int X, int Y) {
+    const double x = (double)X, y = (double)Y;
+    const double n0 = A[0] * x + A[1] * y + A[2];
+    const double m0 = A[3] * x + A[4] * y + A[5];
+    const double d0 = A[6] * x + A[7] * y + A[8];
+    double u0 = n0 / d0, v0 = m0 / d0;
+    u0 = fmin(fmax(u0, -1.0e8), 1.0e8);
+    v0 = fmin(fmax(v0, -1.0e8), 1.0e8);
+    const double U = rint(u0), V = rint(v0);
+    TileMap t;
+    t.U0 = (int)U;
+    t.V0 = (int)V;
+    t.pu0 = (float)(n0 - U * d0);
+    t.pu1 = (float)(A[0] - U * A[6]);
+    t.pu2 = (float)(A[1] - U * A[7]);
+    t.pv0 = (float)(m0 - V * d0);
+    t.pv1 = (float)(A[3] - V * A[6]);
+    t.pv2 = (float)(A[4] - V * A[7]);
+    t.q0 = (float)d0;
+    t.q1 = (float)A[6];
+    t.q2 = (float)A[7];
+    return t;
+}
+
+// Source position of canvas point (anchor + (dx, dy)) as integer part + fraction in [0, 1).
+struct SrcPos {
+    int iu, iv;
+    float fu, fv;
+    float den;
+};
+
+__device__ __forceinline__ SrcPos map_point(const TileMap& t, float dx, float dy) {
+    SrcPos s;
+    s.den = fmaf(t.q2, dy, fmaf(t.q1, dx, t.q0));
+    const float rden = __frcp_rn(s.den);
+    float ru = fmaf(t.pu2, dy, fmaf(t.pu1, dx, t.pu0)) * rden;
+    float rv = fmaf(t.pv2, dy, fmaf(t.pv1, dx, t.pv0)) * rden;
+    ru = fminf(fmaxf(ru, -1.0e7f), 1.0e7f);
+    rv = fminf(fmaxf(rv, -1.0e7f), 1.0e7f);
+    const float flu = floorf(ru), flv = floorf(rv);
+    s.iu = t.U0 + (int)flu;
+    s.iv = t.V0 + (int)flv;
+    s.fu = ru - flu;
+    s.fv = rv - flv;
+    return s;
+}
+
+// Raw feather weight: distance (source px) to the nearest border of the validity rectangle
+// [-0.5, W-0.5) x [-0.5, H-0.5), zero outside it or behind the camera.
+__device__ __forceinline__ float feather_weight(const SrcPos& s, int W, int H) {
+    if (!(s.den > 0.0f)) return 0.0f;
+    const bool okx = (s.iu >= 0 || (s.iu == -1 && s.fu >= 0.5f)) && (s.iu <= W - 2 || (s.iu == W - 1 && s.fu < 0.5f));
+    const bool oky = (s.iv >= 0 || (s.iv == -1 && s.fv >= 0.5f)) && (s.iv <= H - 2 || (s.iv == H - 1 && s.fv < 0.5f));
+    if (!(okx && oky)) return 0.0f;
+    const float u = (float)s.iu + s.fu, v = (float)s.iv + s.fv;
+    float m = fminf(fminf(u + 0.5f, v + 0.5f), fminf(((float)W - 0.5f) - u, ((float)H - 0.5f) - v));
+    return fmaxf(m, 0.0f);
+}
+
+// Clamped texel coordinates and fractions of a bilinear sample.
+struct Tap {
+    int i0, i1, j0, j1;
+    float fx, fy;
+};
+
+__device__ __forceinline__ Tap clamp_tap(const SrcPos& s, int W, int H) {
+    Tap t;
+    if (s.iu < 0) { t.i0 = 0; t.fx = 0.0f; }
+    else if (s.iu >= W - 1) { t.i0 = W - 1; t.fx = 0.0f; }
+    else { t.i0 = s.iu; t.fx = s.fu; }
+    if (s.iv < 0) { t.j0 = 0; t.fy = 0.0f; }
+    else if (s.iv >= H - 1) { t.j0 = H - 1; t.fy = 0.0f; }
+    else { t.j0 = s.iv; t.fy = s.fv; }
+    t.i1 = min(t.i0 + 1, W - 1);
+    t.j1 = min(t.j0 + 1, H - 1);
+    return t;
+}
+
+// Bilinear RGB sample of an 8-bit frame, scaled by `scale` (= gain / 255).
+__device__ __forceinline__ float3 bilinear_rgb(const uint8_t* __restrict__ px, long long pitch, const Tap& t,
+                                               float scale) {
+    const uint8_t* r0 = px + (long long)t.j0 * pitch;
+    const uint8_t* r1 = px + (long long)t.j1 * pitch;
+    float3 o;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float p00 = __ldg(r0 + 3 * t.i0 + c), p01 = __ldg(r0 + 3 * t.i1 + c);
+        const float p10 = __ldg(r1 + 3 * t.i0 + c), p11 = __ldg(r1 + 3 * t.i1 + c);
+        const float top = fmaf(t.fx, p01 - p00, p00);
+        const float bot = fmaf(t.fx, p11 - p10, p10);
+        const float v = fmaf(t.fy, bot - top, top) * scale;
+        if (c == 0) o.x = v; else if (c == 1) o.y = v; else o.z = v;
+    }
+    return o;
+}
+
+// Anchor for a camera's tile map: the tile origin clamped into the camera's validity box, where
+// w > 0 is guaranteed by the planner.
+__device__ __forceinline__ void tile_anchor(const Rect& V, int X, int Y, int* ax, int* ay) {
+    *ax = min(max(X, V.x0), V.x1 - 1);
+    *ay = min(max(Y, V.y0), V.y1 - 1);
+}
+
+__device__ __forceinline__ unsigned char quantize_u8(float v) {
+    // v already clamped to [0, 1]; round half to even
+    return (unsigned char)__float2int_rn(255.0f * v);
+}
+
+// ------------------------------------------------------------------------------------------------
+// host side
+
+struct KernelStat {
+    const char* name;
+    double ms;
+    long long launches;
+};
+
+struct ProfMark {
+    const char* name;  // kernel that starts at this event (nullptr: end marker)
+    cudaEvent_t ev;
+};
+
+struct stitch_rig {
+    int device = 0;
+    stitch_rig_desc desc{};
+    std::vector<stitch_camera> cams;
+    RigGeom geom{};
+    CamDev hcam[MAXC]{};
+    CamDev* dcam = nullptr;
+    float4* Bl[MAXL]{};  // plain path: blended band / collapse buffer per level (full level grid)
+    std::vector<void*> allocs;
+    long long scratch_bytes = 0;
+    long long roi_pixels = 0;
+    int kernels_per_frame = 0;
+
+    // fused path state
+    void* fused = nullptr;
+
+    // backward state
+    double* bw_partials = nullptr;
+    int bw_blocks = 0;
+    Rect bw_region{};
+
+    // host staging for stitch_frames_host
+    uint8_t* stage_frames[MAXC]{};
+    void* stage_out = nullptr;
+
+    // profiling
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<ProfMark> marks;
+    std::vector<KernelStat> stats;
+};
+
+// Record a profiling mark before a launch (name) or at the end of a call (nullptr).
+void prof_mark(stitch_rig* r, const char* name, cudaStream_t s);
+
+// Device allocation owned by the rig.
+void* rig_alloc(stitch_rig* r, size_t bytes);
+
+// Path entry points (one translation unit each).
+stitch_status plain_plan(stitch_rig* r);
+stitch_status plain_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od, cudaStream_t s);
+stitch_status fused_plan(stitch_rig* r);
+stitch_status fused_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od, cudaStream_t s);
+void fused_release(stitch_rig* r);
+stitch_status backward_plan(stitch_rig* r);
+stitch_status backward_run(stitch_rig* r, const FramePtrs& fp, const double* params, double* loss, double* grad,
+                           cudaStream_t s);
+
+#define STITCH_CUDA_TRY(expr)                         \
+    do {                                              \
+        cudaError_t _e = (expr);                      \
+        if (_e != cudaSuccess) return STITCH_ECUDA;   \
+    } while (0)
+
+static inline stitch_status launch_status() {
+    return cudaGetLastError() == cudaSuccess ? STITCH_OK : STITCH_ECUDA;
+}

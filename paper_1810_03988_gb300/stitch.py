@@ -1,0 +1,316 @@
+"""Thin ctypes binding of libstitch (include/stitch.h).
+
+Argument marshalling only: every step of the stitching path runs in the library's CUDA kernels.
+PyTorch supplies device memory and the current CUDA stream.  The functions named like the C ABI
+(``stitch_rig_create`` ...) take plain integers/pointers; :class:`Rig` wraps them for torch tensors.
+There is no CPU fallback: if the library is missing or the GPU is unavailable the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+STITCH_OK, STITCH_EINVAL, STITCH_ENOMEM, STITCH_ECUDA, STITCH_ETIMEOUT, STITCH_EUNSUPPORTED = range(6)
+STITCH_MAX_CAMERAS = 32
+STITCH_MAX_LEVELS = 12
+STITCH_PATH_FUSED = 0
+STITCH_PATH_PLAIN = 1
+
+_P = ctypes.c_void_p
+_lock = threading.Lock()
+_lib = None
+
+
+class stitch_camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("H", ctypes.c_double * 9),
+                ("gain", ctypes.c_float)]
+
+
+class stitch_rig_desc(ctypes.Structure):
+    _fields_ = [("num_cameras", ctypes.c_int32), ("cameras", ctypes.POINTER(stitch_camera)),
+                ("canvas_w", ctypes.c_int32), ("canvas_h", ctypes.c_int32), ("levels", ctypes.c_int32),
+                ("band_fp16", ctypes.c_int32), ("out_float", ctypes.c_int32), ("path", ctypes.c_int32)]
+
+
+class stitch_rig_info(ctypes.Structure):
+    _fields_ = [("scratch_bytes", ctypes.c_int64), ("num_kernels", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("roi_pixels", ctypes.c_int64)]
+
+
+# every symbol declared by include/stitch.h, with its ctypes signature
+SIGNATURES = {
+    "stitch_rig_create": (ctypes.c_int, [ctypes.POINTER(stitch_rig_desc), ctypes.c_int, ctypes.POINTER(_P)]),
+    "stitch_rig_destroy": (None, [_P]),
+    "stitch_frames": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
+    "stitch_frames_host": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
+    "stitch_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "stitch_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "stitch_rig_get_info": (ctypes.c_int, [_P, ctypes.POINTER(stitch_rig_info)]),
+    "stitch_rig_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "stitch_rig_kernel_times": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "stitch_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "stitch_batch_frames": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "stitch_batch_destroy": (None, [_P]),
+}
+
+
+class StitchError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)}")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libstitch.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise RuntimeError("libstitch.so is not built: run __graft_entry__.build() (nvcc, sm_103a)")
+                _build.build()
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load().stitch_status_string(status).decode()
+    except Exception:  # pragma: no cover - only for messages
+        return f"status {status}"
+
+
+def _check(status: int, what: str):
+    if status != STITCH_OK:
+        raise StitchError(status, what)
+
+
+# ------------------------------------------------------------------------------------------------
+# functions with the C ABI's names (pointers as Python ints)
+
+
+def stitch_rig_create(desc: stitch_rig_desc, device: int) -> int:
+    out = _P()
+    _check(load().stitch_rig_create(ctypes.byref(desc), device, ctypes.byref(out)), "stitch_rig_create")
+    return out.value
+
+
+def stitch_rig_destroy(rig: int) -> None:
+    load().stitch_rig_destroy(rig)
+
+
+def stitch_frames(rig: int, frame_ptrs, pitches, out_ptr: int, out_pitch: int, stream: int) -> None:
+    n = len(frame_ptrs)
+    fp = (_P * n)(*frame_ptrs)
+    pt = (ctypes.c_int64 * n)(*pitches)
+    _check(load().stitch_frames(rig, fp, pt, out_ptr, out_pitch, stream), "stitch_frames")
+
+
+def stitch_frames_host(rig: int, frame_ptrs, pitches, out_ptr: int, out_pitch: int, stream: int) -> None:
+    n = len(frame_ptrs)
+    fp = (_P * n)(*frame_ptrs)
+    pt = (ctypes.c_int64 * n)(*pitches)
+    _check(load().stitch_frames_host(rig, fp, pt, out_ptr, out_pitch, stream), "stitch_frames_host")
+
+
+def stitch_backward(rig: int, frame_ptrs, pitches, params_ptr: int, loss_ptr: int, grad_ptr: int,
+                    stream: int) -> None:
+    n = len(frame_ptrs)
+    fp = (_P * n)(*frame_ptrs)
+    pt = (ctypes.c_int64 * n)(*pitches)
+    _check(load().stitch_backward(rig, fp, pt, params_ptr, loss_ptr, grad_ptr or None, stream), "stitch_backward")
+
+
+def stitch_rig_get_info(rig: int) -> stitch_rig_info:
+    info = stitch_rig_info()
+    _check(load().stitch_rig_get_info(rig, ctypes.byref(info)), "stitch_rig_get_info")
+    return info
+
+
+def stitch_rig_set_profiling(rig: int, enable: bool) -> None:
+    _check(load().stitch_rig_set_profiling(rig, 1 if enable else 0), "stitch_rig_set_profiling")
+
+
+def stitch_rig_kernel_times(rig: int, cap: int = 64) -> dict:
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_double * cap)()
+    launches = (ctypes.c_int64 * cap)()
+    count = ctypes.c_int32()
+    _check(load().stitch_rig_kernel_times(rig, names, ms, launches, cap, ctypes.byref(count)),
+           "stitch_rig_kernel_times")
+    return {names[k].decode(): (ms[k], launches[k]) for k in range(min(count.value, cap))}
+
+
+def stitch_batch_create(rigs) -> int:
+    n = len(rigs)
+    arr = (_P * n)(*rigs)
+    out = _P()
+    _check(load().stitch_batch_create(arr, n, ctypes.byref(out)), "stitch_batch_create")
+    return out.value
+
+
+def stitch_batch_frames(batch: int, frame_ptrs, pitches, out_ptrs, out_pitches, stream: int) -> None:
+    n = len(frame_ptrs)
+    fps = [(_P * len(f))(*f) for f in frame_ptrs]
+    pts = [(ctypes.c_int64 * len(p))(*p) for p in pitches]
+    fa = (_P * n)(*[ctypes.cast(f, _P) for f in fps])
+    pa = (_P * n)(*[ctypes.cast(p, _P) for p in pts])
+    oa = (_P * n)(*out_ptrs)
+    op = (ctypes.c_int64 * n)(*out_pitches)
+    _check(load().stitch_batch_frames(batch, fa, pa, oa, op, stream), "stitch_batch_frames")
+
+
+def stitch_batch_destroy(batch: int) -> None:
+    load().stitch_batch_destroy(batch)
+
+
+# ------------------------------------------------------------------------------------------------
+# torch-facing convenience wrapper
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def make_desc(cameras, canvas_w: int, canvas_h: int, levels: int, band_fp16: bool = False, out_float: bool = False,
+              path: str = "fused"):
+    """Build a stitch_rig_desc from objects with width, height, H (3x3) and gain."""
+    n = len(cameras)
+    arr = (stitch_camera * n)()
+    for k, c in enumerate(cameras):
+        arr[k].width = int(c.width)
+        arr[k].height = int(c.height)
+        Hm = np.asarray(c.H, dtype=np.float64).reshape(9)
+        for j in range(9):
+            arr[k].H[j] = float(Hm[j])
+        arr[k].gain = float(getattr(c, "gain", 1.0))
+    desc = stitch_rig_desc(n, ctypes.cast(arr, ctypes.POINTER(stitch_camera)), int(canvas_w), int(canvas_h),
+                           int(levels), int(bool(band_fp16)), int(bool(out_float)),
+                           STITCH_PATH_PLAIN if path == "plain" else STITCH_PATH_FUSED)
+    return desc, arr
+
+
+class Rig:
+    """A created rig: cameras, canvas and pyramid depth fixed; frames stitched on the GPU."""
+
+    def __init__(self, cameras, canvas_w: int, canvas_h: int, levels: int, band_fp16: bool = False,
+                 out_float: bool = False, path: str = "fused", device: int | None = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libstitch needs a CUDA GPU; no CPU fallback exists")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.cameras = list(cameras)
+        self.canvas_w, self.canvas_h, self.levels = int(canvas_w), int(canvas_h), int(levels)
+        self.out_float = bool(out_float)
+        self.band_fp16 = bool(band_fp16)
+        self.path = path
+        desc, keep = make_desc(self.cameras, canvas_w, canvas_h, levels, band_fp16, out_float, path)
+        self.handle = stitch_rig_create(desc, self.device)
+        del keep
+
+    def close(self):
+        if getattr(self, "handle", None):
+            stitch_rig_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def new_output(self):
+        import torch
+        dt = torch.float32 if self.out_float else torch.uint8
+        return torch.empty((self.canvas_h, self.canvas_w, 3), dtype=dt, device=f"cuda:{self.device}")
+
+    def stitch(self, frames, out=None, stream=None):
+        """frames: list of (H, W, 3) uint8 CUDA tensors (row-contiguous).  Returns the canvas tensor."""
+        if out is None:
+            out = self.new_output()
+        ptrs, pitches = _frame_args(frames, self.cameras)
+        assert out.is_cuda and out.stride(1) == 3 and out.stride(2) == 1
+        stitch_frames(self.handle, ptrs, pitches, out.data_ptr(), out.stride(0) * out.element_size(),
+                      _stream_handle(stream))
+        return out
+
+    def stitch_host(self, frames, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """frames: list of (H, W, 3) uint8 host arrays or pinned tensors; returns a host canvas."""
+        import torch
+        if out is None:
+            out = np.empty((self.canvas_h, self.canvas_w, 3), dtype=np.float32 if self.out_float else np.uint8)
+        ptrs, pitches = [], []
+        for f in frames:
+            if isinstance(f, torch.Tensor):
+                assert not f.is_cuda and f.stride(1) == 3 and f.stride(2) == 1
+                ptrs.append(f.data_ptr())
+                pitches.append(f.stride(0))
+            else:
+                assert f.flags.c_contiguous and f.dtype == np.uint8
+                ptrs.append(f.ctypes.data)
+                pitches.append(f.strides[0])
+        if isinstance(out, torch.Tensor):
+            optr, opitch = out.data_ptr(), out.stride(0) * out.element_size()
+        else:
+            optr, opitch = out.ctypes.data, out.strides[0]
+        stitch_frames_host(self.handle, ptrs, pitches, optr, opitch, _stream_handle(stream))
+        return out
+
+    def backward(self, frames, params, loss=None, grad=None, stream=None):
+        """params: (N, 9) float64 CUDA tensor (a11..a32, gain).  Returns (loss (1,), grad (N, 9))."""
+        import torch
+        assert params.is_cuda and params.dtype == torch.float64 and params.is_contiguous()
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float64, device=params.device)
+        if grad is None:
+            grad = torch.empty_like(params)
+        ptrs, pitches = _frame_args(frames, self.cameras)
+        stitch_backward(self.handle, ptrs, pitches, params.data_ptr(), loss.data_ptr(), grad.data_ptr(),
+                        _stream_handle(stream))
+        return loss, grad
+
+    def info(self) -> dict:
+        i = stitch_rig_get_info(self.handle)
+        return {"scratch_bytes": i.scratch_bytes, "num_kernels": i.num_kernels, "path": i.path,
+                "roi_pixels": i.roi_pixels}
+
+    def set_profiling(self, enable: bool):
+        stitch_rig_set_profiling(self.handle, enable)
+
+    def kernel_times(self) -> dict:
+        return stitch_rig_kernel_times(self.handle)
+
+
+def _frame_args(frames, cameras):
+    ptrs, pitches = [], []
+    for f, c in zip(frames, cameras):
+        assert f.is_cuda and f.dtype.itemsize == 1 and tuple(f.shape) == (c.height, c.width, 3), \
+            (tuple(f.shape), c.width, c.height)
+        assert f.stride(1) == 3 and f.stride(2) == 1
+        ptrs.append(f.data_ptr())
+        pitches.append(f.stride(0))
+    return ptrs, pitches

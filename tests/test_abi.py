@@ -1,0 +1,77 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared symbol, and rejects
+bad descriptors before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "stitch.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(stitch_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1810_03988_gb300 import _build, stitch
+    _build.build()
+    return stitch.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for n in ["stitch_rig_create", "stitch_frames", "stitch_backward", "stitch_rig_destroy", "stitch_batch_create",
+              "stitch_batch_frames", "stitch_batch_destroy", "stitch_status_string"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1810_03988_gb300 import stitch
+    for n in _declared_functions():
+        assert hasattr(lib, n), f"{n} declared in include/stitch.h but not exported"
+        assert n in stitch.SIGNATURES, f"{n} has no binding signature"
+
+
+def test_status_strings(lib):
+    from paper_1810_03988_gb300 import stitch
+    for s in range(6):
+        assert stitch.status_string(s).startswith("STITCH_")
+
+
+def test_create_rejects_bad_descriptors_without_a_device(lib):
+    from paper_1810_03988_gb300 import stitch
+    import synth
+    cfg = synth.config_2cam(scale=0.1)
+    out = ctypes.c_void_p()
+
+    def create(**kw):
+        desc, keep = stitch.make_desc(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels)
+        for k, v in kw.items():
+            setattr(desc, k, v)
+        return lib.stitch_rig_create(ctypes.byref(desc), 0, ctypes.byref(out))
+
+    assert create(num_cameras=0) == stitch.STITCH_EINVAL
+    assert create(num_cameras=stitch.STITCH_MAX_CAMERAS + 1) == stitch.STITCH_EINVAL
+    assert create(levels=0) == stitch.STITCH_EINVAL
+    assert create(levels=stitch.STITCH_MAX_LEVELS + 1) == stitch.STITCH_EINVAL
+    assert create(canvas_w=0) == stitch.STITCH_EINVAL
+    assert create(out_float=2) == stitch.STITCH_EINVAL
+    assert create(path=7) == stitch.STITCH_EINVAL
+    assert lib.stitch_rig_create(None, 0, ctypes.byref(out)) == stitch.STITCH_EINVAL
+    assert out.value is None
+    # destroy is NULL-safe
+    lib.stitch_rig_destroy(None)
+
+
+def test_null_rig_calls_are_rejected(lib):
+    from paper_1810_03988_gb300 import stitch
+    assert lib.stitch_frames(None, None, None, None, 0, None) == stitch.STITCH_EINVAL
+    assert lib.stitch_backward(None, None, None, None, None, None, None) == stitch.STITCH_EINVAL
+    assert lib.stitch_rig_get_info(None, None) == stitch.STITCH_EINVAL
+    assert lib.stitch_batch_frames(None, None, None, None, None, None) != stitch.STITCH_OK
