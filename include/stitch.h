@@ -62,8 +62,9 @@ typedef enum {
 
 typedef struct {
     int32_t width, height; /* source frame size in pixels, >= 1 */
-    double H[9];           /* camera->canvas homography, row-major; scaled internally so that the
-                              canvas->camera inverse has a33 = 1 (its sign must make a33 > 0) */
+    double H[9];           /* camera->canvas homography, row-major, with m31 u + m32 v + m33 > 0 for
+                              the camera's pixels (points in front); its inverse is scaled internally
+                              by 1/|a33|, so the canvas->camera map has a33 = +1 or -1 */
     float gain;            /* intensity gain applied to the sampled value (1 = unchanged) */
 } stitch_camera;
 
@@ -118,7 +119,8 @@ stitch_status stitch_frames_host(stitch_rig* rig, const uint8_t* const* host_fra
 /*
  * S7: overlap photometric loss and its gradient.
  *   params  DEVICE, num_cameras x 9 doubles per camera: a11 a12 a13 a21 a22 a23 a31 a32 gain of
- *           the canvas->camera map A (a33 = 1).  Validity masks are taken from these params.
+ *           the canvas->camera map A whose a33 is the rig's (+1 or -1, see stitch_rig_get_camera).
+ *           Validity masks are taken from these params.
  *   loss    DEVICE, 1 double: sum over canvas pixels and camera pairs i<j valid at the pixel of
  *           the squared RGB difference of the gained, bilinearly sampled [0,1] intensities
  *   grad    DEVICE, num_cameras x 9 doubles: d loss / d params, masks held constant (may be NULL)
@@ -142,6 +144,14 @@ typedef struct {
 } stitch_rig_info;
 
 stitch_status stitch_rig_get_info(const stitch_rig* rig, stitch_rig_info* info);
+
+/*
+ * The rig's canvas->camera map of camera `index` as used by every kernel: a[9] receives
+ * A = H^-1 / |(H^-1)_33| (row-major, a[8] = +1 or -1); *visible is 0 when the camera's footprint
+ * misses the canvas.  The first 8 entries and the camera gain are the stitch_backward params of
+ * the rig's own geometry.
+ */
+stitch_status stitch_rig_get_camera(const stitch_rig* rig, int32_t index, double* a, int32_t* visible);
 
 /*
  * Per-kernel CUDA-event timing of stitch_frames (events recorded on the call's stream around

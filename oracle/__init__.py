@@ -60,7 +60,7 @@ def _load():
             lib.oracle_forward.argtypes = [_I, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _P, _P, _P,
                                            _P, _P]
             lib.oracle_warp.argtypes = [_I, _I, _P, _D, _P, ctypes.c_int64, _I, _I, _P, _P]
-            lib.oracle_loss_grad.argtypes = [_I, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _P, _P]
+            lib.oracle_loss_grad.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _P, _P]
             for f in ("oracle_invert_h", "oracle_reduce", "oracle_expand", "oracle_regions", "oracle_forward",
                       "oracle_warp", "oracle_loss_grad"):
                 getattr(lib, f).restype = _I
@@ -85,7 +85,7 @@ def _check(rc: int, what: str):
 
 
 def invert_h(M) -> np.ndarray:
-    """Canvas->camera map A = M^-1 with a33 = 1."""
+    """Canvas->camera map A = M^-1 / |(M^-1)_33| (a33 = +1 or -1, the sign of w is kept)."""
     M = np.ascontiguousarray(M, dtype=np.float64).reshape(9)
     A = np.empty(9)
     _check(_load().oracle_invert_h(M.ctypes.data, A.ctypes.data), "invert_h")
@@ -205,11 +205,11 @@ def warp(cam, frame, canvas_w: int, canvas_h: int):
     return img, wr
 
 
-def loss_grad(widths, heights, params, frames, window, mask_params=None, grad: bool = True):
+def loss_grad(widths, heights, params, frames, window, mask_params=None, grad: bool = True, a33=None):
     """Overlap SSD loss (S7) and its gradient with respect to (a11..a32, gain) per camera.
 
-    ``params``/``mask_params``: (n, 9) arrays; ``window``: canvas (x0, y0, w, h).
-    Returns (loss, grad (n, 9) or None)."""
+    ``params``/``mask_params``: (n, 9) arrays; ``a33``: per-camera +-1 (default +1);
+    ``window``: canvas (x0, y0, w, h).  Returns (loss, grad (n, 9) or None)."""
     lib = _load()
     n = len(widths)
     Ws = np.asarray(widths, dtype=np.int32)
@@ -222,8 +222,10 @@ def loss_grad(widths, heights, params, frames, window, mask_params=None, grad: b
     loss = np.zeros(1)
     g = np.zeros((n, 9)) if grad else None
     x0, y0, w, h = window
+    s33 = None if a33 is None else np.ascontiguousarray(a33, dtype=np.float64).reshape(n)
     rc = lib.oracle_loss_grad(n, Ws.ctypes.data, Hs.ctypes.data, p.ctypes.data,
-                              None if mp is None else mp.ctypes.data, fp, pitches.ctypes.data, x0, y0, w, h,
-                              loss.ctypes.data, None if g is None else g.ctypes.data)
+                              None if mp is None else mp.ctypes.data, None if s33 is None else s33.ctypes.data,
+                              fp, pitches.ctypes.data, x0, y0, w, h, loss.ctypes.data,
+                              None if g is None else g.ctypes.data)
     _check(rc, "loss_grad")
     return float(loss[0]), g

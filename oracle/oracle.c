@@ -12,7 +12,9 @@
  * Burt-Adelson multiresolution spline with the readings listed in the design
  * notes (C1-C17).  Everything is evaluated literally in double precision:
  *
- *  S1 warp:   A_i = M_i^-1 scaled so a33 = 1.  For canvas pixel (x, y):
+ *  S1 warp:   A_i = M_i^-1 scaled by 1/|a33| (a positive factor, so the sign of w, which
+ *             tells points in front of the camera from points behind it, is kept; a33 = +-1).
+ *             For canvas pixel (x, y):
  *             (nu, nv, w) = A_i (x, y, 1); u = nu/w, v = nv/w.
  *             I_i = gain_i * bilinear(frame_i, clamp(u), clamp(v)) / 255,
  *             coordinates clamped to [0, W-1] x [0, H-1]; I_i = 0 where w <= 0.
@@ -67,8 +69,10 @@ static int reflect101(int i, int n) {
 /* ------------------------------------------------------------------------------------------ */
 /* homography inverse                                                                          */
 
-/* A = M^-1 scaled so that A[8] == 1.  Returns 0, or -1 when M is singular or the unscaled
- * inverse has a33 <= 0 (then the sign convention w > 0 <=> in front of the camera is lost). */
+/* A = M^-1 / |(M^-1)_33|, so a33 = +1 or -1.  Only a positive factor is applied: for a canvas
+ * point x = M p / w_c(p) the third component of M^-1 x is 1 / w_c(p), positive exactly when the
+ * camera point p is in front, and that sign must survive the scaling (a33 = -1 happens when the
+ * canvas origin lies behind the camera).  Returns 0, or -1 when M is singular or a33 == 0. */
 int oracle_invert_h(const double* M, double* A) {
     double a = M[0], b = M[1], c = M[2], d = M[3], e = M[4], f = M[5], g = M[6], h = M[7], k = M[8];
     double C00 = e * k - f * h, C01 = -(d * k - f * g), C02 = d * h - e * g;
@@ -84,9 +88,10 @@ int oracle_invert_h(const double* M, double* A) {
     inv[6] = C02 / det;
     inv[7] = -(a * h - b * g) / det;
     inv[8] = (a * e - b * d) / det;
-    if (!(inv[8] > 0.0)) return -1;
-    for (int i = 0; i < 9; ++i) A[i] = inv[i] / inv[8];
-    A[8] = 1.0;
+    double s = fabs(inv[8]);
+    if (!(s > 0.0)) return -1;
+    for (int i = 0; i < 9; ++i) A[i] = inv[i] / s;
+    A[8] = inv[8] > 0.0 ? 1.0 : -1.0;
     return 0;
 }
 
@@ -498,11 +503,11 @@ typedef struct {
 } gsample;
 
 /* I = gain * bilinear / 255 with clamped coordinates, and dI/du, dI/dv (zero on a clamped axis). */
-static void grad_sample(const int W, const int H, const uint8_t* px, int64_t pitch, const double* p, double x,
-                        double y, gsample* s) {
+static void grad_sample(const int W, const int H, const uint8_t* px, int64_t pitch, const double* p, double a33,
+                        double x, double y, gsample* s) {
     double nu = p[0] * x + p[1] * y + p[2];
     double nv = p[3] * x + p[4] * y + p[5];
-    double w = p[6] * x + p[7] * y + 1.0;
+    double w = p[6] * x + p[7] * y + a33;
     memset(s, 0, sizeof(*s));
     if (!(w > 0.0)) return;
     s->ok = 1;
@@ -528,25 +533,26 @@ static void grad_sample(const int W, const int H, const uint8_t* px, int64_t pit
     }
 }
 
-static int mask_valid(int W, int H, const double* p, double x, double y) {
+static int mask_valid(int W, int H, const double* p, double a33, double x, double y) {
     double nu = p[0] * x + p[1] * y + p[2];
     double nv = p[3] * x + p[4] * y + p[5];
-    double w = p[6] * x + p[7] * y + 1.0;
+    double w = p[6] * x + p[7] * y + a33;
     if (!(w > 0.0)) return 0;
     double u = nu / w, v = nv / w;
     return (u >= -0.5) && (u < W - 0.5) && (v >= -0.5) && (v < H - 0.5);
 }
 
 /*
- * params: n*9 doubles per camera (a11 a12 a13 a21 a22 a23 a31 a32 gain), a33 = 1, A maps canvas
- * to camera.  mask_params: same layout, used only for the validity masks (NULL: params).
+ * params: n*9 doubles per camera (a11 a12 a13 a21 a22 a23 a31 a32 gain) of the canvas->camera map
+ * A whose a33 is given per camera in a33 (+1 or -1, NULL: all +1).  mask_params: same layout,
+ * used only for the validity masks (NULL: params).
  * Window [x0,x0+w) x [y0,y0+h) of the canvas.  loss: 1 double; grad: n*9 doubles (may be NULL).
  * Rows are summed independently and then added in row order, so the result does not depend on
  * the number of threads.
  */
 int oracle_loss_grad(int n, const int32_t* Ws, const int32_t* Hs, const double* params, const double* mask_params,
-                     const uint8_t* const* frames, const int64_t* pitches, int x0, int y0, int w, int h,
-                     double* loss, double* grad) {
+                     const double* a33, const uint8_t* const* frames, const int64_t* pitches, int x0, int y0, int w,
+                     int h, double* loss, double* grad) {
     if (n < 1 || n > 64 || w < 0 || h < 0 || !loss) return OR_EINVAL;
     for (int i = 0; i < n; ++i)
         if (Ws[i] < 1 || Hs[i] < 1 || !frames[i] || pitches[i] < 3LL * Ws[i]) return OR_EINVAL;
@@ -564,12 +570,13 @@ int oracle_loss_grad(int n, const int32_t* Ws, const int32_t* Hs, const double* 
             double x = (double)(x0 + xx);
             int k = 0;
             for (int i = 0; i < n; ++i) {
-                val[i] = mask_valid(Ws[i], Hs[i], mp + 9 * i, x, y);
+                val[i] = mask_valid(Ws[i], Hs[i], mp + 9 * i, a33 ? a33[i] : 1.0, x, y);
                 k += val[i];
             }
             if (k < 2) continue;
             for (int i = 0; i < n; ++i)
-                if (val[i]) grad_sample(Ws[i], Hs[i], frames[i], pitches[i], params + 9 * i, x, y, &s[i]);
+                if (val[i])
+                    grad_sample(Ws[i], Hs[i], frames[i], pitches[i], params + 9 * i, a33 ? a33[i] : 1.0, x, y, &s[i]);
             for (int i = 0; i < n; ++i) {
                 if (!val[i]) continue;
                 for (int j = i + 1; j < n; ++j) {

@@ -84,9 +84,13 @@ bool invert_normalised(const double* M, double* A) {
     double inv[9] = {c00, c * h - b * k, b * f - c * e, c01, a * k - c * g, c * d - a * f, c02, b * g - a * h,
                      a * e - b * d};
     for (double& v : inv) v /= det;
-    if (!(inv[8] > 0.0)) return false;
-    for (int i = 0; i < 9; ++i) A[i] = inv[i] / inv[8];
-    A[8] = 1.0;
+    // scale by the positive factor 1/|a33|: the third component of A x stays 1/w_c(p) up to that
+    // factor, positive exactly for canvas points whose camera point p is in front (a33 = -1 when
+    // the canvas origin lies behind the camera)
+    const double s = fabs(inv[8]);
+    if (!(s > 0.0)) return false;
+    for (int i = 0; i < 9; ++i) A[i] = inv[i] / s;
+    A[8] = inv[8] > 0.0 ? 1.0 : -1.0;
     for (int i = 0; i < 9; ++i)
         if (!std::isfinite(A[i])) return false;
     return true;
@@ -161,7 +165,7 @@ stitch_status plan_camera(stitch_rig* r, int i) {
     const double qx[2] = {(double)o.x0, (double)(o.x1 - 1)}, qy[2] = {(double)o.y0, (double)(o.y1 - 1)};
     for (double x : qx)
         for (double y : qy)
-            if (!(d.A[6] * x + d.A[7] * y + 1.0 > 0.0)) return STITCH_EINVAL;
+            if (!(d.A[6] * x + d.A[7] * y + d.A[8] > 0.0)) return STITCH_EINVAL;
     r->roi_pixels += o.area();
     return STITCH_OK;
 }
@@ -315,6 +319,13 @@ stitch_status stitch_rig_get_info(const stitch_rig* r, stitch_rig_info* info) {
     info->num_kernels = r->kernels_per_frame;
     info->path = r->desc.path;
     info->roi_pixels = r->roi_pixels;
+    return STITCH_OK;
+}
+
+stitch_status stitch_rig_get_camera(const stitch_rig* r, int32_t index, double* a, int32_t* visible) {
+    if (!r || !a || index < 0 || index >= r->geom.ncam) return STITCH_EINVAL;
+    for (int k = 0; k < 9; ++k) a[k] = r->hcam[index].A[k];
+    if (visible) *visible = r->hcam[index].visible;
     return STITCH_OK;
 }
 

@@ -51,6 +51,7 @@ SIGNATURES = {
     "stitch_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "stitch_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "stitch_rig_get_info": (ctypes.c_int, [_P, ctypes.POINTER(stitch_rig_info)]),
+    "stitch_rig_get_camera": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.POINTER(ctypes.c_int32)]),
     "stitch_rig_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
     "stitch_rig_kernel_times": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "stitch_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
@@ -140,6 +141,13 @@ def stitch_rig_get_info(rig: int) -> stitch_rig_info:
     info = stitch_rig_info()
     _check(load().stitch_rig_get_info(rig, ctypes.byref(info)), "stitch_rig_get_info")
     return info
+
+
+def stitch_rig_get_camera(rig: int, index: int):
+    a = (ctypes.c_double * 9)()
+    vis = ctypes.c_int32()
+    _check(load().stitch_rig_get_camera(rig, index, a, ctypes.byref(vis)), "stitch_rig_get_camera")
+    return np.array(a[:]).reshape(3, 3), bool(vis.value)
 
 
 def stitch_rig_set_profiling(rig: int, enable: bool) -> None:
@@ -292,6 +300,10 @@ class Rig:
         stitch_backward(self.handle, ptrs, pitches, params.data_ptr(), loss.data_ptr(), grad.data_ptr(),
                         _stream_handle(stream))
         return loss, grad
+
+    def camera_map(self, index: int):
+        """(A as 3x3 with a33 = +-1, visible) of camera ``index`` as the kernels use it."""
+        return stitch_rig_get_camera(self.handle, index)
 
     def info(self) -> dict:
         i = stitch_rig_get_info(self.handle)

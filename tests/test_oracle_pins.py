@@ -288,6 +288,7 @@ def _params_of(cams, gains=None):
     ps = []
     for i, c in enumerate(cams):
         A = oracle.invert_h(c.H).reshape(9)
+        assert A[8] == 1.0
         ps.append(np.r_[A[:8], 1.0 if gains is None else gains[i]])
     return np.array(ps)
 
@@ -376,3 +377,19 @@ def test_invert_h_roundtrip():
     P = M @ A
     np.testing.assert_allclose(P / P[2, 2], np.eye(3), atol=1e-12)
     assert A[2, 2] == 1.0
+
+
+def test_inverse_keeps_the_in_front_sign():
+    """A camera yawed so far that the canvas origin is behind it: the inverse keeps w > 0 on the
+    camera's own footprint (a33 = -1 then), so its pixels are valid and the footprint centre maps
+    back to the image centre."""
+    cfg = synth.config_4x1080p(scale=0.25, frames=1)
+    cam = cfg.cameras[3]
+    A = oracle.invert_h(cam.H)
+    assert A[2, 2] == -1.0
+    p = cam.H @ np.array([(cam.width - 1) / 2, (cam.height - 1) / 2, 1.0])
+    q = A @ (p / p[2])
+    assert q[2] > 0
+    np.testing.assert_allclose(q[:2] / q[2], [(cam.width - 1) / 2, (cam.height - 1) / 2], atol=1e-9)
+    _, wr = oracle.warp(cam, np.zeros((cam.height, cam.width, 3), np.uint8), cfg.canvas_w, cfg.canvas_h)
+    assert (wr > 0).sum() > 0.5 * cam.width * cam.height
