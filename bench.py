@@ -314,7 +314,7 @@ def main():
             "roofline": roof, "step_roofline": step_roof, "plain_path": plain, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk, "gpu_launches": info["num_kernels"] * args.steps,
             "rig": {"scratch_bytes": info["scratch_bytes"], "roi_pixels": info["roi_pixels"],
-                    "kernels_per_step": info["num_kernels"]},
+                    "kernels_per_step": info["num_kernels"], "tiles": info["tiles"]},
             "kernel_times_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kt.items()},
             "frame_generation_s": gen_s,
         }

@@ -84,9 +84,9 @@ typedef struct stitch_rig stitch_rig; /* opaque, owned by the library */
 /*
  * Validate a rig, plan it and preallocate every buffer the per-frame path needs (the paper
  * precomputes grid/block sizes and static/dynamic memory at start-up, Sec. 4.3.2; this is the
- * counterpart).  Checks: each H is finite and invertible with a33 > 0 after inversion; each
- * camera's footprint is bounded (w > 0 at the four corners of its image rectangle); w > 0 over
- * every canvas region the camera's blend depends on.  `device` is the CUDA ordinal; create makes
+ * counterpart).  Checks: each H is finite and invertible with a non-zero a33 after inversion;
+ * each camera's footprint is bounded (w > 0 at the four corners of its image rectangle); w > 0
+ * over every canvas region the camera's blend depends on.  `device` is the CUDA ordinal; create makes
  * it current and leaves it current.  On success *out receives the rig; on failure *out is NULL.
  * Status: OK, EINVAL, ENOMEM, ECUDA.
  */
@@ -141,6 +141,13 @@ typedef struct {
     int32_t num_kernels;     /* kernel launches per stitch_frames call */
     int32_t path;            /* STITCH_PATH_* actually used */
     int64_t roi_pixels;      /* sum over cameras of level-0 pixels the path evaluates */
+    /* fused path: canvas tiles (64 x 32) by class, and camera tiles of the level-1 pass */
+    int32_t tiles_zero;      /* no camera: written as 0 */
+    int32_t tiles_solo;      /* one exclusive camera: the pyramid telescopes to its warp */
+    int32_t tiles_full2;     /* blended, at most 2 cameras */
+    int32_t tiles_full4;     /* blended, 3 or 4 cameras */
+    int32_t tiles_general;   /* blended, more than 4 cameras */
+    int32_t tiles_down1;     /* camera tiles that build Gaussian level 1 */
 } stitch_rig_info;
 
 stitch_status stitch_rig_get_info(const stitch_rig* rig, stitch_rig_info* info);

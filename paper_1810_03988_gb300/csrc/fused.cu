@@ -1,9 +1,1055 @@
-// Fused forward path (work in progress).
+// Fused forward path.
+//
+// Data that crosses HBM per frame: the source frames (read by `down1` and again by `up`), the
+// Gaussian level 1 of every camera (written by `down1`, read by `reduce` and `up`), the small
+// levels >= 2 and the output canvas.  Level 0 never leaves the chip and neither does the
+// collapsed level 1.
+//
+//   down1   per camera tile: warp + feather weights (S1, S2) of a level-0 tile and its halo into
+//           shared memory, both separable REDUCE passes on chip (S3), write G^1 (r, g, b, weight).
+//   reduce  G^{l+1} = REDUCE(G^l) for l >= 1, every camera in one launch.
+//   coarse  levels L-1 .. 2: Laplacian (S4) + normalised blend (S5) + collapse step (S6) fused,
+//           writing R^l on the canvas grid of level l.
+//   up      per canvas tile: level 1 bands of every contributing camera, blend and collapse to
+//           R^1 in shared memory; then level 0: warp again, Laplacian against EXPAND(G^1_i),
+//           blend, add EXPAND(R^1), mask, clamp, quantise and write the output.
+//
+// The per-level blend and collapse are evaluated in the equivalent form
+//   R^l = sum_i a_i (G^l_i + EXPAND(R^{l+1} - G^{l+1}_i)),  a_i = G^l(What_i) / S^l,
+// which follows from B^l = sum_i a_i (G^l_i - EXPAND(G^{l+1}_i)) and sum_i a_i = 1 wherever
+// S^l > 1e-12 (elsewhere R^l = EXPAND(R^{l+1})); it needs one EXPAND per camera and level.
+// At level 0, a_i = w_i / sum_j w_j with the raw feather weights.
+//
+// Canvas tiles of `up` are classified when the rig is created:
+//   ZERO   no camera's validity box meets the tile: the output is 0;
+//   SOLO   one camera c is valid with weight > 0 on every level-0 pixel that the tile's outputs
+//          depend on (the whole pyramid cone) and no other camera's validity box meets that
+//          region.  Then every weight pyramid of c is exactly 1 there, every other one exactly 0,
+//          B^l = L^l_c at every level and the collapse telescopes to G^0_c: the output is the
+//          clamped warp of camera c, with no pyramid work;
+//   FULL   up to 2 or 4 contributing cameras, everything in shared memory;
+//   GENERAL more cameras: a slower kernel that streams one camera at a time.
 #include "stitch_internal.cuh"
 
-stitch_status fused_plan(stitch_rig* r) { (void)r; return STITCH_EUNSUPPORTED; }
-stitch_status fused_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od, cudaStream_t s) {
-    (void)r; (void)fp; (void)od; (void)s;
-    return STITCH_EUNSUPPORTED;
+namespace {
+
+// ------------------------------------------------------------------------------------------------
+// storage of pyramid data between kernels: FP32 (float4) or FP16 (four halves)
+
+struct __align__(8) half4 {
+    __half2 a, b;
+};
+
+__device__ __forceinline__ float4 ld(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ float4 ld(const half4* p) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    __half2 a = *reinterpret_cast<const __half2*>(&u.x), b = *reinterpret_cast<const __half2*>(&u.y);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
 }
-void fused_release(stitch_rig* r) { (void)r; }
+__device__ __forceinline__ void st(float4* p, float4 v) { *p = v; }
+__device__ __forceinline__ void st(half4* p, float4 v) {
+    half4 h;
+    h.a = __floats2half2_rn(v.x, v.y);
+    h.b = __floats2half2_rn(v.z, v.w);
+    *p = h;
+}
+
+__device__ __forceinline__ float4 f4fma(float s, float4 v, float4 acc) {
+    return make_float4(fmaf(s, v.x, acc.x), fmaf(s, v.y, acc.y), fmaf(s, v.z, acc.z), fmaf(s, v.w, acc.w));
+}
+
+__constant__ float c_w5[5] = {1.f / 16, 4.f / 16, 6.f / 16, 4.f / 16, 1.f / 16};
+
+// Tile of work of the reduce kernel: camera and origin in level coordinates.
+struct Tile {
+    int cam, x0, y0, pad;
+};
+
+// A camera taking part in a tile, with its homography anchored near the tile (host-built).
+struct CamRef {
+    TileMap tm;
+    int cam, ax, ay, pad;
+};
+
+// down1 tile: camera, level-1 origin, and the cameras (CamRef range) whose validity box meets
+// the tile's level-0 inputs (for the weight normalisation), in camera order.
+struct D1Tile {
+    int cam, k0, j0, first, count, self, pad0, pad1;
+};
+
+// up tile: level-0 origin and the contributing cameras (CamRef range), in camera order.
+struct UpTile {
+    int x0, y0, first, count;
+};
+
+// ------------------------------------------------------------------------------------------------
+// down1
+
+constexpr int D1_TX = 32, D1_TY = 16;                        // level-1 outputs per tile
+constexpr int D1_SX = 2 * D1_TX + 3, D1_SY = 2 * D1_TY + 3;  // level-0 virtual region (67 x 35)
+constexpr int D1_THREADS = 256;
+constexpr int D1_MAXREF = 8;                                 // cameras per tile kept in shared memory
+constexpr size_t D1_SMEM = sizeof(float4) * (D1_SX * D1_SY + D1_TX * D1_SY);
+
+template <typename T>
+__global__ void __launch_bounds__(D1_THREADS) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
+                                                       const D1Tile* __restrict__ tiles,
+                                                       const CamRef* __restrict__ refs) {
+    extern __shared__ float4 smem[];
+    float4* s0 = smem;                  // [D1_SY][D1_SX] level 0 (virtual coordinates)
+    float4* sh = smem + D1_SX * D1_SY;  // [D1_SY][D1_TX] horizontally reduced
+    __shared__ CamRef cr[D1_MAXREF];
+    __shared__ int cw[D1_MAXREF], chh[D1_MAXREF];
+    __shared__ Rect cv[D1_MAXREF];
+
+    const D1Tile tl = tiles[blockIdx.x];
+    const int i = tl.cam;
+    const CamDev& ci = cams[i];
+    const Rect o1 = ci.Om[1], o0 = ci.Om[0];
+    const int k0 = tl.k0, j0 = tl.j0;              // level-1 tile origin
+    const int vx0 = 2 * k0 - 2, vy0 = 2 * j0 - 2;  // level-0 virtual origin
+    const int t = threadIdx.x;
+    const int na = tl.count;
+    if (t < min(na, D1_MAXREF)) {
+        cr[t] = refs[tl.first + t];
+        const CamDev& cj = cams[cr[t].cam];
+        cw[t] = cj.W;
+        chh[t] = cj.H;
+        cv[t] = cj.V;
+    }
+    __syncthreads();
+    const int self = tl.self;
+    const float scale = ci.gain * (1.0f / 255.0f);
+    const uint8_t* px_i = fp.p[i];
+    const long long pitch_i = fp.pitch[i];
+
+    // S1 + S2 on the virtual level-0 region
+    for (int q = t; q < D1_SX * D1_SY; q += D1_THREADS) {
+        const int r = q / D1_SX, c = q - r * D1_SX;
+        const int x = fold101(vx0 + c, g.nx[0]), y = fold101(vy0 + r, g.ny[0]);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (o0.contains(x, y)) {
+            float ws = 0.f, wi = 0.f;
+            float3 rgb = make_float3(0.f, 0.f, 0.f);
+            for (int a = 0; a < na; ++a) {
+                // references beyond the shared-memory slots are read from global memory
+                const bool sm = a < D1_MAXREF;
+                const CamRef& ref = sm ? cr[a] : refs[tl.first + a];
+                const CamDev* cjp = sm ? nullptr : &cams[ref.cam];
+                const int Wj = sm ? cw[a] : cjp->W, Hj = sm ? chh[a] : cjp->H;
+                const Rect Vj = sm ? cv[a] : cjp->V;
+                const SrcPos sp = map_point(ref.tm, (float)(x - ref.ax), (float)(y - ref.ay));
+                const float w = Vj.contains(x, y) ? feather_weight(sp, Wj, Hj) : 0.f;
+                ws += w;
+                if (a == self) {
+                    wi = w;
+                    rgb = bilinear_rgb(px_i, pitch_i, clamp_tap(sp, Wj, Hj), scale);
+                }
+            }
+            v = make_float4(rgb.x, rgb.y, rgb.z, ws > 0.f ? wi / ws : 0.f);
+        }
+        s0[q] = v;
+    }
+    __syncthreads();
+    // S3 horizontal pass: sh[r][p] = sum_m w(m) s0[r][2p + m]
+    for (int q = t; q < D1_TX * D1_SY; q += D1_THREADS) {
+        const int r = q / D1_TX, p = q - r * D1_TX;
+        const float4* row = s0 + r * D1_SX + 2 * p;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) acc = f4fma(c_w5[m], row[m], acc);
+        sh[q] = acc;
+    }
+    __syncthreads();
+    // S3 vertical pass and store of G^1
+    T* dst = reinterpret_cast<T*>(ci.FG[1]);
+    for (int q = t; q < D1_TX * D1_TY; q += D1_THREADS) {
+        const int jj = q / D1_TX, p = q - jj * D1_TX;
+        const int k = k0 + p, j = j0 + jj;
+        if (k >= o1.x1 || j >= o1.y1) continue;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int n = 0; n < 5; ++n) acc = f4fma(c_w5[n], sh[(2 * jj + n) * D1_TX + p], acc);
+        st(dst + (long long)(j - o1.y0) * o1.w() + (k - o1.x0), acc);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// reduce (levels >= 1 -> next), gather form; tiles of 32 x 8 outputs
+
+constexpr int R_TX = 32, R_TY = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(R_TX* R_TY) k_reduce(const CamDev* __restrict__ cams, RigGeom g, int l,
+                                                        const Tile* __restrict__ tiles) {
+    const Tile tl = tiles[blockIdx.x];
+    const CamDev& c = cams[tl.cam];
+    const Rect oc = c.Om[l + 1], of = c.Om[l];
+    const int k = tl.x0 + (threadIdx.x & (R_TX - 1)), j = tl.y0 + threadIdx.x / R_TX;
+    if (k >= oc.x1 || j >= oc.y1) return;
+    const T* src = reinterpret_cast<const T*>(c.FG[l]);
+    const int nxl = g.nx[l], nyl = g.ny[l];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int n = 0; n < 5; ++n) {
+        const int yy = fold101(2 * j + n - 2, nyl) - of.y0;
+        float4 row = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const int xx = fold101(2 * k + m - 2, nxl) - of.x0;
+            row = f4fma(c_w5[m], ld(src + (long long)yy * of.w() + xx), row);
+        }
+        acc = f4fma(c_w5[n], row, acc);
+    }
+    st(reinterpret_cast<T*>(c.FG[l + 1]) + (long long)(j - oc.y0) * oc.w() + (k - oc.x0), acc);
+}
+
+// EXPAND (rgb) of level data stored on rect r of a level of size nxc x nyc, at fine (x, y).
+template <typename T>
+__device__ __forceinline__ float3 expand_g(const T* __restrict__ buf, const Rect& r, int nxc, int nyc, int x, int y) {
+    const int ky0 = (y & 1) ? (y - 1) / 2 : y / 2 - 1, nky = (y & 1) ? 2 : 3;
+    const int kx0 = (x & 1) ? (x - 1) / 2 : x / 2 - 1, nkx = (x & 1) ? 2 : 3;
+    float3 acc = make_float3(0.f, 0.f, 0.f);
+    for (int a = 0; a < nky; ++a) {
+        const float wy = (y & 1) ? 0.5f : (a == 1 ? 0.75f : 0.125f);
+        const int yy = fold101(ky0 + a, nyc) - r.y0;
+        float3 row = make_float3(0.f, 0.f, 0.f);
+        for (int b = 0; b < nkx; ++b) {
+            const float wx = (x & 1) ? 0.5f : (b == 1 ? 0.75f : 0.125f);
+            const int xx = fold101(kx0 + b, nxc) - r.x0;
+            const float4 v = ld(buf + (long long)yy * r.w() + xx);
+            row.x = fmaf(wx, v.x, row.x);
+            row.y = fmaf(wx, v.y, row.y);
+            row.z = fmaf(wx, v.z, row.z);
+        }
+        acc.x = fmaf(wy, row.x, acc.x);
+        acc.y = fmaf(wy, row.y, acc.y);
+        acc.z = fmaf(wy, row.z, acc.z);
+    }
+    return acc;
+}
+
+// ------------------------------------------------------------------------------------------------
+// coarse: R^l for l = L-1 .. 2 on the canvas grid of level l
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse(const CamDev* __restrict__ cams, RigGeom g, int l, T* __restrict__ Rl,
+                                                 const T* __restrict__ Rc) {
+    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + threadIdx.x / 32;
+    if (x >= g.nx[l] || y >= g.ny[l]) return;
+    const bool top = l == g.levels - 1;
+    float nr = 0.f, ng = 0.f, nb = 0.f, s = 0.f;
+    for (int i = 0; i < g.ncam; ++i) {
+        const CamDev& c = cams[i];
+        if (!c.visible || !c.Z[l].contains(x, y)) continue;
+        const Rect o = c.Om[l];
+        const float4 gv = ld(reinterpret_cast<const T*>(c.FG[l]) + (long long)(y - o.y0) * o.w() + (x - o.x0));
+        float lr = gv.x, lg = gv.y, lb = gv.z;
+        if (!top) {
+            const float3 e = expand_g(reinterpret_cast<const T*>(c.FG[l + 1]), c.Om[l + 1], g.nx[l + 1], g.ny[l + 1], x, y);
+            lr -= e.x;
+            lg -= e.y;
+            lb -= e.z;
+        }
+        nr = fmaf(gv.w, lr, nr);
+        ng = fmaf(gv.w, lg, ng);
+        nb = fmaf(gv.w, lb, nb);
+        s += gv.w;
+    }
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s > 1e-12f) {
+        r.x = nr / s;
+        r.y = ng / s;
+        r.z = nb / s;
+    }
+    if (!top) {
+        const float3 e = expand_g(Rc, Rect{0, g.nx[l + 1], 0, g.ny[l + 1]}, g.nx[l + 1], g.ny[l + 1], x, y);
+        r.x += e.x;
+        r.y += e.y;
+        r.z += e.z;
+    }
+    st(Rl + (long long)y * g.nx[l] + x, r);
+}
+
+// ------------------------------------------------------------------------------------------------
+// up: levels 1 and 0 of one canvas tile
+
+constexpr int U_TX = 64, U_TY = 32;                     // level-0 pixels per tile
+constexpr int U_THREADS = 256;
+// virtual regions, origins (X0/2 - 2, Y0/2 - 2) at level 1 and (X0/4 - 2, Y0/4 - 2) at level 2
+constexpr int U1_X = U_TX / 2 + 4, U1_Y = U_TY / 2 + 4;  // 36 x 20
+constexpr int U2_X = U_TX / 4 + 4, U2_Y = U_TY / 4 + 4;  // 20 x 12
+constexpr int U1_N = U1_X * U1_Y, U2_N = U2_X * U2_Y;
+constexpr int U_QUADS0 = (U_TX / 2) * (U_TY / 2);        // 512 level-0 quads
+constexpr int U_QUADS1 = (U1_X / 2) * (U1_Y / 2);        // 180 level-1 quads
+
+// Polyphase EXPAND of a 2x2 block of fine samples whose coarse 3x3 neighbourhood starts at
+// a[oy][ox] (row stride ld): even-even, odd-even (x odd), even-odd (y odd), odd-odd.
+__device__ __forceinline__ void expand_quad(const float4* __restrict__ a, int ld, int ox, int oy, float3 e[4]) {
+    float3 he[3], ho[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float4 c0 = a[(oy + r) * ld + ox], c1 = a[(oy + r) * ld + ox + 1], c2 = a[(oy + r) * ld + ox + 2];
+        he[r] = make_float3(fmaf(0.75f, c1.x, 0.125f * (c0.x + c2.x)), fmaf(0.75f, c1.y, 0.125f * (c0.y + c2.y)),
+                            fmaf(0.75f, c1.z, 0.125f * (c0.z + c2.z)));
+        ho[r] = make_float3(0.5f * (c1.x + c2.x), 0.5f * (c1.y + c2.y), 0.5f * (c1.z + c2.z));
+    }
+    e[0] = make_float3(fmaf(0.75f, he[1].x, 0.125f * (he[0].x + he[2].x)),
+                       fmaf(0.75f, he[1].y, 0.125f * (he[0].y + he[2].y)),
+                       fmaf(0.75f, he[1].z, 0.125f * (he[0].z + he[2].z)));
+    e[1] = make_float3(fmaf(0.75f, ho[1].x, 0.125f * (ho[0].x + ho[2].x)),
+                       fmaf(0.75f, ho[1].y, 0.125f * (ho[0].y + ho[2].y)),
+                       fmaf(0.75f, ho[1].z, 0.125f * (ho[0].z + ho[2].z)));
+    e[2] = make_float3(0.5f * (he[1].x + he[2].x), 0.5f * (he[1].y + he[2].y), 0.5f * (he[1].z + he[2].z));
+    e[3] = make_float3(0.5f * (ho[1].x + ho[2].x), 0.5f * (ho[1].y + ho[2].y), 0.5f * (ho[1].z + ho[2].z));
+}
+
+// Write a tile's uint8 output staged in shared memory (rows of 3*U_TX bytes): 32-bit stores when
+// the destination rows are 4-byte aligned and the tile is full width, bytes otherwise.
+__device__ __forceinline__ void store_u8_tile(const unsigned char* __restrict__ stage, const OutDesc& od, int X0,
+                                              int Y0, int X1, int Y1) {
+    const int bytes = 3 * (X1 - X0), rows = Y1 - Y0;
+    unsigned char* base = (unsigned char*)od.ptr + (long long)Y0 * od.pitch + 3LL * X0;
+    const bool words = (bytes == 3 * U_TX) && ((((uintptr_t)base) | (uintptr_t)od.pitch) % 4 == 0);
+    if (words) {
+        constexpr int WPR = 3 * U_TX / 4;  // 48 words per row
+        for (int q = threadIdx.x; q < rows * WPR; q += blockDim.x) {
+            const int r = q / WPR, c = q - r * WPR;
+            reinterpret_cast<uint32_t*>(base + (long long)r * od.pitch)[c] =
+                reinterpret_cast<const uint32_t*>(stage + r * 3 * U_TX)[c];
+        }
+    } else {
+        for (int q = threadIdx.x; q < rows * bytes; q += blockDim.x) {
+            const int r = q / bytes, c = q - r * bytes;
+            base[(long long)r * od.pitch + c] = stage[r * 3 * U_TX + c];
+        }
+    }
+}
+
+__device__ __forceinline__ void put_pixel(unsigned char* stage, const OutDesc& od, int dx, int dy, int x, int y,
+                                          float r, float g, float b) {
+    if (od.is_float) {
+        float* o = (float*)((char*)od.ptr + (long long)y * od.pitch) + 3 * x;
+        o[0] = r;
+        o[1] = g;
+        o[2] = b;
+    } else {
+        unsigned char* o = stage + dy * 3 * U_TX + 3 * dx;
+        o[0] = quantize_u8(r);
+        o[1] = quantize_u8(g);
+        o[2] = quantize_u8(b);
+    }
+}
+
+// ZERO and SOLO tiles: output 0, or the clamped warp of the one exclusive camera.
+__global__ void __launch_bounds__(U_THREADS) k_up_simple(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
+                                                          OutDesc od, const UpTile* __restrict__ tiles,
+                                                          const CamRef* __restrict__ refs) {
+    __shared__ __align__(16) unsigned char stage[3 * U_TX * U_TY];
+    const UpTile tl = tiles[blockIdx.x];
+    const int X0 = tl.x0, Y0 = tl.y0;
+    const int X1 = min(X0 + U_TX, g.nx[0]), Y1 = min(Y0 + U_TY, g.ny[0]);
+    if (tl.count == 0) {
+        for (int p = threadIdx.x; p < U_TX * U_TY; p += U_THREADS) {
+            const int dx = p % U_TX, dy = p / U_TX;
+            if (X0 + dx < X1 && Y0 + dy < Y1) put_pixel(stage, od, dx, dy, X0 + dx, Y0 + dy, 0.f, 0.f, 0.f);
+        }
+    } else {
+        const CamRef cr = refs[tl.first];
+        const CamDev& c = cams[cr.cam];
+        const int W = c.W, H = c.H;
+        const float scale = c.gain * (1.0f / 255.0f);
+        const uint8_t* px = fp.p[cr.cam];
+        const long long pitch = fp.pitch[cr.cam];
+        for (int p = threadIdx.x; p < U_TX * U_TY; p += U_THREADS) {
+            const int dx = p % U_TX, dy = p / U_TX;
+            const int x = X0 + dx, y = Y0 + dy;
+            if (x >= X1 || y >= Y1) continue;
+            const SrcPos sp = map_point(cr.tm, (float)(x - cr.ax), (float)(y - cr.ay));
+            const float3 v = bilinear_rgb(px, pitch, clamp_tap(sp, W, H), scale);
+            put_pixel(stage, od, dx, dy, x, y, __saturatef(v.x), __saturatef(v.y), __saturatef(v.z));
+        }
+    }
+    if (!od.is_float) {
+        __syncthreads();
+        store_u8_tile(stage, od, X0, Y0, X1, Y1);
+    }
+}
+
+// FULL tiles with at most NC contributing cameras.
+template <typename T, int NC>
+__global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
+                                                        OutDesc od, const T* __restrict__ R2,
+                                                        const UpTile* __restrict__ tiles,
+                                                        const CamRef* __restrict__ refs) {
+    extern __shared__ float4 usm[];
+    float4* d1 = usm;                // [NC][U1_N]: G^1 of each camera, then R^1 - G^1
+    float4* d2 = d1 + NC * U1_N;     // [NC][U2_N]: G^2 of each camera, then R^2 - G^2
+    float4* r2s = d2 + NC * U2_N;    // [U2_N]: R^2
+    unsigned char* stage = reinterpret_cast<unsigned char*>(r2s + U2_N);
+    __shared__ CamRef cr[NC];
+    __shared__ Rect cv[NC], cz1[NC];
+    __shared__ int cwh[NC][2];
+    __shared__ float cscale[NC];
+
+    const int L = g.levels;
+    const UpTile tl = tiles[blockIdx.x];
+    const int nc = min(tl.count, NC);
+    const int X0 = tl.x0, Y0 = tl.y0;
+    const int X1 = min(X0 + U_TX, g.nx[0]), Y1 = min(Y0 + U_TY, g.ny[0]);
+    const int a1x = X0 / 2 - 2, a1y = Y0 / 2 - 2;
+    const int a2x = X0 / 4 - 2, a2y = Y0 / 4 - 2;
+    const int t = threadIdx.x;
+    if (t < nc) {
+        cr[t] = refs[tl.first + t];
+        const CamDev& c = cams[cr[t].cam];
+        cv[t] = c.V;
+        cz1[t] = L >= 2 ? c.Z[1] : Rect{0, 0, 0, 0};
+        cwh[t][0] = c.W;
+        cwh[t][1] = c.H;
+        cscale[t] = c.gain * (1.0f / 255.0f);
+    }
+    // loads of level 1 and 2 data
+    if (L >= 2) {
+        for (int q = t; q < nc * U1_N; q += U_THREADS) {
+            const int ci = q / U1_N, qq = q - ci * U1_N;
+            const CamDev& c = cams[refs[tl.first + ci].cam];
+            const int r = qq / U1_X, cc = qq - r * U1_X;
+            const int x = fold101(a1x + cc, g.nx[1]), y = fold101(a1y + r, g.ny[1]);
+            const Rect o1 = c.Om[1];
+            d1[q] = o1.contains(x, y)
+                        ? ld(reinterpret_cast<const T*>(c.FG[1]) + (long long)(y - o1.y0) * o1.w() + (x - o1.x0))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    if (L >= 3) {
+        for (int q = t; q < (nc + 1) * U2_N; q += U_THREADS) {
+            const int ci = q / U2_N, qq = q - ci * U2_N;
+            const int r = qq / U2_X, cc = qq - r * U2_X;
+            const int x = fold101(a2x + cc, g.nx[2]), y = fold101(a2y + r, g.ny[2]);
+            if (ci == nc) {
+                r2s[qq] = ld(R2 + (long long)y * g.nx[2] + x);
+            } else {
+                const CamDev& c = cams[refs[tl.first + ci].cam];
+                const Rect o2 = c.Om[2];
+                d2[q] = o2.contains(x, y)
+                            ? ld(reinterpret_cast<const T*>(c.FG[2]) + (long long)(y - o2.y0) * o2.w() + (x - o2.x0))
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+    __syncthreads();
+    if (L >= 3) {
+        // Delta^2_i = R^2 - G^2_i
+        for (int q = t; q < nc * U2_N; q += U_THREADS) {
+            const float4 rv = r2s[q % U2_N], gv = d2[q];
+            d2[q] = make_float4(rv.x - gv.x, rv.y - gv.y, rv.z - gv.z, 0.f);
+        }
+        __syncthreads();
+    }
+    if (L >= 2 && t < U_QUADS1) {
+        // level 1: R^1 = sum_i a_i (G^1_i + EXPAND(Delta^2_i)), then Delta^1_i = R^1 - G^1_i in place
+        const int qx = t % (U1_X / 2), qy = t / (U1_X / 2);
+        float3 num[4];
+        float den[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            num[k] = make_float3(0.f, 0.f, 0.f);
+            den[k] = 0.f;
+        }
+        int px[4], py[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            px[k] = fold101(a1x + 2 * qx + (k & 1), g.nx[1]);
+            py[k] = fold101(a1y + 2 * qy + (k >> 1), g.ny[1]);
+        }
+        for (int c = 0; c < nc; ++c) {
+            float3 e[4] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f),
+                           make_float3(0.f, 0.f, 0.f)};
+            if (L >= 3) expand_quad(d2 + c * U2_N, U2_X, qx, qy, e);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (!cz1[c].contains(px[k], py[k])) continue;
+                const float4 gv = d1[c * U1_N + (2 * qy + (k >> 1)) * U1_X + 2 * qx + (k & 1)];
+                num[k].x = fmaf(gv.w, gv.x + e[k].x, num[k].x);
+                num[k].y = fmaf(gv.w, gv.y + e[k].y, num[k].y);
+                num[k].z = fmaf(gv.w, gv.z + e[k].z, num[k].z);
+                den[k] += gv.w;
+            }
+        }
+        float3 r1[4];
+        bool need_plain = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (den[k] > 1e-12f) {
+                r1[k] = make_float3(num[k].x / den[k], num[k].y / den[k], num[k].z / den[k]);
+            } else {
+                r1[k] = make_float3(0.f, 0.f, 0.f);
+                need_plain = true;
+            }
+        }
+        if (need_plain && L >= 3) {
+            float3 e[4];
+            expand_quad(r2s, U2_X, qx, qy, e);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (!(den[k] > 1e-12f)) r1[k] = e[k];
+        }
+        for (int c = 0; c < nc; ++c) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float4& dv = d1[c * U1_N + (2 * qy + (k >> 1)) * U1_X + 2 * qx + (k & 1)];
+                dv = make_float4(r1[k].x - dv.x, r1[k].y - dv.y, r1[k].z - dv.z, 0.f);
+            }
+        }
+    }
+    __syncthreads();
+    // level 0: R^0 = sum_i w_i (G^0_i + EXPAND(Delta^1_i)) / sum_i w_i on covered pixels
+    for (int qd = t; qd < U_QUADS0; qd += U_THREADS) {
+        const int qx = qd % (U_TX / 2), qy = qd / (U_TX / 2);
+        float3 num[4];
+        float den[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            num[k] = make_float3(0.f, 0.f, 0.f);
+            den[k] = 0.f;
+        }
+        for (int c = 0; c < nc; ++c) {
+            float3 e[4] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f),
+                           make_float3(0.f, 0.f, 0.f)};
+            if (L >= 2) expand_quad(d1 + c * U1_N, U1_X, qx + 1, qy + 1, e);
+            const CamRef& r = cr[c];
+            const uint8_t* pxp = fp.p[r.cam];
+            const long long pitch = fp.pitch[r.cam];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
+                if (x >= X1 || y >= Y1 || !cv[c].contains(x, y)) continue;
+                const SrcPos sp = map_point(r.tm, (float)(x - r.ax), (float)(y - r.ay));
+                const float w = feather_weight(sp, cwh[c][0], cwh[c][1]);
+                if (!(w > 0.f)) continue;
+                const float3 v = bilinear_rgb(pxp, pitch, clamp_tap(sp, cwh[c][0], cwh[c][1]), cscale[c]);
+                num[k].x = fmaf(w, v.x + e[k].x, num[k].x);
+                num[k].y = fmaf(w, v.y + e[k].y, num[k].y);
+                num[k].z = fmaf(w, v.z + e[k].z, num[k].z);
+                den[k] += w;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int dx = 2 * qx + (k & 1), dy = 2 * qy + (k >> 1);
+            const int x = X0 + dx, y = Y0 + dy;
+            if (x >= X1 || y >= Y1) continue;
+            float rr = 0.f, gg = 0.f, bb = 0.f;
+            if (den[k] > 0.f) {
+                rr = __saturatef(num[k].x / den[k]);
+                gg = __saturatef(num[k].y / den[k]);
+                bb = __saturatef(num[k].z / den[k]);
+            }
+            put_pixel(stage, od, dx, dy, x, y, rr, gg, bb);
+        }
+    }
+    if (!od.is_float) {
+        __syncthreads();
+        store_u8_tile(stage, od, X0, Y0, X1, Y1);
+    }
+}
+
+template <int NC>
+constexpr size_t up_full_smem() {
+    return sizeof(float4) * (NC * U1_N + NC * U2_N + U2_N) + 3 * U_TX * U_TY;
+}
+
+// ------------------------------------------------------------------------------------------------
+// GENERAL tiles (more than 4 contributing cameras): one camera at a time through shared memory.
+
+constexpr int UG_PPT = U_TX * U_TY / U_THREADS;                  // level-0 pixels per thread (8)
+constexpr int UG1_X = U_TX / 2 + 2, UG1_Y = U_TY / 2 + 2;       // level-1 virtual region (34 x 18)
+constexpr int UG2_X = U_TX / 4 + 3, UG2_Y = U_TY / 4 + 3;       // level-2 virtual region (19 x 11)
+constexpr int UG1_N = UG1_X * UG1_Y;
+constexpr int UG1_PT = (UG1_N + U_THREADS - 1) / U_THREADS;
+
+// EXPAND at fine offset (dx, dy) from a virtual coarse array whose index 0 sits one coarse
+// sample before the fine origin's coarse position.
+__device__ __forceinline__ float3 expand_smem(const float4* __restrict__ a, int ldx, int dx, int dy) {
+    const int ky0 = (dy & 1) ? (dy + 1) / 2 : dy / 2, nky = (dy & 1) ? 2 : 3;
+    const int kx0 = (dx & 1) ? (dx + 1) / 2 : dx / 2, nkx = (dx & 1) ? 2 : 3;
+    float3 acc = make_float3(0.f, 0.f, 0.f);
+    for (int p = 0; p < nky; ++p) {
+        const float wy = (dy & 1) ? 0.5f : (p == 1 ? 0.75f : 0.125f);
+        float3 row = make_float3(0.f, 0.f, 0.f);
+        const float4* rp = a + (ky0 + p) * ldx + kx0;
+        for (int q = 0; q < nkx; ++q) {
+            const float wx = (dx & 1) ? 0.5f : (q == 1 ? 0.75f : 0.125f);
+            const float4 v = rp[q];
+            row.x = fmaf(wx, v.x, row.x);
+            row.y = fmaf(wx, v.y, row.y);
+            row.z = fmaf(wx, v.z, row.z);
+        }
+        acc.x = fmaf(wy, row.x, acc.x);
+        acc.y = fmaf(wy, row.y, acc.y);
+        acc.z = fmaf(wy, row.z, acc.z);
+    }
+    return acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(U_THREADS) k_up_general(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
+                                                           OutDesc od, const T* __restrict__ R2,
+                                                           const UpTile* __restrict__ tiles,
+                                                           const CamRef* __restrict__ refs) {
+    __shared__ float4 g1[UG1_N];
+    __shared__ float4 g2[UG2_X * UG2_Y];
+    __shared__ float4 r2[UG2_X * UG2_Y];
+    __shared__ float4 r1[UG1_N];
+
+    const int L = g.levels;
+    const UpTile tl = tiles[blockIdx.x];
+    const int X0 = tl.x0, Y0 = tl.y0;
+    const int X1 = min(X0 + U_TX, g.nx[0]), Y1 = min(Y0 + U_TY, g.ny[0]);
+    const int a1x = X0 / 2 - 1, a1y = Y0 / 2 - 1;          // level-1 virtual origin
+    const int a2x = (a1x - 1) / 2, a2y = (a1y - 1) / 2;    // level-2 virtual origin (a1 odd)
+    const int t = threadIdx.x;
+    const int na = tl.count;
+    if (L >= 3) {
+        for (int q = t; q < UG2_X * UG2_Y; q += U_THREADS) {
+            const int r = q / UG2_X, c = q - r * UG2_X;
+            const int x = fold101(a2x + c, g.nx[2]), y = fold101(a2y + r, g.ny[2]);
+            r2[q] = ld(R2 + (long long)y * g.nx[2] + x);
+        }
+    }
+    __syncthreads();
+
+    float ws[UG_PPT];
+    float4 n0[UG_PPT];
+#pragma unroll
+    for (int k = 0; k < UG_PPT; ++k) {
+        const int p = t + k * U_THREADS;
+        const int x = X0 + (p & (U_TX - 1)), y = Y0 + p / U_TX;
+        float s = 0.f;
+        if (x < X1 && y < Y1) {
+            for (int a = 0; a < na; ++a) {
+                const CamRef cr = refs[tl.first + a];
+                const CamDev& c = cams[cr.cam];
+                if (!c.V.contains(x, y)) continue;
+                const SrcPos sp = map_point(cr.tm, (float)(x - cr.ax), (float)(y - cr.ay));
+                s += feather_weight(sp, c.W, c.H);
+            }
+        }
+        ws[k] = s;
+        n0[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float4 n1[UG1_PT];
+#pragma unroll
+    for (int k = 0; k < UG1_PT; ++k) n1[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    for (int a = 0; a < na; ++a) {
+        const CamRef cr = refs[tl.first + a];
+        const int i = cr.cam;
+        const CamDev& c = cams[i];
+        if (L >= 2) {
+            const Rect o1 = c.Om[1];
+            const T* G1 = reinterpret_cast<const T*>(c.FG[1]);
+            for (int q = t; q < UG1_N; q += U_THREADS) {
+                const int r = q / UG1_X, cc = q - r * UG1_X;
+                const int x = fold101(a1x + cc, g.nx[1]), y = fold101(a1y + r, g.ny[1]);
+                g1[q] = o1.contains(x, y) ? ld(G1 + (long long)(y - o1.y0) * o1.w() + (x - o1.x0))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (L >= 3) {
+                const Rect o2 = c.Om[2];
+                const T* G2 = reinterpret_cast<const T*>(c.FG[2]);
+                for (int q = t; q < UG2_X * UG2_Y; q += U_THREADS) {
+                    const int r = q / UG2_X, cc = q - r * UG2_X;
+                    const int x = fold101(a2x + cc, g.nx[2]), y = fold101(a2y + r, g.ny[2]);
+                    g2[q] = o2.contains(x, y) ? ld(G2 + (long long)(y - o2.y0) * o2.w() + (x - o2.x0))
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            __syncthreads();
+            const Rect z1 = c.Z[1];
+#pragma unroll
+            for (int k = 0; k < UG1_PT; ++k) {
+                const int q = t + k * U_THREADS;
+                if (q >= UG1_N) break;
+                const int r = q / UG1_X, cc = q - r * UG1_X;
+                const int x = fold101(a1x + cc, g.nx[1]), y = fold101(a1y + r, g.ny[1]);
+                if (!z1.contains(x, y)) continue;
+                const float4 gv = g1[q];
+                float lr = gv.x, lg = gv.y, lb = gv.z;
+                if (L >= 3) {
+                    const float3 e = expand_smem(g2, UG2_X, cc - 1, r - 1);
+                    lr -= e.x;
+                    lg -= e.y;
+                    lb -= e.z;
+                }
+                n1[k].x = fmaf(gv.w, lr, n1[k].x);
+                n1[k].y = fmaf(gv.w, lg, n1[k].y);
+                n1[k].z = fmaf(gv.w, lb, n1[k].z);
+                n1[k].w += gv.w;
+            }
+        }
+        const float scale = c.gain * (1.0f / 255.0f);
+#pragma unroll
+        for (int k = 0; k < UG_PPT; ++k) {
+            const int p = t + k * U_THREADS;
+            const int dx = p & (U_TX - 1), dy = p / U_TX;
+            const int x = X0 + dx, y = Y0 + dy;
+            if (x >= X1 || y >= Y1 || !(ws[k] > 0.f) || !c.V.contains(x, y)) continue;
+            const SrcPos sp = map_point(cr.tm, (float)(x - cr.ax), (float)(y - cr.ay));
+            const float w = feather_weight(sp, c.W, c.H);
+            if (!(w > 0.f)) continue;
+            const float what = w / ws[k];
+            float3 v = bilinear_rgb(fp.p[i], fp.pitch[i], clamp_tap(sp, c.W, c.H), scale);
+            if (L >= 2) {
+                const float3 e = expand_smem(g1, UG1_X, dx, dy);
+                v.x -= e.x;
+                v.y -= e.y;
+                v.z -= e.z;
+            }
+            n0[k].x = fmaf(what, v.x, n0[k].x);
+            n0[k].y = fmaf(what, v.y, n0[k].y);
+            n0[k].z = fmaf(what, v.z, n0[k].z);
+            n0[k].w += what;
+        }
+        __syncthreads();
+    }
+    if (L >= 2) {
+#pragma unroll
+        for (int k = 0; k < UG1_PT; ++k) {
+            const int q = t + k * U_THREADS;
+            if (q >= UG1_N) break;
+            const int r = q / UG1_X, cc = q - r * UG1_X;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float s = n1[k].w;
+            if (s > 1e-12f) {
+                v.x = n1[k].x / s;
+                v.y = n1[k].y / s;
+                v.z = n1[k].z / s;
+            }
+            if (L >= 3) {
+                const float3 e = expand_smem(r2, UG2_X, cc - 1, r - 1);
+                v.x += e.x;
+                v.y += e.y;
+                v.z += e.z;
+            }
+            r1[q] = v;
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < UG_PPT; ++k) {
+        const int p = t + k * U_THREADS;
+        const int dx = p & (U_TX - 1), dy = p / U_TX;
+        const int x = X0 + dx, y = Y0 + dy;
+        if (x >= X1 || y >= Y1) continue;
+        float3 v = make_float3(0.f, 0.f, 0.f);
+        const float s = n0[k].w;
+        if (s > 1e-12f) {
+            v.x = n0[k].x / s;
+            v.y = n0[k].y / s;
+            v.z = n0[k].z / s;
+        }
+        if (L >= 2) {
+            const float3 e = expand_smem(r1, UG1_X, dx, dy);
+            v.x += e.x;
+            v.y += e.y;
+            v.z += e.z;
+        }
+        const bool cov = ws[k] > 0.f;
+        const float rr = cov ? __saturatef(v.x) : 0.f, gg = cov ? __saturatef(v.y) : 0.f,
+                    bb = cov ? __saturatef(v.z) : 0.f;
+        if (od.is_float) {
+            float* o = (float*)((char*)od.ptr + (long long)y * od.pitch) + 3 * x;
+            o[0] = rr;
+            o[1] = gg;
+            o[2] = bb;
+        } else {
+            unsigned char* o = (unsigned char*)od.ptr + (long long)y * od.pitch + 3 * x;
+            o[0] = quantize_u8(rr);
+            o[1] = quantize_u8(gg);
+            o[2] = quantize_u8(bb);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// host side
+
+enum UpKind { UP_SIMPLE = 0, UP_FULL2 = 1, UP_FULL4 = 2, UP_GENERAL = 3, UP_KINDS = 4 };
+
+struct FusedState {
+    D1Tile* d1_tiles = nullptr;
+    int n_d1 = 0;
+    Tile* red_tiles[MAXL] = {};  // tiles producing level l (l >= 2)
+    int n_red[MAXL] = {};
+    void* R[MAXL] = {};          // R^l on the canvas grid, l >= 2
+    CamRef* refs = nullptr;
+    UpTile* up_tiles[UP_KINDS] = {};
+    int n_up[UP_KINDS] = {};
+    int n_zero = 0, n_solo = 0;  // classification counts (UP_SIMPLE = zero + solo)
+    bool fp16 = false;
+};
+
+int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+template <typename V>
+stitch_status upload(stitch_rig* r, const std::vector<V>& v, V** out) {
+    *out = nullptr;
+    if (v.empty()) return STITCH_OK;
+    *out = (V*)rig_alloc(r, sizeof(V) * v.size());
+    if (!*out) return STITCH_ENOMEM;
+    STITCH_CUDA_TRY(cudaMemcpy(*out, v.data(), sizeof(V) * v.size(), cudaMemcpyHostToDevice));
+    return STITCH_OK;
+}
+
+bool rects_meet(const Rect& a, int x0, int x1, int y0, int y1) {
+    return !a.empty() && a.x0 < x1 && a.x1 > x0 && a.y0 < y1 && a.y1 > y0;
+}
+
+CamRef make_ref(const CamDev& c, int cam, int X, int Y) {
+    CamRef r;
+    int ax, ay;
+    tile_anchor(c.V, X, Y, &ax, &ay);
+    r.tm = make_tile_map(c.A, ax, ay);
+    r.cam = cam;
+    r.ax = ax;
+    r.ay = ay;
+    r.pad = 0;
+    return r;
+}
+
+// Level-0 rectangle on which the outputs of tile [x0,x1) x [y0,y1) depend (pyramid cone).
+Rect cone_level0(const RigGeom& g, int x0, int x1, int y0, int y1) {
+    const int L = g.levels;
+    Span xs[MAXL], ys[MAXL];
+    xs[0] = {x0, x1};
+    ys[0] = {y0, y1};
+    for (int l = 0; l + 1 < L; ++l) {
+        xs[l + 1] = expand_reads(xs[l], g.nx[l + 1]);
+        ys[l + 1] = expand_reads(ys[l], g.ny[l + 1]);
+    }
+    Span yx = xs[L - 1], yy = ys[L - 1];
+    for (int l = L - 2; l >= 0; --l) {
+        yx = span_union(xs[l], reduce_reads(yx, g.nx[l]));
+        yy = span_union(ys[l], reduce_reads(yy, g.ny[l]));
+    }
+    return make_rect(yx, yy);
+}
+
+// Camera c is valid with feather weight >= 0.5 at every pixel of rect q (convex quad: corners).
+bool solidly_inside(const CamDev& c, const Rect& q) {
+    const double xs[2] = {(double)q.x0, (double)(q.x1 - 1)}, ys[2] = {(double)q.y0, (double)(q.y1 - 1)};
+    for (double x : xs)
+        for (double y : ys) {
+            const double w = c.A[6] * x + c.A[7] * y + c.A[8];
+            if (!(w > 0.0)) return false;
+            const double u = (c.A[0] * x + c.A[1] * y + c.A[2]) / w, v = (c.A[3] * x + c.A[4] * y + c.A[5]) / w;
+            if (!(u >= 0.0 && u <= c.W - 1.0 && v >= 0.0 && v <= c.H - 1.0)) return false;
+        }
+    return true;
+}
+
+template <typename T>
+stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, const OutDesc& od, cudaStream_t s) {
+    const RigGeom& g = r->geom;
+    const int L = g.levels;
+    if (L >= 2 && fs->n_d1 > 0) {
+        prof_mark(r, "fused_down1", s);
+        k_down1<T><<<fs->n_d1, D1_THREADS, D1_SMEM, s>>>(r->dcam, g, fp, fs->d1_tiles, fs->refs);
+    }
+    for (int l = 1; l + 1 < L; ++l) {
+        if (fs->n_red[l + 1] == 0) continue;
+        prof_mark(r, "fused_reduce", s);
+        k_reduce<T><<<fs->n_red[l + 1], R_TX * R_TY, 0, s>>>(r->dcam, g, l, fs->red_tiles[l + 1]);
+    }
+    for (int l = L - 1; l >= 2; --l) {
+        prof_mark(r, "fused_coarse", s);
+        dim3 grid(cdiv(g.nx[l], 32), cdiv(g.ny[l], 8));
+        k_coarse<T><<<grid, 256, 0, s>>>(r->dcam, g, l, (T*)fs->R[l], l + 1 < L ? (const T*)fs->R[l + 1] : nullptr);
+    }
+    const T* R2 = L >= 3 ? (const T*)fs->R[2] : nullptr;
+    if (fs->n_up[UP_SIMPLE]) {
+        prof_mark(r, "fused_up_simple", s);
+        k_up_simple<<<fs->n_up[UP_SIMPLE], U_THREADS, 0, s>>>(r->dcam, g, fp, od, fs->up_tiles[UP_SIMPLE], fs->refs);
+    }
+    if (fs->n_up[UP_FULL2]) {
+        prof_mark(r, "fused_up_full", s);
+        k_up_full<T, 2><<<fs->n_up[UP_FULL2], U_THREADS, up_full_smem<2>(), s>>>(r->dcam, g, fp, od, R2,
+                                                                               fs->up_tiles[UP_FULL2], fs->refs);
+    }
+    if (fs->n_up[UP_FULL4]) {
+        prof_mark(r, "fused_up_full4", s);
+        k_up_full<T, 4><<<fs->n_up[UP_FULL4], U_THREADS, up_full_smem<4>(), s>>>(r->dcam, g, fp, od, R2,
+                                                                               fs->up_tiles[UP_FULL4], fs->refs);
+    }
+    if (fs->n_up[UP_GENERAL]) {
+        prof_mark(r, "fused_up_general", s);
+        k_up_general<T><<<fs->n_up[UP_GENERAL], U_THREADS, 0, s>>>(r->dcam, g, fp, od, R2,
+                                                                    fs->up_tiles[UP_GENERAL], fs->refs);
+    }
+    return launch_status();
+}
+
+template <typename T>
+stitch_status set_smem_attrs() {
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)up_full_smem<2>()));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)up_full_smem<4>()));
+    return STITCH_OK;
+}
+
+}  // namespace
+
+stitch_status fused_plan(stitch_rig* r) {
+    const RigGeom& g = r->geom;
+    const int L = g.levels;
+    FusedState* fs = new (std::nothrow) FusedState();
+    if (!fs) return STITCH_ENOMEM;
+    r->fused = fs;
+    fs->fp16 = r->desc.band_fp16 != 0;
+    const size_t elem = fs->fp16 ? sizeof(half4) : sizeof(float4);
+    std::vector<CamRef> refs;
+    std::vector<D1Tile> d1;
+    std::vector<Tile> red[MAXL];
+    for (int i = 0; i < g.ncam; ++i) {
+        CamDev& c = r->hcam[i];
+        if (!c.visible) continue;
+        for (int l = 1; l < L; ++l) {
+            c.FG[l] = rig_alloc(r, elem * (size_t)c.Om[l].area());
+            if (!c.FG[l]) return STITCH_ENOMEM;
+        }
+        if (L >= 2) {
+            const Rect o = c.Om[1];
+            for (int y = o.y0; y < o.y1; y += D1_TY)
+                for (int x = o.x0; x < o.x1; x += D1_TX) {
+                    // level-0 bounding box of the tile's inputs
+                    const int bx0 = std::max(2 * x - 2, 0), bx1 = std::min(2 * x - 2 + D1_SX, g.nx[0]);
+                    const int by0 = std::max(2 * y - 2, 0), by1 = std::min(2 * y - 2 + D1_SY, g.ny[0]);
+                    D1Tile t{i, x, y, (int)refs.size(), 0, -1, 0, 0};
+                    for (int j = 0; j < g.ncam; ++j) {
+                        const CamDev& cj = r->hcam[j];
+                        if (!cj.visible || (j != i && !rects_meet(cj.V, bx0, bx1, by0, by1))) continue;
+                        if (j == i) t.self = t.count;
+                        refs.push_back(make_ref(cj, j, bx0, by0));
+                        ++t.count;
+                    }
+                    d1.push_back(t);
+                }
+        }
+        for (int l = 2; l < L; ++l) {
+            const Rect o = c.Om[l];
+            for (int y = o.y0; y < o.y1; y += R_TY)
+                for (int x = o.x0; x < o.x1; x += R_TX) red[l].push_back({i, x, y, 0});
+        }
+    }
+    for (int l = 2; l < L; ++l) {
+        fs->R[l] = rig_alloc(r, elem * (size_t)g.nx[l] * g.ny[l]);
+        if (!fs->R[l]) return STITCH_ENOMEM;
+    }
+    // classify the canvas tiles of `up`
+    std::vector<UpTile> up[UP_KINDS];
+    for (int Y0 = 0; Y0 < g.ny[0]; Y0 += U_TY)
+        for (int X0 = 0; X0 < g.nx[0]; X0 += U_TX) {
+            const int X1 = std::min(X0 + U_TX, g.nx[0]), Y1 = std::min(Y0 + U_TY, g.ny[0]);
+            UpTile t{X0, Y0, (int)refs.size(), 0};
+            // level-1 region read by the tile (actual coordinates; folding stays inside it)
+            int bx0 = 0, bx1 = 0, by0 = 0, by1 = 0;
+            if (L >= 2) {
+                bx0 = std::max(X0 / 2 - 2, 0);
+                bx1 = std::min(X0 / 2 - 2 + U1_X, g.nx[1]);
+                by0 = std::max(Y0 / 2 - 2, 0);
+                by1 = std::min(Y0 / 2 - 2 + U1_Y, g.ny[1]);
+            }
+            int nv = 0, last_v = -1;
+            for (int j = 0; j < g.ncam; ++j) {
+                const CamDev& cj = r->hcam[j];
+                if (!cj.visible) continue;
+                const bool at0 = rects_meet(cj.V, X0, X1, Y0, Y1);
+                const bool at1 = L >= 2 && rects_meet(cj.Z[1], bx0, bx1, by0, by1);
+                if (at0) {
+                    ++nv;
+                    last_v = j;
+                }
+                if (!(at0 || at1)) continue;
+                refs.push_back(make_ref(cj, j, X0, Y0));
+                ++t.count;
+            }
+            int kind;
+            if (t.count == 0) {
+                kind = UP_SIMPLE;
+                ++fs->n_zero;
+            } else {
+                bool solo = false;
+                if (nv == 1) {
+                    const Rect cone = cone_level0(g, X0, X1, Y0, Y1);
+                    solo = solidly_inside(r->hcam[last_v], cone);
+                    for (int j = 0; j < g.ncam && solo; ++j)
+                        if (j != last_v && r->hcam[j].visible && rects_meet(r->hcam[j].V, cone.x0, cone.x1, cone.y0, cone.y1))
+                            solo = false;
+                }
+                if (solo) {
+                    // one reference: the exclusive camera
+                    refs.resize(t.first);
+                    refs.push_back(make_ref(r->hcam[last_v], last_v, X0, Y0));
+                    t.count = 1;
+                    kind = UP_SIMPLE;
+                    ++fs->n_solo;
+                } else if (t.count <= 2) {
+                    kind = UP_FULL2;
+                } else if (t.count <= 4) {
+                    kind = UP_FULL4;
+                } else {
+                    kind = UP_GENERAL;
+                }
+            }
+            up[kind].push_back(t);
+        }
+    stitch_status st = upload(r, refs, &fs->refs);
+    if (st != STITCH_OK) return st;
+    st = upload(r, d1, &fs->d1_tiles);
+    if (st != STITCH_OK) return st;
+    fs->n_d1 = (int)d1.size();
+    for (int l = 2; l < L; ++l) {
+        st = upload(r, red[l], &fs->red_tiles[l]);
+        if (st != STITCH_OK) return st;
+        fs->n_red[l] = (int)red[l].size();
+    }
+    for (int k = 0; k < UP_KINDS; ++k) {
+        st = upload(r, up[k], &fs->up_tiles[k]);
+        if (st != STITCH_OK) return st;
+        fs->n_up[k] = (int)up[k].size();
+    }
+    int kernels = 0;
+    if (L >= 2 && fs->n_d1 > 0) kernels += 1;
+    for (int l = 2; l < L; ++l) kernels += (fs->n_red[l] > 0) + 1;
+    for (int k = 0; k < UP_KINDS; ++k) kernels += fs->n_up[k] > 0;
+    r->kernels_per_frame = kernels;
+    return fs->fp16 ? set_smem_attrs<half4>() : set_smem_attrs<float4>();
+}
+
+stitch_status fused_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od, cudaStream_t s) {
+    FusedState* fs = (FusedState*)r->fused;
+    if (!fs) return STITCH_EINVAL;
+    return fs->fp16 ? launch_all<half4>(r, fs, fp, od, s) : launch_all<float4>(r, fs, fp, od, s);
+}
+
+void fused_release(stitch_rig* r) {
+    delete (FusedState*)r->fused;
+    r->fused = nullptr;
+}
+
+void fused_tile_counts(const stitch_rig* r, int counts[6]) {
+    const FusedState* fs = (const FusedState*)r->fused;
+    for (int k = 0; k < 6; ++k) counts[k] = 0;
+    if (!fs) return;
+    counts[0] = fs->n_zero;
+    counts[1] = fs->n_solo;
+    counts[2] = fs->n_up[UP_FULL2];
+    counts[3] = fs->n_up[UP_FULL4];
+    counts[4] = fs->n_up[UP_GENERAL];
+    counts[5] = fs->n_d1;
+}

@@ -10,72 +10,6 @@
 
 namespace {
 
-// ------------------------------------------------------------------------------------------------
-// index-range planning on one axis
-
-struct Span {
-    int lo, hi;  // half-open [lo, hi); empty when lo >= hi
-    bool empty() const { return hi <= lo; }
-};
-
-Span span_union(Span a, Span b) {
-    if (a.empty()) return b;
-    if (b.empty()) return a;
-    return {std::min(a.lo, b.lo), std::max(a.hi, b.hi)};
-}
-
-// finer-level samples read by REDUCE outputs in `c` (finer level of size n)
-Span reduce_reads(Span c, int n) {
-    if (c.empty()) return {0, 0};
-    int lo = n, hi = -1;
-    for (int k = c.lo; k < c.hi; ++k)
-        for (int m = -2; m <= 2; ++m) {
-            const int i = fold101(2 * k + m, n);
-            lo = std::min(lo, i);
-            hi = std::max(hi, i);
-        }
-    return {lo, hi + 1};
-}
-
-// coarser-level samples read by EXPAND outputs in `f` (coarser level of size n)
-Span expand_reads(Span f, int n) {
-    if (f.empty()) return {0, 0};
-    int lo = n, hi = -1;
-    for (int x = f.lo; x < f.hi; ++x) {
-        const int k0 = (x % 2 == 0) ? x / 2 - 1 : (x - 1) / 2;
-        const int k1 = (x % 2 == 0) ? x / 2 + 1 : (x + 1) / 2;
-        for (int k = k0; k <= k1; ++k) {
-            const int i = fold101(k, n);
-            lo = std::min(lo, i);
-            hi = std::max(hi, i);
-        }
-    }
-    return {lo, hi + 1};
-}
-
-// coarser-level outputs (level size nc) whose REDUCE support meets the finer span `f` (size nf)
-Span reduce_touch(Span f, int nf, int nc) {
-    if (f.empty()) return {0, 0};
-    int lo = nc, hi = -1;
-    for (int k = 0; k < nc; ++k) {
-        bool hit = false;
-        for (int m = -2; m <= 2 && !hit; ++m) {
-            const int i = fold101(2 * k + m, nf);
-            hit = i >= f.lo && i < f.hi;
-        }
-        if (hit) {
-            lo = std::min(lo, k);
-            hi = std::max(hi, k);
-        }
-    }
-    return hi < lo ? Span{0, 0} : Span{lo, hi + 1};
-}
-
-Rect make_rect(Span x, Span y) {
-    if (x.empty() || y.empty()) return Rect{0, 0, 0, 0};
-    return Rect{x.lo, x.hi, y.lo, y.hi};
-}
-
 bool invert_normalised(const double* M, double* A) {
     const double a = M[0], b = M[1], c = M[2], d = M[3], e = M[4], f = M[5], g = M[6], h = M[7], k = M[8];
     const double c00 = e * k - f * h, c01 = f * g - d * k, c02 = d * h - e * g;
@@ -319,6 +253,14 @@ stitch_status stitch_rig_get_info(const stitch_rig* r, stitch_rig_info* info) {
     info->num_kernels = r->kernels_per_frame;
     info->path = r->desc.path;
     info->roi_pixels = r->roi_pixels;
+    int tc[6];
+    fused_tile_counts(r, tc);
+    info->tiles_zero = tc[0];
+    info->tiles_solo = tc[1];
+    info->tiles_full2 = tc[2];
+    info->tiles_full4 = tc[3];
+    info->tiles_general = tc[4];
+    info->tiles_down1 = tc[5];
     return STITCH_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "stitch.h"
@@ -25,7 +26,7 @@ struct Rect {
 
 // Per-camera descriptor, resident in device memory for the life of a rig.
 struct CamDev {
-    double A[9];     // canvas -> camera homography, a33 = 1
+    double A[9];     // canvas -> camera homography, a33 = +1 or -1
     int W, H;        // source frame size
     float gain;
     int visible;     // 0 when the camera's footprint misses the canvas
@@ -63,6 +64,7 @@ struct OutDesc {
 
 // reflect-101 border folding on a grid of n samples: ... 2 1 | 0 1 2 ... n-1 | n-2 n-3 ...
 __host__ __device__ __forceinline__ int fold101(int i, int n) {
+    if (i >= 0 && i < n) return i;
     if (n == 1) return 0;
     const int period = 2 * n - 2;
     int r = i % period;
@@ -79,7 +81,7 @@ struct TileMap {
     float pu0, pu1, pu2, pv0, pv1, pv2, q0, q1, q2;
 };
 
-__device__ __forceinline__ TileMap make_tile_map(const double* A, int X, int Y) {
+__host__ __device__ __forceinline__ TileMap make_tile_map(const double* A, int X, int Y) {
     const double x = (double)X, y = (double)Y;
     const double n0 = A[0] * x + A[1] * y + A[2];
     const double m0 = A[3] * x + A[4] * y + A[5];
@@ -113,7 +115,9 @@ struct SrcPos {
 __device__ __forceinline__ SrcPos map_point(const TileMap& t, float dx, float dy) {
     SrcPos s;
     s.den = fmaf(t.q2, dy, fmaf(t.q1, dx, t.q0));
-    const float rden = __frcp_rn(s.den);
+    // approximate reciprocal (2 ulp): the offsets it scales are below ~100 px, so the error in
+    // the source position stays near 1e-5 px
+    const float rden = __fdividef(1.0f, s.den);
     float ru = fmaf(t.pu2, dy, fmaf(t.pu1, dx, t.pu0)) * rden;
     float rv = fmaf(t.pv2, dy, fmaf(t.pv1, dx, t.pv0)) * rden;
     ru = fminf(fmaxf(ru, -1.0e7f), 1.0e7f);
@@ -177,7 +181,7 @@ __device__ __forceinline__ float3 bilinear_rgb(const uint8_t* __restrict__ px, l
 
 // Anchor for a camera's tile map: the tile origin clamped into the camera's validity box, where
 // w > 0 is guaranteed by the planner.
-__device__ __forceinline__ void tile_anchor(const Rect& V, int X, int Y, int* ax, int* ay) {
+__host__ __device__ __forceinline__ void tile_anchor(const Rect& V, int X, int Y, int* ax, int* ay) {
     *ax = min(max(X, V.x0), V.x1 - 1);
     *ay = min(max(Y, V.y0), V.y1 - 1);
 }
@@ -186,6 +190,73 @@ __device__ __forceinline__ unsigned char quantize_u8(float v) {
     // v already clamped to [0, 1]; round half to even
     return (unsigned char)__float2int_rn(255.0f * v);
 }
+
+// ------------------------------------------------------------------------------------------------
+// index-range planning on one axis (host)
+
+struct Span {
+    int lo, hi;  // half-open [lo, hi); empty when lo >= hi
+    bool empty() const { return hi <= lo; }
+};
+
+inline Span span_union(Span a, Span b) {
+    if (a.empty()) return b;
+    if (b.empty()) return a;
+    return {std::min(a.lo, b.lo), std::max(a.hi, b.hi)};
+}
+
+// finer-level samples read by REDUCE outputs in `c` (finer level of size n)
+inline Span reduce_reads(Span c, int n) {
+    if (c.empty()) return {0, 0};
+    int lo = n, hi = -1;
+    for (int k = c.lo; k < c.hi; ++k)
+        for (int m = -2; m <= 2; ++m) {
+            const int i = fold101(2 * k + m, n);
+            lo = std::min(lo, i);
+            hi = std::max(hi, i);
+        }
+    return {lo, hi + 1};
+}
+
+// coarser-level samples read by EXPAND outputs in `f` (coarser level of size n)
+inline Span expand_reads(Span f, int n) {
+    if (f.empty()) return {0, 0};
+    int lo = n, hi = -1;
+    for (int x = f.lo; x < f.hi; ++x) {
+        const int k0 = (x % 2 == 0) ? x / 2 - 1 : (x - 1) / 2;
+        const int k1 = (x % 2 == 0) ? x / 2 + 1 : (x + 1) / 2;
+        for (int k = k0; k <= k1; ++k) {
+            const int i = fold101(k, n);
+            lo = std::min(lo, i);
+            hi = std::max(hi, i);
+        }
+    }
+    return {lo, hi + 1};
+}
+
+// coarser-level outputs (level size nc) whose REDUCE support meets the finer span `f` (size nf)
+inline Span reduce_touch(Span f, int nf, int nc) {
+    if (f.empty()) return {0, 0};
+    int lo = nc, hi = -1;
+    for (int k = 0; k < nc; ++k) {
+        bool hit = false;
+        for (int m = -2; m <= 2 && !hit; ++m) {
+            const int i = fold101(2 * k + m, nf);
+            hit = i >= f.lo && i < f.hi;
+        }
+        if (hit) {
+            lo = std::min(lo, k);
+            hi = std::max(hi, k);
+        }
+    }
+    return hi < lo ? Span{0, 0} : Span{lo, hi + 1};
+}
+
+inline Rect make_rect(Span x, Span y) {
+    if (x.empty() || y.empty()) return Rect{0, 0, 0, 0};
+    return Rect{x.lo, x.hi, y.lo, y.hi};
+}
+
 
 // ------------------------------------------------------------------------------------------------
 // host side
@@ -246,6 +317,7 @@ stitch_status plain_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od
 stitch_status fused_plan(stitch_rig* r);
 stitch_status fused_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od, cudaStream_t s);
 void fused_release(stitch_rig* r);
+void fused_tile_counts(const stitch_rig* r, int counts[6]);
 stitch_status backward_plan(stitch_rig* r);
 stitch_status backward_run(stitch_rig* r, const FramePtrs& fp, const double* params, double* loss, double* grad,
                            cudaStream_t s);

@@ -39,7 +39,9 @@ class stitch_rig_desc(ctypes.Structure):
 
 class stitch_rig_info(ctypes.Structure):
     _fields_ = [("scratch_bytes", ctypes.c_int64), ("num_kernels", ctypes.c_int32), ("path", ctypes.c_int32),
-                ("roi_pixels", ctypes.c_int64)]
+                ("roi_pixels", ctypes.c_int64), ("tiles_zero", ctypes.c_int32), ("tiles_solo", ctypes.c_int32),
+                ("tiles_full2", ctypes.c_int32), ("tiles_full4", ctypes.c_int32),
+                ("tiles_general", ctypes.c_int32), ("tiles_down1", ctypes.c_int32)]
 
 
 # every symbol declared by include/stitch.h, with its ctypes signature
@@ -308,7 +310,9 @@ class Rig:
     def info(self) -> dict:
         i = stitch_rig_get_info(self.handle)
         return {"scratch_bytes": i.scratch_bytes, "num_kernels": i.num_kernels, "path": i.path,
-                "roi_pixels": i.roi_pixels}
+                "roi_pixels": i.roi_pixels,
+                "tiles": {"zero": i.tiles_zero, "solo": i.tiles_solo, "full2": i.tiles_full2,
+                          "full4": i.tiles_full4, "general": i.tiles_general, "down1": i.tiles_down1}}
 
     def set_profiling(self, enable: bool):
         stitch_rig_set_profiling(self.handle, enable)

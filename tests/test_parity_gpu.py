@@ -9,7 +9,7 @@ from tests import gpu_util
 
 pytestmark = pytest.mark.gpu
 
-PATHS = ["plain"]
+PATHS = ["plain", "fused"]
 
 
 def _T(tx, ty):
@@ -207,3 +207,20 @@ def test_8x4k_full_size_windows(path):
     for (x0, y0, w, h) in gpu_util.sample_windows(cfg, 26, 32):
         ref = oracle.forward(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h, cfg.levels, window=(x0, y0, w, h))
         gpu_util.compare(got[y0:y0 + h, x0:x0 + w], ref, False)
+
+
+def test_tile_classes_are_exercised():
+    """The full-canvas parity cases above cover every class of canvas tile of the fused path."""
+    from paper_1810_03988_gb300 import Rig
+    cfg = synth.config_2cam()
+    with Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels) as rig:
+        t = rig.info()["tiles"]
+    assert t["zero"] > 0 and t["solo"] > 0 and t["full2"] > 0, t
+    cams = [Camera(40, 30, _T(gx * 25.3, gy * 18.7)) for gy in range(3) for gx in range(4)]
+    with Rig(cams, 120, 70, 4) as rig:
+        t = rig.info()["tiles"]
+    assert t["full4"] + t["general"] > 0 and t["general"] > 0, t
+    cfg = synth.config_8x4k(frames=1)
+    with Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels) as rig:
+        t = rig.info()["tiles"]
+    assert t["solo"] > 0 and t["full2"] > 0, t
