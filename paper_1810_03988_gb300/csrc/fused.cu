@@ -89,19 +89,19 @@ struct UpTile {
 constexpr int D1_TX = 32, D1_TY = 16;                        // level-1 outputs per tile
 constexpr int D1_SX = 2 * D1_TX + 3, D1_SY = 2 * D1_TY + 3;  // level-0 virtual region (67 x 35)
 constexpr int D1_THREADS = 256;
-constexpr int D1_MAXREF = 8;                                 // cameras per tile kept in shared memory
 constexpr size_t D1_SMEM = sizeof(float4) * (D1_SX * D1_SY + D1_TX * D1_SY);
 
+// Level-0 samples of the virtual region handled per thread in one chunk of rows.
+constexpr int D1_CHUNK_ROWS = (D1_SY + 1) / 2;                                   // 18
+constexpr int D1_NS = (D1_CHUNK_ROWS * D1_SX + D1_THREADS - 1) / D1_THREADS;   // 5
+
 template <typename T>
-__global__ void __launch_bounds__(D1_THREADS) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
+__global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
                                                        const D1Tile* __restrict__ tiles,
                                                        const CamRef* __restrict__ refs) {
     extern __shared__ float4 smem[];
     float4* s0 = smem;                  // [D1_SY][D1_SX] level 0 (virtual coordinates)
     float4* sh = smem + D1_SX * D1_SY;  // [D1_SY][D1_TX] horizontally reduced
-    __shared__ CamRef cr[D1_MAXREF];
-    __shared__ int cw[D1_MAXREF], chh[D1_MAXREF];
-    __shared__ Rect cv[D1_MAXREF];
 
     const D1Tile tl = tiles[blockIdx.x];
     const int i = tl.cam;
@@ -111,45 +111,54 @@ __global__ void __launch_bounds__(D1_THREADS) k_down1(const CamDev* __restrict__
     const int vx0 = 2 * k0 - 2, vy0 = 2 * j0 - 2;  // level-0 virtual origin
     const int t = threadIdx.x;
     const int na = tl.count;
-    if (t < min(na, D1_MAXREF)) {
-        cr[t] = refs[tl.first + t];
-        const CamDev& cj = cams[cr[t].cam];
-        cw[t] = cj.W;
-        chh[t] = cj.H;
-        cv[t] = cj.V;
-    }
-    __syncthreads();
-    const int self = tl.self;
     const float scale = ci.gain * (1.0f / 255.0f);
     const uint8_t* px_i = fp.p[i];
     const long long pitch_i = fp.pitch[i];
 
-    // S1 + S2 on the virtual level-0 region
-    for (int q = t; q < D1_SX * D1_SY; q += D1_THREADS) {
-        const int r = q / D1_SX, c = q - r * D1_SX;
-        const int x = fold101(vx0 + c, g.nx[0]), y = fold101(vy0 + r, g.ny[0]);
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (o0.contains(x, y)) {
-            float ws = 0.f, wi = 0.f;
-            float3 rgb = make_float3(0.f, 0.f, 0.f);
-            for (int a = 0; a < na; ++a) {
-                // references beyond the shared-memory slots are read from global memory
-                const bool sm = a < D1_MAXREF;
-                const CamRef& ref = sm ? cr[a] : refs[tl.first + a];
-                const CamDev* cjp = sm ? nullptr : &cams[ref.cam];
-                const int Wj = sm ? cw[a] : cjp->W, Hj = sm ? chh[a] : cjp->H;
-                const Rect Vj = sm ? cv[a] : cjp->V;
-                const SrcPos sp = map_point(ref.tm, (float)(x - ref.ax), (float)(y - ref.ay));
-                const float w = Vj.contains(x, y) ? feather_weight(sp, Wj, Hj) : 0.f;
-                ws += w;
-                if (a == self) {
-                    wi = w;
-                    rgb = bilinear_rgb(px_i, pitch_i, clamp_tap(sp, Wj, Hj), scale);
+    // S1 + S2 on the virtual level-0 region, two chunks of rows; cameras in the outer loop so
+    // each camera's constants are loaded once per chunk
+    for (int r0 = 0; r0 < D1_SY; r0 += D1_CHUNK_ROWS) {
+        const int nq = min(D1_CHUNK_ROWS, D1_SY - r0) * D1_SX;
+        float ws[D1_NS];
+        float4 val[D1_NS];
+#pragma unroll
+        for (int k = 0; k < D1_NS; ++k) {
+            ws[k] = 0.f;
+            val[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int a = 0; a < na; ++a) {
+            const CamRef ref = refs[tl.first + a];
+            const CamDev& cj = cams[ref.cam];
+            const Rect V = cj.V;
+            const int W = cj.W, H = cj.H;
+            const float Wm = (float)W - 0.5f, Hm = (float)H - 0.5f;
+            const float fU0 = (float)ref.tm.U0, fV0 = (float)ref.tm.V0;
+            const bool self = a == tl.self;
+#pragma unroll
+            for (int k = 0; k < D1_NS; ++k) {
+                const int q = t + k * D1_THREADS;
+                if (q >= nq) break;
+                const int r = r0 + q / D1_SX, c = q % D1_SX;
+                const int x = fold101(vx0 + c, g.nx[0]), y = fold101(vy0 + r, g.ny[0]);
+                const bool inV = V.contains(x, y);
+                if (!(self || inV) || !o0.contains(x, y)) continue;
+                const Pos p = map_pos(ref.tm, fU0, fV0, (float)(x - ref.ax), (float)(y - ref.ay));
+                const float w = inV ? weight_of(p, Wm, Hm) : 0.f;
+                ws[k] += w;
+                if (self) {
+                    const float3 v = sample_rgb(px_i, pitch_i, p, W, H, scale);
+                    val[k] = make_float4(v.x, v.y, v.z, w);
                 }
             }
-            v = make_float4(rgb.x, rgb.y, rgb.z, ws > 0.f ? wi / ws : 0.f);
         }
-        s0[q] = v;
+#pragma unroll
+        for (int k = 0; k < D1_NS; ++k) {
+            const int q = t + k * D1_THREADS;
+            if (q >= nq) break;
+            float4 v = val[k];
+            v.w = ws[k] > 0.f ? __fdividef(v.w, ws[k]) : 0.f;
+            s0[r0 * D1_SX + q] = v;
+        }
     }
     __syncthreads();
     // S3 horizontal pass: sh[r][p] = sum_m w(m) s0[r][2p + m]
@@ -176,113 +185,56 @@ __global__ void __launch_bounds__(D1_THREADS) k_down1(const CamDev* __restrict__
 }
 
 // ------------------------------------------------------------------------------------------------
-// reduce (levels >= 1 -> next), gather form; tiles of 32 x 8 outputs
+// reduce (levels >= 1 -> next)
 
-constexpr int R_TX = 32, R_TY = 8;
+// Tiled separable REDUCE: 32 x 16 outputs of level l+1 from a 67 x 35 input region of level l
+// staged in shared memory with coalesced loads.
+constexpr int RT_X = 32, RT_Y = 16;
+constexpr int RS_X = 2 * RT_X + 3, RS_Y = 2 * RT_Y + 3;
+constexpr size_t RT_SMEM = sizeof(float4) * (RS_X * RS_Y + RT_X * RS_Y);
 
 template <typename T>
-__global__ void __launch_bounds__(R_TX* R_TY) k_reduce(const CamDev* __restrict__ cams, RigGeom g, int l,
-                                                        const Tile* __restrict__ tiles) {
+__global__ void __launch_bounds__(256) k_reduce_t(const CamDev* __restrict__ cams, RigGeom g, int l,
+                                                   const Tile* __restrict__ tiles) {
+    extern __shared__ float4 smem[];
+    float4* s0 = smem;
+    float4* sh = smem + RS_X * RS_Y;
     const Tile tl = tiles[blockIdx.x];
     const CamDev& c = cams[tl.cam];
     const Rect oc = c.Om[l + 1], of = c.Om[l];
-    const int k = tl.x0 + (threadIdx.x & (R_TX - 1)), j = tl.y0 + threadIdx.x / R_TX;
-    if (k >= oc.x1 || j >= oc.y1) return;
+    const int vx0 = 2 * tl.x0 - 2, vy0 = 2 * tl.y0 - 2;
     const T* src = reinterpret_cast<const T*>(c.FG[l]);
     const int nxl = g.nx[l], nyl = g.ny[l];
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int n = 0; n < 5; ++n) {
-        const int yy = fold101(2 * j + n - 2, nyl) - of.y0;
-        float4 row = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            const int xx = fold101(2 * k + m - 2, nxl) - of.x0;
-            row = f4fma(c_w5[m], ld(src + (long long)yy * of.w() + xx), row);
-        }
-        acc = f4fma(c_w5[n], row, acc);
+    for (int q = threadIdx.x; q < RS_X * RS_Y; q += 256) {
+        const int r = q / RS_X, cc = q - r * RS_X;
+        const int x = fold101(vx0 + cc, nxl), y = fold101(vy0 + r, nyl);
+        s0[q] = of.contains(x, y) ? ld(src + (long long)(y - of.y0) * of.w() + (x - of.x0))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    st(reinterpret_cast<T*>(c.FG[l + 1]) + (long long)(j - oc.y0) * oc.w() + (k - oc.x0), acc);
-}
-
-// EXPAND (rgb) of level data stored on rect r of a level of size nxc x nyc, at fine (x, y).
-template <typename T>
-__device__ __forceinline__ float3 expand_g(const T* __restrict__ buf, const Rect& r, int nxc, int nyc, int x, int y) {
-    const int ky0 = (y & 1) ? (y - 1) / 2 : y / 2 - 1, nky = (y & 1) ? 2 : 3;
-    const int kx0 = (x & 1) ? (x - 1) / 2 : x / 2 - 1, nkx = (x & 1) ? 2 : 3;
-    float3 acc = make_float3(0.f, 0.f, 0.f);
-    for (int a = 0; a < nky; ++a) {
-        const float wy = (y & 1) ? 0.5f : (a == 1 ? 0.75f : 0.125f);
-        const int yy = fold101(ky0 + a, nyc) - r.y0;
-        float3 row = make_float3(0.f, 0.f, 0.f);
-        for (int b = 0; b < nkx; ++b) {
-            const float wx = (x & 1) ? 0.5f : (b == 1 ? 0.75f : 0.125f);
-            const int xx = fold101(kx0 + b, nxc) - r.x0;
-            const float4 v = ld(buf + (long long)yy * r.w() + xx);
-            row.x = fmaf(wx, v.x, row.x);
-            row.y = fmaf(wx, v.y, row.y);
-            row.z = fmaf(wx, v.z, row.z);
-        }
-        acc.x = fmaf(wy, row.x, acc.x);
-        acc.y = fmaf(wy, row.y, acc.y);
-        acc.z = fmaf(wy, row.z, acc.z);
+    __syncthreads();
+    for (int q = threadIdx.x; q < RT_X * RS_Y; q += 256) {
+        const int r = q / RT_X, p = q - r * RT_X;
+        const float4* row = s0 + r * RS_X + 2 * p;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) acc = f4fma(c_w5[m], row[m], acc);
+        sh[q] = acc;
     }
-    return acc;
+    __syncthreads();
+    T* dst = reinterpret_cast<T*>(c.FG[l + 1]);
+    for (int q = threadIdx.x; q < RT_X * RT_Y; q += 256) {
+        const int jj = q / RT_X, p = q - jj * RT_X;
+        const int k = tl.x0 + p, j = tl.y0 + jj;
+        if (k >= oc.x1 || j >= oc.y1) continue;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int n = 0; n < 5; ++n) acc = f4fma(c_w5[n], sh[(2 * jj + n) * RT_X + p], acc);
+        st(dst + (long long)(j - oc.y0) * oc.w() + (k - oc.x0), acc);
+    }
 }
 
 // ------------------------------------------------------------------------------------------------
-// coarse: R^l for l = L-1 .. 2 on the canvas grid of level l
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_coarse(const CamDev* __restrict__ cams, RigGeom g, int l, T* __restrict__ Rl,
-                                                 const T* __restrict__ Rc) {
-    const int x = blockIdx.x * 32 + (threadIdx.x & 31), y = blockIdx.y * 8 + threadIdx.x / 32;
-    if (x >= g.nx[l] || y >= g.ny[l]) return;
-    const bool top = l == g.levels - 1;
-    float nr = 0.f, ng = 0.f, nb = 0.f, s = 0.f;
-    for (int i = 0; i < g.ncam; ++i) {
-        const CamDev& c = cams[i];
-        if (!c.visible || !c.Z[l].contains(x, y)) continue;
-        const Rect o = c.Om[l];
-        const float4 gv = ld(reinterpret_cast<const T*>(c.FG[l]) + (long long)(y - o.y0) * o.w() + (x - o.x0));
-        float lr = gv.x, lg = gv.y, lb = gv.z;
-        if (!top) {
-            const float3 e = expand_g(reinterpret_cast<const T*>(c.FG[l + 1]), c.Om[l + 1], g.nx[l + 1], g.ny[l + 1], x, y);
-            lr -= e.x;
-            lg -= e.y;
-            lb -= e.z;
-        }
-        nr = fmaf(gv.w, lr, nr);
-        ng = fmaf(gv.w, lg, ng);
-        nb = fmaf(gv.w, lb, nb);
-        s += gv.w;
-    }
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (s > 1e-12f) {
-        r.x = nr / s;
-        r.y = ng / s;
-        r.z = nb / s;
-    }
-    if (!top) {
-        const float3 e = expand_g(Rc, Rect{0, g.nx[l + 1], 0, g.ny[l + 1]}, g.nx[l + 1], g.ny[l + 1], x, y);
-        r.x += e.x;
-        r.y += e.y;
-        r.z += e.z;
-    }
-    st(Rl + (long long)y * g.nx[l] + x, r);
-}
-
-// ------------------------------------------------------------------------------------------------
-// up: levels 1 and 0 of one canvas tile
-
-constexpr int U_TX = 64, U_TY = 32;                     // level-0 pixels per tile
-constexpr int U_THREADS = 256;
-// virtual regions, origins (X0/2 - 2, Y0/2 - 2) at level 1 and (X0/4 - 2, Y0/4 - 2) at level 2
-constexpr int U1_X = U_TX / 2 + 4, U1_Y = U_TY / 2 + 4;  // 36 x 20
-constexpr int U2_X = U_TX / 4 + 4, U2_Y = U_TY / 4 + 4;  // 20 x 12
-constexpr int U1_N = U1_X * U1_Y, U2_N = U2_X * U2_Y;
-constexpr int U_QUADS0 = (U_TX / 2) * (U_TY / 2);        // 512 level-0 quads
-constexpr int U_QUADS1 = (U1_X / 2) * (U1_Y / 2);        // 180 level-1 quads
+// coarse levels
 
 // Polyphase EXPAND of a 2x2 block of fine samples whose coarse 3x3 neighbourhood starts at
 // a[oy][ox] (row stride ld): even-even, odd-even (x odd), even-odd (y odd), odd-odd.
@@ -304,6 +256,127 @@ __device__ __forceinline__ void expand_quad(const float4* __restrict__ a, int ld
     e[2] = make_float3(0.5f * (he[1].x + he[2].x), 0.5f * (he[1].y + he[2].y), 0.5f * (he[1].z + he[2].z));
     e[3] = make_float3(0.5f * (ho[1].x + ho[2].x), 0.5f * (ho[1].y + ho[2].y), 0.5f * (ho[1].z + ho[2].z));
 }
+
+// Tiled coarse level: R^l on a 32 x 16 tile of level l (l >= 2), cameras in chunks of 4.
+// Virtual level-(l+1) region: origin (X0/2 - 2, Y0/2 - 2), 20 x 12.
+constexpr int CT_X = 32, CT_Y = 16, CT_NC = 2;
+constexpr int CC_X = CT_X / 2 + 4, CC_Y = CT_Y / 2 + 4;
+constexpr int CC_N = CC_X * CC_Y, CT_N = CT_X * CT_Y;
+constexpr int CT_QUADS = (CT_X / 2) * (CT_Y / 2);  // 128
+
+struct LevelTile {
+    int x0, y0, first, count;  // level origin, range of camera indices in the list
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_t(const CamDev* __restrict__ cams, RigGeom g, int l,
+                                                   T* __restrict__ Rl, const T* __restrict__ Rc,
+                                                   const LevelTile* __restrict__ tiles,
+                                                   const int* __restrict__ camlist) {
+    __shared__ float4 rc[CC_N];             // R^{l+1}
+    __shared__ float4 gl[CT_NC][CT_N];      // G^l of each camera of the chunk
+    __shared__ float4 gc[CT_NC][CC_N];      // G^{l+1}, then R^{l+1} - G^{l+1}
+    const LevelTile tl = tiles[blockIdx.x];
+    const bool top = l == g.levels - 1;
+    const int X0 = tl.x0, Y0 = tl.y0;
+    const int ax = X0 / 2 - 2, ay = Y0 / 2 - 2;
+    const int nxl = g.nx[l], nyl = g.ny[l];
+    const int t = threadIdx.x;
+    if (!top) {
+        for (int q = t; q < CC_N; q += 256) {
+            const int r = q / CC_X, c = q - r * CC_X;
+            const int x = fold101(ax + c, g.nx[l + 1]), y = fold101(ay + r, g.ny[l + 1]);
+            rc[q] = ld(Rc + (long long)y * g.nx[l + 1] + x);
+        }
+    }
+    const int qx = t % (CT_X / 2), qy = t / (CT_X / 2);
+    const bool has_quad = t < CT_QUADS;
+    float3 num[4];
+    float den[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        num[k] = make_float3(0.f, 0.f, 0.f);
+        den[k] = 0.f;
+    }
+    for (int c0 = 0; c0 < tl.count; c0 += CT_NC) {
+        const int nc = min(CT_NC, tl.count - c0);
+        __syncthreads();
+        for (int q = t; q < nc * CT_N; q += 256) {
+            const int ci = q / CT_N, qq = q - ci * CT_N;
+            const CamDev& c = cams[camlist[tl.first + c0 + ci]];
+            const int x = X0 + qq % CT_X, y = Y0 + qq / CT_X;
+            const Rect o = c.Om[l];
+            gl[ci][qq] = o.contains(x, y) ? ld(reinterpret_cast<const T*>(c.FG[l]) + (long long)(y - o.y0) * o.w() + (x - o.x0))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (!top) {
+            for (int q = t; q < nc * CC_N; q += 256) {
+                const int ci = q / CC_N, qq = q - ci * CC_N;
+                const CamDev& c = cams[camlist[tl.first + c0 + ci]];
+                const int r = qq / CC_X, cc = qq - r * CC_X;
+                const int x = fold101(ax + cc, g.nx[l + 1]), y = fold101(ay + r, g.ny[l + 1]);
+                const Rect o = c.Om[l + 1];
+                gc[ci][qq] = o.contains(x, y)
+                                 ? ld(reinterpret_cast<const T*>(c.FG[l + 1]) + (long long)(y - o.y0) * o.w() + (x - o.x0))
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        __syncthreads();
+        if (!top) {
+            for (int q = t; q < nc * CC_N; q += 256) {
+                const int ci = q / CC_N, qq = q - ci * CC_N;
+                const float4 a = rc[qq], b = gc[ci][qq];
+                gc[ci][qq] = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, 0.f);
+            }
+            __syncthreads();
+        }
+        if (has_quad) {
+            for (int ci = 0; ci < nc; ++ci) {
+                const Rect z = cams[camlist[tl.first + c0 + ci]].Z[l];
+                float3 e[4] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f),
+                               make_float3(0.f, 0.f, 0.f)};
+                if (!top) expand_quad(gc[ci], CC_X, qx + 1, qy + 1, e);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
+                    if (!z.contains(x, y)) continue;
+                    const float4 gv = gl[ci][(2 * qy + (k >> 1)) * CT_X + 2 * qx + (k & 1)];
+                    num[k].x = fmaf(gv.w, gv.x + e[k].x, num[k].x);
+                    num[k].y = fmaf(gv.w, gv.y + e[k].y, num[k].y);
+                    num[k].z = fmaf(gv.w, gv.z + e[k].z, num[k].z);
+                    den[k] += gv.w;
+                }
+            }
+        }
+    }
+    if (!has_quad) return;
+    float3 e[4] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f),
+                   make_float3(0.f, 0.f, 0.f)};
+    bool need = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) need |= !(den[k] > 1e-12f);
+    if (need && !top) expand_quad(rc, CC_X, qx + 1, qy + 1, e);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
+        if (x >= nxl || y >= nyl) continue;
+        float4 r = make_float4(e[k].x, e[k].y, e[k].z, 0.f);
+        if (den[k] > 1e-12f) r = make_float4(num[k].x / den[k], num[k].y / den[k], num[k].z / den[k], 0.f);
+        st(Rl + (long long)y * nxl + x, r);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// up: levels 1 and 0 of one canvas tile
+
+constexpr int U_TX = 64, U_TY = 32;                     // level-0 pixels per tile
+constexpr int U_THREADS = 256;
+// virtual regions, origins (X0/2 - 2, Y0/2 - 2) at level 1 and (X0/4 - 2, Y0/4 - 2) at level 2
+constexpr int U1_X = U_TX / 2 + 4, U1_Y = U_TY / 2 + 4;  // 36 x 20
+constexpr int U2_X = U_TX / 4 + 4, U2_Y = U_TY / 4 + 4;  // 20 x 12
+constexpr int U1_N = U1_X * U1_Y, U2_N = U2_X * U2_Y;
+constexpr int U_QUADS0 = (U_TX / 2) * (U_TY / 2);        // 512 level-0 quads
+constexpr int U_QUADS1 = (U1_X / 2) * (U1_Y / 2);        // 180 level-1 quads
 
 // Write a tile's uint8 output staged in shared memory (rows of 3*U_TX bytes): 32-bit stores when
 // the destination rows are 4-byte aligned and the tile is full width, bytes otherwise.
@@ -360,14 +433,15 @@ __global__ void __launch_bounds__(U_THREADS) k_up_simple(const CamDev* __restric
         const CamDev& c = cams[cr.cam];
         const int W = c.W, H = c.H;
         const float scale = c.gain * (1.0f / 255.0f);
+        const float fU0 = (float)cr.tm.U0, fV0 = (float)cr.tm.V0;
         const uint8_t* px = fp.p[cr.cam];
         const long long pitch = fp.pitch[cr.cam];
         for (int p = threadIdx.x; p < U_TX * U_TY; p += U_THREADS) {
             const int dx = p % U_TX, dy = p / U_TX;
             const int x = X0 + dx, y = Y0 + dy;
             if (x >= X1 || y >= Y1) continue;
-            const SrcPos sp = map_point(cr.tm, (float)(x - cr.ax), (float)(y - cr.ay));
-            const float3 v = bilinear_rgb(px, pitch, clamp_tap(sp, W, H), scale);
+            const Pos ps = map_pos(cr.tm, fU0, fV0, (float)(x - cr.ax), (float)(y - cr.ay));
+            const float3 v = sample_rgb(px, pitch, ps, W, H, scale);
             put_pixel(stage, od, dx, dy, x, y, __saturatef(v.x), __saturatef(v.y), __saturatef(v.z));
         }
     }
@@ -391,7 +465,7 @@ __global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict_
     __shared__ CamRef cr[NC];
     __shared__ Rect cv[NC], cz1[NC];
     __shared__ int cwh[NC][2];
-    __shared__ float cscale[NC];
+    __shared__ float cscale[NC], cwm[NC], chm[NC];
 
     const int L = g.levels;
     const UpTile tl = tiles[blockIdx.x];
@@ -408,6 +482,8 @@ __global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict_
         cz1[t] = L >= 2 ? c.Z[1] : Rect{0, 0, 0, 0};
         cwh[t][0] = c.W;
         cwh[t][1] = c.H;
+        cwm[t] = (float)c.W - 0.5f;
+        chm[t] = (float)c.H - 0.5f;
         cscale[t] = c.gain * (1.0f / 255.0f);
     }
     // loads of level 1 and 2 data
@@ -522,14 +598,15 @@ __global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict_
             const CamRef& r = cr[c];
             const uint8_t* pxp = fp.p[r.cam];
             const long long pitch = fp.pitch[r.cam];
+            const float fU0 = (float)r.tm.U0, fV0 = (float)r.tm.V0;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
                 if (x >= X1 || y >= Y1 || !cv[c].contains(x, y)) continue;
-                const SrcPos sp = map_point(r.tm, (float)(x - r.ax), (float)(y - r.ay));
-                const float w = feather_weight(sp, cwh[c][0], cwh[c][1]);
+                const Pos ps = map_pos(r.tm, fU0, fV0, (float)(x - r.ax), (float)(y - r.ay));
+                const float w = weight_of(ps, cwm[c], chm[c]);
                 if (!(w > 0.f)) continue;
-                const float3 v = bilinear_rgb(pxp, pitch, clamp_tap(sp, cwh[c][0], cwh[c][1]), cscale[c]);
+                const float3 v = sample_rgb(pxp, pitch, ps, cwh[c][0], cwh[c][1], cscale[c]);
                 num[k].x = fmaf(w, v.x + e[k].x, num[k].x);
                 num[k].y = fmaf(w, v.y + e[k].y, num[k].y);
                 num[k].z = fmaf(w, v.z + e[k].z, num[k].z);
@@ -784,6 +861,9 @@ struct FusedState {
     int n_d1 = 0;
     Tile* red_tiles[MAXL] = {};  // tiles producing level l (l >= 2)
     int n_red[MAXL] = {};
+    LevelTile* co_tiles[MAXL] = {};  // coarse tiles of level l (l >= 2)
+    int n_co[MAXL] = {};
+    int* camlist = nullptr;
     void* R[MAXL] = {};          // R^l on the canvas grid, l >= 2
     CamRef* refs = nullptr;
     UpTile* up_tiles[UP_KINDS] = {};
@@ -791,8 +871,6 @@ struct FusedState {
     int n_zero = 0, n_solo = 0;  // classification counts (UP_SIMPLE = zero + solo)
     bool fp16 = false;
 };
-
-int cdiv(int a, int b) { return (a + b - 1) / b; }
 
 template <typename V>
 stitch_status upload(stitch_rig* r, const std::vector<V>& v, V** out) {
@@ -862,12 +940,13 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
     for (int l = 1; l + 1 < L; ++l) {
         if (fs->n_red[l + 1] == 0) continue;
         prof_mark(r, "fused_reduce", s);
-        k_reduce<T><<<fs->n_red[l + 1], R_TX * R_TY, 0, s>>>(r->dcam, g, l, fs->red_tiles[l + 1]);
+        k_reduce_t<T><<<fs->n_red[l + 1], 256, RT_SMEM, s>>>(r->dcam, g, l, fs->red_tiles[l + 1]);
     }
     for (int l = L - 1; l >= 2; --l) {
         prof_mark(r, "fused_coarse", s);
-        dim3 grid(cdiv(g.nx[l], 32), cdiv(g.ny[l], 8));
-        k_coarse<T><<<grid, 256, 0, s>>>(r->dcam, g, l, (T*)fs->R[l], l + 1 < L ? (const T*)fs->R[l + 1] : nullptr);
+        k_coarse_t<T><<<fs->n_co[l], 256, 0, s>>>(r->dcam, g, l, (T*)fs->R[l],
+                                                   l + 1 < L ? (const T*)fs->R[l + 1] : nullptr, fs->co_tiles[l],
+                                                   fs->camlist);
     }
     const T* R2 = L >= 3 ? (const T*)fs->R[2] : nullptr;
     if (fs->n_up[UP_SIMPLE]) {
@@ -895,6 +974,7 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
 template <typename T>
 stitch_status set_smem_attrs() {
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_reduce_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)up_full_smem<2>()));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -942,13 +1022,27 @@ stitch_status fused_plan(stitch_rig* r) {
         }
         for (int l = 2; l < L; ++l) {
             const Rect o = c.Om[l];
-            for (int y = o.y0; y < o.y1; y += R_TY)
-                for (int x = o.x0; x < o.x1; x += R_TX) red[l].push_back({i, x, y, 0});
+            for (int y = o.y0; y < o.y1; y += RT_Y)
+                for (int x = o.x0; x < o.x1; x += RT_X) red[l].push_back({i, x, y, 0});
         }
     }
+    std::vector<LevelTile> co[MAXL];
+    std::vector<int> camlist;
     for (int l = 2; l < L; ++l) {
         fs->R[l] = rig_alloc(r, elem * (size_t)g.nx[l] * g.ny[l]);
         if (!fs->R[l]) return STITCH_ENOMEM;
+        for (int y = 0; y < g.ny[l]; y += CT_Y)
+            for (int x = 0; x < g.nx[l]; x += CT_X) {
+                LevelTile t{x, y, (int)camlist.size(), 0};
+                for (int j = 0; j < g.ncam; ++j) {
+                    const CamDev& cj = r->hcam[j];
+                    if (!cj.visible || !rects_meet(cj.Z[l], x, std::min(x + CT_X, g.nx[l]), y, std::min(y + CT_Y, g.ny[l])))
+                        continue;
+                    camlist.push_back(j);
+                    ++t.count;
+                }
+                co[l].push_back(t);
+            }
     }
     // classify the canvas tiles of `up`
     std::vector<UpTile> up[UP_KINDS];
@@ -1017,6 +1111,13 @@ stitch_status fused_plan(stitch_rig* r) {
         st = upload(r, red[l], &fs->red_tiles[l]);
         if (st != STITCH_OK) return st;
         fs->n_red[l] = (int)red[l].size();
+    }
+    st = upload(r, camlist, &fs->camlist);
+    if (st != STITCH_OK) return st;
+    for (int l = 2; l < L; ++l) {
+        st = upload(r, co[l], &fs->co_tiles[l]);
+        if (st != STITCH_OK) return st;
+        fs->n_co[l] = (int)co[l].size();
     }
     for (int k = 0; k < UP_KINDS; ++k) {
         st = upload(r, up[k], &fs->up_tiles[k]);

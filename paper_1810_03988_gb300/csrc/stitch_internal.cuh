@@ -186,6 +186,77 @@ __host__ __device__ __forceinline__ void tile_anchor(const Rect& V, int X, int Y
     *ay = min(max(Y, V.y0), V.y1 - 1);
 }
 
+// ------------------------------------------------------------------------------------------------
+// lean per-sample helpers used by the fused kernels
+
+// Exact float of an 8-bit value with one integer OR and one add: the bits 0x4B000000 | b encode
+// 2^23 + b, so subtracting 2^23 leaves b (IEEE-754 single precision, no rounding).
+__device__ __forceinline__ float u8_to_f(uint32_t b) { return __int_as_float(0x4B000000u | b) - 8388608.0f; }
+
+// One camera's mapping of canvas point anchor + (dx, dy): fraction-exact source position,
+// float source coordinates for the weight, and the sign of w.
+struct Pos {
+    int iu, iv;    // floor of the source coordinates
+    float fu, fv;  // fractions in [0, 1)
+    float u, v;    // source coordinates (for validity and weight)
+    float den;     // w, positive in front of the camera
+};
+
+__device__ __forceinline__ Pos map_pos(const TileMap& t, float fU0, float fV0, float dx, float dy) {
+    Pos p;
+    p.den = fmaf(t.q2, dy, fmaf(t.q1, dx, t.q0));
+    const float rden = __fdividef(1.0f, p.den);
+    float ru = fmaf(t.pu2, dy, fmaf(t.pu1, dx, t.pu0)) * rden;
+    float rv = fmaf(t.pv2, dy, fmaf(t.pv1, dx, t.pv0)) * rden;
+    ru = fminf(fmaxf(ru, -1.0e7f), 1.0e7f);
+    rv = fminf(fmaxf(rv, -1.0e7f), 1.0e7f);
+    const float flu = floorf(ru), flv = floorf(rv);
+    p.iu = t.U0 + (int)flu;
+    p.iv = t.V0 + (int)flv;
+    p.fu = ru - flu;
+    p.fv = rv - flv;
+    p.u = fU0 + ru;
+    p.v = fV0 + rv;
+    return p;
+}
+
+// Raw feather weight from float source coordinates; Wm = W - 0.5, Hm = H - 0.5.  Within ~1e-4 px
+// of a validity border the float test may differ from the exact one (those pixels are the
+// coverage-boundary set that parity excludes); everywhere else it is the same decision.
+__device__ __forceinline__ float weight_of(const Pos& p, float Wm, float Hm) {
+    const float m = fminf(fminf(p.u + 0.5f, p.v + 0.5f), fminf(Wm - p.u, Hm - p.v));
+    const bool ok = (p.den > 0.0f) & (p.u >= -0.5f) & (p.u < Wm) & (p.v >= -0.5f) & (p.v < Hm);
+    return ok ? fmaxf(m, 0.0f) : 0.0f;
+}
+
+// Bilinear RGB sample with clamped coordinates, scaled by `scale` (= gain / 255).
+__device__ __forceinline__ float3 sample_rgb(const uint8_t* __restrict__ px, long long pitch, const Pos& p, int W,
+                                             int H, float scale) {
+    int i0, j0;
+    float fx, fy;
+    if (p.iu < 0) { i0 = 0; fx = 0.0f; }
+    else if (p.iu >= W - 1) { i0 = W - 1; fx = 0.0f; }
+    else { i0 = p.iu; fx = p.fu; }
+    if (p.iv < 0) { j0 = 0; fy = 0.0f; }
+    else if (p.iv >= H - 1) { j0 = H - 1; fy = 0.0f; }
+    else { j0 = p.iv; fy = p.fv; }
+    const int di = (i0 + 1 < W) ? 3 : 0;
+    const long long dj = (j0 + 1 < H) ? pitch : 0;
+    const uint8_t* a = px + (long long)j0 * pitch + 3 * i0;
+    const uint8_t* b = a + dj;
+    float3 o;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float p00 = u8_to_f(__ldg(a + c)), p01 = u8_to_f(__ldg(a + di + c));
+        const float p10 = u8_to_f(__ldg(b + c)), p11 = u8_to_f(__ldg(b + di + c));
+        const float top = fmaf(fx, p01 - p00, p00);
+        const float bot = fmaf(fx, p11 - p10, p10);
+        const float v = fmaf(fy, bot - top, top) * scale;
+        if (c == 0) o.x = v; else if (c == 1) o.y = v; else o.z = v;
+    }
+    return o;
+}
+
 __device__ __forceinline__ unsigned char quantize_u8(float v) {
     // v already clamped to [0, 1]; round half to even
     return (unsigned char)__float2int_rn(255.0f * v);
