@@ -49,7 +49,8 @@ typedef enum {
     STITCH_ENOMEM = 2,      /* device or host allocation failed (create calls only) */
     STITCH_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
     STITCH_ETIMEOUT = 4,    /* a bounded device-side wait gave up (batched schedule) */
-    STITCH_EUNSUPPORTED = 5 /* valid request this build does not handle */
+    STITCH_EUNSUPPORTED = 5, /* valid request this build does not handle */
+    STITCH_ETOOLARGE = 6     /* request needs more than the fixed static scratch (stitch_frames_static) */
 } stitch_status;
 
 /* Limits of this build. */
@@ -132,6 +133,27 @@ stitch_status stitch_backward(stitch_rig* rig, const uint8_t* const* frames, con
 
 /* Human-readable name of a status code (static string). */
 const char* stitch_status_string(stitch_status s);
+
+/*
+ * Stitch one frame set with no device allocation at all (the paper has no counterpart; this is
+ * a deployment convenience).  Callers that cannot call cudaMalloc (code running inside a CUDA
+ * graph capture or replay, real-time loops that cannot afford the allocator's implicit device
+ * synchronisation, hosts that hand the library a fixed memory budget) describe the rig in `desc`
+ * and get the same result as a STITCH_PATH_PLAIN rig's stitch_frames: the plain-path kernels run
+ * with every scratch buffer carved from one file-scope device array of STITCH_STATIC_SCRATCH_BYTES
+ * (64 MiB) that each GPU loading the library holds until the process exits.
+ *   desc     as for stitch_rig_create (path is ignored; band_fp16 must be 0); planned per call on
+ *            the host stack, so each call also re-validates the geometry
+ *   frames, pitches, out, out_pitch, stream   as for stitch_frames, on the CURRENT device
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Every call shares the array
+ * and keeps the last call's contents; calls whose kernels overlap on the GPU race on it.  A rig
+ * needing more scratch than the array holds returns STITCH_ETOOLARGE before any GPU work.
+ * Status: OK, EINVAL, ETOOLARGE, ECUDA.
+ */
+#define STITCH_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+stitch_status stitch_frames_static(const stitch_rig_desc* desc, const uint8_t* const* frames, const int64_t* pitches,
+                                   void* out, int64_t out_pitch, void* stream);
 
 /* ------------------------------------------------------------------------------------------ */
 /* Introspection and profiling                                                                 */

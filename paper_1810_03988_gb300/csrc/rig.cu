@@ -30,11 +30,12 @@ bool invert_normalised(const double* M, double* A) {
     return true;
 }
 
-stitch_status plan_camera(stitch_rig* r, int i) {
-    const stitch_camera& c = r->cams[i];
-    CamDev& d = r->hcam[i];
+}  // namespace
+
+// Validate one camera and plan its regions (validity box V, weight support Z^l, pyramid region
+// Omega^l).  Adds the camera's level-0 region area to *roi.
+stitch_status plan_camera_geometry(const stitch_camera& c, const RigGeom& g, CamDev& d, long long* roi) {
     memset(&d, 0, sizeof(d));
-    const RigGeom& g = r->geom;
     const int L = g.levels, Wc = g.nx[0], Hc = g.ny[0];
     if (c.width < 1 || c.height < 1 || !std::isfinite(c.gain)) return STITCH_EINVAL;
     for (double v : c.H)
@@ -100,8 +101,14 @@ stitch_status plan_camera(stitch_rig* r, int i) {
     for (double x : qx)
         for (double y : qy)
             if (!(d.A[6] * x + d.A[7] * y + d.A[8] > 0.0)) return STITCH_EINVAL;
-    r->roi_pixels += o.area();
+    *roi += o.area();
     return STITCH_OK;
+}
+
+namespace {
+
+stitch_status plan_camera(stitch_rig* r, int i) {
+    return plan_camera_geometry(r->cams[i], r->geom, r->hcam[i], &r->roi_pixels);
 }
 
 struct DeviceGuard {
@@ -180,6 +187,7 @@ const char* stitch_status_string(stitch_status s) {
         case STITCH_ECUDA: return "STITCH_ECUDA: CUDA error";
         case STITCH_ETIMEOUT: return "STITCH_ETIMEOUT: bounded device wait gave up";
         case STITCH_EUNSUPPORTED: return "STITCH_EUNSUPPORTED: not supported by this build";
+        case STITCH_ETOOLARGE: return "STITCH_ETOOLARGE: request exceeds the static scratch array";
     }
     return "unknown stitch_status";
 }

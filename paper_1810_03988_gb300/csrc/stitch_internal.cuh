@@ -376,6 +376,9 @@ struct stitch_rig {
     std::vector<KernelStat> stats;
 };
 
+// Validate one camera and plan its regions; adds its level-0 region area to *roi.
+stitch_status plan_camera_geometry(const stitch_camera& c, const RigGeom& g, CamDev& d, long long* roi);
+
 // Record a profiling mark before a launch (name) or at the end of a call (nullptr).
 void prof_mark(stitch_rig* r, const char* name, cudaStream_t s);
 

@@ -15,7 +15,8 @@ import numpy as np
 
 from . import _build
 
-STITCH_OK, STITCH_EINVAL, STITCH_ENOMEM, STITCH_ECUDA, STITCH_ETIMEOUT, STITCH_EUNSUPPORTED = range(6)
+STITCH_OK, STITCH_EINVAL, STITCH_ENOMEM, STITCH_ECUDA, STITCH_ETIMEOUT, STITCH_EUNSUPPORTED, STITCH_ETOOLARGE = range(7)
+STITCH_STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 STITCH_MAX_CAMERAS = 32
 STITCH_MAX_LEVELS = 12
 STITCH_PATH_FUSED = 0
@@ -59,6 +60,7 @@ SIGNATURES = {
     "stitch_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
     "stitch_batch_frames": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "stitch_batch_destroy": (None, [_P]),
+    "stitch_frames_static": (ctypes.c_int, [ctypes.POINTER(stitch_rig_desc), _P, _P, _P, ctypes.c_int64, _P]),
 }
 
 
@@ -137,6 +139,17 @@ def stitch_backward(rig: int, frame_ptrs, pitches, params_ptr: int, loss_ptr: in
     fp = (_P * n)(*frame_ptrs)
     pt = (ctypes.c_int64 * n)(*pitches)
     _check(load().stitch_backward(rig, fp, pt, params_ptr, loss_ptr, grad_ptr or None, stream), "stitch_backward")
+
+
+def stitch_frames_static(desc: stitch_rig_desc, frame_ptrs, pitches, out_ptr: int, out_pitch: int,
+                         stream: int) -> None:
+    """Stitch with no device allocation: scratch lives in the library's fixed static device array
+    (for callers that cannot allocate, e.g. inside a graph capture); same result as a plain rig."""
+    n = len(frame_ptrs)
+    fp = (_P * n)(*frame_ptrs)
+    pt = (ctypes.c_int64 * n)(*pitches)
+    _check(load().stitch_frames_static(ctypes.byref(desc), fp, pt, out_ptr, out_pitch, stream),
+           "stitch_frames_static")
 
 
 def stitch_rig_get_info(rig: int) -> stitch_rig_info:

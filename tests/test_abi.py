@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_status_strings(lib):
     from paper_1810_03988_gb300 import stitch
-    for s in range(6):
+    for s in range(7):
         assert stitch.status_string(s).startswith("STITCH_")
 
 
