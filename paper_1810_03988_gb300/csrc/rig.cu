@@ -238,6 +238,7 @@ stitch_status stitch_rig_create(const stitch_rig_desc* desc, int device, stitch_
         st = STITCH_ECUDA;
     if (st != STITCH_OK) {
         fused_release(r);
+        backward_release(r);
         free_all(r);
         delete r;
         return st;
@@ -251,6 +252,7 @@ void stitch_rig_destroy(stitch_rig* r) {
     DeviceGuard dg(r->device);
     cudaDeviceSynchronize();
     fused_release(r);
+    backward_release(r);
     free_all(r);
     delete r;
 }

@@ -360,9 +360,7 @@ struct stitch_rig {
     void* fused = nullptr;
 
     // backward state
-    double* bw_partials = nullptr;
-    int bw_blocks = 0;
-    Rect bw_region{};
+    void* bw = nullptr;
 
     // host staging for stitch_frames_host
     uint8_t* stage_frames[MAXC]{};
@@ -395,6 +393,7 @@ void fused_tile_counts(const stitch_rig* r, int counts[6]);
 stitch_status backward_plan(stitch_rig* r);
 stitch_status backward_run(stitch_rig* r, const FramePtrs& fp, const double* params, double* loss, double* grad,
                            cudaStream_t s);
+void backward_release(stitch_rig* r);
 
 #define STITCH_CUDA_TRY(expr)                         \
     do {                                              \

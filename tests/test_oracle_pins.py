@@ -393,3 +393,4 @@ def test_inverse_keeps_the_in_front_sign():
     np.testing.assert_allclose(q[:2] / q[2], [(cam.width - 1) / 2, (cam.height - 1) / 2], atol=1e-9)
     _, wr = oracle.warp(cam, np.zeros((cam.height, cam.width, 3), np.uint8), cfg.canvas_w, cfg.canvas_h)
     assert (wr > 0).sum() > 0.5 * cam.width * cam.height
+

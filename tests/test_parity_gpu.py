@@ -224,3 +224,24 @@ def test_tile_classes_are_exercised():
     with Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels) as rig:
         t = rig.info()["tiles"]
     assert t["solo"] > 0 and t["full2"] > 0, t
+
+
+@pytest.mark.parametrize("cfg_name", ["2cam", "4x1080p_scaled", "8x4k_scaled"])
+def test_fp16_bands(cfg_name):
+    """Pyramid data stored in FP16 between kernels (all arithmetic FP32): within 1e-3 of the oracle
+    on the float canvas and 1 LSB on uint8."""
+    cfg = {"2cam": lambda: synth.config_2cam(),
+           "4x1080p_scaled": lambda: synth.config_4x1080p(scale=0.25, frames=1),
+           "8x4k_scaled": lambda: synth.config_8x4k(scale=0.1, frames=1)}[cfg_name]()
+    frames = cfg.frame(0)
+    gpu_util.full_parity(cfg, frames, "fused", True, band_fp16=True, tol=gpu_util.TOL_F16)
+    gpu_util.full_parity(cfg, frames, "fused", False, band_fp16=True)
+
+
+def test_fp16_bands_8x4k_full_size_windows():
+    cfg = synth.config_8x4k(frames=1)
+    frames = cfg.frame(0)
+    got = gpu_util.run_gpu(cfg, frames, "fused", out_float=True, band_fp16=True)
+    for (x0, y0, w, h) in gpu_util.sample_windows(cfg, 20, 32):
+        ref = oracle.forward(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h, cfg.levels, window=(x0, y0, w, h))
+        gpu_util.compare(got[y0:y0 + h, x0:x0 + w], ref, True, tol=gpu_util.TOL_F16)
