@@ -29,6 +29,8 @@
 //          clamped warp of camera c, with no pyramid work;
 //   FULL   up to 2 or 4 contributing cameras, everything in shared memory;
 //   GENERAL more cameras: a slower kernel that streams one camera at a time.
+#include <unordered_map>
+
 #include "stitch_internal.cuh"
 
 namespace {
@@ -75,8 +77,10 @@ struct CamRef {
 // down1 tile: camera, level-1 origin, and the cameras (CamRef range) whose validity box meets
 // the tile's level-0 inputs (for the weight normalisation), in camera order.
 struct D1Tile {
-    int cam, k0, j0, first, count, self, pad0, pad1;
+    int cam, k0, j0, first, count, self, flags, pad;
 };
+constexpr int D1_INTERIOR = 1;  // inputs solidly inside the camera, no other camera: weight 1
+constexpr int D1_SOLO_OUT = 2;  // the canvas tile under this tile is SOLO for this camera
 
 // up tile: level-0 origin and the contributing cameras (CamRef range), in camera order.
 struct UpTile {
@@ -95,9 +99,14 @@ constexpr size_t D1_SMEM = sizeof(float4) * (D1_SX * D1_SY + D1_TX * D1_SY);
 constexpr int D1_CHUNK_ROWS = (D1_SY + 1) / 2;                                   // 18
 constexpr int D1_NS = (D1_CHUNK_ROWS * D1_SX + D1_THREADS - 1) / D1_THREADS;   // 5
 
+__device__ __forceinline__ void store_u8_tile(const unsigned char* __restrict__ stage, const OutDesc& od, int X0,
+                                              int Y0, int X1, int Y1);
+__device__ __forceinline__ void put_pixel(unsigned char* stage, const OutDesc& od, int dx, int dy, int x, int y,
+                                          float r, float g, float b);
+
 template <typename T>
 __global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
-                                                       const D1Tile* __restrict__ tiles,
+                                                       OutDesc od, const D1Tile* __restrict__ tiles,
                                                        const CamRef* __restrict__ refs) {
     extern __shared__ float4 smem[];
     float4* s0 = smem;                  // [D1_SY][D1_SX] level 0 (virtual coordinates)
@@ -115,6 +124,19 @@ __global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restric
     const uint8_t* px_i = fp.p[i];
     const long long pitch_i = fp.pitch[i];
 
+    if (tl.flags & D1_INTERIOR) {
+        // every input is valid for this camera alone, weight 1: the warp only
+        const CamRef ref = refs[tl.first];
+        const int W = ci.W, H = ci.H;
+        const float fU0 = (float)ref.tm.U0, fV0 = (float)ref.tm.V0;
+        for (int q = t; q < D1_SX * D1_SY; q += D1_THREADS) {
+            const int r = q / D1_SX, c = q % D1_SX;
+            const int x = fold101(vx0 + c, g.nx[0]), y = fold101(vy0 + r, g.ny[0]);
+            const Pos p = map_pos(ref.tm, fU0, fV0, (float)(x - ref.ax), (float)(y - ref.ay));
+            const float3 v = sample_rgb(px_i, pitch_i, p, W, H, scale);
+            s0[q] = make_float4(v.x, v.y, v.z, 1.f);
+        }
+    } else
     // S1 + S2 on the virtual level-0 region, two chunks of rows; cameras in the outer loop so
     // each camera's constants are loaded once per chunk
     for (int r0 = 0; r0 < D1_SY; r0 += D1_CHUNK_ROWS) {
@@ -161,6 +183,24 @@ __global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restric
         }
     }
     __syncthreads();
+    if (tl.flags & D1_SOLO_OUT) {
+        // the canvas tile [2 k0, 2 k0 + 64) x [2 j0, 2 j0 + 32) is exclusive to this camera: its
+        // output is the clamped level-0 warp, already in s0 (virtual offset 2)
+        unsigned char* stage = reinterpret_cast<unsigned char*>(sh);
+        const int X0 = 2 * k0, Y0 = 2 * j0;
+        const int X1 = min(X0 + 2 * D1_TX, g.nx[0]), Y1 = min(Y0 + 2 * D1_TY, g.ny[0]);
+        for (int q = t; q < 4 * D1_TX * D1_TY; q += D1_THREADS) {
+            const int dx = q % (2 * D1_TX), dy = q / (2 * D1_TX);
+            if (X0 + dx >= X1 || Y0 + dy >= Y1) continue;
+            const float4 v = s0[(dy + 2) * D1_SX + dx + 2];
+            put_pixel(stage, od, dx, dy, X0 + dx, Y0 + dy, __saturatef(v.x), __saturatef(v.y), __saturatef(v.z));
+        }
+        if (!od.is_float) {
+            __syncthreads();
+            store_u8_tile(stage, od, X0, Y0, X1, Y1);
+        }
+        __syncthreads();
+    }
     // S3 horizontal pass: sh[r][p] = sum_m w(m) s0[r][2p + m]
     for (int q = t; q < D1_TX * D1_SY; q += D1_THREADS) {
         const int r = q / D1_TX, p = q - r * D1_TX;
@@ -176,7 +216,8 @@ __global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restric
     for (int q = t; q < D1_TX * D1_TY; q += D1_THREADS) {
         const int jj = q / D1_TX, p = q - jj * D1_TX;
         const int k = k0 + p, j = j0 + jj;
-        if (k >= o1.x1 || j >= o1.y1) continue;
+        // tiles lie on the global grid, so they may start before and end after Omega^1
+        if (!o1.contains(k, j)) continue;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int n = 0; n < 5; ++n) acc = f4fma(c_w5[n], sh[(2 * jj + n) * D1_TX + p], acc);
@@ -205,11 +246,25 @@ __global__ void __launch_bounds__(256) k_reduce_t(const CamDev* __restrict__ cam
     const int vx0 = 2 * tl.x0 - 2, vy0 = 2 * tl.y0 - 2;
     const T* src = reinterpret_cast<const T*>(c.FG[l]);
     const int nxl = g.nx[l], nyl = g.ny[l];
-    for (int q = threadIdx.x; q < RS_X * RS_Y; q += 256) {
-        const int r = q / RS_X, cc = q - r * RS_X;
-        const int x = fold101(vx0 + cc, nxl), y = fold101(vy0 + r, nyl);
-        s0[q] = of.contains(x, y) ? ld(src + (long long)(y - of.y0) * of.w() + (x - of.x0))
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    {
+        // all loads of a thread in flight before the shared-memory stores
+        constexpr int NL = (RS_X * RS_Y + 255) / 256;
+        float4 v[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int q = threadIdx.x + 256 * k;
+            v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < RS_X * RS_Y) {
+                const int r = q / RS_X, cc = q - r * RS_X;
+                const int x = fold101(vx0 + cc, nxl), y = fold101(vy0 + r, nyl);
+                if (of.contains(x, y)) v[k] = ld(src + (long long)(y - of.y0) * of.w() + (x - of.x0));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int q = threadIdx.x + 256 * k;
+            if (q < RS_X * RS_Y) s0[q] = v[k];
+        }
     }
     __syncthreads();
     for (int q = threadIdx.x; q < RT_X * RS_Y; q += 256) {
@@ -301,24 +356,45 @@ __global__ void __launch_bounds__(256) k_coarse_t(const CamDev* __restrict__ cam
     for (int c0 = 0; c0 < tl.count; c0 += CT_NC) {
         const int nc = min(CT_NC, tl.count - c0);
         __syncthreads();
-        for (int q = t; q < nc * CT_N; q += 256) {
-            const int ci = q / CT_N, qq = q - ci * CT_N;
-            const CamDev& c = cams[camlist[tl.first + c0 + ci]];
-            const int x = X0 + qq % CT_X, y = Y0 + qq / CT_X;
-            const Rect o = c.Om[l];
-            gl[ci][qq] = o.contains(x, y) ? ld(reinterpret_cast<const T*>(c.FG[l]) + (long long)(y - o.y0) * o.w() + (x - o.x0))
-                                          : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        if (!top) {
-            for (int q = t; q < nc * CC_N; q += 256) {
-                const int ci = q / CC_N, qq = q - ci * CC_N;
-                const CamDev& c = cams[camlist[tl.first + c0 + ci]];
-                const int r = qq / CC_X, cc = qq - r * CC_X;
-                const int x = fold101(ax + cc, g.nx[l + 1]), y = fold101(ay + r, g.ny[l + 1]);
-                const Rect o = c.Om[l + 1];
-                gc[ci][qq] = o.contains(x, y)
-                                 ? ld(reinterpret_cast<const T*>(c.FG[l + 1]) + (long long)(y - o.y0) * o.w() + (x - o.x0))
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        {
+            constexpr int NL = (CT_NC * CT_N + 255) / 256, NC2 = (CT_NC * CC_N + 255) / 256;
+            float4 v[NL], w[NC2];
+#pragma unroll
+            for (int k = 0; k < NL; ++k) {
+                const int q = t + 256 * k;
+                v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (q < nc * CT_N) {
+                    const int ci = q / CT_N, qq = q - ci * CT_N;
+                    const CamDev& c = cams[camlist[tl.first + c0 + ci]];
+                    const int x = X0 + qq % CT_X, y = Y0 + qq / CT_X;
+                    const Rect o = c.Om[l];
+                    if (o.contains(x, y))
+                        v[k] = ld(reinterpret_cast<const T*>(c.FG[l]) + (long long)(y - o.y0) * o.w() + (x - o.x0));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NC2; ++k) {
+                const int q = t + 256 * k;
+                w[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (!top && q < nc * CC_N) {
+                    const int ci = q / CC_N, qq = q - ci * CC_N;
+                    const CamDev& c = cams[camlist[tl.first + c0 + ci]];
+                    const int r = qq / CC_X, cc = qq - r * CC_X;
+                    const int x = fold101(ax + cc, g.nx[l + 1]), y = fold101(ay + r, g.ny[l + 1]);
+                    const Rect o = c.Om[l + 1];
+                    if (o.contains(x, y))
+                        w[k] = ld(reinterpret_cast<const T*>(c.FG[l + 1]) + (long long)(y - o.y0) * o.w() + (x - o.x0));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NL; ++k) {
+                const int q = t + 256 * k;
+                if (q < nc * CT_N) gl[q / CT_N][q % CT_N] = v[k];
+            }
+#pragma unroll
+            for (int k = 0; k < NC2; ++k) {
+                const int q = t + 256 * k;
+                if (!top && q < nc * CC_N) gc[q / CC_N][q % CC_N] = w[k];
             }
         }
         __syncthreads();
@@ -486,32 +562,58 @@ __global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict_
         chm[t] = (float)c.H - 0.5f;
         cscale[t] = c.gain * (1.0f / 255.0f);
     }
-    // loads of level 1 and 2 data
+    // loads of level 1 and 2 data, all of a thread's loads in flight before the stores
     if (L >= 2) {
-        for (int q = t; q < nc * U1_N; q += U_THREADS) {
-            const int ci = q / U1_N, qq = q - ci * U1_N;
-            const CamDev& c = cams[refs[tl.first + ci].cam];
-            const int r = qq / U1_X, cc = qq - r * U1_X;
-            const int x = fold101(a1x + cc, g.nx[1]), y = fold101(a1y + r, g.ny[1]);
-            const Rect o1 = c.Om[1];
-            d1[q] = o1.contains(x, y)
-                        ? ld(reinterpret_cast<const T*>(c.FG[1]) + (long long)(y - o1.y0) * o1.w() + (x - o1.x0))
-                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        constexpr int NL = (NC * U1_N + U_THREADS - 1) / U_THREADS;
+        float4 v[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int q = t + k * U_THREADS;
+            v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < nc * U1_N) {
+                const int ci = q / U1_N, qq = q - ci * U1_N;
+                const CamDev& c = cams[refs[tl.first + ci].cam];
+                const int r = qq / U1_X, cc = qq - r * U1_X;
+                const int x = fold101(a1x + cc, g.nx[1]), y = fold101(a1y + r, g.ny[1]);
+                const Rect o1 = c.Om[1];
+                if (o1.contains(x, y))
+                    v[k] = ld(reinterpret_cast<const T*>(c.FG[1]) + (long long)(y - o1.y0) * o1.w() + (x - o1.x0));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int q = t + k * U_THREADS;
+            if (q < nc * U1_N) d1[q] = v[k];
         }
     }
     if (L >= 3) {
-        for (int q = t; q < (nc + 1) * U2_N; q += U_THREADS) {
-            const int ci = q / U2_N, qq = q - ci * U2_N;
-            const int r = qq / U2_X, cc = qq - r * U2_X;
-            const int x = fold101(a2x + cc, g.nx[2]), y = fold101(a2y + r, g.ny[2]);
-            if (ci == nc) {
-                r2s[qq] = ld(R2 + (long long)y * g.nx[2] + x);
-            } else {
-                const CamDev& c = cams[refs[tl.first + ci].cam];
-                const Rect o2 = c.Om[2];
-                d2[q] = o2.contains(x, y)
-                            ? ld(reinterpret_cast<const T*>(c.FG[2]) + (long long)(y - o2.y0) * o2.w() + (x - o2.x0))
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        constexpr int NL = ((NC + 1) * U2_N + U_THREADS - 1) / U_THREADS;
+        float4 v[NL];
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int q = t + k * U_THREADS;
+            v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (q < (nc + 1) * U2_N) {
+                const int ci = q / U2_N, qq = q - ci * U2_N;
+                const int r = qq / U2_X, cc = qq - r * U2_X;
+                const int x = fold101(a2x + cc, g.nx[2]), y = fold101(a2y + r, g.ny[2]);
+                if (ci == nc) {
+                    v[k] = ld(R2 + (long long)y * g.nx[2] + x);
+                } else {
+                    const CamDev& c = cams[refs[tl.first + ci].cam];
+                    const Rect o2 = c.Om[2];
+                    if (o2.contains(x, y))
+                        v[k] = ld(reinterpret_cast<const T*>(c.FG[2]) + (long long)(y - o2.y0) * o2.w() + (x - o2.x0));
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NL; ++k) {
+            const int q = t + k * U_THREADS;
+            if (q < (nc + 1) * U2_N) {
+                const int ci = q / U2_N, qq = q - ci * U2_N;
+                if (ci == nc) r2s[qq] = v[k];
+                else d2[q] = v[k];
             }
         }
     }
@@ -935,7 +1037,7 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
     const int L = g.levels;
     if (L >= 2 && fs->n_d1 > 0) {
         prof_mark(r, "fused_down1", s);
-        k_down1<T><<<fs->n_d1, D1_THREADS, D1_SMEM, s>>>(r->dcam, g, fp, fs->d1_tiles, fs->refs);
+        k_down1<T><<<fs->n_d1, D1_THREADS, D1_SMEM, s>>>(r->dcam, g, fp, od, fs->d1_tiles, fs->refs);
     }
     for (int l = 1; l + 1 < L; ++l) {
         if (fs->n_red[l + 1] == 0) continue;
@@ -1003,9 +1105,11 @@ stitch_status fused_plan(stitch_rig* r) {
             if (!c.FG[l]) return STITCH_ENOMEM;
         }
         if (L >= 2) {
+            // tiles on the global grid of 32 x 16 level-1 samples, so that a tile's level-0 interior
+            // is exactly one 64 x 32 canvas tile of `up`
             const Rect o = c.Om[1];
-            for (int y = o.y0; y < o.y1; y += D1_TY)
-                for (int x = o.x0; x < o.x1; x += D1_TX) {
+            for (int y = (o.y0 / D1_TY) * D1_TY; y < o.y1; y += D1_TY)
+                for (int x = (o.x0 / D1_TX) * D1_TX; x < o.x1; x += D1_TX) {
                     // level-0 bounding box of the tile's inputs
                     const int bx0 = std::max(2 * x - 2, 0), bx1 = std::min(2 * x - 2 + D1_SX, g.nx[0]);
                     const int by0 = std::max(2 * y - 2, 0), by1 = std::min(2 * y - 2 + D1_SY, g.ny[0]);
@@ -1017,6 +1121,7 @@ stitch_status fused_plan(stitch_rig* r) {
                         refs.push_back(make_ref(cj, j, bx0, by0));
                         ++t.count;
                     }
+                    if (t.count == 1 && solidly_inside(c, Rect{bx0, bx1, by0, by1})) t.flags |= D1_INTERIOR;
                     d1.push_back(t);
                 }
         }
@@ -1046,6 +1151,9 @@ stitch_status fused_plan(stitch_rig* r) {
     }
     // classify the canvas tiles of `up`
     std::vector<UpTile> up[UP_KINDS];
+    std::unordered_map<long long, size_t> d1_index;  // (camera, level-1 origin) -> down1 tile
+    for (size_t k = 0; k < d1.size(); ++k)
+        d1_index[((long long)d1[k].cam << 42) | ((long long)d1[k].k0 << 21) | d1[k].j0] = k;
     for (int Y0 = 0; Y0 < g.ny[0]; Y0 += U_TY)
         for (int X0 = 0; X0 < g.nx[0]; X0 += U_TX) {
             const int X1 = std::min(X0 + U_TX, g.nx[0]), Y1 = std::min(Y0 + U_TY, g.ny[0]);
@@ -1092,6 +1200,15 @@ stitch_status fused_plan(stitch_rig* r) {
                     t.count = 1;
                     kind = UP_SIMPLE;
                     ++fs->n_solo;
+                    // with a level-1 pass, the camera's down1 tile over this canvas tile writes the
+                    // output (its level-0 samples are the output here)
+                    if (L >= 2) {
+                        auto it = d1_index.find(((long long)last_v << 42) | ((long long)(X0 / 2) << 21) | (Y0 / 2));
+                        if (it != d1_index.end()) {
+                            d1[it->second].flags |= D1_SOLO_OUT;
+                            kind = -1;
+                        }
+                    }
                 } else if (t.count <= 2) {
                     kind = UP_FULL2;
                 } else if (t.count <= 4) {
@@ -1100,7 +1217,7 @@ stitch_status fused_plan(stitch_rig* r) {
                     kind = UP_GENERAL;
                 }
             }
-            up[kind].push_back(t);
+            if (kind >= 0) up[kind].push_back(t);
         }
     stitch_status st = upload(r, refs, &fs->refs);
     if (st != STITCH_OK) return st;
