@@ -219,6 +219,21 @@ stitch_status stitch_batch_frames(stitch_batch* batch, const uint8_t* const* con
 
 void stitch_batch_destroy(stitch_batch* batch);
 
+/*
+ * The schedule the batch runs (chosen on its first stitch_batch_frames call by timing every
+ * candidate on the real frames, unless the environment sets STITCH_TUNE=off): *order 0 ranks
+ * every rig's stages from the start, 1 aligns them so every rig finishes together; *grid is the
+ * number of persistent blocks; *tasks the number of tile tasks per call.
+ */
+stitch_status stitch_batch_get_schedule(const stitch_batch* batch, int32_t* order, int32_t* grid, int64_t* tasks);
+
+/*
+ * Test hook for the bounded device waits: sets the waits' iteration limit (default 2^22, about a
+ * second) and, when rig >= 0, raises that rig's first-stage completion target out of reach so the
+ * next stitch_batch_frames call gives up waiting and returns STITCH_ETIMEOUT; rig = -1 restores it.
+ */
+stitch_status stitch_batch_wait_test(stitch_batch* batch, int32_t spin_limit, int32_t rig);
+
 #ifdef __cplusplus
 }
 #endif

@@ -3,7 +3,7 @@
 The compute runs in hand-written CUDA kernels (``csrc/``); ``stitch`` is the ctypes binding of
 ``include/stitch.h`` (argument marshalling only).
 """
-from .stitch import (STITCH_PATH_FUSED, STITCH_PATH_PLAIN, Rig, StitchError, library_path, load,  # noqa: F401
+from .stitch import (STITCH_PATH_FUSED, STITCH_PATH_PLAIN, Batch, Rig, StitchError, library_path, load,  # noqa: F401
                      status_string, stitch_backward, stitch_batch_create, stitch_batch_destroy,
                      stitch_batch_frames, stitch_frames, stitch_frames_host, stitch_frames_static, stitch_rig_create, stitch_rig_destroy,
                      stitch_rig_get_camera, stitch_rig_get_info, stitch_rig_kernel_times, stitch_rig_set_profiling)

@@ -42,9 +42,11 @@ struct __align__(8) half4 {
     __half2 a, b;
 };
 
-__device__ __forceinline__ float4 ld(const float4* p) { return __ldg(p); }
+// Pyramid data is read through L2 (ld.global.cg): in the batched persistent kernel it is written
+// by other blocks of the same launch, which the non-coherent read-only path would not see.
+__device__ __forceinline__ float4 ld(const float4* p) { return __ldcg(p); }
 __device__ __forceinline__ float4 ld(const half4* p) {
-    const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    const uint2 u = __ldcg(reinterpret_cast<const uint2*>(p));
     __half2 a = *reinterpret_cast<const __half2*>(&u.x), b = *reinterpret_cast<const __half2*>(&u.y);
     const float2 fa = __half22float2(a), fb = __half22float2(b);
     return make_float4(fa.x, fa.y, fb.x, fb.y);
@@ -105,14 +107,12 @@ __device__ __forceinline__ void put_pixel(unsigned char* stage, const OutDesc& o
                                           float r, float g, float b);
 
 template <typename T>
-__global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
-                                                       OutDesc od, const D1Tile* __restrict__ tiles,
-                                                       const CamRef* __restrict__ refs) {
-    extern __shared__ float4 smem[];
+__device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
+                                           const OutDesc& od, const D1Tile& tl, const CamRef* __restrict__ refs,
+                                           float4* smem) {
     float4* s0 = smem;                  // [D1_SY][D1_SX] level 0 (virtual coordinates)
     float4* sh = smem + D1_SX * D1_SY;  // [D1_SY][D1_TX] horizontally reduced
 
-    const D1Tile tl = tiles[blockIdx.x];
     const int i = tl.cam;
     const CamDev& ci = cams[i];
     const Rect o1 = ci.Om[1], o0 = ci.Om[0];
@@ -225,6 +225,14 @@ __global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restric
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
+                                                       OutDesc od, const D1Tile* __restrict__ tiles,
+                                                       const CamRef* __restrict__ refs) {
+    extern __shared__ float4 smem[];
+    down1_tile<T>(cams, g, fp, od, tiles[blockIdx.x], refs, smem);
+}
+
 // ------------------------------------------------------------------------------------------------
 // reduce (levels >= 1 -> next)
 
@@ -235,12 +243,10 @@ constexpr int RS_X = 2 * RT_X + 3, RS_Y = 2 * RT_Y + 3;
 constexpr size_t RT_SMEM = sizeof(float4) * (RS_X * RS_Y + RT_X * RS_Y);
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_reduce_t(const CamDev* __restrict__ cams, RigGeom g, int l,
-                                                   const Tile* __restrict__ tiles) {
-    extern __shared__ float4 smem[];
+__device__ __forceinline__ void reduce_tile(const CamDev* __restrict__ cams, const RigGeom& g, int l, const Tile& tl,
+                                            float4* smem) {
     float4* s0 = smem;
     float4* sh = smem + RS_X * RS_Y;
-    const Tile tl = tiles[blockIdx.x];
     const CamDev& c = cams[tl.cam];
     const Rect oc = c.Om[l + 1], of = c.Om[l];
     const int vx0 = 2 * tl.x0 - 2, vy0 = 2 * tl.y0 - 2;
@@ -288,6 +294,13 @@ __global__ void __launch_bounds__(256) k_reduce_t(const CamDev* __restrict__ cam
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_reduce_t(const CamDev* __restrict__ cams, RigGeom g, int l,
+                                                   const Tile* __restrict__ tiles) {
+    extern __shared__ float4 smem[];
+    reduce_tile<T>(cams, g, l, tiles[blockIdx.x], smem);
+}
+
 // ------------------------------------------------------------------------------------------------
 // coarse levels
 
@@ -318,20 +331,19 @@ constexpr int CT_X = 32, CT_Y = 16, CT_NC = 2;
 constexpr int CC_X = CT_X / 2 + 4, CC_Y = CT_Y / 2 + 4;
 constexpr int CC_N = CC_X * CC_Y, CT_N = CT_X * CT_Y;
 constexpr int CT_QUADS = (CT_X / 2) * (CT_Y / 2);  // 128
+constexpr int CT_SMEM_F4 = CC_N + CT_NC * CT_N + CT_NC * CC_N;  // shared memory in float4 units
 
 struct LevelTile {
     int x0, y0, first, count;  // level origin, range of camera indices in the list
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_coarse_t(const CamDev* __restrict__ cams, RigGeom g, int l,
-                                                   T* __restrict__ Rl, const T* __restrict__ Rc,
-                                                   const LevelTile* __restrict__ tiles,
-                                                   const int* __restrict__ camlist) {
-    __shared__ float4 rc[CC_N];             // R^{l+1}
-    __shared__ float4 gl[CT_NC][CT_N];      // G^l of each camera of the chunk
-    __shared__ float4 gc[CT_NC][CC_N];      // G^{l+1}, then R^{l+1} - G^{l+1}
-    const LevelTile tl = tiles[blockIdx.x];
+__device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, const RigGeom& g, int l,
+                                            T* __restrict__ Rl, const T* __restrict__ Rc, const LevelTile& tl,
+                                            const int* __restrict__ camlist, float4* smem) {
+    float4* rc = smem;                                                   // [CC_N] R^{l+1}
+    float4 (*gl)[CT_N] = reinterpret_cast<float4 (*)[CT_N]>(rc + CC_N);  // [CT_NC][CT_N] G^l per camera
+    float4 (*gc)[CC_N] = reinterpret_cast<float4 (*)[CC_N]>(rc + CC_N + CT_NC * CT_N);  // G^{l+1}, then R - G
     const bool top = l == g.levels - 1;
     const int X0 = tl.x0, Y0 = tl.y0;
     const int ax = X0 / 2 - 2, ay = Y0 / 2 - 2;
@@ -442,6 +454,15 @@ __global__ void __launch_bounds__(256) k_coarse_t(const CamDev* __restrict__ cam
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_t(const CamDev* __restrict__ cams, RigGeom g, int l,
+                                                   T* __restrict__ Rl, const T* __restrict__ Rc,
+                                                   const LevelTile* __restrict__ tiles,
+                                                   const int* __restrict__ camlist) {
+    __shared__ float4 smem[CT_SMEM_F4];
+    coarse_tile<T>(cams, g, l, Rl, Rc, tiles[blockIdx.x], camlist, smem);
+}
+
 // ------------------------------------------------------------------------------------------------
 // up: levels 1 and 0 of one canvas tile
 
@@ -492,11 +513,9 @@ __device__ __forceinline__ void put_pixel(unsigned char* stage, const OutDesc& o
 }
 
 // ZERO and SOLO tiles: output 0, or the clamped warp of the one exclusive camera.
-__global__ void __launch_bounds__(U_THREADS) k_up_simple(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
-                                                          OutDesc od, const UpTile* __restrict__ tiles,
-                                                          const CamRef* __restrict__ refs) {
-    __shared__ __align__(16) unsigned char stage[3 * U_TX * U_TY];
-    const UpTile tl = tiles[blockIdx.x];
+__device__ __forceinline__ void up_simple_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
+                                               const OutDesc& od, const UpTile& tl, const CamRef* __restrict__ refs,
+                                               unsigned char* stage) {
     const int X0 = tl.x0, Y0 = tl.y0;
     const int X1 = min(X0 + U_TX, g.nx[0]), Y1 = min(Y0 + U_TY, g.ny[0]);
     if (tl.count == 0) {
@@ -527,24 +546,41 @@ __global__ void __launch_bounds__(U_THREADS) k_up_simple(const CamDev* __restric
     }
 }
 
+__global__ void __launch_bounds__(U_THREADS) k_up_simple(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
+                                                          OutDesc od, const UpTile* __restrict__ tiles,
+                                                          const CamRef* __restrict__ refs) {
+    __shared__ __align__(16) unsigned char stage[3 * U_TX * U_TY];
+    up_simple_tile(cams, g, fp, od, tiles[blockIdx.x], refs, stage);
+}
+
 // FULL tiles with at most NC contributing cameras.
+// Per-camera constants of a FULL tile, kept in shared memory.
+template <int NC>
+struct UpCams {
+    CamRef cr[NC];
+    Rect cv[NC], cz1[NC];
+    int cwh[NC][2];
+    float cscale[NC], cwm[NC], chm[NC];
+};
+
 template <typename T, int NC>
-__global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
-                                                        OutDesc od, const T* __restrict__ R2,
-                                                        const UpTile* __restrict__ tiles,
-                                                        const CamRef* __restrict__ refs) {
-    extern __shared__ float4 usm[];
+__device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
+                                             const OutDesc& od, const T* __restrict__ R2, const UpTile& tl,
+                                             const CamRef* __restrict__ refs, float4* usm) {
     float4* d1 = usm;                // [NC][U1_N]: G^1 of each camera, then R^1 - G^1
     float4* d2 = d1 + NC * U1_N;     // [NC][U2_N]: G^2 of each camera, then R^2 - G^2
     float4* r2s = d2 + NC * U2_N;    // [U2_N]: R^2
     unsigned char* stage = reinterpret_cast<unsigned char*>(r2s + U2_N);
-    __shared__ CamRef cr[NC];
-    __shared__ Rect cv[NC], cz1[NC];
-    __shared__ int cwh[NC][2];
-    __shared__ float cscale[NC], cwm[NC], chm[NC];
+    UpCams<NC>& ucs = *reinterpret_cast<UpCams<NC>*>(stage + 3 * U_TX * U_TY);
+    CamRef* cr = ucs.cr;
+    Rect* cv = ucs.cv;
+    Rect* cz1 = ucs.cz1;
+    int (*cwh)[2] = ucs.cwh;
+    float* cscale = ucs.cscale;
+    float* cwm = ucs.cwm;
+    float* chm = ucs.chm;
 
     const int L = g.levels;
-    const UpTile tl = tiles[blockIdx.x];
     const int nc = min(tl.count, NC);
     const int X0 = tl.x0, Y0 = tl.y0;
     const int X1 = min(X0 + U_TX, g.nx[0]), Y1 = min(Y0 + U_TY, g.ny[0]);
@@ -735,9 +771,18 @@ __global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict_
     }
 }
 
+template <typename T, int NC>
+__global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
+                                                        OutDesc od, const T* __restrict__ R2,
+                                                        const UpTile* __restrict__ tiles,
+                                                        const CamRef* __restrict__ refs) {
+    extern __shared__ float4 usm[];
+    up_full_tile<T, NC>(cams, g, fp, od, R2, tiles[blockIdx.x], refs, usm);
+}
+
 template <int NC>
 constexpr size_t up_full_smem() {
-    return sizeof(float4) * (NC * U1_N + NC * U2_N + U2_N) + 3 * U_TX * U_TY;
+    return sizeof(float4) * (NC * U1_N + NC * U2_N + U2_N) + 3 * U_TX * U_TY + sizeof(UpCams<NC>);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -774,17 +819,15 @@ __device__ __forceinline__ float3 expand_smem(const float4* __restrict__ a, int 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(U_THREADS) k_up_general(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
-                                                           OutDesc od, const T* __restrict__ R2,
-                                                           const UpTile* __restrict__ tiles,
-                                                           const CamRef* __restrict__ refs) {
-    __shared__ float4 g1[UG1_N];
-    __shared__ float4 g2[UG2_X * UG2_Y];
-    __shared__ float4 r2[UG2_X * UG2_Y];
-    __shared__ float4 r1[UG1_N];
+__device__ __forceinline__ void up_general_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
+                                                const OutDesc& od, const T* __restrict__ R2, const UpTile& tl,
+                                                const CamRef* __restrict__ refs, float4* smem) {
+    float4* g1 = smem;                   // [UG1_N]
+    float4* g2 = g1 + UG1_N;             // [UG2_X * UG2_Y]
+    float4* r2 = g2 + UG2_X * UG2_Y;     // [UG2_X * UG2_Y]
+    float4* r1 = r2 + UG2_X * UG2_Y;     // [UG1_N]
 
     const int L = g.levels;
-    const UpTile tl = tiles[blockIdx.x];
     const int X0 = tl.x0, Y0 = tl.y0;
     const int X1 = min(X0 + U_TX, g.nx[0]), Y1 = min(Y0 + U_TY, g.ny[0]);
     const int a1x = X0 / 2 - 1, a1y = Y0 / 2 - 1;          // level-1 virtual origin
@@ -951,6 +994,17 @@ __global__ void __launch_bounds__(U_THREADS) k_up_general(const CamDev* __restri
             o[2] = quantize_u8(bb);
         }
     }
+}
+
+constexpr int UG_SMEM_F4 = 2 * UG1_N + 2 * UG2_X * UG2_Y;
+
+template <typename T>
+__global__ void __launch_bounds__(U_THREADS) k_up_general(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
+                                                           OutDesc od, const T* __restrict__ R2,
+                                                           const UpTile* __restrict__ tiles,
+                                                           const CamRef* __restrict__ refs) {
+    __shared__ float4 smem[UG_SMEM_F4];
+    up_general_tile<T>(cams, g, fp, od, R2, tiles[blockIdx.x], refs, smem);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1270,4 +1324,478 @@ void fused_tile_counts(const stitch_rig* r, int counts[6]) {
     counts[3] = fs->n_up[UP_FULL4];
     counts[4] = fs->n_up[UP_GENERAL];
     counts[5] = fs->n_d1;
+}
+
+// ================================================================================================
+// Batched persistent schedule: several rigs stitched by one launch.
+//
+// Every rig's per-frame work is a chain of stages (down1, the REDUCEs, the coarse levels, the
+// canvas tiles); each stage's tiles become tasks of one device task list spanning all rigs, ordered
+// so that every task's inputs come from tasks earlier in the list.  A persistent grid of resident
+// blocks dequeues tasks in list order with an atomic counter; before a task of stage s of rig r it
+// waits until all tasks of stage s-1 of rig r have completed (a counter per rig and stage).  Since
+// those tasks were dequeued earlier by resident blocks that only wait on still earlier tasks, the
+// waits always end; each wait nevertheless has an iteration limit, after which the block records a
+// status, raises an abort flag that stops every block, and returns.
+// ================================================================================================
+
+namespace {
+
+enum BatchType { BT_D1 = 0, BT_RED = 1, BT_CO = 2, BT_UPS = 3, BT_UPF2 = 4, BT_UPF4 = 5, BT_UPG = 6 };
+constexpr int B_MAXSTAGE = 2 * MAXL + 2;
+constexpr int B_THREADS = 256;
+
+struct BatchRigDev {
+    const CamDev* cams;
+    RigGeom g;
+    FramePtrs fp;
+    OutDesc od;
+    const D1Tile* d1;
+    const Tile* red[MAXL];
+    const LevelTile* co[MAXL];
+    const int* camlist;
+    const CamRef* refs;
+    const UpTile* up[UP_KINDS];
+    void* R[MAXL];
+};
+
+struct BTask {
+    int rig, type, idx, level, stage, pad0, pad1, pad2;
+};
+
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t B_SMEM = cmax(cmax(cmax(D1_SMEM, RT_SMEM), sizeof(float4) * CT_SMEM_F4),
+                               cmax(up_full_smem<4>(), (size_t)3 * U_TX * U_TY));
+
+// ctl[0] next task, ctl[1] status (1: a wait gave up), ctl[2] abort, ctl[3] spin limit
+template <typename T>
+__global__ void __launch_bounds__(B_THREADS, 3) k_batch(const BatchRigDev* __restrict__ rigs,
+                                                         const BTask* __restrict__ tasks, int ntasks, int* ctl,
+                                                         int* done, const int* __restrict__ need) {
+    extern __shared__ float4 smem[];
+    __shared__ int s_task, s_go;
+    volatile int* vctl = ctl;
+    volatile int* vdone = done;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int go = 1;
+            const int ti = atomicAdd(&ctl[0], 1);
+            if (ti >= ntasks || vctl[2]) {
+                go = 0;
+            } else {
+                const BTask tk = tasks[ti];
+                if (tk.stage > 0) {
+                    const int ix = tk.rig * B_MAXSTAGE + tk.stage - 1;
+                    const int limit = vctl[3];
+                    int it = 0;
+                    while (vdone[ix] < need[ix]) {
+                        if (vctl[2]) {
+                            go = 0;
+                            break;
+                        }
+                        if (++it > limit) {
+                            atomicExch(&ctl[1], 1);
+                            atomicExch(&ctl[2], 1);
+                            go = 0;
+                            break;
+                        }
+                        __nanosleep(200);
+                    }
+                }
+                __threadfence();
+            }
+            s_task = ti;
+            s_go = go;
+        }
+        __syncthreads();
+        const int ti = s_task, go = s_go;
+        if (!go) return;
+        const BTask tk = tasks[ti];
+        const BatchRigDev& rg = rigs[tk.rig];
+        const T* R2 = rg.g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
+        switch (tk.type) {
+            case BT_D1:
+                down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, rg.d1[tk.idx], rg.refs, smem);
+                break;
+            case BT_RED:
+                reduce_tile<T>(rg.cams, rg.g, tk.level - 1, rg.red[tk.level][tk.idx], smem);
+                break;
+            case BT_CO:
+                coarse_tile<T>(rg.cams, rg.g, tk.level, (T*)rg.R[tk.level],
+                               tk.level + 1 < rg.g.levels ? (const T*)rg.R[tk.level + 1] : nullptr,
+                               rg.co[tk.level][tk.idx], rg.camlist, smem);
+                break;
+            case BT_UPS:
+                up_simple_tile(rg.cams, rg.g, rg.fp, rg.od, rg.up[UP_SIMPLE][tk.idx], rg.refs,
+                               reinterpret_cast<unsigned char*>(smem));
+                break;
+            case BT_UPF2:
+                up_full_tile<T, 2>(rg.cams, rg.g, rg.fp, rg.od, R2, rg.up[UP_FULL2][tk.idx], rg.refs, smem);
+                break;
+            case BT_UPF4:
+                up_full_tile<T, 4>(rg.cams, rg.g, rg.fp, rg.od, R2, rg.up[UP_FULL4][tk.idx], rg.refs, smem);
+                break;
+            default:
+                break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(&done[tk.rig * B_MAXSTAGE + tk.stage], 1);
+        }
+    }
+}
+
+// Canvas tiles with more than 4 contributing cameras, after the persistent launch.
+template <typename T>
+__global__ void __launch_bounds__(U_THREADS) k_batch_general(const BatchRigDev* __restrict__ rigs,
+                                                              const BTask* __restrict__ tasks, const int* ctl) {
+    __shared__ float4 smem[UG_SMEM_F4];
+    if (((volatile const int*)ctl)[2]) return;
+    const BTask tk = tasks[blockIdx.x];
+    const BatchRigDev& rg = rigs[tk.rig];
+    const T* R2 = rg.g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
+    up_general_tile<T>(rg.cams, rg.g, rg.fp, rg.od, R2, rg.up[UP_GENERAL][tk.idx], rg.refs, smem);
+}
+
+struct BatchState {
+    int device = 0, n = 0;
+    bool fp16 = false;
+    std::vector<stitch_rig*> rigs;
+    std::vector<void*> allocs;
+    BatchRigDev* d_rigs = nullptr;
+    BatchRigDev* h_rigs = nullptr;  // pinned
+    BTask* d_tasks[2] = {};         // two orderings
+    int ntasks = 0;
+    BTask* d_gtasks = nullptr;
+    int ngtasks = 0;
+    int* d_ctl = nullptr;
+    int* d_done = nullptr;
+    int* d_need = nullptr;
+    int* h_status = nullptr;  // pinned
+    std::vector<int> need;
+    int max_bpsm = 1, sms = 1;
+    int order = 1, grid = 0;
+    bool tuned = false;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    long long tasks_by_type[8] = {};
+};
+
+template <typename V>
+stitch_status b_upload(BatchState* b, const std::vector<V>& v, V** out) {
+    *out = nullptr;
+    if (v.empty()) return STITCH_OK;
+    if (cudaMalloc((void**)out, sizeof(V) * v.size()) != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return STITCH_ENOMEM;
+    }
+    b->allocs.push_back(*out);
+    STITCH_CUDA_TRY(cudaMemcpy(*out, v.data(), sizeof(V) * v.size(), cudaMemcpyHostToDevice));
+    return STITCH_OK;
+}
+
+void b_free(BatchState* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (void* p : b->allocs) cudaFree(p);
+    if (b->h_rigs) cudaFreeHost(b->h_rigs);
+    if (b->h_status) cudaFreeHost(b->h_status);
+    delete b;
+}
+
+// The persistent kernel's blocks wait on one another, so it is launched cooperatively: the grid
+// (at most the resident capacity) is guaranteed to run at once.
+template <typename T>
+stitch_status b_launch(BatchState* b, int order, int grid, cudaStream_t s) {
+    int ntasks = b->ntasks;
+    void* args[] = {(void*)&b->d_rigs, (void*)&b->d_tasks[order], (void*)&ntasks, (void*)&b->d_ctl,
+                    (void*)&b->d_done, (void*)&b->d_need};
+    STITCH_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_batch<T>, dim3(grid), dim3(B_THREADS), args, B_SMEM, s));
+    if (b->ngtasks) k_batch_general<T><<<b->ngtasks, U_THREADS, 0, s>>>(b->d_rigs, b->d_gtasks, b->d_ctl);
+    return launch_status();
+}
+
+stitch_status b_prepare(BatchState* b, cudaStream_t s) {
+    STITCH_CUDA_TRY(cudaMemcpyAsync(b->d_rigs, b->h_rigs, sizeof(BatchRigDev) * b->n, cudaMemcpyHostToDevice, s));
+    STITCH_CUDA_TRY(cudaMemsetAsync(b->d_ctl, 0, 3 * sizeof(int), s));
+    STITCH_CUDA_TRY(cudaMemsetAsync(b->d_done, 0, sizeof(int) * b->need.size(), s));
+    return STITCH_OK;
+}
+
+template <typename T>
+stitch_status b_build_graph(BatchState* b) {
+    cudaGraph_t g;
+    STITCH_CUDA_TRY(cudaGraphCreate(&g, 0));
+    b->graph = g;
+    cudaGraphNode_t cp, m1, m2, kb, kg = nullptr, st;
+    STITCH_CUDA_TRY(cudaGraphAddMemcpyNode1D(&cp, g, nullptr, 0, b->d_rigs, b->h_rigs, sizeof(BatchRigDev) * b->n,
+                                             cudaMemcpyHostToDevice));
+    cudaMemsetParams ms{};
+    ms.dst = b->d_ctl;
+    ms.value = 0;
+    ms.elementSize = sizeof(int);
+    ms.width = 3;
+    ms.height = 1;
+    ms.pitch = 0;
+    STITCH_CUDA_TRY(cudaGraphAddMemsetNode(&m1, g, nullptr, 0, &ms));
+    ms.dst = b->d_done;
+    ms.width = b->need.size();
+    STITCH_CUDA_TRY(cudaGraphAddMemsetNode(&m2, g, nullptr, 0, &ms));
+    int ntasks = b->ntasks;
+    void* args[] = {(void*)&b->d_rigs, (void*)&b->d_tasks[b->order], (void*)&ntasks, (void*)&b->d_ctl,
+                    (void*)&b->d_done, (void*)&b->d_need};
+    cudaKernelNodeParams kp{};
+    kp.func = (void*)k_batch<T>;
+    kp.gridDim = dim3(b->grid);
+    kp.blockDim = dim3(B_THREADS);
+    kp.sharedMemBytes = (unsigned)B_SMEM;
+    kp.kernelParams = args;
+    cudaGraphNode_t deps[3] = {cp, m1, m2};
+    STITCH_CUDA_TRY(cudaGraphAddKernelNode(&kb, g, deps, 3, &kp));
+    cudaLaunchAttributeValue coop{};
+    coop.cooperative = 1;
+    STITCH_CUDA_TRY(cudaGraphKernelNodeSetAttribute(kb, cudaLaunchAttributeCooperative, &coop));
+    cudaGraphNode_t last = kb;
+    if (b->ngtasks) {
+        void* gargs[] = {(void*)&b->d_rigs, (void*)&b->d_gtasks, (void*)&b->d_ctl};
+        cudaKernelNodeParams gp{};
+        gp.func = (void*)k_batch_general<T>;
+        gp.gridDim = dim3(b->ngtasks);
+        gp.blockDim = dim3(U_THREADS);
+        gp.sharedMemBytes = 0;
+        gp.kernelParams = gargs;
+        STITCH_CUDA_TRY(cudaGraphAddKernelNode(&kg, g, &kb, 1, &gp));
+        last = kg;
+    }
+    STITCH_CUDA_TRY(cudaGraphAddMemcpyNode1D(&st, g, &last, 1, b->h_status, b->d_ctl + 1, sizeof(int),
+                                             cudaMemcpyDeviceToHost));
+    STITCH_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+    return STITCH_OK;
+}
+
+// Time every (ordering, blocks per SM) candidate once on the real frames and keep the fastest.
+template <typename T>
+stitch_status b_tune(BatchState* b, cudaStream_t s) {
+    const char* mode = getenv("STITCH_TUNE");
+    b->grid = b->max_bpsm * b->sms;
+    b->order = 1;
+    if (mode && strcmp(mode, "off") == 0) return STITCH_OK;
+    cudaEvent_t e0, e1;
+    STITCH_CUDA_TRY(cudaEventCreate(&e0));
+    STITCH_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int order = 0; order < 2; ++order)
+        for (int bpsm = 1; bpsm <= b->max_bpsm; ++bpsm)
+            for (int rep = 0; rep < 2; ++rep) {
+                stitch_status st = b_prepare(b, s);
+                if (st != STITCH_OK) return st;
+                cudaEventRecord(e0, s);
+                st = b_launch<T>(b, order, bpsm * b->sms, s);
+                if (st != STITCH_OK) return st;
+                cudaEventRecord(e1, s);
+                STITCH_CUDA_TRY(cudaEventSynchronize(e1));
+                int status = 0;
+                STITCH_CUDA_TRY(cudaMemcpy(&status, b->d_ctl + 1, sizeof(int), cudaMemcpyDeviceToHost));
+                if (status) return STITCH_ETIMEOUT;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 1 && ms < best) {
+                    best = ms;
+                    b->order = order;
+                    b->grid = bpsm * b->sms;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return STITCH_OK;
+}
+
+}  // namespace
+
+stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
+    *out = nullptr;
+    if (!rigs || n < 1) return STITCH_EINVAL;
+    for (int k = 0; k < n; ++k)
+        if (!rigs[k] || rigs[k]->desc.path != STITCH_PATH_FUSED || !rigs[k]->fused) return STITCH_EINVAL;
+    const int dev = rigs[0]->device;
+    const bool fp16 = rigs[0]->desc.band_fp16 != 0;
+    for (int k = 1; k < n; ++k)
+        if (rigs[k]->device != dev || (rigs[k]->desc.band_fp16 != 0) != fp16) return STITCH_EUNSUPPORTED;
+    if (cudaSetDevice(dev) != cudaSuccess) return STITCH_ECUDA;
+    BatchState* b = new (std::nothrow) BatchState();
+    if (!b) return STITCH_ENOMEM;
+    b->device = dev;
+    b->n = n;
+    b->fp16 = fp16;
+    b->rigs.assign(rigs, rigs + n);
+    b->need.assign((size_t)n * B_MAXSTAGE, 0);
+    // per rig: descriptor and stage lists
+    std::vector<std::vector<std::vector<BTask>>> stages(n);
+    std::vector<BTask> gtasks;
+    if (cudaMallocHost((void**)&b->h_rigs, sizeof(BatchRigDev) * n) != cudaSuccess ||
+        cudaMallocHost((void**)&b->h_status, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        b_free(b);
+        return STITCH_ENOMEM;
+    }
+    for (int k = 0; k < n; ++k) {
+        stitch_rig* r = rigs[k];
+        FusedState* fs = (FusedState*)r->fused;
+        BatchRigDev& d = b->h_rigs[k];
+        memset(&d, 0, sizeof(d));
+        d.cams = r->dcam;
+        d.g = r->geom;
+        d.d1 = fs->d1_tiles;
+        for (int l = 0; l < MAXL; ++l) {
+            d.red[l] = fs->red_tiles[l];
+            d.co[l] = fs->co_tiles[l];
+            d.R[l] = fs->R[l];
+        }
+        d.camlist = fs->camlist;
+        d.refs = fs->refs;
+        for (int q = 0; q < UP_KINDS; ++q) d.up[q] = fs->up_tiles[q];
+        const int L = r->geom.levels;
+        auto add_stage = [&](int type, int level, int count) {
+            const int st = (int)stages[k].size();
+            stages[k].emplace_back();
+            for (int i = 0; i < count; ++i) stages[k].back().push_back({k, type, i, level, st, 0, 0, 0});
+            b->need[(size_t)k * B_MAXSTAGE + st] = count;
+            b->tasks_by_type[type] += count;
+        };
+        if (L >= 2) add_stage(BT_D1, 1, fs->n_d1);
+        for (int l = 2; l < L; ++l) add_stage(BT_RED, l, fs->n_red[l]);
+        for (int l = L - 1; l >= 2; --l) add_stage(BT_CO, l, fs->n_co[l]);
+        {
+            const int st = (int)stages[k].size();
+            stages[k].emplace_back();
+            int cnt = 0;
+            for (int i = 0; i < fs->n_up[UP_SIMPLE]; ++i) stages[k].back().push_back({k, BT_UPS, i, 0, st, 0, 0, 0});
+            for (int i = 0; i < fs->n_up[UP_FULL2]; ++i) stages[k].back().push_back({k, BT_UPF2, i, 0, st, 0, 0, 0});
+            for (int i = 0; i < fs->n_up[UP_FULL4]; ++i) stages[k].back().push_back({k, BT_UPF4, i, 0, st, 0, 0, 0});
+            cnt = (int)stages[k].back().size();
+            b->need[(size_t)k * B_MAXSTAGE + st] = cnt;
+            b->tasks_by_type[BT_UPS] += fs->n_up[UP_SIMPLE];
+            b->tasks_by_type[BT_UPF2] += fs->n_up[UP_FULL2];
+            b->tasks_by_type[BT_UPF4] += fs->n_up[UP_FULL4];
+            for (int i = 0; i < fs->n_up[UP_GENERAL]; ++i) gtasks.push_back({k, BT_UPG, i, 0, st, 0, 0, 0});
+        }
+    }
+    // two orderings: stages ranked from the start, or aligned so that every rig ends together
+    int maxs = 0;
+    for (int k = 0; k < n; ++k) maxs = std::max(maxs, (int)stages[k].size());
+    std::vector<BTask> ord[2];
+    for (int o = 0; o < 2; ++o)
+        for (int rank = 0; rank < maxs; ++rank)
+            for (int k = 0; k < n; ++k) {
+                const int s = o == 0 ? rank : rank - (maxs - (int)stages[k].size());
+                if (s < 0 || s >= (int)stages[k].size()) continue;
+                ord[o].insert(ord[o].end(), stages[k][s].begin(), stages[k][s].end());
+            }
+    b->ntasks = (int)ord[0].size();
+    stitch_status st = STITCH_OK;
+    if ((st = b_upload(b, ord[0], &b->d_tasks[0])) != STITCH_OK || (st = b_upload(b, ord[1], &b->d_tasks[1])) != STITCH_OK ||
+        (st = b_upload(b, gtasks, &b->d_gtasks)) != STITCH_OK || (st = b_upload(b, b->need, &b->d_need)) != STITCH_OK) {
+        b_free(b);
+        return st;
+    }
+    b->ngtasks = (int)gtasks.size();
+    std::vector<int> zeros(b->need.size(), 0), ctl = {0, 0, 0, 1 << 22};
+    if ((st = b_upload(b, zeros, &b->d_done)) != STITCH_OK || (st = b_upload(b, ctl, &b->d_ctl)) != STITCH_OK) {
+        b_free(b);
+        return st;
+    }
+    if (cudaMalloc((void**)&b->d_rigs, sizeof(BatchRigDev) * n) != cudaSuccess) {
+        cudaGetLastError();
+        b_free(b);
+        return STITCH_ENOMEM;
+    }
+    b->allocs.push_back(b->d_rigs);
+    // resident blocks per SM of the persistent kernel: the grid never exceeds what fits at once
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        b_free(b);
+        return STITCH_ECUDA;
+    }
+    b->sms = prop.multiProcessorCount;
+    int bpsm = 0;
+    cudaError_t e;
+    if (fp16) {
+        e = cudaFuncSetAttribute(k_batch<half4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B_SMEM);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_batch<half4>, B_THREADS, B_SMEM);
+    } else {
+        e = cudaFuncSetAttribute(k_batch<float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B_SMEM);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_batch<float4>, B_THREADS, B_SMEM);
+    }
+    if (e != cudaSuccess || bpsm < 1) {
+        cudaGetLastError();
+        b_free(b);
+        return STITCH_ECUDA;
+    }
+    b->max_bpsm = bpsm;
+    b->grid = bpsm * b->sms;
+    *out = b;
+    return STITCH_OK;
+}
+
+stitch_status fused_batch_frames(void* bp, const uint8_t* const* const* frames, const int64_t* const* pitches,
+                                 void* const* outs, const int64_t* out_pitches, cudaStream_t s) {
+    BatchState* b = (BatchState*)bp;
+    if (!b || !frames || !pitches || !outs || !out_pitches) return STITCH_EINVAL;
+    for (int k = 0; k < b->n; ++k) {
+        stitch_rig* r = b->rigs[k];
+        if (!frames[k] || !pitches[k] || !outs[k]) return STITCH_EINVAL;
+        const long long row = (long long)r->geom.nx[0] * (r->desc.out_float ? 12 : 3);
+        if (out_pitches[k] < row) return STITCH_EINVAL;
+        FramePtrs& fp = b->h_rigs[k].fp;
+        memset(&fp, 0, sizeof(fp));
+        for (int i = 0; i < r->geom.ncam; ++i) {
+            if (!r->hcam[i].visible) continue;
+            if (!frames[k][i] || pitches[k][i] < 3LL * r->cams[i].width) return STITCH_EINVAL;
+            fp.p[i] = frames[k][i];
+            fp.pitch[i] = pitches[k][i];
+        }
+        b->h_rigs[k].od = OutDesc{outs[k], out_pitches[k], r->desc.out_float};
+    }
+    if (!b->tuned) {
+        const stitch_status st = b->fp16 ? b_tune<half4>(b, s) : b_tune<float4>(b, s);
+        if (st != STITCH_OK) return st;
+        b->tuned = true;
+        const stitch_status gs = b->fp16 ? b_build_graph<half4>(b) : b_build_graph<float4>(b);
+        if (gs != STITCH_OK) return gs;
+    }
+    *b->h_status = 0;
+    STITCH_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+    STITCH_CUDA_TRY(cudaStreamSynchronize(s));
+    return *b->h_status ? STITCH_ETIMEOUT : STITCH_OK;
+}
+
+void fused_batch_destroy(void* bp) {
+    BatchState* b = (BatchState*)bp;
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaDeviceSynchronize();
+    b_free(b);
+}
+
+stitch_status fused_batch_info(void* bp, int32_t* order, int32_t* grid, int64_t* ntasks) {
+    BatchState* b = (BatchState*)bp;
+    if (!b) return STITCH_EINVAL;
+    if (order) *order = b->order;
+    if (grid) *grid = b->grid;
+    if (ntasks) *ntasks = b->ntasks + b->ngtasks;
+    return STITCH_OK;
+}
+
+// Test hook: spin limit of the waits, and optionally make the second stage of rig `rig` wait for a
+// count that is never reached (the first stage's `need` raised), so the bounded wait runs out.
+stitch_status fused_batch_wait_test(void* bp, int spin_limit, int rig) {
+    BatchState* b = (BatchState*)bp;
+    if (!b || spin_limit < 1) return STITCH_EINVAL;
+    STITCH_CUDA_TRY(cudaMemcpy(b->d_ctl + 3, &spin_limit, sizeof(int), cudaMemcpyHostToDevice));
+    std::vector<int> need = b->need;
+    if (rig >= 0 && rig < b->n) need[(size_t)rig * B_MAXSTAGE] += 1 << 30;
+    STITCH_CUDA_TRY(cudaMemcpy(b->d_need, need.data(), sizeof(int) * need.size(), cudaMemcpyHostToDevice));
+    return STITCH_OK;
 }

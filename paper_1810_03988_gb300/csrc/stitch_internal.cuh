@@ -394,6 +394,12 @@ stitch_status backward_plan(stitch_rig* r);
 stitch_status backward_run(stitch_rig* r, const FramePtrs& fp, const double* params, double* loss, double* grad,
                            cudaStream_t s);
 void backward_release(stitch_rig* r);
+stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out);
+stitch_status fused_batch_frames(void* b, const uint8_t* const* const* frames, const int64_t* const* pitches,
+                                 void* const* outs, const int64_t* out_pitches, cudaStream_t s);
+void fused_batch_destroy(void* b);
+stitch_status fused_batch_info(void* b, int32_t* order, int32_t* grid, int64_t* ntasks);
+stitch_status fused_batch_wait_test(void* b, int spin_limit, int rig);
 
 #define STITCH_CUDA_TRY(expr)                         \
     do {                                              \

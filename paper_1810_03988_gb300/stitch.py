@@ -60,6 +60,9 @@ SIGNATURES = {
     "stitch_batch_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
     "stitch_batch_frames": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "stitch_batch_destroy": (None, [_P]),
+    "stitch_batch_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                                 ctypes.POINTER(ctypes.c_int64)]),
+    "stitch_batch_wait_test": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "stitch_frames_static": (ctypes.c_int, [ctypes.POINTER(stitch_rig_desc), _P, _P, _P, ctypes.c_int64, _P]),
 }
 
@@ -202,6 +205,17 @@ def stitch_batch_destroy(batch: int) -> None:
     load().stitch_batch_destroy(batch)
 
 
+def stitch_batch_get_schedule(batch: int) -> dict:
+    o, g, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().stitch_batch_get_schedule(batch, ctypes.byref(o), ctypes.byref(g), ctypes.byref(t)),
+           "stitch_batch_get_schedule")
+    return {"order": o.value, "grid": g.value, "tasks": t.value}
+
+
+def stitch_batch_wait_test(batch: int, spin_limit: int, rig: int) -> None:
+    _check(load().stitch_batch_wait_test(batch, spin_limit, rig), "stitch_batch_wait_test")
+
+
 # ------------------------------------------------------------------------------------------------
 # torch-facing convenience wrapper
 
@@ -332,6 +346,50 @@ class Rig:
 
     def kernel_times(self) -> dict:
         return stitch_rig_kernel_times(self.handle)
+
+
+class Batch:
+    """Several rigs (fused path, same device and band storage) stitched by one persistent launch."""
+
+    def __init__(self, rigs):
+        self.rigs = list(rigs)
+        self.handle = stitch_batch_create([r.handle for r in self.rigs])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            stitch_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def stitch(self, frames_per_rig, outs=None, stream=None):
+        """frames_per_rig: one list of CUDA frame tensors per rig.  Returns the output tensors."""
+        if outs is None:
+            outs = [r.new_output() for r in self.rigs]
+        fps, pts = [], []
+        for fr, r in zip(frames_per_rig, self.rigs):
+            a, b = _frame_args(fr, r.cameras)
+            fps.append(a)
+            pts.append(b)
+        stitch_batch_frames(self.handle, fps, pts, [o.data_ptr() for o in outs],
+                            [o.stride(0) * o.element_size() for o in outs], _stream_handle(stream))
+        return outs
+
+    def schedule(self) -> dict:
+        return stitch_batch_get_schedule(self.handle)
+
+    def wait_test(self, spin_limit: int, rig: int):
+        stitch_batch_wait_test(self.handle, spin_limit, rig)
 
 
 def _frame_args(frames, cameras):

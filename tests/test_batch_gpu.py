@@ -1,0 +1,119 @@
+"""S8: several rigs in one persistent launch (CUDA graph), against per-rig launches and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import gpu_util
+
+pytestmark = pytest.mark.gpu
+
+
+def _rigs_and_frames(cfgs, out_float=False, band_fp16=False):
+    from paper_1810_03988_gb300 import Rig
+    rigs = [Rig(c.cameras, c.canvas_w, c.canvas_h, c.levels, out_float=out_float, band_fp16=band_fp16) for c in cfgs]
+    frames = [gpu_util.gpu_frames(c.frame(0)) for c in cfgs]
+    return rigs, frames
+
+
+def _per_rig(rigs, frames):
+    import torch
+    outs = [r.stitch(f) for r, f in zip(rigs, frames)]
+    torch.cuda.synchronize()
+    return [o.cpu().numpy() for o in outs]
+
+
+@pytest.mark.parametrize("out_float", [False, True])
+def test_batch_equals_per_rig_launches(out_float):
+    """16 uneven rigs (2-6 cameras, 720p/1080p/4K views, 4-6 levels) at 1/4 scale: the batched
+    launch gives bit-identical canvases to one launch sequence per rig, on repeated calls."""
+    from paper_1810_03988_gb300 import Batch
+    cfgs = synth.config_batch(16, seed=0, scale=0.25)
+    rigs, frames = _rigs_and_frames(cfgs, out_float=out_float)
+    ref = _per_rig(rigs, frames)
+    with Batch(rigs) as b:
+        for _ in range(2):
+            outs = b.stitch(frames)
+            got = [o.cpu().numpy() for o in outs]
+            for g, r in zip(got, ref):
+                assert np.array_equal(g, r)
+        sch = b.schedule()
+        assert sch["grid"] > 0 and sch["tasks"] > 0 and sch["order"] in (0, 1)
+    for r in rigs:
+        r.close()
+
+
+def test_batch_full_size_equals_per_rig_launches():
+    from paper_1810_03988_gb300 import Batch
+    cfgs = synth.config_batch(16, seed=0)
+    rigs, frames = _rigs_and_frames(cfgs)
+    ref = _per_rig(rigs, frames)
+    with Batch(rigs) as b:
+        got = [o.cpu().numpy() for o in b.stitch(frames)]
+    for g, r in zip(got, ref):
+        assert np.array_equal(g, r)
+    for r in rigs:
+        r.close()
+
+
+def test_batch_matches_oracle():
+    from paper_1810_03988_gb300 import Batch
+    cfgs = synth.config_batch(5, seed=4, scale=0.125)
+    rigs, frames = _rigs_and_frames(cfgs, out_float=True)
+    with Batch(rigs) as b:
+        got = [o.cpu().numpy() for o in b.stitch(frames)]
+    for cfg, g in zip(cfgs, got):
+        ref = oracle.forward(cfg.cameras, cfg.frame(0), cfg.canvas_w, cfg.canvas_h, cfg.levels)
+        gpu_util.compare(g, ref, True)
+    for r in rigs:
+        r.close()
+
+
+def test_batch_fp16_bands():
+    from paper_1810_03988_gb300 import Batch
+    cfgs = synth.config_batch(4, seed=2, scale=0.125)
+    rigs, frames = _rigs_and_frames(cfgs, out_float=True, band_fp16=True)
+    ref = _per_rig(rigs, frames)
+    with Batch(rigs) as b:
+        got = [o.cpu().numpy() for o in b.stitch(frames)]
+    for g, r in zip(got, ref):
+        assert np.array_equal(g, r)
+    for r in rigs:
+        r.close()
+
+
+def test_batch_bounded_wait_times_out_and_recovers():
+    """A stage target that is never reached makes the device wait give up: the call returns
+    STITCH_ETIMEOUT, and after restoring the target the same batch stitches correctly."""
+    from paper_1810_03988_gb300 import Batch, StitchError, stitch
+    cfgs = synth.config_batch(3, seed=1, scale=0.125)
+    rigs, frames = _rigs_and_frames(cfgs)
+    ref = _per_rig(rigs, frames)
+    with Batch(rigs) as b:
+        b.stitch(frames)  # tune and build the graph first
+        b.wait_test(2000, 0)
+        with pytest.raises(StitchError) as e:
+            b.stitch(frames)
+        assert e.value.status == stitch.STITCH_ETIMEOUT
+        b.wait_test(1 << 22, -1)
+        got = [o.cpu().numpy() for o in b.stitch(frames)]
+    for g, r in zip(got, ref):
+        assert np.array_equal(g, r)
+    for r in rigs:
+        r.close()
+
+
+def test_batch_rejects_unsupported_mixes():
+    from paper_1810_03988_gb300 import Batch, Rig, StitchError, stitch
+    cfg = synth.config_2cam(scale=0.2)
+    a = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels)
+    p = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, path="plain")
+    h = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, band_fp16=True)
+    with pytest.raises(StitchError) as e:
+        Batch([a, p])
+    assert e.value.status == stitch.STITCH_EINVAL
+    with pytest.raises(StitchError) as e:
+        Batch([a, h])
+    assert e.value.status == stitch.STITCH_EUNSUPPORTED
+    for r in (a, p, h):
+        r.close()
