@@ -66,17 +66,28 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.thread = None
+        self.begin = self.end = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5.0:  # wait for the first sample
+            time.sleep(0.02)
+
+    def mark_begin(self):
+        self.begin = len(self.lines)
+
+    def mark_end(self):
+        time.sleep(0.05)  # let samples taken inside the region arrive
+        self.end = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -92,9 +103,13 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
+        sel = self.lines[self.begin:self.end] if self.begin is not None and self.end is not None else []
+        in_region = len(sel)
+        if not sel:
+            sel = self.lines[-3:]
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in sel:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -107,7 +122,7 @@ class ClockSampler:
                 if parts[5 + k].lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "samples_in_timed_region": in_region}
 
 
 def cpu_baseline(cfg, frames0, budget_s: float = 15.0):
@@ -129,6 +144,60 @@ def cpu_baseline(cfg, frames0, budget_s: float = 15.0):
     return {"value": px_total / 1e6 / t_total, "unit": "MPix/s", "cores": oracle.threads(), "kind": "oracle",
             "sample": f"{len(wins)} windows of {side}x{side} canvas px of the {cfg.name} rig "
                       f"(each with its full pyramid dependency region), {t_total:.1f} s"}
+
+
+def measure_batch(Rig, dev, torch, args, n_rigs: int = 16):
+    """The 16-rig batching workload: every rig stitched by its own launch sequence, then all rigs by
+    one persistent launch (CUDA graph).  Device-timed, 3 warm-up calls each."""
+    from paper_1810_03988_gb300 import Batch
+    cfgs = synth.config_batch(n_rigs, seed=0)
+    rigs = [Rig(c.cameras, c.canvas_w, c.canvas_h, c.levels, device=dev.index) for c in cfgs]
+    frames = [[torch.from_numpy(f).to(dev) for f in c.frame(0)] for c in cfgs]
+    outs = [r.new_output() for r in rigs]
+    mpix = sum(c.canvas_w * c.canvas_h for c in cfgs) / 1e6
+    steps = max(3, min(args.steps, 10))
+    stream = torch.cuda.current_stream()
+
+    def run(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def per_rig():
+        for r, f, o in zip(rigs, frames, outs):
+            r.stitch(f, o)
+
+    per_ms = run(per_rig)
+    with Batch(rigs) as b:
+        b.stitch(frames, outs)  # first call: autotune + graph build
+        bat_ms = run(lambda: b.stitch(frames, outs))
+        sch = b.schedule()
+    # the persistent launch alone, for reference
+    prev = os.environ.get("STITCH_TUNE")
+    os.environ["STITCH_TUNE"] = "persistent"
+    with Batch(rigs) as b:
+        b.stitch(frames, outs)
+        pers_ms = run(lambda: b.stitch(frames, outs))
+        pers_sch = b.schedule()
+    if prev is None:
+        del os.environ["STITCH_TUNE"]
+    else:
+        os.environ["STITCH_TUNE"] = prev
+    for r in rigs:
+        r.close()
+    return {"rigs": n_rigs, "cameras": sum(len(c.cameras) for c in cfgs), "canvas_mpix": mpix,
+            "per_rig_launches": {"ms": per_ms, "value": mpix / (per_ms / 1e3), "unit": "MPix/s"},
+            "batched_launch": {"ms": bat_ms, "value": mpix / (bat_ms / 1e3), "unit": "MPix/s",
+                               "note": "includes the host synchronisation the batch call performs"},
+            "speedup": per_ms / bat_ms, "schedule": sch,
+            "persistent_launch": {"ms": pers_ms, "value": mpix / (pers_ms / 1e3), "schedule": pers_sch}}
 
 
 def run_reference(args):
@@ -171,7 +240,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="8x4k", choices=sorted(WORKLOADS))
     ap.add_argument("--frames", type=int, default=None, help="distinct frame sets (default: the sequence length)")
@@ -181,6 +250,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison run")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-band comparison run")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-per-rig comparison")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -209,7 +280,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def timed(rig, out, steps, warmup, profile):
+    def timed(rig, out, steps, warmup, profile, sampler=None):
         for k in range(warmup):
             rig.stitch(dframes[k % nfr], out)
         torch.cuda.synchronize()
@@ -219,11 +290,15 @@ def main():
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
+        if sampler:
+            sampler.mark_begin()
         ev0.record(stream)
         for k in range(steps):
             rig.stitch(dframes[(warmup + k) % nfr], out)
         ev1.record(stream)
         torch.cuda.synchronize()
+        if sampler:
+            sampler.mark_end()
         barrier()
         ms = ev0.elapsed_time(ev1) / steps
         kt = rig.kernel_times() if profile else {}
@@ -243,7 +318,7 @@ def main():
     # warm-up and an unprofiled timing pass, then the profiled timed region that is reported
     timed(rig, out, max(1, min(args.steps, 5)), args.warmup, False)
     clocks.start()
-    ms, kt = timed(rig, out, args.steps, 3, True)
+    ms, kt = timed(rig, out, args.steps, 3, True, clocks)
     clk = clocks.stop()
 
     mpix = cfg.canvas_w * cfg.canvas_h / 1e6
@@ -252,20 +327,24 @@ def main():
     hbm_peak, peak_kind = _peaks()
     cbytes = compulsory_bytes(cfg)
 
-    # dominant kernel and its roofline
+    # dominant kernel and its roofline: the fused kernels are issue-bound (FP32 sample arithmetic),
+    # so the bound is the FP32 ALU peak at the clock measured during the timed region
     dom = max(kt.items(), key=lambda kv: kv[1][0]) if kt else None
     roof = None
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     if dom:
         name, (tot_ms, launches) = dom
         per_launch_ms = tot_ms / launches
-        alg = kernel_algorithmic_bytes(name, cfg, info, launches // args.steps if args.steps else 1)
-        achieved = alg / (per_launch_ms / 1e3) / 1e9 if alg else None
-        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": (achieved / hbm_peak) if achieved else None, "traffic": None,
-                "peak_source": f"{peak_kind} hbm_gbs (copy)", "avg_launch_ms": per_launch_ms,
-                "launches_per_step": launches / args.steps,
-                "share": tot_ms / sum(v[0] for v in kt.values()),
-                "algorithmic_bytes_per_launch": alg}
+        flops = kernel_algorithmic_flops(name, cfg, info)
+        peak_tf = fp32_peak_tflops(clk.get("sm_mhz"), sms)
+        achieved = flops / (per_launch_ms / 1e3) / 1e12 if flops else None
+        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": (achieved / peak_tf) if achieved else None, "traffic": None,
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x median SM clock under load",
+                "avg_launch_ms": per_launch_ms, "launches_per_step": launches / args.steps,
+                "share": tot_ms / sum(v[0] for v in kt.values()), "algorithmic_flops_per_launch": flops,
+                "hbm_achieved_gbs_compulsory": cbytes / (ms / 1e3) / 1e9, "hbm_peak_gbs": hbm_peak,
+                "hbm_peak_source": f"{peak_kind} hbm_gbs (copy)"}
     step_roof = {"achieved": cbytes / (ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                  "frac": cbytes / (ms / 1e3) / 1e9 / hbm_peak, "compulsory_bytes_per_step": cbytes}
 
@@ -276,6 +355,19 @@ def main():
         plain = {"value": world * mpix / (pms / 1e3), "ms_per_step": pms,
                  "hbm_frac": cbytes / (pms / 1e3) / 1e9 / hbm_peak, "speedup_fused_over_plain": pms / ms}
         prig.close()
+
+    # FP16 storage of pyramid data between kernels (arithmetic still FP32), same frames
+    fp16 = None
+    if not args.fp16_bands and not args.no_fp16:
+        hrig = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, band_fp16=True, device=local)
+        hms, _ = timed(hrig, out, max(3, min(args.steps, 10)), 3, False)
+        fp16 = {"value": world * mpix / (hms / 1e3), "ms_per_step": hms}
+        hrig.close()
+
+    # batching: 16 uneven rigs, one launch sequence per rig against one persistent launch
+    batched = None
+    if not args.no_batch:
+        batched = measure_batch(Rig, dev, torch, args)
 
     # end to end through the host-buffer entry point: H2D of the frames, stitch, D2H of the canvas
     pinned = [[torch.from_numpy(f).pin_memory() for f in fs] for fs in host_frames[:min(nfr, 4)]]
@@ -311,7 +403,8 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: each frame set is a distinct device buffer "
                              f"({cbytes / 1e6:.0f} MB compulsory traffic per step)"},
-            "roofline": roof, "step_roofline": step_roof, "plain_path": plain, "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roof, "step_roofline": step_roof, "plain_path": plain, "fp16_bands": fp16,
+            "batched": batched, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk, "gpu_launches": info["num_kernels"] * args.steps,
             "rig": {"scratch_bytes": info["scratch_bytes"], "roi_pixels": info["roi_pixels"],
                     "kernels_per_step": info["num_kernels"], "tiles": info["tiles"]},
@@ -325,13 +418,36 @@ def main():
     return 0
 
 
-def kernel_algorithmic_bytes(name: str, cfg, info: dict, launches_per_step: int) -> float | None:
-    """Algorithmic (compulsory) bytes of one launch of a kernel: the source pixels it must read and
-    the canvas pixels it must write, split evenly over its launches in a step.  Kernels that only
-    move intermediates have no compulsory bytes of their own and report the step's compulsory bytes
-    over their launches (a lower bound on what the path must move)."""
-    cb = compulsory_bytes(cfg)
-    return cb / max(1, launches_per_step)
+# Algorithmic FP32 operations (FMA = 2) per unit of work, counted from the method's definition:
+#   warp sample: homography numerator/denominator (6 FMA = 12), perspective divide (3), bilinear
+#     RGB (9 lerps = 18), gain/255 (3), feather weight and its normalisation (8)          -> 44
+#   REDUCE to level 1 per level-0 pixel: 4 channels x (5-tap horizontal at half the columns
+#     + 5-tap vertical at a quarter) x 2                                                    -> 30
+#   blend + collapse per canvas pixel and camera at levels 0-1 (EXPAND 3ch x ~3 taps x 2 x 2
+#     levels, weighted sum 8, divide/clamp 6)                                              -> 50
+FLOPS_WARP = 44
+FLOPS_REDUCE1 = 30
+FLOPS_BLEND = 50
+
+
+def kernel_algorithmic_flops(name: str, cfg, info: dict) -> float | None:
+    """Algorithmic FP32 operations of one launch of the named fused kernel (see the table above);
+    the level-0 samples counted are the cameras' planned level-0 regions (roi_pixels), not the
+    halo samples the tiling adds."""
+    roi = info["roi_pixels"]
+    t = info["tiles"]
+    if name == "fused_down1":
+        return roi * (FLOPS_WARP + FLOPS_REDUCE1)
+    if name == "fused_up_full":
+        px = t["full2"] * 64 * 32
+        return px * 2 * (FLOPS_WARP + FLOPS_BLEND)
+    return None
+
+
+def fp32_peak_tflops(sm_mhz: float | None, sms: int) -> float:
+    """FP32 peak from unit counts and clock: SMs x 128 FP32 lanes x 2 (FMA) x clock."""
+    mhz = sm_mhz or 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
 if __name__ == "__main__":

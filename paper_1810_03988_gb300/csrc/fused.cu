@@ -1026,6 +1026,11 @@ struct FusedState {
     int n_up[UP_KINDS] = {};
     int n_zero = 0, n_solo = 0;  // classification counts (UP_SIMPLE = zero + solo)
     bool fp16 = false;
+    // host copies of the tile tables (the batched schedule embeds them in its tasks)
+    std::vector<D1Tile> h_d1;
+    std::vector<Tile> h_red[MAXL];
+    std::vector<LevelTile> h_co[MAXL];
+    std::vector<UpTile> h_up[UP_KINDS];
 };
 
 template <typename V>
@@ -1273,6 +1278,12 @@ stitch_status fused_plan(stitch_rig* r) {
             }
             if (kind >= 0) up[kind].push_back(t);
         }
+    fs->h_d1 = d1;
+    for (int l = 0; l < MAXL; ++l) {
+        fs->h_red[l] = red[l];
+        fs->h_co[l] = co[l];
+    }
+    for (int k = 0; k < UP_KINDS; ++k) fs->h_up[k] = up[k];
     stitch_status st = upload(r, refs, &fs->refs);
     if (st != STITCH_OK) return st;
     st = upload(r, d1, &fs->d1_tiles);
@@ -1359,32 +1370,69 @@ struct BatchRigDev {
     void* R[MAXL];
 };
 
+// A task carries a copy of its tile record, so a block needs one load to start.
 struct BTask {
     int rig, type, idx, level, stage, pad0, pad1, pad2;
+    int tile[8];
 };
+template <typename TL>
+__device__ __forceinline__ const TL& task_tile(const BTask& tk) {
+    static_assert(sizeof(TL) <= sizeof(tk.tile), "tile record fits the task");
+    return *reinterpret_cast<const TL*>(tk.tile);
+}
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t B_SMEM = cmax(cmax(cmax(D1_SMEM, RT_SMEM), sizeof(float4) * CT_SMEM_F4),
                                cmax(up_full_smem<4>(), (size_t)3 * U_TX * U_TY));
 
-// ctl[0] next task, ctl[1] status (1: a wait gave up), ctl[2] abort, ctl[3] spin limit
-template <typename T>
-__global__ void __launch_bounds__(B_THREADS, 3) k_batch(const BatchRigDev* __restrict__ rigs,
-                                                         const BTask* __restrict__ tasks, int ntasks, int* ctl,
-                                                         int* done, const int* __restrict__ need) {
+constexpr int B_MAXRIGS = 64;
+constexpr int B_MAXCHUNK = 16;
+
+// Persistent executor.  ctl[0] next task, ctl[1] status (1: a wait gave up), ctl[2] abort,
+// ctl[3] spin limit.  Blocks dequeue `chunk` consecutive tasks at a time; a block remembers the
+// latest stage of each rig it has seen complete, so it polls a rig's counter once per stage rather
+// than once per task, and it publishes its completed tasks once per chunk (always before it starts
+// waiting, so a block never waits on its own unpublished work).
+template <typename T, int MINB>
+__global__ void __launch_bounds__(B_THREADS, MINB) k_batch(const BatchRigDev* __restrict__ rigs,
+                                                            const BTask* __restrict__ tasks, int ntasks, int* ctl,
+                                                            int* done, const int* __restrict__ need, int nrigs,
+                                                            int chunk) {
     extern __shared__ float4 smem[];
-    __shared__ int s_task, s_go;
+    __shared__ int s_base, s_go;
+    __shared__ int s_seen[B_MAXRIGS];
+    __shared__ int p_ix[B_MAXCHUNK], p_cnt[B_MAXCHUNK];
+    __shared__ int s_np;
     volatile int* vctl = ctl;
     volatile int* vdone = done;
+    const int t = threadIdx.x;
+    for (int r = t; r < nrigs; r += blockDim.x) s_seen[r] = -1;
+    if (t == 0) s_np = 0;
+    __syncthreads();
+    // publish pending completions (thread 0 only)
+    auto flush = [&]() {
+        if (s_np > 0) {
+            __threadfence();
+            for (int k = 0; k < s_np; ++k) atomicAdd(&done[p_ix[k]], p_cnt[k]);
+            s_np = 0;
+        }
+    };
     for (;;) {
-        if (threadIdx.x == 0) {
-            int go = 1;
-            const int ti = atomicAdd(&ctl[0], 1);
-            if (ti >= ntasks || vctl[2]) {
-                go = 0;
-            } else {
-                const BTask tk = tasks[ti];
-                if (tk.stage > 0) {
+        if (t == 0) {
+            const int base = atomicAdd(&ctl[0], chunk);
+            s_base = base;
+            s_go = base < ntasks && !vctl[2];
+        }
+        __syncthreads();
+        if (!s_go) break;
+        const int base = s_base;
+        bool stop = false;
+        for (int k = 0; k < chunk && base + k < ntasks; ++k) {
+            const BTask tk = tasks[base + k];
+            if (t == 0) {
+                int go = 1;
+                if (tk.stage > 0 && s_seen[tk.rig] < tk.stage - 1) {
+                    flush();
                     const int ix = tk.rig * B_MAXSTAGE + tk.stage - 1;
                     const int limit = vctl[3];
                     int it = 0;
@@ -1401,49 +1449,60 @@ __global__ void __launch_bounds__(B_THREADS, 3) k_batch(const BatchRigDev* __res
                         }
                         __nanosleep(200);
                     }
+                    if (go) s_seen[tk.rig] = tk.stage - 1;
+                    __threadfence();
                 }
-                __threadfence();
+                s_go = go;
             }
-            s_task = ti;
-            s_go = go;
+            __syncthreads();
+            if (!s_go) {
+                stop = true;
+                break;
+            }
+            const BatchRigDev& rg = rigs[tk.rig];
+            const T* R2 = rg.g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
+            switch (tk.type) {
+                case BT_D1:
+                    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, smem);
+                    break;
+                case BT_RED:
+                    reduce_tile<T>(rg.cams, rg.g, tk.level - 1, task_tile<Tile>(tk), smem);
+                    break;
+                case BT_CO:
+                    coarse_tile<T>(rg.cams, rg.g, tk.level, (T*)rg.R[tk.level],
+                                   tk.level + 1 < rg.g.levels ? (const T*)rg.R[tk.level + 1] : nullptr,
+                                   task_tile<LevelTile>(tk), rg.camlist, smem);
+                    break;
+                case BT_UPS:
+                    up_simple_tile(rg.cams, rg.g, rg.fp, rg.od, task_tile<UpTile>(tk), rg.refs,
+                                   reinterpret_cast<unsigned char*>(smem));
+                    break;
+                case BT_UPF2:
+                    up_full_tile<T, 2>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, smem);
+                    break;
+                case BT_UPF4:
+                    up_full_tile<T, 4>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, smem);
+                    break;
+                default:
+                    break;
+            }
+            __syncthreads();
+            if (t == 0) {
+                const int ix = tk.rig * B_MAXSTAGE + tk.stage;
+                if (s_np > 0 && p_ix[s_np - 1] == ix) {
+                    ++p_cnt[s_np - 1];
+                } else {
+                    if (s_np == B_MAXCHUNK) flush();
+                    p_ix[s_np] = ix;
+                    p_cnt[s_np] = 1;
+                    ++s_np;
+                }
+            }
         }
-        __syncthreads();
-        const int ti = s_task, go = s_go;
-        if (!go) return;
-        const BTask tk = tasks[ti];
-        const BatchRigDev& rg = rigs[tk.rig];
-        const T* R2 = rg.g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
-        switch (tk.type) {
-            case BT_D1:
-                down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, rg.d1[tk.idx], rg.refs, smem);
-                break;
-            case BT_RED:
-                reduce_tile<T>(rg.cams, rg.g, tk.level - 1, rg.red[tk.level][tk.idx], smem);
-                break;
-            case BT_CO:
-                coarse_tile<T>(rg.cams, rg.g, tk.level, (T*)rg.R[tk.level],
-                               tk.level + 1 < rg.g.levels ? (const T*)rg.R[tk.level + 1] : nullptr,
-                               rg.co[tk.level][tk.idx], rg.camlist, smem);
-                break;
-            case BT_UPS:
-                up_simple_tile(rg.cams, rg.g, rg.fp, rg.od, rg.up[UP_SIMPLE][tk.idx], rg.refs,
-                               reinterpret_cast<unsigned char*>(smem));
-                break;
-            case BT_UPF2:
-                up_full_tile<T, 2>(rg.cams, rg.g, rg.fp, rg.od, R2, rg.up[UP_FULL2][tk.idx], rg.refs, smem);
-                break;
-            case BT_UPF4:
-                up_full_tile<T, 4>(rg.cams, rg.g, rg.fp, rg.od, R2, rg.up[UP_FULL4][tk.idx], rg.refs, smem);
-                break;
-            default:
-                break;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(&done[tk.rig * B_MAXSTAGE + tk.stage], 1);
-        }
+        if (t == 0) flush();
+        if (stop) break;
     }
+    if (t == 0) flush();
 }
 
 // Canvas tiles with more than 4 contributing cameras, after the persistent launch.
@@ -1455,8 +1514,61 @@ __global__ void __launch_bounds__(U_THREADS) k_batch_general(const BatchRigDev* 
     const BTask tk = tasks[blockIdx.x];
     const BatchRigDev& rg = rigs[tk.rig];
     const T* R2 = rg.g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
-    up_general_tile<T>(rg.cams, rg.g, rg.fp, rg.od, R2, rg.up[UP_GENERAL][tk.idx], rg.refs, smem);
+    up_general_tile<T>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, smem);
 }
+
+// Multi-rig stage kernels (the alternative batched schedule): one block per task of one task type,
+// tasks of every rig in one launch, each kernel with its own register and shared-memory budget.
+template <typename T>
+__global__ void __launch_bounds__(D1_THREADS, 3) k_mr_down1(const BatchRigDev* __restrict__ rigs,
+                                                             const BTask* __restrict__ tasks) {
+    extern __shared__ float4 smem[];
+    const BTask tk = tasks[blockIdx.x];
+    const BatchRigDev& rg = rigs[tk.rig];
+    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, smem);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mr_reduce(const BatchRigDev* __restrict__ rigs, const BTask* __restrict__ tasks) {
+    extern __shared__ float4 smem[];
+    const BTask tk = tasks[blockIdx.x];
+    const BatchRigDev& rg = rigs[tk.rig];
+    reduce_tile<T>(rg.cams, rg.g, tk.level - 1, task_tile<Tile>(tk), smem);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_mr_coarse(const BatchRigDev* __restrict__ rigs, const BTask* __restrict__ tasks) {
+    __shared__ float4 smem[CT_SMEM_F4];
+    const BTask tk = tasks[blockIdx.x];
+    const BatchRigDev& rg = rigs[tk.rig];
+    coarse_tile<T>(rg.cams, rg.g, tk.level, (T*)rg.R[tk.level],
+                   tk.level + 1 < rg.g.levels ? (const T*)rg.R[tk.level + 1] : nullptr, rg.co[tk.level][tk.idx],
+                   rg.camlist, smem);
+}
+
+__global__ void __launch_bounds__(U_THREADS) k_mr_up_simple(const BatchRigDev* __restrict__ rigs,
+                                                             const BTask* __restrict__ tasks) {
+    __shared__ __align__(16) unsigned char stage[3 * U_TX * U_TY];
+    const BTask tk = tasks[blockIdx.x];
+    const BatchRigDev& rg = rigs[tk.rig];
+    up_simple_tile(rg.cams, rg.g, rg.fp, rg.od, task_tile<UpTile>(tk), rg.refs, stage);
+}
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(U_THREADS) k_mr_up_full(const BatchRigDev* __restrict__ rigs,
+                                                           const BTask* __restrict__ tasks) {
+    extern __shared__ float4 usm[];
+    const BTask tk = tasks[blockIdx.x];
+    const BatchRigDev& rg = rigs[tk.rig];
+    const T* R2 = rg.g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
+    up_full_tile<T, NC>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, usm);
+}
+
+// A launch of the staged schedule: all tasks of one type and level, over every rig.
+struct StageGroup {
+    int type, level, count;
+    BTask* d_tasks;
+};
 
 struct BatchState {
     int device = 0, n = 0;
@@ -1474,11 +1586,14 @@ struct BatchState {
     int* d_need = nullptr;
     int* h_status = nullptr;  // pinned
     std::vector<int> need;
-    int max_bpsm = 1, sms = 1;
-    int order = 1, grid = 0;
+    int max_bpsm[2] = {1, 1}, sms = 1;
+    int order = 1, grid = 0, variant = 1, chunk = 4;
+    float tuned_ms = 0.f;
     bool tuned = false;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
+    std::vector<StageGroup> groups;  // staged schedule, in launch order
+    bool staged = false;             // schedule chosen by the tuner: staged launches or persistent
     long long tasks_by_type[8] = {};
 };
 
@@ -1508,13 +1623,73 @@ void b_free(BatchState* b) {
 // The persistent kernel's blocks wait on one another, so it is launched cooperatively: the grid
 // (at most the resident capacity) is guaranteed to run at once.
 template <typename T>
-stitch_status b_launch(BatchState* b, int order, int grid, cudaStream_t s) {
-    int ntasks = b->ntasks;
+void* batch_kernel(int variant) {
+    return variant == 0 ? (void*)k_batch<T, 2> : (void*)k_batch<T, 3>;
+}
+
+template <typename T>
+stitch_status b_launch(BatchState* b, int order, int variant, int grid, int chunk, cudaStream_t s) {
+    int ntasks = b->ntasks, nrigs = b->n;
     void* args[] = {(void*)&b->d_rigs, (void*)&b->d_tasks[order], (void*)&ntasks, (void*)&b->d_ctl,
-                    (void*)&b->d_done, (void*)&b->d_need};
-    STITCH_CUDA_TRY(cudaLaunchCooperativeKernel((void*)k_batch<T>, dim3(grid), dim3(B_THREADS), args, B_SMEM, s));
+                    (void*)&b->d_done, (void*)&b->d_need, (void*)&nrigs, (void*)&chunk};
+    STITCH_CUDA_TRY(cudaLaunchCooperativeKernel(batch_kernel<T>(variant), dim3(grid), dim3(B_THREADS), args, B_SMEM, s));
     if (b->ngtasks) k_batch_general<T><<<b->ngtasks, U_THREADS, 0, s>>>(b->d_rigs, b->d_gtasks, b->d_ctl);
     return launch_status();
+}
+
+stitch_status b_prepare(BatchState* b, cudaStream_t s);
+
+template <typename T>
+stitch_status b_launch_staged(BatchState* b, cudaStream_t s) {
+    for (const StageGroup& gr : b->groups) {
+        if (!gr.count) continue;
+        switch (gr.type) {
+            case BT_D1: k_mr_down1<T><<<gr.count, D1_THREADS, D1_SMEM, s>>>(b->d_rigs, gr.d_tasks); break;
+            case BT_RED: k_mr_reduce<T><<<gr.count, 256, RT_SMEM, s>>>(b->d_rigs, gr.d_tasks); break;
+            case BT_CO: k_mr_coarse<T><<<gr.count, 256, 0, s>>>(b->d_rigs, gr.d_tasks); break;
+            case BT_UPS: k_mr_up_simple<<<gr.count, U_THREADS, 0, s>>>(b->d_rigs, gr.d_tasks); break;
+            case BT_UPF2: k_mr_up_full<T, 2><<<gr.count, U_THREADS, up_full_smem<2>(), s>>>(b->d_rigs, gr.d_tasks); break;
+            case BT_UPF4: k_mr_up_full<T, 4><<<gr.count, U_THREADS, up_full_smem<4>(), s>>>(b->d_rigs, gr.d_tasks); break;
+            case BT_UPG: k_batch_general<T><<<gr.count, U_THREADS, 0, s>>>(b->d_rigs, gr.d_tasks, b->d_ctl); break;
+            default: break;
+        }
+    }
+    return launch_status();
+}
+
+template <typename T>
+stitch_status b_staged_attrs() {
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_up_full<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)up_full_smem<2>()));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_up_full<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)up_full_smem<4>()));
+    return STITCH_OK;
+}
+
+// Graph of the staged schedule, captured from a private stream: descriptor copy, status reset,
+// the stage launches in dependency order, status readback.
+template <typename T>
+stitch_status b_build_staged_graph(BatchState* b) {
+    cudaStream_t cs;
+    STITCH_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    stitch_status st = STITCH_OK;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = STITCH_ECUDA;
+    if (st == STITCH_OK) st = b_prepare(b, cs);
+    if (st == STITCH_OK) st = b_launch_staged<T>(b, cs);
+    if (st == STITCH_OK && cudaMemcpyAsync(b->h_status, b->d_ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+        st = STITCH_ECUDA;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(cs, &g) != cudaSuccess) st = STITCH_ECUDA;
+    cudaStreamDestroy(cs);
+    if (st != STITCH_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    b->graph = g;
+    STITCH_CUDA_TRY(cudaGraphInstantiate(&b->exec, g, 0));
+    return STITCH_OK;
 }
 
 stitch_status b_prepare(BatchState* b, cudaStream_t s) {
@@ -1543,11 +1718,11 @@ stitch_status b_build_graph(BatchState* b) {
     ms.dst = b->d_done;
     ms.width = b->need.size();
     STITCH_CUDA_TRY(cudaGraphAddMemsetNode(&m2, g, nullptr, 0, &ms));
-    int ntasks = b->ntasks;
+    int ntasks = b->ntasks, nrigs = b->n, chunk = b->chunk;
     void* args[] = {(void*)&b->d_rigs, (void*)&b->d_tasks[b->order], (void*)&ntasks, (void*)&b->d_ctl,
-                    (void*)&b->d_done, (void*)&b->d_need};
+                    (void*)&b->d_done, (void*)&b->d_need, (void*)&nrigs, (void*)&chunk};
     cudaKernelNodeParams kp{};
-    kp.func = (void*)k_batch<T>;
+    kp.func = batch_kernel<T>(b->variant);
     kp.gridDim = dim3(b->grid);
     kp.blockDim = dim3(B_THREADS);
     kp.sharedMemBytes = (unsigned)B_SMEM;
@@ -1575,38 +1750,66 @@ stitch_status b_build_graph(BatchState* b) {
     return STITCH_OK;
 }
 
-// Time every (ordering, blocks per SM) candidate once on the real frames and keep the fastest.
+// Time every candidate schedule (stage ordering, register variant with its resident blocks per
+// SM, tasks per dequeue) on the real frames and keep the fastest.
 template <typename T>
 stitch_status b_tune(BatchState* b, cudaStream_t s) {
     const char* mode = getenv("STITCH_TUNE");
-    b->grid = b->max_bpsm * b->sms;
+    b->variant = 1;
+    b->grid = b->max_bpsm[1] * b->sms;
     b->order = 1;
+    b->chunk = 4;
+    b->staged = false;
     if (mode && strcmp(mode, "off") == 0) return STITCH_OK;
     cudaEvent_t e0, e1;
     STITCH_CUDA_TRY(cudaEventCreate(&e0));
     STITCH_CUDA_TRY(cudaEventCreate(&e1));
     float best = 1e30f;
+    const int chunks[3] = {1, 4, 8};
     for (int order = 0; order < 2; ++order)
-        for (int bpsm = 1; bpsm <= b->max_bpsm; ++bpsm)
-            for (int rep = 0; rep < 2; ++rep) {
-                stitch_status st = b_prepare(b, s);
-                if (st != STITCH_OK) return st;
-                cudaEventRecord(e0, s);
-                st = b_launch<T>(b, order, bpsm * b->sms, s);
-                if (st != STITCH_OK) return st;
-                cudaEventRecord(e1, s);
-                STITCH_CUDA_TRY(cudaEventSynchronize(e1));
-                int status = 0;
-                STITCH_CUDA_TRY(cudaMemcpy(&status, b->d_ctl + 1, sizeof(int), cudaMemcpyDeviceToHost));
-                if (status) return STITCH_ETIMEOUT;
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep == 1 && ms < best) {
-                    best = ms;
-                    b->order = order;
-                    b->grid = bpsm * b->sms;
+        for (int variant = 0; variant < 2; ++variant)
+            for (int ci = 0; ci < 3; ++ci)
+                for (int rep = 0; rep < 2; ++rep) {
+                    const int grid = b->max_bpsm[variant] * b->sms;
+                    stitch_status st = b_prepare(b, s);
+                    if (st != STITCH_OK) return st;
+                    cudaEventRecord(e0, s);
+                    st = b_launch<T>(b, order, variant, grid, chunks[ci], s);
+                    if (st != STITCH_OK) return st;
+                    cudaEventRecord(e1, s);
+                    STITCH_CUDA_TRY(cudaEventSynchronize(e1));
+                    int status = 0;
+                    STITCH_CUDA_TRY(cudaMemcpy(&status, b->d_ctl + 1, sizeof(int), cudaMemcpyDeviceToHost));
+                    if (status) return STITCH_ETIMEOUT;
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep == 1 && ms < best) {
+                        best = ms;
+                        b->order = order;
+                        b->variant = variant;
+                        b->grid = grid;
+                        b->chunk = chunks[ci];
+                    }
                 }
-            }
+    // the staged schedule
+    for (int rep = 0; rep < 2; ++rep) {
+        stitch_status st = b_prepare(b, s);
+        if (st != STITCH_OK) return st;
+        cudaEventRecord(e0, s);
+        st = b_launch_staged<T>(b, s);
+        if (st != STITCH_OK) return st;
+        cudaEventRecord(e1, s);
+        STITCH_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep == 1 && ms < best) {
+            best = ms;
+            b->staged = true;
+        }
+    }
+    if (mode && strcmp(mode, "persistent") == 0) b->staged = false;
+    if (mode && strcmp(mode, "staged") == 0) b->staged = true;
+    b->tuned_ms = best;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return STITCH_OK;
@@ -1657,10 +1860,24 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
         d.refs = fs->refs;
         for (int q = 0; q < UP_KINDS; ++q) d.up[q] = fs->up_tiles[q];
         const int L = r->geom.levels;
+        auto mk = [&](int type, int idx, int level, int st) {
+            BTask tk{k, type, idx, level, st, 0, 0, 0, {}};
+            switch (type) {
+                case BT_D1: memcpy(tk.tile, &fs->h_d1[idx], sizeof(D1Tile)); break;
+                case BT_RED: memcpy(tk.tile, &fs->h_red[level][idx], sizeof(Tile)); break;
+                case BT_CO: memcpy(tk.tile, &fs->h_co[level][idx], sizeof(LevelTile)); break;
+                case BT_UPS: memcpy(tk.tile, &fs->h_up[UP_SIMPLE][idx], sizeof(UpTile)); break;
+                case BT_UPF2: memcpy(tk.tile, &fs->h_up[UP_FULL2][idx], sizeof(UpTile)); break;
+                case BT_UPF4: memcpy(tk.tile, &fs->h_up[UP_FULL4][idx], sizeof(UpTile)); break;
+                case BT_UPG: memcpy(tk.tile, &fs->h_up[UP_GENERAL][idx], sizeof(UpTile)); break;
+                default: break;
+            }
+            return tk;
+        };
         auto add_stage = [&](int type, int level, int count) {
             const int st = (int)stages[k].size();
             stages[k].emplace_back();
-            for (int i = 0; i < count; ++i) stages[k].back().push_back({k, type, i, level, st, 0, 0, 0});
+            for (int i = 0; i < count; ++i) stages[k].back().push_back(mk(type, i, level, st));
             b->need[(size_t)k * B_MAXSTAGE + st] = count;
             b->tasks_by_type[type] += count;
         };
@@ -1671,15 +1888,15 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
             const int st = (int)stages[k].size();
             stages[k].emplace_back();
             int cnt = 0;
-            for (int i = 0; i < fs->n_up[UP_SIMPLE]; ++i) stages[k].back().push_back({k, BT_UPS, i, 0, st, 0, 0, 0});
-            for (int i = 0; i < fs->n_up[UP_FULL2]; ++i) stages[k].back().push_back({k, BT_UPF2, i, 0, st, 0, 0, 0});
-            for (int i = 0; i < fs->n_up[UP_FULL4]; ++i) stages[k].back().push_back({k, BT_UPF4, i, 0, st, 0, 0, 0});
+            for (int i = 0; i < fs->n_up[UP_SIMPLE]; ++i) stages[k].back().push_back(mk(BT_UPS, i, 0, st));
+            for (int i = 0; i < fs->n_up[UP_FULL2]; ++i) stages[k].back().push_back(mk(BT_UPF2, i, 0, st));
+            for (int i = 0; i < fs->n_up[UP_FULL4]; ++i) stages[k].back().push_back(mk(BT_UPF4, i, 0, st));
             cnt = (int)stages[k].back().size();
             b->need[(size_t)k * B_MAXSTAGE + st] = cnt;
             b->tasks_by_type[BT_UPS] += fs->n_up[UP_SIMPLE];
             b->tasks_by_type[BT_UPF2] += fs->n_up[UP_FULL2];
             b->tasks_by_type[BT_UPF4] += fs->n_up[UP_FULL4];
-            for (int i = 0; i < fs->n_up[UP_GENERAL]; ++i) gtasks.push_back({k, BT_UPG, i, 0, st, 0, 0, 0});
+            for (int i = 0; i < fs->n_up[UP_GENERAL]; ++i) gtasks.push_back(mk(BT_UPG, i, 0, st));
         }
     }
     // two orderings: stages ranked from the start, or aligned so that every rig ends together
@@ -1701,6 +1918,38 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
         return st;
     }
     b->ngtasks = (int)gtasks.size();
+    // staged schedule: groups by (type, level) in dependency order
+    {
+        int maxL = 0;
+        for (int k = 0; k < n; ++k) maxL = std::max(maxL, rigs[k]->geom.levels);
+        std::vector<std::pair<int, int>> order_tl;
+        order_tl.push_back({BT_D1, 1});
+        for (int l = 2; l < maxL; ++l) order_tl.push_back({BT_RED, l});
+        for (int l = maxL - 1; l >= 2; --l) order_tl.push_back({BT_CO, l});
+        order_tl.push_back({BT_UPS, 0});
+        order_tl.push_back({BT_UPF2, 0});
+        order_tl.push_back({BT_UPF4, 0});
+        for (auto [type, level] : order_tl) {
+            std::vector<BTask> v;
+            for (int k = 0; k < n; ++k)
+                for (const auto& stv : stages[k])
+                    for (const BTask& tk : stv)
+                        if (tk.type == type && tk.level == level) v.push_back(tk);
+            if (v.empty()) continue;
+            StageGroup gr{type, level, (int)v.size(), nullptr};
+            if ((st = b_upload(b, v, &gr.d_tasks)) != STITCH_OK) {
+                b_free(b);
+                return st;
+            }
+            b->groups.push_back(gr);
+        }
+        if (!gtasks.empty()) b->groups.push_back({BT_UPG, 0, (int)gtasks.size(), b->d_gtasks});
+        const stitch_status as = fp16 ? b_staged_attrs<half4>() : b_staged_attrs<float4>();
+        if (as != STITCH_OK) {
+            b_free(b);
+            return as;
+        }
+    }
     std::vector<int> zeros(b->need.size(), 0), ctl = {0, 0, 0, 1 << 22};
     if ((st = b_upload(b, zeros, &b->d_done)) != STITCH_OK || (st = b_upload(b, ctl, &b->d_ctl)) != STITCH_OK) {
         b_free(b);
@@ -1719,22 +1968,23 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
         return STITCH_ECUDA;
     }
     b->sms = prop.multiProcessorCount;
-    int bpsm = 0;
-    cudaError_t e;
-    if (fp16) {
-        e = cudaFuncSetAttribute(k_batch<half4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B_SMEM);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_batch<half4>, B_THREADS, B_SMEM);
-    } else {
-        e = cudaFuncSetAttribute(k_batch<float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B_SMEM);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_batch<float4>, B_THREADS, B_SMEM);
-    }
-    if (e != cudaSuccess || bpsm < 1) {
-        cudaGetLastError();
+    if (n > B_MAXRIGS) {
         b_free(b);
-        return STITCH_ECUDA;
+        return STITCH_EUNSUPPORTED;
     }
-    b->max_bpsm = bpsm;
-    b->grid = bpsm * b->sms;
+    for (int variant = 0; variant < 2; ++variant) {
+        int bpsm = 0;
+        void* fn = fp16 ? batch_kernel<half4>(variant) : batch_kernel<float4>(variant);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B_SMEM);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, fn, B_THREADS, B_SMEM);
+        if (e != cudaSuccess || bpsm < 1) {
+            cudaGetLastError();
+            b_free(b);
+            return STITCH_ECUDA;
+        }
+        b->max_bpsm[variant] = bpsm;
+    }
+    b->grid = b->max_bpsm[1] * b->sms;
     *out = b;
     return STITCH_OK;
 }
@@ -1762,7 +2012,8 @@ stitch_status fused_batch_frames(void* bp, const uint8_t* const* const* frames, 
         const stitch_status st = b->fp16 ? b_tune<half4>(b, s) : b_tune<float4>(b, s);
         if (st != STITCH_OK) return st;
         b->tuned = true;
-        const stitch_status gs = b->fp16 ? b_build_graph<half4>(b) : b_build_graph<float4>(b);
+        const stitch_status gs = b->staged ? (b->fp16 ? b_build_staged_graph<half4>(b) : b_build_staged_graph<float4>(b))
+                                           : (b->fp16 ? b_build_graph<half4>(b) : b_build_graph<float4>(b));
         if (gs != STITCH_OK) return gs;
     }
     *b->h_status = 0;
@@ -1782,7 +2033,7 @@ void fused_batch_destroy(void* bp) {
 stitch_status fused_batch_info(void* bp, int32_t* order, int32_t* grid, int64_t* ntasks) {
     BatchState* b = (BatchState*)bp;
     if (!b) return STITCH_EINVAL;
-    if (order) *order = b->order;
+    if (order) *order = b->staged ? 0xF : (b->order | (b->variant << 4) | (b->chunk << 8));
     if (grid) *grid = b->grid;
     if (ntasks) *ntasks = b->ntasks + b->ngtasks;
     return STITCH_OK;

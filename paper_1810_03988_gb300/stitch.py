@@ -209,7 +209,10 @@ def stitch_batch_get_schedule(batch: int) -> dict:
     o, g, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
     _check(load().stitch_batch_get_schedule(batch, ctypes.byref(o), ctypes.byref(g), ctypes.byref(t)),
            "stitch_batch_get_schedule")
-    return {"order": o.value, "grid": g.value, "tasks": t.value}
+    if o.value == 0xF:
+        return {"mode": "staged", "tasks": t.value}
+    return {"mode": "persistent", "order": o.value & 15, "register_variant": (o.value >> 4) & 15,
+            "chunk": o.value >> 8, "grid": g.value, "tasks": t.value}
 
 
 def stitch_batch_wait_test(batch: int, spin_limit: int, rig: int) -> None:

@@ -38,7 +38,7 @@ def test_batch_equals_per_rig_launches(out_float):
             for g, r in zip(got, ref):
                 assert np.array_equal(g, r)
         sch = b.schedule()
-        assert sch["grid"] > 0 and sch["tasks"] > 0 and sch["order"] in (0, 1)
+        assert sch["tasks"] > 0 and sch["mode"] in ("persistent", "staged")
     for r in rigs:
         r.close()
 
@@ -82,10 +82,36 @@ def test_batch_fp16_bands():
         r.close()
 
 
-def test_batch_bounded_wait_times_out_and_recovers():
-    """A stage target that is never reached makes the device wait give up: the call returns
-    STITCH_ETIMEOUT, and after restoring the target the same batch stitches correctly."""
+@pytest.fixture
+def forced_schedule(monkeypatch):
+    def force(mode):
+        monkeypatch.setenv("STITCH_TUNE", mode)
+    return force
+
+
+@pytest.mark.parametrize("mode", ["persistent", "staged"])
+def test_each_schedule_equals_per_rig_launches(mode, forced_schedule):
+    from paper_1810_03988_gb300 import Batch
+    forced_schedule(mode)
+    cfgs = synth.config_batch(6, seed=5, scale=0.25)
+    rigs, frames = _rigs_and_frames(cfgs)
+    ref = _per_rig(rigs, frames)
+    with Batch(rigs) as b:
+        for _ in range(2):
+            got = [o.cpu().numpy() for o in b.stitch(frames)]
+            for g, r in zip(got, ref):
+                assert np.array_equal(g, r)
+        assert b.schedule()["mode"] == mode
+    for r in rigs:
+        r.close()
+
+
+def test_batch_bounded_wait_times_out_and_recovers(forced_schedule):
+    """A stage target that is never reached makes the device wait of the persistent schedule give
+    up: the call returns STITCH_ETIMEOUT, and after restoring the target the same batch stitches
+    correctly."""
     from paper_1810_03988_gb300 import Batch, StitchError, stitch
+    forced_schedule("persistent")
     cfgs = synth.config_batch(3, seed=1, scale=0.125)
     rigs, frames = _rigs_and_frames(cfgs)
     ref = _per_rig(rigs, frames)
