@@ -95,7 +95,12 @@ struct UpTile {
 constexpr int D1_TX = 32, D1_TY = 16;                        // level-1 outputs per tile
 constexpr int D1_SX = 2 * D1_TX + 3, D1_SY = 2 * D1_TY + 3;  // level-0 virtual region (67 x 35)
 constexpr int D1_THREADS = 256;
-constexpr size_t D1_SMEM = sizeof(float4) * (D1_SX * D1_SY + D1_TX * D1_SY);
+constexpr int D1_SXH = (D1_SX + 1) / 2;  // level-0 samples are stored as even and odd column planes
+constexpr size_t D1_SMEM = sizeof(float4) * (2 * D1_SXH * D1_SY + D1_TX * D1_SY);
+
+// Shared-memory slot of level-0 virtual sample (row r, column c): even and odd columns in separate
+// planes, so the horizontal REDUCE pass (columns 2p .. 2p+4 for output p) reads consecutive slots.
+__device__ __forceinline__ int s0_slot(int r, int c) { return r * (2 * D1_SXH) + (c & 1) * D1_SXH + (c >> 1); }
 
 // Level-0 samples of the virtual region handled per thread in one chunk of rows.
 constexpr int D1_CHUNK_ROWS = (D1_SY + 1) / 2;                                   // 18
@@ -110,8 +115,8 @@ template <typename T>
 __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
                                            const OutDesc& od, const D1Tile& tl, const CamRef* __restrict__ refs,
                                            float4* smem) {
-    float4* s0 = smem;                  // [D1_SY][D1_SX] level 0 (virtual coordinates)
-    float4* sh = smem + D1_SX * D1_SY;  // [D1_SY][D1_TX] horizontally reduced
+    float4* s0 = smem;                        // level 0 (virtual coordinates), see s0_slot
+    float4* sh = smem + 2 * D1_SXH * D1_SY;   // [D1_SY][D1_TX] horizontally reduced
 
     const int i = tl.cam;
     const CamDev& ci = cams[i];
@@ -129,12 +134,14 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
         const CamRef ref = refs[tl.first];
         const int W = ci.W, H = ci.H;
         const float fU0 = (float)ref.tm.U0, fV0 = (float)ref.tm.V0;
+        (void)W;
+        (void)H;
         for (int q = t; q < D1_SX * D1_SY; q += D1_THREADS) {
             const int r = q / D1_SX, c = q % D1_SX;
             const int x = fold101(vx0 + c, g.nx[0]), y = fold101(vy0 + r, g.ny[0]);
             const Pos p = map_pos(ref.tm, fU0, fV0, (float)(x - ref.ax), (float)(y - ref.ay));
-            const float3 v = sample_rgb(px_i, pitch_i, p, W, H, scale);
-            s0[q] = make_float4(v.x, v.y, v.z, 1.f);
+            const float3 v = sample_rgb_inside(px_i, pitch_i, p, scale);
+            s0[s0_slot(r, c)] = make_float4(v.x, v.y, v.z, 1.f);
         }
     } else
     // S1 + S2 on the virtual level-0 region, two chunks of rows; cameras in the outer loop so
@@ -179,7 +186,8 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
             if (q >= nq) break;
             float4 v = val[k];
             v.w = ws[k] > 0.f ? __fdividef(v.w, ws[k]) : 0.f;
-            s0[r0 * D1_SX + q] = v;
+            const int qq = r0 * D1_SX + q;
+            s0[s0_slot(qq / D1_SX, qq % D1_SX)] = v;
         }
     }
     __syncthreads();
@@ -192,7 +200,7 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
         for (int q = t; q < 4 * D1_TX * D1_TY; q += D1_THREADS) {
             const int dx = q % (2 * D1_TX), dy = q / (2 * D1_TX);
             if (X0 + dx >= X1 || Y0 + dy >= Y1) continue;
-            const float4 v = s0[(dy + 2) * D1_SX + dx + 2];
+            const float4 v = s0[s0_slot(dy + 2, dx + 2)];
             put_pixel(stage, od, dx, dy, X0 + dx, Y0 + dy, __saturatef(v.x), __saturatef(v.y), __saturatef(v.z));
         }
         if (!od.is_float) {
@@ -204,10 +212,13 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
     // S3 horizontal pass: sh[r][p] = sum_m w(m) s0[r][2p + m]
     for (int q = t; q < D1_TX * D1_SY; q += D1_THREADS) {
         const int r = q / D1_TX, p = q - r * D1_TX;
-        const float4* row = s0 + r * D1_SX + 2 * p;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int m = 0; m < 5; ++m) acc = f4fma(c_w5[m], row[m], acc);
+        const float4* ev = s0 + r * (2 * D1_SXH) + p;  // columns 2p, 2p+2, 2p+4
+        const float4* od_ = ev + D1_SXH;              // columns 2p+1, 2p+3
+        float4 acc = f4fma(c_w5[0], ev[0], make_float4(0.f, 0.f, 0.f, 0.f));
+        acc = f4fma(c_w5[1], od_[0], acc);
+        acc = f4fma(c_w5[2], ev[1], acc);
+        acc = f4fma(c_w5[3], od_[1], acc);
+        acc = f4fma(c_w5[4], ev[2], acc);
         sh[q] = acc;
     }
     __syncthreads();
@@ -1077,15 +1088,17 @@ Rect cone_level0(const RigGeom& g, int x0, int x1, int y0, int y1) {
     return make_rect(yx, yy);
 }
 
-// Camera c is valid with feather weight >= 0.5 at every pixel of rect q (convex quad: corners).
-bool solidly_inside(const CamDev& c, const Rect& q) {
+// Camera c maps every pixel of rect q into [m, W-1-m] x [m, H-1-m] of its image (the image of a
+// rectangle under a homography in front of the camera is convex, so its corners decide).  With
+// m = 0 the feather weight is >= 0.5 everywhere; with m > 0 no sample needs coordinate clamping.
+bool solidly_inside(const CamDev& c, const Rect& q, double m = 0.0) {
     const double xs[2] = {(double)q.x0, (double)(q.x1 - 1)}, ys[2] = {(double)q.y0, (double)(q.y1 - 1)};
     for (double x : xs)
         for (double y : ys) {
             const double w = c.A[6] * x + c.A[7] * y + c.A[8];
             if (!(w > 0.0)) return false;
             const double u = (c.A[0] * x + c.A[1] * y + c.A[2]) / w, v = (c.A[3] * x + c.A[4] * y + c.A[5]) / w;
-            if (!(u >= 0.0 && u <= c.W - 1.0 && v >= 0.0 && v <= c.H - 1.0)) return false;
+            if (!(u >= m && u <= c.W - 1.0 - m && v >= m && v <= c.H - 1.0 - m)) return false;
         }
     return true;
 }
@@ -1180,7 +1193,9 @@ stitch_status fused_plan(stitch_rig* r) {
                         refs.push_back(make_ref(cj, j, bx0, by0));
                         ++t.count;
                     }
-                    if (t.count == 1 && solidly_inside(c, Rect{bx0, bx1, by0, by1})) t.flags |= D1_INTERIOR;
+                    // interior: one camera, every input at least 0.01 px inside its image, so the
+                    // weight is 1 and no coordinate needs clamping (FP32 positions err by ~1e-5 px)
+                    if (t.count == 1 && solidly_inside(c, Rect{bx0, bx1, by0, by1}, 0.01)) t.flags |= D1_INTERIOR;
                     d1.push_back(t);
                 }
         }

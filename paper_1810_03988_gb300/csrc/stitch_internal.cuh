@@ -257,6 +257,24 @@ __device__ __forceinline__ float3 sample_rgb(const uint8_t* __restrict__ px, lon
     return o;
 }
 
+// Bilinear RGB sample of a position known to lie in [0, W-1) x [0, H-1) (no clamping needed).
+__device__ __forceinline__ float3 sample_rgb_inside(const uint8_t* __restrict__ px, long long pitch, const Pos& p,
+                                                    float scale) {
+    const uint8_t* a = px + (long long)p.iv * pitch + 3 * p.iu;
+    const uint8_t* b = a + pitch;
+    float3 o;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float p00 = u8_to_f(__ldg(a + c)), p01 = u8_to_f(__ldg(a + 3 + c));
+        const float p10 = u8_to_f(__ldg(b + c)), p11 = u8_to_f(__ldg(b + 3 + c));
+        const float top = fmaf(p.fu, p01 - p00, p00);
+        const float bot = fmaf(p.fu, p11 - p10, p10);
+        const float v = fmaf(p.fv, bot - top, top) * scale;
+        if (c == 0) o.x = v; else if (c == 1) o.y = v; else o.z = v;
+    }
+    return o;
+}
+
 __device__ __forceinline__ unsigned char quantize_u8(float v) {
     // v already clamped to [0, 1]; round half to even
     return (unsigned char)__float2int_rn(255.0f * v);
