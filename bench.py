@@ -38,6 +38,22 @@ DEFAULT_FRAMES = {"8x4k": 30, "4x1080p": 60, "2cam": 1}
 METRIC = "stitched output MPix/s and frames/s on 1 GB300; % of HBM roofline vs plain path"
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's time: every rank contributes its value, all receive the maximum."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_step_per_rank: float, world: int, ms_per_step: float) -> float:
+    """Whole-job throughput: every rank processes the same units per step (replicas), over the
+    slowest rank's step time."""
+    return world * units_per_step_per_rank / (ms_per_step / 1e3)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -304,10 +320,7 @@ def main():
         kt = rig.kernel_times() if profile else {}
         if profile:
             rig.set_profiling(False)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist if world > 1 else None, dev)
         return ms, kt
 
     rig = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, band_fp16=args.fp16_bands, path=args.path,
@@ -322,7 +335,7 @@ def main():
     clk = clocks.stop()
 
     mpix = cfg.canvas_w * cfg.canvas_h / 1e6
-    value = world * mpix / (ms / 1e3)
+    value = job_value(mpix, world, ms)
     fps = 1e3 / ms
     hbm_peak, peak_kind = _peaks()
     cbytes = compulsory_bytes(cfg)
@@ -378,10 +391,7 @@ def main():
     for k in range(args.e2e_steps):
         rig.stitch_host(pinned[k % len(pinned)], hout)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist if world > 1 else None, dev)
     h2d = sum(c.width * c.height * 3 for c in cfg.cameras)
     d2h = cfg.canvas_w * cfg.canvas_h * 3
     e2e = {"value": world * mpix / e2e_s, "unit": "MPix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
