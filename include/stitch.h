@@ -118,6 +118,20 @@ stitch_status stitch_frames_host(stitch_rig* rig, const uint8_t* const* host_fra
                                  void* host_out, int64_t out_pitch, void* stream);
 
 /*
+ * Asynchronous HOST-buffer variant with upload, stitching and download of consecutive calls
+ * overlapped (the paper's stream strategy, Sec. 4.3.2 / Fig. 3b: the next frame is uploaded while
+ * the current one is processed).  The call only enqueues work: `stream` waits for this call's
+ * download, so the canvas in `host_out` is complete once `stream` has reached this point (e.g.
+ * after cudaStreamSynchronize(stream)).  Host frames and `host_out` must stay valid and untouched
+ * until then; pinned memory makes the copies asynchronous.  The upload is NOT ordered after work
+ * queued earlier on `stream` (it reads host memory, which the caller has filled before the call).  The rig keeps two staging slots and
+ * three streams of its own, created by the first call (which may therefore return ENOMEM).
+ * Status: OK, EINVAL, ENOMEM, ECUDA.
+ */
+stitch_status stitch_frames_host_async(stitch_rig* rig, const uint8_t* const* host_frames, const int64_t* pitches,
+                                       void* host_out, int64_t out_pitch, void* stream);
+
+/*
  * S7: overlap photometric loss and its gradient.
  *   params  DEVICE, num_cameras x 9 doubles per camera: a11 a12 a13 a21 a22 a23 a31 a32 gain of
  *           the canvas->camera map A whose a33 is the rig's (+1 or -1, see stitch_rig_get_camera).

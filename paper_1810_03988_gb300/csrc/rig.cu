@@ -251,6 +251,7 @@ void stitch_rig_destroy(stitch_rig* r) {
     if (!r) return;
     DeviceGuard dg(r->device);
     cudaDeviceSynchronize();
+    pipeline_release(r);
     fused_release(r);
     backward_release(r);
     free_all(r);

@@ -380,9 +380,10 @@ struct stitch_rig {
     // backward state
     void* bw = nullptr;
 
-    // host staging for stitch_frames_host
+    // host staging for stitch_frames_host, and the overlapped pipeline of stitch_frames_host_async
     uint8_t* stage_frames[MAXC]{};
     void* stage_out = nullptr;
+    void* pipe = nullptr;
 
     // profiling
     bool prof = false;
@@ -412,6 +413,7 @@ stitch_status backward_plan(stitch_rig* r);
 stitch_status backward_run(stitch_rig* r, const FramePtrs& fp, const double* params, double* loss, double* grad,
                            cudaStream_t s);
 void backward_release(stitch_rig* r);
+void pipeline_release(stitch_rig* r);
 stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out);
 stitch_status fused_batch_frames(void* b, const uint8_t* const* const* frames, const int64_t* const* pitches,
                                  void* const* outs, const int64_t* out_pitches, cudaStream_t s);

@@ -51,6 +51,7 @@ SIGNATURES = {
     "stitch_rig_destroy": (None, [_P]),
     "stitch_frames": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
     "stitch_frames_host": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
+    "stitch_frames_host_async": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int64, _P]),
     "stitch_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "stitch_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "stitch_rig_get_info": (ctypes.c_int, [_P, ctypes.POINTER(stitch_rig_info)]),
@@ -134,6 +135,13 @@ def stitch_frames_host(rig: int, frame_ptrs, pitches, out_ptr: int, out_pitch: i
     fp = (_P * n)(*frame_ptrs)
     pt = (ctypes.c_int64 * n)(*pitches)
     _check(load().stitch_frames_host(rig, fp, pt, out_ptr, out_pitch, stream), "stitch_frames_host")
+
+
+def stitch_frames_host_async(rig: int, frame_ptrs, pitches, out_ptr: int, out_pitch: int, stream: int) -> None:
+    n = len(frame_ptrs)
+    fp = (_P * n)(*frame_ptrs)
+    pt = (ctypes.c_int64 * n)(*pitches)
+    _check(load().stitch_frames_host_async(rig, fp, pt, out_ptr, out_pitch, stream), "stitch_frames_host_async")
 
 
 def stitch_backward(rig: int, frame_ptrs, pitches, params_ptr: int, loss_ptr: int, grad_ptr: int,
@@ -318,6 +326,28 @@ class Rig:
         else:
             optr, opitch = out.ctypes.data, out.strides[0]
         stitch_frames_host(self.handle, ptrs, pitches, optr, opitch, _stream_handle(stream))
+        return out
+
+    def stitch_host_async(self, frames, out, stream=None):
+        """Enqueue a host-buffer stitch (frames: pinned uint8 tensors or arrays; out: pinned host
+        canvas); consecutive calls overlap upload, compute and download.  Synchronise `stream`
+        (default: the current torch stream) before reading `out` or reusing the inputs."""
+        import torch
+        ptrs, pitches = [], []
+        for f in frames:
+            if isinstance(f, torch.Tensor):
+                assert not f.is_cuda and f.stride(1) == 3 and f.stride(2) == 1
+                ptrs.append(f.data_ptr())
+                pitches.append(f.stride(0))
+            else:
+                assert f.flags.c_contiguous and f.dtype == np.uint8
+                ptrs.append(f.ctypes.data)
+                pitches.append(f.strides[0])
+        if isinstance(out, torch.Tensor):
+            optr, opitch = out.data_ptr(), out.stride(0) * out.element_size()
+        else:
+            optr, opitch = out.ctypes.data, out.strides[0]
+        stitch_frames_host_async(self.handle, ptrs, pitches, optr, opitch, _stream_handle(stream))
         return out
 
     def backward(self, frames, params, loss=None, grad=None, stream=None):
