@@ -184,6 +184,8 @@ typedef struct {
     int32_t tiles_full4;     /* blended, 3 or 4 cameras */
     int32_t tiles_general;   /* blended, more than 4 cameras */
     int32_t tiles_down1;     /* camera tiles that build Gaussian level 1 */
+    int32_t tiles_down1_staged;    /* of which: source footprint staged in shared memory */
+    int32_t tiles_down1_interior;  /* of which: one camera, weight 1, no coordinate clamping */
 } stitch_rig_info;
 
 stitch_status stitch_rig_get_info(const stitch_rig* rig, stitch_rig_info* info);

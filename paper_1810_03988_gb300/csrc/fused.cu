@@ -76,10 +76,18 @@ struct CamRef {
     int cam, ax, ay, pad;
 };
 
-// down1 tile: camera, level-1 origin, and the cameras (CamRef range) whose validity box meets
-// the tile's level-0 inputs (for the weight normalisation), in camera order.
+// down1 tile: camera, level-1 origin, the camera's CamRef anchored at the tile, the tile's block in
+// the table of normalised level-0 weights (-1 for INTERIOR tiles, whose weight is 1 everywhere),
+// and the source-image footprint of its samples staged in shared memory (fx0 | fy0 << 16,
+// fw | fh << 16; fwh = 0 when the footprint does not fit and samples are read from the frame).
 struct D1Tile {
-    int cam, k0, j0, first, count, self, flags, pad;
+    int cam, k0, j0, ref, wtab, flags, fxy, fwh;
+};
+
+// Cameras (CamRef range, in camera order) whose validity box meets a down1 tile's level-0 inputs,
+// and the position of the tile's own camera among them: the weight normalisation of the tile.
+struct D1Cams {
+    int first, count, self, pad;
 };
 constexpr int D1_INTERIOR = 1;  // inputs solidly inside the camera, no other camera: weight 1
 constexpr int D1_SOLO_OUT = 2;  // the canvas tile under this tile is SOLO for this camera
@@ -96,98 +104,297 @@ constexpr int D1_TX = 32, D1_TY = 16;                        // level-1 outputs 
 constexpr int D1_SX = 2 * D1_TX + 3, D1_SY = 2 * D1_TY + 3;  // level-0 virtual region (67 x 35)
 constexpr int D1_THREADS = 256;
 constexpr int D1_SXH = (D1_SX + 1) / 2;  // level-0 samples are stored as even and odd column planes
-constexpr size_t D1_SMEM = sizeof(float4) * (2 * D1_SXH * D1_SY + D1_TX * D1_SY);
+// Source footprint capacity in texels.  The footprint is staged as three planes of floats (R, G,
+// B; rows padded to a multiple of 4 texels) and shares its space with the horizontal REDUCE
+// buffer, which is used after the samples are taken.  With it a block needs ~73 KB of shared
+// memory, so three blocks fit on an SM.
+constexpr int D1_FOOT = 3072;
+constexpr int D1_S0_F4 = 2 * D1_SXH * D1_SY;                                    // level-0 planes
+constexpr int D1_SH_F4 = 3 * D1_FOOT / 4 > D1_TX * D1_SY ? 3 * D1_FOOT / 4 : D1_TX * D1_SY;  // footprint / sh
+constexpr int D1_ROW_F4 = (D1_SY + 3) / 4;                                      // per-row offsets
+constexpr size_t D1_SMEM = sizeof(float4) * (D1_S0_F4 + D1_SH_F4 + D1_ROW_F4);
+static_assert(D1_THREADS == 256 && D1_SX == 67, "the staged pass maps 64 columns x 4 row phases");
 
 // Shared-memory slot of level-0 virtual sample (row r, column c): even and odd columns in separate
 // planes, so the horizontal REDUCE pass (columns 2p .. 2p+4 for output p) reads consecutive slots.
 __device__ __forceinline__ int s0_slot(int r, int c) { return r * (2 * D1_SXH) + (c & 1) * D1_SXH + (c >> 1); }
 
-// Level-0 samples of the virtual region handled per thread in one chunk of rows.
-constexpr int D1_CHUNK_ROWS = (D1_SY + 1) / 2;                                   // 18
-constexpr int D1_NS = (D1_CHUNK_ROWS * D1_SX + D1_THREADS - 1) / D1_THREADS;   // 5
+constexpr int D1_NSAMP = D1_SX * D1_SY;  // level-0 samples of a tile's virtual region
+
+// Normalised feather weights of the level-0 samples of a down1 tile (S2: w_i / sum_j w_j over the
+// cameras whose validity box contains the sample), or -1 for samples outside the camera's pyramid
+// region Omega^0_i.  They depend on the geometry only, so the rig computes them once at creation
+// (the paper's pre-corrected parameters, Algorithm 4, and start-up preallocation, Sec. 4.3.2), one
+// block per tile; down1 then warps only its own camera.
+__global__ void __launch_bounds__(D1_THREADS) k_d1_weights(const CamDev* __restrict__ cams, RigGeom g,
+                                                          const D1Tile* __restrict__ tiles,
+                                                          const D1Cams* __restrict__ tcams,
+                                                          const CamRef* __restrict__ refs, float* __restrict__ d1w) {
+    const D1Tile tl = tiles[blockIdx.x];
+    const D1Cams tc = tcams[blockIdx.x];
+    if (tl.wtab < 0) return;
+    const Rect o0 = cams[tl.cam].Om[0];
+    const int vx0 = 2 * tl.k0 - 2, vy0 = 2 * tl.j0 - 2;
+    float* out = d1w + (long long)tl.wtab * D1_NSAMP;
+    for (int q = threadIdx.x; q < D1_NSAMP; q += D1_THREADS) {
+        const int r = q / D1_SX, c = q % D1_SX;
+        const int x = fold101(vx0 + c, g.nx[0]), y = fold101(vy0 + r, g.ny[0]);
+        if (!o0.contains(x, y)) {
+            out[q] = -1.f;
+            continue;
+        }
+        float ws = 0.f, wself = 0.f;
+        for (int a = 0; a < tc.count; ++a) {
+            const CamRef ref = refs[tc.first + a];
+            const CamDev& cj = cams[ref.cam];
+            if (!cj.V.contains(x, y)) continue;
+            const Pos p = map_pos(ref.tm, (float)ref.tm.U0, (float)ref.tm.V0, (float)(x - ref.ax), (float)(y - ref.ay));
+            const float w = weight_of(p, (float)cj.W - 0.5f, (float)cj.H - 0.5f);
+            ws += w;
+            if (a == tc.self) wself = w;
+        }
+        out[q] = ws > 0.f ? __fdividef(wself, ws) : 0.f;
+    }
+}
 
 __device__ __forceinline__ void store_u8_tile(const unsigned char* __restrict__ stage, const OutDesc& od, int X0,
                                               int Y0, int X1, int Y1);
 __device__ __forceinline__ void put_pixel(unsigned char* stage, const OutDesc& od, int dx, int dy, int x, int y,
                                           float r, float g, float b);
 
+// Copy the footprint [fx0, fx0 + fw) x [fy0, fy0 + fh) of an RGB8 frame into shared memory as
+// three planes of floats (exact integer values) with rows of fw4 = fw rounded up to 4 texels.  A
+// thread takes groups of 4 texels (12 bytes: three aligned 32-bit words, since fx0 is a multiple
+// of 4), issues the loads of all its groups before converting, and writes each plane's 4 values
+// with one 16-byte store.  Frames whose base or pitch is not a multiple of 4 bytes are read byte
+// by byte.
+constexpr int D1_SG = (D1_FOOT / 4 + D1_THREADS - 1) / D1_THREADS;  // groups per thread
+
+__device__ __forceinline__ float byte_f(uint32_t w, uint32_t j) {
+    return __int_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | j)) - 8388608.0f;
+}
+
+__device__ __forceinline__ void stage_footprint(float* __restrict__ foot, const uint8_t* __restrict__ px,
+                                                long long pitch, int W, int fx0, int fy0, int fw, int fh) {
+    const int t = threadIdx.x;
+    const int gpr = (fw + 3) >> 2, ng = gpr * fh;  // groups per row = fw4 / 4
+    if (((reinterpret_cast<uintptr_t>(px) | (uintptr_t)pitch) & 3) != 0) {
+        for (int q = t; q < 4 * ng; q += D1_THREADS) {
+            const int rr = q / (4 * gpr), u = q - rr * 4 * gpr;
+            float r = 0.f, g = 0.f, b = 0.f;
+            if (u < fw) {
+                const uint8_t* src = px + (long long)(fy0 + rr) * pitch + 3 * (fx0 + u);
+                r = u8_to_f(__ldg(src));
+                g = u8_to_f(__ldg(src + 1));
+                b = u8_to_f(__ldg(src + 2));
+            }
+            foot[q] = r;
+            foot[D1_FOOT + q] = g;
+            foot[2 * D1_FOOT + q] = b;
+        }
+        return;
+    }
+    uint32_t w[D1_SG][3];
+#pragma unroll
+    for (int k = 0; k < D1_SG; ++k) {
+        const int q = t + k * D1_THREADS;
+        w[k][0] = w[k][1] = w[k][2] = 0u;
+        if (q < ng) {
+            const int rr = q / gpr, gx = q - rr * gpr;
+            const int u0 = fx0 + 4 * gx;
+            const uint8_t* src = px + (long long)(fy0 + rr) * pitch + 3 * u0;
+            if (u0 + 4 <= W) {
+                const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
+                w[k][0] = __ldg(s32);
+                w[k][1] = __ldg(s32 + 1);
+                w[k][2] = __ldg(s32 + 2);
+            } else {
+                // the image's last texels: only the bytes of texels < W exist
+                const int nb = 3 * (W - u0);
+#pragma unroll
+                for (int j = 0; j < 12; ++j)
+                    if (j < nb) w[k][j >> 2] |= (uint32_t)__ldg(src + j) << (8 * (j & 3));
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < D1_SG; ++k) {
+        const int q = t + k * D1_THREADS;
+        if (q < ng) {
+            // texels 4q .. 4q+3 of the padded rows (bytes R G B R | G B R G | B R G B)
+            float4* r4 = reinterpret_cast<float4*>(foot) + q;
+            r4[0] = make_float4(byte_f(w[k][0], 0), byte_f(w[k][0], 3), byte_f(w[k][1], 2), byte_f(w[k][2], 1));
+            r4[D1_FOOT / 4] = make_float4(byte_f(w[k][0], 1), byte_f(w[k][1], 0), byte_f(w[k][1], 3), byte_f(w[k][2], 2));
+            r4[D1_FOOT / 2] = make_float4(byte_f(w[k][0], 2), byte_f(w[k][1], 1), byte_f(w[k][2], 0), byte_f(w[k][2], 3));
+        }
+    }
+}
+
+// One level-0 sample from the staged footprint (planes R, G, B of D1_FOOT floats, rows of fw4).
+// (nu, nv, den) are the anchored numerators and denominator of the camera's TileMap at the
+// sample, bu = U0 - fx0 and bv = V0 - fy0.  Position, taps and arithmetic are those of map_pos +
+// sample_rgb (CLAMP) or sample_rgb_inside (!CLAMP), so the result is bit-identical whenever the
+// planned footprint holds the taps (the planner bounds |u|, |v| < 1e6 for staged tiles, so
+// map_pos's range clamp has no effect there).  Footprint-local taps are clamped into the
+// footprint: any other position reads a wrong texel of the footprint, never outside it; such
+// positions only feed level-1 samples outside the pyramid region, which are not stored.
+template <bool CLAMP>
+__device__ __forceinline__ float3 foot_sample(const float* __restrict__ foot, int fw, int fw4, int fh, int bu,
+                                              int bv, int fx0, int fy0, int W, int H, float nu, float nv,
+                                              float den, float scale) {
+    const float rden = __fdividef(1.0f, den);
+    const float ru = nu * rden, rv = nv * rden;
+    const float flu = floorf(ru), flv = floorf(rv);
+    float fx = ru - flu, fy = rv - flv;
+    const int lu = bu + (int)flu, lv = bv + (int)flv;  // footprint-local top-left tap
+    int lx, ly, ox, oy;
+    if (CLAMP) {
+        // image clamp of S1: outside [0, W-1) x [0, H-1) the border texel, fraction 0
+        if ((unsigned)(lu + fx0) >= (unsigned)(W - 1)) fx = 0.0f;
+        if ((unsigned)(lv + fy0) >= (unsigned)(H - 1)) fy = 0.0f;
+        lx = min(max(lu, 0), fw - 1);
+        ly = min(max(lv, 0), fh - 1);
+        ox = lx < fw - 1 ? 1 : 0;
+        oy = ly < fh - 1 ? fw4 : 0;
+    } else {
+        lx = min(max(lu, 0), fw - 2);
+        ly = min(max(lv, 0), fh - 2);
+        ox = 1;
+        oy = fw4;
+    }
+    const float* a = foot + ly * fw4 + lx;
+    float3 o;
+    {
+        const float p00 = a[0], p01 = a[ox], p10 = a[oy], p11 = a[oy + ox];
+        const float top = fmaf(fx, p01 - p00, p00), bot = fmaf(fx, p11 - p10, p10);
+        o.x = fmaf(fy, bot - top, top) * scale;
+    }
+    a += D1_FOOT;
+    {
+        const float p00 = a[0], p01 = a[ox], p10 = a[oy], p11 = a[oy + ox];
+        const float top = fmaf(fx, p01 - p00, p00), bot = fmaf(fx, p11 - p10, p10);
+        o.y = fmaf(fy, bot - top, top) * scale;
+    }
+    a += D1_FOOT;
+    {
+        const float p00 = a[0], p01 = a[ox], p10 = a[oy], p11 = a[oy + ox];
+        const float top = fmaf(fx, p01 - p00, p00), bot = fmaf(fx, p11 - p10, p10);
+        o.z = fmaf(fy, bot - top, top) * scale;
+    }
+    return o;
+}
+
+// S1 + S2 of a down1 tile from its staged footprint.  Thread t takes virtual column t % 64 at
+// the rows of residue t / 64 mod 4 (D1_RPT rows; the column's map terms are formed once) and,
+// for t < 105, one sample of the last 3 columns.  INTERIOR tiles have weight 1; the others take
+// the normalised weights `a` (loaded by d1_load_weights before the footprint was staged) and take
+// every sample: one outside Omega^0 (a < 0) reads a clamped texel and is then zeroed.
+constexpr int D1_RPT = (D1_SY + 3) / 4;  // rows per thread in the staged pass (9)
+
+__device__ __forceinline__ void d1_load_weights(const float* __restrict__ wt, float a[D1_RPT + 1]) {
+    const int t = threadIdx.x, c = t & 63;
+#pragma unroll
+    for (int k = 0; k < D1_RPT; ++k) {
+        const int r = (t >> 6) + 4 * k;
+        a[k] = r < D1_SY ? __ldg(wt + r * D1_SX + c) : -1.f;
+    }
+    a[D1_RPT] = t < 3 * D1_SY ? __ldg(wt + (t / 3) * D1_SX + 64 + t % 3) : -1.f;
+}
+
+template <bool INTERIOR>
+__device__ __forceinline__ void d1_staged_samples(float4* __restrict__ s0, const float* __restrict__ foot,
+                                                  const float* __restrict__ rowdy, const float a[D1_RPT + 1],
+                                                  const RigGeom& g, const CamRef& ref, int vx0, int fx0, int fy0,
+                                                  int fw, int fh, int W, int H, float scale) {
+    const TileMap& tm = ref.tm;
+    const int bu = tm.U0 - fx0, bv = tm.V0 - fy0;
+    const int fw4 = (fw + 3) & ~3;
+    const int t = threadIdx.x;
+    auto one = [&](int r, int c, float nuc, float nvc, float dqc, float ak) {
+        const float dy = rowdy[r];
+        const float nu = fmaf(tm.pu2, dy, nuc), nv = fmaf(tm.pv2, dy, nvc), den = fmaf(tm.q2, dy, dqc);
+        if (INTERIOR) {
+            const float3 v = foot_sample<false>(foot, fw, fw4, fh, bu, bv, fx0, fy0, W, H, nu, nv, den, scale);
+            s0[s0_slot(r, c)] = make_float4(v.x, v.y, v.z, 1.f);
+        } else {
+            const float3 v = foot_sample<true>(foot, fw, fw4, fh, bu, bv, fx0, fy0, W, H, nu, nv, den, scale);
+            s0[s0_slot(r, c)] = ak >= 0.f ? make_float4(v.x, v.y, v.z, ak) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    {
+        const int c = t & 63;
+        const float dx = (float)(fold101(vx0 + c, g.nx[0]) - ref.ax);
+        const float nuc = fmaf(tm.pu1, dx, tm.pu0), nvc = fmaf(tm.pv1, dx, tm.pv0), dqc = fmaf(tm.q1, dx, tm.q0);
+#pragma unroll
+        for (int k = 0; k < D1_RPT; ++k) {
+            const int r = (t >> 6) + 4 * k;
+            if (r < D1_SY) one(r, c, nuc, nvc, dqc, INTERIOR ? 1.f : a[k]);
+        }
+    }
+    if (t < 3 * D1_SY) {
+        const int c = 64 + t % 3, r = t / 3;
+        const float dx = (float)(fold101(vx0 + c, g.nx[0]) - ref.ax);
+        one(r, c, fmaf(tm.pu1, dx, tm.pu0), fmaf(tm.pv1, dx, tm.pv0), fmaf(tm.q1, dx, tm.q0),
+            INTERIOR ? 1.f : a[D1_RPT]);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
                                            const OutDesc& od, const D1Tile& tl, const CamRef* __restrict__ refs,
-                                           float4* smem) {
+                                           const float* __restrict__ d1w, float4* smem) {
     float4* s0 = smem;                        // level 0 (virtual coordinates), see s0_slot
-    float4* sh = smem + 2 * D1_SXH * D1_SY;   // [D1_SY][D1_TX] horizontally reduced
+    float4* sh = smem + D1_S0_F4;             // [D1_SY][D1_TX] horizontally reduced (or the footprint)
 
     const int i = tl.cam;
     const CamDev& ci = cams[i];
-    const Rect o1 = ci.Om[1], o0 = ci.Om[0];
+    const Rect o1 = ci.Om[1];
     const int k0 = tl.k0, j0 = tl.j0;              // level-1 tile origin
     const int vx0 = 2 * k0 - 2, vy0 = 2 * j0 - 2;  // level-0 virtual origin
     const int t = threadIdx.x;
-    const int na = tl.count;
     const float scale = ci.gain * (1.0f / 255.0f);
     const uint8_t* px_i = fp.p[i];
     const long long pitch_i = fp.pitch[i];
 
-    if (tl.flags & D1_INTERIOR) {
-        // every input is valid for this camera alone, weight 1: the warp only
-        const CamRef ref = refs[tl.first];
-        const int W = ci.W, H = ci.H;
-        const float fU0 = (float)ref.tm.U0, fV0 = (float)ref.tm.V0;
-        (void)W;
-        (void)H;
-        for (int q = t; q < D1_SX * D1_SY; q += D1_THREADS) {
+    const CamRef ref = refs[tl.ref];
+    const int W = ci.W, H = ci.H;
+    const float fU0 = (float)ref.tm.U0, fV0 = (float)ref.tm.V0;
+    const bool interior = tl.flags & D1_INTERIOR;
+    const float* __restrict__ wt = d1w + (long long)max(tl.wtab, 0) * D1_NSAMP;
+    if (tl.fwh != 0) {
+        // S1 from the source footprint staged in shared memory (the footprint shares its space
+        // with sh, which is written only after the samples are taken)
+        const int fx0 = tl.fxy & 0xffff, fy0 = (int)((unsigned)tl.fxy >> 16), fw = tl.fwh & 0xffff, fh = tl.fwh >> 16;
+        float* foot = reinterpret_cast<float*>(sh);
+        float* rowdy = reinterpret_cast<float*>(smem + D1_S0_F4 + D1_SH_F4);
+        float a[D1_RPT + 1];
+        if (!interior) d1_load_weights(wt, a);  // in flight together with the footprint loads
+        stage_footprint(foot, px_i, pitch_i, W, fx0, fy0, fw, fh);
+        if (t < D1_SY) rowdy[t] = (float)(fold101(vy0 + t, g.ny[0]) - ref.ay);
+        __syncthreads();
+        if (interior) d1_staged_samples<true>(s0, foot, rowdy, a, g, ref, vx0, fx0, fy0, fw, fh, W, H, scale);
+        else d1_staged_samples<false>(s0, foot, rowdy, a, g, ref, vx0, fx0, fy0, fw, fh, W, H, scale);
+        __syncthreads();  // the footprint is dead from here on
+    } else if (interior) {
+        for (int q = t; q < D1_NSAMP; q += D1_THREADS) {
             const int r = q / D1_SX, c = q % D1_SX;
             const int x = fold101(vx0 + c, g.nx[0]), y = fold101(vy0 + r, g.ny[0]);
             const Pos p = map_pos(ref.tm, fU0, fV0, (float)(x - ref.ax), (float)(y - ref.ay));
             const float3 v = sample_rgb_inside(px_i, pitch_i, p, scale);
             s0[s0_slot(r, c)] = make_float4(v.x, v.y, v.z, 1.f);
         }
-    } else
-    // S1 + S2 on the virtual level-0 region, two chunks of rows; cameras in the outer loop so
-    // each camera's constants are loaded once per chunk
-    for (int r0 = 0; r0 < D1_SY; r0 += D1_CHUNK_ROWS) {
-        const int nq = min(D1_CHUNK_ROWS, D1_SY - r0) * D1_SX;
-        float ws[D1_NS];
-        float4 val[D1_NS];
-#pragma unroll
-        for (int k = 0; k < D1_NS; ++k) {
-            ws[k] = 0.f;
-            val[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        for (int a = 0; a < na; ++a) {
-            const CamRef ref = refs[tl.first + a];
-            const CamDev& cj = cams[ref.cam];
-            const Rect V = cj.V;
-            const int W = cj.W, H = cj.H;
-            const float Wm = (float)W - 0.5f, Hm = (float)H - 0.5f;
-            const float fU0 = (float)ref.tm.U0, fV0 = (float)ref.tm.V0;
-            const bool self = a == tl.self;
-#pragma unroll
-            for (int k = 0; k < D1_NS; ++k) {
-                const int q = t + k * D1_THREADS;
-                if (q >= nq) break;
-                const int r = r0 + q / D1_SX, c = q % D1_SX;
+    } else {
+        for (int q = t; q < D1_NSAMP; q += D1_THREADS) {
+            const int r = q / D1_SX, c = q % D1_SX;
+            const float a = __ldg(wt + q);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a >= 0.f) {
                 const int x = fold101(vx0 + c, g.nx[0]), y = fold101(vy0 + r, g.ny[0]);
-                const bool inV = V.contains(x, y);
-                if (!(self || inV) || !o0.contains(x, y)) continue;
                 const Pos p = map_pos(ref.tm, fU0, fV0, (float)(x - ref.ax), (float)(y - ref.ay));
-                const float w = inV ? weight_of(p, Wm, Hm) : 0.f;
-                ws[k] += w;
-                if (self) {
-                    const float3 v = sample_rgb(px_i, pitch_i, p, W, H, scale);
-                    val[k] = make_float4(v.x, v.y, v.z, w);
-                }
+                const float3 s3 = sample_rgb(px_i, pitch_i, p, W, H, scale);
+                v = make_float4(s3.x, s3.y, s3.z, a);
             }
-        }
-#pragma unroll
-        for (int k = 0; k < D1_NS; ++k) {
-            const int q = t + k * D1_THREADS;
-            if (q >= nq) break;
-            float4 v = val[k];
-            v.w = ws[k] > 0.f ? __fdividef(v.w, ws[k]) : 0.f;
-            const int qq = r0 * D1_SX + q;
-            s0[s0_slot(qq / D1_SX, qq % D1_SX)] = v;
+            s0[s0_slot(r, c)] = v;
         }
     }
     __syncthreads();
@@ -239,9 +446,9 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
 template <typename T>
 __global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
                                                        OutDesc od, const D1Tile* __restrict__ tiles,
-                                                       const CamRef* __restrict__ refs) {
+                                                       const CamRef* __restrict__ refs, const float* __restrict__ d1w) {
     extern __shared__ float4 smem[];
-    down1_tile<T>(cams, g, fp, od, tiles[blockIdx.x], refs, smem);
+    down1_tile<T>(cams, g, fp, od, tiles[blockIdx.x], refs, d1w, smem);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1031,6 +1238,10 @@ struct FusedState {
     LevelTile* co_tiles[MAXL] = {};  // coarse tiles of level l (l >= 2)
     int n_co[MAXL] = {};
     int* camlist = nullptr;
+    float* d1w = nullptr;        // normalised level-0 weights of the non-INTERIOR down1 tiles
+    int n_wtab = 0;
+    D1Cams* d1_cams = nullptr;   // weight normalisation cameras of every down1 tile
+    int n_staged = 0;            // down1 tiles with a staged source footprint
     void* R[MAXL] = {};          // R^l on the canvas grid, l >= 2
     CamRef* refs = nullptr;
     UpTile* up_tiles[UP_KINDS] = {};
@@ -1103,13 +1314,58 @@ bool solidly_inside(const CamDev& c, const Rect& q, double m = 0.0) {
     return true;
 }
 
+// Source-pixel footprint of camera c over the level-0 rectangle q: every tap of a bilinear sample
+// of a point of q (after the image clamp of S1) lies in [fx0, fx0 + fw) x [fy0, fy0 + fh).  The
+// kernels' FP32 positions err by ~1e-5 px; the footprint allows 1e-3 px.  fx0 is a multiple of 4
+// and the footprint is at least 2 x 2 texels (grown inside the image where the rectangle maps
+// beyond an image border).  False when q is not entirely in front of the camera, maps beyond
+// |u|, |v| < 1e6, or the footprint (rows padded to 4 texels) exceeds the shared-memory capacity.
+bool d1_footprint(const CamDev& c, const Rect& q, int& fx0, int& fy0, int& fw, int& fh) {
+    if (c.W < 2 || c.H < 2) return false;
+    const double xs[2] = {(double)q.x0, (double)(q.x1 - 1)}, ys[2] = {(double)q.y0, (double)(q.y1 - 1)};
+    double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
+    for (double x : xs)
+        for (double y : ys) {
+            const double w = c.A[6] * x + c.A[7] * y + c.A[8];
+            if (!(w > 0.0)) return false;
+            const double u = (c.A[0] * x + c.A[1] * y + c.A[2]) / w, v = (c.A[3] * x + c.A[4] * y + c.A[5]) / w;
+            if (!(std::fabs(u) < 1e6 && std::fabs(v) < 1e6)) return false;
+            umin = std::min(umin, u);
+            umax = std::max(umax, u);
+            vmin = std::min(vmin, v);
+            vmax = std::max(vmax, v);
+        }
+    constexpr double eps = 1e-3;
+    int x0 = std::min(std::max((int)std::floor(umin - eps), 0), c.W - 1);
+    int x1 = std::min(std::max((int)std::floor(umax + eps) + 2, 1), c.W);
+    int y0 = std::min(std::max((int)std::floor(vmin - eps), 0), c.H - 1);
+    int y1 = std::min(std::max((int)std::floor(vmax + eps) + 2, 1), c.H);
+    if (x1 - x0 < 2) {
+        x0 = std::min(x0, c.W - 2);
+        x1 = x0 + 2;
+    }
+    if (y1 - y0 < 2) {
+        y0 = std::min(y0, c.H - 2);
+        y1 = y0 + 2;
+    }
+    x0 &= ~3;
+    if (x1 - x0 < 2 || y1 - y0 < 2 || (long long)((x1 - x0 + 3) & ~3) * (y1 - y0) > D1_FOOT || y0 > 0xffff ||
+        x0 > 0xffff)
+        return false;
+    fx0 = x0;
+    fy0 = y0;
+    fw = x1 - x0;
+    fh = y1 - y0;
+    return true;
+}
+
 template <typename T>
 stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, const OutDesc& od, cudaStream_t s) {
     const RigGeom& g = r->geom;
     const int L = g.levels;
     if (L >= 2 && fs->n_d1 > 0) {
         prof_mark(r, "fused_down1", s);
-        k_down1<T><<<fs->n_d1, D1_THREADS, D1_SMEM, s>>>(r->dcam, g, fp, od, fs->d1_tiles, fs->refs);
+        k_down1<T><<<fs->n_d1, D1_THREADS, D1_SMEM, s>>>(r->dcam, g, fp, od, fs->d1_tiles, fs->refs, fs->d1w);
     }
     for (int l = 1; l + 1 < L; ++l) {
         if (fs->n_red[l + 1] == 0) continue;
@@ -1168,6 +1424,7 @@ stitch_status fused_plan(stitch_rig* r) {
     const size_t elem = fs->fp16 ? sizeof(half4) : sizeof(float4);
     std::vector<CamRef> refs;
     std::vector<D1Tile> d1;
+    std::vector<D1Cams> d1c;
     std::vector<Tile> red[MAXL];
     for (int i = 0; i < g.ncam; ++i) {
         CamDev& c = r->hcam[i];
@@ -1185,18 +1442,28 @@ stitch_status fused_plan(stitch_rig* r) {
                     // level-0 bounding box of the tile's inputs
                     const int bx0 = std::max(2 * x - 2, 0), bx1 = std::min(2 * x - 2 + D1_SX, g.nx[0]);
                     const int by0 = std::max(2 * y - 2, 0), by1 = std::min(2 * y - 2 + D1_SY, g.ny[0]);
-                    D1Tile t{i, x, y, (int)refs.size(), 0, -1, 0, 0};
+                    D1Tile t{i, x, y, -1, -1, 0, 0, 0};
+                    D1Cams tc{(int)refs.size(), 0, -1, 0};
                     for (int j = 0; j < g.ncam; ++j) {
                         const CamDev& cj = r->hcam[j];
                         if (!cj.visible || (j != i && !rects_meet(cj.V, bx0, bx1, by0, by1))) continue;
-                        if (j == i) t.self = t.count;
+                        if (j == i) tc.self = tc.count;
                         refs.push_back(make_ref(cj, j, bx0, by0));
-                        ++t.count;
+                        ++tc.count;
                     }
+                    t.ref = tc.first + tc.self;
                     // interior: one camera, every input at least 0.01 px inside its image, so the
                     // weight is 1 and no coordinate needs clamping (FP32 positions err by ~1e-5 px)
-                    if (t.count == 1 && solidly_inside(c, Rect{bx0, bx1, by0, by1}, 0.01)) t.flags |= D1_INTERIOR;
+                    if (tc.count == 1 && solidly_inside(c, Rect{bx0, bx1, by0, by1}, 0.01)) t.flags |= D1_INTERIOR;
+                    t.wtab = (t.flags & D1_INTERIOR) ? -1 : fs->n_wtab++;
+                    int fx0, fy0, fw, fh;
+                    if (d1_footprint(c, Rect{bx0, bx1, by0, by1}, fx0, fy0, fw, fh)) {
+                        t.fxy = fx0 | (fy0 << 16);
+                        t.fwh = fw | (fh << 16);
+                        ++fs->n_staged;
+                    }
                     d1.push_back(t);
+                    d1c.push_back(tc);
                 }
         }
         for (int l = 2; l < L; ++l) {
@@ -1303,7 +1570,13 @@ stitch_status fused_plan(stitch_rig* r) {
     if (st != STITCH_OK) return st;
     st = upload(r, d1, &fs->d1_tiles);
     if (st != STITCH_OK) return st;
+    st = upload(r, d1c, &fs->d1_cams);
+    if (st != STITCH_OK) return st;
     fs->n_d1 = (int)d1.size();
+    if (fs->n_wtab > 0) {
+        fs->d1w = (float*)rig_alloc(r, sizeof(float) * D1_NSAMP * (size_t)fs->n_wtab);
+        if (!fs->d1w) return STITCH_ENOMEM;
+    }
     for (int l = 2; l < L; ++l) {
         st = upload(r, red[l], &fs->red_tiles[l]);
         if (st != STITCH_OK) return st;
@@ -1335,14 +1608,23 @@ stitch_status fused_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od
     return fs->fp16 ? launch_all<half4>(r, fs, fp, od, s) : launch_all<float4>(r, fs, fp, od, s);
 }
 
+stitch_status fused_precompute(stitch_rig* r) {
+    FusedState* fs = (FusedState*)r->fused;
+    if (!fs || fs->n_wtab == 0) return STITCH_OK;
+    k_d1_weights<<<fs->n_d1, D1_THREADS>>>(r->dcam, r->geom, fs->d1_tiles, fs->d1_cams, fs->refs, fs->d1w);
+    STITCH_CUDA_TRY(cudaGetLastError());
+    STITCH_CUDA_TRY(cudaDeviceSynchronize());
+    return STITCH_OK;
+}
+
 void fused_release(stitch_rig* r) {
     delete (FusedState*)r->fused;
     r->fused = nullptr;
 }
 
-void fused_tile_counts(const stitch_rig* r, int counts[6]) {
+void fused_tile_counts(const stitch_rig* r, int counts[8]) {
     const FusedState* fs = (const FusedState*)r->fused;
-    for (int k = 0; k < 6; ++k) counts[k] = 0;
+    for (int k = 0; k < 8; ++k) counts[k] = 0;
     if (!fs) return;
     counts[0] = fs->n_zero;
     counts[1] = fs->n_solo;
@@ -1350,6 +1632,8 @@ void fused_tile_counts(const stitch_rig* r, int counts[6]) {
     counts[3] = fs->n_up[UP_FULL4];
     counts[4] = fs->n_up[UP_GENERAL];
     counts[5] = fs->n_d1;
+    counts[6] = fs->n_staged;
+    counts[7] = fs->n_d1 - fs->n_wtab;
 }
 
 // ================================================================================================
@@ -1381,6 +1665,7 @@ struct BatchRigDev {
     const LevelTile* co[MAXL];
     const int* camlist;
     const CamRef* refs;
+    const float* d1w;
     const UpTile* up[UP_KINDS];
     void* R[MAXL];
 };
@@ -1478,7 +1763,7 @@ __global__ void __launch_bounds__(B_THREADS, MINB) k_batch(const BatchRigDev* __
             const T* R2 = rg.g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
             switch (tk.type) {
                 case BT_D1:
-                    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, smem);
+                    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, smem);
                     break;
                 case BT_RED:
                     reduce_tile<T>(rg.cams, rg.g, tk.level - 1, task_tile<Tile>(tk), smem);
@@ -1540,7 +1825,7 @@ __global__ void __launch_bounds__(D1_THREADS, 3) k_mr_down1(const BatchRigDev* _
     extern __shared__ float4 smem[];
     const BTask tk = tasks[blockIdx.x];
     const BatchRigDev& rg = rigs[tk.rig];
-    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, smem);
+    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, smem);
 }
 
 template <typename T>
@@ -1873,6 +2158,7 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
         }
         d.camlist = fs->camlist;
         d.refs = fs->refs;
+        d.d1w = fs->d1w;
         for (int q = 0; q < UP_KINDS; ++q) d.up[q] = fs->up_tiles[q];
         const int L = r->geom.levels;
         auto mk = [&](int type, int idx, int level, int st) {

@@ -236,6 +236,7 @@ stitch_status stitch_rig_create(const stitch_rig_desc* desc, int device, stitch_
     }
     if (st == STITCH_OK && cudaMemcpy(r->dcam, r->hcam, sizeof(CamDev) * g.ncam, cudaMemcpyHostToDevice) != cudaSuccess)
         st = STITCH_ECUDA;
+    if (st == STITCH_OK && desc->path != STITCH_PATH_PLAIN) st = fused_precompute(r);
     if (st != STITCH_OK) {
         fused_release(r);
         backward_release(r);
@@ -264,7 +265,7 @@ stitch_status stitch_rig_get_info(const stitch_rig* r, stitch_rig_info* info) {
     info->num_kernels = r->kernels_per_frame;
     info->path = r->desc.path;
     info->roi_pixels = r->roi_pixels;
-    int tc[6];
+    int tc[8];
     fused_tile_counts(r, tc);
     info->tiles_zero = tc[0];
     info->tiles_solo = tc[1];
@@ -272,6 +273,8 @@ stitch_status stitch_rig_get_info(const stitch_rig* r, stitch_rig_info* info) {
     info->tiles_full4 = tc[3];
     info->tiles_general = tc[4];
     info->tiles_down1 = tc[5];
+    info->tiles_down1_staged = tc[6];
+    info->tiles_down1_interior = tc[7];
     return STITCH_OK;
 }
 

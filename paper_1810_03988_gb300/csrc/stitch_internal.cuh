@@ -408,12 +408,13 @@ stitch_status plain_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od
 stitch_status fused_plan(stitch_rig* r);
 stitch_status fused_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od, cudaStream_t s);
 void fused_release(stitch_rig* r);
-void fused_tile_counts(const stitch_rig* r, int counts[6]);
+void fused_tile_counts(const stitch_rig* r, int counts[8]);
 stitch_status backward_plan(stitch_rig* r);
 stitch_status backward_run(stitch_rig* r, const FramePtrs& fp, const double* params, double* loss, double* grad,
                            cudaStream_t s);
 void backward_release(stitch_rig* r);
 void pipeline_release(stitch_rig* r);
+stitch_status fused_precompute(stitch_rig* r);  // geometry-only tables, after the camera upload
 stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out);
 stitch_status fused_batch_frames(void* b, const uint8_t* const* const* frames, const int64_t* const* pitches,
                                  void* const* outs, const int64_t* out_pitches, cudaStream_t s);

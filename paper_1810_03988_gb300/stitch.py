@@ -42,7 +42,8 @@ class stitch_rig_info(ctypes.Structure):
     _fields_ = [("scratch_bytes", ctypes.c_int64), ("num_kernels", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("roi_pixels", ctypes.c_int64), ("tiles_zero", ctypes.c_int32), ("tiles_solo", ctypes.c_int32),
                 ("tiles_full2", ctypes.c_int32), ("tiles_full4", ctypes.c_int32),
-                ("tiles_general", ctypes.c_int32), ("tiles_down1", ctypes.c_int32)]
+                ("tiles_general", ctypes.c_int32), ("tiles_down1", ctypes.c_int32),
+                ("tiles_down1_staged", ctypes.c_int32), ("tiles_down1_interior", ctypes.c_int32)]
 
 
 # every symbol declared by include/stitch.h, with its ctypes signature
@@ -372,7 +373,8 @@ class Rig:
         return {"scratch_bytes": i.scratch_bytes, "num_kernels": i.num_kernels, "path": i.path,
                 "roi_pixels": i.roi_pixels,
                 "tiles": {"zero": i.tiles_zero, "solo": i.tiles_solo, "full2": i.tiles_full2,
-                          "full4": i.tiles_full4, "general": i.tiles_general, "down1": i.tiles_down1}}
+                          "full4": i.tiles_full4, "general": i.tiles_general, "down1": i.tiles_down1,
+                          "down1_staged": i.tiles_down1_staged, "down1_interior": i.tiles_down1_interior}}
 
     def set_profiling(self, enable: bool):
         stitch_rig_set_profiling(self.handle, enable)

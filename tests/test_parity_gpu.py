@@ -252,6 +252,29 @@ def test_tile_classes_are_exercised():
     assert t["solo"] > 0 and t["full2"] > 0, t
 
 
+def test_down1_staged_and_unstaged_tiles():
+    """down1 stages a tile's source footprint in shared memory when it fits; a camera whose source
+    pixels are 2.5x denser than the canvas has footprints beyond the capacity and takes the
+    unstaged path.  One rig holds both kinds of tile; the canvas matches the oracle."""
+    from paper_1810_03988_gb300 import Rig
+    S = lambda s, tx, ty: np.array([[s, 0, tx], [0, s, ty], [0, 0, 1.0]])
+    cams = [Camera(400, 240, S(0.4, 10.3, 8.7)), Camera(400, 240, S(0.9, 150.2, 5.1))]
+    cfg = synth.RigConfig("mixed_density", cams, 520, 230, 4, 1, None)
+    rng = np.random.default_rng(11)
+    frames = [rng.integers(0, 256, (240, 400, 3), dtype=np.uint8) for _ in cams]
+    with Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels) as rig:
+        t = rig.info()["tiles"]
+    assert 0 < t["down1_staged"] < t["down1"], t
+    ref = oracle.forward(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h, cfg.levels)
+    for out_float in (True, False):
+        gpu_util.compare(gpu_util.run_gpu(cfg, frames, "fused", out_float), ref, out_float)
+    # every tile of the 8x4K rig is staged
+    cfg = synth.config_8x4k(frames=1)
+    with Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels) as rig:
+        t = rig.info()["tiles"]
+    assert t["down1_staged"] == t["down1"] and t["down1_interior"] > 0, t
+
+
 @pytest.mark.parametrize("cfg_name", ["2cam", "4x1080p_scaled", "8x4k_scaled"])
 def test_fp16_bands(cfg_name):
     """Pyramid data stored in FP16 between kernels (all arithmetic FP32): within 1e-3 of the oracle
