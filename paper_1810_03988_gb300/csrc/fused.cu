@@ -70,10 +70,12 @@ struct Tile {
     int cam, x0, y0, pad;
 };
 
-// A camera taking part in a tile, with its homography anchored near the tile (host-built).
+// A camera taking part in a tile, with its homography anchored near the tile (host-built).  For
+// the cameras blended at level 0 of a FULL canvas tile, g0 is the slot of the tile's level-0
+// samples written by the camera's down1 tile (-1 otherwise).
 struct CamRef {
     TileMap tm;
-    int cam, ax, ay, pad;
+    int cam, ax, ay, g0;
 };
 
 // down1 tile: camera, level-1 origin, the camera's CamRef anchored at the tile, the tile's block in
@@ -81,7 +83,7 @@ struct CamRef {
 // and the source-image footprint of its samples staged in shared memory (fx0 | fy0 << 16,
 // fw | fh << 16; fwh = 0 when the footprint does not fit and samples are read from the frame).
 struct D1Tile {
-    int cam, k0, j0, ref, wtab, flags, fxy, fwh;
+    int cam, k0, j0, ref, wtab, flags, fxy, fwh, g0;  // g0: slot of the level-0 samples (D1_G0_OUT)
 };
 
 // Cameras (CamRef range, in camera order) whose validity box meets a down1 tile's level-0 inputs,
@@ -91,6 +93,7 @@ struct D1Cams {
 };
 constexpr int D1_INTERIOR = 1;  // inputs solidly inside the camera, no other camera: weight 1
 constexpr int D1_SOLO_OUT = 2;  // the canvas tile under this tile is SOLO for this camera
+constexpr int D1_G0_OUT = 4;    // the canvas tile under this tile is FULL: write its level-0 samples
 
 // up tile: level-0 origin and the contributing cameras (CamRef range), in camera order.
 struct UpTile {
@@ -342,7 +345,7 @@ __device__ __forceinline__ void d1_staged_samples(float4* __restrict__ s0, const
 template <typename T>
 __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
                                            const OutDesc& od, const D1Tile& tl, const CamRef* __restrict__ refs,
-                                           const float* __restrict__ d1w, float4* smem) {
+                                           const float* __restrict__ d1w, T* __restrict__ g0buf, float4* smem) {
     float4* s0 = smem;                        // level 0 (virtual coordinates), see s0_slot
     float4* sh = smem + D1_S0_F4;             // [D1_SY][D1_TX] horizontally reduced (or the footprint)
 
@@ -416,6 +419,15 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
         }
         __syncthreads();
     }
+    if (tl.flags & D1_G0_OUT) {
+        // the FULL canvas tile under this tile blends this camera: its level-0 samples (value and
+        // normalised weight, at virtual offset 2) go to the tile's slot, read by up_full
+        T* dst = g0buf + (long long)tl.g0 * (4 * D1_TX * D1_TY);
+        for (int q = t; q < 4 * D1_TX * D1_TY; q += D1_THREADS) {
+            const int dx = q % (2 * D1_TX), dy = q / (2 * D1_TX);
+            st(dst + q, s0[s0_slot(dy + 2, dx + 2)]);
+        }
+    }
     // S3 horizontal pass: sh[r][p] = sum_m w(m) s0[r][2p + m]
     for (int q = t; q < D1_TX * D1_SY; q += D1_THREADS) {
         const int r = q / D1_TX, p = q - r * D1_TX;
@@ -446,9 +458,10 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
 template <typename T>
 __global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
                                                        OutDesc od, const D1Tile* __restrict__ tiles,
-                                                       const CamRef* __restrict__ refs, const float* __restrict__ d1w) {
+                                                       const CamRef* __restrict__ refs, const float* __restrict__ d1w,
+                                                       T* __restrict__ g0buf) {
     extern __shared__ float4 smem[];
-    down1_tile<T>(cams, g, fp, od, tiles[blockIdx.x], refs, d1w, smem);
+    down1_tile<T>(cams, g, fp, od, tiles[blockIdx.x], refs, d1w, g0buf, smem);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -784,7 +797,8 @@ struct UpCams {
 template <typename T, int NC>
 __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
                                              const OutDesc& od, const T* __restrict__ R2, const UpTile& tl,
-                                             const CamRef* __restrict__ refs, float4* usm) {
+                                             const CamRef* __restrict__ refs, const T* __restrict__ g0buf,
+                                             float4* usm) {
     float4* d1 = usm;                // [NC][U1_N]: G^1 of each camera, then R^1 - G^1
     float4* d2 = d1 + NC * U1_N;     // [NC][U2_N]: G^2 of each camera, then R^2 - G^2
     float4* r2s = d2 + NC * U2_N;    // [U2_N]: R^2
@@ -937,7 +951,9 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
         }
     }
     __syncthreads();
-    // level 0: R^0 = sum_i w_i (G^0_i + EXPAND(Delta^1_i)) / sum_i w_i on covered pixels
+    // level 0: R^0 = sum_i a_i (G^0_i + EXPAND(Delta^1_i)) / sum_i a_i on covered pixels, with the
+    // level-0 sample G^0_i and normalised weight a_i of every blended camera written by its down1
+    // tile (slot g0)
     for (int qd = t; qd < U_QUADS0; qd += U_THREADS) {
         const int qx = qd % (U_TX / 2), qy = qd / (U_TX / 2);
         float3 num[4];
@@ -948,25 +964,22 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
             den[k] = 0.f;
         }
         for (int c = 0; c < nc; ++c) {
-            float3 e[4] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f),
-                           make_float3(0.f, 0.f, 0.f)};
-            if (L >= 2) expand_quad(d1 + c * U1_N, U1_X, qx + 1, qy + 1, e);
-            const CamRef& r = cr[c];
-            const uint8_t* pxp = fp.p[r.cam];
-            const long long pitch = fp.pitch[r.cam];
-            const float fU0 = (float)r.tm.U0, fV0 = (float)r.tm.V0;
+            const int slot = cr[c].g0;
+            if (slot < 0) continue;
+            float3 e[4];
+            expand_quad(d1 + c * U1_N, U1_X, qx + 1, qy + 1, e);
+            const T* gq = g0buf + (long long)slot * (U_TX * U_TY) + (2 * qy) * U_TX + 2 * qx;
+            float4 gv[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) gv[k] = ld(gq + (k >> 1) * U_TX + (k & 1));
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
-                if (x >= X1 || y >= Y1 || !cv[c].contains(x, y)) continue;
-                const Pos ps = map_pos(r.tm, fU0, fV0, (float)(x - r.ax), (float)(y - r.ay));
-                const float w = weight_of(ps, cwm[c], chm[c]);
-                if (!(w > 0.f)) continue;
-                const float3 v = sample_rgb(pxp, pitch, ps, cwh[c][0], cwh[c][1], cscale[c]);
-                num[k].x = fmaf(w, v.x + e[k].x, num[k].x);
-                num[k].y = fmaf(w, v.y + e[k].y, num[k].y);
-                num[k].z = fmaf(w, v.z + e[k].z, num[k].z);
-                den[k] += w;
+                const float a = gv[k].w;
+                if (!(a > 0.f)) continue;
+                num[k].x = fmaf(a, gv[k].x + e[k].x, num[k].x);
+                num[k].y = fmaf(a, gv[k].y + e[k].y, num[k].y);
+                num[k].z = fmaf(a, gv[k].z + e[k].z, num[k].z);
+                den[k] += a;
             }
         }
 #pragma unroll
@@ -993,9 +1006,9 @@ template <typename T, int NC>
 __global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
                                                         OutDesc od, const T* __restrict__ R2,
                                                         const UpTile* __restrict__ tiles,
-                                                        const CamRef* __restrict__ refs) {
+                                                        const CamRef* __restrict__ refs, const T* __restrict__ g0buf) {
     extern __shared__ float4 usm[];
-    up_full_tile<T, NC>(cams, g, fp, od, R2, tiles[blockIdx.x], refs, usm);
+    up_full_tile<T, NC>(cams, g, fp, od, R2, tiles[blockIdx.x], refs, g0buf, usm);
 }
 
 template <int NC>
@@ -1241,6 +1254,8 @@ struct FusedState {
     float* d1w = nullptr;        // normalised level-0 weights of the non-INTERIOR down1 tiles
     int n_wtab = 0;
     D1Cams* d1_cams = nullptr;   // weight normalisation cameras of every down1 tile
+    void* g0buf = nullptr;       // level-0 samples of the FULL canvas tiles, one slot per camera
+    int n_g0 = 0;
     int n_staged = 0;            // down1 tiles with a staged source footprint
     void* R[MAXL] = {};          // R^l on the canvas grid, l >= 2
     CamRef* refs = nullptr;
@@ -1277,7 +1292,7 @@ CamRef make_ref(const CamDev& c, int cam, int X, int Y) {
     r.cam = cam;
     r.ax = ax;
     r.ay = ay;
-    r.pad = 0;
+    r.g0 = -1;
     return r;
 }
 
@@ -1365,7 +1380,8 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
     const int L = g.levels;
     if (L >= 2 && fs->n_d1 > 0) {
         prof_mark(r, "fused_down1", s);
-        k_down1<T><<<fs->n_d1, D1_THREADS, D1_SMEM, s>>>(r->dcam, g, fp, od, fs->d1_tiles, fs->refs, fs->d1w);
+        k_down1<T><<<fs->n_d1, D1_THREADS, D1_SMEM, s>>>(r->dcam, g, fp, od, fs->d1_tiles, fs->refs, fs->d1w,
+                                                         (T*)fs->g0buf);
     }
     for (int l = 1; l + 1 < L; ++l) {
         if (fs->n_red[l + 1] == 0) continue;
@@ -1386,12 +1402,14 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
     if (fs->n_up[UP_FULL2]) {
         prof_mark(r, "fused_up_full", s);
         k_up_full<T, 2><<<fs->n_up[UP_FULL2], U_THREADS, up_full_smem<2>(), s>>>(r->dcam, g, fp, od, R2,
-                                                                               fs->up_tiles[UP_FULL2], fs->refs);
+                                                                               fs->up_tiles[UP_FULL2], fs->refs,
+                                                                               (const T*)fs->g0buf);
     }
     if (fs->n_up[UP_FULL4]) {
         prof_mark(r, "fused_up_full4", s);
         k_up_full<T, 4><<<fs->n_up[UP_FULL4], U_THREADS, up_full_smem<4>(), s>>>(r->dcam, g, fp, od, R2,
-                                                                               fs->up_tiles[UP_FULL4], fs->refs);
+                                                                               fs->up_tiles[UP_FULL4], fs->refs,
+                                                                               (const T*)fs->g0buf);
     }
     if (fs->n_up[UP_GENERAL]) {
         prof_mark(r, "fused_up_general", s);
@@ -1442,7 +1460,7 @@ stitch_status fused_plan(stitch_rig* r) {
                     // level-0 bounding box of the tile's inputs
                     const int bx0 = std::max(2 * x - 2, 0), bx1 = std::min(2 * x - 2 + D1_SX, g.nx[0]);
                     const int by0 = std::max(2 * y - 2, 0), by1 = std::min(2 * y - 2 + D1_SY, g.ny[0]);
-                    D1Tile t{i, x, y, -1, -1, 0, 0, 0};
+                    D1Tile t{i, x, y, -1, -1, 0, 0, 0, -1};
                     D1Cams tc{(int)refs.size(), 0, -1, 0};
                     for (int j = 0; j < g.ncam; ++j) {
                         const CamDev& cj = r->hcam[j];
@@ -1550,10 +1568,27 @@ stitch_status fused_plan(stitch_rig* r) {
                             kind = -1;
                         }
                     }
-                } else if (t.count <= 2) {
-                    kind = UP_FULL2;
-                } else if (t.count <= 4) {
-                    kind = UP_FULL4;
+                } else if (t.count <= 4 && L >= 2) {
+                    // FULL: every camera blended at level 0 takes its level-0 samples (value and
+                    // normalised weight) from its down1 tile over this canvas tile
+                    kind = t.count <= 2 ? UP_FULL2 : UP_FULL4;
+                    size_t d1k[4];
+                    for (int k = 0; k < t.count && kind != UP_GENERAL; ++k) {
+                        const CamRef& rk = refs[t.first + k];
+                        d1k[k] = SIZE_MAX;
+                        if (!rects_meet(r->hcam[rk.cam].V, X0, X1, Y0, Y1)) continue;
+                        auto it = d1_index.find(((long long)rk.cam << 42) | ((long long)(X0 / 2) << 21) | (Y0 / 2));
+                        if (it == d1_index.end()) kind = UP_GENERAL;
+                        else d1k[k] = it->second;
+                    }
+                    if (kind != UP_GENERAL)
+                        for (int k = 0; k < t.count; ++k) {
+                            if (d1k[k] == SIZE_MAX) continue;
+                            D1Tile& dt = d1[d1k[k]];
+                            dt.g0 = fs->n_g0++;
+                            dt.flags |= D1_G0_OUT;
+                            refs[t.first + k].g0 = dt.g0;
+                        }
                 } else {
                     kind = UP_GENERAL;
                 }
@@ -1576,6 +1611,10 @@ stitch_status fused_plan(stitch_rig* r) {
     if (fs->n_wtab > 0) {
         fs->d1w = (float*)rig_alloc(r, sizeof(float) * D1_NSAMP * (size_t)fs->n_wtab);
         if (!fs->d1w) return STITCH_ENOMEM;
+    }
+    if (fs->n_g0 > 0) {
+        fs->g0buf = rig_alloc(r, elem * (size_t)U_TX * U_TY * fs->n_g0);
+        if (!fs->g0buf) return STITCH_ENOMEM;
     }
     for (int l = 2; l < L; ++l) {
         st = upload(r, red[l], &fs->red_tiles[l]);
@@ -1666,6 +1705,7 @@ struct BatchRigDev {
     const int* camlist;
     const CamRef* refs;
     const float* d1w;
+    void* g0buf;
     const UpTile* up[UP_KINDS];
     void* R[MAXL];
 };
@@ -1673,7 +1713,7 @@ struct BatchRigDev {
 // A task carries a copy of its tile record, so a block needs one load to start.
 struct BTask {
     int rig, type, idx, level, stage, pad0, pad1, pad2;
-    int tile[8];
+    int tile[12];
 };
 template <typename TL>
 __device__ __forceinline__ const TL& task_tile(const BTask& tk) {
@@ -1763,7 +1803,7 @@ __global__ void __launch_bounds__(B_THREADS, MINB) k_batch(const BatchRigDev* __
             const T* R2 = rg.g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
             switch (tk.type) {
                 case BT_D1:
-                    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, smem);
+                    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, (T*)rg.g0buf, smem);
                     break;
                 case BT_RED:
                     reduce_tile<T>(rg.cams, rg.g, tk.level - 1, task_tile<Tile>(tk), smem);
@@ -1778,10 +1818,10 @@ __global__ void __launch_bounds__(B_THREADS, MINB) k_batch(const BatchRigDev* __
                                    reinterpret_cast<unsigned char*>(smem));
                     break;
                 case BT_UPF2:
-                    up_full_tile<T, 2>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, smem);
+                    up_full_tile<T, 2>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, (const T*)rg.g0buf, smem);
                     break;
                 case BT_UPF4:
-                    up_full_tile<T, 4>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, smem);
+                    up_full_tile<T, 4>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, (const T*)rg.g0buf, smem);
                     break;
                 default:
                     break;
@@ -1825,7 +1865,7 @@ __global__ void __launch_bounds__(D1_THREADS, 3) k_mr_down1(const BatchRigDev* _
     extern __shared__ float4 smem[];
     const BTask tk = tasks[blockIdx.x];
     const BatchRigDev& rg = rigs[tk.rig];
-    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, smem);
+    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, (T*)rg.g0buf, smem);
 }
 
 template <typename T>
@@ -1861,7 +1901,7 @@ __global__ void __launch_bounds__(U_THREADS) k_mr_up_full(const BatchRigDev* __r
     const BTask tk = tasks[blockIdx.x];
     const BatchRigDev& rg = rigs[tk.rig];
     const T* R2 = rg.g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
-    up_full_tile<T, NC>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, usm);
+    up_full_tile<T, NC>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, (const T*)rg.g0buf, usm);
 }
 
 // A launch of the staged schedule: all tasks of one type and level, over every rig.
@@ -2159,6 +2199,7 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
         d.camlist = fs->camlist;
         d.refs = fs->refs;
         d.d1w = fs->d1w;
+        d.g0buf = fs->g0buf;
         for (int q = 0; q < UP_KINDS; ++q) d.up[q] = fs->up_tiles[q];
         const int L = r->geom.levels;
         auto mk = [&](int type, int idx, int level, int st) {
