@@ -471,13 +471,14 @@ __global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restric
 // staged in shared memory with coalesced loads.
 constexpr int RT_X = 32, RT_Y = 16;
 constexpr int RS_X = 2 * RT_X + 3, RS_Y = 2 * RT_Y + 3;
-constexpr size_t RT_SMEM = sizeof(float4) * (RS_X * RS_Y + RT_X * RS_Y);
+constexpr int RS_XH = (RS_X + 1) / 2;  // inputs stored as even and odd column planes
+constexpr size_t RT_SMEM = sizeof(float4) * (2 * RS_XH * RS_Y + RT_X * RS_Y);
 
 template <typename T>
 __device__ __forceinline__ void reduce_tile(const CamDev* __restrict__ cams, const RigGeom& g, int l, const Tile& tl,
                                             float4* smem) {
-    float4* s0 = smem;
-    float4* sh = smem + RS_X * RS_Y;
+    float4* s0 = smem;  // [RS_Y][2][RS_XH]: even columns, then odd columns, of each row
+    float4* sh = smem + 2 * RS_XH * RS_Y;
     const CamDev& c = cams[tl.cam];
     const Rect oc = c.Om[l + 1], of = c.Om[l];
     const int vx0 = 2 * tl.x0 - 2, vy0 = 2 * tl.y0 - 2;
@@ -500,16 +501,22 @@ __device__ __forceinline__ void reduce_tile(const CamDev* __restrict__ cams, con
 #pragma unroll
         for (int k = 0; k < NL; ++k) {
             const int q = threadIdx.x + 256 * k;
-            if (q < RS_X * RS_Y) s0[q] = v[k];
+            if (q < RS_X * RS_Y) {
+                const int r = q / RS_X, cc = q - r * RS_X;
+                s0[r * (2 * RS_XH) + (cc & 1) * RS_XH + (cc >> 1)] = v[k];
+            }
         }
     }
     __syncthreads();
     for (int q = threadIdx.x; q < RT_X * RS_Y; q += 256) {
         const int r = q / RT_X, p = q - r * RT_X;
-        const float4* row = s0 + r * RS_X + 2 * p;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int m = 0; m < 5; ++m) acc = f4fma(c_w5[m], row[m], acc);
+        const float4* ev = s0 + r * (2 * RS_XH) + p;  // columns 2p, 2p+2, 2p+4
+        const float4* od = ev + RS_XH;                // columns 2p+1, 2p+3
+        float4 acc = f4fma(c_w5[0], ev[0], make_float4(0.f, 0.f, 0.f, 0.f));
+        acc = f4fma(c_w5[1], od[0], acc);
+        acc = f4fma(c_w5[2], ev[1], acc);
+        acc = f4fma(c_w5[3], od[1], acc);
+        acc = f4fma(c_w5[4], ev[2], acc);
         sh[q] = acc;
     }
     __syncthreads();
@@ -526,7 +533,7 @@ __device__ __forceinline__ void reduce_tile(const CamDev* __restrict__ cams, con
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_reduce_t(const CamDev* __restrict__ cams, RigGeom g, int l,
+__global__ void __launch_bounds__(256) k_reduce_t(const CamDev* __restrict__ cams, const __grid_constant__ RigGeom g, int l,
                                                    const Tile* __restrict__ tiles) {
     extern __shared__ float4 smem[];
     reduce_tile<T>(cams, g, l, tiles[blockIdx.x], smem);
@@ -556,12 +563,12 @@ __device__ __forceinline__ void expand_quad(const float4* __restrict__ a, int ld
     e[3] = make_float3(0.5f * (ho[1].x + ho[2].x), 0.5f * (ho[1].y + ho[2].y), 0.5f * (ho[1].z + ho[2].z));
 }
 
-// Tiled coarse level: R^l on a 32 x 16 tile of level l (l >= 2), cameras in chunks of 4.
-// Virtual level-(l+1) region: origin (X0/2 - 2, Y0/2 - 2), 20 x 12.
-constexpr int CT_X = 32, CT_Y = 16, CT_NC = 2;
+// Tiled coarse level: R^l on a 32 x 32 tile of level l (l >= 2), one 2 x 2 quad per thread,
+// cameras in chunks of 2.  Virtual level-(l+1) region: origin (X0/2 - 2, Y0/2 - 2), 20 x 20.
+constexpr int CT_X = 32, CT_Y = 32, CT_NC = 2;
 constexpr int CC_X = CT_X / 2 + 4, CC_Y = CT_Y / 2 + 4;
 constexpr int CC_N = CC_X * CC_Y, CT_N = CT_X * CT_Y;
-constexpr int CT_QUADS = (CT_X / 2) * (CT_Y / 2);  // 128
+constexpr int CT_QUADS = (CT_X / 2) * (CT_Y / 2);  // 256
 constexpr int CT_SMEM_F4 = CC_N + CT_NC * CT_N + CT_NC * CC_N;  // shared memory in float4 units
 
 struct LevelTile {
@@ -680,17 +687,20 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
         const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
         if (x >= nxl || y >= nyl) continue;
         float4 r = make_float4(e[k].x, e[k].y, e[k].z, 0.f);
-        if (den[k] > 1e-12f) r = make_float4(num[k].x / den[k], num[k].y / den[k], num[k].z / den[k], 0.f);
+        if (den[k] > 1e-12f) {
+            const float rd = __frcp_rn(den[k]);  // one reciprocal, three products (within 1 ulp of division)
+            r = make_float4(num[k].x * rd, num[k].y * rd, num[k].z * rd, 0.f);
+        }
         st(Rl + (long long)y * nxl + x, r);
     }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_coarse_t(const CamDev* __restrict__ cams, RigGeom g, int l,
+__global__ void __launch_bounds__(256, 3) k_coarse_t(const CamDev* __restrict__ cams, const __grid_constant__ RigGeom g, int l,
                                                    T* __restrict__ Rl, const T* __restrict__ Rc,
                                                    const LevelTile* __restrict__ tiles,
                                                    const int* __restrict__ camlist) {
-    __shared__ float4 smem[CT_SMEM_F4];
+    extern __shared__ float4 smem[];
     coarse_tile<T>(cams, g, l, Rl, Rc, tiles[blockIdx.x], camlist, smem);
 }
 
@@ -929,7 +939,8 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (den[k] > 1e-12f) {
-                r1[k] = make_float3(num[k].x / den[k], num[k].y / den[k], num[k].z / den[k]);
+                const float rd = __frcp_rn(den[k]);
+                r1[k] = make_float3(num[k].x * rd, num[k].y * rd, num[k].z * rd);
             } else {
                 r1[k] = make_float3(0.f, 0.f, 0.f);
                 need_plain = true;
@@ -989,9 +1000,10 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
             if (x >= X1 || y >= Y1) continue;
             float rr = 0.f, gg = 0.f, bb = 0.f;
             if (den[k] > 0.f) {
-                rr = __saturatef(num[k].x / den[k]);
-                gg = __saturatef(num[k].y / den[k]);
-                bb = __saturatef(num[k].z / den[k]);
+                const float rd = __frcp_rn(den[k]);
+                rr = __saturatef(num[k].x * rd);
+                gg = __saturatef(num[k].y * rd);
+                bb = __saturatef(num[k].z * rd);
             }
             put_pixel(stage, od, dx, dy, x, y, rr, gg, bb);
         }
@@ -1390,7 +1402,7 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
     }
     for (int l = L - 1; l >= 2; --l) {
         prof_mark(r, "fused_coarse", s);
-        k_coarse_t<T><<<fs->n_co[l], 256, 0, s>>>(r->dcam, g, l, (T*)fs->R[l],
+        k_coarse_t<T><<<fs->n_co[l], 256, sizeof(float4) * CT_SMEM_F4, s>>>(r->dcam, g, l, (T*)fs->R[l],
                                                    l + 1 < L ? (const T*)fs->R[l + 1] : nullptr, fs->co_tiles[l],
                                                    fs->camlist);
     }
@@ -1423,6 +1435,8 @@ template <typename T>
 stitch_status set_smem_attrs() {
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_reduce_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_coarse_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float4) * CT_SMEM_F4)));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)up_full_smem<2>()));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1877,8 +1891,8 @@ __global__ void __launch_bounds__(256) k_mr_reduce(const BatchRigDev* __restrict
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_mr_coarse(const BatchRigDev* __restrict__ rigs, const BTask* __restrict__ tasks) {
-    __shared__ float4 smem[CT_SMEM_F4];
+__global__ void __launch_bounds__(256, 3) k_mr_coarse(const BatchRigDev* __restrict__ rigs, const BTask* __restrict__ tasks) {
+    extern __shared__ float4 smem[];
     const BTask tk = tasks[blockIdx.x];
     const BatchRigDev& rg = rigs[tk.rig];
     coarse_tile<T>(rg.cams, rg.g, tk.level, (T*)rg.R[tk.level],
@@ -1986,7 +2000,7 @@ stitch_status b_launch_staged(BatchState* b, cudaStream_t s) {
         switch (gr.type) {
             case BT_D1: k_mr_down1<T><<<gr.count, D1_THREADS, D1_SMEM, s>>>(b->d_rigs, gr.d_tasks); break;
             case BT_RED: k_mr_reduce<T><<<gr.count, 256, RT_SMEM, s>>>(b->d_rigs, gr.d_tasks); break;
-            case BT_CO: k_mr_coarse<T><<<gr.count, 256, 0, s>>>(b->d_rigs, gr.d_tasks); break;
+            case BT_CO: k_mr_coarse<T><<<gr.count, 256, sizeof(float4) * CT_SMEM_F4, s>>>(b->d_rigs, gr.d_tasks); break;
             case BT_UPS: k_mr_up_simple<<<gr.count, U_THREADS, 0, s>>>(b->d_rigs, gr.d_tasks); break;
             case BT_UPF2: k_mr_up_full<T, 2><<<gr.count, U_THREADS, up_full_smem<2>(), s>>>(b->d_rigs, gr.d_tasks); break;
             case BT_UPF4: k_mr_up_full<T, 4><<<gr.count, U_THREADS, up_full_smem<4>(), s>>>(b->d_rigs, gr.d_tasks); break;
@@ -2001,6 +2015,8 @@ template <typename T>
 stitch_status b_staged_attrs() {
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float4) * CT_SMEM_F4)));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_up_full<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)up_full_smem<2>()));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_up_full<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
