@@ -58,7 +58,7 @@ def _load():
             lib.oracle_expand.argtypes = [_P, _I, _I, _I, _I, _I, _P]
             lib.oracle_regions.argtypes = [_I, _I, _I, _I, _I, _I, _I, _P]
             lib.oracle_forward.argtypes = [_I, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _P, _P, _P,
-                                           _P, _P]
+                                           _P, _P, _I]
             lib.oracle_warp.argtypes = [_I, _I, _P, _D, _P, ctypes.c_int64, _I, _I, _P, _P]
             lib.oracle_loss_grad.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _P, _P]
             for f in ("oracle_invert_h", "oracle_reduce", "oracle_expand", "oracle_regions", "oracle_forward",
@@ -156,8 +156,12 @@ def regions(canvas_w: int, canvas_h: int, levels: int, window=None) -> np.ndarra
     return out
 
 
-def forward(cams, frames, canvas_w: int, canvas_h: int, levels: int, window=None, debug: bool = False):
+def forward(cams, frames, canvas_w: int, canvas_h: int, levels: int, window=None, debug: bool = False,
+            weights: str = "feather"):
     """Stitch one frame set (S1-S6) in double precision.
+
+    ``weights``: "feather" (normalised distance-to-border weights) or "seam" (binary masks: each
+    pixel owned by the camera with the largest feather weight, ties to the lower index).
 
     ``cams``: objects with ``width``, ``height``, ``H`` (camera->canvas 3x3) and ``gain``.
     ``window``: (x0, y0, w, h) output rectangle, default the whole canvas.
@@ -182,7 +186,7 @@ def forward(cams, frames, canvas_w: int, canvas_h: int, levels: int, window=None
         dB = (ctypes.c_void_p * levels)(*[a.ctypes.data for a in B])
     rc = lib.oracle_forward(n, Ws.ctypes.data, Hs.ctypes.data, Ms.ctypes.data, gains.ctypes.data, fp,
                             pitches.ctypes.data, canvas_w, canvas_h, levels, x0, y0, w, h, out.ctypes.data,
-                            u8.ctypes.data, md.ctypes.data, dS, dB)
+                            u8.ctypes.data, md.ctypes.data, dS, dB, {"feather": 0, "seam": 1}[weights])
     _check(rc, "forward")
     del keep
     res = {"out": out, "u8": u8, "mindist": md, "regions": reg}

@@ -20,7 +20,11 @@
  *             coordinates clamped to [0, W-1] x [0, H-1]; I_i = 0 where w <= 0.
  *             valid_i = w > 0 and -0.5 <= u < W-0.5 and -0.5 <= v < H-0.5.
  *  S2 weight: w_i = valid_i * max(0, min(u+0.5, v+0.5, W-0.5-u, H-0.5-v)),
- *             What_i = w_i / sum_j w_j where the sum is > 0, else 0.
+ *             What_i = w_i / sum_j w_j where the sum is > 0, else 0 (feather weights).
+ *             Seam weights (binary masks of the Burt-Adelson multiresolution spline, the
+ *             "multi band fusion" of Sec. 1): What_i = 1 for the owner of the pixel, the
+ *             lowest-index camera with w_i > 0 and w_i >= (1 - 1e-9) max_j w_j, 0 for the
+ *             others (no owner: all 0).
  *  S3 REDUCE: G^{l+1}(k, j) = sum_{m,n=-2..2} w(m) w(n) G^l(r(2k+m), r(2j+n)),
  *             w = [1,4,6,4,1]/16, r = reflect-101 on the finer grid, size ceil(n/2).
  *  S4 EXPAND: E(x, y) = sum_{k,j} 2w(x-2k) 2w(y-2j) G(r(k), r(j)), r = reflect-101
@@ -343,9 +347,9 @@ int oracle_regions(int Wc, int Hc, int L, int wx0, int wy0, int ww, int wh, int3
 int oracle_forward(int n, const int32_t* Ws, const int32_t* Hs, const double* Ms, const double* gains,
                    const uint8_t* const* frames, const int64_t* pitches, int Wc, int Hc, int L, int wx0,
                    int wy0, int ww, int wh, double* out, uint8_t* out_u8, double* mindist, double** dbg_S,
-                   double** dbg_B) {
+                   double** dbg_B, int seam) {
     if (n < 1 || n > 64 || L < 1 || L > 24 || Wc < 1 || Hc < 1 || ww < 1 || wh < 1 || wx0 < 0 || wy0 < 0 ||
-        wx0 + ww > Wc || wy0 + wh > Hc)
+        wx0 + ww > Wc || wy0 + wh > Hc || (seam != 0 && seam != 1))
         return OR_EINVAL;
     ocam cams[64];
     int rc = setup_cams(n, Ws, Hs, Ms, gains, frames, pitches, cams);
@@ -367,14 +371,23 @@ int oracle_forward(int n, const int32_t* Ws, const int32_t* Hs, const double* Ms
             goto done;
     if (limg_alloc(&wsum, Yx[0], Yy[0], 1)) goto done;
 
-    /* S2 denominator: sum of raw feather weights at level 0 */
+    /* S2 denominator: sum of raw feather weights at level 0; with seam weights, 1 + the index of
+     * the pixel's owner (0: none), so that the coverage test "> 0" of S6 reads both alike */
 #pragma omp parallel for schedule(static)
     for (int y = Yy[0].lo; y <= Yy[0].hi; ++y)
         for (int x = Yx[0].lo; x <= Yx[0].hi; ++x) {
-            double s = 0.0, rgb[3], wr;
+            double s = 0.0, rgb[3], wr, wv[64], wmax = 0.0;
             for (int i = 0; i < n; ++i) {
                 cam_sample(&cams[i], x, y, rgb, &wr, NULL);
                 s += wr;
+                wv[i] = wr;
+                if (wr > wmax) wmax = wr;
+            }
+            if (seam) {
+                int owner = -1;
+                for (int i = 0; i < n && owner < 0; ++i)
+                    if (wv[i] > 0.0 && wv[i] >= (1.0 - 1e-9) * wmax) owner = i;
+                s = (double)(owner + 1);
             }
             *limg_at(&wsum, x, y) = s;
         }
@@ -391,7 +404,8 @@ int oracle_forward(int n, const int32_t* Ws, const int32_t* Hs, const double* Ms
                 g[0] = rgb[0];
                 g[1] = rgb[1];
                 g[2] = rgb[2];
-                g[3] = s > 0.0 ? wr / s : 0.0;
+                if (seam) g[3] = (s == (double)(i + 1)) ? 1.0 : 0.0;
+                else g[3] = s > 0.0 ? wr / s : 0.0;
             }
         /* S3: Gaussian pyramids of image and weight */
         for (int l = 0; l + 1 < L; ++l) reduce_into(&G[l], nx[l], ny[l], &G[l + 1]);

@@ -394,3 +394,95 @@ def test_inverse_keeps_the_in_front_sign():
     _, wr = oracle.warp(cam, np.zeros((cam.height, cam.width, 3), np.uint8), cfg.canvas_w, cfg.canvas_h)
     assert (wr > 0).sum() > 0.5 * cam.width * cam.height
 
+
+
+# ---------------------------------------------------------------------------------------------
+# seam weights (binary masks of the multiresolution spline)
+
+
+def _owner_map(cams, frames, Wc, Hc):
+    """Owner of every canvas pixel from the cameras' raw feather weights (oracle.warp), with the
+    tie rule written out in NumPy: lowest index with w > 0 and w >= (1 - 1e-9) max w; -1: none."""
+    w = np.stack([oracle.warp(c, f, Wc, Hc)[1] for c, f in zip(cams, frames)])
+    wmax = w.max(axis=0)
+    ok = (w > 0) & (w >= (1 - 1e-9) * wmax[None])
+    own = np.where(ok.any(axis=0), ok.argmax(axis=0), -1)
+    return own, w
+
+
+def test_seam_single_level_is_hard_cut_to_the_owner():
+    """With one level there is no pyramid: each covered pixel is its owner camera's warped
+    sample, uncovered pixels are 0."""
+    cfg = synth.config_2cam(scale=0.2)
+    frames = cfg.frame(0)
+    r = oracle.forward(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h, 1, weights="seam")
+    own, _ = _owner_map(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h)
+    imgs = [oracle.warp(c, f, cfg.canvas_w, cfg.canvas_h)[0] for c, f in zip(cfg.cameras, frames)]
+    expect = np.zeros_like(r["out"])
+    for i, img in enumerate(imgs):
+        expect[own == i] = np.clip(img[own == i], 0, 1)
+    assert (own == 0).any() and (own == 1).any() and (own == -1).any()
+    np.testing.assert_allclose(r["out"], expect, atol=1e-15)
+
+
+def test_seam_ties_go_to_the_lower_camera():
+    """Two mirror-symmetric cameras: on the symmetry column both feather weights are equal, and
+    the pixel belongs to camera 0 (one level, so the output is the owner's sample)."""
+    Wc, Hc = 41, 16
+    ca = Camera(30, 16, _T(0, 0))    # covers x in [0, 30)
+    cb = Camera(30, 16, _T(11, 0))   # covers x in [11, 41); column 20 is equidistant
+    fa = np.full((16, 30, 3), 50, np.uint8)
+    fb = np.full((16, 30, 3), 150, np.uint8)
+    r = oracle.forward([ca, cb], [fa, fb], Wc, Hc, 1, weights="seam")
+    wa = oracle.warp(ca, fa, Wc, Hc)[1]
+    wb = oracle.warp(cb, fb, Wc, Hc)[1]
+    tie = (wa == wb) & (wa > 0)
+    assert tie[:, 20].all()
+    np.testing.assert_allclose(r["out"][tie], 50 / 255.0, atol=1e-15)
+    np.testing.assert_allclose(r["out"][(wa > wb)], 50 / 255.0, atol=1e-15)
+    np.testing.assert_allclose(r["out"][(wb > wa) & (wb > 0)], 150 / 255.0, atol=1e-15)
+
+
+def test_seam_weights_are_one_hot_and_blend_constants_exactly():
+    """S^0 = 1 on covered pixels (exactly one owner), S^l follows the REDUCE of the coverage, and
+    constant frames still blend to the constant (P4 holds for binary masks too)."""
+    cfg = synth.config_2cam(scale=0.2)
+    frames = cfg.frame(0)
+    L = 4
+    r = oracle.forward(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h, L, debug=True, weights="seam")
+    own, _ = _owner_map(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h)
+    covered = (own >= 0).astype(float)
+    g = dense_ref.gaussian(covered, L)
+    for l in range(L):
+        np.testing.assert_allclose(r["S"][l], g[l], atol=1e-13)
+    const = [np.full((c.height, c.width, 3), (90, 12, 240), np.uint8) for c in cfg.cameras]
+    rc = oracle.forward(cfg.cameras, const, cfg.canvas_w, cfg.canvas_h, L, weights="seam")
+    np.testing.assert_allclose(rc["out"][own >= 0], np.broadcast_to(np.array([90, 12, 240]) / 255.0,
+                                                                    rc["out"][own >= 0].shape), atol=1e-12)
+
+
+def test_seam_blend_of_two_constants_follows_the_mask_pyramid():
+    """Camera A constant a, camera B constant b, seam masks: out = E^{L-1}(G^{L-1}(M_A))(a - b) + b
+    with M_A the owner mask of A (dense-matrix operators), as for feather weights."""
+    Wc, Hc, L = 48, 20, 3
+    ca = Camera(30, 20, _T(0, 0))
+    cb = Camera(30, 20, _T(18, 0))
+    fa = np.full((20, 30, 3), 60, np.uint8)
+    fb = np.full((20, 30, 3), 220, np.uint8)
+    r = oracle.forward([ca, cb], [fa, fb], Wc, Hc, L, weights="seam")
+    own, _ = _owner_map([ca, cb], [fa, fb], Wc, Hc)
+    assert (own >= 0).all()
+    e = dense_ref.gaussian((own == 0).astype(float), L)[-1]
+    shapes = [dense_ref.gaussian(np.zeros((Hc, Wc)), L)[l].shape for l in range(L)]
+    for l in range(L - 2, -1, -1):
+        e = dense_ref.expand2d(e, shapes[l])
+    expect = e * (60 / 255.0) + (1 - e) * (220 / 255.0)
+    np.testing.assert_allclose(r["out"][:, :, 0], expect, atol=1e-12)
+
+
+def test_seam_and_feather_agree_for_one_camera():
+    cfg = synth.config_2cam(scale=0.2)
+    frames = cfg.frame(0)
+    a = oracle.forward(cfg.cameras[:1], frames[:1], cfg.canvas_w, cfg.canvas_h, 4)
+    b = oracle.forward(cfg.cameras[:1], frames[:1], cfg.canvas_w, cfg.canvas_h, 4, weights="seam")
+    assert np.array_equal(a["out"], b["out"])
