@@ -268,6 +268,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison run")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-band comparison run")
+    ap.add_argument("--no-seam", action="store_true", help="skip the seam-weight run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-per-rig comparison")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -380,6 +381,20 @@ def main():
         fp16 = {"value": world * mpix / (hms / 1e3), "ms_per_step": hms}
         hrig.close()
 
+    # seam weights (binary owner masks): the masks are decided in FP64 when the rig is created,
+    # the per-frame work is that of feather weights
+    seam = None
+    if not args.no_seam:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        srig = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, band_fp16=args.fp16_bands, path=args.path,
+                   device=local, weights="seam")
+        torch.cuda.synchronize()
+        create_ms = (time.perf_counter() - t0) * 1e3
+        sms, _ = timed(srig, out, max(3, min(args.steps, 10)), 3, False)
+        seam = {"value": world * mpix / (sms / 1e3), "ms_per_step": sms, "rig_create_ms": create_ms}
+        srig.close()
+
     # batching: 16 uneven rigs, one launch sequence per rig against one persistent launch
     batched = None
     if not args.no_batch:
@@ -428,6 +443,7 @@ def main():
                        "l2": "inputs larger than L2: each frame set is a distinct device buffer "
                              f"({cbytes / 1e6:.0f} MB compulsory traffic per step)"},
             "roofline": roof, "step_roofline": step_roof, "plain_path": plain, "fp16_bands": fp16,
+            "seam_weights": seam,
             "batched": batched, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk, "gpu_launches": info["num_kernels"] * args.steps,
             "rig": {"scratch_bytes": info["scratch_bytes"], "roi_pixels": info["roi_pixels"],

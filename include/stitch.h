@@ -61,6 +61,13 @@ typedef enum {
 #define STITCH_PATH_FUSED 0 /* fused kernels, pyramid levels kept on chip where they fit */
 #define STITCH_PATH_PLAIN 1 /* one kernel per step, FP32 intermediates in HBM (comparison path) */
 
+/* Level-0 blend weights (S2). FEATHER: w_i / sum_j w_j with w the distance to the image border.
+ * SEAM: binary masks of the multiresolution spline: 1 for the pixel's owner, the lowest-index
+ * camera whose feather weight is > 0 and >= (1 - 1e-9) times the largest, 0 for the others; the
+ * owner is decided in FP64 when the rig is created (the pyramids then blend across the seams). */
+#define STITCH_WEIGHTS_FEATHER 0
+#define STITCH_WEIGHTS_SEAM 1
+
 typedef struct {
     int32_t width, height; /* source frame size in pixels, >= 1 */
     double H[9];           /* camera->canvas homography, row-major, with m31 u + m32 v + m33 > 0 for
@@ -78,6 +85,7 @@ typedef struct {
                                      between kernels (all filtering and blending still FP32) */
     int32_t out_float;            /* 0: uint8 RGB output; 1: float RGB output in [0,1] */
     int32_t path;                 /* STITCH_PATH_FUSED or STITCH_PATH_PLAIN */
+    int32_t weights;              /* STITCH_WEIGHTS_FEATHER or STITCH_WEIGHTS_SEAM */
 } stitch_rig_desc;
 
 typedef struct stitch_rig stitch_rig; /* opaque, owned by the library */

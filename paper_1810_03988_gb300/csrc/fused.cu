@@ -146,6 +146,11 @@ __global__ void __launch_bounds__(D1_THREADS) k_d1_weights(const CamDev* __restr
             out[q] = -1.f;
             continue;
         }
+        if (g.seam) {
+            const int own = seam_owner(tc.count, [&](int k) -> const CamDev& { return cams[refs[tc.first + k].cam]; }, x, y);
+            out[q] = own == tc.self ? 1.f : 0.f;
+            continue;
+        }
         float ws = 0.f, wself = 0.f;
         for (int a = 0; a < tc.count; ++a) {
             const CamRef ref = refs[tc.first + a];
@@ -1087,13 +1092,19 @@ __device__ __forceinline__ void up_general_tile(const CamDev* __restrict__ cams,
     __syncthreads();
 
     float ws[UG_PPT];
+    int own[UG_PPT];  // seam weights: list position of the pixel's owner
     float4 n0[UG_PPT];
 #pragma unroll
     for (int k = 0; k < UG_PPT; ++k) {
         const int p = t + k * U_THREADS;
         const int x = X0 + (p & (U_TX - 1)), y = Y0 + p / U_TX;
         float s = 0.f;
-        if (x < X1 && y < Y1) {
+        own[k] = -1;
+        if (g.seam) {
+            if (x < X1 && y < Y1)
+                own[k] = seam_owner(na, [&](int m) -> const CamDev& { return cams[refs[tl.first + m].cam]; }, x, y);
+            s = own[k] >= 0 ? 1.f : 0.f;
+        } else if (x < X1 && y < Y1) {
             for (int a = 0; a < na; ++a) {
                 const CamRef cr = refs[tl.first + a];
                 const CamDev& c = cams[cr.cam];
@@ -1163,7 +1174,7 @@ __device__ __forceinline__ void up_general_tile(const CamDev* __restrict__ cams,
             const int x = X0 + dx, y = Y0 + dy;
             if (x >= X1 || y >= Y1 || !(ws[k] > 0.f) || !c.V.contains(x, y)) continue;
             const SrcPos sp = map_point(cr.tm, (float)(x - cr.ax), (float)(y - cr.ay));
-            const float w = feather_weight(sp, c.W, c.H);
+            const float w = g.seam ? (own[k] == a ? 1.f : 0.f) : feather_weight(sp, c.W, c.H);
             if (!(w > 0.f)) continue;
             const float what = w / ws[k];
             float3 v = bilinear_rgb(fp.p[i], fp.pitch[i], clamp_tap(sp, c.W, c.H), scale);

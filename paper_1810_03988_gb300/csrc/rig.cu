@@ -199,7 +199,8 @@ stitch_status stitch_rig_create(const stitch_rig_desc* desc, int device, stitch_
         desc->canvas_h < 1 || desc->levels < 1 || desc->levels > MAXL || desc->canvas_w > (1 << 28) ||
         desc->canvas_h > (1 << 28) || (desc->band_fp16 != 0 && desc->band_fp16 != 1) ||
         (desc->out_float != 0 && desc->out_float != 1) ||
-        (desc->path != STITCH_PATH_FUSED && desc->path != STITCH_PATH_PLAIN))
+        (desc->path != STITCH_PATH_FUSED && desc->path != STITCH_PATH_PLAIN) ||
+        (desc->weights != STITCH_WEIGHTS_FEATHER && desc->weights != STITCH_WEIGHTS_SEAM))
         return STITCH_EINVAL;
     if ((long long)desc->canvas_w * desc->canvas_h > (1LL << 31)) return STITCH_EINVAL;
     int ndev = 0;
@@ -219,6 +220,7 @@ stitch_status stitch_rig_create(const stitch_rig_desc* desc, int device, stitch_
     RigGeom& g = r->geom;
     g.ncam = desc->num_cameras;
     g.levels = desc->levels;
+    g.seam = desc->weights == STITCH_WEIGHTS_SEAM;
     g.nx[0] = desc->canvas_w;
     g.ny[0] = desc->canvas_h;
     for (int l = 1; l < g.levels; ++l) {

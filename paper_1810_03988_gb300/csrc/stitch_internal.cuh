@@ -43,6 +43,7 @@ struct CamDev {
 // Rig-wide sizes passed by value to kernels.
 struct RigGeom {
     int ncam, levels;
+    int seam;  // level-0 weights: 0 feather, 1 seam owner masks
     int nx[MAXL], ny[MAXL];  // canvas size of every level (nx[l+1] = ceil(nx[l] / 2))
 };
 
@@ -140,6 +141,39 @@ __device__ __forceinline__ float feather_weight(const SrcPos& s, int W, int H) {
     const float u = (float)s.iu + s.fu, v = (float)s.iv + s.fv;
     float m = fminf(fminf(u + 0.5f, v + 0.5f), fminf(((float)W - 0.5f) - u, ((float)H - 0.5f) - v));
     return fmaxf(m, 0.0f);
+}
+
+// S2 feather weight of camera c at canvas point (x, y) in FP64: distance from the source point to
+// the border of the pixel-edge rectangle [-0.5, W-0.5) x [-0.5, H-0.5), 0 outside it or behind
+// the camera.
+__host__ __device__ inline double feather_weight64(const CamDev& c, double x, double y) {
+    const double w = c.A[6] * x + c.A[7] * y + c.A[8];
+    if (!(w > 0.0)) return 0.0;
+    const double u = (c.A[0] * x + c.A[1] * y + c.A[2]) / w, v = (c.A[3] * x + c.A[4] * y + c.A[5]) / w;
+    if (!(u >= -0.5 && u < c.W - 0.5 && v >= -0.5 && v < c.H - 0.5)) return 0.0;
+    const double m = fmin(fmin(u + 0.5, v + 0.5), fmin(c.W - 0.5 - u, c.H - 0.5 - v));
+    return m > 0.0 ? m : 0.0;
+}
+
+// Seam owner of canvas point (x, y) among n cameras given in ascending camera order by cam_at(k)
+// (which must include every camera whose validity box contains the point): the first position k
+// whose feather weight is > 0 and >= (1 - 1e-9) times the largest, -1 when no weight is > 0.
+// Decided in FP64, so that the binary masks do not depend on the FP32 tile anchoring.
+template <class CamAt>
+__device__ inline int seam_owner(int n, const CamAt& cam_at, int x, int y) {
+    double wmax = 0.0;
+    for (int k = 0; k < n; ++k) {
+        const CamDev& c = cam_at(k);
+        if (c.V.contains(x, y)) wmax = fmax(wmax, feather_weight64(c, (double)x, (double)y));
+    }
+    if (!(wmax > 0.0)) return -1;
+    for (int k = 0; k < n; ++k) {
+        const CamDev& c = cam_at(k);
+        if (!c.V.contains(x, y)) continue;
+        const double w = feather_weight64(c, (double)x, (double)y);
+        if (w > 0.0 && w >= (1.0 - 1e-9) * wmax) return k;
+    }
+    return -1;
 }
 
 // Clamped texel coordinates and fractions of a bilinear sample.

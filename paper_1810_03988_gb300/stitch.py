@@ -21,6 +21,8 @@ STITCH_MAX_CAMERAS = 32
 STITCH_MAX_LEVELS = 12
 STITCH_PATH_FUSED = 0
 STITCH_PATH_PLAIN = 1
+STITCH_WEIGHTS_FEATHER = 0
+STITCH_WEIGHTS_SEAM = 1
 
 _P = ctypes.c_void_p
 _lock = threading.Lock()
@@ -35,7 +37,8 @@ class stitch_camera(ctypes.Structure):
 class stitch_rig_desc(ctypes.Structure):
     _fields_ = [("num_cameras", ctypes.c_int32), ("cameras", ctypes.POINTER(stitch_camera)),
                 ("canvas_w", ctypes.c_int32), ("canvas_h", ctypes.c_int32), ("levels", ctypes.c_int32),
-                ("band_fp16", ctypes.c_int32), ("out_float", ctypes.c_int32), ("path", ctypes.c_int32)]
+                ("band_fp16", ctypes.c_int32), ("out_float", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("weights", ctypes.c_int32)]
 
 
 class stitch_rig_info(ctypes.Structure):
@@ -240,8 +243,9 @@ def _stream_handle(stream) -> int:
 
 
 def make_desc(cameras, canvas_w: int, canvas_h: int, levels: int, band_fp16: bool = False, out_float: bool = False,
-              path: str = "fused"):
-    """Build a stitch_rig_desc from objects with width, height, H (3x3) and gain."""
+              path: str = "fused", weights: str = "feather"):
+    """Build a stitch_rig_desc from objects with width, height, H (3x3) and gain; ``weights`` is
+    "feather" or "seam"."""
     n = len(cameras)
     arr = (stitch_camera * n)()
     for k, c in enumerate(cameras):
@@ -253,7 +257,8 @@ def make_desc(cameras, canvas_w: int, canvas_h: int, levels: int, band_fp16: boo
         arr[k].gain = float(getattr(c, "gain", 1.0))
     desc = stitch_rig_desc(n, ctypes.cast(arr, ctypes.POINTER(stitch_camera)), int(canvas_w), int(canvas_h),
                            int(levels), int(bool(band_fp16)), int(bool(out_float)),
-                           STITCH_PATH_PLAIN if path == "plain" else STITCH_PATH_FUSED)
+                           STITCH_PATH_PLAIN if path == "plain" else STITCH_PATH_FUSED,
+                           {"feather": STITCH_WEIGHTS_FEATHER, "seam": STITCH_WEIGHTS_SEAM}[weights])
     return desc, arr
 
 
@@ -261,7 +266,7 @@ class Rig:
     """A created rig: cameras, canvas and pyramid depth fixed; frames stitched on the GPU."""
 
     def __init__(self, cameras, canvas_w: int, canvas_h: int, levels: int, band_fp16: bool = False,
-                 out_float: bool = False, path: str = "fused", device: int | None = None):
+                 out_float: bool = False, path: str = "fused", device: int | None = None, weights: str = "feather"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libstitch needs a CUDA GPU; no CPU fallback exists")
@@ -271,7 +276,8 @@ class Rig:
         self.out_float = bool(out_float)
         self.band_fp16 = bool(band_fp16)
         self.path = path
-        desc, keep = make_desc(self.cameras, canvas_w, canvas_h, levels, band_fp16, out_float, path)
+        self.weights = weights
+        desc, keep = make_desc(self.cameras, canvas_w, canvas_h, levels, band_fp16, out_float, path, weights)
         self.handle = stitch_rig_create(desc, self.device)
         del keep
 

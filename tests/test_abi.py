@@ -63,6 +63,7 @@ def test_create_rejects_bad_descriptors_without_a_device(lib):
     assert create(canvas_w=0) == stitch.STITCH_EINVAL
     assert create(out_float=2) == stitch.STITCH_EINVAL
     assert create(path=7) == stitch.STITCH_EINVAL
+    assert create(weights=2) == stitch.STITCH_EINVAL
     assert lib.stitch_rig_create(None, 0, ctypes.byref(out)) == stitch.STITCH_EINVAL
     assert out.value is None
     # destroy is NULL-safe
