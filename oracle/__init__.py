@@ -58,8 +58,8 @@ def _load():
             lib.oracle_expand.argtypes = [_P, _I, _I, _I, _I, _I, _P]
             lib.oracle_regions.argtypes = [_I, _I, _I, _I, _I, _I, _I, _P]
             lib.oracle_forward.argtypes = [_I, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _P, _P, _P,
-                                           _P, _P, _I]
-            lib.oracle_warp.argtypes = [_I, _I, _P, _D, _P, ctypes.c_int64, _I, _I, _P, _P]
+                                           _P, _P, _I, _P]
+            lib.oracle_warp.argtypes = [_I, _I, _P, _D, _P, ctypes.c_int64, _I, _I, _P, _P, _P]
             lib.oracle_loss_grad.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _P, _P]
             for f in ("oracle_invert_h", "oracle_reduce", "oracle_expand", "oracle_regions", "oracle_forward",
                       "oracle_warp", "oracle_loss_grad"):
@@ -156,12 +156,22 @@ def regions(canvas_w: int, canvas_h: int, levels: int, window=None) -> np.ndarra
     return out
 
 
+def _cyl_arg(canvas):
+    """None for the planar canvas, else a (f, cx, cy) double array for a cylindrical one."""
+    if canvas is None:
+        return None, None
+    arr = np.ascontiguousarray(np.asarray(canvas, dtype=np.float64).reshape(3))
+    return arr.ctypes.data, arr
+
+
 def forward(cams, frames, canvas_w: int, canvas_h: int, levels: int, window=None, debug: bool = False,
-            weights: str = "feather"):
+            weights: str = "feather", canvas=None):
     """Stitch one frame set (S1-S6) in double precision.
 
     ``weights``: "feather" (normalised distance-to-border weights) or "seam" (binary masks: each
     pixel owned by the camera with the largest feather weight, ties to the lower index).
+    ``canvas``: None (planar canvas; ``cam.H`` is camera->canvas) or (f, cx, cy) of a cylindrical
+    canvas (``cam.H`` is the camera's P = K R, applied to the canvas ray).
 
     ``cams``: objects with ``width``, ``height``, ``H`` (camera->canvas 3x3) and ``gain``.
     ``window``: (x0, y0, w, h) output rectangle, default the whole canvas.
@@ -184,9 +194,12 @@ def forward(cams, frames, canvas_w: int, canvas_h: int, levels: int, window=None
         B = [np.empty((r[3] - r[2], r[1] - r[0], 3)) for r in reg]
         dS = (ctypes.c_void_p * levels)(*[a.ctypes.data for a in S])
         dB = (ctypes.c_void_p * levels)(*[a.ctypes.data for a in B])
+    cyl_ptr, cyl_keep = _cyl_arg(canvas)
     rc = lib.oracle_forward(n, Ws.ctypes.data, Hs.ctypes.data, Ms.ctypes.data, gains.ctypes.data, fp,
                             pitches.ctypes.data, canvas_w, canvas_h, levels, x0, y0, w, h, out.ctypes.data,
-                            u8.ctypes.data, md.ctypes.data, dS, dB, {"feather": 0, "seam": 1}[weights])
+                            u8.ctypes.data, md.ctypes.data, dS, dB, {"feather": 0, "seam": 1}[weights],
+                            cyl_ptr)
+    del cyl_keep
     _check(rc, "forward")
     del keep
     res = {"out": out, "u8": u8, "mindist": md, "regions": reg}
@@ -196,15 +209,19 @@ def forward(cams, frames, canvas_w: int, canvas_h: int, levels: int, window=None
     return res
 
 
-def warp(cam, frame, canvas_w: int, canvas_h: int):
-    """Level 0 of one camera on the whole canvas: (I_i as HcxWcx3, raw feather weight HcxWc)."""
+def warp(cam, frame, canvas_w: int, canvas_h: int, canvas=None):
+    """Level 0 of one camera on the whole canvas: (I_i as HcxWcx3, raw feather weight HcxWc);
+    ``canvas`` as for forward."""
     lib = _load()
     frame = np.ascontiguousarray(frame, dtype=np.uint8)
     M = np.ascontiguousarray(np.asarray(cam.H, dtype=np.float64).reshape(9))
     img = np.empty((canvas_h, canvas_w, 3))
     wr = np.empty((canvas_h, canvas_w))
+    cyl_ptr, cyl_keep = _cyl_arg(canvas)
     rc = lib.oracle_warp(cam.width, cam.height, M.ctypes.data, float(getattr(cam, "gain", 1.0)),
-                         frame.ctypes.data, frame.strides[0], canvas_w, canvas_h, img.ctypes.data, wr.ctypes.data)
+                         frame.ctypes.data, frame.strides[0], canvas_w, canvas_h, img.ctypes.data, wr.ctypes.data,
+                         cyl_ptr)
+    del cyl_keep
     _check(rc, "warp")
     return img, wr
 

@@ -16,6 +16,9 @@
  *             tells points in front of the camera from points behind it, is kept; a33 = +-1).
  *             For canvas pixel (x, y):
  *             (nu, nv, w) = A_i (x, y, 1); u = nu/w, v = nv/w.
+ *             Cylindrical canvas (focal length f, centre (cx, cy); a canvas column is an angle):
+ *             the camera's 3x3 matrix P_i (= K_i R_i) is used as given, A_i = P_i, on the ray
+ *             (sin t, (y - cy)/f, cos t) with t = (x - cx)/f instead of (x, y, 1).
  *             I_i = gain_i * bilinear(frame_i, clamp(u), clamp(v)) / 255,
  *             coordinates clamped to [0, W-1] x [0, H-1]; I_i = 0 where w <= 0.
  *             valid_i = w > 0 and -0.5 <= u < W-0.5 and -0.5 <= v < H-0.5.
@@ -108,6 +111,8 @@ typedef struct {
     double gain;
     const uint8_t* px;
     int64_t pitch;
+    int cyl;             /* cylindrical canvas */
+    double cf, ccx, ccy; /* its focal length and centre */
 } ocam;
 
 static inline double texel(const ocam* c, int x, int y, int ch) {
@@ -118,9 +123,16 @@ static inline double texel(const ocam* c, int x, int y, int ch) {
  * *dist the distance (source px) to the border of the validity rectangle, or DBL_MAX when w<=0. */
 static void cam_sample(const ocam* c, double x, double y, double rgb[3], double* wraw, double* dist) {
     const double* A = c->A;
-    double nu = A[0] * x + A[1] * y + A[2];
-    double nv = A[3] * x + A[4] * y + A[5];
-    double w = A[6] * x + A[7] * y + A[8];
+    double X = x, Y = y, Z = 1.0;
+    if (c->cyl) {
+        const double t = (x - c->ccx) / c->cf;
+        X = sin(t);
+        Y = (y - c->ccy) / c->cf;
+        Z = cos(t);
+    }
+    double nu = A[0] * X + A[1] * Y + A[2] * Z;
+    double nv = A[3] * X + A[4] * Y + A[5] * Z;
+    double w = A[6] * X + A[7] * Y + A[8] * Z;
     if (!(w > 0.0)) {
         rgb[0] = rgb[1] = rgb[2] = 0.0;
         *wraw = 0.0;
@@ -281,13 +293,21 @@ int oracle_expand(const double* in, int wc, int hc, int ch, int w, int h, double
 /* ------------------------------------------------------------------------------------------ */
 /* forward                                                                                     */
 
+/* cyl: NULL for the planar canvas, else {f, cx, cy} of the cylindrical canvas (matrices are then
+ * the cameras' P = K R, used as given). */
 static int setup_cams(int n, const int32_t* Ws, const int32_t* Hs, const double* Ms, const double* gains,
-                      const uint8_t* const* frames, const int64_t* pitches, ocam* cams) {
+                      const uint8_t* const* frames, const int64_t* pitches, const double* cyl, ocam* cams) {
+    if (cyl && !(cyl[0] > 0.0)) return OR_EINVAL;
     for (int i = 0; i < n; ++i) {
         if (Ws[i] < 1 || Hs[i] < 1 || !frames[i] || pitches[i] < 3LL * Ws[i]) return OR_EINVAL;
         cams[i].W = Ws[i];
         cams[i].H = Hs[i];
-        if (oracle_invert_h(Ms + 9 * i, cams[i].A) != 0) return OR_EINVAL;
+        cams[i].cyl = cyl != NULL;
+        cams[i].cf = cyl ? cyl[0] : 0.0;
+        cams[i].ccx = cyl ? cyl[1] : 0.0;
+        cams[i].ccy = cyl ? cyl[2] : 0.0;
+        if (cyl) memcpy(cams[i].A, Ms + 9 * i, 9 * sizeof(double));
+        else if (oracle_invert_h(Ms + 9 * i, cams[i].A) != 0) return OR_EINVAL;
         cams[i].gain = gains ? gains[i] : 1.0;
         cams[i].px = frames[i];
         cams[i].pitch = pitches[i];
@@ -347,12 +367,12 @@ int oracle_regions(int Wc, int Hc, int L, int wx0, int wy0, int ww, int wh, int3
 int oracle_forward(int n, const int32_t* Ws, const int32_t* Hs, const double* Ms, const double* gains,
                    const uint8_t* const* frames, const int64_t* pitches, int Wc, int Hc, int L, int wx0,
                    int wy0, int ww, int wh, double* out, uint8_t* out_u8, double* mindist, double** dbg_S,
-                   double** dbg_B, int seam) {
+                   double** dbg_B, int seam, const double* cyl) {
     if (n < 1 || n > 64 || L < 1 || L > 24 || Wc < 1 || Hc < 1 || ww < 1 || wh < 1 || wx0 < 0 || wy0 < 0 ||
         wx0 + ww > Wc || wy0 + wh > Hc || (seam != 0 && seam != 1))
         return OR_EINVAL;
     ocam cams[64];
-    int rc = setup_cams(n, Ws, Hs, Ms, gains, frames, pitches, cams);
+    int rc = setup_cams(n, Ws, Hs, Ms, gains, frames, pitches, cyl, cams);
     if (rc) return rc;
 
     int nx[24], ny[24];
@@ -488,10 +508,10 @@ done:
  * img: Hc*Wc*3 doubles, wraw: Hc*Wc doubles (either may be NULL).
  */
 int oracle_warp(int W, int H, const double* M, double gain, const uint8_t* frame, int64_t pitch, int Wc,
-                int Hc, double* img, double* wraw) {
+                int Hc, double* img, double* wraw, const double* cyl) {
     ocam c;
     int32_t Ws = W, Hs = H;
-    if (setup_cams(1, &Ws, &Hs, M, &gain, &frame, &pitch, &c)) return OR_EINVAL;
+    if (setup_cams(1, &Ws, &Hs, M, &gain, &frame, &pitch, cyl, &c)) return OR_EINVAL;
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < Hc; ++y)
         for (int x = 0; x < Wc; ++x) {

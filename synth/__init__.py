@@ -63,6 +63,11 @@ def _load():
             lib.synth_render_view.argtypes = [
                 ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                 ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64]
+            lib.synth_render_view_cyl.restype = ctypes.c_int
+            lib.synth_render_view_cyl.argtypes = [
+                ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                ctypes.c_double, ctypes.c_void_p, ctypes.c_int64]
             lib.synth_render_scene.restype = ctypes.c_int
             lib.synth_render_scene.argtypes = [
                 ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
@@ -150,6 +155,29 @@ def _norm(M: np.ndarray) -> np.ndarray:
     return M / M[2, 2]
 
 
+def render_view_cyl(scene: Scene, P: np.ndarray, W: int, H: int, canvas, t: int = 0) -> np.ndarray:
+    """Render frame ``t`` of a camera with ray->camera matrix ``P`` (= K R) looking at a scene laid
+    on the cylindrical canvas ``canvas`` = (f, cx, cy), as HxWx3 uint8."""
+    lib = _load()
+    Pinv = np.ascontiguousarray(np.linalg.inv(np.asarray(P, dtype=np.float64)), dtype=np.float64).reshape(9)
+    out = np.empty((H, W, 3), dtype=np.uint8)
+    f, cx, cy = (float(v) for v in canvas)
+    rc = lib.synth_render_view_cyl(
+        ctypes.c_uint64(scene.seed & 0xFFFFFFFFFFFFFFFF), scene.lattice,
+        scene.rects.ctypes.data if len(scene.rects) else None, len(scene.rects), Pinv.ctypes.data, W, H, f, cx, cy,
+        scene.off_x - scene.shift_per_frame * t, scene.off_y, out.ctypes.data, W * 3)
+    if rc != 0:
+        raise RuntimeError(f"synth_render_view_cyl failed ({rc})")
+    return out
+
+
+def rig_cylindrical(W: int, H: int, f: float, yaws_deg) -> list[np.ndarray]:
+    """Ray->camera matrices P_i = K R_y(-yaw_i) of pinhole cameras rotating about the vertical axis
+    (for a cylindrical canvas, whose column angle increases with x)."""
+    K = _K(f, W, H)
+    return [K @ _Ry(-math.radians(a)) for a in yaws_deg]
+
+
 def rig_planar(W: int, H: int, f: float, yaws_deg, Wc: int, Hc: int) -> list[np.ndarray]:
     """Camera->canvas homographies of a rig of pinhole cameras rotating about the vertical axis,
     all projected onto one plane at focal length f, plane origin at the canvas centre."""
@@ -197,7 +225,14 @@ class RigConfig:
     scene: Scene
     extra: dict = field(default_factory=dict)
 
+    @property
+    def canvas(self):
+        """None for a planar canvas, else (f, cx, cy) of the cylindrical canvas."""
+        return self.extra.get("cylinder")
+
     def frame(self, t: int = 0) -> list[np.ndarray]:
+        if self.canvas is not None:
+            return [render_view_cyl(self.scene, c.H, c.width, c.height, self.canvas, t) for c in self.cameras]
         return [render_view(self.scene, c.H, c.width, c.height, t) for c in self.cameras]
 
     @property
@@ -227,6 +262,18 @@ def _scaled(v: float, s: float, odd: bool = False) -> int:
     if odd and r % 2 == 0:
         r += 1
     return r
+
+
+def config_cyl(scale: float = 1.0, seed: int = 0, frames: int = 1) -> RigConfig:
+    """Four 1280x720 cameras (f = 900) at yaws -45, -15, 15, 45 deg on a cylindrical canvas of focal
+    length 900: 2528x760, 5 levels; the scene translates 3 px per frame along the canvas."""
+    W, H = _scaled(1280, scale), _scaled(720, scale)
+    f = 900.0 * scale
+    Wc, Hc = _scaled(2528, scale, odd=scale != 1.0), _scaled(760, scale, odd=scale != 1.0)
+    canvas = (f, (Wc - 1) / 2.0, (Hc - 1) / 2.0)
+    Ps = rig_cylindrical(W, H, f, [-45.0, -15.0, 15.0, 45.0])
+    return RigConfig("cyl_4x720p", [Camera(W, H, P) for P in Ps], Wc, Hc, 5, frames,
+                     _scene_for(seed, Wc, Hc, frames, scale), {"cylinder": canvas})
 
 
 def config_2cam(scale: float = 1.0, seed: int = 0) -> RigConfig:

@@ -168,6 +168,43 @@ int synth_render_view(uint64_t seed, double lattice, const synth_rect* rects, in
     return bad ? -1 : 0;
 }
 
+/*
+ * Render one camera view of a scene laid on a cylindrical canvas (focal length f, centre
+ * (cx, cy)).  Pixel (u, v) of the view looks along the ray Pinv * (u, v, 1) = (X, Y, Z), which
+ * meets the canvas at x = cx + f atan2(X, Z), y = cy + f Y / hypot(X, Z); the scene is evaluated
+ * there, translated by (off_x, off_y).  Returns 0, or -1 when a ray points backwards (Z <= 0 and
+ * X = 0) so that its canvas column is undefined.
+ */
+int synth_render_view_cyl(uint64_t seed, double lattice, const synth_rect* rects, int n_rects,
+                          const double* Pinv, int W, int H, double f, double cx, double cy, double off_x,
+                          double off_y, uint8_t* out, int64_t pitch) {
+    rect_bins b;
+    memset(&b, 0, sizeof(b));
+    if (bins_build(rects, n_rects, 64.0, &b) != 0) return -2;
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (int v = 0; v < H; ++v) {
+        uint8_t* row = out + (int64_t)v * pitch;
+        for (int u = 0; u < W; ++u) {
+            double X = Pinv[0] * u + Pinv[1] * v + Pinv[2];
+            double Y = Pinv[3] * u + Pinv[4] * v + Pinv[5];
+            double Z = Pinv[6] * u + Pinv[7] * v + Pinv[8];
+            double r = hypot(X, Z);
+            if (!(r > 0.0)) { bad |= 1; row[3 * u] = row[3 * u + 1] = row[3 * u + 2] = 0; continue; }
+            double xs = cx + f * atan2(X, Z) + off_x, ys = cy + f * Y / r + off_y;
+            double c[3];
+            scene_eval(seed, lattice, rects, &b, xs, ys, c);
+            for (int k = 0; k < 3; ++k) {
+                double t = c[k] < 0.0 ? 0.0 : (c[k] > 1.0 ? 1.0 : c[k]);
+                row[3 * u + k] = (uint8_t)nearbyint(255.0 * t);
+            }
+        }
+    }
+    free(b.start);
+    free(b.idx);
+    return bad ? -1 : 0;
+}
+
 /* Render the scene itself on an axis-aligned grid (scene px), for inspection. */
 int synth_render_scene(uint64_t seed, double lattice, const synth_rect* rects, int n_rects,
                        double x0, double y0, int W, int H, uint8_t* out) {
