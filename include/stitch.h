@@ -68,6 +68,15 @@ typedef enum {
 #define STITCH_WEIGHTS_FEATHER 0
 #define STITCH_WEIGHTS_SEAM 1
 
+/* Canvas model. PLANAR: stitch_camera.H is the camera->canvas homography M (inverted by create).
+ * CYLINDRICAL: canvas column x is the angle t = (x - cx)/f about the vertical axis and row y the
+ * height (y - cy)/f on the unit cylinder; stitch_camera.H is then the camera's 3x3 matrix P
+ * (= K R, row-major) that takes the canvas ray (sin t, (y - cy)/f, cos t) to homogeneous source
+ * coordinates, used as given (w > 0 in front of the camera).  stitch_backward supports the
+ * planar canvas only. */
+#define STITCH_CANVAS_PLANAR 0
+#define STITCH_CANVAS_CYLINDRICAL 1
+
 typedef struct {
     int32_t width, height; /* source frame size in pixels, >= 1 */
     double H[9];           /* camera->canvas homography, row-major, with m31 u + m32 v + m33 > 0 for
@@ -86,6 +95,8 @@ typedef struct {
     int32_t out_float;            /* 0: uint8 RGB output; 1: float RGB output in [0,1] */
     int32_t path;                 /* STITCH_PATH_FUSED or STITCH_PATH_PLAIN */
     int32_t weights;              /* STITCH_WEIGHTS_FEATHER or STITCH_WEIGHTS_SEAM */
+    int32_t canvas_model;         /* STITCH_CANVAS_PLANAR or STITCH_CANVAS_CYLINDRICAL */
+    double cylinder[3];           /* cylindrical canvas: focal length f (> 0, px per radian), cx, cy */
 } stitch_rig_desc;
 
 typedef struct stitch_rig stitch_rig; /* opaque, owned by the library */

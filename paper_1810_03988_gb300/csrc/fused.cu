@@ -84,6 +84,7 @@ struct CamRef {
 // fw | fh << 16; fwh = 0 when the footprint does not fit and samples are read from the frame).
 struct D1Tile {
     int cam, k0, j0, ref, wtab, flags, fxy, fwh, g0;  // g0: slot of the level-0 samples (D1_G0_OUT)
+    int coltab;                                       // cylindrical canvas: the tile's column table
 };
 
 // Cameras (CamRef range, in camera order) whose validity box meets a down1 tile's level-0 inputs,
@@ -147,8 +148,20 @@ __global__ void __launch_bounds__(D1_THREADS) k_d1_weights(const CamDev* __restr
             continue;
         }
         if (g.seam) {
-            const int own = seam_owner(tc.count, [&](int k) -> const CamDev& { return cams[refs[tc.first + k].cam]; }, x, y);
+            const int own = seam_owner(g, tc.count, [&](int k) -> const CamDev& { return cams[refs[tc.first + k].cam]; }, x, y);
             out[q] = own == tc.self ? 1.f : 0.f;
+            continue;
+        }
+        if (g.cyl) {
+            double ws = 0.0, wself = 0.0;
+            for (int a = 0; a < tc.count; ++a) {
+                const CamDev& cj = cams[refs[tc.first + a].cam];
+                if (!cj.V.contains(x, y)) continue;
+                const double w = feather_weight64(cj, g, (double)x, (double)y);
+                ws += w;
+                if (a == tc.self) wself = w;
+            }
+            out[q] = ws > 0.0 ? (float)(wself / ws) : 0.f;
             continue;
         }
         float ws = 0.f, wself = 0.f;
@@ -312,9 +325,24 @@ __device__ __forceinline__ void d1_load_weights(const float* __restrict__ wt, fl
 template <bool INTERIOR>
 __device__ __forceinline__ void d1_staged_samples(float4* __restrict__ s0, const float* __restrict__ foot,
                                                   const float* __restrict__ rowdy, const float a[D1_RPT + 1],
-                                                  const RigGeom& g, const CamRef& ref, int vx0, int fx0, int fy0,
-                                                  int fw, int fh, int W, int H, float scale) {
+                                                  const RigGeom& g, const CamRef& ref, const float4* __restrict__ cols,
+                                                  int vx0, int fx0, int fy0, int fw, int fh, int W, int H, float scale) {
     const TileMap& tm = ref.tm;
+    // column terms: the anchored homography on the planar canvas, the column table on the
+    // cylindrical one
+    auto colterms = [&](int c, float& nuc, float& nvc, float& dqc) {
+        if (cols) {
+            const float4 cc = cols[c];
+            nuc = cc.x;
+            nvc = cc.y;
+            dqc = cc.z;
+        } else {
+            const float dx = (float)(fold101(vx0 + c, g.nx[0]) - ref.ax);
+            nuc = fmaf(tm.pu1, dx, tm.pu0);
+            nvc = fmaf(tm.pv1, dx, tm.pv0);
+            dqc = fmaf(tm.q1, dx, tm.q0);
+        }
+    };
     const int bu = tm.U0 - fx0, bv = tm.V0 - fy0;
     const int fw4 = (fw + 3) & ~3;
     const int t = threadIdx.x;
@@ -331,8 +359,8 @@ __device__ __forceinline__ void d1_staged_samples(float4* __restrict__ s0, const
     };
     {
         const int c = t & 63;
-        const float dx = (float)(fold101(vx0 + c, g.nx[0]) - ref.ax);
-        const float nuc = fmaf(tm.pu1, dx, tm.pu0), nvc = fmaf(tm.pv1, dx, tm.pv0), dqc = fmaf(tm.q1, dx, tm.q0);
+        float nuc, nvc, dqc;
+        colterms(c, nuc, nvc, dqc);
 #pragma unroll
         for (int k = 0; k < D1_RPT; ++k) {
             const int r = (t >> 6) + 4 * k;
@@ -341,16 +369,17 @@ __device__ __forceinline__ void d1_staged_samples(float4* __restrict__ s0, const
     }
     if (t < 3 * D1_SY) {
         const int c = 64 + t % 3, r = t / 3;
-        const float dx = (float)(fold101(vx0 + c, g.nx[0]) - ref.ax);
-        one(r, c, fmaf(tm.pu1, dx, tm.pu0), fmaf(tm.pv1, dx, tm.pv0), fmaf(tm.q1, dx, tm.q0),
-            INTERIOR ? 1.f : a[D1_RPT]);
+        float nuc, nvc, dqc;
+        colterms(c, nuc, nvc, dqc);
+        one(r, c, nuc, nvc, dqc, INTERIOR ? 1.f : a[D1_RPT]);
     }
 }
 
 template <typename T>
 __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
                                            const OutDesc& od, const D1Tile& tl, const CamRef* __restrict__ refs,
-                                           const float* __restrict__ d1w, T* __restrict__ g0buf, float4* smem) {
+                                           const float* __restrict__ d1w, const float4* __restrict__ d1cols,
+                                           T* __restrict__ g0buf, float4* smem) {
     float4* s0 = smem;                        // level 0 (virtual coordinates), see s0_slot
     float4* sh = smem + D1_S0_F4;             // [D1_SY][D1_TX] horizontally reduced (or the footprint)
 
@@ -369,6 +398,17 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
     const float fU0 = (float)ref.tm.U0, fV0 = (float)ref.tm.V0;
     const bool interior = tl.flags & D1_INTERIOR;
     const float* __restrict__ wt = d1w + (long long)max(tl.wtab, 0) * D1_NSAMP;
+    const float4* __restrict__ cols = g.cyl ? d1cols + (long long)tl.coltab * D1_SX : nullptr;
+    // position of virtual sample (r, c) for the paths that read taps from the frame
+    auto pos_of = [&](int r, int c) -> Pos {
+        const int y = fold101(vy0 + r, g.ny[0]);
+        if (cols) {
+            const float4 cc = cols[c];
+            return map_pos_col(ref.tm, fU0, fV0, cc.x, cc.y, cc.z, (float)(y - ref.ay));
+        }
+        const int x = fold101(vx0 + c, g.nx[0]);
+        return map_pos(ref.tm, fU0, fV0, (float)(x - ref.ax), (float)(y - ref.ay));
+    };
     if (tl.fwh != 0) {
         // S1 from the source footprint staged in shared memory (the footprint shares its space
         // with sh, which is written only after the samples are taken)
@@ -380,14 +420,13 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
         stage_footprint(foot, px_i, pitch_i, W, fx0, fy0, fw, fh);
         if (t < D1_SY) rowdy[t] = (float)(fold101(vy0 + t, g.ny[0]) - ref.ay);
         __syncthreads();
-        if (interior) d1_staged_samples<true>(s0, foot, rowdy, a, g, ref, vx0, fx0, fy0, fw, fh, W, H, scale);
-        else d1_staged_samples<false>(s0, foot, rowdy, a, g, ref, vx0, fx0, fy0, fw, fh, W, H, scale);
+        if (interior) d1_staged_samples<true>(s0, foot, rowdy, a, g, ref, cols, vx0, fx0, fy0, fw, fh, W, H, scale);
+        else d1_staged_samples<false>(s0, foot, rowdy, a, g, ref, cols, vx0, fx0, fy0, fw, fh, W, H, scale);
         __syncthreads();  // the footprint is dead from here on
     } else if (interior) {
         for (int q = t; q < D1_NSAMP; q += D1_THREADS) {
             const int r = q / D1_SX, c = q % D1_SX;
-            const int x = fold101(vx0 + c, g.nx[0]), y = fold101(vy0 + r, g.ny[0]);
-            const Pos p = map_pos(ref.tm, fU0, fV0, (float)(x - ref.ax), (float)(y - ref.ay));
+            const Pos p = pos_of(r, c);
             const float3 v = sample_rgb_inside(px_i, pitch_i, p, scale);
             s0[s0_slot(r, c)] = make_float4(v.x, v.y, v.z, 1.f);
         }
@@ -397,8 +436,7 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
             const float a = __ldg(wt + q);
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (a >= 0.f) {
-                const int x = fold101(vx0 + c, g.nx[0]), y = fold101(vy0 + r, g.ny[0]);
-                const Pos p = map_pos(ref.tm, fU0, fV0, (float)(x - ref.ax), (float)(y - ref.ay));
+                const Pos p = pos_of(r, c);
                 const float3 s3 = sample_rgb(px_i, pitch_i, p, W, H, scale);
                 v = make_float4(s3.x, s3.y, s3.z, a);
             }
@@ -464,9 +502,9 @@ template <typename T>
 __global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
                                                        OutDesc od, const D1Tile* __restrict__ tiles,
                                                        const CamRef* __restrict__ refs, const float* __restrict__ d1w,
-                                                       T* __restrict__ g0buf) {
+                                                       const float4* __restrict__ d1cols, T* __restrict__ g0buf) {
     extern __shared__ float4 smem[];
-    down1_tile<T>(cams, g, fp, od, tiles[blockIdx.x], refs, d1w, g0buf, smem);
+    down1_tile<T>(cams, g, fp, od, tiles[blockIdx.x], refs, d1w, d1cols, g0buf, smem);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -781,7 +819,7 @@ __device__ __forceinline__ void up_simple_tile(const CamDev* __restrict__ cams, 
             const int dx = p % U_TX, dy = p / U_TX;
             const int x = X0 + dx, y = Y0 + dy;
             if (x >= X1 || y >= Y1) continue;
-            const Pos ps = map_pos(cr.tm, fU0, fV0, (float)(x - cr.ax), (float)(y - cr.ay));
+            const Pos ps = g.cyl ? map_pos64(c, g, x, y) : map_pos(cr.tm, fU0, fV0, (float)(x - cr.ax), (float)(y - cr.ay));
             const float3 v = sample_rgb(px, pitch, ps, W, H, scale);
             put_pixel(stage, od, dx, dy, x, y, __saturatef(v.x), __saturatef(v.y), __saturatef(v.z));
         }
@@ -1102,14 +1140,14 @@ __device__ __forceinline__ void up_general_tile(const CamDev* __restrict__ cams,
         own[k] = -1;
         if (g.seam) {
             if (x < X1 && y < Y1)
-                own[k] = seam_owner(na, [&](int m) -> const CamDev& { return cams[refs[tl.first + m].cam]; }, x, y);
+                own[k] = seam_owner(g, na, [&](int m) -> const CamDev& { return cams[refs[tl.first + m].cam]; }, x, y);
             s = own[k] >= 0 ? 1.f : 0.f;
         } else if (x < X1 && y < Y1) {
             for (int a = 0; a < na; ++a) {
                 const CamRef cr = refs[tl.first + a];
                 const CamDev& c = cams[cr.cam];
                 if (!c.V.contains(x, y)) continue;
-                const SrcPos sp = map_point(cr.tm, (float)(x - cr.ax), (float)(y - cr.ay));
+                const SrcPos sp = g.cyl ? map_point64(c, g, x, y) : map_point(cr.tm, (float)(x - cr.ax), (float)(y - cr.ay));
                 s += feather_weight(sp, c.W, c.H);
             }
         }
@@ -1173,7 +1211,7 @@ __device__ __forceinline__ void up_general_tile(const CamDev* __restrict__ cams,
             const int dx = p & (U_TX - 1), dy = p / U_TX;
             const int x = X0 + dx, y = Y0 + dy;
             if (x >= X1 || y >= Y1 || !(ws[k] > 0.f) || !c.V.contains(x, y)) continue;
-            const SrcPos sp = map_point(cr.tm, (float)(x - cr.ax), (float)(y - cr.ay));
+            const SrcPos sp = g.cyl ? map_point64(c, g, x, y) : map_point(cr.tm, (float)(x - cr.ax), (float)(y - cr.ay));
             const float w = g.seam ? (own[k] == a ? 1.f : 0.f) : feather_weight(sp, c.W, c.H);
             if (!(w > 0.f)) continue;
             const float what = w / ws[k];
@@ -1277,6 +1315,7 @@ struct FusedState {
     float* d1w = nullptr;        // normalised level-0 weights of the non-INTERIOR down1 tiles
     int n_wtab = 0;
     D1Cams* d1_cams = nullptr;   // weight normalisation cameras of every down1 tile
+    float4* d1cols = nullptr;    // cylindrical canvas: column terms of every down1 tile
     void* g0buf = nullptr;       // level-0 samples of the FULL canvas tiles, one slot per camera
     int n_g0 = 0;
     int n_staged = 0;            // down1 tiles with a staged source footprint
@@ -1307,16 +1346,50 @@ bool rects_meet(const Rect& a, int x0, int x1, int y0, int y1) {
     return !a.empty() && a.x0 < x1 && a.x1 > x0 && a.y0 < y1 && a.y1 > y0;
 }
 
-CamRef make_ref(const CamDev& c, int cam, int X, int Y) {
+// A camera's reference for a tile.  Planar canvas: the homography anchored at the tile.
+// Cylindrical canvas: U0, V0 at the anchor and the per-row slopes of the anchored numerators and
+// denominator (they are affine in the canvas row on every column); the column terms come from the
+// tile's column table (cyl_columns), or from the FP64 map on the paths that are not hot.
+CamRef make_ref(const CamDev& c, const RigGeom& g, int cam, int X, int Y) {
     CamRef r;
     int ax, ay;
     tile_anchor(c.V, X, Y, &ax, &ay);
-    r.tm = make_tile_map(c.A, ax, ay);
+    if (g.cyl) {
+        double u, v;
+        source_point64(c, g, (double)ax, (double)ay, &u, &v);
+        u = std::fmin(std::fmax(u, -1.0e8), 1.0e8);
+        v = std::fmin(std::fmax(v, -1.0e8), 1.0e8);
+        const double U = std::rint(u), V = std::rint(v);
+        TileMap t{};
+        t.U0 = (int)U;
+        t.V0 = (int)V;
+        t.pu2 = (float)((c.A[1] - U * c.A[7]) / g.cf);
+        t.pv2 = (float)((c.A[4] - V * c.A[7]) / g.cf);
+        t.q2 = (float)(c.A[7] / g.cf);
+        r.tm = t;
+    } else {
+        r.tm = make_tile_map(c.A, ax, ay);
+    }
     r.cam = cam;
     r.ax = ax;
     r.ay = ay;
     r.g0 = -1;
     return r;
+}
+
+// Column terms of a down1 tile on the cylindrical canvas: for virtual column k (canvas column
+// x = fold(vx0 + k)) the anchored numerators and denominator at the anchor row, in FP64, so that
+// a sample at row dy = y - ay is (col.x + pu2 dy, col.y + pv2 dy) / (col.z + q2 dy).
+void cyl_columns(const CamDev& c, const RigGeom& g, const CamRef& r, int vx0, float4* out) {
+    const double py = ((double)r.ay - g.ccy) / g.cf;
+    for (int k = 0; k < D1_SX; ++k) {
+        const double x = (double)fold101(vx0 + k, g.nx[0]);
+        const double t = (x - g.ccx) / g.cf, sx = std::sin(t), cx = std::cos(t);
+        const double nu = c.A[0] * sx + c.A[1] * py + c.A[2] * cx;
+        const double nv = c.A[3] * sx + c.A[4] * py + c.A[5] * cx;
+        const double w = c.A[6] * sx + c.A[7] * py + c.A[8] * cx;
+        out[k] = make_float4((float)(nu - r.tm.U0 * w), (float)(nv - r.tm.V0 * w), (float)w, 0.f);
+    }
 }
 
 // Level-0 rectangle on which the outputs of tile [x0,x1) x [y0,y1) depend (pyramid cone).
@@ -1337,19 +1410,39 @@ Rect cone_level0(const RigGeom& g, int x0, int x1, int y0, int y1) {
     return make_rect(yx, yy);
 }
 
-// Camera c maps every pixel of rect q into [m, W-1-m] x [m, H-1-m] of its image (the image of a
-// rectangle under a homography in front of the camera is convex, so its corners decide).  With
-// m = 0 the feather weight is >= 0.5 everywhere; with m > 0 no sample needs coordinate clamping.
-bool solidly_inside(const CamDev& c, const Rect& q, double m = 0.0) {
-    const double xs[2] = {(double)q.x0, (double)(q.x1 - 1)}, ys[2] = {(double)q.y0, (double)(q.y1 - 1)};
-    for (double x : xs)
-        for (double y : ys) {
-            const double w = c.A[6] * x + c.A[7] * y + c.A[8];
-            if (!(w > 0.0)) return false;
-            const double u = (c.A[0] * x + c.A[1] * y + c.A[2]) / w, v = (c.A[3] * x + c.A[4] * y + c.A[5]) / w;
-            if (!(u >= m && u <= c.W - 1.0 - m && v >= m && v <= c.H - 1.0 - m)) return false;
+// Range of source coordinates of camera c over the pixels of rect q; false when some pixel is not
+// in front of the camera or maps beyond |u|, |v| < 1e6.  Planar canvas: the image of a rectangle
+// under a homography in front of the camera is convex, so its corners decide.  Cylindrical
+// canvas: on every column u, v are Moebius functions of the row (monotonic where w > 0) and w is
+// affine in it, so the top and bottom rows of every column decide.
+bool source_range(const CamDev& c, const RigGeom& g, const Rect& q, double* umin, double* umax, double* vmin,
+                  double* vmax) {
+    *umin = *vmin = 1e300;
+    *umax = *vmax = -1e300;
+    const double ys[2] = {(double)q.y0, (double)(q.y1 - 1)};
+    const int step = g.cyl ? 1 : std::max(1, q.x1 - 1 - q.x0);
+    for (int xi = q.x0; xi < q.x1; xi += step)
+        for (int pass = 0; pass < 2; ++pass) {
+            const double x = pass == 0 ? (double)xi : (double)(q.x1 - 1);
+            for (double y : ys) {
+                double u, v;
+                if (!(source_point64(c, g, x, y, &u, &v) > 0.0)) return false;
+                if (!(std::fabs(u) < 1e6 && std::fabs(v) < 1e6)) return false;
+                *umin = std::min(*umin, u);
+                *umax = std::max(*umax, u);
+                *vmin = std::min(*vmin, v);
+                *vmax = std::max(*vmax, v);
+            }
         }
     return true;
+}
+
+// Camera c maps every pixel of rect q into [m, W-1-m] x [m, H-1-m] of its image.  With m = 0 the
+// feather weight is >= 0.5 everywhere; with m > 0 no sample needs coordinate clamping.
+bool solidly_inside(const CamDev& c, const RigGeom& g, const Rect& q, double m = 0.0) {
+    double umin, umax, vmin, vmax;
+    if (!source_range(c, g, q, &umin, &umax, &vmin, &vmax)) return false;
+    return umin >= m && umax <= c.W - 1.0 - m && vmin >= m && vmax <= c.H - 1.0 - m;
 }
 
 // Source-pixel footprint of camera c over the level-0 rectangle q: every tap of a bilinear sample
@@ -1358,21 +1451,10 @@ bool solidly_inside(const CamDev& c, const Rect& q, double m = 0.0) {
 // and the footprint is at least 2 x 2 texels (grown inside the image where the rectangle maps
 // beyond an image border).  False when q is not entirely in front of the camera, maps beyond
 // |u|, |v| < 1e6, or the footprint (rows padded to 4 texels) exceeds the shared-memory capacity.
-bool d1_footprint(const CamDev& c, const Rect& q, int& fx0, int& fy0, int& fw, int& fh) {
+bool d1_footprint(const CamDev& c, const RigGeom& g, const Rect& q, int& fx0, int& fy0, int& fw, int& fh) {
     if (c.W < 2 || c.H < 2) return false;
-    const double xs[2] = {(double)q.x0, (double)(q.x1 - 1)}, ys[2] = {(double)q.y0, (double)(q.y1 - 1)};
-    double umin = 1e300, umax = -1e300, vmin = 1e300, vmax = -1e300;
-    for (double x : xs)
-        for (double y : ys) {
-            const double w = c.A[6] * x + c.A[7] * y + c.A[8];
-            if (!(w > 0.0)) return false;
-            const double u = (c.A[0] * x + c.A[1] * y + c.A[2]) / w, v = (c.A[3] * x + c.A[4] * y + c.A[5]) / w;
-            if (!(std::fabs(u) < 1e6 && std::fabs(v) < 1e6)) return false;
-            umin = std::min(umin, u);
-            umax = std::max(umax, u);
-            vmin = std::min(vmin, v);
-            vmax = std::max(vmax, v);
-        }
+    double umin, umax, vmin, vmax;
+    if (!source_range(c, g, q, &umin, &umax, &vmin, &vmax)) return false;
     constexpr double eps = 1e-3;
     int x0 = std::min(std::max((int)std::floor(umin - eps), 0), c.W - 1);
     int x1 = std::min(std::max((int)std::floor(umax + eps) + 2, 1), c.W);
@@ -1404,7 +1486,7 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
     if (L >= 2 && fs->n_d1 > 0) {
         prof_mark(r, "fused_down1", s);
         k_down1<T><<<fs->n_d1, D1_THREADS, D1_SMEM, s>>>(r->dcam, g, fp, od, fs->d1_tiles, fs->refs, fs->d1w,
-                                                         (T*)fs->g0buf);
+                                                         fs->d1cols, (T*)fs->g0buf);
     }
     for (int l = 1; l + 1 < L; ++l) {
         if (fs->n_red[l + 1] == 0) continue;
@@ -1468,6 +1550,7 @@ stitch_status fused_plan(stitch_rig* r) {
     std::vector<CamRef> refs;
     std::vector<D1Tile> d1;
     std::vector<D1Cams> d1c;
+    std::vector<float4> cols;  // cylindrical canvas: D1_SX column terms per down1 tile
     std::vector<Tile> red[MAXL];
     for (int i = 0; i < g.ncam; ++i) {
         CamDev& c = r->hcam[i];
@@ -1485,22 +1568,27 @@ stitch_status fused_plan(stitch_rig* r) {
                     // level-0 bounding box of the tile's inputs
                     const int bx0 = std::max(2 * x - 2, 0), bx1 = std::min(2 * x - 2 + D1_SX, g.nx[0]);
                     const int by0 = std::max(2 * y - 2, 0), by1 = std::min(2 * y - 2 + D1_SY, g.ny[0]);
-                    D1Tile t{i, x, y, -1, -1, 0, 0, 0, -1};
+                    D1Tile t{i, x, y, -1, -1, 0, 0, 0, -1, -1};
                     D1Cams tc{(int)refs.size(), 0, -1, 0};
                     for (int j = 0; j < g.ncam; ++j) {
                         const CamDev& cj = r->hcam[j];
                         if (!cj.visible || (j != i && !rects_meet(cj.V, bx0, bx1, by0, by1))) continue;
                         if (j == i) tc.self = tc.count;
-                        refs.push_back(make_ref(cj, j, bx0, by0));
+                        refs.push_back(make_ref(cj, g, j, bx0, by0));
                         ++tc.count;
                     }
                     t.ref = tc.first + tc.self;
+                    if (g.cyl) {
+                        t.coltab = (int)d1.size();
+                        cols.resize(cols.size() + D1_SX);
+                        cyl_columns(c, g, refs[t.ref], 2 * x - 2, cols.data() + (size_t)t.coltab * D1_SX);
+                    }
                     // interior: one camera, every input at least 0.01 px inside its image, so the
                     // weight is 1 and no coordinate needs clamping (FP32 positions err by ~1e-5 px)
-                    if (tc.count == 1 && solidly_inside(c, Rect{bx0, bx1, by0, by1}, 0.01)) t.flags |= D1_INTERIOR;
+                    if (tc.count == 1 && solidly_inside(c, g, Rect{bx0, bx1, by0, by1}, 0.01)) t.flags |= D1_INTERIOR;
                     t.wtab = (t.flags & D1_INTERIOR) ? -1 : fs->n_wtab++;
                     int fx0, fy0, fw, fh;
-                    if (d1_footprint(c, Rect{bx0, bx1, by0, by1}, fx0, fy0, fw, fh)) {
+                    if (d1_footprint(c, g, Rect{bx0, bx1, by0, by1}, fx0, fy0, fw, fh)) {
                         t.fxy = fx0 | (fy0 << 16);
                         t.fwh = fw | (fh << 16);
                         ++fs->n_staged;
@@ -1561,7 +1649,7 @@ stitch_status fused_plan(stitch_rig* r) {
                     last_v = j;
                 }
                 if (!(at0 || at1)) continue;
-                refs.push_back(make_ref(cj, j, X0, Y0));
+                refs.push_back(make_ref(cj, g, j, X0, Y0));
                 ++t.count;
             }
             int kind;
@@ -1572,7 +1660,7 @@ stitch_status fused_plan(stitch_rig* r) {
                 bool solo = false;
                 if (nv == 1) {
                     const Rect cone = cone_level0(g, X0, X1, Y0, Y1);
-                    solo = solidly_inside(r->hcam[last_v], cone);
+                    solo = solidly_inside(r->hcam[last_v], g, cone);
                     for (int j = 0; j < g.ncam && solo; ++j)
                         if (j != last_v && r->hcam[j].visible && rects_meet(r->hcam[j].V, cone.x0, cone.x1, cone.y0, cone.y1))
                             solo = false;
@@ -1580,7 +1668,7 @@ stitch_status fused_plan(stitch_rig* r) {
                 if (solo) {
                     // one reference: the exclusive camera
                     refs.resize(t.first);
-                    refs.push_back(make_ref(r->hcam[last_v], last_v, X0, Y0));
+                    refs.push_back(make_ref(r->hcam[last_v], g, last_v, X0, Y0));
                     t.count = 1;
                     kind = UP_SIMPLE;
                     ++fs->n_solo;
@@ -1631,6 +1719,8 @@ stitch_status fused_plan(stitch_rig* r) {
     st = upload(r, d1, &fs->d1_tiles);
     if (st != STITCH_OK) return st;
     st = upload(r, d1c, &fs->d1_cams);
+    if (st != STITCH_OK) return st;
+    st = upload(r, cols, &fs->d1cols);
     if (st != STITCH_OK) return st;
     fs->n_d1 = (int)d1.size();
     if (fs->n_wtab > 0) {
@@ -1730,6 +1820,7 @@ struct BatchRigDev {
     const int* camlist;
     const CamRef* refs;
     const float* d1w;
+    const float4* d1cols;
     void* g0buf;
     const UpTile* up[UP_KINDS];
     void* R[MAXL];
@@ -1828,7 +1919,7 @@ __global__ void __launch_bounds__(B_THREADS, MINB) k_batch(const BatchRigDev* __
             const T* R2 = rg.g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
             switch (tk.type) {
                 case BT_D1:
-                    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, (T*)rg.g0buf, smem);
+                    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, rg.d1cols, (T*)rg.g0buf, smem);
                     break;
                 case BT_RED:
                     reduce_tile<T>(rg.cams, rg.g, tk.level - 1, task_tile<Tile>(tk), smem);
@@ -1890,7 +1981,7 @@ __global__ void __launch_bounds__(D1_THREADS, 3) k_mr_down1(const BatchRigDev* _
     extern __shared__ float4 smem[];
     const BTask tk = tasks[blockIdx.x];
     const BatchRigDev& rg = rigs[tk.rig];
-    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, (T*)rg.g0buf, smem);
+    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, rg.d1cols, (T*)rg.g0buf, smem);
 }
 
 template <typename T>
@@ -2226,6 +2317,7 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
         d.camlist = fs->camlist;
         d.refs = fs->refs;
         d.d1w = fs->d1w;
+        d.d1cols = fs->d1cols;
         d.g0buf = fs->g0buf;
         for (int q = 0; q < UP_KINDS; ++q) d.up[q] = fs->up_tiles[q];
         const int L = r->geom.levels;

@@ -12,7 +12,7 @@ __device__ __forceinline__ float4 ld4(const float4* p) { return __ldg(p); }
 
 // S1 + S2: level 0 of camera i on Om[0]: (I_i rgb, What_i).
 __global__ void __launch_bounds__(BX* BY) k_plain_warp(const CamDev* __restrict__ cams, int ncam, int i,
-                                                        FramePtrs fp, int seam) {
+                                                        FramePtrs fp, const __grid_constant__ RigGeom g) {
     __shared__ TileMap tm[MAXC];
     __shared__ int act[MAXC];
     __shared__ int ax[MAXC], ay[MAXC];
@@ -40,12 +40,12 @@ __global__ void __launch_bounds__(BX* BY) k_plain_warp(const CamDev* __restrict_
     float3 rgb = make_float3(0.f, 0.f, 0.f);
     float wi = 0.f, ws = 0.f;
     // seam weights: the pixel's owner among all cameras (FP64 decision)
-    const int own = seam ? seam_owner(ncam, [&](int k) -> const CamDev& { return cams[k]; }, x, y) : -1;
+    const int own = g.seam ? seam_owner(g, ncam, [&](int k) -> const CamDev& { return cams[k]; }, x, y) : -1;
     for (int j = 0; j < ncam; ++j) {
         if (!act[j]) continue;
         const CamDev& cj = cams[j];
-        const SrcPos s = map_point(tm[j], (float)(x - ax[j]), (float)(y - ay[j]));
-        const float w = seam ? (own == j ? 1.f : 0.f) : (cj.V.contains(x, y) ? feather_weight(s, cj.W, cj.H) : 0.f);
+        const SrcPos s = g.cyl ? map_point64(cj, g, x, y) : map_point(tm[j], (float)(x - ax[j]), (float)(y - ay[j]));
+        const float w = g.seam ? (own == j ? 1.f : 0.f) : (cj.V.contains(x, y) ? feather_weight(s, cj.W, cj.H) : 0.f);
         ws += w;
         if (j == i) {
             wi = w;
@@ -241,7 +241,7 @@ stitch_status plain_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od
     for (int i = 0; i < g.ncam; ++i) {
         if (!r->hcam[i].visible || !launchable(r->hcam[i].Om[0])) continue;
         prof_mark(r, "plain_warp", s);
-        k_plain_warp<<<grid_for(r->hcam[i].Om[0]), blk, 0, s>>>(r->dcam, g.ncam, i, fp, g.seam);
+        k_plain_warp<<<grid_for(r->hcam[i].Om[0]), blk, 0, s>>>(r->dcam, g.ncam, i, fp, g);
     }
     for (int i = 0; i < g.ncam; ++i) {
         if (!r->hcam[i].visible) continue;

@@ -34,36 +34,92 @@ bool invert_normalised(const double* M, double* A) {
 
 // Validate one camera and plan its regions (validity box V, weight support Z^l, pyramid region
 // Omega^l).  Adds the camera's level-0 region area to *roi.
+// Footprint on the cylindrical canvas of camera P's pixel-edge rectangle: its border, sampled
+// every 0.25 px, mapped through the rays P^-1 (u, v, 1).  False when a border ray points along
+// the axis or the border crosses the back of the cylinder (the footprint would wrap around).
+static bool cylinder_footprint(const stitch_camera& c, const RigGeom& g, double* xmin, double* xmax, double* ymin,
+                               double* ymax) {
+    // P^-1 (adjugate over the determinant)
+    const double* M = c.H;
+    const double a = M[0], b = M[1], cc = M[2], d = M[3], e = M[4], f = M[5], gg = M[6], h = M[7], k = M[8];
+    const double det = a * (e * k - f * h) + b * (f * gg - d * k) + cc * (d * h - e * gg);
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return false;
+    const double Pi[9] = {(e * k - f * h) / det,  (cc * h - b * k) / det, (b * f - cc * e) / det,
+                          (f * gg - d * k) / det, (a * k - cc * gg) / det, (cc * d - a * f) / det,
+                          (d * h - e * gg) / det, (b * gg - a * h) / det, (a * e - b * d) / det};
+    const double W = c.width, H = c.height;
+    const long long nu = (long long)std::ceil(W * 4.0), nv = (long long)std::ceil(H * 4.0);
+    double tprev = 0.0;
+    bool first = true;
+    *xmin = *ymin = 1e300;
+    *xmax = *ymax = -1e300;
+    for (int side = 0; side < 4; ++side) {
+        const long long n = (side % 2 == 0) ? nu : nv;
+        for (long long k = 0; k <= n; ++k) {
+            const double s = (double)k / (double)n;
+            double u, v;
+            if (side == 0) { u = -0.5 + s * W; v = -0.5; }
+            else if (side == 1) { u = W - 0.5; v = -0.5 + s * H; }
+            else if (side == 2) { u = W - 0.5 - s * W; v = H - 0.5; }
+            else { u = -0.5; v = H - 0.5 - s * H; }
+            double r[3];
+            // P r = (u, v, 1): in front of the camera
+            for (int i = 0; i < 3; ++i) r[i] = Pi[3 * i] * u + Pi[3 * i + 1] * v + Pi[3 * i + 2];
+            const double rxz = std::hypot(r[0], r[2]);
+            if (!(rxz > 0.0)) return false;
+            const double t = std::atan2(r[0], r[2]);
+            if (!first && std::fabs(t - tprev) > 1.0) return false;
+            first = false;
+            tprev = t;
+            const double x = g.ccx + g.cf * t, y = g.ccy + g.cf * r[1] / rxz;
+            *xmin = std::min(*xmin, x);
+            *xmax = std::max(*xmax, x);
+            *ymin = std::min(*ymin, y);
+            *ymax = std::max(*ymax, y);
+        }
+    }
+    return true;
+}
+
 stitch_status plan_camera_geometry(const stitch_camera& c, const RigGeom& g, CamDev& d, long long* roi) {
     memset(&d, 0, sizeof(d));
     const int L = g.levels, Wc = g.nx[0], Hc = g.ny[0];
     if (c.width < 1 || c.height < 1 || !std::isfinite(c.gain)) return STITCH_EINVAL;
     for (double v : c.H)
         if (!std::isfinite(v)) return STITCH_EINVAL;
-    if (!invert_normalised(c.H, d.A)) return STITCH_EINVAL;
+    if (g.cyl) {
+        for (int i = 0; i < 9; ++i) d.A[i] = c.H[i];  // P acts on the canvas ray as given
+    } else if (!invert_normalised(c.H, d.A)) {
+        return STITCH_EINVAL;
+    }
     d.W = c.width;
     d.H = c.height;
     d.gain = c.gain;
 
-    // footprint of the validity rectangle: image of its corners under H (must stay in front)
-    const double cu[4] = {-0.5, c.width - 0.5, -0.5, c.width - 0.5};
-    const double cv[4] = {-0.5, -0.5, c.height - 0.5, c.height - 0.5};
-    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
-    for (int k = 0; k < 4; ++k) {
-        const double X = c.H[0] * cu[k] + c.H[1] * cv[k] + c.H[2];
-        const double Y = c.H[3] * cu[k] + c.H[4] * cv[k] + c.H[5];
-        const double Wh = c.H[6] * cu[k] + c.H[7] * cv[k] + c.H[8];
-        // the corner must be in front of the camera for the footprint to be a bounded quad
-        if (!(Wh > 0.0)) return STITCH_EINVAL;
-        xmin = std::min(xmin, X / Wh);
-        xmax = std::max(xmax, X / Wh);
-        ymin = std::min(ymin, Y / Wh);
-        ymax = std::max(ymax, Y / Wh);
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300, margin = 1.0;
+    if (g.cyl) {
+        if (!cylinder_footprint(c, g, &xmin, &xmax, &ymin, &ymax)) return STITCH_EINVAL;
+        margin = 2.0;  // the border is sampled, not mapped exactly
+    } else {
+        // footprint of the validity rectangle: image of its corners under H (must stay in front)
+        const double cu[4] = {-0.5, c.width - 0.5, -0.5, c.width - 0.5};
+        const double cv[4] = {-0.5, -0.5, c.height - 0.5, c.height - 0.5};
+        for (int k = 0; k < 4; ++k) {
+            const double X = c.H[0] * cu[k] + c.H[1] * cv[k] + c.H[2];
+            const double Y = c.H[3] * cu[k] + c.H[4] * cv[k] + c.H[5];
+            const double Wh = c.H[6] * cu[k] + c.H[7] * cv[k] + c.H[8];
+            // the corner must be in front of the camera for the footprint to be a bounded quad
+            if (!(Wh > 0.0)) return STITCH_EINVAL;
+            xmin = std::min(xmin, X / Wh);
+            xmax = std::max(xmax, X / Wh);
+            ymin = std::min(ymin, Y / Wh);
+            ymax = std::max(ymax, Y / Wh);
+        }
     }
-    // one pixel of margin beyond the footprint so single-precision evaluation near its edge is
-    // still inside the box (outside the box the camera's weight is exactly zero)
-    const double bx0 = std::max(0.0, floor(xmin) - 1.0), bx1 = std::min((double)Wc, ceil(xmax) + 2.0);
-    const double by0 = std::max(0.0, floor(ymin) - 1.0), by1 = std::min((double)Hc, ceil(ymax) + 2.0);
+    // a margin beyond the footprint so single-precision evaluation near its edge is still inside
+    // the box (outside the box the camera's weight is exactly zero)
+    const double bx0 = std::max(0.0, floor(xmin) - margin), bx1 = std::min((double)Wc, ceil(xmax) + margin + 1.0);
+    const double by0 = std::max(0.0, floor(ymin) - margin), by1 = std::min((double)Hc, ceil(ymax) + margin + 1.0);
     if (bx1 <= bx0 || by1 <= by0) {
         d.visible = 0;
         return STITCH_OK;
@@ -95,12 +151,21 @@ stitch_status plan_camera_geometry(const stitch_camera& c, const RigGeom& g, Cam
         d.Z[l] = make_rect(zx[l], zy[l]);
         d.Om[l] = make_rect(ox[l], oy[l]);
     }
-    // the camera must be in front (w > 0) everywhere its level-0 values are evaluated
+    // the camera must be in front (w > 0) everywhere its level-0 values are evaluated: w is affine
+    // in (x, y) on the planar canvas (corners decide) and affine in y on every column of the
+    // cylindrical one (the top and bottom rows of every column decide)
     const Rect& o = d.Om[0];
-    const double qx[2] = {(double)o.x0, (double)(o.x1 - 1)}, qy[2] = {(double)o.y0, (double)(o.y1 - 1)};
-    for (double x : qx)
-        for (double y : qy)
-            if (!(d.A[6] * x + d.A[7] * y + d.A[8] > 0.0)) return STITCH_EINVAL;
+    const double qy[2] = {(double)o.y0, (double)(o.y1 - 1)};
+    const int step = g.cyl ? 1 : std::max(1, o.x1 - 1 - o.x0);
+    for (int xi = o.x0; xi < o.x1; xi += step) {
+        for (int pass = 0; pass < 2; ++pass) {
+            const double x = pass == 0 ? (double)xi : (double)(o.x1 - 1);
+            for (double y : qy) {
+                double u, v;
+                if (!(source_point64(d, g, x, y, &u, &v) > 0.0)) return STITCH_EINVAL;
+            }
+        }
+    }
     *roi += o.area();
     return STITCH_OK;
 }
@@ -200,7 +265,11 @@ stitch_status stitch_rig_create(const stitch_rig_desc* desc, int device, stitch_
         desc->canvas_h > (1 << 28) || (desc->band_fp16 != 0 && desc->band_fp16 != 1) ||
         (desc->out_float != 0 && desc->out_float != 1) ||
         (desc->path != STITCH_PATH_FUSED && desc->path != STITCH_PATH_PLAIN) ||
-        (desc->weights != STITCH_WEIGHTS_FEATHER && desc->weights != STITCH_WEIGHTS_SEAM))
+        (desc->weights != STITCH_WEIGHTS_FEATHER && desc->weights != STITCH_WEIGHTS_SEAM) ||
+        (desc->canvas_model != STITCH_CANVAS_PLANAR && desc->canvas_model != STITCH_CANVAS_CYLINDRICAL) ||
+        (desc->canvas_model == STITCH_CANVAS_CYLINDRICAL &&
+         !(std::isfinite(desc->cylinder[0]) && desc->cylinder[0] > 0.0 && std::isfinite(desc->cylinder[1]) &&
+           std::isfinite(desc->cylinder[2]))))
         return STITCH_EINVAL;
     if ((long long)desc->canvas_w * desc->canvas_h > (1LL << 31)) return STITCH_EINVAL;
     int ndev = 0;
@@ -221,6 +290,10 @@ stitch_status stitch_rig_create(const stitch_rig_desc* desc, int device, stitch_
     g.ncam = desc->num_cameras;
     g.levels = desc->levels;
     g.seam = desc->weights == STITCH_WEIGHTS_SEAM;
+    g.cyl = desc->canvas_model == STITCH_CANVAS_CYLINDRICAL;
+    g.cf = g.cyl ? desc->cylinder[0] : 0.0;
+    g.ccx = g.cyl ? desc->cylinder[1] : 0.0;
+    g.ccy = g.cyl ? desc->cylinder[2] : 0.0;
     g.nx[0] = desc->canvas_w;
     g.ny[0] = desc->canvas_h;
     for (int l = 1; l < g.levels; ++l) {
@@ -346,6 +419,7 @@ stitch_status stitch_backward(stitch_rig* r, const uint8_t* const* frames, const
                               const double* params, double* loss, double* grad, void* stream) {
     if (!r || !params || !loss) return STITCH_EINVAL;
     if (!frames || !pitches) return STITCH_EINVAL;
+    if (r->geom.cyl) return STITCH_EUNSUPPORTED;  // the loss is parametrised by planar homographies
     FramePtrs fp;
     memset(&fp, 0, sizeof(fp));
     for (int i = 0; i < r->geom.ncam; ++i) {

@@ -82,7 +82,9 @@ extern "C" stitch_status stitch_frames_static(const stitch_rig_desc* desc, const
     if (desc->num_cameras < 1 || desc->num_cameras > MAXC || desc->canvas_w < 1 || desc->canvas_h < 1 ||
         desc->levels < 1 || desc->levels > MAXL || desc->canvas_w > (1 << 28) || desc->canvas_h > (1 << 28) ||
         desc->band_fp16 != 0 || (desc->out_float != 0 && desc->out_float != 1) ||
-        (desc->weights != STITCH_WEIGHTS_FEATHER && desc->weights != STITCH_WEIGHTS_SEAM))
+        (desc->weights != STITCH_WEIGHTS_FEATHER && desc->weights != STITCH_WEIGHTS_SEAM) ||
+        (desc->canvas_model != STITCH_CANVAS_PLANAR && desc->canvas_model != STITCH_CANVAS_CYLINDRICAL) ||
+        (desc->canvas_model == STITCH_CANVAS_CYLINDRICAL && !(desc->cylinder[0] > 0.0)))
         return STITCH_EINVAL;
     if ((long long)desc->canvas_w * desc->canvas_h > (1LL << 31)) return STITCH_EINVAL;
     const long long row = (long long)desc->canvas_w * (desc->out_float ? 12 : 3);
@@ -97,6 +99,10 @@ extern "C" stitch_status stitch_frames_static(const stitch_rig_desc* desc, const
     g.ncam = desc->num_cameras;
     g.levels = desc->levels;
     g.seam = desc->weights == STITCH_WEIGHTS_SEAM;
+    g.cyl = desc->canvas_model == STITCH_CANVAS_CYLINDRICAL;
+    g.cf = g.cyl ? desc->cylinder[0] : 0.0;
+    g.ccx = g.cyl ? desc->cylinder[1] : 0.0;
+    g.ccy = g.cyl ? desc->cylinder[2] : 0.0;
     g.nx[0] = desc->canvas_w;
     g.ny[0] = desc->canvas_h;
     for (int l = 1; l < g.levels; ++l) {

@@ -44,6 +44,8 @@ struct CamDev {
 struct RigGeom {
     int ncam, levels;
     int seam;  // level-0 weights: 0 feather, 1 seam owner masks
+    int cyl;   // canvas: 0 planar (homographies), 1 cylindrical (focal length cf, centre ccx, ccy)
+    double cf, ccx, ccy;
     int nx[MAXL], ny[MAXL];  // canvas size of every level (nx[l+1] = ceil(nx[l] / 2))
 };
 
@@ -143,16 +145,58 @@ __device__ __forceinline__ float feather_weight(const SrcPos& s, int W, int H) {
     return fmaxf(m, 0.0f);
 }
 
+// The canvas point (x, y) as the vector the camera matrix A acts on: (x, y, 1) on the planar
+// canvas; on the cylindrical canvas the ray (sin t, (y - cy)/f, cos t) with t = (x - cx)/f.
+__host__ __device__ inline void canvas_ray(const RigGeom& g, double x, double y, double r[3]) {
+    if (g.cyl) {
+        const double t = (x - g.ccx) / g.cf;
+        r[0] = sin(t);
+        r[1] = (y - g.ccy) / g.cf;
+        r[2] = cos(t);
+    } else {
+        r[0] = x;
+        r[1] = y;
+        r[2] = 1.0;
+    }
+}
+
+// Source point of canvas point (x, y) in camera c, FP64: (u, v) and w (> 0 in front).
+__host__ __device__ inline double source_point64(const CamDev& c, const RigGeom& g, double x, double y, double* u,
+                                                 double* v) {
+    double r[3];
+    canvas_ray(g, x, y, r);
+    const double w = c.A[6] * r[0] + c.A[7] * r[1] + c.A[8] * r[2];
+    *u = (c.A[0] * r[0] + c.A[1] * r[1] + c.A[2] * r[2]) / w;
+    *v = (c.A[3] * r[0] + c.A[4] * r[1] + c.A[5] * r[2]) / w;
+    return w;
+}
+
 // S2 feather weight of camera c at canvas point (x, y) in FP64: distance from the source point to
 // the border of the pixel-edge rectangle [-0.5, W-0.5) x [-0.5, H-0.5), 0 outside it or behind
 // the camera.
-__host__ __device__ inline double feather_weight64(const CamDev& c, double x, double y) {
-    const double w = c.A[6] * x + c.A[7] * y + c.A[8];
+__host__ __device__ inline double feather_weight64(const CamDev& c, const RigGeom& g, double x, double y) {
+    double u, v;
+    const double w = source_point64(c, g, x, y, &u, &v);
     if (!(w > 0.0)) return 0.0;
-    const double u = (c.A[0] * x + c.A[1] * y + c.A[2]) / w, v = (c.A[3] * x + c.A[4] * y + c.A[5]) / w;
     if (!(u >= -0.5 && u < c.W - 0.5 && v >= -0.5 && v < c.H - 0.5)) return 0.0;
     const double m = fmin(fmin(u + 0.5, v + 0.5), fmin(c.W - 0.5 - u, c.H - 0.5 - v));
     return m > 0.0 ? m : 0.0;
+}
+
+// SrcPos of canvas pixel (x, y) in camera c from the FP64 map (see map_pos64).
+__device__ inline SrcPos map_point64(const CamDev& c, const RigGeom& g, int x, int y) {
+    double u, v;
+    const double w = source_point64(c, g, (double)x, (double)y, &u, &v);
+    u = fmin(fmax(u, -1.0e7), 1.0e7);
+    v = fmin(fmax(v, -1.0e7), 1.0e7);
+    const double fu = floor(u), fv = floor(v);
+    SrcPos s;
+    s.iu = (int)fu;
+    s.iv = (int)fv;
+    s.fu = (float)(u - fu);
+    s.fv = (float)(v - fv);
+    s.den = w > 0.0 ? 1.0f : -1.0f;
+    return s;
 }
 
 // Seam owner of canvas point (x, y) among n cameras given in ascending camera order by cam_at(k)
@@ -160,17 +204,17 @@ __host__ __device__ inline double feather_weight64(const CamDev& c, double x, do
 // whose feather weight is > 0 and >= (1 - 1e-9) times the largest, -1 when no weight is > 0.
 // Decided in FP64, so that the binary masks do not depend on the FP32 tile anchoring.
 template <class CamAt>
-__device__ inline int seam_owner(int n, const CamAt& cam_at, int x, int y) {
+__device__ inline int seam_owner(const RigGeom& g, int n, const CamAt& cam_at, int x, int y) {
     double wmax = 0.0;
     for (int k = 0; k < n; ++k) {
         const CamDev& c = cam_at(k);
-        if (c.V.contains(x, y)) wmax = fmax(wmax, feather_weight64(c, (double)x, (double)y));
+        if (c.V.contains(x, y)) wmax = fmax(wmax, feather_weight64(c, g, (double)x, (double)y));
     }
     if (!(wmax > 0.0)) return -1;
     for (int k = 0; k < n; ++k) {
         const CamDev& c = cam_at(k);
         if (!c.V.contains(x, y)) continue;
-        const double w = feather_weight64(c, (double)x, (double)y);
+        const double w = feather_weight64(c, g, (double)x, (double)y);
         if (w > 0.0 && w >= (1.0 - 1e-9) * wmax) return k;
     }
     return -1;
@@ -235,6 +279,47 @@ struct Pos {
     float u, v;    // source coordinates (for validity and weight)
     float den;     // w, positive in front of the camera
 };
+
+// map_pos with the column terms (the anchored numerators and denominator at row dy = 0) given:
+// fmaf(t.pu1, dx, t.pu0) etc. on the planar canvas, a host-built column table on the cylindrical
+// canvas (where a column is an angle); t.pu2, t.pv2, t.q2 are the per-row slopes on both.
+__device__ __forceinline__ Pos map_pos_col(const TileMap& t, float fU0, float fV0, float nuc, float nvc, float dqc,
+                                           float dy) {
+    Pos p;
+    p.den = fmaf(t.q2, dy, dqc);
+    const float rden = __fdividef(1.0f, p.den);
+    float ru = fmaf(t.pu2, dy, nuc) * rden;
+    float rv = fmaf(t.pv2, dy, nvc) * rden;
+    ru = fminf(fmaxf(ru, -1.0e7f), 1.0e7f);
+    rv = fminf(fmaxf(rv, -1.0e7f), 1.0e7f);
+    const float flu = floorf(ru), flv = floorf(rv);
+    p.iu = t.U0 + (int)flu;
+    p.iv = t.V0 + (int)flv;
+    p.fu = ru - flu;
+    p.fv = rv - flv;
+    p.u = fU0 + ru;
+    p.v = fV0 + rv;
+    return p;
+}
+
+// Position of canvas pixel (x, y) in camera c from the FP64 map (paths that are not per-frame
+// hot: GENERAL tiles and the plain path on the cylindrical canvas).
+__device__ inline Pos map_pos64(const CamDev& c, const RigGeom& g, int x, int y) {
+    double u, v;
+    const double w = source_point64(c, g, (double)x, (double)y, &u, &v);
+    Pos p;
+    u = fmin(fmax(u, -1.0e7), 1.0e7);
+    v = fmin(fmax(v, -1.0e7), 1.0e7);
+    const double fu = floor(u), fv = floor(v);
+    p.iu = (int)fu;
+    p.iv = (int)fv;
+    p.fu = (float)(u - fu);
+    p.fv = (float)(v - fv);
+    p.u = (float)u;
+    p.v = (float)v;
+    p.den = w > 0.0 ? 1.0f : -1.0f;
+    return p;
+}
 
 __device__ __forceinline__ Pos map_pos(const TileMap& t, float fU0, float fV0, float dx, float dy) {
     Pos p;

@@ -23,6 +23,8 @@ STITCH_PATH_FUSED = 0
 STITCH_PATH_PLAIN = 1
 STITCH_WEIGHTS_FEATHER = 0
 STITCH_WEIGHTS_SEAM = 1
+STITCH_CANVAS_PLANAR = 0
+STITCH_CANVAS_CYLINDRICAL = 1
 
 _P = ctypes.c_void_p
 _lock = threading.Lock()
@@ -38,7 +40,8 @@ class stitch_rig_desc(ctypes.Structure):
     _fields_ = [("num_cameras", ctypes.c_int32), ("cameras", ctypes.POINTER(stitch_camera)),
                 ("canvas_w", ctypes.c_int32), ("canvas_h", ctypes.c_int32), ("levels", ctypes.c_int32),
                 ("band_fp16", ctypes.c_int32), ("out_float", ctypes.c_int32), ("path", ctypes.c_int32),
-                ("weights", ctypes.c_int32)]
+                ("weights", ctypes.c_int32), ("canvas_model", ctypes.c_int32),
+                ("cylinder", ctypes.c_double * 3)]
 
 
 class stitch_rig_info(ctypes.Structure):
@@ -243,9 +246,10 @@ def _stream_handle(stream) -> int:
 
 
 def make_desc(cameras, canvas_w: int, canvas_h: int, levels: int, band_fp16: bool = False, out_float: bool = False,
-              path: str = "fused", weights: str = "feather"):
+              path: str = "fused", weights: str = "feather", canvas=None):
     """Build a stitch_rig_desc from objects with width, height, H (3x3) and gain; ``weights`` is
-    "feather" or "seam"."""
+    "feather" or "seam"; ``canvas`` is None (planar: H is camera->canvas) or (f, cx, cy) of a
+    cylindrical canvas (H is the camera's ray->camera matrix P = K R)."""
     n = len(cameras)
     arr = (stitch_camera * n)()
     for k, c in enumerate(cameras):
@@ -259,6 +263,10 @@ def make_desc(cameras, canvas_w: int, canvas_h: int, levels: int, band_fp16: boo
                            int(levels), int(bool(band_fp16)), int(bool(out_float)),
                            STITCH_PATH_PLAIN if path == "plain" else STITCH_PATH_FUSED,
                            {"feather": STITCH_WEIGHTS_FEATHER, "seam": STITCH_WEIGHTS_SEAM}[weights])
+    if canvas is not None:
+        desc.canvas_model = STITCH_CANVAS_CYLINDRICAL
+        for k, v in enumerate(canvas):
+            desc.cylinder[k] = float(v)
     return desc, arr
 
 
@@ -266,7 +274,8 @@ class Rig:
     """A created rig: cameras, canvas and pyramid depth fixed; frames stitched on the GPU."""
 
     def __init__(self, cameras, canvas_w: int, canvas_h: int, levels: int, band_fp16: bool = False,
-                 out_float: bool = False, path: str = "fused", device: int | None = None, weights: str = "feather"):
+                 out_float: bool = False, path: str = "fused", device: int | None = None, weights: str = "feather",
+                 canvas=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libstitch needs a CUDA GPU; no CPU fallback exists")
@@ -277,7 +286,8 @@ class Rig:
         self.band_fp16 = bool(band_fp16)
         self.path = path
         self.weights = weights
-        desc, keep = make_desc(self.cameras, canvas_w, canvas_h, levels, band_fp16, out_float, path, weights)
+        self.canvas = canvas
+        desc, keep = make_desc(self.cameras, canvas_w, canvas_h, levels, band_fp16, out_float, path, weights, canvas)
         self.handle = stitch_rig_create(desc, self.device)
         del keep
 
