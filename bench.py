@@ -33,8 +33,9 @@ WORKLOADS = {
     "8x4k": lambda frames: synth.config_8x4k(frames=frames),
     "4x1080p": lambda frames: synth.config_4x1080p(frames=frames),
     "2cam": lambda frames: synth.config_2cam(),
+    "cyl4x720p": lambda frames: synth.config_cyl(frames=frames),
 }
-DEFAULT_FRAMES = {"8x4k": 30, "4x1080p": 60, "2cam": 1}
+DEFAULT_FRAMES = {"8x4k": 30, "4x1080p": 60, "2cam": 1, "cyl4x720p": 30}
 METRIC = "stitched output MPix/s and frames/s on 1 GB300; % of HBM roofline vs plain path"
 
 
@@ -154,7 +155,7 @@ def cpu_baseline(cfg, frames0, budget_s: float = 10.0):
         s = min(side, Wc, Hc)
         w = (int(rng.integers(0, Wc - s + 1)), int(rng.integers(0, Hc - s + 1)), s, s)
         t0 = time.perf_counter()
-        oracle.forward(cfg.cameras, frames0, Wc, Hc, cfg.levels, window=w)
+        oracle.forward(cfg.cameras, frames0, Wc, Hc, cfg.levels, window=w, canvas=cfg.canvas)
         t_total += time.perf_counter() - t0
         px_total += s * s
         wins.append(w)
@@ -230,7 +231,7 @@ def run_reference(args):
 
     def step():
         w = (int(rng.integers(0, cfg.canvas_w - side + 1)), int(rng.integers(0, cfg.canvas_h - side + 1)), side, side)
-        oracle.forward(cfg.cameras, frames0, cfg.canvas_w, cfg.canvas_h, cfg.levels, window=w)
+        oracle.forward(cfg.cameras, frames0, cfg.canvas_w, cfg.canvas_h, cfg.levels, window=w, canvas=cfg.canvas)
 
     for _ in range(args.warmup):
         step()
@@ -326,7 +327,7 @@ def main():
         return ms, kt
 
     rig = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, band_fp16=args.fp16_bands, path=args.path,
-              device=local)
+              device=local, canvas=cfg.canvas)
     info = rig.info()
     out = rig.new_output()
     clocks = ClockSampler(local)
@@ -367,7 +368,8 @@ def main():
 
     plain = None
     if args.path == "fused" and not args.no_plain:
-        prig = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, path="plain", device=local)
+        prig = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, path="plain", device=local,
+                   canvas=cfg.canvas)
         pms, _ = timed(prig, out, max(3, min(args.steps, 10)), 3, False)
         plain = {"value": world * mpix / (pms / 1e3), "ms_per_step": pms,
                  "hbm_frac": cbytes / (pms / 1e3) / 1e9 / hbm_peak, "speedup_fused_over_plain": pms / ms}
@@ -376,7 +378,8 @@ def main():
     # FP16 storage of pyramid data between kernels (arithmetic still FP32), same frames
     fp16 = None
     if not args.fp16_bands and not args.no_fp16:
-        hrig = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, band_fp16=True, device=local)
+        hrig = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, band_fp16=True, device=local,
+                   canvas=cfg.canvas)
         hms, _ = timed(hrig, out, max(3, min(args.steps, 10)), 3, False)
         fp16 = {"value": world * mpix / (hms / 1e3), "ms_per_step": hms}
         hrig.close()
@@ -388,7 +391,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         srig = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, band_fp16=args.fp16_bands, path=args.path,
-                   device=local, weights="seam")
+                   device=local, weights="seam", canvas=cfg.canvas)
         torch.cuda.synchronize()
         create_ms = (time.perf_counter() - t0) * 1e3
         sms, _ = timed(srig, out, max(3, min(args.steps, 10)), 3, False)
