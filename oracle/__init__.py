@@ -60,6 +60,9 @@ def _load():
             lib.oracle_forward.argtypes = [_I, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _I, _I, _I, _P, _P, _P,
                                            _P, _P, _I, _P]
             lib.oracle_warp.argtypes = [_I, _I, _P, _D, _P, ctypes.c_int64, _I, _I, _P, _P, _P]
+            lib.oracle_lorb.argtypes = [_I, _I, _P, ctypes.c_int64, _P, _I, _I, ctypes.c_int64, _I, _P, _P, _P, _P,
+                                        _P, _P]
+            lib.oracle_lorb.restype = _I
             lib.oracle_loss_grad.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _P, _P]
             for f in ("oracle_invert_h", "oracle_reduce", "oracle_expand", "oracle_regions", "oracle_forward",
                       "oracle_warp", "oracle_loss_grad"):
@@ -250,3 +253,30 @@ def loss_grad(widths, heights, params, frames, window, mask_params=None, grad: b
                               None if g is None else g.ctypes.data)
     _check(rc, "loss_grad")
     return float(loss[0]), g
+
+
+def lorb(frame, areas, pattern, fast_t: int = 20, harris_t: int = 0, max_points: int = 500, debug: bool = False):
+    """L-ORB features (FAST-9 + Harris + NMS + top-N + BRIEF, integer arithmetic) of one RGB8 frame.
+
+    ``areas``: (m, 4) int rectangles (x0, y0, x1, y1); ``pattern``: (256, 4) int8 BRIEF point
+    pairs.  Returns dict(xy (n, 2) int32, resp (n,) int64, desc (n, 32) uint8[, resp_map])."""
+    lib = _load()
+    frame = np.ascontiguousarray(frame, dtype=np.uint8)
+    H, W = frame.shape[:2]
+    ar = np.ascontiguousarray(np.asarray(areas, dtype=np.int32).reshape(-1, 4))
+    pat = np.ascontiguousarray(np.asarray(pattern, dtype=np.int8).reshape(256, 4))
+    xy = np.zeros((max_points, 2), np.int32)
+    resp = np.zeros(max_points, np.int64)
+    desc = np.zeros((max_points, 32), np.uint8)
+    cnt = np.zeros(1, np.int32)
+    rmap = np.empty((H, W), np.int64) if debug else None
+    rc = lib.oracle_lorb(W, H, frame.ctypes.data, frame.strides[0], ar.ctypes.data if len(ar) else None, len(ar),
+                         int(fast_t), int(harris_t), int(max_points), pat.ctypes.data, xy.ctypes.data,
+                         resp.ctypes.data, desc.ctypes.data, cnt.ctypes.data,
+                         rmap.ctypes.data if debug else None)
+    _check(rc, "lorb")
+    n = int(cnt[0])
+    res = {"xy": xy[:n], "resp": resp[:n], "desc": desc[:n]}
+    if debug:
+        res["resp_map"] = rmap
+    return res

@@ -657,3 +657,177 @@ int oracle_loss_grad(int n, const int32_t* Ws, const int32_t* Hs, const double* 
     free(rows);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* L-ORB feature extraction (Sec. 4.1, Algorithms 1 and 2), all in exact integer arithmetic     */
+/*                                                                                            */
+/* Readings (the paper fixes the steps, not their constants):                                 */
+/*  L1 gray = (77 R + 150 G + 29 B + 128) >> 8.                                               */
+/*  L2 candidates: pixels inside one of the m detection areas (Algorithm 2, step 1) and at     */
+/*     least LORB_MARGIN px from the image border (room for every neighbourhood below).       */
+/*  L3 FAST (Algorithm 1, step 4): FAST-9 on the 16-pixel circle of radius 3, threshold t:    */
+/*     a corner when 9 contiguous circle pixels are all > I(p) + t or all < I(p) - t.         */
+/*  L4 gradients (step 1): Ix = I(x+1, y) - I(x-1, y), Iy = I(x, y+1) - I(x, y-1).           */
+/*  L5 Gaussian weighting with sigma = 1 (step 3): the binomial [1,4,6,4,1] in x and y        */
+/*     (variance exactly 1), unnormalised: A = sum b b Ix^2, B = sum b b Iy^2, C = sum b b IxIy.*/
+/*  L6 Harris response with alpha = 0.04 (step 5): R' = 25 (AB - C^2) - (A + B)^2 = 25 R;      */
+/*     kept when R' > harris_t.                                                               */
+/*  L7 non-maximum suppression (step 6) over the 8-neighbourhood, ties to the lower index     */
+/*     y W + x; the N (= P) strongest (step 7, Algorithm 2 step 3): R' descending, index      */
+/*     ascending.                                                                             */
+/*  L8 BRIEF (Sec. 4.1.2, Algorithm 2 step 4): smoothed image S = binomial 5x5 of gray        */
+/*     (unnormalised); n_d = 256 point pairs (p_k, q_k) of offsets in [-15, 15]^2 (an input);  */
+/*     bit k = [S(x + p_k) > S(x + q_k)], stored LSB-first in 32 bytes.                       */
+/* ------------------------------------------------------------------------------------------ */
+
+#define LORB_MARGIN 18
+#define LORB_ND 256
+
+static const int fast_dx[16] = {0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1};
+static const int fast_dy[16] = {-3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3};
+static const int binom5[5] = {1, 4, 6, 4, 1};
+
+static int fast9(const uint8_t* g, int W, int x, int y, int t) {
+    const int p = g[(int64_t)y * W + x];
+    int run_b = 0, run_d = 0;
+    /* walk the circle twice so that arcs wrapping past the start are seen */
+    for (int k = 0; k < 32; ++k) {
+        const int c = g[(int64_t)(y + fast_dy[k & 15]) * W + x + fast_dx[k & 15]];
+        run_b = c > p + t ? run_b + 1 : 0;
+        run_d = c < p - t ? run_d + 1 : 0;
+        if (run_b >= 9 || run_d >= 9) return 1;
+    }
+    return 0;
+}
+
+typedef struct {
+    int64_t r;
+    int32_t idx;
+} lorb_cand;
+
+static int lorb_better(const lorb_cand* a, const lorb_cand* b) {
+    return a->r > b->r || (a->r == b->r && a->idx < b->idx);
+}
+
+static int lorb_cmp(const void* pa, const void* pb) {
+    const lorb_cand* a = (const lorb_cand*)pa;
+    const lorb_cand* b = (const lorb_cand*)pb;
+    if (lorb_better(a, b)) return -1;
+    if (lorb_better(b, a)) return 1;
+    return 0;
+}
+
+/*
+ * frame: W x H RGB8 (pitch bytes); areas: n_areas x (x0, y0, x1, y1), half-open image
+ * rectangles; pattern: LORB_ND x (px, py, qx, qy).  Outputs (up to max_points): out_xy
+ * (x, y), out_resp (R'), out_desc (32 bytes each); *out_count the number written.  dbg_resp
+ * (optional, W*H): R' of every candidate that is a FAST corner with R' > harris_t, INT64_MIN
+ * elsewhere (before non-maximum suppression).
+ */
+int oracle_lorb(int W, int H, const uint8_t* frame, int64_t pitch, const int32_t* areas, int n_areas, int fast_t,
+                int64_t harris_t, int max_points, const int8_t* pattern, int32_t* out_xy, int64_t* out_resp,
+                uint8_t* out_desc, int32_t* out_count, int64_t* dbg_resp) {
+    if (W < 1 || H < 1 || !frame || pitch < 3LL * W || n_areas < 0 || (n_areas > 0 && !areas) || fast_t < 0 ||
+        max_points < 0 || !pattern || !out_count)
+        return OR_EINVAL;
+    for (int k = 0; k < LORB_ND; ++k)
+        for (int j = 0; j < 4; ++j)
+            if (pattern[4 * k + j] < -15 || pattern[4 * k + j] > 15) return OR_EINVAL;
+    const int64_t N = (int64_t)W * H;
+    uint8_t* gray = (uint8_t*)malloc((size_t)N);
+    int64_t* resp = (int64_t*)malloc(sizeof(int64_t) * (size_t)N);
+    uint8_t* mask = (uint8_t*)calloc((size_t)N, 1);
+    lorb_cand* cand = (lorb_cand*)malloc(sizeof(lorb_cand) * (size_t)N);
+    if (!gray || !resp || !mask || !cand) {
+        free(gray); free(resp); free(mask); free(cand);
+        return OR_ENOMEM;
+    }
+    /* L1 */
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const uint8_t* q = frame + (int64_t)y * pitch + 3 * (int64_t)x;
+            gray[(int64_t)y * W + x] = (uint8_t)((77 * q[0] + 150 * q[1] + 29 * q[2] + 128) >> 8);
+        }
+    /* L2: candidate mask */
+    for (int a = 0; a < n_areas; ++a) {
+        int x0 = areas[4 * a], y0 = areas[4 * a + 1], x1 = areas[4 * a + 2], y1 = areas[4 * a + 3];
+        if (x0 < LORB_MARGIN) x0 = LORB_MARGIN;
+        if (y0 < LORB_MARGIN) y0 = LORB_MARGIN;
+        if (x1 > W - LORB_MARGIN) x1 = W - LORB_MARGIN;
+        if (y1 > H - LORB_MARGIN) y1 = H - LORB_MARGIN;
+        for (int y = y0; y < y1; ++y)
+            for (int x = x0; x < x1; ++x) mask[(int64_t)y * W + x] = 1;
+    }
+    /* L3-L6 */
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int64_t o = (int64_t)y * W + x;
+            resp[o] = INT64_MIN;
+            if (!mask[o] || !fast9(gray, W, x, y, fast_t)) continue;
+            int64_t A = 0, B = 0, C = 0;
+            for (int dy = -2; dy <= 2; ++dy)
+                for (int dx = -2; dx <= 2; ++dx) {
+                    const int64_t q = (int64_t)(y + dy) * W + (x + dx);
+                    const int ix = (int)gray[q + 1] - (int)gray[q - 1];
+                    const int iy = (int)gray[q + W] - (int)gray[q - W];
+                    const int64_t w = binom5[dx + 2] * binom5[dy + 2];
+                    A += w * ix * ix;
+                    B += w * iy * iy;
+                    C += w * ix * iy;
+                }
+            const int64_t r = 25 * (A * B - C * C) - (A + B) * (A + B);
+            if (r > harris_t) resp[o] = r;
+        }
+    if (dbg_resp) memcpy(dbg_resp, resp, sizeof(int64_t) * (size_t)N);
+    /* L7 */
+    int64_t nc = 0;
+    for (int y = 1; y < H - 1; ++y)
+        for (int x = 1; x < W - 1; ++x) {
+            const int64_t o = (int64_t)y * W + x;
+            if (resp[o] == INT64_MIN) continue;
+            lorb_cand me = {resp[o], (int32_t)o};
+            int keep = 1;
+            for (int dy = -1; dy <= 1 && keep; ++dy)
+                for (int dx = -1; dx <= 1 && keep; ++dx) {
+                    if (!dx && !dy) continue;
+                    const int64_t q = o + (int64_t)dy * W + dx;
+                    if (resp[q] == INT64_MIN) continue;
+                    lorb_cand other = {resp[q], (int32_t)q};
+                    if (!lorb_better(&me, &other)) keep = 0;
+                }
+            if (keep) cand[nc++] = me;
+        }
+    qsort(cand, (size_t)nc, sizeof(lorb_cand), lorb_cmp);
+    const int n = nc < max_points ? (int)nc : max_points;
+    /* L8 */
+    for (int k = 0; k < n; ++k) {
+        const int x = cand[k].idx % W, y = cand[k].idx / W;
+        if (out_xy) {
+            out_xy[2 * k] = x;
+            out_xy[2 * k + 1] = y;
+        }
+        if (out_resp) out_resp[k] = cand[k].r;
+        if (!out_desc) continue;
+        uint8_t* d = out_desc + 32 * (int64_t)k;
+        memset(d, 0, 32);
+        for (int b = 0; b < LORB_ND; ++b) {
+            int64_t s[2];
+            for (int e = 0; e < 2; ++e) {
+                const int px = x + pattern[4 * b + 2 * e], py = y + pattern[4 * b + 2 * e + 1];
+                int64_t acc = 0;
+                for (int dy = -2; dy <= 2; ++dy)
+                    for (int dx = -2; dx <= 2; ++dx)
+                        acc += binom5[dx + 2] * binom5[dy + 2] * gray[(int64_t)(py + dy) * W + px + dx];
+                s[e] = acc;
+            }
+            if (s[0] > s[1]) d[b >> 3] |= (uint8_t)(1u << (b & 7));
+        }
+    }
+    *out_count = n;
+    free(gray);
+    free(resp);
+    free(mask);
+    free(cand);
+    return OR_OK;
+}

@@ -352,3 +352,10 @@ CONFIGS = {
     "refine_4x1080p": config_refine,
     "8x4k": config_8x4k,
 }
+
+
+def brief_pattern(seed: int = 0, n: int = 256) -> np.ndarray:
+    """BRIEF point pairs (n, 4) int8 (px, py, qx, qy): isotropic Gaussian offsets with sigma =
+    31/5 px, rounded and clipped to the 31 x 31 patch [-15, 15]^2, seeded."""
+    rng = np.random.default_rng(seed)
+    return np.clip(np.rint(rng.normal(0.0, 31.0 / 5.0, (n, 4))), -15, 15).astype(np.int8)
