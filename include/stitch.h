@@ -228,6 +228,47 @@ stitch_status stitch_rig_kernel_times(stitch_rig* rig, const char** names, doubl
                                       int32_t cap, int32_t* count);
 
 /* ------------------------------------------------------------------------------------------ */
+/* L-ORB feature extraction (Sec. 4.1, Algorithms 1 and 2): the registration step before the    */
+/* per-frame path.  Integer definition (bit-exact against the CPU oracle):                      */
+/*   gray = (77 R + 150 G + 29 B + 128) >> 8; candidates inside the detection areas (Algorithm   */
+/*   2, step 1) and at least 18 px from the image border; FAST-9 on the radius-3 circle with     */
+/*   threshold fast_t (Algorithm 1, step 4); Ix, Iy central differences; A, B, C = their         */
+/*   products weighted by the binomial [1,4,6,4,1]^2 (sigma = 1, unnormalised, step 3);          */
+/*   R' = 25 (AB - C^2) - (A + B)^2 (25 x the Harris response with alpha = 0.04), kept when      */
+/*   R' > harris_t (step 5); non-maximum suppression over the 8-neighbourhood, ties to the lower */
+/*   index y W + x (step 6); the max_points strongest, R' descending then index ascending (step  */
+/*   7); BRIEF (Sec. 4.1.2) bit k = [S(p + a_k) > S(p + b_k)] with S the binomial-smoothed gray   */
+/*   and 256 point pairs given by the caller, stored LSB-first in 32 bytes per point.            */
+/* ------------------------------------------------------------------------------------------ */
+
+typedef struct stitch_lorb stitch_lorb; /* opaque: preallocated scratch for images up to a size */
+
+typedef struct {
+    int32_t fast_t;     /* FAST intensity threshold, >= 0 */
+    int64_t harris_t;   /* keep R' > harris_t */
+    int32_t max_points; /* N, <= the context's max_points */
+} stitch_lorb_params;
+
+/* Scratch for images up to max_width x max_height (each >= 37) and up to max_points (<= 2048)
+ * points, on `device`.  Status: OK, EINVAL, ENOMEM, ECUDA. */
+stitch_status stitch_lorb_create(int32_t max_width, int32_t max_height, int32_t max_points, int32_t device,
+                                 stitch_lorb** out);
+void stitch_lorb_destroy(stitch_lorb* ctx); /* NULL-safe; synchronises the device */
+
+/*
+ * Features of one RGB8 device frame (pitch bytes >= 3 width), asynchronous on `stream`.
+ *   areas    host array of n_areas (<= 64) rectangles x0, y0, x1, y1 (half-open, image px)
+ *   pattern  host array of 256 point pairs ax, ay, bx, by (each in [-15, 15])
+ *   xy       device, 2 int32 per point (x, y); resp device, int64 R' per point;
+ *   desc     device, 32 bytes per point (4-byte aligned); count device, number of points written
+ * The context may serve one call at a time.  Status: OK, EINVAL, ECUDA.
+ */
+stitch_status stitch_lorb_detect(stitch_lorb* ctx, const uint8_t* frame, int32_t width, int32_t height, int64_t pitch,
+                                 const int32_t* areas, int32_t n_areas, const stitch_lorb_params* params,
+                                 const int8_t* pattern, int32_t* xy, int64_t* resp, uint8_t* desc, int32_t* count,
+                                 void* stream);
+
+/* ------------------------------------------------------------------------------------------ */
 /* Batching: several independent rigs stitched by one persistent launch                        */
 
 typedef struct stitch_batch stitch_batch; /* opaque */

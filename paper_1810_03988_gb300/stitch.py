@@ -44,6 +44,10 @@ class stitch_rig_desc(ctypes.Structure):
                 ("cylinder", ctypes.c_double * 3)]
 
 
+class stitch_lorb_params(ctypes.Structure):
+    _fields_ = [("fast_t", ctypes.c_int32), ("harris_t", ctypes.c_int64), ("max_points", ctypes.c_int32)]
+
+
 class stitch_rig_info(ctypes.Structure):
     _fields_ = [("scratch_bytes", ctypes.c_int64), ("num_kernels", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("roi_pixels", ctypes.c_int64), ("tiles_zero", ctypes.c_int32), ("tiles_solo", ctypes.c_int32),
@@ -72,6 +76,11 @@ SIGNATURES = {
                                                  ctypes.POINTER(ctypes.c_int64)]),
     "stitch_batch_wait_test": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "stitch_frames_static": (ctypes.c_int, [ctypes.POINTER(stitch_rig_desc), _P, _P, _P, ctypes.c_int64, _P]),
+    "stitch_lorb_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(_P)]),
+    "stitch_lorb_destroy": (None, [_P]),
+    "stitch_lorb_detect": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_int32,
+                                          ctypes.POINTER(stitch_lorb_params), _P, _P, _P, _P, _P, _P]),
 }
 
 
@@ -452,3 +461,68 @@ def _frame_args(frames, cameras):
         ptrs.append(f.data_ptr())
         pitches.append(f.stride(0))
     return ptrs, pitches
+
+
+def stitch_lorb_create(max_width: int, max_height: int, max_points: int, device: int) -> int:
+    out = _P()
+    _check(load().stitch_lorb_create(max_width, max_height, max_points, device, ctypes.byref(out)), "stitch_lorb_create")
+    return out.value
+
+
+def stitch_lorb_destroy(ctx: int) -> None:
+    load().stitch_lorb_destroy(ctx)
+
+
+def stitch_lorb_detect(ctx: int, frame_ptr: int, width: int, height: int, pitch: int, areas, params, pattern,
+                       xy_ptr: int, resp_ptr: int, desc_ptr: int, count_ptr: int, stream: int) -> None:
+    ar = np.ascontiguousarray(np.asarray(areas, dtype=np.int32).reshape(-1, 4))
+    pat = np.ascontiguousarray(np.asarray(pattern, dtype=np.int8).reshape(256, 4))
+    _check(load().stitch_lorb_detect(ctx, frame_ptr, width, height, pitch, ar.ctypes.data if len(ar) else None, len(ar),
+                                     ctypes.byref(params), pat.ctypes.data, xy_ptr, resp_ptr, desc_ptr, count_ptr,
+                                     stream), "stitch_lorb_detect")
+
+
+class LORB:
+    """L-ORB feature extraction on the GPU (Sec. 4.1): FAST-9 + Harris + NMS + top-N + BRIEF."""
+
+    def __init__(self, max_width: int, max_height: int, max_points: int = 500, device: int | None = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libstitch needs a CUDA GPU; no CPU fallback exists")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.max_points = int(max_points)
+        self.handle = stitch_lorb_create(int(max_width), int(max_height), self.max_points, self.device)
+        d = f"cuda:{self.device}"
+        self.xy = torch.empty((self.max_points, 2), dtype=torch.int32, device=d)
+        self.resp = torch.empty(self.max_points, dtype=torch.int64, device=d)
+        self.desc = torch.empty((self.max_points, 32), dtype=torch.uint8, device=d)
+        self.count = torch.zeros(1, dtype=torch.int32, device=d)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            stitch_lorb_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def detect(self, frame, areas, pattern, fast_t: int = 20, harris_t: int = 0, max_points: int | None = None,
+               stream=None):
+        """frame: (H, W, 3) uint8 CUDA tensor.  Enqueues the detection; returns (xy, resp, desc, count)
+        views of the context's output tensors (valid after the stream reaches them)."""
+        assert frame.is_cuda and frame.dtype.itemsize == 1 and frame.stride(1) == 3 and frame.stride(2) == 1
+        n = self.max_points if max_points is None else int(max_points)
+        prm = stitch_lorb_params(int(fast_t), int(harris_t), n)
+        stitch_lorb_detect(self.handle, frame.data_ptr(), frame.shape[1], frame.shape[0], frame.stride(0), areas, prm,
+                           pattern, self.xy.data_ptr(), self.resp.data_ptr(), self.desc.data_ptr(),
+                           self.count.data_ptr(), _stream_handle(stream))
+        return self.xy, self.resp, self.desc, self.count
