@@ -164,6 +164,36 @@ def cpu_baseline(cfg, frames0, budget_s: float = 10.0):
                       f"(each with its full pyramid dependency region), {t_total:.1f} s"}
 
 
+def measure_lorb(torch, dframes, hframes, device: int, points: int = 500, reps: int = 20):
+    """L-ORB on every view of one frame set (whole views as detection areas): ms per frame set and
+    input MPix/s on the GPU (CUDA events, after warm-up), and the integer oracle on one view."""
+    import oracle
+    from paper_1810_03988_gb300 import LORB
+    pat = synth.brief_pattern(0)
+    H, W = dframes[0].shape[:2]
+    areas = [(0, 0, W, H)]
+    with LORB(W, H, points, device) as ctx:
+        for _ in range(3):
+            for f in dframes:
+                ctx.detect(f, areas, pat, 20, 0, points)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            for f in dframes:
+                ctx.detect(f, areas, pat, 20, 0, points)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+    mpix = sum(f.shape[0] * f.shape[1] for f in dframes) / 1e6
+    t0 = time.perf_counter()
+    oracle.lorb(hframes[0], areas, pat, 20, 0, points)
+    cpu_s = time.perf_counter() - t0
+    return {"value": mpix / (ms / 1e3), "unit": "MPix/s", "ms_per_frame_set": ms, "views": len(dframes),
+            "points_per_view": points, "cpu_oracle": {"value": (W * H / 1e6) / cpu_s, "unit": "MPix/s",
+                                                      "cores": oracle.threads(), "sample": "one view"}}
+
+
 def measure_batch(Rig, dev, torch, args, n_rigs: int = 16):
     """The 16-rig batching workload: every rig stitched by its own launch sequence, then all rigs by
     one persistent launch (CUDA graph).  Device-timed, 3 warm-up calls each."""
@@ -270,6 +300,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-band comparison run")
     ap.add_argument("--no-seam", action="store_true", help="skip the seam-weight run")
+    ap.add_argument("--no-lorb", action="store_true", help="skip the L-ORB feature-extraction run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-per-rig comparison")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -399,6 +430,12 @@ def main():
         seam = {"value": world * mpix / (sms / 1e3), "ms_per_step": sms, "rig_create_ms": create_ms}
         srig.close()
 
+    # L-ORB feature extraction (the registration step): every camera view of a frame set, whole
+    # view as the detection area, 500 points per view; the oracle on the host for one view
+    lorb = None
+    if not args.no_lorb and rank == 0:
+        lorb = measure_lorb(torch, dframes[0], host_frames[0], local)
+
     # batching: 16 uneven rigs, one launch sequence per rig against one persistent launch
     batched = None
     if not args.no_batch:
@@ -447,7 +484,7 @@ def main():
                        "l2": "inputs larger than L2: each frame set is a distinct device buffer "
                              f"({cbytes / 1e6:.0f} MB compulsory traffic per step)"},
             "roofline": roof, "step_roofline": step_roof, "plain_path": plain, "fp16_bands": fp16,
-            "seam_weights": seam,
+            "seam_weights": seam, "lorb": lorb,
             "batched": batched, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk, "gpu_launches": info["num_kernels"] * args.steps,
             "rig": {"scratch_bytes": info["scratch_bytes"], "roi_pixels": info["roi_pixels"],
