@@ -63,6 +63,9 @@ def _load():
             lib.oracle_lorb.argtypes = [_I, _I, _P, ctypes.c_int64, _P, _I, _I, ctypes.c_int64, _I, _P, _P, _P, _P,
                                         _P, _P]
             lib.oracle_lorb.restype = _I
+            lib.oracle_match_prosac.argtypes = [_I, _P, _P, _I, _P, _P, _I, _I, _P, _I, _I, _I, _D, _I, _P, _P, _P,
+                                                _P, _P, _P]
+            lib.oracle_match_prosac.restype = _I
             lib.oracle_loss_grad.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _P, _P]
             for f in ("oracle_invert_h", "oracle_reduce", "oracle_expand", "oracle_regions", "oracle_forward",
                       "oracle_warp", "oracle_loss_grad"):
@@ -280,3 +283,30 @@ def lorb(frame, areas, pattern, fast_t: int = 20, harris_t: int = 0, max_points:
     if debug:
         res["resp_map"] = rmap
     return res
+
+
+def match_prosac(xy_a, desc_a, xy_b, desc_b, bits, rnd, max_dist: int = 80, ratio=(4, 5), inlier_px: float = 3.0):
+    """Multi-Probe LSH matching (bits: (L, k) positions) and PROSAC homography (rnd: (iters, 4)
+    uint32 words).  Returns dict(matches (n, 3): a, b, distance in quality order; H (3, 3) mapping
+    image-A points to image B; inliers (count); inlier (n,) bool)."""
+    lib = _load()
+    xa = np.ascontiguousarray(np.asarray(xy_a, dtype=np.int32).reshape(-1, 2))
+    xb = np.ascontiguousarray(np.asarray(xy_b, dtype=np.int32).reshape(-1, 2))
+    da = np.ascontiguousarray(np.asarray(desc_a, dtype=np.uint8).reshape(-1, 32))
+    db = np.ascontiguousarray(np.asarray(desc_b, dtype=np.uint8).reshape(-1, 32))
+    bt = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8))
+    L, k = bt.shape
+    rw = np.ascontiguousarray(np.asarray(rnd, dtype=np.uint32).reshape(-1, 4))
+    na, nb = len(xa), len(xb)
+    matches = np.zeros((max(na, 1), 3), np.int32)
+    nm = np.zeros(1, np.int32)
+    H = np.zeros(9)
+    ni = np.zeros(1, np.int32)
+    inl = np.zeros(max(na, 1), np.uint8)
+    rc = lib.oracle_match_prosac(na, xa.ctypes.data, da.ctypes.data, nb, xb.ctypes.data, db.ctypes.data, L, k,
+                                 bt.ctypes.data, int(max_dist), int(ratio[0]), int(ratio[1]), float(inlier_px),
+                                 len(rw), rw.ctypes.data if len(rw) else None, matches.ctypes.data, nm.ctypes.data,
+                                 H.ctypes.data, ni.ctypes.data, inl.ctypes.data)
+    _check(rc, "match_prosac")
+    n = int(nm[0])
+    return {"matches": matches[:n], "H": H.reshape(3, 3), "inliers": int(ni[0]), "inlier": inl[:n].astype(bool)}

@@ -831,3 +831,327 @@ int oracle_lorb(int W, int H, const uint8_t* frame, int64_t pitch, const int32_t
     free(cand);
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Feature matching and homography estimation (Sec. 4.2, Algorithm 3)                         */
+/*                                                                                            */
+/* Readings:                                                                                  */
+/*  M1 Multi-Probe LSH (Sec. 4.2.1): L tables, each hashing a descriptor to k of its 256 bits  */
+/*     (positions given); a query probes its own bucket and the k buckets at Hamming distance  */
+/*     1 of every table.  Among the probed descriptors of image B the nearest (Hamming, ties to  */
+/*     the lower index) is the match when its distance is <= max_dist and passes the ratio     */
+/*     test ratio_den * d1 < ratio_num * d2 (d2: nearest other probed index; none: passes).    */
+/*  M2 quality order (Algorithm 3, step 1): distance ascending, then query index ascending.    */
+/*  M3 PROSAC (Sec. 4.2.2, Algorithm 3, step 2): the growth schedule of Chum and Matas with     */
+/*     m = 4 and T_N = 200000; iteration t samples the newest of the top n and 3 others from    */
+/*     the top n - 1 (or 4 from the top n once t exceeds T'_n); samples are drawn without        */
+/*     replacement from given random words (4 per iteration).  Hypothesis: the homography with  */
+/*     h33 = 1 through the 4 pairs (8x8 Gaussian elimination, partial pivoting, ties to the     */
+/*     lower row; |pivot| < 1e-12 rejects the sample), fitted in coordinates normalised per     */
+/*     image (centre and half-extent of the matched points' bounding box, as Hartley's          */
+/*     normalisation).  Inlier: in front (w > 0) and squared transfer error < inlier_px^2 (in   */
+/*     normalised units of image B).  Best: most inliers, ties to the earlier iteration; then   */
+/*     least squares on its inliers (normal equations summed in quality order, same solver),    */
+/*     returned in pixel coordinates with h33 = 1.                                              */
+/*  All in IEEE double without contractions, so that a device implementation in the same    */
+/*  operation order takes the same decisions.                                                 */
+/* ------------------------------------------------------------------------------------------ */
+
+static int hamming256(const uint8_t* a, const uint8_t* b) {
+    int d = 0;
+    for (int k = 0; k < 32; ++k) d += __builtin_popcount((unsigned)(a[k] ^ b[k]));
+    return d;
+}
+
+static uint32_t lsh_key(const uint8_t* d, const uint8_t* bits, int k) {
+    uint32_t key = 0;
+    for (int j = 0; j < k; ++j) key |= (uint32_t)((d[bits[j] >> 3] >> (bits[j] & 7)) & 1u) << j;
+    return key;
+}
+
+/* solve the 8x8 system M h = r in place (row-major M), partial pivoting; returns 0 when singular */
+static int solve8(double M[8][8], double r[8], double h[8]) {
+    for (int c = 0; c < 8; ++c) {
+        int p = c;
+        for (int i = c + 1; i < 8; ++i)
+            if (fabs(M[i][c]) > fabs(M[p][c])) p = i;
+        if (!(fabs(M[p][c]) >= 1e-12)) return 0;
+        if (p != c) {
+            for (int j = 0; j < 8; ++j) {
+                const double t = M[c][j];
+                M[c][j] = M[p][j];
+                M[p][j] = t;
+            }
+            const double t = r[c];
+            r[c] = r[p];
+            r[p] = t;
+        }
+        for (int i = c + 1; i < 8; ++i) {
+            const double f = M[i][c] / M[c][c];
+            for (int j = c; j < 8; ++j) M[i][j] = M[i][j] - f * M[c][j];
+            r[i] = r[i] - f * r[c];
+        }
+    }
+    for (int c = 7; c >= 0; --c) {
+        double s = r[c];
+        for (int j = c + 1; j < 8; ++j) s = s - M[c][j] * h[j];
+        h[c] = s / M[c][c];
+    }
+    return 1;
+}
+
+static int homography4(const double* ax, const double* ay, const double* bx, const double* by, double h[8]) {
+    double M[8][8], r[8];
+    for (int k = 0; k < 4; ++k) {
+        const double x = ax[k], y = ay[k], u = bx[k], v = by[k];
+        double* m0 = M[2 * k];
+        double* m1 = M[2 * k + 1];
+        m0[0] = x; m0[1] = y; m0[2] = 1.0; m0[3] = 0.0; m0[4] = 0.0; m0[5] = 0.0; m0[6] = -(u * x); m0[7] = -(u * y);
+        m1[0] = 0.0; m1[1] = 0.0; m1[2] = 0.0; m1[3] = x; m1[4] = y; m1[5] = 1.0; m1[6] = -(v * x); m1[7] = -(v * y);
+        r[2 * k] = u;
+        r[2 * k + 1] = v;
+    }
+    return solve8(M, r, h);
+}
+
+static int is_inlier(const double h[8], double x, double y, double u, double v, double t2) {
+    const double w = h[6] * x + h[7] * y + 1.0;
+    if (!(w > 0.0)) return 0;
+    const double pu = (h[0] * x + h[1] * y + h[2]) / w - u;
+    const double pv = (h[3] * x + h[4] * y + h[5]) / w - v;
+    return pu * pu + pv * pv < t2;
+}
+
+/* PROSAC schedule: n(t) and whether iteration t samples uniformly from the top n (t = 1..T) */
+static void prosac_schedule(int N, int T, int* nt, uint8_t* uni) {
+    const int m = 4;
+    double Tn = 200000.0;
+    for (int i = 0; i < m; ++i) Tn = Tn * (double)(m - i) / (double)(N - i);
+    int n = m;
+    double Tp = 1.0;
+    for (int t = 1; t <= T; ++t) {
+        if ((double)t == Tp && n < N) {
+            const double Tn1 = Tn * (double)(n + 1) / (double)(n + 1 - m);
+            Tp = Tp + ceil(Tn1 - Tn);
+            Tn = Tn1;
+            n = n + 1;
+        }
+        nt[t - 1] = n;
+        uni[t - 1] = Tp < (double)t ? 1 : 0;
+    }
+}
+
+/* the j-th smallest element of {0..n-1} not in chosen[0..c) */
+static int nth_free(int j, const int* chosen, int c) {
+    int s[4];
+    for (int i = 0; i < c; ++i) s[i] = chosen[i];
+    for (int i = 1; i < c; ++i)
+        for (int k = i; k > 0 && s[k - 1] > s[k]; --k) {
+            const int tmp = s[k];
+            s[k] = s[k - 1];
+            s[k - 1] = tmp;
+        }
+    for (int i = 0; i < c; ++i)
+        if (s[i] <= j) ++j;
+    return j;
+}
+
+/* the 4 sample indices (into the quality order) of iteration t */
+static void prosac_sample(int n, int uniform, const uint32_t* rnd, int* idx) {
+    if (uniform) {
+        for (int k = 0; k < 4; ++k) idx[k] = nth_free((int)(rnd[k] % (uint32_t)(n - k)), idx, k);
+    } else {
+        idx[0] = n - 1;
+        int chosen[3];
+        for (int k = 0; k < 3; ++k) {
+            chosen[k] = nth_free((int)(rnd[k] % (uint32_t)(n - 1 - k)), chosen, k);
+            idx[k + 1] = chosen[k];
+        }
+    }
+}
+
+/*
+ * xy_a, desc_a (na points), xy_b, desc_b (nb points); bits: L x k bit positions.  rnd: iters x 4
+ * random words.  Outputs: matches (up to na, quality order) as (index a, index b, distance),
+ * *n_matches; H (9, h33 = 1, maps image-A points to image B), *n_inliers (0: no model), inlier
+ * flags per match (optional).
+ */
+int oracle_match_prosac(int na, const int32_t* xy_a, const uint8_t* desc_a, int nb, const int32_t* xy_b,
+                        const uint8_t* desc_b, int L, int k, const uint8_t* bits, int max_dist, int ratio_num,
+                        int ratio_den, double inlier_px, int iters, const uint32_t* rnd, int32_t* matches,
+                        int32_t* n_matches, double* H, int32_t* n_inliers, uint8_t* inlier) {
+    if (na < 0 || nb < 0 || L < 1 || L > 32 || k < 1 || k > 20 || !bits || iters < 0 || (iters > 0 && !rnd) ||
+        !matches || !n_matches || !H || !n_inliers || ratio_den < 1 || ratio_num < 1)
+        return OR_EINVAL;
+    for (int i = 0; i < L * k; ++i)
+        if (bits[i] > 255) return OR_EINVAL;
+    /* M1: tables as (key, index) sorted by key, index */
+    uint32_t* keys = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)L * (nb > 0 ? nb : 1));
+    int32_t* ord = (int32_t*)malloc(sizeof(int32_t) * (size_t)L * (nb > 0 ? nb : 1));
+    int32_t* mt = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)(na > 0 ? na : 1));
+    if (!keys || !ord || !mt) {
+        free(keys); free(ord); free(mt);
+        return OR_ENOMEM;
+    }
+    for (int l = 0; l < L; ++l) {
+        for (int i = 0; i < nb; ++i) {
+            keys[(size_t)l * nb + i] = lsh_key(desc_b + 32 * (size_t)i, bits + l * k, k);
+            ord[(size_t)l * nb + i] = i;
+        }
+        /* insertion sort by (key, index): small tables */
+        uint32_t* kk = keys + (size_t)l * nb;
+        int32_t* oo = ord + (size_t)l * nb;
+        for (int i = 1; i < nb; ++i)
+            for (int j = i; j > 0 && kk[j - 1] > kk[j]; --j) {
+                const uint32_t tk = kk[j]; kk[j] = kk[j - 1]; kk[j - 1] = tk;
+                const int32_t to = oo[j]; oo[j] = oo[j - 1]; oo[j - 1] = to;
+            }
+    }
+    int nm = 0;
+    for (int a = 0; a < na; ++a) {
+        const uint8_t* da = desc_a + 32 * (size_t)a;
+        int b1 = -1, d1 = 1 << 30, b2 = -1, d2 = 1 << 30;
+        for (int l = 0; l < L; ++l) {
+            const uint32_t q0 = lsh_key(da, bits + l * k, k);
+            for (int p = -1; p < k; ++p) {
+                const uint32_t q = p < 0 ? q0 : (q0 ^ (1u << p));
+                /* bucket range by binary search */
+                int lo = 0, hi = nb;
+                while (lo < hi) {
+                    const int mid = (lo + hi) / 2;
+                    if (keys[(size_t)l * nb + mid] < q) lo = mid + 1; else hi = mid;
+                }
+                for (int i = lo; i < nb && keys[(size_t)l * nb + i] == q; ++i) {
+                    const int b = ord[(size_t)l * nb + i];
+                    const int d = hamming256(da, desc_b + 32 * (size_t)b);
+                    if (d < d1 || (d == d1 && b < b1)) {
+                        if (b != b1) { d2 = d1; b2 = b1; }
+                        d1 = d; b1 = b;
+                    } else if (b != b1 && (d < d2 || (d == d2 && b < b2))) {
+                        d2 = d; b2 = b;
+                    }
+                }
+            }
+        }
+        (void)b2;
+        if (b1 >= 0 && d1 <= max_dist && (d2 == (1 << 30) || (long long)ratio_den * d1 < (long long)ratio_num * d2)) {
+            mt[3 * nm] = a;
+            mt[3 * nm + 1] = b1;
+            mt[3 * nm + 2] = d1;
+            ++nm;
+        }
+    }
+    /* M2: quality order (insertion sort: distance, then query index; stable in a) */
+    for (int i = 1; i < nm; ++i)
+        for (int j = i; j > 0 && mt[3 * (j - 1) + 2] > mt[3 * j + 2]; --j)
+            for (int e = 0; e < 3; ++e) {
+                const int32_t t = mt[3 * j + e]; mt[3 * j + e] = mt[3 * (j - 1) + e]; mt[3 * (j - 1) + e] = t;
+            }
+    memcpy(matches, mt, sizeof(int32_t) * 3 * (size_t)nm);
+    *n_matches = nm;
+    /* M3 */
+    for (int i = 0; i < 9; ++i) H[i] = i % 4 == 0 ? 1.0 : 0.0;
+    *n_inliers = 0;
+    if (inlier) memset(inlier, 0, (size_t)nm);
+    int best_t = -1, best_c = -1;
+    double best_h[8];
+    /* normalisation of each image's matched points: centre and scale of their bounding box */
+    double ca[2] = {0.0, 0.0}, cb[2] = {0.0, 0.0}, sa = 1.0, sb = 1.0;
+    if (nm > 0) {
+        int mn[2][2], mx[2][2];
+        for (int e = 0; e < 2; ++e) {
+            const int32_t* xy = e == 0 ? xy_a : xy_b;
+            for (int c = 0; c < 2; ++c) mn[e][c] = mx[e][c] = xy[2 * mt[e] + c];
+            for (int i = 1; i < nm; ++i)
+                for (int c = 0; c < 2; ++c) {
+                    const int v = xy[2 * mt[3 * i + e] + c];
+                    if (v < mn[e][c]) mn[e][c] = v;
+                    if (v > mx[e][c]) mx[e][c] = v;
+                }
+        }
+        for (int c = 0; c < 2; ++c) {
+            ca[c] = 0.5 * ((double)mn[0][c] + (double)mx[0][c]);
+            cb[c] = 0.5 * ((double)mn[1][c] + (double)mx[1][c]);
+        }
+        int ra = mx[0][0] - mn[0][0], rb = mx[1][0] - mn[1][0];
+        if (mx[0][1] - mn[0][1] > ra) ra = mx[0][1] - mn[0][1];
+        if (mx[1][1] - mn[1][1] > rb) rb = mx[1][1] - mn[1][1];
+        sa = 2.0 / (double)(ra > 1 ? ra : 1);
+        sb = 2.0 / (double)(rb > 1 ? rb : 1);
+    }
+#define NAX(i) (((double)xy_a[2 * mt[3 * (i)]] - ca[0]) * sa)
+#define NAY(i) (((double)xy_a[2 * mt[3 * (i)] + 1] - ca[1]) * sa)
+#define NBX(i) (((double)xy_b[2 * mt[3 * (i) + 1]] - cb[0]) * sb)
+#define NBY(i) (((double)xy_b[2 * mt[3 * (i) + 1] + 1] - cb[1]) * sb)
+    if (nm >= 4 && iters > 0) {
+        int* nt = (int*)malloc(sizeof(int) * (size_t)iters);
+        uint8_t* uni = (uint8_t*)malloc((size_t)iters);
+        if (!nt || !uni) {
+            free(nt); free(uni); free(keys); free(ord); free(mt);
+            return OR_ENOMEM;
+        }
+        prosac_schedule(nm, iters, nt, uni);
+        const double tn = inlier_px * sb;
+        const double t2 = tn * tn;
+        for (int t = 0; t < iters; ++t) {
+            int idx[4];
+            prosac_sample(nt[t], uni[t], rnd + 4 * (size_t)t, idx);
+            double ax[4], ay[4], bx[4], by[4], h[8];
+            for (int q = 0; q < 4; ++q) {
+                ax[q] = NAX(idx[q]);
+                ay[q] = NAY(idx[q]);
+                bx[q] = NBX(idx[q]);
+                by[q] = NBY(idx[q]);
+            }
+            if (!homography4(ax, ay, bx, by, h)) continue;
+            int c = 0;
+            for (int i = 0; i < nm; ++i) c += is_inlier(h, NAX(i), NAY(i), NBX(i), NBY(i), t2);
+            if (c > best_c) {
+                best_c = c;
+                best_t = t;
+                memcpy(best_h, h, sizeof(best_h));
+            }
+        }
+        free(nt);
+        free(uni);
+        if (best_t >= 0 && best_c >= 4) {
+            /* least squares on the inliers: normal equations in quality order */
+            double M[8][8], r[8], h[8];
+            memset(M, 0, sizeof(M));
+            memset(r, 0, sizeof(r));
+            for (int i = 0; i < nm; ++i) {
+                const double x = NAX(i), y = NAY(i), u = NBX(i), v = NBY(i);
+                if (!is_inlier(best_h, x, y, u, v, t2)) continue;
+                if (inlier) inlier[i] = 1;
+                const double row0[8] = {x, y, 1.0, 0.0, 0.0, 0.0, -(u * x), -(u * y)};
+                const double row1[8] = {0.0, 0.0, 0.0, x, y, 1.0, -(v * x), -(v * y)};
+                for (int p = 0; p < 8; ++p) {
+                    for (int q = 0; q < 8; ++q) M[p][q] = M[p][q] + row0[p] * row0[q] + row1[p] * row1[q];
+                    r[p] = r[p] + row0[p] * u + row1[p] * v;
+                }
+            }
+            const double* hn = solve8(M, r, h) ? h : best_h;
+            /* back to pixels: H = Tb^-1 Hn Ta, Ta = [[sa, 0, -sa ca0], [0, sa, -sa ca1], [0, 0, 1]] */
+            const double Hn[9] = {hn[0], hn[1], hn[2], hn[3], hn[4], hn[5], hn[6], hn[7], 1.0};
+            const double Ta[9] = {sa, 0.0, -(sa * ca[0]), 0.0, sa, -(sa * ca[1]), 0.0, 0.0, 1.0};
+            const double Tbi[9] = {1.0 / sb, 0.0, cb[0], 0.0, 1.0 / sb, cb[1], 0.0, 0.0, 1.0};
+            double P[9], Q[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    P[3 * i + j] = Hn[3 * i] * Ta[j] + Hn[3 * i + 1] * Ta[3 + j] + Hn[3 * i + 2] * Ta[6 + j];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    Q[3 * i + j] = Tbi[3 * i] * P[j] + Tbi[3 * i + 1] * P[3 + j] + Tbi[3 * i + 2] * P[6 + j];
+            for (int i = 0; i < 9; ++i) H[i] = Q[i] / Q[8];
+            *n_inliers = best_c;
+        }
+    }
+#undef NAX
+#undef NAY
+#undef NBX
+#undef NBY
+    free(keys);
+    free(ord);
+    free(mt);
+    return OR_OK;
+}

@@ -359,3 +359,14 @@ def brief_pattern(seed: int = 0, n: int = 256) -> np.ndarray:
     31/5 px, rounded and clipped to the 31 x 31 patch [-15, 15]^2, seeded."""
     rng = np.random.default_rng(seed)
     return np.clip(np.rint(rng.normal(0.0, 31.0 / 5.0, (n, 4))), -15, 15).astype(np.int8)
+
+
+def lsh_bits(seed: int = 0, tables: int = 8, bits: int = 16) -> np.ndarray:
+    """Bit positions of the LSH tables: (tables, bits) distinct positions of 256 per table, seeded."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.choice(256, bits, replace=False) for _ in range(tables)]).astype(np.uint8)
+
+
+def prosac_words(seed: int = 0, iters: int = 1024) -> np.ndarray:
+    """Random words of the PROSAC samples: (iters, 4) uint32, seeded."""
+    return np.random.default_rng(seed).integers(0, 2 ** 32, (iters, 4), dtype=np.uint64).astype(np.uint32)

@@ -1,0 +1,93 @@
+"""Pins of the matching/homography oracle (Sec. 4.2, Algorithm 3): Multi-Probe LSH against an
+independent NumPy formulation, homography recovery from exact and contaminated correspondences,
+and registration of two synthetic views against the rig's true relative homography."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def _numpy_lsh_matches(desc_a, desc_b, bits, max_dist, ratio):
+    da = np.unpackbits(desc_a, axis=1, bitorder="little").astype(np.int64)
+    db = np.unpackbits(desc_b, axis=1, bitorder="little").astype(np.int64)
+    dist = (da[:, None, :] != db[None, :, :]).sum(axis=2)
+    L, k = bits.shape
+    weights = (1 << np.arange(k)).astype(np.int64)
+    out = []
+    for a in range(len(desc_a)):
+        cand = np.zeros(len(desc_b), bool)
+        for l in range(L):
+            ka = int((da[a, bits[l]] * weights).sum())
+            kb = (db[:, bits[l]] * weights).sum(axis=1)
+            probes = [ka] + [ka ^ (1 << p) for p in range(k)]
+            cand |= np.isin(kb, probes)
+        if not cand.any():
+            continue
+        idx = np.nonzero(cand)[0]
+        order = np.lexsort((idx, dist[a, idx]))
+        b1, d1 = idx[order[0]], dist[a, idx[order[0]]]
+        d2 = dist[a, idx[order[1]]] if len(idx) > 1 else None
+        if d1 <= max_dist and (d2 is None or ratio[1] * d1 < ratio[0] * d2):
+            out.append((a, b1, d1))
+    out.sort(key=lambda m: (m[2], m[0]))
+    return np.array(out, dtype=np.int64).reshape(-1, 3)
+
+
+def _views(scale=0.5):
+    cfg = synth.config_4x1080p(scale=scale, frames=1)
+    fr = cfg.frame(0)
+    pat = synth.brief_pattern(0)
+    H, W = fr[0].shape[:2]
+    fa = oracle.lorb(fr[0], [(W // 2, 0, W, H)], pat, max_points=600)
+    fb = oracle.lorb(fr[1], [(0, 0, W // 2, H)], pat, max_points=600)
+    Ht = np.linalg.inv(np.asarray(cfg.cameras[1].H)) @ np.asarray(cfg.cameras[0].H)
+    return fa, fb, Ht / Ht[2, 2], (W, H)
+
+
+@pytest.mark.parametrize("max_dist,ratio", [(80, (4, 5)), (40, (3, 4)), (256, (1, 1))])
+def test_lsh_matches_independent_numpy_formulation(max_dist, ratio):
+    fa, fb, _, _ = _views()
+    bits = synth.lsh_bits(2, 6, 12)
+    r = oracle.match_prosac(fa["xy"], fa["desc"], fb["xy"], fb["desc"], bits, np.zeros((0, 4)), max_dist, ratio)
+    ref = _numpy_lsh_matches(fa["desc"], fb["desc"], bits, max_dist, ratio)
+    assert len(ref) > 20
+    np.testing.assert_array_equal(r["matches"], ref)
+
+
+def test_homography_from_exact_and_contaminated_correspondences():
+    rng = np.random.default_rng(5)
+    Ht = np.array([[1.05, 0.02, 30.0], [-0.01, 0.97, -12.0], [2e-5, -1e-5, 1.0]])
+    n, n_out = 120, 40
+    a = rng.uniform(50, 900, (n, 2))
+    xa = np.rint(a).astype(np.int32)
+    xb = np.c_[xa, np.ones(n)] @ Ht.T
+    xb = np.rint(xb[:, :2] / xb[:, 2:3]).astype(np.int32)
+    xb[n - n_out:] = rng.integers(0, 900, (n_out, 2))  # outliers, last in the quality order (PROSAC's premise)
+    # descriptors that match i <-> i exactly (a unique random pattern per point)
+    desc = rng.integers(0, 256, (n, 32), dtype=np.uint8)
+    r = oracle.match_prosac(xa, desc, xb, desc, synth.lsh_bits(0), synth.prosac_words(1, 512))
+    m = r["matches"]
+    assert len(m) == n and np.all(m[:, 0] == m[:, 1]) and np.all(m[:, 2] == 0)
+    inl = np.zeros(n, bool)
+    inl[m[r["inlier"], 0]] = True
+    assert not inl[n - n_out:].any() and inl[:n - n_out].mean() > 0.95, inl.sum()
+    p = np.array([[100.0, 100.0, 1], [800, 120, 1], [450, 700, 1]]).T
+    pe, pt = r["H"] @ p, Ht @ p
+    assert np.abs(pe[:2] / pe[2] - pt[:2] / pt[2]).max() < 0.5
+
+
+def test_two_views_register_to_the_rig_geometry():
+    fa, fb, Ht, (W, H) = _views()
+    r = oracle.match_prosac(fa["xy"], fa["desc"], fb["xy"], fb["desc"], synth.lsh_bits(0), synth.prosac_words(0, 1024))
+    assert r["inliers"] > 100
+    p = np.array([[W * 0.6, H * 0.2, 1], [W * 0.9, H * 0.8, 1], [W * 0.75, H * 0.5, 1]]).T
+    pe, pt = r["H"] @ p, Ht @ p
+    assert np.abs(pe[:2] / pe[2] - pt[:2] / pt[2]).max() < 1.0
+
+
+def test_too_few_matches_give_no_model():
+    fa, fb, _, _ = _views()
+    r = oracle.match_prosac(fa["xy"][:3], fa["desc"][:3], fb["xy"], fb["desc"], synth.lsh_bits(0),
+                            synth.prosac_words(0, 64))
+    assert r["inliers"] == 0 and np.array_equal(r["H"], np.eye(3))
