@@ -194,6 +194,43 @@ def measure_lorb(torch, dframes, hframes, device: int, points: int = 500, reps: 
                                                       "cores": oracle.threads(), "sample": "one view"}}
 
 
+def measure_match(torch, dframes, hframes, device: int, points: int = 1000, iters: int = 1000, reps: int = 20):
+    """Registration of the first two views (Sec. 4.2): GPU L-ORB features of each (whole views),
+    then Multi-Probe LSH matching (8 tables x 16 bits) and PROSAC (T iterations) on the GPU, timed
+    with CUDA events after warm-up; the oracle on the same feature sets beside it."""
+    import oracle
+    from paper_1810_03988_gb300 import LORB, Matcher
+    pat, bits = synth.brief_pattern(0), synth.lsh_bits(0)
+    rnd = synth.prosac_words(0, iters)
+    H, W = dframes[0].shape[:2]
+    areas = [(0, 0, W, H)]
+    with LORB(W, H, points, device) as la, LORB(W, H, points, device) as lb, Matcher(points, iters, device) as m:
+        fa = la.detect(dframes[0], areas, pat, 20, 0, points)
+        fb = lb.detect(dframes[1], areas, pat, 20, 0, points)
+        rw = torch.from_numpy(rnd.view(np.int32)).to(dframes[0].device)
+        args = (fa[0], fa[2], fa[3], fb[0], fb[2], fb[3], bits, rw)
+        for _ in range(3):
+            m.match(*args)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            m.match(*args)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        n_matches, n_inl = int(m.n_matches.cpu()[0]), int(m.n_inliers.cpu()[0])
+        ha = [t[:int(fa[3].cpu()[0])].cpu().numpy() for t in (fa[0], fa[2])]
+        hb = [t[:int(fb[3].cpu()[0])].cpu().numpy() for t in (fb[0], fb[2])]
+    t0 = time.perf_counter()
+    oracle.match_prosac(ha[0], ha[1], hb[0], hb[1], bits, rnd)
+    cpu_s = time.perf_counter() - t0
+    return {"value": 1e3 / ms, "unit": "view pairs/s", "ms_per_pair": ms, "points_per_view": points,
+            "prosac_iters": iters, "tables": int(bits.shape[0]), "bits": int(bits.shape[1]),
+            "matches": n_matches, "inliers": n_inl,
+            "cpu_oracle": {"value": 1.0 / cpu_s, "unit": "view pairs/s", "cores": 1, "sample": "the same pair"}}
+
+
 def measure_batch(Rig, dev, torch, args, n_rigs: int = 16):
     """The 16-rig batching workload: every rig stitched by its own launch sequence, then all rigs by
     one persistent launch (CUDA graph).  Device-timed, 3 warm-up calls each."""
@@ -431,10 +468,12 @@ def main():
         srig.close()
 
     # L-ORB feature extraction (the registration step): every camera view of a frame set, whole
-    # view as the detection area, 500 points per view; the oracle on the host for one view
-    lorb = None
+    # view as the detection area, 500 points per view; the oracle on the host for one view.  Then
+    # matching and PROSAC on the first two views' features (1000 points each)
+    lorb = match = None
     if not args.no_lorb and rank == 0:
         lorb = measure_lorb(torch, dframes[0], host_frames[0], local)
+        match = measure_match(torch, dframes[0], host_frames[0], local)
 
     # batching: 16 uneven rigs, one launch sequence per rig against one persistent launch
     batched = None
@@ -484,7 +523,7 @@ def main():
                        "l2": "inputs larger than L2: each frame set is a distinct device buffer "
                              f"({cbytes / 1e6:.0f} MB compulsory traffic per step)"},
             "roofline": roof, "step_roofline": step_roof, "plain_path": plain, "fp16_bands": fp16,
-            "seam_weights": seam, "lorb": lorb,
+            "seam_weights": seam, "lorb": lorb, "match": match,
             "batched": batched, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk, "gpu_launches": info["num_kernels"] * args.steps,
             "rig": {"scratch_bytes": info["scratch_bytes"], "roi_pixels": info["roi_pixels"],

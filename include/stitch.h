@@ -269,6 +269,61 @@ stitch_status stitch_lorb_detect(stitch_lorb* ctx, const uint8_t* frame, int32_t
                                  void* stream);
 
 /* ------------------------------------------------------------------------------------------ */
+/* Feature matching and homography estimation (Sec. 4.2, Algorithm 3): Multi-Probe LSH over     */
+/* BRIEF descriptors and PROSAC, bit-exact against the CPU oracle (integer decisions, and IEEE   */
+/* double arithmetic without contractions in the order stated):                                  */
+/*   M1 table l hashes a descriptor to the k bits bits[l*k + j] (bit j of the key = descriptor   */
+/*      bit bits[l*k + j], LSB-first bytes); a query probes its own key and the k keys one bit   */
+/*      away in each of the L tables; b1 = nearest probed descriptor of image B (Hamming, ties    */
+/*      to the lower index), d2 = distance of the nearest other probed index; the query matches  */
+/*      b1 when d1 <= max_dist and (no other, or ratio_den d1 < ratio_num d2);                   */
+/*   M2 matches in quality order: d1 ascending, query index ascending;                           */
+/*   M3 PROSAC (progressive sampling with the Chum-Matas growth schedule, m = 4, T_N = 200000):  */
+/*      iteration t (0-based) draws 4 matches of the top n(t) from rnd[4t..4t+3] (the newest of  */
+/*      the top n and 3 of the top n-1, or 4 of the top n once the schedule has passed; the      */
+/*      j-th remaining index is taken for word w as j = w mod remaining); coordinates normalised */
+/*      per image (centre and 2/extent of the matched points' bounding box); 4-point DLT, h33=1, */
+/*      8x8 Gaussian elimination with partial pivoting (pivot magnitude >= 1e-12, else skipped); */
+/*      inlier: w > 0 and squared transfer error < (inlier_px * scale_B)^2; best hypothesis:     */
+/*      most inliers, ties to the earlier iteration; with >= 4 inliers, least squares on them   */
+/*      (normal equations summed in quality order), de-normalised, h33 = 1.                     */
+/* ------------------------------------------------------------------------------------------ */
+
+typedef struct stitch_matcher stitch_matcher; /* opaque: preallocated scratch */
+
+typedef struct {
+    int32_t tables;    /* L, 1..32 */
+    int32_t bits;      /* k, 1..20 */
+    int32_t max_dist;  /* accept d1 <= max_dist */
+    int32_t ratio_num; /* ratio test den * d1 < num * d2, both >= 1 */
+    int32_t ratio_den;
+    int32_t iters;     /* PROSAC iterations T, 0..the context's max_iters */
+    double inlier_px;  /* inlier threshold in image-B pixels, > 0 */
+} stitch_match_params;
+
+/* Scratch for up to max_points (<= 2048) points per image and max_iters (<= 65536) PROSAC
+ * iterations on `device`.  Status: OK, EINVAL, ENOMEM, ECUDA. */
+stitch_status stitch_matcher_create(int32_t max_points, int32_t max_iters, int32_t device, stitch_matcher** out);
+void stitch_matcher_destroy(stitch_matcher* ctx); /* NULL-safe; synchronises the device */
+
+/*
+ * Match image A's features to image B's and estimate the homography A -> B, asynchronously on
+ * `stream`.  Device arrays: xy_a/xy_b 2 int32 per point; desc_a/desc_b 32 bytes per point
+ * (4-byte aligned); count_a/count_b one int32 each (points used: min(count, max_points)) -- the
+ * outputs of stitch_lorb_detect chain in directly.  Host arrays: bits (tables x bits bytes,
+ * each a descriptor bit 0..255), params.  rnd: device, 4 uint32 per iteration.
+ * Outputs (device): matches (3 int32 per match: index a, index b, distance; room for
+ * max_points), n_matches (1 int32), H (9 doubles, row-major, h33 = 1; identity when no model),
+ * n_inliers (1 int32; 0 when no model), inlier (1 byte per match).
+ * The context may serve one call at a time.  Status: OK, EINVAL, ECUDA.
+ */
+stitch_status stitch_match_homography(stitch_matcher* ctx, const int32_t* xy_a, const uint8_t* desc_a,
+                                      const int32_t* count_a, const int32_t* xy_b, const uint8_t* desc_b,
+                                      const int32_t* count_b, const stitch_match_params* params, const uint8_t* bits,
+                                      const uint32_t* rnd, int32_t* matches, int32_t* n_matches, double* H,
+                                      int32_t* n_inliers, uint8_t* inlier, void* stream);
+
+/* ------------------------------------------------------------------------------------------ */
 /* Batching: several independent rigs stitched by one persistent launch                        */
 
 typedef struct stitch_batch stitch_batch; /* opaque */

@@ -48,6 +48,12 @@ class stitch_lorb_params(ctypes.Structure):
     _fields_ = [("fast_t", ctypes.c_int32), ("harris_t", ctypes.c_int64), ("max_points", ctypes.c_int32)]
 
 
+class stitch_match_params(ctypes.Structure):
+    _fields_ = [("tables", ctypes.c_int32), ("bits", ctypes.c_int32), ("max_dist", ctypes.c_int32),
+                ("ratio_num", ctypes.c_int32), ("ratio_den", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("inlier_px", ctypes.c_double)]
+
+
 class stitch_rig_info(ctypes.Structure):
     _fields_ = [("scratch_bytes", ctypes.c_int64), ("num_kernels", ctypes.c_int32), ("path", ctypes.c_int32),
                 ("roi_pixels", ctypes.c_int64), ("tiles_zero", ctypes.c_int32), ("tiles_solo", ctypes.c_int32),
@@ -81,6 +87,10 @@ SIGNATURES = {
     "stitch_lorb_destroy": (None, [_P]),
     "stitch_lorb_detect": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_int32,
                                           ctypes.POINTER(stitch_lorb_params), _P, _P, _P, _P, _P, _P]),
+    "stitch_matcher_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "stitch_matcher_destroy": (None, [_P]),
+    "stitch_match_homography": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(stitch_match_params), _P,
+                                               _P, _P, _P, _P, _P, _P, _P]),
 }
 
 
@@ -526,3 +536,78 @@ class LORB:
                            pattern, self.xy.data_ptr(), self.resp.data_ptr(), self.desc.data_ptr(),
                            self.count.data_ptr(), _stream_handle(stream))
         return self.xy, self.resp, self.desc, self.count
+
+
+def stitch_matcher_create(max_points: int, max_iters: int, device: int) -> int:
+    out = _P()
+    _check(load().stitch_matcher_create(max_points, max_iters, device, ctypes.byref(out)), "stitch_matcher_create")
+    return out.value
+
+
+def stitch_matcher_destroy(ctx: int) -> None:
+    load().stitch_matcher_destroy(ctx)
+
+
+def stitch_match_homography(ctx: int, xy_a: int, desc_a: int, count_a: int, xy_b: int, desc_b: int, count_b: int,
+                            params, bits, rnd: int, matches: int, n_matches: int, H: int, n_inliers: int,
+                            inlier: int, stream: int) -> None:
+    bt = np.ascontiguousarray(np.asarray(bits, dtype=np.uint8))
+    _check(load().stitch_match_homography(ctx, xy_a, desc_a, count_a, xy_b, desc_b, count_b, ctypes.byref(params),
+                                          bt.ctypes.data, rnd or None, matches, n_matches, H, n_inliers, inlier,
+                                          stream), "stitch_match_homography")
+
+
+class Matcher:
+    """Multi-Probe LSH matching and PROSAC homography on the GPU (Sec. 4.2, Algorithm 3)."""
+
+    def __init__(self, max_points: int = 500, max_iters: int = 1024, device: int | None = None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libstitch needs a CUDA GPU; no CPU fallback exists")
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        self.max_points, self.max_iters = int(max_points), int(max_iters)
+        self.handle = stitch_matcher_create(self.max_points, self.max_iters, self.device)
+        d = f"cuda:{self.device}"
+        self.matches = torch.empty((self.max_points, 3), dtype=torch.int32, device=d)
+        self.n_matches = torch.zeros(1, dtype=torch.int32, device=d)
+        self.H = torch.empty(9, dtype=torch.float64, device=d)
+        self.n_inliers = torch.zeros(1, dtype=torch.int32, device=d)
+        self.inlier = torch.empty(self.max_points, dtype=torch.uint8, device=d)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            stitch_matcher_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def match(self, xy_a, desc_a, count_a, xy_b, desc_b, count_b, bits, rnd, max_dist: int = 80, ratio=(4, 5),
+              inlier_px: float = 3.0, stream=None):
+        """Device tensors: xy (n, 2) int32, desc (n, 32) uint8, count (1,) int32 per image (the
+        outputs of LORB.detect); bits (L, k) host array of descriptor bit positions; rnd (T, 4)
+        uint32/int32 CUDA tensor of random words.  Enqueues the work; returns views (matches,
+        n_matches, H (9,) float64, n_inliers, inlier) of the context's outputs."""
+        for t in (xy_a, desc_a, count_a, xy_b, desc_b, count_b):
+            assert t.is_cuda and t.is_contiguous()
+        bt = np.asarray(bits, dtype=np.uint8)
+        iters = 0 if rnd is None else int(rnd.shape[0])
+        if iters:
+            assert rnd.is_cuda and rnd.is_contiguous() and rnd.element_size() == 4 and rnd.shape[1] == 4
+        prm = stitch_match_params(int(bt.shape[0]), int(bt.shape[1]), int(max_dist), int(ratio[0]), int(ratio[1]),
+                                  iters, float(inlier_px))
+        stitch_match_homography(self.handle, xy_a.data_ptr(), desc_a.data_ptr(), count_a.data_ptr(), xy_b.data_ptr(),
+                                desc_b.data_ptr(), count_b.data_ptr(), prm, bt,
+                                rnd.data_ptr() if iters else 0, self.matches.data_ptr(), self.n_matches.data_ptr(),
+                                self.H.data_ptr(), self.n_inliers.data_ptr(), self.inlier.data_ptr(),
+                                _stream_handle(stream))
+        return self.matches, self.n_matches, self.H, self.n_inliers, self.inlier

@@ -76,3 +76,16 @@ def test_null_rig_calls_are_rejected(lib):
     assert lib.stitch_backward(None, None, None, None, None, None, None) == stitch.STITCH_EINVAL
     assert lib.stitch_rig_get_info(None, None) == stitch.STITCH_EINVAL
     assert lib.stitch_batch_frames(None, None, None, None, None, None) != stitch.STITCH_OK
+
+
+def test_matcher_rejects_bad_arguments_without_a_device(lib):
+    from paper_1810_03988_gb300 import stitch
+    out = ctypes.c_void_p()
+    assert lib.stitch_matcher_create(0, 16, 0, ctypes.byref(out)) == stitch.STITCH_EINVAL
+    assert lib.stitch_matcher_create(4096, 16, 0, ctypes.byref(out)) == stitch.STITCH_EINVAL
+    assert lib.stitch_matcher_create(100, -1, 0, ctypes.byref(out)) == stitch.STITCH_EINVAL
+    assert lib.stitch_matcher_create(100, 16, 0, None) == stitch.STITCH_EINVAL
+    prm = stitch.stitch_match_params(8, 16, 80, 4, 5, 0, 3.0)
+    assert lib.stitch_match_homography(None, None, None, None, None, None, None, ctypes.byref(prm), None, None, None,
+                                       None, None, None, None, None) == stitch.STITCH_EINVAL
+    lib.stitch_matcher_destroy(None)
