@@ -66,6 +66,8 @@ def _load():
             lib.oracle_match_prosac.argtypes = [_I, _P, _P, _I, _P, _P, _I, _I, _P, _I, _I, _I, _D, _I, _P, _P, _P,
                                                 _P, _P, _P]
             lib.oracle_match_prosac.restype = _I
+            lib.oracle_prosac_schedule.argtypes = [_I, _I, _P, _P]
+            lib.oracle_prosac_schedule.restype = _I
             lib.oracle_loss_grad.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _P, _P]
             for f in ("oracle_invert_h", "oracle_reduce", "oracle_expand", "oracle_regions", "oracle_forward",
                       "oracle_warp", "oracle_loss_grad"):
@@ -283,6 +285,14 @@ def lorb(frame, areas, pattern, fast_t: int = 20, harris_t: int = 0, max_points:
     if debug:
         res["resp_map"] = rmap
     return res
+
+
+def prosac_schedule(N: int, T: int):
+    """PROSAC growth schedule for N matches over iterations t = 1..T: (n(t) int32, uniform(t) bool)."""
+    nt = np.zeros(max(T, 1), np.int32)
+    uni = np.zeros(max(T, 1), np.uint8)
+    _check(_load().oracle_prosac_schedule(int(N), int(T), nt.ctypes.data, uni.ctypes.data), "prosac_schedule")
+    return nt[:T], uni[:T].astype(bool)
 
 
 def match_prosac(xy_a, desc_a, xy_b, desc_b, bits, rnd, max_dist: int = 80, ratio=(4, 5), inlier_px: float = 3.0):

@@ -843,7 +843,7 @@ int oracle_lorb(int W, int H, const uint8_t* frame, int64_t pitch, const int32_t
 /*     test ratio_den * d1 < ratio_num * d2 (d2: nearest other probed index; none: passes).    */
 /*  M2 quality order (Algorithm 3, step 1): distance ascending, then query index ascending.    */
 /*  M3 PROSAC (Sec. 4.2.2, Algorithm 3, step 2): the growth schedule of Chum and Matas with     */
-/*     m = 4 and T_N = 200000; iteration t samples the newest of the top n and 3 others from    */
+/*     m = 4 and T_N = 200000 (its increments evaluated exactly in integers); iteration t samples the newest of the top n and 3 others from    */
 /*     the top n - 1 (or 4 from the top n once t exceeds T'_n); samples are drawn without        */
 /*     replacement from given random words (4 per iteration).  Hypothesis: the homography with  */
 /*     h33 = 1 through the 4 pairs (8x8 Gaussian elimination, partial pivoting, ties to the     */
@@ -853,8 +853,8 @@ int oracle_lorb(int W, int H, const uint8_t* frame, int64_t pitch, const int32_t
 /*     normalised units of image B).  Best: most inliers, ties to the earlier iteration; then   */
 /*     least squares on its inliers (normal equations summed in quality order, same solver),    */
 /*     returned in pixel coordinates with h33 = 1.                                              */
-/*  All in IEEE double without contractions, so that a device implementation in the same    */
-/*  operation order takes the same decisions.                                                 */
+/*  Geometry in IEEE double without contractions, so that a device implementation in the    */
+/*  same operation order takes the same decisions.                                            */
 /* ------------------------------------------------------------------------------------------ */
 
 static int hamming256(const uint8_t* a, const uint8_t* b) {
@@ -922,23 +922,31 @@ static int is_inlier(const double h[8], double x, double y, double u, double v, 
     return pu * pu + pv * pv < t2;
 }
 
-/* PROSAC schedule: n(t) and whether iteration t samples uniformly from the top n (t = 1..T) */
+/* PROSAC growth schedule (m = 4, T_N = 200000): T_n = T_N C(n, m) / C(N, m) is the expected
+ * number of the T_N samples drawn from the top n; the top n grows to n + 1 at iteration T'_n, with
+ * T'_m = 1 and T'_{n+1} = T'_n + ceil(T_{n+1} - T_n).  The increment is evaluated exactly:
+ * T_{n+1} - T_n = T_N m n (n-1) (n-2) / (N (N-1) (N-2) (N-3)), an integer ceiling division.
+ * Output for t = 1..T: n(t), and whether the schedule has passed (T'_n < t: sample uniformly
+ * from the top n). */
 static void prosac_schedule(int N, int T, int* nt, uint8_t* uni) {
-    const int m = 4;
-    double Tn = 200000.0;
-    for (int i = 0; i < m; ++i) Tn = Tn * (double)(m - i) / (double)(N - i);
-    int n = m;
-    double Tp = 1.0;
+    const long long Q = (long long)N * (N - 1) * (N - 2) * (N - 3);
+    int n = 4;
+    long long Tp = 1;
     for (int t = 1; t <= T; ++t) {
-        if ((double)t == Tp && n < N) {
-            const double Tn1 = Tn * (double)(n + 1) / (double)(n + 1 - m);
-            Tp = Tp + ceil(Tn1 - Tn);
-            Tn = Tn1;
+        if (t == Tp && n < N) {
+            const long long num = 800000LL * n * (n - 1) * (n - 2);
+            Tp += (num + Q - 1) / Q;
             n = n + 1;
         }
         nt[t - 1] = n;
-        uni[t - 1] = Tp < (double)t ? 1 : 0;
+        uni[t - 1] = Tp < t ? 1 : 0;
     }
+}
+
+int oracle_prosac_schedule(int N, int T, int32_t* nt, uint8_t* uni) {
+    if (N < 4 || N > 65536 || T < 0 || (T > 0 && (!nt || !uni))) return OR_EINVAL;
+    prosac_schedule(N, T, nt, uni);
+    return OR_OK;
 }
 
 /* the j-th smallest element of {0..n-1} not in chosen[0..c) */

@@ -23,6 +23,8 @@ namespace {
 
 constexpr int MT_MAX_POINTS = 2048;
 constexpr int MT_MAX_TABLES = 32, MT_MAX_BITS = 20;
+constexpr int MT_DIR_BITS = 11;                        // radix directory of each sorted table
+constexpr int MT_DIR = (1 << MT_DIR_BITS) + 1;
 
 struct LshBits {
     int L, k;
@@ -57,7 +59,7 @@ __device__ __forceinline__ int hamming(const unsigned* a, const unsigned* b) {
 // one block per table: keys of image B's descriptors, sorted by (key, index)
 __global__ void __launch_bounds__(1024) mt_build(const unsigned* __restrict__ desc_b, const int* __restrict__ count_b,
                                                  const __grid_constant__ LshBits lb, unsigned* __restrict__ keys,
-                                                 int* __restrict__ ord, int cap) {
+                                                 int* __restrict__ ord, int* __restrict__ dir, int cap) {
     __shared__ unsigned long long e[MT_MAX_POINTS];
     const int l = blockIdx.x, nb = min(*count_b, cap);
     int m = 1;
@@ -82,6 +84,18 @@ __global__ void __launch_bounds__(1024) mt_build(const unsigned* __restrict__ de
         keys[(size_t)l * cap + i] = (unsigned)(e[i] >> 32);
         ord[(size_t)l * cap + i] = (int)(unsigned)e[i];
     }
+    // directory: dir[v] = first sorted position whose key's top bits are >= v (v = 0..2^D)
+    const int D = lb.k < MT_DIR_BITS ? lb.k : MT_DIR_BITS, shift = lb.k - D;
+    for (int v = threadIdx.x; v <= (1 << D); v += blockDim.x) {
+        const unsigned long long bound = (unsigned long long)v << shift;
+        int lo = 0, hi = nb;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((e[mid] >> 32) < bound) lo = mid + 1;
+            else hi = mid;
+        }
+        dir[(size_t)l * MT_DIR + v] = lo;
+    }
 }
 
 struct Top2 {
@@ -103,14 +117,16 @@ __device__ __forceinline__ void top2_add(Top2& t, int d, int b) {
 }
 
 // a warp per query: lanes take the (table, probe) pairs; (nearest, second nearest other index)
-// merged across lanes
+// merged across lanes.  A bucket is located through the table's directory (the range of sorted
+// positions whose key has given top bits), then by binary search inside that range.
 __global__ void __launch_bounds__(256) mt_query(const unsigned* __restrict__ desc_a, const int* __restrict__ count_a,
                                                 const unsigned* __restrict__ desc_b, const int* __restrict__ count_b,
                                                 const __grid_constant__ LshBits lb, const unsigned* __restrict__ keys,
-                                                const int* __restrict__ ord, int cap, int max_dist, int rnum, int rden,
-                                                int* __restrict__ best) {
+                                                const int* __restrict__ ord, const int* __restrict__ dir, int cap,
+                                                int max_dist, int rnum, int rden, int* __restrict__ best) {
     const int a = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     const int na = min(*count_a, cap), nb = min(*count_b, cap);
+    const int shift = lb.k > MT_DIR_BITS ? lb.k - MT_DIR_BITS : 0;
     if (a >= na) return;
     unsigned da[8];
 #pragma unroll
@@ -123,7 +139,8 @@ __global__ void __launch_bounds__(256) mt_query(const unsigned* __restrict__ des
         const unsigned q0 = lsh_key(da, lb, l);
         const unsigned q = p < 0 ? q0 : (q0 ^ (1u << p));
         const unsigned* kl = keys + (size_t)l * cap;
-        int lo = 0, hi = nb;
+        const int* dl = dir + (size_t)l * MT_DIR;
+        int lo = dl[q >> shift], hi = dl[(q >> shift) + 1];
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (kl[mid] < q) lo = mid + 1;
@@ -223,42 +240,68 @@ __global__ void __launch_bounds__(1024) mt_order(const int* __restrict__ best, c
     }
 }
 
-__device__ __forceinline__ void norm_pair(const Norm& z, const int* xy_a, const int* xy_b, const int* mt, int i,
-                                          double& x, double& y, double& u, double& v) {
-    const int a = mt[3 * i], b = mt[3 * i + 1];
-    x = dM(dS((double)xy_a[2 * a], z.ca0), z.sa);
-    y = dM(dS((double)xy_a[2 * a + 1], z.ca1), z.sa);
-    u = dM(dS((double)xy_b[2 * b], z.cb0), z.sb);
-    v = dM(dS((double)xy_b[2 * b + 1], z.cb1), z.sb);
+// M h = r by Gaussian elimination with partial pivoting (the first row of largest |M[i][c]|; a
+// pivot below 1e-12 in magnitude, or NaN, means singular), then back substitution.  Fully
+// unrolled so that M stays in registers: the row exchange is a select per element.  |x| of a
+// finite or infinite double orders like its bit pattern read as an integer.
+__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffll; }
+
+template <int c>
+__device__ __forceinline__ bool elim_column(double (&M)[8][8], double (&r)[8]) {
+    long long best = abs_bits(M[c][c]);
+    int p = c;
+#pragma unroll
+    for (int i = c + 1; i < 8; ++i) {
+        const long long a = abs_bits(M[i][c]);
+        if (a > best) {
+            best = a;
+            p = i;
+        }
+    }
+    if (best < __double_as_longlong(1e-12) || best > 0x7ff0000000000000ll) return false;
+#pragma unroll
+    for (int i = c + 1; i < 8; ++i) {
+        const bool sw = i == p;
+#pragma unroll
+        for (int j = c; j < 8; ++j) {  // columns left of c are never read again
+            const double a = M[c][j], b = M[i][j];
+            M[c][j] = sw ? b : a;
+            M[i][j] = sw ? a : b;
+        }
+        const double a = r[c], b = r[i];
+        r[c] = sw ? b : a;
+        r[i] = sw ? a : b;
+    }
+#pragma unroll
+    for (int i = c + 1; i < 8; ++i) {
+        const double f = dD(M[i][c], M[c][c]);
+#pragma unroll
+        for (int j = c; j < 8; ++j) M[i][j] = dS(M[i][j], dM(f, M[c][j]));
+        r[i] = dS(r[i], dM(f, r[c]));
+    }
+    return true;
 }
 
-__device__ bool solve8(double M[8][8], double r[8], double h[8]) {
-    for (int c = 0; c < 8; ++c) {
-        int p = c;
-        for (int i = c + 1; i < 8; ++i)
-            if (fabs(M[i][c]) > fabs(M[p][c])) p = i;
-        if (!(fabs(M[p][c]) >= 1e-12)) return false;
-        if (p != c) {
-            for (int j = 0; j < 8; ++j) {
-                const double tt = M[c][j];
-                M[c][j] = M[p][j];
-                M[p][j] = tt;
-            }
-            const double tt = r[c];
-            r[c] = r[p];
-            r[p] = tt;
-        }
-        for (int i = c + 1; i < 8; ++i) {
-            const double f = dD(M[i][c], M[c][c]);
-            for (int j = c; j < 8; ++j) M[i][j] = dS(M[i][j], dM(f, M[c][j]));
-            r[i] = dS(r[i], dM(f, r[c]));
-        }
-    }
-    for (int c = 7; c >= 0; --c) {
-        double s = r[c];
-        for (int j = c + 1; j < 8; ++j) s = dS(s, dM(M[c][j], h[j]));
-        h[c] = dD(s, M[c][c]);
-    }
+template <int c>
+__device__ __forceinline__ void back_row(const double (&M)[8][8], const double (&r)[8], double (&h)[8]) {
+    double s = r[c];
+#pragma unroll
+    for (int j = c + 1; j < 8; ++j) s = dS(s, dM(M[c][j], h[j]));
+    h[c] = dD(s, M[c][c]);
+}
+
+__device__ __forceinline__ bool solve8(double (&M)[8][8], double (&r)[8], double (&h)[8]) {
+    if (!elim_column<0>(M, r) || !elim_column<1>(M, r) || !elim_column<2>(M, r) || !elim_column<3>(M, r) ||
+        !elim_column<4>(M, r) || !elim_column<5>(M, r) || !elim_column<6>(M, r) || !elim_column<7>(M, r))
+        return false;
+    back_row<7>(M, r, h);
+    back_row<6>(M, r, h);
+    back_row<5>(M, r, h);
+    back_row<4>(M, r, h);
+    back_row<3>(M, r, h);
+    back_row<2>(M, r, h);
+    back_row<1>(M, r, h);
+    back_row<0>(M, r, h);
     return true;
 }
 
@@ -270,24 +313,69 @@ __device__ __forceinline__ bool inlier(const double h[8], double x, double y, do
     return dA(dM(pu, pu), dM(pv, pv)) < t2;
 }
 
-// the growth schedule (sequential recurrence, one thread)
-__global__ void mt_schedule(const int* __restrict__ n_matches, int iters, int* __restrict__ nt,
-                            unsigned char* __restrict__ uni) {
-    const int N = *n_matches, m = 4;
-    if (N < m) return;
-    double Tn = 200000.0;
-    for (int i = 0; i < m; ++i) Tn = dD(dM(Tn, (double)(m - i)), (double)(N - i));
-    int n = m;
-    double Tp = 1.0;
-    for (int t = 1; t <= iters; ++t) {
-        if ((double)t == Tp && n < N) {
-            const double Tn1 = dD(dM(Tn, (double)(n + 1)), (double)(n + 1 - m));
-            Tp = dA(Tp, ceil(dS(Tn1, Tn)));
-            Tn = Tn1;
-            n = n + 1;
+// one block: the normalised coordinates (x, y, u, v) of every match, and the PROSAC growth
+// schedule.  The top n grows to n + 1 at iteration E_j (j = n - 4), E_0 = 1 and E_{j+1} = E_j +
+// ceil(T_N m n (n-1) (n-2) / (N (N-1) (N-2) (N-3))) (m = 4, T_N = 200000: the exact increment
+// T_{n+1} - T_n of T_n = T_N C(n, m) / C(N, m)), up to n = N; E by a block scan.  For iteration t:
+// c = #{j < N - 4 : E_j <= t}, n(t) = 4 + c, uniform sampling when E_c < t.
+__global__ void __launch_bounds__(1024) mt_prep(const int* __restrict__ n_matches, const int* __restrict__ mt,
+                                                const int* __restrict__ xy_a, const int* __restrict__ xy_b,
+                                                const Norm* __restrict__ norm, int iters, double* __restrict__ xyuv,
+                                                int* __restrict__ nt, unsigned char* __restrict__ uni) {
+    __shared__ long long E[MT_MAX_POINTS];
+    __shared__ long long wsum[32];
+    const int N = *n_matches, tid = threadIdx.x;
+    const Norm z = *norm;
+    for (int i = tid; i < N; i += blockDim.x) {
+        const int a = mt[3 * i], b = mt[3 * i + 1];
+        xyuv[4 * i] = dM(dS((double)xy_a[2 * a], z.ca0), z.sa);
+        xyuv[4 * i + 1] = dM(dS((double)xy_a[2 * a + 1], z.ca1), z.sa);
+        xyuv[4 * i + 2] = dM(dS((double)xy_b[2 * b], z.cb0), z.sb);
+        xyuv[4 * i + 3] = dM(dS((double)xy_b[2 * b + 1], z.cb1), z.sb);
+    }
+    if (N < 4 || iters == 0) return;
+    const int K = N - 4;  // growth events j = 0..K-1 (n = 4 + j)
+    const long long Q = (long long)N * (N - 1) * (N - 2) * (N - 3);
+    long long d[2] = {0, 0};
+    for (int e = 0; e < 2; ++e) {
+        const int j = 2 * tid + e;
+        if (j < K) {
+            const long long n = 4 + j;
+            d[e] = (800000LL * n * (n - 1) * (n - 2) + Q - 1) / Q;
         }
-        nt[t - 1] = n;
-        uni[t - 1] = Tp < (double)t ? 1 : 0;
+    }
+    // inclusive scan of the pair sums over the block
+    long long v = d[0] + d[1];
+    const int lane = tid & 31, w = tid >> 5;
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long o = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += o;
+    }
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        long long x = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long o = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += o;
+        }
+        wsum[lane] = x;
+    }
+    __syncthreads();
+    const long long excl = v - (d[0] + d[1]) + (w > 0 ? wsum[w - 1] : 0);
+    // E_j = 1 + sum_{i<j} d_i for j = 0..K
+    if (2 * tid <= K) E[2 * tid] = 1 + excl;
+    if (2 * tid + 1 <= K) E[2 * tid + 1] = 1 + excl + d[0];
+    __syncthreads();
+    for (int t = tid + 1; t <= iters; t += blockDim.x) {
+        int lo = 0, hi = K;  // c = first j in [0, K) with E_j > t, else K
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (E[mid] <= t) lo = mid + 1;
+            else hi = mid;
+        }
+        nt[t - 1] = 4 + lo;
+        uni[t - 1] = E[lo] < t ? 1 : 0;
     }
 }
 
@@ -305,18 +393,16 @@ __device__ __forceinline__ int nth_free(int j, const int* chosen, int c) {
     return j;
 }
 
-// one thread per iteration: its sample and 4-point hypothesis (valid flag 0 when singular)
-__global__ void __launch_bounds__(128) mt_hypotheses(const int* __restrict__ n_matches, int iters,
-                                                     const int* __restrict__ nt, const unsigned char* __restrict__ uni,
-                                                     const unsigned* __restrict__ rnd, const int* __restrict__ mt,
-                                                     const int* __restrict__ xy_a, const int* __restrict__ xy_b,
-                                                     const Norm* __restrict__ norm, double* __restrict__ hyp,
-                                                     int* __restrict__ valid) {
+// one thread per iteration: its sample and 4-point hypothesis (valid flag 0 when singular).
+// Small blocks spread the FP64 work over many SMs.
+__global__ void __launch_bounds__(32) mt_hypotheses(const int* __restrict__ n_matches, int iters,
+                                                    const int* __restrict__ nt, const unsigned char* __restrict__ uni,
+                                                    const unsigned* __restrict__ rnd, const double* __restrict__ xyuv,
+                                                    double* __restrict__ hyp, int* __restrict__ valid) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= iters) return;
     valid[t] = 0;
     if (*n_matches < 4) return;
-    const Norm z = *norm;
     const int n = nt[t];
     const unsigned* rw = rnd + 4 * (size_t)t;
     int idx[4];
@@ -331,25 +417,32 @@ __global__ void __launch_bounds__(128) mt_hypotheses(const int* __restrict__ n_m
         }
     }
     double M[8][8], r[8], h[8];
+#pragma unroll
     for (int k = 0; k < 4; ++k) {
-        double x, y, u, v;
-        norm_pair(z, xy_a, xy_b, mt, idx[k], x, y, u, v);
-        double* m0 = M[2 * k];
-        double* m1 = M[2 * k + 1];
-        m0[0] = x; m0[1] = y; m0[2] = 1.0; m0[3] = 0.0; m0[4] = 0.0; m0[5] = 0.0; m0[6] = -dM(u, x); m0[7] = -dM(u, y);
-        m1[0] = 0.0; m1[1] = 0.0; m1[2] = 0.0; m1[3] = x; m1[4] = y; m1[5] = 1.0; m1[6] = -dM(v, x); m1[7] = -dM(v, y);
-        r[2 * k] = u;
-        r[2 * k + 1] = v;
+        const double x = xyuv[4 * idx[k]], y = xyuv[4 * idx[k] + 1];
+        const double u = xyuv[4 * idx[k] + 2], v = xyuv[4 * idx[k] + 3];
+        const int a = 2 * k, b = 2 * k + 1;
+        M[a][0] = x; M[a][1] = y; M[a][2] = 1.0; M[a][3] = 0.0; M[a][4] = 0.0; M[a][5] = 0.0;
+        M[a][6] = -dM(u, x); M[a][7] = -dM(u, y);
+        M[b][0] = 0.0; M[b][1] = 0.0; M[b][2] = 0.0; M[b][3] = x; M[b][4] = y; M[b][5] = 1.0;
+        M[b][6] = -dM(v, x); M[b][7] = -dM(v, y);
+        r[a] = u;
+        r[b] = v;
     }
     if (!solve8(M, r, h)) return;
+#pragma unroll
     for (int k = 0; k < 8; ++k) hyp[8 * (size_t)t + k] = h[k];
     valid[t] = 1;
 }
 
+__device__ __forceinline__ double inlier_t2(double inlier_px, const Norm& z) {
+    const double tn = dM(inlier_px, z.sb);
+    return dM(tn, tn);
+}
+
 // one block per hypothesis: its inlier count (-1 when not valid)
 __global__ void __launch_bounds__(256) mt_score(const int* __restrict__ n_matches, const double* __restrict__ hyp,
-                                                const int* __restrict__ valid, const int* __restrict__ mt,
-                                                const int* __restrict__ xy_a, const int* __restrict__ xy_b,
+                                                const int* __restrict__ valid, const double* __restrict__ xyuv,
                                                 const Norm* __restrict__ norm, double inlier_px,
                                                 int* __restrict__ counts) {
     __shared__ int s_c;
@@ -358,39 +451,30 @@ __global__ void __launch_bounds__(256) mt_score(const int* __restrict__ n_matche
         if (threadIdx.x == 0) counts[t] = -1;
         return;
     }
-    const Norm z = *norm;
     const int nm = *n_matches;
     double h[8];
     for (int k = 0; k < 8; ++k) h[k] = hyp[8 * (size_t)t + k];
-    const double tn = dM(inlier_px, z.sb), t2 = dM(tn, tn);
+    const double t2 = inlier_t2(inlier_px, *norm);
     if (threadIdx.x == 0) s_c = 0;
     __syncthreads();
     int c = 0;
-    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
-        double x, y, u, v;
-        norm_pair(z, xy_a, xy_b, mt, i, x, y, u, v);
-        c += inlier(h, x, y, u, v, t2);
-    }
+    for (int i = threadIdx.x; i < nm; i += blockDim.x)
+        c += inlier(h, xyuv[4 * i], xyuv[4 * i + 1], xyuv[4 * i + 2], xyuv[4 * i + 3], t2);
     for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(0xffffffffu, c, off);
     if ((threadIdx.x & 31) == 0) atomicAdd(&s_c, c);
     __syncthreads();
     if (threadIdx.x == 0) counts[t] = s_c;
 }
 
-// one block: the best hypothesis, the inlier flags, the least-squares refit (each normal-equation
-// entry summed by one thread over the inliers in quality order), back to pixels
-__global__ void __launch_bounds__(256) mt_refit(const int* __restrict__ n_matches, int iters,
-                                                const double* __restrict__ hyp, const int* __restrict__ counts,
-                                                const int* __restrict__ mt, const int* __restrict__ xy_a,
-                                                const int* __restrict__ xy_b, const Norm* __restrict__ norm,
-                                                double inlier_px, double* __restrict__ H, int* __restrict__ n_inliers,
-                                                unsigned char* __restrict__ inl) {
-    __shared__ int s_best, s_cnt;
-    __shared__ double Ms[8][8], rs[8];
-    const int nm = *n_matches, t = threadIdx.x;
-    const Norm z = *norm;
-    // best: most inliers, ties to the earliest iteration (a strided scan per thread, then the block)
+// one block: the best hypothesis (most inliers, ties to the earliest iteration) and its inlier
+// flags; best = {iteration or -1, count}
+__global__ void __launch_bounds__(256) mt_best(const int* __restrict__ n_matches, int iters,
+                                               const double* __restrict__ hyp, const int* __restrict__ counts,
+                                               const double* __restrict__ xyuv, const Norm* __restrict__ norm,
+                                               double inlier_px, int* __restrict__ best, unsigned char* __restrict__ inl) {
     __shared__ long long s_red[8];
+    __shared__ int s_best;
+    const int nm = *n_matches, t = threadIdx.x;
     long long key = -1;  // (count + 1) << 32 | (2^32 - 1 - t): larger is better
     if (nm >= 4)
         for (int k = t; k < iters; k += blockDim.x) {
@@ -406,50 +490,104 @@ __global__ void __launch_bounds__(256) mt_refit(const int* __restrict__ n_matche
     if (t == 0) {
         long long b = s_red[0];
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = s_red[w] > b ? s_red[w] : b;
-        // an invalid hypothesis (count -1) never wins: key (0 << 32 | .) counts as no model
-        s_best = (b >> 32) > 0 ? (int)(0xffffffffu - (unsigned)(b & 0xffffffffll)) : -1;
-        s_cnt = (int)(b >> 32) - 1;
-        for (int i = 0; i < 9; ++i) H[i] = i % 4 == 0 ? 1.0 : 0.0;
-        *n_inliers = 0;
+        // invalid hypotheses (count -1) have key (0 << 32 | .): no model
+        const int bt = (b >> 32) > 0 ? (int)(0xffffffffu - (unsigned)(b & 0xffffffffll)) : -1;
+        const int bc = (int)(b >> 32) - 1;
+        s_best = bt >= 0 && bc >= 4 ? bt : -1;
+        best[0] = s_best;
+        best[1] = bc;
     }
     __syncthreads();
     const int bt = s_best;
-    for (int i = t; i < nm; i += blockDim.x) inl[i] = 0;
-    if (bt < 0 || s_cnt < 4) return;
-    double hb[8];
-    for (int k = 0; k < 8; ++k) hb[k] = hyp[8 * (size_t)bt + k];
-    const double tn = dM(inlier_px, z.sb), t2 = dM(tn, tn);
-    for (int i = t; i < nm; i += blockDim.x) {
-        double x, y, u, v;
-        norm_pair(z, xy_a, xy_b, mt, i, x, y, u, v);
-        inl[i] = inlier(hb, x, y, u, v, t2) ? 1 : 0;
+    if (bt < 0) {
+        for (int i = t; i < nm; i += blockDim.x) inl[i] = 0;
+        return;
     }
-    __syncthreads();
-    // entries: 64 of M (p, q) and 8 of r
-    if (t < 72) {
-        const int p = t < 64 ? t / 8 : t - 64, q = t < 64 ? t % 8 : 0;
-        double acc = 0.0;
-        for (int i = 0; i < nm; ++i) {
-            if (!inl[i]) continue;
-            double x, y, u, v;
-            norm_pair(z, xy_a, xy_b, mt, i, x, y, u, v);
-            const double row0[8] = {x, y, 1.0, 0.0, 0.0, 0.0, -dM(u, x), -dM(u, y)};
-            const double row1[8] = {0.0, 0.0, 0.0, x, y, 1.0, -dM(v, x), -dM(v, y)};
-            if (t < 64) acc = dA(dA(acc, dM(row0[p], row0[q])), dM(row1[p], row1[q]));
-            else acc = dA(dA(acc, dM(row0[p], u)), dM(row1[p], v));
+    double h[8];
+    for (int k = 0; k < 8; ++k) h[k] = hyp[8 * (size_t)bt + k];
+    const double t2 = inlier_t2(inlier_px, *norm);
+    for (int i = t; i < nm; i += blockDim.x)
+        inl[i] = inlier(h, xyuv[4 * i], xyuv[4 * i + 1], xyuv[4 * i + 2], xyuv[4 * i + 3], t2) ? 1 : 0;
+}
+
+// the least-squares normal equations on the best hypothesis' inliers: 64 entries of M and 8 of r,
+// one warp each.  The two DLT rows of a match are
+//   row0 = (x, y, 1, 0, 0, 0, -ux, -uy), row1 = (0, 0, 0, x, y, 1, -vx, -vy),
+// M[p][q] += row0[p] row0[q] + row1[p] row1[q], r[p] += row0[p] u + row1[p] v, in quality order.
+// The lanes form the products (32 matches at a time, stored in quality order); one lane sums them
+// in order.  A product with a structural zero adds +-0 to a sum that is never
+// -0, so it is skipped without changing a bit.
+__global__ void __launch_bounds__(32) mt_sums(const int* __restrict__ n_matches, const int* __restrict__ best,
+                                              const unsigned char* __restrict__ inl, const double* __restrict__ xyuv,
+                                              double* __restrict__ sums) {
+    if (best[0] < 0) return;
+    const int nm = *n_matches, lane = threadIdx.x;
+    const int e = blockIdx.x;
+    const bool isr = e >= 64;
+    const int p = isr ? e - 64 : e / 8, q = isr ? 0 : e % 8;
+    const bool p0 = p < 3 || p > 5, p1 = p > 2, q0 = q < 3 || q > 5, q1 = q > 2;
+    const bool use0 = isr ? p0 : (p0 && q0), use1 = isr ? p1 : (p1 && q1);
+    auto r0 = [](int k, double x, double y, double u) {
+        return k == 0 ? x : k == 1 ? y : k == 2 ? 1.0 : k == 6 ? -dM(u, x) : -dM(u, y);
+    };
+    auto r1 = [](int k, double x, double y, double v) {
+        return k == 3 ? x : k == 4 ? y : k == 5 ? 1.0 : k == 6 ? -dM(v, x) : -dM(v, y);
+    };
+    // the products of every inlier, in quality order, into shared memory
+    __shared__ double s0[MT_MAX_POINTS], s1[MT_MAX_POINTS];
+    int n = 0;
+    for (int i0 = 0; i0 < nm; i0 += 32) {
+        const int i = i0 + lane;
+        const bool f = i < nm && inl[i];
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (f) {
+            const double x = xyuv[4 * i], y = xyuv[4 * i + 1], u = xyuv[4 * i + 2], v = xyuv[4 * i + 3];
+            const int pos = n + __popc(bal & ((1u << lane) - 1u));
+            s0[pos] = use0 ? dM(r0(p, x, y, u), isr ? u : r0(q, x, y, u)) : 0.0;
+            s1[pos] = use1 ? dM(r1(p, x, y, v), isr ? v : r1(q, x, y, v)) : 0.0;
         }
-        if (t < 64) Ms[p][q] = acc;
-        else rs[p] = acc;
+        n += __popc(bal);
     }
-    __syncthreads();
-    if (t != 0) return;
+    __syncwarp();
+    if (lane != 0) return;
+    double acc = 0.0;
+    if (use0 && use1) {
+#pragma unroll 8
+        for (int j = 0; j < n; ++j) acc = dA(dA(acc, s0[j]), s1[j]);
+    } else if (use0) {
+#pragma unroll 8
+        for (int j = 0; j < n; ++j) acc = dA(acc, s0[j]);
+    } else if (use1) {
+#pragma unroll 8
+        for (int j = 0; j < n; ++j) acc = dA(acc, s1[j]);
+    }
+    sums[e] = acc;
+}
+
+// one thread: solve the normal equations (the 4-point hypothesis when singular), back to pixels
+// H = Tb^-1 Hn Ta, h33 = 1; identity and 0 inliers when there is no model
+__global__ void mt_solve(const int* __restrict__ best, const double* __restrict__ hyp,
+                         const double* __restrict__ sums, const Norm* __restrict__ norm, double* __restrict__ H,
+                         int* __restrict__ n_inliers) {
+    const int bt = best[0];
+    if (bt < 0) {
+        for (int i = 0; i < 9; ++i) H[i] = i % 4 == 0 ? 1.0 : 0.0;
+        *n_inliers = 0;
+        return;
+    }
+    const Norm z = *norm;
     double M[8][8], r[8], h[8];
+#pragma unroll
     for (int p = 0; p < 8; ++p) {
-        for (int q = 0; q < 8; ++q) M[p][q] = Ms[p][q];
-        r[p] = rs[p];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) M[p][q] = sums[8 * p + q];
+        r[p] = sums[64 + p];
     }
-    const double* hn = solve8(M, r, h) ? h : hb;
-    const double Hn[9] = {hn[0], hn[1], hn[2], hn[3], hn[4], hn[5], hn[6], hn[7], 1.0};
+    if (!solve8(M, r, h)) {
+#pragma unroll
+        for (int p = 0; p < 8; ++p) h[p] = hyp[8 * (size_t)bt + p];
+    }
+    const double Hn[9] = {h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7], 1.0};
     const double Ta[9] = {z.sa, 0.0, -dM(z.sa, z.ca0), 0.0, z.sa, -dM(z.sa, z.ca1), 0.0, 0.0, 1.0};
     const double Tbi[9] = {dD(1.0, z.sb), 0.0, z.cb0, 0.0, dD(1.0, z.sb), z.cb1, 0.0, 0.0, 1.0};
     double P[9], Q[9];
@@ -460,7 +598,7 @@ __global__ void __launch_bounds__(256) mt_refit(const int* __restrict__ n_matche
         for (int j = 0; j < 3; ++j)
             Q[3 * i + j] = dA(dA(dM(Tbi[3 * i], P[j]), dM(Tbi[3 * i + 1], P[3 + j])), dM(Tbi[3 * i + 2], P[6 + j]));
     for (int i = 0; i < 9; ++i) H[i] = dD(Q[i], Q[8]);
-    *n_inliers = s_cnt;
+    *n_inliers = best[1];
 }
 
 }  // namespace
@@ -469,6 +607,7 @@ struct stitch_matcher {
     int device = 0, max_points = 0, max_iters = 0;
     unsigned* keys = nullptr;
     int* ord = nullptr;
+    int* dir = nullptr;
     int* best = nullptr;
     Norm* norm = nullptr;
     int* nt = nullptr;
@@ -476,12 +615,16 @@ struct stitch_matcher {
     double* hyp = nullptr;
     int* valid = nullptr;
     int* counts = nullptr;
+    double* xyuv = nullptr;
+    int* pick = nullptr;  // best hypothesis: iteration (or -1), inlier count
+    double* sums = nullptr;
 };
 
 static void matcher_free(stitch_matcher* c) {
     if (!c) return;
     cudaFree(c->keys);
     cudaFree(c->ord);
+    cudaFree(c->dir);
     cudaFree(c->best);
     cudaFree(c->norm);
     cudaFree(c->nt);
@@ -489,6 +632,9 @@ static void matcher_free(stitch_matcher* c) {
     cudaFree(c->hyp);
     cudaFree(c->valid);
     cudaFree(c->counts);
+    cudaFree(c->xyuv);
+    cudaFree(c->pick);
+    cudaFree(c->sums);
     delete c;
 }
 
@@ -514,11 +660,14 @@ extern "C" stitch_status stitch_matcher_create(int32_t max_points, int32_t max_i
     const size_t it = (size_t)std::max(max_iters, 1);
     bool okm = cudaMalloc(&c->keys, sizeof(unsigned) * MT_MAX_TABLES * max_points) == cudaSuccess &&
                cudaMalloc(&c->ord, sizeof(int) * MT_MAX_TABLES * max_points) == cudaSuccess &&
+               cudaMalloc(&c->dir, sizeof(int) * MT_MAX_TABLES * MT_DIR) == cudaSuccess &&
                cudaMalloc(&c->best, sizeof(int) * 2 * max_points) == cudaSuccess &&
                cudaMalloc(&c->norm, sizeof(Norm)) == cudaSuccess && cudaMalloc(&c->nt, sizeof(int) * it) == cudaSuccess &&
                cudaMalloc(&c->uni, it) == cudaSuccess && cudaMalloc(&c->hyp, sizeof(double) * 8 * it) == cudaSuccess &&
                cudaMalloc(&c->valid, sizeof(int) * it) == cudaSuccess &&
-               cudaMalloc(&c->counts, sizeof(int) * it) == cudaSuccess;
+               cudaMalloc(&c->counts, sizeof(int) * it) == cudaSuccess &&
+               cudaMalloc(&c->xyuv, sizeof(double) * 4 * max_points) == cudaSuccess &&
+               cudaMalloc(&c->pick, sizeof(int) * 2) == cudaSuccess && cudaMalloc(&c->sums, sizeof(double) * 72) == cudaSuccess;
     if (prev >= 0) cudaSetDevice(prev);
     if (!okm) {
         cudaGetLastError();
@@ -565,20 +714,20 @@ extern "C" stitch_status stitch_match_homography(stitch_matcher* c, const int32_
     const int cap = c->max_points;
     const unsigned* da = reinterpret_cast<const unsigned*>(desc_a);
     const unsigned* db = reinterpret_cast<const unsigned*>(desc_b);
-    mt_build<<<lb.L, 1024, 0, s>>>(db, count_b, lb, c->keys, c->ord, cap);
-    mt_query<<<(cap + 7) / 8, 256, 0, s>>>(da, count_a, db, count_b, lb, c->keys, c->ord, cap, prm->max_dist,
-                                           prm->ratio_num, prm->ratio_den, c->best);
+    mt_build<<<lb.L, 1024, 0, s>>>(db, count_b, lb, c->keys, c->ord, c->dir, cap);
+    mt_query<<<(cap + 7) / 8, 256, 0, s>>>(da, count_a, db, count_b, lb, c->keys, c->ord, c->dir, cap,
+                                           prm->max_dist, prm->ratio_num, prm->ratio_den, c->best);
     mt_order<<<1, 1024, 0, s>>>(c->best, count_a, cap, xy_a, xy_b, matches, n_matches, c->norm);
     const int iters = prm->iters;
+    mt_prep<<<1, 1024, 0, s>>>(n_matches, matches, xy_a, xy_b, c->norm, iters, c->xyuv, c->nt, c->uni);
     if (iters > 0) {
-        mt_schedule<<<1, 1, 0, s>>>(n_matches, iters, c->nt, c->uni);
-        mt_hypotheses<<<(iters + 127) / 128, 128, 0, s>>>(n_matches, iters, c->nt, c->uni, rnd, matches, xy_a, xy_b,
-                                                          c->norm, c->hyp, c->valid);
-        mt_score<<<iters, 256, 0, s>>>(n_matches, c->hyp, c->valid, matches, xy_a, xy_b, c->norm, prm->inlier_px,
-                                       c->counts);
+        mt_hypotheses<<<(iters + 31) / 32, 32, 0, s>>>(n_matches, iters, c->nt, c->uni, rnd, c->xyuv, c->hyp,
+                                                       c->valid);
+        mt_score<<<iters, 256, 0, s>>>(n_matches, c->hyp, c->valid, c->xyuv, c->norm, prm->inlier_px, c->counts);
     }
-    mt_refit<<<1, 256, 0, s>>>(n_matches, iters, c->hyp, c->counts, matches, xy_a, xy_b, c->norm, prm->inlier_px, H,
-                               n_inliers, inlier);
+    mt_best<<<1, 256, 0, s>>>(n_matches, iters, c->hyp, c->counts, c->xyuv, c->norm, prm->inlier_px, c->pick, inlier);
+    mt_sums<<<72, 32, 0, s>>>(n_matches, c->pick, inlier, c->xyuv, c->sums);
+    mt_solve<<<1, 1, 0, s>>>(c->pick, c->hyp, c->sums, c->norm, H, n_inliers);
     stitch_status st = cudaGetLastError() == cudaSuccess ? STITCH_OK : STITCH_ECUDA;
     if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
     return st;

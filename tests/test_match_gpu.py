@@ -155,3 +155,65 @@ def test_context_reuse_and_bad_arguments():
         with pytest.raises(StitchError):  # 33 tables
             _gpu(fa["xy"], fa["desc"], fb["xy"], fb["desc"], synth.lsh_bits(0, 33, 8), synth.prosac_words(0, 10),
                  ctx=ctx)
+
+
+def test_rig_registered_from_its_own_frames_stitches_like_the_true_rig():
+    """The loop of Algorithm 4 on the GPU: L-ORB in the overlap halves of neighbouring views,
+    matching and PROSAC per pair, the pairwise homographies chained outwards from camera 1 (placed
+    as in the true rig), then stitch_rig_create with the estimates.  Each pair registers to a
+    fraction of a pixel over its overlap; chained maps drift where they extrapolate (beyond the
+    overlaps), so the canvases are compared between the camera centres."""
+    import torch
+    from paper_1810_03988_gb300 import LORB, Matcher, Rig
+    cfg = synth.config_4x1080p(scale=0.5, frames=1)
+    fr = cfg.frame(0)
+    dfr = [torch.from_numpy(f).cuda() for f in fr]
+    pat, bits = synth.brief_pattern(5), synth.lsh_bits(5)
+    rw = torch.from_numpy(synth.prosac_words(5, 2000).view(np.int32)).cuda()
+    H, W = fr[0].shape[:2]
+    true = [np.asarray(c.H, dtype=np.float64) for c in cfg.cameras]
+    pair = []
+    with LORB(W, H, 1000) as la, LORB(W, H, 1000) as lb, Matcher(1000, 2000) as m:
+        for i in range(len(fr) - 1):
+            xa, _, da, ca = la.detect(dfr[i], [(W // 2, 0, W, H)], pat, 20, 0, 1000)
+            xb, _, db, cb = lb.detect(dfr[i + 1], [(0, 0, W // 2, H)], pat, 20, 0, 1000)
+            _, _, Hab, ni, _ = m.match(xa, da, ca, xb, db, cb, bits, rw)
+            torch.cuda.synchronize()
+            assert int(ni.cpu()[0]) > 200
+            pair.append(Hab.cpu().numpy().reshape(3, 3))
+
+    def err(Ha, Hb, pts):
+        pa, pb = Ha @ pts, Hb @ pts
+        return np.abs(pa[:2] / pa[2] - pb[:2] / pb[2]).max()
+
+    grid = np.array([[x, y, 1.0] for x in np.linspace(0, W - 1, 24) for y in np.linspace(0, H - 1, 12)]).T
+    for i, Hp in enumerate(pair):  # pairwise: over the points of view i that view i + 1 sees
+        Ht = np.linalg.inv(true[i + 1]) @ true[i]
+        q = Ht @ grid
+        q = q[:2] / q[2]
+        seen = (q[0] >= 0) & (q[0] < W) & (q[1] >= 0) & (q[1] < H)
+        assert seen.sum() > 50 and err(Hp, Ht, grid[:, seen]) < 0.5
+    ref = 1
+    est = [None] * len(true)
+    est[ref] = true[ref]
+    for i in range(ref - 1, -1, -1):
+        est[i] = est[i + 1] @ pair[i]
+    for i in range(ref + 1, len(true)):
+        est[i] = est[i - 1] @ np.linalg.inv(pair[i - 1])
+    est = [h / h[2, 2] for h in est]
+    for i in (ref - 1, ref + 1):  # neighbours of the reference, over their overlap with it
+        q = np.linalg.inv(true[ref]) @ true[i] @ grid
+        q = q[:2] / q[2]
+        seen = (q[0] >= 0) & (q[0] < W) & (q[1] >= 0) & (q[1] < H)
+        assert err(est[i], true[i], grid[:, seen]) < 1.0
+    cams = [synth.Camera(c.width, c.height, h) for c, h in zip(cfg.cameras, est)]
+    with Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels) as rt, \
+            Rig(cams, cfg.canvas_w, cfg.canvas_h, cfg.levels) as re:
+        ot = rt.stitch(dfr).cpu().numpy().astype(np.float64)
+        oe = re.stitch(dfr).cpu().numpy().astype(np.float64)
+    both = (ot.sum(axis=2) > 0) & (oe.sum(axis=2) > 0)
+    d = np.abs(ot - oe).mean(axis=2)
+    cx = [int(round((h @ [W / 2, H / 2, 1])[0] / (h @ [W / 2, H / 2, 1])[2])) for h in true]
+    for a in range(len(cx) - 1):  # between neighbouring camera centres: each seam region
+        sl = slice(cx[a], cx[a + 1])
+        assert d[:, sl][both[:, sl]].mean() < 2.5, a

@@ -91,3 +91,33 @@ def test_too_few_matches_give_no_model():
     r = oracle.match_prosac(fa["xy"][:3], fa["desc"][:3], fb["xy"], fb["desc"], synth.lsh_bits(0),
                             synth.prosac_words(0, 64))
     assert r["inliers"] == 0 and np.array_equal(r["H"], np.eye(3))
+
+
+@pytest.mark.parametrize("N,T", [(4, 50), (5, 300), (37, 2000), (255, 1000), (600, 5000), (2048, 20000)])
+def test_prosac_schedule_from_the_definition(N, T):
+    """Growth schedule against its definition in exact rationals: T_n = T_N prod_{i<m} (n-i)/(N-i)
+    (m = 4, T_N = 200000), T'_m = 1, T'_{n+1} = T'_n + ceil(T_{n+1} - T_n); at t = T'_n the top n
+    grows (up to N); sampling is uniform from the top n once t > T'_n."""
+    from fractions import Fraction
+    import math
+    m, TN = 4, 200000
+
+    def Tn(n):
+        v = Fraction(TN)
+        for i in range(m):
+            v *= Fraction(n - i, N - i)
+        return v
+
+    n, Tp = m, 1
+    want_n, want_u = [], []
+    for t in range(1, T + 1):
+        if t == Tp and n < N:
+            Tp += math.ceil(Tn(n + 1) - Tn(n))
+            n += 1
+        want_n.append(n)
+        want_u.append(Tp < t)
+    nt, uni = oracle.prosac_schedule(N, T)
+    np.testing.assert_array_equal(nt, want_n)
+    np.testing.assert_array_equal(uni, want_u)
+    if N > m and T > 10:
+        assert nt[0] == m + 1 and nt.max() <= N  # the first growth happens at t = 1
