@@ -194,6 +194,49 @@ def measure_lorb(torch, dframes, hframes, device: int, points: int = 500, reps: 
                                                       "cores": oracle.threads(), "sample": "one view"}}
 
 
+def measure_accuracy(torch, Rig, cfg, frames0, dframes0, out_u8, device: int, n_random: int = 16):
+    """Error of the stitched canvas against the FP64 oracle on sampled 256x256 windows of frame 0:
+    the windows centred between neighbouring cameras (blended regions) plus seeded random ones.
+    FP32 bands (uint8 output: `out_u8` holds frame 0; float output from an out_float rig) and
+    FP16 bands (float output)."""
+    import oracle
+    side = min(256, cfg.canvas_w, cfg.canvas_h)
+    wins = []
+    cx = []
+    for c in cfg.cameras:
+        if cfg.canvas is None:
+            p = np.asarray(c.H, dtype=np.float64) @ [c.width / 2.0, c.height / 2.0, 1.0]
+            cx.append(p[0] / p[2])
+    cx.sort()
+    for a, b in zip(cx[:-1], cx[1:]):
+        x0 = int(min(max((a + b) / 2 - side / 2, 0), cfg.canvas_w - side))
+        wins.append((x0, (cfg.canvas_h - side) // 2, side, side))
+    rng = np.random.default_rng(7)
+    for _ in range(n_random):
+        wins.append((int(rng.integers(0, cfg.canvas_w - side + 1)), int(rng.integers(0, cfg.canvas_h - side + 1)),
+                     side, side))
+    ref = [oracle.forward(cfg.cameras, frames0, cfg.canvas_w, cfg.canvas_h, cfg.levels, window=w, canvas=cfg.canvas)
+           for w in wins]
+    res = {"windows": len(wins), "window": f"{side}x{side}", "frame": 0,
+           "placement": "one between each pair of neighbouring camera centres, the rest seeded random"}
+    u8 = out_u8.cpu().numpy()
+    d8 = [np.abs(u8[y:y + h, x:x + w].astype(np.int32) - r["u8"].astype(np.int32)) for (x, y, w, h), r in zip(wins, ref)]
+    for fp16 in (False, True):
+        frig = Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, band_fp16=fp16, out_float=True, device=device,
+                   canvas=cfg.canvas)
+        fo = frig.stitch(dframes0).cpu().numpy()
+        torch.cuda.synchronize()
+        frig.close()
+        df = [float(np.abs(fo[y:y + h, x:x + w].astype(np.float64) - r["out"]).max()) for (x, y, w, h), r in zip(wins, ref)]
+        key = "fp16_bands" if fp16 else "fp32"
+        res[key] = {"max_abs_float": max(df), "bound_float": 1e-3 if fp16 else 2e-4}
+        del fo
+    res["fp32"].update({"u8_max_lsb": int(max(int(d.max()) for d in d8)),
+                        "u8_frac_differing": float(sum(int((d > 0).sum()) for d in d8) / sum(d.size for d in d8)),
+                        "bound_u8_lsb": 1})
+    return res
+
+
 def measure_match(torch, dframes, hframes, device: int, points: int = 1000, iters: int = 1000, reps: int = 20):
     """Registration of the first two views (Sec. 4.2): GPU L-ORB features of each (whole views),
     then Multi-Probe LSH matching (8 tables x 16 bits) and PROSAC (T iterations) on the GPU, timed
@@ -339,6 +382,7 @@ def main():
     ap.add_argument("--no-seam", action="store_true", help="skip the seam-weight run")
     ap.add_argument("--no-lorb", action="store_true", help="skip the L-ORB feature-extraction run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-per-rig comparison")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the error measurement against the oracle")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -444,6 +488,13 @@ def main():
                  "hbm_frac": cbytes / (pms / 1e3) / 1e9 / hbm_peak, "speedup_fused_over_plain": pms / ms}
         prig.close()
 
+    # error against the FP64 oracle on sampled windows of frame 0, FP32 and FP16 bands
+    accuracy = None
+    if rank == 0 and not args.no_accuracy and args.path == "fused" and not args.fp16_bands:
+        rig.stitch(dframes[0], out)
+        torch.cuda.synchronize()
+        accuracy = measure_accuracy(torch, Rig, cfg, host_frames[0], dframes[0], out, local)
+
     # FP16 storage of pyramid data between kernels (arithmetic still FP32), same frames
     fp16 = None
     if not args.fp16_bands and not args.no_fp16:
@@ -523,7 +574,7 @@ def main():
                        "l2": "inputs larger than L2: each frame set is a distinct device buffer "
                              f"({cbytes / 1e6:.0f} MB compulsory traffic per step)"},
             "roofline": roof, "step_roofline": step_roof, "plain_path": plain, "fp16_bands": fp16,
-            "seam_weights": seam, "lorb": lorb, "match": match,
+            "seam_weights": seam, "lorb": lorb, "match": match, "accuracy": accuracy,
             "batched": batched, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk, "gpu_launches": info["num_kernels"] * args.steps,
             "rig": {"scratch_bytes": info["scratch_bytes"], "roi_pixels": info["roi_pixels"],
