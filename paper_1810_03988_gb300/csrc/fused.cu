@@ -59,6 +59,7 @@ __device__ __forceinline__ void st(half4* p, float4 v) {
     *p = h;
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 __device__ __forceinline__ float4 f4fma(float s, float4 v, float4 acc) {
     return make_float4(fmaf(s, v.x, acc.x), fmaf(s, v.y, acc.y), fmaf(s, v.z, acc.z), fmaf(s, v.w, acc.w));
 }
@@ -85,6 +86,9 @@ struct CamRef {
 struct D1Tile {
     int cam, k0, j0, ref, wtab, flags, fxy, fwh, g0;  // g0: slot of the level-0 samples (D1_G0_OUT)
     int coltab;                                       // cylindrical canvas: the tile's column table
+    // the staging inputs of the tile one resident wave later (footprint as fxy/fwh, camera and
+    // weight block as cam | (wtab + 1) << 8; pf_fwh = 0: none), prefetched into L2 by this tile
+    int pf_fxy, pf_fwh, pf_cw;
 };
 
 // Cameras (CamRef range, in camera order) whose validity box meets a down1 tile's level-0 inputs,
@@ -107,6 +111,7 @@ struct UpTile {
 constexpr int D1_TX = 32, D1_TY = 16;                        // level-1 outputs per tile
 constexpr int D1_SX = 2 * D1_TX + 3, D1_SY = 2 * D1_TY + 3;  // level-0 virtual region (67 x 35)
 constexpr int D1_THREADS = 256;
+constexpr int D1_BLOCKS_PER_SM = 3;  // resident blocks per SM (launch bound; registers and shared memory)
 constexpr int D1_SXH = (D1_SX + 1) / 2;  // level-0 samples are stored as even and odd column planes
 // Source footprint capacity in texels.  The footprint is staged as three planes of floats (R, G,
 // B; rows padded to a multiple of 4 texels) and shares its space with the horizontal REDUCE
@@ -393,6 +398,23 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
     const uint8_t* px_i = fp.p[i];
     const long long pitch_i = fp.pitch[i];
 
+    if (tl.pf_fwh != 0) {
+        // L2 prefetch of the staging inputs of the tile one resident wave later: its footprint rows
+        // (8 threads per row, one 128-byte line each, the row's last byte for the tail) and its
+        // weight block
+        const int pc = tl.pf_cw & 0xff, pw = (tl.pf_cw >> 8) - 1;
+        const int pfx = tl.pf_fxy & 0xffff, pfy = (int)((unsigned)tl.pf_fxy >> 16);
+        const int pfw = tl.pf_fwh & 0xffff, pfh = tl.pf_fwh >> 16;
+        const uint8_t* pp = fp.p[pc];
+        const long long ppitch = fp.pitch[pc];
+        const int len = 3 * pfw;
+        for (int q = t; q < 8 * pfh; q += D1_THREADS) {
+            const int rr = q >> 3, k = q & 7;
+            if (128 * k < len + 127) prefetch_l2(pp + (long long)(pfy + rr) * ppitch + 3 * pfx + min(128 * k, len - 1));
+        }
+        if (pw >= 0 && t < (4 * D1_NSAMP + 127) / 128)
+            prefetch_l2(d1w + (long long)pw * D1_NSAMP + min(32 * t, D1_NSAMP - 1));
+    }
     const CamRef ref = refs[tl.ref];
     const int W = ci.W, H = ci.H;
     const float fU0 = (float)ref.tm.U0, fV0 = (float)ref.tm.V0;
@@ -499,7 +521,7 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
 }
 
 template <typename T>
-__global__ void __launch_bounds__(D1_THREADS, 3) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
+__global__ void __launch_bounds__(D1_THREADS, D1_BLOCKS_PER_SM) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
                                                        OutDesc od, const D1Tile* __restrict__ tiles,
                                                        const CamRef* __restrict__ refs, const float* __restrict__ d1w,
                                                        const float4* __restrict__ d1cols, T* __restrict__ g0buf) {
@@ -1568,7 +1590,7 @@ stitch_status fused_plan(stitch_rig* r) {
                     // level-0 bounding box of the tile's inputs
                     const int bx0 = std::max(2 * x - 2, 0), bx1 = std::min(2 * x - 2 + D1_SX, g.nx[0]);
                     const int by0 = std::max(2 * y - 2, 0), by1 = std::min(2 * y - 2 + D1_SY, g.ny[0]);
-                    D1Tile t{i, x, y, -1, -1, 0, 0, 0, -1, -1};
+                    D1Tile t{i, x, y, -1, -1, 0, 0, 0, -1, -1, 0, 0, 0};
                     D1Cams tc{(int)refs.size(), 0, -1, 0};
                     for (int j = 0; j < g.ncam; ++j) {
                         const CamDev& cj = r->hcam[j];
@@ -1708,6 +1730,21 @@ stitch_status fused_plan(stitch_rig* r) {
             }
             if (kind >= 0) up[kind].push_back(t);
         }
+    // L2 prefetch chain: blocks start in index order as resident ones finish, so tile i + K
+    // (K = resident blocks of k_down1 on the device) starts about when tile i ends
+    {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device) != cudaSuccess || sms < 1)
+            return STITCH_ECUDA;
+        const size_t K = (size_t)D1_BLOCKS_PER_SM * sms;
+        for (size_t k = 0; k + K < d1.size(); ++k) {
+            const D1Tile& nx = d1[k + K];
+            if (nx.fwh == 0) continue;
+            d1[k].pf_fxy = nx.fxy;
+            d1[k].pf_fwh = nx.fwh;
+            d1[k].pf_cw = nx.cam | ((nx.wtab + 1) << 8);
+        }
+    }
     fs->h_d1 = d1;
     for (int l = 0; l < MAXL; ++l) {
         fs->h_red[l] = red[l];
@@ -1829,7 +1866,7 @@ struct BatchRigDev {
 // A task carries a copy of its tile record, so a block needs one load to start.
 struct BTask {
     int rig, type, idx, level, stage, pad0, pad1, pad2;
-    int tile[12];
+    int tile[14];
 };
 template <typename TL>
 __device__ __forceinline__ const TL& task_tile(const BTask& tk) {
