@@ -539,9 +539,27 @@ constexpr int RS_X = 2 * RT_X + 3, RS_Y = 2 * RT_Y + 3;
 constexpr int RS_XH = (RS_X + 1) / 2;  // inputs stored as even and odd column planes
 constexpr size_t RT_SMEM = sizeof(float4) * (2 * RS_XH * RS_Y + RT_X * RS_Y);
 
+// L2 prefetch of a reduce tile's input rows (the part inside Omega^l; rows that fold at the canvas
+// border are left to the loads), 16 threads per row, one 128-byte line each.
+template <typename T>
+__device__ __forceinline__ void reduce_prefetch(const CamDev* __restrict__ cams, int l, const Tile& tn) {
+    const CamDev& c = cams[tn.cam];
+    const Rect of = c.Om[l];
+    const int vx0 = 2 * tn.x0 - 2, vy0 = 2 * tn.y0 - 2;
+    const int x0 = max(vx0, of.x0), x1 = min(vx0 + RS_X, of.x1);
+    if (x1 <= x0) return;
+    const char* base = reinterpret_cast<const char*>(c.FG[l]);
+    const int len = (x1 - x0) * (int)sizeof(T);
+    for (int q = threadIdx.x; q < 16 * RS_Y; q += 256) {
+        const int rr = q >> 4, k = q & 15, y = vy0 + rr;
+        if (y < of.y0 || y >= of.y1 || 128 * k >= len + 127) continue;
+        prefetch_l2(base + ((long long)(y - of.y0) * of.w() + (x0 - of.x0)) * (long long)sizeof(T) + min(128 * k, len - 1));
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void reduce_tile(const CamDev* __restrict__ cams, const RigGeom& g, int l, const Tile& tl,
-                                            float4* smem) {
+                                            float4* smem, const Tile* pf = nullptr) {
     float4* s0 = smem;  // [RS_Y][2][RS_XH]: even columns, then odd columns, of each row
     float4* sh = smem + 2 * RS_XH * RS_Y;
     const CamDev& c = cams[tl.cam];
@@ -572,6 +590,7 @@ __device__ __forceinline__ void reduce_tile(const CamDev* __restrict__ cams, con
             }
         }
     }
+    if (pf) reduce_prefetch<T>(cams, l, *pf);  // the tile one resident wave later
     __syncthreads();
     for (int q = threadIdx.x; q < RT_X * RS_Y; q += 256) {
         const int r = q / RT_X, p = q - r * RT_X;
@@ -597,11 +616,14 @@ __device__ __forceinline__ void reduce_tile(const CamDev* __restrict__ cams, con
     }
 }
 
+// Blocks start in index order as resident ones finish, so block b prefetches into L2 the input of
+// tile b + wave (wave = resident blocks on the device), which starts about when b ends.
 template <typename T>
 __global__ void __launch_bounds__(256) k_reduce_t(const CamDev* __restrict__ cams, const __grid_constant__ RigGeom g, int l,
-                                                   const Tile* __restrict__ tiles) {
+                                                   const Tile* __restrict__ tiles, int n, int wave) {
     extern __shared__ float4 smem[];
-    reduce_tile<T>(cams, g, l, tiles[blockIdx.x], smem);
+    const int nb = blockIdx.x + wave;
+    reduce_tile<T>(cams, g, l, tiles[blockIdx.x], smem, nb < n ? tiles + nb : nullptr);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -869,11 +891,38 @@ struct UpCams {
     float cscale[NC], cwm[NC], chm[NC];
 };
 
+// L2 prefetch of an up_full tile's largest inputs: the level-0 slots of its blended cameras
+// (one 128-byte line per thread and pass) and their G^1 rows inside Omega^1.
+template <typename T, int NC>
+__device__ __forceinline__ void up_prefetch(const CamDev* __restrict__ cams, const UpTile& tn,
+                                            const CamRef* __restrict__ refs, const T* __restrict__ g0buf) {
+    const int nc = min(tn.count, NC);
+    const int a1x = tn.x0 / 2 - 2, a1y = tn.y0 / 2 - 2;
+    for (int c = 0; c < nc; ++c) {
+        const CamRef& cr = refs[tn.first + c];
+        if (cr.g0 >= 0) {
+            const char* p = reinterpret_cast<const char*>(g0buf + (long long)cr.g0 * (U_TX * U_TY));
+            for (int q = threadIdx.x; q < (int)(U_TX * U_TY * sizeof(T)) / 128; q += U_THREADS) prefetch_l2(p + 128 * q);
+        }
+        const CamDev& cd = cams[cr.cam];
+        const Rect o1 = cd.Om[1];
+        const int x0 = max(a1x, o1.x0), x1 = min(a1x + U1_X, o1.x1);
+        if (x1 <= x0) continue;
+        const char* base = reinterpret_cast<const char*>(cd.FG[1]);
+        const int len = (x1 - x0) * (int)sizeof(T);
+        for (int q = threadIdx.x; q < 8 * U1_Y; q += U_THREADS) {
+            const int rr = q >> 3, k = q & 7, y = a1y + rr;
+            if (y < o1.y0 || y >= o1.y1 || 128 * k >= len + 127) continue;
+            prefetch_l2(base + ((long long)(y - o1.y0) * o1.w() + (x0 - o1.x0)) * (long long)sizeof(T) + min(128 * k, len - 1));
+        }
+    }
+}
+
 template <typename T, int NC>
 __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
                                              const OutDesc& od, const T* __restrict__ R2, const UpTile& tl,
                                              const CamRef* __restrict__ refs, const T* __restrict__ g0buf,
-                                             float4* usm) {
+                                             float4* usm, const UpTile* pf = nullptr) {
     float4* d1 = usm;                // [NC][U1_N]: G^1 of each camera, then R^1 - G^1
     float4* d2 = d1 + NC * U1_N;     // [NC][U2_N]: G^2 of each camera, then R^2 - G^2
     float4* r2s = d2 + NC * U2_N;    // [U2_N]: R^2
@@ -960,6 +1009,7 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
             }
         }
     }
+    if (pf) up_prefetch<T, NC>(cams, *pf, refs, g0buf);  // the tile one resident wave later
     __syncthreads();
     if (L >= 3) {
         // Delta^2_i = R^2 - G^2_i
@@ -1083,9 +1133,11 @@ template <typename T, int NC>
 __global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
                                                         OutDesc od, const T* __restrict__ R2,
                                                         const UpTile* __restrict__ tiles,
-                                                        const CamRef* __restrict__ refs, const T* __restrict__ g0buf) {
+                                                        const CamRef* __restrict__ refs, const T* __restrict__ g0buf,
+                                                        int n, int wave) {
     extern __shared__ float4 usm[];
-    up_full_tile<T, NC>(cams, g, fp, od, R2, tiles[blockIdx.x], refs, g0buf, usm);
+    const int nb = blockIdx.x + wave;  // prefetched: the tile one resident wave later (see k_reduce_t)
+    up_full_tile<T, NC>(cams, g, fp, od, R2, tiles[blockIdx.x], refs, g0buf, usm, nb < n ? tiles + nb : nullptr);
 }
 
 template <int NC>
@@ -1341,6 +1393,7 @@ struct FusedState {
     void* g0buf = nullptr;       // level-0 samples of the FULL canvas tiles, one slot per camera
     int n_g0 = 0;
     int n_staged = 0;            // down1 tiles with a staged source footprint
+    int wave_red = 0, wave_up2 = 0, wave_up4 = 0;  // resident blocks on the device (L2 prefetch distance)
     void* R[MAXL] = {};          // R^l on the canvas grid, l >= 2
     CamRef* refs = nullptr;
     UpTile* up_tiles[UP_KINDS] = {};
@@ -1513,7 +1566,8 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
     for (int l = 1; l + 1 < L; ++l) {
         if (fs->n_red[l + 1] == 0) continue;
         prof_mark(r, "fused_reduce", s);
-        k_reduce_t<T><<<fs->n_red[l + 1], 256, RT_SMEM, s>>>(r->dcam, g, l, fs->red_tiles[l + 1]);
+        k_reduce_t<T><<<fs->n_red[l + 1], 256, RT_SMEM, s>>>(r->dcam, g, l, fs->red_tiles[l + 1], fs->n_red[l + 1],
+                                                             fs->wave_red);
     }
     for (int l = L - 1; l >= 2; --l) {
         prof_mark(r, "fused_coarse", s);
@@ -1530,13 +1584,15 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
         prof_mark(r, "fused_up_full", s);
         k_up_full<T, 2><<<fs->n_up[UP_FULL2], U_THREADS, up_full_smem<2>(), s>>>(r->dcam, g, fp, od, R2,
                                                                                fs->up_tiles[UP_FULL2], fs->refs,
-                                                                               (const T*)fs->g0buf);
+                                                                               (const T*)fs->g0buf,
+                                                                               fs->n_up[UP_FULL2], fs->wave_up2);
     }
     if (fs->n_up[UP_FULL4]) {
         prof_mark(r, "fused_up_full4", s);
         k_up_full<T, 4><<<fs->n_up[UP_FULL4], U_THREADS, up_full_smem<4>(), s>>>(r->dcam, g, fp, od, R2,
                                                                                fs->up_tiles[UP_FULL4], fs->refs,
-                                                                               (const T*)fs->g0buf);
+                                                                               (const T*)fs->g0buf,
+                                                                               fs->n_up[UP_FULL4], fs->wave_up4);
     }
     if (fs->n_up[UP_GENERAL]) {
         prof_mark(r, "fused_up_general", s);
@@ -1556,6 +1612,21 @@ stitch_status set_smem_attrs() {
                                          (int)up_full_smem<2>()));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)up_full_smem<4>()));
+    return STITCH_OK;
+}
+
+// Resident blocks of the reduce and up_full kernels on the rig's device: the distance of their L2
+// prefetch chains.
+template <typename T>
+stitch_status set_waves(stitch_rig* r, FusedState* fs) {
+    int sms = 0, pr = 0, p2 = 0, p4 = 0;
+    STITCH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device));
+    STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pr, k_reduce_t<T>, 256, RT_SMEM));
+    STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_up_full<T, 2>, U_THREADS, up_full_smem<2>()));
+    STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p4, k_up_full<T, 4>, U_THREADS, up_full_smem<4>()));
+    fs->wave_red = std::max(pr, 1) * sms;
+    fs->wave_up2 = std::max(p2, 1) * sms;
+    fs->wave_up4 = std::max(p4, 1) * sms;
     return STITCH_OK;
 }
 
@@ -1790,7 +1861,9 @@ stitch_status fused_plan(stitch_rig* r) {
     for (int l = 2; l < L; ++l) kernels += (fs->n_red[l] > 0) + 1;
     for (int k = 0; k < UP_KINDS; ++k) kernels += fs->n_up[k] > 0;
     r->kernels_per_frame = kernels;
-    return fs->fp16 ? set_smem_attrs<half4>() : set_smem_attrs<float4>();
+    st = fs->fp16 ? set_smem_attrs<half4>() : set_smem_attrs<float4>();
+    if (st != STITCH_OK) return st;
+    return fs->fp16 ? set_waves<half4>(r, fs) : set_waves<float4>(r, fs);
 }
 
 stitch_status fused_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od, cudaStream_t s) {
