@@ -114,23 +114,44 @@ __global__ void __launch_bounds__(256) lorb_response(const uint8_t* __restrict__
         hxy[r][c] = sxy;
     }
     __syncthreads();
-    const int fdx[16] = {0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1};
-    const int fdy[16] = {-3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3};
+    constexpr int fdx[16] = {0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1};
+    constexpr int fdy[16] = {-3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3};
     for (int q = t; q < LT_X * LT_Y; q += 256) {
         const int r = q / LT_X, c = q - r * LT_X;
         const int x = bx + c, y = by + r;
         if (x >= x1 || y >= y1) continue;
         long long out = LLONG_MIN;
         if (in_areas(areas, x, y)) {
-            // FAST-9: runs along the circle walked twice
-            const int p = g[r + 3][c + 3];
-            int run_b = 0, run_d = 0;
+            // FAST-9: a run of >= 9 contiguous circle pixels all brighter than p + t, or all darker
+            // than p - t.  Such an arc holds at least 2 of the 4 compass pixels (0, 4, 8, 12), so a
+            // pixel with fewer than 2 brighter and fewer than 2 darker compass pixels is no corner;
+            // the others test the 16-bit masks, doubled so that a run may wrap around.
+            const int p = g[r + 3][c + 3], hi = p + fast_t, lo = p - fast_t;
+            int nb = 0, nd = 0;
+#pragma unroll
+            for (int k = 0; k < 16; k += 4) {
+                const int v = g[r + 3 + fdy[k]][c + 3 + fdx[k]];
+                nb += v > hi;
+                nd += v < lo;
+            }
             bool corner = false;
-            for (int k = 0; k < 32 && !corner; ++k) {
-                const int v = g[r + 3 + fdy[k & 15]][c + 3 + fdx[k & 15]];
-                run_b = v > p + fast_t ? run_b + 1 : 0;
-                run_d = v < p - fast_t ? run_d + 1 : 0;
-                corner = run_b >= 9 || run_d >= 9;
+            if (nb >= 2 || nd >= 2) {
+                unsigned mb = 0, md = 0;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int v = g[r + 3 + fdy[k]][c + 3 + fdx[k]];
+                    mb |= (unsigned)(v > hi) << k;
+                    md |= (unsigned)(v < lo) << k;
+                }
+                mb |= mb << 16;
+                md |= md << 16;
+                unsigned rb = mb, rd = md;
+#pragma unroll
+                for (int k = 1; k < 9; ++k) {
+                    rb &= mb >> k;
+                    rd &= md >> k;
+                }
+                corner = (rb | rd) != 0;
             }
             if (corner) {
                 long long A = 0, B = 0, C = 0;
@@ -148,9 +169,22 @@ __global__ void __launch_bounds__(256) lorb_response(const uint8_t* __restrict__
     }
 }
 
-// non-maximum suppression: survivors appended to cand (ties to the lower index)
+// Coarse, monotone (non-decreasing in R') bin of a response: the position of its leading bit and
+// the 4 bits below it; R' <= 0 in bin 0.  The N strongest candidates all lie in the bins at or above
+// the bin where the count from the top reaches N.
+constexpr int LORB_BINS = 1024;
+__device__ __forceinline__ int lorb_bin(long long r) {
+    if (r <= 0) return 0;
+    const int e = 64 - __clzll(r);  // 1 .. 63
+    const int m = e > 5 ? (int)((r >> (e - 5)) & 15) : (int)(r & 15);
+    return 16 * e + m;
+}
+
+// non-maximum suppression: survivors appended to cand (ties to the lower index), and counted in
+// the bin histogram
 __global__ void __launch_bounds__(256) lorb_nms(const long long* __restrict__ resp, int W, int x0, int y0, int x1,
-                                                int y1, Cand* __restrict__ cand, int* __restrict__ ncand, int cap) {
+                                                int y1, Cand* __restrict__ cand, int* __restrict__ ncand, int cap,
+                                                int* __restrict__ hist) {
     const int x = x0 + blockIdx.x * 32 + (threadIdx.x & 31), y = y0 + blockIdx.y * 8 + (threadIdx.x >> 5);
     bool keep = false;
     long long r = LLONG_MIN;
@@ -178,13 +212,110 @@ __global__ void __launch_bounds__(256) lorb_nms(const long long* __restrict__ re
     base = __shfl_sync(0xffffffffu, base, leader);
     if (keep) {
         const int pos = base + __popc(m & ((1u << lane) - 1));
-        if (pos < cap) cand[pos] = Cand{r, idx, 0};
+        if (pos < cap) {
+            cand[pos] = Cand{r, idx, 0};
+            atomicAdd(&hist[lorb_bin(r)], 1);
+        }
+    }
+}
+
+// The candidates in the bins at or above the threshold bin (where the count from the top reaches
+// N) appended to cand2: a superset of the N strongest, typically a small one.  Grid-stride; every
+// block finds the threshold bin from the histogram (a suffix sum over the bins).
+constexpr int PRUNE_THREADS = 1024, PRUNE_BLOCKS = 64;
+__global__ void __launch_bounds__(PRUNE_THREADS) lorb_prune(const Cand* __restrict__ cand, const int* __restrict__ ncand,
+                                                            int cap, int npts, const int* __restrict__ hist,
+                                                            Cand* __restrict__ cand2, int* __restrict__ n2,
+                                                            int* __restrict__ overflow) {
+    static_assert(PRUNE_THREADS == LORB_BINS, "one bin per thread");
+    __shared__ int wsum[32];
+    __shared__ int s_b;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int total = *ncand, n = min(total, cap), want = min(n, npts);
+    if (blockIdx.x == 0 && t == 0) *overflow = total > cap ? 1 : 0;
+    if (t == 0) s_b = LORB_BINS;  // want == 0: nothing
+    // suffix sums: thread t takes bin 1023 - t and an inclusive prefix sum over t
+    const int b = LORB_BINS - 1 - t;
+    int v = hist[b];
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += o;
+    }
+    if (lane == 31) wsum[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int x = wsum[lane];
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += o;
+        }
+        wsum[lane] = x;
+    }
+    __syncthreads();
+    const int S = v + (w > 0 ? wsum[w - 1] : 0);  // candidates in bins >= b
+    const int S_above = S - hist[b];             // in bins > b
+    if (want > 0 && S >= want && S_above < want) s_b = b;
+    __syncthreads();
+    const int bT = s_b;
+    for (int i0 = blockIdx.x * PRUNE_THREADS; i0 < n; i0 += gridDim.x * PRUNE_THREADS) {
+        const int i = i0 + t;
+        Cand cv{0, 0, 0};
+        bool keep = false;
+        if (i < n) {
+            cv = cand[i];
+            keep = lorb_bin(cv.r) >= bT;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (!m) continue;
+        int base = 0;
+        const int leader = __ffs(m) - 1;
+        if (lane == leader) base = atomicAdd(n2, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (keep) cand2[base + __popc(m & ((1u << lane) - 1))] = cv;
     }
 }
 
 // key order: R' descending, index ascending == (u, ~idx) descending with u = R' with the sign
 // bit flipped
 __device__ __forceinline__ unsigned long long ukey(long long r) { return (unsigned long long)r ^ (1ull << 63); }
+
+// Threshold digit of one radix-selection pass over the 256-bin histogram (threads 0..255 take a
+// bin each; every thread of the block calls this): from the top, the bin b where the count of the
+// bins from the top down to b first reaches `need` (the largest keys); from the bottom, the same
+// counting up (the smallest indices).  Returns b and leaves in `need` what is still wanted among
+// the keys of bin b.  If the count never reaches `need`, the last bin and the remainder, as a
+// sequential scan would leave them.
+__device__ __forceinline__ int select_digit(const int* hist, int* wsum, int& need, bool from_top, int* s_out) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const bool act = t < 256;
+    const int b = from_top ? 255 - t : t;
+    const int own = act ? hist[b] : 0;
+    int v = own;  // inclusive prefix over the bins in scan order
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += o;
+    }
+    if (act && lane == 31) wsum[w] = v;
+    const int nd = need;
+    __syncthreads();
+    int S = v;
+    if (act)
+        for (int k = 0; k < w; ++k) S += wsum[k];
+    if (t == 255) {  // the last bin in scan order: the fallback
+        s_out[0] = b;
+        s_out[1] = nd - (S - own);
+    }
+    __syncthreads();
+    if (act && t < 255 && S >= nd && S - own < nd) {
+        s_out[0] = b;
+        s_out[1] = nd - (S - own);
+    }
+    __syncthreads();
+    need = s_out[1];
+    const int r = s_out[0];
+    __syncthreads();
+    return r;
+}
 
 // One block: the N strongest survivors, sorted.  Radix selection (8-bit digits, most
 // significant first) of the N-th largest u; survivors above it are taken, and among those equal
@@ -199,9 +330,10 @@ __global__ void __launch_bounds__(SEL_THREADS) lorb_select(const Cand* __restric
     __shared__ int s_need;
     __shared__ Cand win[LORB_MAX_POINTS];
     __shared__ int s_nwin;
+    __shared__ int s_wsum[32], s_pick[2];
     const int t = threadIdx.x;
     const int total = *ncand;
-    if (t == 0) *overflow = total > cap ? 1 : 0;
+    if (t == 0 && overflow) *overflow = total > cap ? 1 : 0;
     const int n = min(total, cap);
     const int want = min(n, npts);
     if (t == 0) {
@@ -221,9 +353,9 @@ __global__ void __launch_bounds__(SEL_THREADS) lorb_select(const Cand* __restric
             if ((u & mask) == prefix) atomicAdd(&hist[(u >> (8 * d)) & 255], 1);
         }
         __syncthreads();
+        int need = s_need;
+        const int b = select_digit(hist, s_wsum, need, true, s_pick);
         if (t == 0) {
-            int need = s_need, b = 255;
-            while (b > 0 && hist[b] < need) need -= hist[b--];
             s_prefix = prefix | ((unsigned long long)b << (8 * d));
             s_need = need;  // how many of the keys equal to the final prefix are still wanted
         }
@@ -247,9 +379,9 @@ __global__ void __launch_bounds__(SEL_THREADS) lorb_select(const Cand* __restric
                 if ((ix & imask) == prefix) atomicAdd(&hist[(ix >> (8 * d)) & 255], 1);
             }
             __syncthreads();
+            int need = s_need;
+            const int b = select_digit(hist, s_wsum, need, false, s_pick);
             if (t == 0) {
-                int need = s_need, b = 0;
-                while (b < 255 && hist[b] < need) need -= hist[b++];
                 s_prefix = prefix | ((unsigned)b << (8 * d));
                 s_need = need;
             }
@@ -325,7 +457,8 @@ struct stitch_lorb {
     int* smooth = nullptr;
     long long* resp = nullptr;
     Cand* cand = nullptr;
-    int* ncand = nullptr;  // [0] survivors, [1] overflow flag
+    Cand* cand2 = nullptr;  // the pruned candidates
+    int* ncand = nullptr;   // [0] survivors, [1] overflow flag, [2] pruned count, then the bin histogram
 };
 
 static void lorb_free(stitch_lorb* c) {
@@ -334,6 +467,7 @@ static void lorb_free(stitch_lorb* c) {
     cudaFree(c->smooth);
     cudaFree(c->resp);
     cudaFree(c->cand);
+    cudaFree(c->cand2);
     cudaFree(c->ncand);
     delete c;
 }
@@ -366,11 +500,12 @@ extern "C" stitch_status stitch_lorb_create(int32_t max_width, int32_t max_heigh
     if (cudaMalloc(&c->gray, N) != cudaSuccess || cudaMalloc(&c->smooth, N * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&c->resp, N * sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&c->cand, (size_t)c->cap * sizeof(Cand)) != cudaSuccess ||
-        cudaMalloc(&c->ncand, 2 * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&c->cand2, (size_t)c->cap * sizeof(Cand)) != cudaSuccess ||
+        cudaMalloc(&c->ncand, (4 + LORB_BINS) * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         st = STITCH_ENOMEM;
     }
-    if (st == STITCH_OK && cudaMemset(c->ncand, 0, 2 * sizeof(int)) != cudaSuccess) st = STITCH_ECUDA;
+    if (st == STITCH_OK && cudaMemset(c->ncand, 0, (4 + LORB_BINS) * sizeof(int)) != cudaSuccess) st = STITCH_ECUDA;
     if (prev >= 0) cudaSetDevice(prev);
     if (st != STITCH_OK) {
         lorb_free(c);
@@ -431,7 +566,8 @@ extern "C" stitch_status stitch_lorb_detect(stitch_lorb* c, const uint8_t* frame
     auto ok = [&](cudaError_t e) {
         if (e != cudaSuccess && st == STITCH_OK) st = STITCH_ECUDA;
     };
-    ok(cudaMemsetAsync(c->ncand, 0, 2 * sizeof(int), s));
+    int* hist = c->ncand + 4;
+    ok(cudaMemsetAsync(c->ncand, 0, (4 + LORB_BINS) * sizeof(int), s));
     if (ar.n > 0) {
         // gray and S on the candidates' box grown by the BRIEF reach (15 + 2) and the FAST / tensor
         // halo, inside the image
@@ -442,10 +578,12 @@ extern "C" stitch_status stitch_lorb_detect(stitch_lorb* c, const uint8_t* frame
         lorb_response<<<dim3((bx1 - bx0 + LT_X - 1) / LT_X, (by1 - by0 + LT_Y - 1) / LT_Y), 256, 0, s>>>(
             c->gray, width, bx0, by0, bx1, by1, ar, params->fast_t, (long long)params->harris_t, c->resp);
         lorb_nms<<<dim3((bx1 - bx0 + 31) / 32, (by1 - by0 + 7) / 8), 256, 0, s>>>(c->resp, width, bx0, by0, bx1, by1,
-                                                                               c->cand, c->ncand, c->cap);
+                                                                               c->cand, c->ncand, c->cap, hist);
     }
-    lorb_select<<<1, SEL_THREADS, 0, s>>>(c->cand, c->ncand, c->cap, params->max_points, width, xy,
-                                          reinterpret_cast<long long*>(resp), count, c->ncand + 1);
+    lorb_prune<<<PRUNE_BLOCKS, PRUNE_THREADS, 0, s>>>(c->cand, c->ncand, c->cap, params->max_points, hist, c->cand2,
+                                                      c->ncand + 2, c->ncand + 1);
+    lorb_select<<<1, SEL_THREADS, 0, s>>>(c->cand2, c->ncand + 2, c->cap, params->max_points, width, xy,
+                                          reinterpret_cast<long long*>(resp), count, nullptr);
     lorb_brief<<<(params->max_points + 7) / 8 + 1, 256, 0, s>>>(c->smooth, width, pat, xy, count,
                                                                 reinterpret_cast<unsigned*>(desc));
     ok(cudaGetLastError());
