@@ -46,11 +46,14 @@ __device__ __forceinline__ bool in_areas(const LorbAreas& a, int x, int y) {
     return false;
 }
 
-// gray (uint8) and binomial-smoothed gray S (int32, unnormalised) on [x0, x1) x [y0, y1)
+// gray (uint8) and binomial-smoothed gray S (unnormalised, at most 255 * 256: uint16) on
+// [x0, x1) x [y0, y1); S by a horizontal then a vertical [1,4,6,4,1] pass (the same integers as
+// the 5 x 5 product weights)
 __global__ void __launch_bounds__(256) lorb_maps(const uint8_t* __restrict__ frame, long long pitch, int W, int H,
                                                  int x0, int y0, int x1, int y1, uint8_t* __restrict__ gray,
-                                                 int* __restrict__ smooth) {
+                                                 uint16_t* __restrict__ smooth) {
     __shared__ int g[20][36];
+    __shared__ int hs[20][32];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
     const int bx = x0 + blockIdx.x * 32, by = y0 + blockIdx.y * 16;
     for (int q = threadIdx.x; q < 20 * 36; q += 256) {
@@ -60,19 +63,19 @@ __global__ void __launch_bounds__(256) lorb_maps(const uint8_t* __restrict__ fra
         g[r][c] = (77 * p[0] + 150 * p[1] + 29 * p[2] + 128) >> 8;
     }
     __syncthreads();
-    const int b5[5] = {1, 4, 6, 4, 1};
+    for (int q = threadIdx.x; q < 20 * 32; q += 256) {
+        const int r = q >> 5, c = q & 31;
+        hs[r][c] = g[r][c] + 4 * g[r][c + 1] + 6 * g[r][c + 2] + 4 * g[r][c + 3] + g[r][c + 4];
+    }
+    __syncthreads();
     for (int rr = ty; rr < 16; rr += 8) {
         const int x = bx + tx, y = by + rr;
         if (x >= x1 || y >= y1) continue;
         gray[(long long)y * W + x] = (uint8_t)g[rr + 2][tx + 2];
         // S only where its 5 x 5 window is inside the image (BRIEF never reads it elsewhere)
         if (x < 2 || y < 2 || x >= W - 2 || y >= H - 2) continue;
-        int s = 0;
-#pragma unroll
-        for (int dy = 0; dy < 5; ++dy)
-#pragma unroll
-            for (int dx = 0; dx < 5; ++dx) s += b5[dy] * b5[dx] * g[rr + dy][tx + dx];
-        smooth[(long long)y * W + x] = s;
+        smooth[(long long)y * W + x] =
+            (uint16_t)(hs[rr][tx] + 4 * hs[rr + 1][tx] + 6 * hs[rr + 2][tx] + 4 * hs[rr + 3][tx] + hs[rr + 4][tx]);
     }
 }
 
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(SEL_THREADS) lorb_select(const Cand* __restric
 }
 
 // BRIEF: a warp per keypoint, lane l computes bits l, l + 32, ..., packed by ballots
-__global__ void __launch_bounds__(256) lorb_brief(const int* __restrict__ smooth, int W,
+__global__ void __launch_bounds__(256) lorb_brief(const uint16_t* __restrict__ smooth, int W,
                                                   const __grid_constant__ LorbPattern pat,
                                                   const int* __restrict__ xy, const int* __restrict__ count,
                                                   unsigned* __restrict__ desc) {
@@ -442,7 +445,7 @@ __global__ void __launch_bounds__(256) lorb_brief(const int* __restrict__ smooth
     for (int j = 0; j < 8; ++j) {
         const int b = 32 * j + lane;
         const int sp = smooth[(long long)(y + pat.p[b][1]) * W + x + pat.p[b][0]];
-        const int sq = smooth[(long long)(y + pat.p[b][3]) * W + x + pat.p[b][2]];
+        const int sq = smooth[(long long)(y + pat.p[b][3]) * W + x + pat.p[b][2]];  // uint16 -> int
         const unsigned bits = __ballot_sync(0xffffffffu, sp > sq);
         if (lane == 0) desc[8 * k + j] = bits;  // bit b of the descriptor: byte b/8, bit b%8 (little endian)
     }
@@ -454,7 +457,7 @@ struct stitch_lorb {
     int device = 0;
     int max_w = 0, max_h = 0, max_points = 0, cap = 0;
     uint8_t* gray = nullptr;
-    int* smooth = nullptr;
+    uint16_t* smooth = nullptr;
     long long* resp = nullptr;
     Cand* cand = nullptr;
     Cand* cand2 = nullptr;  // the pruned candidates
@@ -497,7 +500,7 @@ extern "C" stitch_status stitch_lorb_create(int32_t max_width, int32_t max_heigh
     const size_t N = (size_t)max_width * max_height;
     c->cap = (int)(((size_t)max_width + 1) / 2 * (((size_t)max_height + 1) / 2));  // NMS survivors are never adjacent
     stitch_status st = STITCH_OK;
-    if (cudaMalloc(&c->gray, N) != cudaSuccess || cudaMalloc(&c->smooth, N * sizeof(int)) != cudaSuccess ||
+    if (cudaMalloc(&c->gray, N) != cudaSuccess || cudaMalloc(&c->smooth, N * sizeof(uint16_t)) != cudaSuccess ||
         cudaMalloc(&c->resp, N * sizeof(long long)) != cudaSuccess ||
         cudaMalloc(&c->cand, (size_t)c->cap * sizeof(Cand)) != cudaSuccess ||
         cudaMalloc(&c->cand2, (size_t)c->cap * sizeof(Cand)) != cudaSuccess ||
