@@ -240,70 +240,8 @@ __global__ void __launch_bounds__(1024) mt_order(const int* __restrict__ best, c
     }
 }
 
-// M h = r by Gaussian elimination with partial pivoting (the first row of largest |M[i][c]|; a
-// pivot below 1e-12 in magnitude, or NaN, means singular), then back substitution.  Fully
-// unrolled so that M stays in registers: the row exchange is a select per element.  |x| of a
-// finite or infinite double orders like its bit pattern read as an integer.
+// |x| of a finite or infinite double orders like its bit pattern read as an integer.
 __device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffll; }
-
-template <int c>
-__device__ __forceinline__ bool elim_column(double (&M)[8][8], double (&r)[8]) {
-    long long best = abs_bits(M[c][c]);
-    int p = c;
-#pragma unroll
-    for (int i = c + 1; i < 8; ++i) {
-        const long long a = abs_bits(M[i][c]);
-        if (a > best) {
-            best = a;
-            p = i;
-        }
-    }
-    if (best < __double_as_longlong(1e-12) || best > 0x7ff0000000000000ll) return false;
-#pragma unroll
-    for (int i = c + 1; i < 8; ++i) {
-        const bool sw = i == p;
-#pragma unroll
-        for (int j = c; j < 8; ++j) {  // columns left of c are never read again
-            const double a = M[c][j], b = M[i][j];
-            M[c][j] = sw ? b : a;
-            M[i][j] = sw ? a : b;
-        }
-        const double a = r[c], b = r[i];
-        r[c] = sw ? b : a;
-        r[i] = sw ? a : b;
-    }
-#pragma unroll
-    for (int i = c + 1; i < 8; ++i) {
-        const double f = dD(M[i][c], M[c][c]);
-#pragma unroll
-        for (int j = c; j < 8; ++j) M[i][j] = dS(M[i][j], dM(f, M[c][j]));
-        r[i] = dS(r[i], dM(f, r[c]));
-    }
-    return true;
-}
-
-template <int c>
-__device__ __forceinline__ void back_row(const double (&M)[8][8], const double (&r)[8], double (&h)[8]) {
-    double s = r[c];
-#pragma unroll
-    for (int j = c + 1; j < 8; ++j) s = dS(s, dM(M[c][j], h[j]));
-    h[c] = dD(s, M[c][c]);
-}
-
-__device__ __forceinline__ bool solve8(double (&M)[8][8], double (&r)[8], double (&h)[8]) {
-    if (!elim_column<0>(M, r) || !elim_column<1>(M, r) || !elim_column<2>(M, r) || !elim_column<3>(M, r) ||
-        !elim_column<4>(M, r) || !elim_column<5>(M, r) || !elim_column<6>(M, r) || !elim_column<7>(M, r))
-        return false;
-    back_row<7>(M, r, h);
-    back_row<6>(M, r, h);
-    back_row<5>(M, r, h);
-    back_row<4>(M, r, h);
-    back_row<3>(M, r, h);
-    back_row<2>(M, r, h);
-    back_row<1>(M, r, h);
-    back_row<0>(M, r, h);
-    return true;
-}
 
 __device__ __forceinline__ bool inlier(const double h[8], double x, double y, double u, double v, double t2) {
     const double w = dA(dA(dM(h[6], x), dM(h[7], y)), 1.0);
@@ -393,46 +331,114 @@ __device__ __forceinline__ int nth_free(int j, const int* chosen, int c) {
     return j;
 }
 
-// one thread per iteration: its sample and 4-point hypothesis (valid flag 0 when singular).
-// Small blocks spread the FP64 work over many SMs.
-__global__ void __launch_bounds__(32) mt_hypotheses(const int* __restrict__ n_matches, int iters,
-                                                    const int* __restrict__ nt, const unsigned char* __restrict__ uni,
-                                                    const unsigned* __restrict__ rnd, const double* __restrict__ xyuv,
-                                                    double* __restrict__ hyp, int* __restrict__ valid) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= iters) return;
-    valid[t] = 0;
-    if (*n_matches < 4) return;
-    const int n = nt[t];
-    const unsigned* rw = rnd + 4 * (size_t)t;
-    int idx[4];
-    if (uni[t]) {
-        for (int k = 0; k < 4; ++k) idx[k] = nth_free((int)(rw[k] % (unsigned)(n - k)), idx, k);
-    } else {
-        idx[0] = n - 1;
-        int chosen[3];
-        for (int k = 0; k < 3; ++k) {
-            chosen[k] = nth_free((int)(rw[k] % (unsigned)(n - 1 - k)), chosen, k);
-            idx[k + 1] = chosen[k];
+// M h = r on one block (at least 72 threads; every thread calls it): thread (i, j) of the first 72
+// holds entry j of row i of A = [M | r] in shared memory and receives the operations of the
+// sequential elimination (solve8) in the same order, so h is bit-identical; the pivot search and
+// the ordered subtractions of the back substitution run on one thread.  Returns false (on every
+// thread) when a pivot is below 1e-12 in magnitude or NaN; h in hs.
+struct BlockSolve {
+    double A[8][9];
+    double hs[8], fv[8], prod[8];
+    int piv, sing;
+};
+
+__device__ bool solve8_block(BlockSolve& b) {
+    const int t = threadIdx.x, i = t / 9, j = t - 9 * (t / 9);
+    const bool own = t < 72;
+    if (t == 0) b.sing = 0;
+    __syncthreads();
+    for (int c = 0; c < 8; ++c) {
+        if (t == 0) {
+            long long bst = abs_bits(b.A[c][c]);
+            int p = c;
+            for (int k = c + 1; k < 8; ++k) {
+                const long long v = abs_bits(b.A[k][c]);
+                if (v > bst) {
+                    bst = v;
+                    p = k;
+                }
+            }
+            b.piv = p;
+            if (bst < __double_as_longlong(1e-12) || bst > 0x7ff0000000000000ll) b.sing = 1;
         }
+        __syncthreads();
+        if (b.sing) return false;
+        const int p = b.piv;
+        if (p != c && own && i == c && j >= c) {  // columns left of c are never read again
+            const double x = b.A[c][j];
+            b.A[c][j] = b.A[p][j];
+            b.A[p][j] = x;
+        }
+        __syncthreads();
+        if (own && i > c && j == c) b.fv[i] = dD(b.A[i][c], b.A[c][c]);
+        __syncthreads();
+        if (own && i > c && j >= c) b.A[i][j] = dS(b.A[i][j], dM(b.fv[i], b.A[c][j]));
+        __syncthreads();
     }
-    double M[8][8], r[8], h[8];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const double x = xyuv[4 * idx[k]], y = xyuv[4 * idx[k] + 1];
-        const double u = xyuv[4 * idx[k] + 2], v = xyuv[4 * idx[k] + 3];
-        const int a = 2 * k, b = 2 * k + 1;
-        M[a][0] = x; M[a][1] = y; M[a][2] = 1.0; M[a][3] = 0.0; M[a][4] = 0.0; M[a][5] = 0.0;
-        M[a][6] = -dM(u, x); M[a][7] = -dM(u, y);
-        M[b][0] = 0.0; M[b][1] = 0.0; M[b][2] = 0.0; M[b][3] = x; M[b][4] = y; M[b][5] = 1.0;
-        M[b][6] = -dM(v, x); M[b][7] = -dM(v, y);
-        r[a] = u;
-        r[b] = v;
+    for (int c = 7; c >= 0; --c) {
+        if (t > c && t < 8) b.prod[t] = dM(b.A[c][t], b.hs[t]);
+        __syncthreads();
+        if (t == 0) {
+            double sacc = b.A[c][8];
+            for (int k = c + 1; k < 8; ++k) sacc = dS(sacc, b.prod[k]);
+            b.hs[c] = dD(sacc, b.A[c][c]);
+        }
+        __syncthreads();
     }
-    if (!solve8(M, r, h)) return;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) hyp[8 * (size_t)t + k] = h[k];
-    valid[t] = 1;
+    return true;
+}
+
+// one block of 96 threads per iteration: its sample and 4-point hypothesis (valid flag 0 when
+// singular)
+__global__ void __launch_bounds__(96) mt_hypotheses_b(const int* __restrict__ n_matches, int iters,
+                                                      const int* __restrict__ nt,
+                                                      const unsigned char* __restrict__ uni,
+                                                      const unsigned* __restrict__ rnd,
+                                                      const double* __restrict__ xyuv, double* __restrict__ hyp,
+                                                      int* __restrict__ valid) {
+    __shared__ BlockSolve b;
+    __shared__ int sidx[4];
+    const int it = blockIdx.x, t = threadIdx.x;
+    if (*n_matches < 4) {
+        if (t == 0) valid[it] = 0;
+        return;
+    }
+    if (t == 0) {
+        const int n = nt[it];
+        const unsigned* rw = rnd + 4 * (size_t)it;
+        int idx[4];
+        if (uni[it]) {
+            for (int k = 0; k < 4; ++k) idx[k] = nth_free((int)(rw[k] % (unsigned)(n - k)), idx, k);
+        } else {
+            idx[0] = n - 1;
+            int chosen[3];
+            for (int k = 0; k < 3; ++k) {
+                chosen[k] = nth_free((int)(rw[k] % (unsigned)(n - 1 - k)), chosen, k);
+                idx[k + 1] = chosen[k];
+            }
+        }
+        for (int k = 0; k < 4; ++k) sidx[k] = idx[k];
+    }
+    __syncthreads();
+    if (t < 72) {
+        // rows 2k, 2k+1 of pair k: (x, y, 1, 0, 0, 0, -ux, -uy | u), (0, 0, 0, x, y, 1, -vx, -vy | v)
+        const int i = t / 9, j = t - 9 * (t / 9), k = i >> 1, m = sidx[k];
+        const double x = xyuv[4 * m], y = xyuv[4 * m + 1], u = xyuv[4 * m + 2], v = xyuv[4 * m + 3];
+        const double w = (i & 1) ? v : u;
+        double e;
+        if (j == 8) e = w;
+        else if (j == 6) e = -dM(w, x);
+        else if (j == 7) e = -dM(w, y);
+        else {
+            const int jj = (i & 1) ? j - 3 : j;  // position within the row's (x, y, 1) block
+            e = jj == 0 ? x : jj == 1 ? y : jj == 2 ? 1.0 : 0.0;
+        }
+        b.A[i][j] = e;
+    }
+    __syncthreads();
+    const bool ok = solve8_block(b);
+    if (t == 0) valid[it] = ok ? 1 : 0;
+    if (ok && t < 8) hyp[8 * (size_t)it + t] = b.hs[t];
 }
 
 __device__ __forceinline__ double inlier_t2(double inlier_px, const Norm& z) {
@@ -564,41 +570,46 @@ __global__ void __launch_bounds__(32) mt_sums(const int* __restrict__ n_matches,
     sums[e] = acc;
 }
 
-// one thread: solve the normal equations (the 4-point hypothesis when singular), back to pixels
-// H = Tb^-1 Hn Ta, h33 = 1; identity and 0 inliers when there is no model
-__global__ void mt_solve(const int* __restrict__ best, const double* __restrict__ hyp,
-                         const double* __restrict__ sums, const Norm* __restrict__ norm, double* __restrict__ H,
-                         int* __restrict__ n_inliers) {
-    const int bt = best[0];
+// one block of 96 threads: solve the normal equations (the 4-point hypothesis when singular) and
+// go back to pixels, H = Tb^-1 Hn Ta with h33 = 1; identity and 0 inliers when there is no model
+__global__ void __launch_bounds__(96) mt_solve(const int* __restrict__ best, const double* __restrict__ hyp,
+                                               const double* __restrict__ sums, const Norm* __restrict__ norm,
+                                               double* __restrict__ H, int* __restrict__ n_inliers) {
+    __shared__ BlockSolve b;
+    __shared__ double P[9], Q[9];
+    const int t = threadIdx.x, bt = best[0];
     if (bt < 0) {
-        for (int i = 0; i < 9; ++i) H[i] = i % 4 == 0 ? 1.0 : 0.0;
-        *n_inliers = 0;
+        if (t < 9) H[t] = t % 4 == 0 ? 1.0 : 0.0;
+        if (t == 0) *n_inliers = 0;
         return;
     }
+    if (t < 72) {
+        const int i = t / 9, j = t - 9 * (t / 9);
+        b.A[i][j] = j < 8 ? sums[8 * i + j] : sums[64 + i];
+    }
+    __syncthreads();
+    if (!solve8_block(b)) {
+        if (t < 8) b.hs[t] = hyp[8 * (size_t)bt + t];
+        __syncthreads();
+    }
     const Norm z = *norm;
-    double M[8][8], r[8], h[8];
-#pragma unroll
-    for (int p = 0; p < 8; ++p) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) M[p][q] = sums[8 * p + q];
-        r[p] = sums[64 + p];
+    // Hn = [h0 h1 h2; h3 h4 h5; h6 h7 1], Ta = [sa 0 -sa ca0; 0 sa -sa ca1; 0 0 1],
+    // Tb^-1 = [1/sb 0 cb0; 0 1/sb cb1; 0 0 1]
+    if (t < 9) {
+        const int r = t / 3, k = t - 3 * (t / 3);
+        const double Hn[9] = {b.hs[0], b.hs[1], b.hs[2], b.hs[3], b.hs[4], b.hs[5], b.hs[6], b.hs[7], 1.0};
+        const double Ta[9] = {z.sa, 0.0, -dM(z.sa, z.ca0), 0.0, z.sa, -dM(z.sa, z.ca1), 0.0, 0.0, 1.0};
+        P[t] = dA(dA(dM(Hn[3 * r], Ta[k]), dM(Hn[3 * r + 1], Ta[3 + k])), dM(Hn[3 * r + 2], Ta[6 + k]));
     }
-    if (!solve8(M, r, h)) {
-#pragma unroll
-        for (int p = 0; p < 8; ++p) h[p] = hyp[8 * (size_t)bt + p];
+    __syncthreads();
+    if (t < 9) {
+        const int r = t / 3, k = t - 3 * (t / 3);
+        const double Tbi[9] = {dD(1.0, z.sb), 0.0, z.cb0, 0.0, dD(1.0, z.sb), z.cb1, 0.0, 0.0, 1.0};
+        Q[t] = dA(dA(dM(Tbi[3 * r], P[k]), dM(Tbi[3 * r + 1], P[3 + k])), dM(Tbi[3 * r + 2], P[6 + k]));
     }
-    const double Hn[9] = {h[0], h[1], h[2], h[3], h[4], h[5], h[6], h[7], 1.0};
-    const double Ta[9] = {z.sa, 0.0, -dM(z.sa, z.ca0), 0.0, z.sa, -dM(z.sa, z.ca1), 0.0, 0.0, 1.0};
-    const double Tbi[9] = {dD(1.0, z.sb), 0.0, z.cb0, 0.0, dD(1.0, z.sb), z.cb1, 0.0, 0.0, 1.0};
-    double P[9], Q[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            P[3 * i + j] = dA(dA(dM(Hn[3 * i], Ta[j]), dM(Hn[3 * i + 1], Ta[3 + j])), dM(Hn[3 * i + 2], Ta[6 + j]));
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            Q[3 * i + j] = dA(dA(dM(Tbi[3 * i], P[j]), dM(Tbi[3 * i + 1], P[3 + j])), dM(Tbi[3 * i + 2], P[6 + j]));
-    for (int i = 0; i < 9; ++i) H[i] = dD(Q[i], Q[8]);
-    *n_inliers = best[1];
+    __syncthreads();
+    if (t < 9) H[t] = dD(Q[t], Q[8]);
+    if (t == 0) *n_inliers = best[1];
 }
 
 }  // namespace
@@ -721,13 +732,12 @@ extern "C" stitch_status stitch_match_homography(stitch_matcher* c, const int32_
     const int iters = prm->iters;
     mt_prep<<<1, 1024, 0, s>>>(n_matches, matches, xy_a, xy_b, c->norm, iters, c->xyuv, c->nt, c->uni);
     if (iters > 0) {
-        mt_hypotheses<<<(iters + 31) / 32, 32, 0, s>>>(n_matches, iters, c->nt, c->uni, rnd, c->xyuv, c->hyp,
-                                                       c->valid);
+        mt_hypotheses_b<<<iters, 96, 0, s>>>(n_matches, iters, c->nt, c->uni, rnd, c->xyuv, c->hyp, c->valid);
         mt_score<<<iters, 256, 0, s>>>(n_matches, c->hyp, c->valid, c->xyuv, c->norm, prm->inlier_px, c->counts);
     }
     mt_best<<<1, 256, 0, s>>>(n_matches, iters, c->hyp, c->counts, c->xyuv, c->norm, prm->inlier_px, c->pick, inlier);
     mt_sums<<<72, 32, 0, s>>>(n_matches, c->pick, inlier, c->xyuv, c->sums);
-    mt_solve<<<1, 1, 0, s>>>(c->pick, c->hyp, c->sums, c->norm, H, n_inliers);
+    mt_solve<<<1, 96, 0, s>>>(c->pick, c->hyp, c->sums, c->norm, H, n_inliers);
     stitch_status st = cudaGetLastError() == cudaSuccess ? STITCH_OK : STITCH_ECUDA;
     if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
     return st;
