@@ -237,6 +237,60 @@ def measure_accuracy(torch, Rig, cfg, frames0, dframes0, out_u8, device: int, n_
     return res
 
 
+def measure_backward(torch, device: int, reps: int = 20):
+    """S7 on the differentiation workload (4 cameras 1920x1080, canvas 5200x1300, corners perturbed
+    by +-3 px, gains in U[0.8, 1.2], camera 0 fixed): the backward call (overlap loss and the 9
+    gradient entries of every camera) timed with CUDA events after warm-up, then 50 Adam steps of
+    the refinement through it (wall clock, loss and corner error before and after).  The oracle's
+    loss and gradient on the whole canvas at the same parameters, timed once on the host."""
+    import oracle
+    from paper_1810_03988_gb300 import Rig
+    from paper_1810_03988_gb300.autograd import corners_of, params_from_corners, refine
+    cfg = synth.config_refine()
+    frames = cfg.frame(0)
+    dev = [torch.from_numpy(f).to(f"cuda:{device}") for f in frames]
+    n = len(cfg.cameras)
+    rng = np.random.default_rng(7)
+    true = np.stack([corners_of(c.H, c.width, c.height) for c in cfg.cameras])
+    start = true.copy()
+    start[1:] += rng.uniform(-3, 3, start[1:].shape)
+    gains = np.ones(n)
+    gains[1:] = rng.uniform(0.8, 1.2, n - 1)
+    sizes = [(c.width, c.height) for c in cfg.cameras]
+    with Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, device=device) as rig:
+        signs = [float(rig.camera_map(i)[0][2, 2]) for i in range(n)]
+        p = params_from_corners(torch.tensor(start), torch.tensor(gains), sizes, signs)
+        pd = p.to(f"cuda:{device}").contiguous()
+        for _ in range(3):
+            rig.backward(dev, pd)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            loss, grad = rig.backward(dev, pd)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        t0 = time.perf_counter()
+        corners, g, hist = refine(rig, dev, start, gains, steps=50)
+        torch.cuda.synchronize()
+        refine_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.loss_grad([c.width for c in cfg.cameras], [c.height for c in cfg.cameras], p.numpy(), frames,
+                     (0, 0, cfg.canvas_w, cfg.canvas_h), a33=signs)
+    cpu_s = time.perf_counter() - t0
+    mpix = cfg.canvas_w * cfg.canvas_h / 1e6
+    err = lambda c: float(np.abs(c - true)[1:].mean())
+    return {"value": mpix / (ms / 1e3), "unit": "canvas MPix/s", "ms_per_call": ms,
+            "workload": "4x1080p refinement rig (5200x1300 canvas), loss + 9 gradient entries per camera",
+            "refine": {"steps": 50, "seconds": refine_s, "loss_start": hist[0], "loss_end": hist[-1],
+                       "corner_error_px_start": err(start), "corner_error_px_end": err(corners),
+                       "gain_error_start": float(np.abs(gains[1:] - 1).mean()),
+                       "gain_error_end": float(np.abs(g[1:] - 1).mean())},
+            "cpu_oracle": {"value": mpix / cpu_s, "unit": "canvas MPix/s", "cores": oracle.threads(),
+                           "sample": "one loss + gradient over the whole canvas"}}
+
+
 def measure_match(torch, dframes, hframes, device: int, points: int = 1000, iters: int = 1000, reps: int = 20):
     """Registration of the first two views (Sec. 4.2): GPU L-ORB features of each (whole views),
     then Multi-Probe LSH matching (8 tables x 16 bits) and PROSAC (T iterations) on the GPU, timed
@@ -384,6 +438,7 @@ def main():
     ap.add_argument("--no-lorb", action="store_true", help="skip the L-ORB feature-extraction run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-per-rig comparison")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the error measurement against the oracle")
+    ap.add_argument("--no-backward", action="store_true", help="skip the backward (S7) and refinement run")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -527,6 +582,11 @@ def main():
         lorb = measure_lorb(torch, dframes[0], host_frames[0], local)
         match = measure_match(torch, dframes[0], host_frames[0], local)
 
+    # S7: the backward (overlap loss and parameter gradient) and the refinement through it
+    backward = None
+    if not args.no_backward and rank == 0:
+        backward = measure_backward(torch, local)
+
     # batching: 16 uneven rigs, one launch sequence per rig against one persistent launch
     batched = None
     if not args.no_batch:
@@ -577,7 +637,7 @@ def main():
                        "l2": "inputs larger than L2: each frame set is a distinct device buffer "
                              f"({cbytes / 1e6:.0f} MB compulsory traffic per step)"},
             "roofline": roof, "step_roofline": step_roof, "plain_path": plain, "fp16_bands": fp16,
-            "seam_weights": seam, "lorb": lorb, "match": match, "accuracy": accuracy,
+            "seam_weights": seam, "lorb": lorb, "match": match, "accuracy": accuracy, "backward": backward,
             "batched": batched, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk, "gpu_launches": info["num_kernels"] * args.steps,
             "rig": {"scratch_bytes": info["scratch_bytes"], "roi_pixels": info["roi_pixels"],

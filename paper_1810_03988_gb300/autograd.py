@@ -1,8 +1,9 @@
 """torch.autograd wrapper of the hand-written backward kernel, and alignment refinement.
 
-``StitchLoss.apply(params, rig, frames)`` returns the overlap photometric loss (scope row S7) for
-per-camera canvas->camera parameters ``params`` (N x 9 float64 CUDA tensor: a11..a32, gain; a33 is
-the rig's ±1); its backward is the gradient computed by ``stitch_backward`` in the same call.
+``StitchLoss.apply(params, rig, frames)`` returns the overlap photometric loss (S7) for per-camera
+canvas->camera parameters ``params`` (N x 9 float64 tensor: a11..a32, gain; a33 is the rig's ±1;
+on any device, moved to the frames' GPU for the kernel); its backward is the gradient computed by
+``stitch_backward`` in the same call, on the parameters' device.
 
 Refinement (the "gradient-refined homographies" use of S7): each camera's homography is
 parametrised by the canvas positions of its four image corners (8 numbers, px) and a gain; the
@@ -24,10 +25,11 @@ class StitchLoss(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, params: torch.Tensor, rig: Rig, frames):
-        p = params.detach().contiguous()
+        # the kernel runs on the frames' device; loss and gradient return to the parameters' device
+        p = params.detach().to(frames[0].device).contiguous()
         loss, grad = rig.backward(frames, p)
-        ctx.save_for_backward(grad)
-        return loss[0]
+        ctx.save_for_backward(grad.to(params.device))
+        return loss[0].to(params.device)
 
     @staticmethod
     def backward(ctx, gout):
@@ -69,7 +71,7 @@ def params_from_corners(corners: torch.Tensor, gains: torch.Tensor, sizes, a33_s
         H = homography_from_corners(image_corners(w, h, corners.dtype, corners.device), corners[i])
         A = torch.linalg.inv(H)
         A = A / A[2, 2].abs()
-        if float(A[2, 2]) * a33_signs[i] < 0:
+        if float(A[2, 2].detach()) * a33_signs[i] < 0:
             raise ValueError("camera moved so far that the canvas origin changed sides of its horizon")
         out.append(torch.cat([A.reshape(9)[:8], gains[i:i + 1]]))
     return torch.stack(out)
@@ -79,9 +81,13 @@ def refine(rig: Rig, frames, corners0: np.ndarray, gains0: np.ndarray, steps: in
            lr_gain: float = 0.01, fixed=(0,), callback=None):
     """Adam on corner offsets (px) and gains, gradient from the hand-written backward kernel.
 
+    The corner -> parameter chain (4-point DLT and inverse per camera, a few hundred scalar
+    operations) and the optimiser run on the host; each step moves the (N, 9) parameters to the
+    GPU, runs the loss/gradient kernel there and brings the gradient back.
+
     Returns (corners, gains, history) with history a list of loss values (one per step, before the
     update of that step)."""
-    dev = frames[0].device
+    dev = torch.device("cpu")
     n = len(rig.cameras)
     sizes = [(c.width, c.height) for c in rig.cameras]
     signs = [float(rig.camera_map(i)[0][2, 2]) for i in range(n)]
