@@ -515,6 +515,11 @@ def main():
     # dominant kernel and its roofline: the fused kernels are issue-bound (FP32 sample arithmetic),
     # so the bound is the FP32 ALU peak at the clock measured during the timed region
     dom = max(kt.items(), key=lambda kv: kv[1][0]) if kt else None
+    dominant = dom[0] if dom else None
+    if dom and kernel_algorithmic_flops(dom[0], cfg, info) is None:
+        # small rigs: the largest kernel with an operation model (down1, up_full) stands in
+        modelled = [kv for kv in kt.items() if kernel_algorithmic_flops(kv[0], cfg, info) is not None]
+        dom = max(modelled, key=lambda kv: kv[1][0]) if modelled else dom
     roof = None
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     if dom:
@@ -524,7 +529,8 @@ def main():
         peak_tf = fp32_peak_tflops(clk.get("sm_mhz"), sms)
         achieved = flops / (per_launch_ms / 1e3) / 1e12 if flops else None
         traffic, traffic_src = profiled_traffic(name, args.workload)
-        roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+        roof = {"kernel": name, "dominant_kernel": dominant, "bound": "alu", "achieved": achieved, "peak": peak_tf,
+                "unit": "TFLOP/s",
                 "frac": (achieved / peak_tf) if achieved else None, "traffic": traffic,
                 "traffic_source": traffic_src,
                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 x median SM clock under load",
