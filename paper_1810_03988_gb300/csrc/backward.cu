@@ -272,20 +272,54 @@ __global__ void __launch_bounds__(256) k_backward_final(const CamDev* __restrict
         if (threadIdx.x == 0) *loss = (double)s + (double)c;
         return;
     }
+    // the camera's BW_NV sums at once: each slot's values are read together (one index load, five
+    // 8-byte loads); per value the order of the additions, and the tree, are those of block_csum
+    __shared__ float ss[BW_NV][256], sc[BW_NV][256];
     double S[BW_NV];
     const int lo = cam_slot_start[b], hi = cam_slot_start[b + 1];
-    for (int v = 0; v < BW_NV; ++v) {
-        float s = 0.f, c = 0.f;
-        for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
-            float ns, ne;
-            two_sum(s, partials[(long long)cam_slots[k] * BW_NV + v], ns, ne);
-            s = ns;
-            c += ne;
+    float s[BW_NV], c[BW_NV];
+#pragma unroll
+    for (int v = 0; v < BW_NV; ++v) s[v] = c[v] = 0.f;
+    static_assert(BW_NV % 2 == 0, "pairs of values per load");
+#pragma unroll 2
+    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) {
+        const float2* p = reinterpret_cast<const float2*>(partials + (long long)cam_slots[k] * BW_NV);
+        float x[BW_NV];
+#pragma unroll
+        for (int v = 0; v < BW_NV / 2; ++v) {
+            const float2 q = p[v];
+            x[2 * v] = q.x;
+            x[2 * v + 1] = q.y;
         }
-        block_csum(s, c, sh_s, sh_c);
-        S[v] = (double)s + (double)c;
+#pragma unroll
+        for (int v = 0; v < BW_NV; ++v) {
+            float ns, ne;
+            two_sum(s[v], x[v], ns, ne);
+            s[v] = ns;
+            c[v] += ne;
+        }
+    }
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int v = 0; v < BW_NV; ++v) {
+        ss[v][t] = s[v];
+        sc[v][t] = c[v];
+    }
+    __syncthreads();
+    for (int stride = blockDim.x / 2; stride > 0; stride >>= 1) {
+        if (t < stride) {
+#pragma unroll
+            for (int v = 0; v < BW_NV; ++v) {
+                float ns, ne;
+                two_sum(ss[v][t], ss[v][t + stride], ns, ne);
+                ss[v][t] = ns;
+                sc[v][t] += sc[v][t + stride] + ne;
+            }
+        }
         __syncthreads();
     }
+#pragma unroll
+    for (int v = 0; v < BW_NV; ++v) S[v] = (double)ss[v][0] + (double)sc[v][0];
     if (threadIdx.x == 0 && grad) {
         const double cx = centers[2 * b], cy = centers[2 * b + 1];
         double* gr = grad + 9 * b;
