@@ -9,12 +9,20 @@
 //      the lower index) is the match when its distance <= max_dist and den * d1 < num * d2 (d2:
 //      nearest other probed index, none passes);
 //   M2 quality order: distance ascending, query index ascending;
-//   M3 PROSAC (Chum and Matas growth schedule, m = 4, T_N = 200000; the newest of the top n plus 3
+//   M3 PROSAC (Chum and Matas growth schedule, m = 4, T_N = 200000, its increments
+//      T_{n+1} - T_n evaluated exactly as integer ceilings; the newest of the top n plus 3
 //      of the top n - 1, or 4 of the top n once t > T'_n, drawn without replacement from given
 //      random words); 4-point homography (h33 = 1) by 8x8 Gaussian elimination with partial
 //      pivoting in coordinates normalised per image (bounding box of the matched points);
 //      inliers: w > 0 and squared transfer error < (inlier_px scaled)^2; best: most inliers,
 //      ties to the earlier iteration; least squares on its inliers; returned in pixels.
+//
+// Kernels, in launch order: mt_build (a block per table: sorted keys and a radix directory),
+// mt_query (a warp per query), mt_order (quality order, bounding boxes), mt_prep (normalised
+// coordinates, growth schedule by a block scan), mt_hypotheses_b (a block per iteration: sample and
+// 8x8 solve with a thread per matrix entry), mt_score (a block per hypothesis), mt_best (arg-max,
+// inlier flags), mt_sums (a warp per normal-equation entry, ordered sums), mt_solve (refit and
+// back to pixels).
 #include <climits>
 
 #include "stitch_internal.cuh"
