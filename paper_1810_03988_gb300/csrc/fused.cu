@@ -1,18 +1,26 @@
 // Fused forward path.
 //
-// Data that crosses HBM per frame: the source frames (read by `down1` and again by `up`), the
-// Gaussian level 1 of every camera (written by `down1`, read by `reduce` and `up`), the small
-// levels >= 2 and the output canvas.  Level 0 never leaves the chip and neither does the
-// collapsed level 1.
+// Data that crosses HBM per frame: the source frames (read once, by `down1`), the Gaussian
+// level 1 of every camera (written by `down1`, read by `reduce` and `up_full`), the level-0
+// samples of the blended (FULL) canvas tiles (written by `down1` into one slot per tile and
+// camera, read by `up_full`), the small levels >= 2 and the output canvas.  The collapsed level 1
+// never leaves the chip.
 //
-//   down1   per camera tile: warp + feather weights (S1, S2) of a level-0 tile and its halo into
-//           shared memory, both separable REDUCE passes on chip (S3), write G^1 (r, g, b, weight).
-//   reduce  G^{l+1} = REDUCE(G^l) for l >= 1, every camera in one launch.
-//   coarse  levels L-1 .. 2: Laplacian (S4) + normalised blend (S5) + collapse step (S6) fused,
-//           writing R^l on the canvas grid of level l.
-//   up      per canvas tile: level 1 bands of every contributing camera, blend and collapse to
-//           R^1 in shared memory; then level 0: warp again, Laplacian against EXPAND(G^1_i),
-//           blend, add EXPAND(R^1), mask, clamp, quantise and write the output.
+//   down1    per camera tile: the source footprint staged in shared memory, warp + feather weights
+//            (S1, S2) of a level-0 tile and its halo, both separable REDUCE passes on chip (S3),
+//            write G^1 (r, g, b, weight); SOLO canvas tiles get their output here, FULL ones their
+//            level-0 slot.
+//   reduce   G^{l+1} = REDUCE(G^l) for l >= 1, every camera in one launch.
+//   coarse   levels L-1 .. 2: Laplacian (S4) + normalised blend (S5) + collapse step (S6) fused,
+//            writing R^l on the canvas grid of level l.
+//   up_full  per FULL canvas tile: level 1 bands of every contributing camera, blend and collapse
+//            to R^1 in shared memory; then level 0 from the cameras' slots: Laplacian against
+//            EXPAND(G^1_i), blend, add EXPAND(R^1), mask, clamp, quantise and write the output.
+//   up_simple / up_general  ZERO tiles (output 0) / tiles with more than 4 cameras (one camera at
+//            a time, warping level 0 itself).
+//
+// down1, reduce and up_full each prefetch into L2 the inputs of the tile one resident wave later
+// (thread blocks start in index order as resident ones finish).
 //
 // The per-level blend and collapse are evaluated in the equivalent form
 //   R^l = sum_i a_i (G^l_i + EXPAND(R^{l+1} - G^{l+1}_i)),  a_i = G^l(What_i) / S^l,
