@@ -9,11 +9,13 @@
 //   to the lower index y W + x; the N strongest (R' descending, index ascending); BRIEF bits
 //   [S(x + p_k) > S(x + q_k)] of the binomial-smoothed image S for 256 given point pairs.
 //
-// Kernels: lorb_maps (gray and S over the areas' neighbourhood), lorb_response (FAST + Harris on
-// 32 x 16 tiles staged in shared memory), lorb_nms (survivors appended with warp-aggregated
-// atomics; their order is irrelevant, the selection below is exact), lorb_select (one block:
-// radix selection of the N-th key, then a bitonic sort of the N winners), lorb_brief (a warp per
-// keypoint, bits packed by ballots).
+// Kernels: lorb_maps (gray and S over the areas' neighbourhood, S by separable passes),
+// lorb_response (FAST + Harris on 32 x 16 tiles staged in shared memory; FAST by a compass
+// pre-test and 16-bit run masks), lorb_nms (survivors appended with warp-aggregated atomics, their
+// order is irrelevant since the selection below is exact, and counted in a histogram of coarse
+// response bins), lorb_prune (the survivors in the bins that can hold the N strongest),
+// lorb_select (one block: radix selection of the N-th key, then a bitonic sort of the N winners),
+// lorb_brief (a warp per keypoint, bits packed by ballots).
 #include "stitch_internal.cuh"
 
 namespace {
