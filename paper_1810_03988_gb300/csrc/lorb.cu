@@ -49,31 +49,51 @@ __device__ __forceinline__ bool in_areas(const LorbAreas& a, int x, int y) {
 }
 
 // gray (uint8) and binomial-smoothed gray S (unnormalised, at most 255 * 256: uint16) on
-// [x0, x1) x [y0, y1); S by a horizontal then a vertical [1,4,6,4,1] pass (the same integers as
-// the 5 x 5 product weights)
+// [x0, x1) x [y0, y1) (x0 a multiple of 4); S by a horizontal then a vertical [1,4,6,4,1] pass (the
+// same integers as the 5 x 5 product weights).  The tile's gray, with a halo of 4 columns and 2
+// rows, is staged from groups of 4 pixels: three aligned 32-bit words where the group lies inside
+// the image and the frame's base and pitch are multiples of 4 bytes, clamped byte loads otherwise.
+__device__ __forceinline__ int gray_of(int r, int g, int b) { return (77 * r + 150 * g + 29 * b + 128) >> 8; }
+
 __global__ void __launch_bounds__(256) lorb_maps(const uint8_t* __restrict__ frame, long long pitch, int W, int H,
                                                  int x0, int y0, int x1, int y1, uint8_t* __restrict__ gray,
                                                  uint16_t* __restrict__ smooth) {
-    __shared__ int g[20][36];
+    __shared__ int g[20][40];  // columns bx - 4 .. bx + 35, rows by - 2 .. by + 17
     __shared__ int hs[20][32];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
     const int bx = x0 + blockIdx.x * 32, by = y0 + blockIdx.y * 16;
-    for (int q = threadIdx.x; q < 20 * 36; q += 256) {
-        const int r = q / 36, c = q - r * 36;
-        const int x = min(max(bx - 2 + c, 0), W - 1), y = min(max(by - 2 + r, 0), H - 1);
-        const uint8_t* p = frame + (long long)y * pitch + 3LL * x;
-        g[r][c] = (77 * p[0] + 150 * p[1] + 29 * p[2] + 128) >> 8;
+    const bool words = ((reinterpret_cast<uintptr_t>(frame) | (uintptr_t)pitch) & 3) == 0;
+    for (int q = threadIdx.x; q < 20 * 10; q += 256) {
+        const int r = q / 10, j = q - r * 10;
+        const int y = min(max(by - 2 + r, 0), H - 1), gx0 = bx - 4 + 4 * j;
+        const uint8_t* row = frame + (long long)y * pitch;
+        if (words && gx0 >= 0 && gx0 + 3 < W) {
+            const uint32_t* w = reinterpret_cast<const uint32_t*>(row + 3LL * gx0);
+            const uint32_t a = __ldg(w), b = __ldg(w + 1), c = __ldg(w + 2);
+            // bytes R G B R | G B R G | B R G B
+            g[r][4 * j] = gray_of(a & 255, (a >> 8) & 255, (a >> 16) & 255);
+            g[r][4 * j + 1] = gray_of(a >> 24, b & 255, (b >> 8) & 255);
+            g[r][4 * j + 2] = gray_of((b >> 16) & 255, b >> 24, c & 255);
+            g[r][4 * j + 3] = gray_of((c >> 8) & 255, (c >> 16) & 255, c >> 24);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int x = min(max(gx0 + k, 0), W - 1);
+                const uint8_t* p = row + 3LL * x;
+                g[r][4 * j + k] = gray_of(p[0], p[1], p[2]);
+            }
+        }
     }
     __syncthreads();
     for (int q = threadIdx.x; q < 20 * 32; q += 256) {
-        const int r = q >> 5, c = q & 31;
-        hs[r][c] = g[r][c] + 4 * g[r][c + 1] + 6 * g[r][c + 2] + 4 * g[r][c + 3] + g[r][c + 4];
+        const int r = q >> 5, c = q & 31;  // window columns c + 2 .. c + 6 (canvas x - 2 .. x + 2)
+        hs[r][c] = g[r][c + 2] + 4 * g[r][c + 3] + 6 * g[r][c + 4] + 4 * g[r][c + 5] + g[r][c + 6];
     }
     __syncthreads();
     for (int rr = ty; rr < 16; rr += 8) {
         const int x = bx + tx, y = by + rr;
         if (x >= x1 || y >= y1) continue;
-        gray[(long long)y * W + x] = (uint8_t)g[rr + 2][tx + 2];
+        gray[(long long)y * W + x] = (uint8_t)g[rr + 2][tx + 4];
         // S only where its 5 x 5 window is inside the image (BRIEF never reads it elsewhere)
         if (x < 2 || y < 2 || x >= W - 2 || y >= H - 2) continue;
         smooth[(long long)y * W + x] =
@@ -576,7 +596,7 @@ extern "C" stitch_status stitch_lorb_detect(stitch_lorb* c, const uint8_t* frame
     if (ar.n > 0) {
         // gray and S on the candidates' box grown by the BRIEF reach (15 + 2) and the FAST / tensor
         // halo, inside the image
-        const int mx0 = std::max(bx0 - 17, 0), my0 = std::max(by0 - 17, 0);
+        const int mx0 = std::max(bx0 - 17, 0) & ~3, my0 = std::max(by0 - 17, 0);  // x0 on a 4-pixel group
         const int mx1 = std::min(bx1 + 17, (int)width), my1 = std::min(by1 + 17, (int)height);
         lorb_maps<<<dim3((mx1 - mx0 + 31) / 32, (my1 - my0 + 15) / 16), 256, 0, s>>>(
             frame, pitch, width, height, mx0, my0, mx1, my1, c->gray, c->smooth);
