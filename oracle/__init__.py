@@ -30,20 +30,28 @@ _I = ctypes.c_int
 _D = ctypes.c_double
 
 
-def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` with gcc (-O2, IEEE double, OpenMP when available)."""
-    global _threads_used
-    src = os.path.join(_HERE, "oracle.c")
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src):
-        return _LIB_PATH
-    os.makedirs(_BUILD, exist_ok=True)
-    tmp = f"{_LIB_PATH}.{os.getpid()}.tmp"
-    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-fno-fast-math", "-ffp-contract=off", src, "-o", tmp,
+def compile_library(src: str, out: str) -> None:
+    """gcc -O2, IEEE double without contractions, OpenMP when available: ``src`` -> shared ``out``."""
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c99", "-fno-fast-math", "-ffp-contract=off", src, "-o", out,
             "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
         subprocess.run(base, check=True, capture_output=True)
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` (see compile_library).  ORACLE_LIBRARY names a prebuilt library to load
+    instead (the pin tests run against deliberately broken copies that way)."""
+    override = os.environ.get("ORACLE_LIBRARY")
+    if override:
+        return override
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src):
+        return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = f"{_LIB_PATH}.{os.getpid()}.tmp"
+    compile_library(src, tmp)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -68,6 +76,8 @@ def _load():
             lib.oracle_match_prosac.restype = _I
             lib.oracle_prosac_schedule.argtypes = [_I, _I, _P, _P]
             lib.oracle_prosac_schedule.restype = _I
+            lib.oracle_prosac_sample.argtypes = [_I, _I, _P, _P]
+            lib.oracle_prosac_sample.restype = _I
             lib.oracle_loss_grad.argtypes = [_I, _P, _P, _P, _P, _P, _P, _P, _I, _I, _I, _I, _P, _P]
             for f in ("oracle_invert_h", "oracle_reduce", "oracle_expand", "oracle_regions", "oracle_forward",
                       "oracle_warp", "oracle_loss_grad"):
@@ -293,6 +303,15 @@ def prosac_schedule(N: int, T: int):
     uni = np.zeros(max(T, 1), np.uint8)
     _check(_load().oracle_prosac_schedule(int(N), int(T), nt.ctypes.data, uni.ctypes.data), "prosac_schedule")
     return nt[:T], uni[:T].astype(bool)
+
+
+def prosac_sample(n: int, uniform: bool, words) -> np.ndarray:
+    """The 4 match indices (into the quality order) that PROSAC draws from the top n for one
+    iteration's 4 random words: (4,) int32."""
+    w = np.ascontiguousarray(np.asarray(words, dtype=np.uint32).reshape(4))
+    idx = np.zeros(4, np.int32)
+    _check(_load().oracle_prosac_sample(int(n), int(bool(uniform)), w.ctypes.data, idx.ctypes.data), "prosac_sample")
+    return idx
 
 
 def match_prosac(xy_a, desc_a, xy_b, desc_b, bits, rnd, max_dist: int = 80, ratio=(4, 5), inlier_px: float = 3.0):

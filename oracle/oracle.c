@@ -978,6 +978,14 @@ static void prosac_sample(int n, int uniform, const uint32_t* rnd, int* idx) {
     }
 }
 
+int oracle_prosac_sample(int n, int uniform, const uint32_t* rnd, int32_t* idx) {
+    if (n < 4 || !rnd || !idx) return OR_EINVAL;
+    int v[4];
+    prosac_sample(n, uniform, rnd, v);
+    for (int k = 0; k < 4; ++k) idx[k] = v[k];
+    return OR_OK;
+}
+
 /*
  * xy_a, desc_a (na points), xy_b, desc_b (nb points); bits: L x k bit positions.  rnd: iters x 4
  * random words.  Outputs: matches (up to na, quality order) as (index a, index b, distance),

@@ -121,3 +121,78 @@ def test_prosac_schedule_from_the_definition(N, T):
     np.testing.assert_array_equal(uni, want_u)
     if N > m and T > 10:
         assert nt[0] == m + 1 and nt.max() <= N  # the first growth happens at t = 1
+
+
+def test_prosac_samples_from_the_definition():
+    """The 4 indices of an iteration against the draw without replacement written out: word k picks
+    the (word mod remaining)-th of the indices still free, in increasing order.  Before the schedule
+    has passed, the newest match (index n - 1) is always taken and 3 come from the top n - 1; after,
+    4 come from the top n."""
+    rng = np.random.default_rng(3)
+    for n in (4, 5, 9, 40, 300):
+        for uniform in (False, True):
+            for _ in range(50):
+                w = rng.integers(0, 2 ** 32, 4, dtype=np.uint64).astype(np.uint32)
+                free = list(range(n if uniform else n - 1))
+                want = [] if uniform else [n - 1]
+                for k in range(4 if uniform else 3):
+                    want.append(free.pop(int(w[k]) % len(free)))
+                np.testing.assert_array_equal(oracle.prosac_sample(n, uniform, w), want)
+
+
+def _exact_pairs(Ht, a):
+    b = np.c_[a, np.ones(len(a))] @ np.asarray(Ht).T
+    return b[:, :2] / b[:, 2:3], b[:, 2]
+
+
+def test_four_exact_matches_of_a_strongly_projective_homography():
+    """With exactly 4 matches every hypothesis is the 4-point solve itself: it must reproduce a
+    homography with large perspective terms (no refit can repair a wrong 4-point system)."""
+    Ht = np.array([[0.9, 0.15, 40.0], [-0.1, 1.1, 25.0], [4e-4, -3e-4, 1.0]])
+    a = np.array([[100, 120], [900, 80], [850, 700], [150, 650]], np.int32)
+    b, w = _exact_pairs(Ht, a)
+    assert (w > 0).all()
+    # integer inputs: choose image-A points whose images are integers by scaling the homography
+    # instead, compare with a sub-pixel tolerance on the rounded targets
+    bi = np.rint(b).astype(np.int32)
+    desc = np.random.default_rng(1).integers(0, 256, (4, 32), dtype=np.uint8)
+    r = oracle.match_prosac(a, desc, bi, desc, synth.lsh_bits(0), synth.prosac_words(0, 8))
+    assert r["inliers"] == 4
+    pa = np.c_[a, np.ones(4)] @ r["H"].T
+    np.testing.assert_allclose(pa[:, :2] / pa[:, 2:3], bi, atol=1e-6)
+
+
+def test_inlier_threshold_is_in_image_b_pixels():
+    """Image B four times larger than image A (H = diag(4, 4, 1) plus a shift): matches displaced by
+    6 px in image B are outliers for inlier_px = 3, whatever the scale of image A."""
+    rng = np.random.default_rng(2)
+    Ht = np.array([[4.0, 0.0, 10.0], [0.0, 4.0, 20.0], [0.0, 0.0, 1.0]])
+    a = rng.integers(0, 300, (60, 2)).astype(np.int32)
+    b = (np.c_[a, np.ones(60)] @ Ht.T)[:, :2]
+    b[40:] += 6.0 * np.array([0.6, 0.8])  # 6 px away in image B
+    b = np.rint(b).astype(np.int32)
+    desc = rng.integers(0, 256, (60, 32), dtype=np.uint8)
+    r = oracle.match_prosac(a, desc, b, desc, synth.lsh_bits(0), synth.prosac_words(4, 256), inlier_px=3.0)
+    m = r["matches"]
+    inl = np.zeros(60, bool)
+    inl[m[r["inlier"], 0]] = True
+    assert inl[:40].all() and not inl[40:].any(), (inl[:40].sum(), inl[40:].sum())
+
+
+def test_points_behind_the_camera_are_no_inliers():
+    """Exact correspondences of a homography whose line w = 0 crosses the point set: the pairs with
+    w < 0 satisfy the projection too but are behind the camera, so they are never inliers."""
+    rng = np.random.default_rng(5)
+    Ht = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [-2e-3, 0.0, 1.0]])  # w = 1 - x/500
+    a = np.c_[rng.integers(10, 490, 50), rng.integers(0, 400, 50)]
+    a = np.r_[a, np.c_[rng.integers(510, 1000, 20), rng.integers(0, 400, 20)]].astype(np.int32)
+    bf, w = _exact_pairs(Ht, a)
+    keep = np.abs(bf).max(axis=1) < 2e5
+    a, bf, w = a[keep], bf[keep], w[keep]
+    b = np.rint(bf).astype(np.int32)
+    desc = rng.integers(0, 256, (len(a), 32), dtype=np.uint8)
+    r = oracle.match_prosac(a, desc, b, desc, synth.lsh_bits(0), synth.prosac_words(6, 512), inlier_px=3.0)
+    m = r["matches"]
+    inl = np.zeros(len(a), bool)
+    inl[m[r["inlier"], 0]] = True
+    assert not inl[w < 0].any() and inl[w > 0].mean() > 0.9
