@@ -31,6 +31,16 @@ MUTANTS = [
     (PINS, "gradient term a31 uses y", "gi[6] += -q * x * iw;", "gi[6] += -q * y * iw;"),
     (PINS, "gain gradient uses the gained value", "gg += 2.0 * r * s[i].B[c];", "gg += 2.0 * r * s[i].I[c];"),
     (PINS, "gradient term a12 uses v", "gi[1] += gu * y * iw;", "gi[1] += gv * y * iw;"),
+    (PINS, "cylinder sin/cos swapped", "X = sin(t);\n        Y = (y - c->ccy) / c->cf;\n        Z = cos(t);",
+     "X = cos(t);\n        Y = (y - c->ccy) / c->cf;\n        Z = sin(t);"),
+    (PINS, "cylinder angle sign", "const double t = (x - c->ccx) / c->cf;", "const double t = (c->ccx - x) / c->cf;"),
+    (PINS, "cylinder height not scaled", "Y = (y - c->ccy) / c->cf;", "Y = (y - c->ccy);"),
+    (PINS, "seam owner off by one", "if (seam) g[3] = (s == (double)(i + 1)) ? 1.0 : 0.0;",
+     "if (seam) g[3] = (s == (double)i) ? 1.0 : 0.0;"),
+    (PINS, "seam owner without coverage", "if (wv[i] > 0.0 && wv[i] >= (1.0 - 1e-9) * wmax) owner = i;",
+     "if (wv[i] >= (1.0 - 1e-9) * wmax) owner = i;"),
+    (PINS, "seam ties to the last camera", "for (int i = 0; i < n && owner < 0; ++i)\n                    if (wv[i] > 0.0",
+     "for (int i = n - 1; i >= 0 && owner < 0; --i)\n                    if (wv[i] > 0.0"),
     (LORB, "gray weights R/B swapped", "(77 * q[0] + 150 * q[1] + 29 * q[2] + 128) >> 8",
      "(29 * q[0] + 150 * q[1] + 77 * q[2] + 128) >> 8"),
     (LORB, "FAST-8 instead of FAST-9", "if (run_b >= 9 || run_d >= 9) return 1;", "if (run_b >= 8 || run_d >= 8) return 1;"),
