@@ -354,9 +354,11 @@ void stitch_batch_destroy(stitch_batch* batch);
  * The schedule the batch runs, chosen on its first stitch_batch_frames call by timing every
  * candidate on the real frames.  Candidates: the cooperative persistent launch (stage ordering x
  * register variant x tasks per dequeue) and the staged schedule (one launch per task type and
- * level over all rigs, no device waits), both replayed from a CUDA graph.  The environment
- * variable STITCH_TUNE=off skips timing (persistent defaults), =persistent or =staged forces one.
- * *order is 0xF for the staged schedule; otherwise bits 0-3 are the stage ordering (0 ranks every
+ * level over all rigs, no device waits), both replayed from a CUDA graph, and the per-rig streams
+ * (every rig's own launch sequence on a stream of its own, launched directly).  The environment
+ * variable STITCH_TUNE=off skips timing (persistent defaults), =persistent, =staged or =streams
+ * forces one.  *order is 0xF for the staged schedule, 0xE for the per-rig streams; otherwise
+ * bits 0-3 are the stage ordering (0 ranks every
  * rig's stages from the start, 1 aligns them so every rig finishes together), bits 4-7 the
  * register variant (0: 2 resident blocks per SM, 1: 3), bits 8+ the tasks a block dequeues at
  * once.  *grid is the number of persistent blocks; *tasks the number of tile tasks per call.

@@ -2168,6 +2168,10 @@ struct BatchState {
     cudaGraph_t graph = nullptr;
     std::vector<StageGroup> groups;  // staged schedule, in launch order
     bool staged = false;             // schedule chosen by the tuner: staged launches or persistent
+    bool streams = false;            // ... or every rig's own launch sequence on its own stream
+    cudaStream_t rs[B_MAXRIGS] = {};
+    cudaEvent_t rdone[B_MAXRIGS] = {};
+    cudaEvent_t fork = nullptr;
     long long tasks_by_type[8] = {};
 };
 
@@ -2186,6 +2190,11 @@ stitch_status b_upload(BatchState* b, const std::vector<V>& v, V** out) {
 }
 
 void b_free(BatchState* b) {
+    for (int k = 0; k < B_MAXRIGS; ++k) {
+        if (b->rs[k]) cudaStreamDestroy(b->rs[k]);
+        if (b->rdone[k]) cudaEventDestroy(b->rdone[k]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (void* p : b->allocs) cudaFree(p);
@@ -2326,8 +2335,33 @@ stitch_status b_build_graph(BatchState* b) {
     return STITCH_OK;
 }
 
+// The per-rig schedule on streams: every rig's own launch sequence (the single-rig kernels) on a
+// stream of its own, forked from and joined back to the caller's stream, so that one rig's small
+// latency-bound levels overlap another's large launches.
+template <typename T>
+stitch_status b_launch_streams(BatchState* b, cudaStream_t s) {
+    if (!b->fork) {
+        STITCH_CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        for (int k = 0; k < b->n; ++k) {
+            STITCH_CUDA_TRY(cudaStreamCreateWithFlags(&b->rs[k], cudaStreamNonBlocking));
+            STITCH_CUDA_TRY(cudaEventCreateWithFlags(&b->rdone[k], cudaEventDisableTiming));
+        }
+    }
+    STITCH_CUDA_TRY(cudaEventRecord(b->fork, s));
+    for (int k = 0; k < b->n; ++k) {
+        stitch_rig* r = b->rigs[k];
+        STITCH_CUDA_TRY(cudaStreamWaitEvent(b->rs[k], b->fork, 0));
+        const stitch_status st = launch_all<T>(r, (FusedState*)r->fused, b->h_rigs[k].fp, b->h_rigs[k].od, b->rs[k]);
+        if (st != STITCH_OK) return st;
+        STITCH_CUDA_TRY(cudaEventRecord(b->rdone[k], b->rs[k]));
+        STITCH_CUDA_TRY(cudaStreamWaitEvent(s, b->rdone[k], 0));
+    }
+    return STITCH_OK;
+}
+
 // Time every candidate schedule (stage ordering, register variant with its resident blocks per
-// SM, tasks per dequeue) on the real frames and keep the fastest.
+// SM, tasks per dequeue; the staged launches; the per-rig streams) on the real frames and keep the
+// fastest.
 template <typename T>
 stitch_status b_tune(BatchState* b, cudaStream_t s) {
     const char* mode = getenv("STITCH_TUNE");
@@ -2383,8 +2417,26 @@ stitch_status b_tune(BatchState* b, cudaStream_t s) {
             b->staged = true;
         }
     }
-    if (mode && strcmp(mode, "persistent") == 0) b->staged = false;
-    if (mode && strcmp(mode, "staged") == 0) b->staged = true;
+    // the per-rig streams
+    for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, s);
+        stitch_status st = b_launch_streams<T>(b, s);
+        if (st != STITCH_OK) return st;
+        cudaEventRecord(e1, s);
+        STITCH_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep == 1 && ms < best) {
+            best = ms;
+            b->streams = true;
+        }
+    }
+    if (mode && strcmp(mode, "persistent") == 0) b->staged = b->streams = false;
+    if (mode && strcmp(mode, "staged") == 0) {
+        b->staged = true;
+        b->streams = false;
+    }
+    if (mode && strcmp(mode, "streams") == 0) b->streams = true;
     b->tuned_ms = best;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -2591,9 +2643,19 @@ stitch_status fused_batch_frames(void* bp, const uint8_t* const* const* frames, 
         const stitch_status st = b->fp16 ? b_tune<half4>(b, s) : b_tune<float4>(b, s);
         if (st != STITCH_OK) return st;
         b->tuned = true;
-        const stitch_status gs = b->staged ? (b->fp16 ? b_build_staged_graph<half4>(b) : b_build_staged_graph<float4>(b))
-                                           : (b->fp16 ? b_build_graph<half4>(b) : b_build_graph<float4>(b));
-        if (gs != STITCH_OK) return gs;
+        if (!b->streams) {
+            const stitch_status gs = b->staged
+                                         ? (b->fp16 ? b_build_staged_graph<half4>(b) : b_build_staged_graph<float4>(b))
+                                         : (b->fp16 ? b_build_graph<half4>(b) : b_build_graph<float4>(b));
+            if (gs != STITCH_OK) return gs;
+        }
+    }
+    if (b->streams) {
+        // the frame and output pointers are kernel arguments here: launched directly, no graph
+        const stitch_status st = b->fp16 ? b_launch_streams<half4>(b, s) : b_launch_streams<float4>(b, s);
+        if (st != STITCH_OK) return st;
+        STITCH_CUDA_TRY(cudaStreamSynchronize(s));
+        return STITCH_OK;
     }
     *b->h_status = 0;
     STITCH_CUDA_TRY(cudaGraphLaunch(b->exec, s));
@@ -2612,7 +2674,7 @@ void fused_batch_destroy(void* bp) {
 stitch_status fused_batch_info(void* bp, int32_t* order, int32_t* grid, int64_t* ntasks) {
     BatchState* b = (BatchState*)bp;
     if (!b) return STITCH_EINVAL;
-    if (order) *order = b->staged ? 0xF : (b->order | (b->variant << 4) | (b->chunk << 8));
+    if (order) *order = b->streams ? 0xE : b->staged ? 0xF : (b->order | (b->variant << 4) | (b->chunk << 8));
     if (grid) *grid = b->grid;
     if (ntasks) *ntasks = b->ntasks + b->ngtasks;
     return STITCH_OK;

@@ -245,6 +245,8 @@ def stitch_batch_get_schedule(batch: int) -> dict:
            "stitch_batch_get_schedule")
     if o.value == 0xF:
         return {"mode": "staged", "tasks": t.value}
+    if o.value == 0xE:
+        return {"mode": "streams", "tasks": t.value}
     return {"mode": "persistent", "order": o.value & 15, "register_variant": (o.value >> 4) & 15,
             "chunk": o.value >> 8, "grid": g.value, "tasks": t.value}
 

@@ -38,7 +38,7 @@ def test_batch_equals_per_rig_launches(out_float):
             for g, r in zip(got, ref):
                 assert np.array_equal(g, r)
         sch = b.schedule()
-        assert sch["tasks"] > 0 and sch["mode"] in ("persistent", "staged")
+        assert sch["tasks"] > 0 and sch["mode"] in ("persistent", "staged", "streams")
     for r in rigs:
         r.close()
 
@@ -89,7 +89,7 @@ def forced_schedule(monkeypatch):
     return force
 
 
-@pytest.mark.parametrize("mode", ["persistent", "staged"])
+@pytest.mark.parametrize("mode", ["persistent", "staged", "streams"])
 def test_each_schedule_equals_per_rig_launches(mode, forced_schedule):
     from paper_1810_03988_gb300 import Batch
     forced_schedule(mode)
