@@ -89,3 +89,48 @@ def test_matcher_rejects_bad_arguments_without_a_device(lib):
     assert lib.stitch_match_homography(None, None, None, None, None, None, None, ctypes.byref(prm), None, None, None,
                                        None, None, None, None, None) == stitch.STITCH_EINVAL
     lib.stitch_matcher_destroy(None)
+
+
+def test_remaining_entry_points_reject_bad_arguments_without_a_device(lib):
+    """Every other entry point validates its handles and sizes before it touches the device."""
+    from paper_1810_03988_gb300 import stitch
+    import synth
+    E = stitch.STITCH_EINVAL
+    out = ctypes.c_void_p()
+    buf = (ctypes.c_uint8 * 64)()
+    pit = (ctypes.c_int64 * 4)(3, 3, 3, 3)
+    # frames through host buffers
+    assert lib.stitch_frames_host(None, buf, pit, buf, 64, None) == E
+    assert lib.stitch_frames_host_async(None, buf, pit, buf, 64, None) == E
+    # per-call scratch path: the descriptor is checked first
+    cfg = synth.config_2cam(scale=0.1)
+    for field, bad in (("num_cameras", 0), ("levels", 0), ("canvas_h", 0), ("out_float", 3), ("band_fp16", 1)):
+        desc, keep = stitch.make_desc(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels)
+        setattr(desc, field, bad)
+        assert lib.stitch_frames_static(ctypes.byref(desc), buf, pit, buf, 64, None) == E, field
+    assert lib.stitch_frames_static(None, buf, pit, buf, 64, None) == E
+    # rig queries and profiling
+    a = (ctypes.c_double * 9)()
+    vis = ctypes.c_int32()
+    cnt = ctypes.c_int32()
+    assert lib.stitch_rig_get_camera(None, 0, a, ctypes.byref(vis)) == E
+    assert lib.stitch_rig_set_profiling(None, 1) == E
+    assert lib.stitch_rig_kernel_times(None, None, None, None, 0, ctypes.byref(cnt)) == E
+    # batches
+    assert lib.stitch_batch_create(None, 1, ctypes.byref(out)) == E
+    assert lib.stitch_batch_create(None, 1, None) == E
+    rigs = (ctypes.c_void_p * 2)(None, None)
+    assert lib.stitch_batch_create(rigs, 2, ctypes.byref(out)) == E and out.value is None
+    assert lib.stitch_batch_get_schedule(None, None, None, None) == E
+    assert lib.stitch_batch_wait_test(None, 10, 0) == E
+    lib.stitch_batch_destroy(None)
+    # L-ORB: sizes below the 37-pixel minimum, point limits, missing outputs
+    assert lib.stitch_lorb_create(36, 100, 100, 0, ctypes.byref(out)) == E
+    assert lib.stitch_lorb_create(100, 36, 100, 0, ctypes.byref(out)) == E
+    assert lib.stitch_lorb_create(100, 100, 0, 0, ctypes.byref(out)) == E
+    assert lib.stitch_lorb_create(100, 100, 2049, 0, ctypes.byref(out)) == E
+    assert lib.stitch_lorb_create(100, 100, 100, 0, None) == E
+    prm = stitch.stitch_lorb_params(20, 0, 100)
+    assert lib.stitch_lorb_detect(None, buf, 8, 8, 24, None, 0, ctypes.byref(prm), buf, buf, buf, buf, buf,
+                                  None) == E
+    lib.stitch_lorb_destroy(None)
