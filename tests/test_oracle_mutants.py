@@ -41,6 +41,22 @@ MUTANTS = [
      "if (wv[i] >= (1.0 - 1e-9) * wmax) owner = i;"),
     (PINS, "seam ties to the last camera", "for (int i = 0; i < n && owner < 0; ++i)\n                    if (wv[i] > 0.0",
      "for (int i = n - 1; i >= 0 && owner < 0; --i)\n                    if (wv[i] > 0.0"),
+    (PINS, "inverse cofactor sign", "inv[5] = -(a * f - c * d) / det;", "inv[5] = (a * f - c * d) / det;"),
+    (PINS, "gain dropped from the sample", "rgb[ch] = c->gain * ((1.0 - fy) * top + fy * bot) / 255.0;",
+     "rgb[ch] = ((1.0 - fy) * top + fy * bot) / 255.0;"),
+    (PINS, "validity starts at the first pixel centre", "int valid = (u >= -0.5) && (u < c->W - 0.5)",
+     "int valid = (u >= 0.0) && (u < c->W - 0.5)"),
+    (PINS, "collapse skips the coarsest band", "for (int l = L - 2; l >= 0; --l) {", "for (int l = L - 3; l >= 0; --l) {"),
+    (PINS, "output not masked by coverage", "int covered = *limg_at(&wsum, x, y) > 0.0;", "int covered = 1;"),
+    (PINS, "output not clamped above", "(r[c] > 1.0 ? 1.0 : r[c])", "r[c]"),
+    (PINS, "residual includes cameras that do not cover the pixel", "if (j != i && val[j]) r += s[i].I[c] - s[j].I[c];",
+     "if (j != i) r += s[i].I[c] - s[j].I[c];"),
+    (PINS, "gradient term a13 scaled by x", "gi[2] += gu * iw;", "gi[2] += gu * x * iw;"),
+    (PINS, "v-derivative weighted by the v fraction",
+     "s->dIv[c] = cv ? 0.0 : g * ((1.0 - fx) * (p10 - p00) + fx * (p11 - p01)) / 255.0;",
+     "s->dIv[c] = cv ? 0.0 : g * ((1.0 - fy) * (p10 - p00) + fy * (p11 - p01)) / 255.0;"),
+    (PINS, "clamped coordinates keep a derivative", "int cu = s->u < 0.0 || s->u > W - 1, cv = s->v < 0.0 || s->v > H - 1;",
+     "int cu = 0, cv = 0;"),
     (LORB, "gray weights R/B swapped", "(77 * q[0] + 150 * q[1] + 29 * q[2] + 128) >> 8",
      "(29 * q[0] + 150 * q[1] + 77 * q[2] + 128) >> 8"),
     (LORB, "FAST-8 instead of FAST-9", "if (run_b >= 9 || run_d >= 9) return 1;", "if (run_b >= 8 || run_d >= 8) return 1;"),

@@ -349,6 +349,54 @@ def test_gradient_matches_central_differences():
     _fd_check(cfg, frames, (0, 0, cfg.canvas_w, cfg.canvas_h))
 
 
+def _three_camera_rig():
+    th = math.radians(7.0)
+    rot = np.array([[math.cos(th), -math.sin(th), 19.4], [math.sin(th), math.cos(th), 1.7], [6e-4, -4e-4, 1.0]])
+    cams = [Camera(24, 18, _T(2.3, 3.7)), Camera(22, 17, rot, 1.1),
+            Camera(20, 16, np.array([[0.8, 0.0, 9.6], [0.0, 0.8, 11.2], [0.0, 0.0, 1.0]]), 0.9)]
+    frames = [_rand_frame(c.height, c.width, seed=k + 11) for k, c in enumerate(cams)]
+    return cams, frames
+
+
+def test_three_camera_loss_and_gradient_are_sums_over_pairs():
+    """The loss is a sum over camera pairs of their overlap terms (S7), so on a rig where some
+    pixels are covered by two cameras and some by all three, the loss and each camera's gradient
+    equal the sums of the two-camera problems that contain it."""
+    cams, frames = _three_camera_rig()
+    Ws, Hs = [c.width for c in cams], [c.height for c in cams]
+    p = _params_of(cams, [1.0, 1.1, 0.9])
+    p[:, 2] += 0.37
+    win = (0, 0, 44, 27)
+    loss, g = oracle.loss_grad(Ws, Hs, p, frames, win)
+    want_loss, want_g = 0.0, np.zeros_like(g)
+    for i, j in ((0, 1), (0, 2), (1, 2)):
+        lij, gij = oracle.loss_grad([Ws[i], Ws[j]], [Hs[i], Hs[j]], p[[i, j]], [frames[i], frames[j]], win)
+        assert lij > 0.0  # every pair overlaps
+        want_loss += lij
+        want_g[i] += gij[0]
+        want_g[j] += gij[1]
+    assert abs(loss - want_loss) <= 1e-12 * want_loss
+    np.testing.assert_allclose(g, want_g, rtol=1e-10, atol=1e-12 * np.abs(want_g).max())
+    # the rig has pixels covered by exactly two cameras and pixels covered by all three
+    ys, xs = np.mgrid[0:27, 0:44]
+    cov = []
+    for k, c in enumerate(cams):
+        q = np.tensordot(np.linalg.inv(np.asarray(c.H)), np.stack([xs, ys, np.ones_like(xs)]), 1)
+        cov.append((q[2] > 0) & (q[0] / q[2] >= -0.5) & (q[0] / q[2] < c.width - 0.5) & (q[1] / q[2] >= -0.5) &
+                   (q[1] / q[2] < c.height - 0.5))
+    n_cov = sum(c.astype(int) for c in cov)
+    assert (n_cov == 2).sum() > 20 and (n_cov == 3).sum() > 20
+
+
+def test_three_camera_gradient_matches_central_differences():
+    """P8 on the three-camera rig (partial triple overlap, a projective camera, gains != 1)."""
+    cams, frames = _three_camera_rig()
+
+    class _Rig:
+        cameras = cams
+    _fd_check(_Rig, frames, (0, 0, 44, 27))
+
+
 def test_translation_gradient_has_lucas_kanade_form():
     """For a pure translation A = T(-t) the a13 / a23 gradients are 2 sum r dI/du and 2 sum r dI/dv
     (w = 1), i.e. minus the gradient of the loss with respect to the canvas shift of the camera;
@@ -588,11 +636,7 @@ def test_full_path_matches_an_independent_numpy_formulation():
     a small canvas with 3 levels: the oracle's output equals the NumPy formulation of S1-S6 to
     rounding level, blended overlaps included (pixels within 1e-6 px of a validity edge, where two
     FP64 evaluations of the position may disagree, are left out)."""
-    th = math.radians(7.0)
-    rot = np.array([[math.cos(th), -math.sin(th), 19.4], [math.sin(th), math.cos(th), 1.7], [6e-4, -4e-4, 1.0]])
-    cams = [Camera(24, 18, _T(2.3, 3.7)), Camera(22, 17, rot, 1.1),
-            Camera(20, 16, np.array([[0.8, 0.0, 9.6], [0.0, 0.8, 11.2], [0.0, 0.0, 1.0]]), 0.9)]
-    frames = [_rand_frame(c.height, c.width, seed=k + 11) for k, c in enumerate(cams)]
+    cams, frames = _three_camera_rig()
     Wc, Hc, L = 44, 27, 3
     ref = oracle.forward(cams, frames, Wc, Hc, L)
     got = _numpy_forward(cams, frames, Wc, Hc, L)
