@@ -338,31 +338,23 @@ class Rig:
         """frames: list of (H, W, 3) uint8 CUDA tensors (row-contiguous).  Returns the canvas tensor."""
         if out is None:
             out = self.new_output()
-        ptrs, pitches = _frame_args(frames, self.cameras)
-        assert out.is_cuda and out.stride(1) == 3 and out.stride(2) == 1
-        stitch_frames(self.handle, ptrs, pitches, out.data_ptr(), out.stride(0) * out.element_size(),
-                      _stream_handle(stream))
+        ptrs, pitches = _frame_args(frames, self.cameras, self.device)
+        optr, opitch = self._canvas_args(out, self.device)
+        stitch_frames(self.handle, ptrs, pitches, optr, opitch, _stream_handle(stream))
         return out
+
+    def _canvas_args(self, out, device):
+        """(pointer, row pitch) of a canvas buffer: (canvas_h, canvas_w, 3), float32 when the rig
+        writes floats, else uint8."""
+        return _image_args(out, self.canvas_h, self.canvas_w, 4 if self.out_float else 1, device, "output canvas")
 
     def stitch_host(self, frames, out: np.ndarray | None = None, stream=None) -> np.ndarray:
         """frames: list of (H, W, 3) uint8 host arrays or pinned tensors; returns a host canvas."""
         import torch
         if out is None:
             out = np.empty((self.canvas_h, self.canvas_w, 3), dtype=np.float32 if self.out_float else np.uint8)
-        ptrs, pitches = [], []
-        for f in frames:
-            if isinstance(f, torch.Tensor):
-                assert not f.is_cuda and f.stride(1) == 3 and f.stride(2) == 1
-                ptrs.append(f.data_ptr())
-                pitches.append(f.stride(0))
-            else:
-                assert f.flags.c_contiguous and f.dtype == np.uint8
-                ptrs.append(f.ctypes.data)
-                pitches.append(f.strides[0])
-        if isinstance(out, torch.Tensor):
-            optr, opitch = out.data_ptr(), out.stride(0) * out.element_size()
-        else:
-            optr, opitch = out.ctypes.data, out.strides[0]
+        ptrs, pitches = _frame_args(frames, self.cameras, None)
+        optr, opitch = self._canvas_args(out, None)
         stitch_frames_host(self.handle, ptrs, pitches, optr, opitch, _stream_handle(stream))
         return out
 
@@ -371,34 +363,23 @@ class Rig:
         canvas); consecutive calls overlap upload, compute and download.  Synchronise `stream`
         (default: the current torch stream) before reading `out` or reusing the inputs."""
         import torch
-        ptrs, pitches = [], []
-        for f in frames:
-            if isinstance(f, torch.Tensor):
-                assert not f.is_cuda and f.stride(1) == 3 and f.stride(2) == 1
-                ptrs.append(f.data_ptr())
-                pitches.append(f.stride(0))
-            else:
-                assert f.flags.c_contiguous and f.dtype == np.uint8
-                ptrs.append(f.ctypes.data)
-                pitches.append(f.strides[0])
-        if isinstance(out, torch.Tensor):
-            optr, opitch = out.data_ptr(), out.stride(0) * out.element_size()
-        else:
-            optr, opitch = out.ctypes.data, out.strides[0]
+        ptrs, pitches = _frame_args(frames, self.cameras, None)
+        optr, opitch = self._canvas_args(out, None)
         stitch_frames_host_async(self.handle, ptrs, pitches, optr, opitch, _stream_handle(stream))
         return out
 
     def backward(self, frames, params, loss=None, grad=None, stream=None):
         """params: (N, 9) float64 CUDA tensor (a11..a32, gain).  Returns (loss (1,), grad (N, 9))."""
         import torch
-        assert params.is_cuda and params.dtype == torch.float64 and params.is_contiguous()
+        n = len(self.cameras)
+        pptr = _float64_args(params, (n, 9), self.device, "params")
         if loss is None:
             loss = torch.empty(1, dtype=torch.float64, device=params.device)
         if grad is None:
             grad = torch.empty_like(params)
-        ptrs, pitches = _frame_args(frames, self.cameras)
-        stitch_backward(self.handle, ptrs, pitches, params.data_ptr(), loss.data_ptr(), grad.data_ptr(),
-                        _stream_handle(stream))
+        ptrs, pitches = _frame_args(frames, self.cameras, self.device)
+        stitch_backward(self.handle, ptrs, pitches, pptr, _float64_args(loss, (1,), self.device, "loss"),
+                        _float64_args(grad, (n, 9), self.device, "grad"), _stream_handle(stream))
         return loss, grad
 
     def camera_map(self, index: int):
@@ -448,13 +429,19 @@ class Batch:
         """frames_per_rig: one list of CUDA frame tensors per rig.  Returns the output tensors."""
         if outs is None:
             outs = [r.new_output() for r in self.rigs]
-        fps, pts = [], []
-        for fr, r in zip(frames_per_rig, self.rigs):
-            a, b = _frame_args(fr, r.cameras)
+        frames_per_rig, outs = list(frames_per_rig), list(outs)
+        if len(frames_per_rig) != len(self.rigs) or len(outs) != len(self.rigs):
+            raise ValueError(f"expected frames and an output for each of {len(self.rigs)} rigs, got "
+                             f"{len(frames_per_rig)} and {len(outs)}")
+        fps, pts, ops, ops_pitch = [], [], [], []
+        for fr, r, o in zip(frames_per_rig, self.rigs, outs):
+            a, b = _frame_args(fr, r.cameras, r.device)
             fps.append(a)
             pts.append(b)
-        stitch_batch_frames(self.handle, fps, pts, [o.data_ptr() for o in outs],
-                            [o.stride(0) * o.element_size() for o in outs], _stream_handle(stream))
+            optr, opitch = r._canvas_args(o, r.device)
+            ops.append(optr)
+            ops_pitch.append(opitch)
+        stitch_batch_frames(self.handle, fps, pts, ops, ops_pitch, _stream_handle(stream))
         return outs
 
     def schedule(self) -> dict:
@@ -464,15 +451,57 @@ class Batch:
         stitch_batch_wait_test(self.handle, spin_limit, rig)
 
 
-def _frame_args(frames, cameras):
+def _image_args(t, h: int, w: int, itemsize: int, device, what: str):
+    """(pointer, row pitch in bytes) of an (h, w, 3) image with packed pixels and rows at any pitch
+    of at least one row: a torch tensor (on CUDA device `device`, or in host memory when `device`
+    is None) or, for host memory, a NumPy array.  Raises ValueError otherwise, before the library
+    could read or write outside the buffer."""
+    import torch
+    if isinstance(t, torch.Tensor):
+        if device is None:
+            if t.is_cuda:
+                raise ValueError(f"{what}: expected a host tensor, got one on {t.device}")
+        elif not t.is_cuda or t.device.index != device:
+            raise ValueError(f"{what}: expected a tensor on cuda:{device}, got one on {t.device}")
+        size = t.element_size()
+        strides = tuple(t.stride()) if t.dim() == 3 else ()
+        ptr = t.data_ptr()
+    elif isinstance(t, np.ndarray) and device is None:
+        size = t.itemsize
+        strides = tuple(s // size for s in t.strides) if t.ndim == 3 and all(s % size == 0 for s in t.strides) else ()
+        ptr = t.ctypes.data
+    else:
+        raise ValueError(f"{what}: expected a {'host' if device is None else 'CUDA'} tensor, got {type(t).__name__}")
+    if tuple(t.shape) != (h, w, 3) or size != itemsize:
+        raise ValueError(f"{what}: expected shape ({h}, {w}, 3) with {itemsize}-byte elements, got "
+                         f"{tuple(t.shape)} with {size}-byte elements")
+    if strides[1:] != (3, 1) or strides[0] < 3 * w:
+        raise ValueError(f"{what}: pixels must be packed (strides (>= {3 * w}, 3, 1) elements), got {strides}")
+    return ptr, strides[0] * size
+
+
+def _frame_args(frames, cameras, device):
+    """Pointers and row pitches of one uint8 frame per camera (device None: host frames)."""
+    frames = list(frames)
+    if len(frames) != len(cameras):
+        raise ValueError(f"expected {len(cameras)} frames (one per camera), got {len(frames)}")
     ptrs, pitches = [], []
-    for f, c in zip(frames, cameras):
-        assert f.is_cuda and f.dtype.itemsize == 1 and tuple(f.shape) == (c.height, c.width, 3), \
-            (tuple(f.shape), c.width, c.height)
-        assert f.stride(1) == 3 and f.stride(2) == 1
-        ptrs.append(f.data_ptr())
-        pitches.append(f.stride(0))
+    for k, (f, c) in enumerate(zip(frames, cameras)):
+        ptr, pitch = _image_args(f, c.height, c.width, 1, device, f"frame {k}")
+        ptrs.append(ptr)
+        pitches.append(pitch)
     return ptrs, pitches
+
+
+def _float64_args(t, shape, device, what: str) -> int:
+    """Pointer of a contiguous float64 CUDA tensor of the given shape on `device`."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != device:
+        raise ValueError(f"{what}: expected a float64 tensor on cuda:{device}")
+    if t.dtype != torch.float64 or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{what}: expected a contiguous float64 tensor of shape {tuple(shape)}, got "
+                         f"{t.dtype} {tuple(t.shape)}")
+    return t.data_ptr()
 
 
 def stitch_lorb_create(max_width: int, max_height: int, max_points: int, device: int) -> int:
@@ -531,10 +560,12 @@ class LORB:
                stream=None):
         """frame: (H, W, 3) uint8 CUDA tensor.  Enqueues the detection; returns (xy, resp, desc, count)
         views of the context's output tensors (valid after the stream reaches them)."""
-        assert frame.is_cuda and frame.dtype.itemsize == 1 and frame.stride(1) == 3 and frame.stride(2) == 1
+        if not hasattr(frame, "shape") or len(frame.shape) != 3:
+            raise ValueError("frame: expected an (H, W, 3) uint8 CUDA tensor")
+        fptr, fpitch = _image_args(frame, frame.shape[0], frame.shape[1], 1, self.device, "frame")
         n = self.max_points if max_points is None else int(max_points)
         prm = stitch_lorb_params(int(fast_t), int(harris_t), n)
-        stitch_lorb_detect(self.handle, frame.data_ptr(), frame.shape[1], frame.shape[0], frame.stride(0), areas, prm,
+        stitch_lorb_detect(self.handle, fptr, frame.shape[1], frame.shape[0], fpitch, areas, prm,
                            pattern, self.xy.data_ptr(), self.resp.data_ptr(), self.desc.data_ptr(),
                            self.count.data_ptr(), _stream_handle(stream))
         return self.xy, self.resp, self.desc, self.count
@@ -599,12 +630,19 @@ class Matcher:
         outputs of LORB.detect); bits (L, k) host array of descriptor bit positions; rnd (T, 4)
         uint32/int32 CUDA tensor of random words.  Enqueues the work; returns views (matches,
         n_matches, H (9,) float64, n_inliers, inlier) of the context's outputs."""
-        for t in (xy_a, desc_a, count_a, xy_b, desc_b, count_b):
-            assert t.is_cuda and t.is_contiguous()
+        import torch
+        for name, t, size, width in (("xy_a", xy_a, 4, 2), ("desc_a", desc_a, 1, 32), ("count_a", count_a, 4, 0),
+                                     ("xy_b", xy_b, 4, 2), ("desc_b", desc_b, 1, 32), ("count_b", count_b, 4, 0)):
+            ok = isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == self.device and t.is_contiguous() \
+                and t.element_size() == size and (t.numel() >= 1 if width == 0 else (t.dim() == 2 and t.shape[1] == width))
+            if not ok:
+                raise ValueError(f"{name}: expected a contiguous CUDA tensor on cuda:{self.device} of "
+                                 f"{'one' if width == 0 else f'(n, {width})'} {size}-byte elements")
         bt = np.asarray(bits, dtype=np.uint8)
         iters = 0 if rnd is None else int(rnd.shape[0])
-        if iters:
-            assert rnd.is_cuda and rnd.is_contiguous() and rnd.element_size() == 4 and rnd.shape[1] == 4
+        if iters and not (isinstance(rnd, torch.Tensor) and rnd.is_cuda and rnd.device.index == self.device and
+                          rnd.is_contiguous() and rnd.element_size() == 4 and rnd.dim() == 2 and rnd.shape[1] == 4):
+            raise ValueError(f"rnd: expected a contiguous (T, 4) tensor of 32-bit words on cuda:{self.device}")
         prm = stitch_match_params(int(bt.shape[0]), int(bt.shape[1]), int(max_dist), int(ratio[0]), int(ratio[1]),
                                   iters, float(inlier_px))
         stitch_match_homography(self.handle, xy_a.data_ptr(), desc_a.data_ptr(), count_a.data_ptr(), xy_b.data_ptr(),
