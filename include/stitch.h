@@ -33,6 +33,9 @@
  *    non-OK status from a compute call the outputs are undefined, and the rig stays usable
  *    unless the status is STITCH_ECUDA (a sticky CUDA error poisons the whole context).
  *  - A rig is not thread-safe: use one rig from one host thread and one stream at a time.
+ *  - A call that takes a rig, batch or context runs on the device it was created on
+ *    (stitch_frames_static: on the current device); no call changes the calling thread's current
+ *    CUDA device.
  */
 #ifndef STITCH_H
 #define STITCH_H

@@ -12,7 +12,11 @@ stitch_status stitch_batch_create(stitch_rig* const* rigs, int32_t n, stitch_bat
     if (!out) return STITCH_EINVAL;
     *out = nullptr;
     void* impl = nullptr;
+    int prev = -1;
+    cudaGetDevice(&prev);
     const stitch_status st = fused_batch_create(rigs, n, &impl);
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     if (st != STITCH_OK) return st;
     stitch_batch* b = new (std::nothrow) stitch_batch{impl, rigs[0]->device};
     if (!b) {
@@ -37,7 +41,10 @@ stitch_status stitch_batch_frames(stitch_batch* batch, const uint8_t* const* con
 
 void stitch_batch_destroy(stitch_batch* batch) {
     if (!batch) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
     fused_batch_destroy(batch->impl);
+    if (prev >= 0 && prev != batch->device) cudaSetDevice(prev);
     delete batch;
 }
 

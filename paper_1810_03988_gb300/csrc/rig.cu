@@ -278,7 +278,8 @@ stitch_status stitch_rig_create(const stitch_rig_desc* desc, int device, stitch_
         return STITCH_ECUDA;
     }
     if (device < 0 || device >= ndev) return STITCH_EINVAL;
-    if (cudaSetDevice(device) != cudaSuccess) return STITCH_ECUDA;
+    DeviceGuard dg(device);  // the caller's current device is restored on return
+    if (!dg.ok) return STITCH_ECUDA;
 
     stitch_rig* r = new (std::nothrow) stitch_rig();
     if (!r) return STITCH_ENOMEM;
