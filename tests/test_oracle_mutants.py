@@ -46,11 +46,14 @@ MUTANTS = [
      "rgb[ch] = ((1.0 - fy) * top + fy * bot) / 255.0;"),
     (PINS, "validity starts at the first pixel centre", "int valid = (u >= -0.5) && (u < c->W - 0.5)",
      "int valid = (u >= 0.0) && (u < c->W - 0.5)"),
-    (PINS, "collapse skips the coarsest band", "for (int l = L - 2; l >= 0; --l) {", "for (int l = L - 3; l >= 0; --l) {"),
+    (PINS, "collapse skips the coarsest band", "for (int l = L - 2; l >= 0; --l) {\n#pragma omp parallel for",
+     "for (int l = L - 3; l >= 0; --l) {\n#pragma omp parallel for"),
     (PINS, "output not masked by coverage", "int covered = *limg_at(&wsum, x, y) > 0.0;", "int covered = 1;"),
     (PINS, "output not clamped above", "(r[c] > 1.0 ? 1.0 : r[c])", "r[c]"),
     (PINS, "residual includes cameras that do not cover the pixel", "if (j != i && val[j]) r += s[i].I[c] - s[j].I[c];",
      "if (j != i) r += s[i].I[c] - s[j].I[c];"),
+    (PINS, "gradient sampler fractions swapped", "double fx = uc - i0, fy = vc - j0;\n    int i1 = i0 + 1 < W ?",
+     "double fx = vc - j0, fy = uc - i0;\n    int i1 = i0 + 1 < W ?"),
     (PINS, "gradient term a13 scaled by x", "gi[2] += gu * iw;", "gi[2] += gu * x * iw;"),
     (PINS, "v-derivative weighted by the v fraction",
      "s->dIv[c] = cv ? 0.0 : g * ((1.0 - fx) * (p10 - p00) + fx * (p11 - p01)) / 255.0;",
