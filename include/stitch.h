@@ -109,8 +109,9 @@ typedef struct stitch_rig stitch_rig; /* opaque, owned by the library */
  * precomputes grid/block sizes and static/dynamic memory at start-up, Sec. 4.3.2; this is the
  * counterpart).  Checks: each H is finite and invertible with a non-zero a33 after inversion;
  * each camera's footprint is bounded (w > 0 at the four corners of its image rectangle); w > 0
- * over every canvas region the camera's blend depends on.  `device` is the CUDA ordinal; create makes
- * it current and leaves it current.  On success *out receives the rig; on failure *out is NULL.
+ * over every canvas region the camera's blend depends on.  `device` is the CUDA ordinal the rig
+ * lives on; the caller's current device is restored on return.  On success *out receives the rig;
+ * on failure *out is NULL.
  * Status: OK, EINVAL, ENOMEM, ECUDA.
  */
 stitch_status stitch_rig_create(const stitch_rig_desc* desc, int device, stitch_rig** out);
