@@ -147,8 +147,11 @@ stitch_status stitch_frames_host(stitch_rig* rig, const uint8_t* const* host_fra
  * download, so the canvas in `host_out` is complete once `stream` has reached this point (e.g.
  * after cudaStreamSynchronize(stream)).  Host frames and `host_out` must stay valid and untouched
  * until then; pinned memory makes the copies asynchronous.  The upload is NOT ordered after work
- * queued earlier on `stream` (it reads host memory, which the caller has filled before the call).  The rig keeps two staging slots and
- * three streams of its own, created by the first call (which may therefore return ENOMEM).
+ * queued earlier on `stream` (it reads host memory, which the caller has filled before the call).
+ * The rig keeps two staging slots and three streams of its own, created by the first call (which
+ * may therefore return ENOMEM).  The stitches run on the rig's compute stream and share the rig's
+ * scratch with stitch_frames and stitch_backward: before switching between this call and those on
+ * the same rig, let the earlier calls' work finish (synchronise their streams).
  * Status: OK, EINVAL, ENOMEM, ECUDA.
  */
 stitch_status stitch_frames_host_async(stitch_rig* rig, const uint8_t* const* host_frames, const int64_t* pitches,
