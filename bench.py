@@ -49,6 +49,15 @@ def max_over_ranks(x: float, dist, device) -> float:
     return float(t.item())
 
 
+def frame_percentiles(ms) -> dict:
+    """Median, 10th and 90th percentile (nearest rank) of per-frame times in ms."""
+    s = sorted(ms)
+    if not s:
+        return {}
+    rank = lambda q: s[min(len(s) - 1, max(0, int(np.ceil(q * len(s))) - 1))]
+    return {"p10": rank(0.1), "median": statistics.median(s), "p90": rank(0.9), "frames": len(s)}
+
+
 def job_value(units_per_step_per_rank: float, world: int, ms_per_step: float) -> float:
     """Whole-job throughput: every rank processes the same units per step (replicas), over the
     slowest rank's step time."""
@@ -467,6 +476,8 @@ def main():
         if world > 1:
             dist.barrier()
 
+    frame_stats = {}
+
     def timed(rig, out, steps, warmup, profile, sampler=None):
         for k in range(warmup):
             rig.stitch(dframes[k % nfr], out)
@@ -479,15 +490,21 @@ def main():
         torch.cuda.synchronize()
         if sampler:
             sampler.mark_begin()
+        # the profiled pass also records one event per frame, for the spread of frame times
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps)] if profile else []
         ev0.record(stream)
         for k in range(steps):
             rig.stitch(dframes[(warmup + k) % nfr], out)
+            if evs:
+                evs[k].record(stream)
         ev1.record(stream)
         torch.cuda.synchronize()
         if sampler:
             sampler.mark_end()
         barrier()
         ms = ev0.elapsed_time(ev1) / steps
+        if evs:
+            frame_stats.update(frame_percentiles([a.elapsed_time(b) for a, b in zip([ev0] + evs[:-1], evs)]))
         kt = rig.kernel_times() if profile else {}
         if profile:
             rig.set_profiling(False)
@@ -649,6 +666,7 @@ def main():
             "rig": {"scratch_bytes": info["scratch_bytes"], "roi_pixels": info["roi_pixels"],
                     "kernels_per_step": info["num_kernels"], "tiles": info["tiles"]},
             "kernel_times_ms": {k: {"total_ms": v[0], "launches": v[1]} for k, v in kt.items()},
+            "frame_ms": dict(frame_stats, source="per-frame CUDA events of the profiled pass (same frames)"),
             "frame_generation_s": gen_s,
         }
         print(json.dumps(line))

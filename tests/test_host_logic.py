@@ -64,3 +64,15 @@ def test_binding_checks_host_images_before_the_library_sees_them():
     row = torch.zeros((1, c.width, 3), dtype=torch.uint8).expand(c.height, c.width, 3)
     with pytest.raises(ValueError, match="packed"):
         _image_args(row, c.height, c.width, 1, None, "r")
+
+
+def test_bench_frame_percentiles():
+    """Nearest-rank percentiles of the bench's per-frame times."""
+    from bench import frame_percentiles
+    assert frame_percentiles([]) == {}
+    r = frame_percentiles([float(v) for v in range(1, 11)])  # 1 .. 10 ms
+    assert (r["p10"], r["median"], r["p90"], r["frames"]) == (1.0, 5.5, 9.0, 10)
+    r = frame_percentiles([3.0])
+    assert r["p10"] == r["median"] == r["p90"] == 3.0
+    r = frame_percentiles([5.0, 1.0, 4.0, 2.0, 3.0])
+    assert (r["p10"], r["median"], r["p90"]) == (1.0, 3.0, 5.0)
