@@ -5,6 +5,8 @@ oracle itself is never modified."""
 import os
 import subprocess
 import sys
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -104,15 +106,48 @@ MUTANTS = [
 ]
 
 
-@pytest.mark.parametrize("pins,what,orig,repl", MUTANTS, ids=[m[1] for m in MUTANTS])
-def test_planted_mistake_fails_a_pin(tmp_path, pins, what, orig, repl):
+def _run_mutant(workdir, threads, pins, what, orig, repl):
+    """Compile one mutant into its own directory and run its pin file against it: (exit code, tail
+    of the output)."""
     src = open(SRC).read()
-    assert orig in src, f"mutation site not found: {orig}"
-    bad = tmp_path / "oracle_mutant.c"
-    bad.write_text(src.replace(orig, repl, 1))
-    lib = str(tmp_path / "liboracle_mutant.so")
-    oracle.compile_library(str(bad), lib)
+    d = tempfile.mkdtemp(dir=workdir)
+    bad = os.path.join(d, "oracle_mutant.c")
+    with open(bad, "w") as f:
+        f.write(src.replace(orig, repl, 1))
+    lib = os.path.join(d, "liboracle_mutant.so")
+    oracle.compile_library(bad, lib)
     r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", pins + ".py"), "-x", "-q",
-                        "-p", "no:cacheprovider"], cwd=ROOT, env=dict(os.environ, ORACLE_LIBRARY=lib),
-                       capture_output=True, text=True, timeout=600)
-    assert r.returncode != 0, f"{what}: the pins in {pins}.py still pass"
+                        "-p", "no:cacheprovider"], cwd=ROOT,
+                       env=dict(os.environ, ORACLE_LIBRARY=lib, OMP_NUM_THREADS=str(threads)),
+                       capture_output=True, text=True, timeout=900)
+    return r.returncode, r.stdout[-1500:]
+
+
+@pytest.fixture(scope="module")
+def mutant_results(request, tmp_path_factory):
+    """Runs of the selected mutants, several at a time (each pin run is mostly single-threaded);
+    under pytest-xdist each worker runs only the mutant it is asked for."""
+    workdir = str(tmp_path_factory.mktemp("mutants"))
+    cores = os.cpu_count() or 2
+    cache = {}
+    if not os.environ.get("PYTEST_XDIST_WORKER"):
+        wanted = {item.callspec.params["what"] for item in request.session.items
+                  if item.module is request.module and hasattr(item, "callspec")}
+        todo = [m for m in MUTANTS if m[1] in wanted and m[2] in open(SRC).read()]
+        workers = max(1, min(len(todo), cores // 2))
+        with ThreadPoolExecutor(workers) as ex:
+            futs = {m[1]: ex.submit(_run_mutant, workdir, max(1, cores // workers), *m) for m in todo}
+            cache.update({k: f.result() for k, f in futs.items()})
+
+    def get(m):
+        if m[1] not in cache:
+            cache[m[1]] = _run_mutant(workdir, cores, *m)
+        return cache[m[1]]
+    return get
+
+
+@pytest.mark.parametrize("pins,what,orig,repl", MUTANTS, ids=[m[1] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(mutant_results, pins, what, orig, repl):
+    assert orig in open(SRC).read(), f"mutation site not found: {orig}"
+    rc, out = mutant_results((pins, what, orig, repl))
+    assert rc != 0, f"{what}: the pins in {pins}.py still pass\n{out}"
