@@ -32,7 +32,7 @@ def test_replica_timing_takes_the_slowest_rank():
     import torch.multiprocessing as mp
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of this multi-threaded process
         results = m.dict()
         mp.spawn(_rank_main, args=(world, port, results), nprocs=world, join=True)
         res = dict(results)
