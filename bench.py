@@ -692,18 +692,43 @@ KERNEL_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_
                              "fused.cu")
 
 
+def code_digest(path: str) -> str:
+    """SHA-256 of a C/C++/CUDA source with its comments removed and runs of whitespace collapsed:
+    edits to comments or layout leave it unchanged, any change to the code changes it."""
+    import hashlib
+    src = open(path, encoding="utf-8").read()
+    out, i, n = [], 0, len(src)
+    while i < n:
+        if src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif src[i] in "\"'":
+            j = i + 1
+            while j < n and src[j] != src[i]:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        else:
+            out.append(src[i])
+            i += 1
+    return hashlib.sha256(" ".join("".join(out).split()).encode()).hexdigest()
+
+
 def profiled_traffic(kernel: str, workload: str):
     """DRAM bytes (read + write) of one launch of `kernel` on `workload` from the committed ncu
     summaries under profiles/ (a `traffic:` line), or None when there is none or the kernel
-    source has changed since the capture (the line records the source's SHA-256)."""
+    source's code has changed since the capture (the line records its code_digest)."""
     import glob
-    import hashlib
     import re
     try:
-        digest = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+        digest = code_digest(KERNEL_SOURCE)
     except OSError:
         return None, None
-    pat = re.compile(r"^traffic: kernel=(\S+) workload=(\S+) bytes_per_launch=(\d+) source_sha256=([0-9a-f]+)")
+    pat = re.compile(r"^traffic: kernel=(\S+) workload=(\S+) bytes_per_launch=(\d+) code_sha256=([0-9a-f]+)")
     for f in sorted(glob.glob(os.path.join(PROFILES, "*.md"))):
         for line in open(f):
             m = pat.match(line.strip())

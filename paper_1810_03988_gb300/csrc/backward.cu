@@ -1,5 +1,6 @@
-// S7: overlap photometric loss and its gradient with respect to each camera's canvas->camera
-// homography entries a11..a32 (a33 = +-1 fixed by the rig) and gain.
+// S7 (an extension beyond the paper, which fixes its homographies by feature matching, Sec. 4.2,
+// Algorithm 4 step 5): overlap photometric loss and its gradient with respect to each camera's
+// canvas->camera homography entries a11..a32 (a33 = +-1 fixed by the rig) and gain.
 //
 //   loss = sum_x sum_{i<j} v_i(x) v_j(x) |I_i(x) - I_j(x)|^2,  I = gain * bilinear(frame, A x) / 255
 //

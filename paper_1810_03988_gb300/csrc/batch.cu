@@ -1,4 +1,5 @@
-// C-ABI entry points of the batched schedule (the machinery lives with the fused kernels).
+// C-ABI entry points of the batched schedule (the machinery lives with the fused kernels).  It
+// takes the place of the paper's per-image CUDA streams (Sec. 4.3.2) for device-resident frames.
 #include "stitch_internal.cuh"
 
 struct stitch_batch {

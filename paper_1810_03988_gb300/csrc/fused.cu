@@ -1,4 +1,6 @@
-// Fused forward path.
+// Fused forward path: the per-frame step of Algorithm 4 (step 6: transform every camera's video and
+// blend it into the panorama; step 1: the transform follows the pre-corrected parameters), with
+// the multi-band fusion that removes the seams (Sec. 1, contribution 3), as S1-S6 below.
 //
 // Data that crosses HBM per frame: the source frames (read once, by `down1`), the Gaussian
 // level 1 of every camera (written by `down1`, read by `reduce` and `up_full`), the level-0

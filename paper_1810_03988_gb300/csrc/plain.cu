@@ -1,4 +1,5 @@
-// Plain path: one kernel per step of the stitching definition, FP32 intermediates in HBM.
+// Plain path: one kernel per step of the stitching definition (Algorithm 4, step 6, with the
+// multi-band fusion of Sec. 1), FP32 intermediates in HBM.
 // It is the comparison path for the fused implementation and follows the steps literally:
 //   warp+weights (S1, S2) -> REDUCE per level (S3) -> Laplacian per level (S4)
 //   -> per-level normalised blend on the canvas grid (S5) -> collapse + output (S6).

@@ -1,5 +1,6 @@
 // libstitch host side: rig validation and planning, buffer ownership, C-ABI entry points,
-// host staging and per-kernel profiling.
+// host staging and per-kernel profiling.  Every buffer the per-frame path needs is allocated when
+// the rig is created, the counterpart of the paper's start-up preallocation (Sec. 4.3.2).
 #include <math.h>
 #include <string.h>
 

@@ -76,3 +76,25 @@ def test_bench_frame_percentiles():
     assert r["p10"] == r["median"] == r["p90"] == 3.0
     r = frame_percentiles([5.0, 1.0, 4.0, 2.0, 3.0])
     assert (r["p10"], r["median"], r["p90"]) == (1.0, 3.0, 5.0)
+
+
+def test_bench_code_digest_ignores_comments_only(tmp_path):
+    """The kernel-source digest that keys the committed DRAM traffic figure changes with the code,
+    not with comments, layout or comment markers inside string literals."""
+    from bench import code_digest, profiled_traffic
+    base = 'int f(int x) {\n    return x + 1;  // one\n}\nconst char* s = "a // b /* c */";\n'
+    variants = {
+        "same": 'int f(int x) {\n    /* block\n comment */ return x + 1;\n}\n// trailing\nconst char* s = "a // b /* c */";\n',
+        "layout": 'int f(int x) { return x + 1; }\n\n\nconst char* s = "a // b /* c */";',
+        "code": 'int f(int x) {\n    return x + 2;  // one\n}\nconst char* s = "a // b /* c */";\n',
+        "string": 'int f(int x) {\n    return x + 1;  // one\n}\nconst char* s = "a // b /* d */";\n',
+    }
+    p = tmp_path / "k.cu"
+    p.write_text(base)
+    d0 = code_digest(str(p))
+    for name, text in variants.items():
+        p.write_text(text)
+        assert (code_digest(str(p)) == d0) == (name in ("same", "layout")), name
+    # the committed traffic line parses: a figure while the code matches, a stale marker after
+    n, src = profiled_traffic("fused_down1", "8x4k")
+    assert src.startswith("profiles/down1_8x4k.md") and (n == 1362720304 or "stale" in src), src
