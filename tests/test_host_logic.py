@@ -98,3 +98,83 @@ def test_bench_code_digest_ignores_comments_only(tmp_path):
     # the committed traffic line parses: a figure while the code matches, a stale marker after
     n, src = profiled_traffic("fused_down1", "8x4k")
     assert src.startswith("profiles/down1_8x4k.md") and (n == 1362720304 or "stale" in src), src
+
+
+class _ReprojectionRig:
+    """Stands in for a Rig on the host: the loss is the squared distance, in source pixels, between
+    where each camera's parameters and its true parameters send a grid of canvas points, plus a
+    gain term; its gradient is exact.  The host side of the refinement (corner parametrisation,
+    chain rule through StitchLoss, gauge, Adam) then runs alone."""
+
+    def __init__(self, cameras, target, signs, boxes):
+        import torch
+        self.cameras, self.signs = cameras, signs
+        self.target = torch.as_tensor(target)
+        self.pts = []
+        for (x0, y0, x1, y1) in boxes:
+            xs, ys = np.meshgrid(np.linspace(x0, x1, 5), np.linspace(y0, y1, 5))
+            self.pts.append(torch.tensor(np.stack([xs.ravel(), ys.ravel(), np.ones(25)]), dtype=torch.float64))
+        self.calls = 0
+
+    def camera_map(self, i):
+        return np.diag([1.0, 1.0, self.signs[i]]), True
+
+    def _loss(self, p):
+        import torch
+        total = torch.zeros((), dtype=torch.float64)
+        for i, x in enumerate(self.pts):
+            def proj(q):
+                A = torch.cat([q[:8], torch.tensor([self.signs[i]], dtype=torch.float64)]).reshape(3, 3)
+                h = A @ x
+                return h[:2] / h[2:3]
+            total = total + ((proj(p[i]) - proj(self.target[i])) ** 2).sum() + (100.0 * (p[i, 8] - self.target[i, 8])) ** 2
+        return total
+
+    def backward(self, frames, p):
+        import torch
+        self.calls += 1
+        with torch.enable_grad():  # called from inside an autograd.Function's forward
+            q = p.detach().clone().requires_grad_(True)
+            loss = self._loss(q)
+            (g,) = torch.autograd.grad(loss, q)
+        return loss.detach().reshape(1), g
+
+
+def test_refine_host_side_converges_and_keeps_the_gauge():
+    torch = pytest.importorskip("torch")
+    from paper_1810_03988_gb300.autograd import StitchLoss, corners_of, params_from_corners, refine
+    cfg = synth.config_refine(scale=0.25)
+    n = len(cfg.cameras)
+    sizes = [(c.width, c.height) for c in cfg.cameras]
+    true_c = np.stack([corners_of(c.H, c.width, c.height) for c in cfg.cameras])
+    true_g = np.ones(n)
+    signs = [float(np.sign(oracle.invert_h(c.H)[2, 2])) for c in cfg.cameras]
+    target = params_from_corners(torch.tensor(true_c), torch.tensor(true_g), sizes, signs).detach()
+    boxes = [(c[:, 0].min(), c[:, 1].min(), c[:, 0].max(), c[:, 1].max()) for c in true_c]
+    rig = _ReprojectionRig(cfg.cameras, target, signs, boxes)
+    frames = [torch.zeros(1)]
+    rng = np.random.default_rng(3)
+    start = true_c.copy()
+    start[1:] += rng.uniform(-3, 3, start[1:].shape)
+    gains0 = np.r_[1.0, rng.uniform(0.8, 1.2, n - 1)]
+    # the gradient that reaches the corner offsets is the chain rule through the DLT: check it
+    # against central differences of the same loss
+    offs = torch.zeros((n, 4, 2), dtype=torch.float64, requires_grad=True)
+    gains = torch.tensor(gains0)
+    StitchLoss.apply(params_from_corners(torch.tensor(start) + offs, gains, sizes, signs), rig, frames).backward()
+    eps = 1e-4
+    for (i, k, j) in [(1, 0, 0), (2, 3, 1), (3, 2, 0)]:
+        dp = torch.zeros((n, 4, 2), dtype=torch.float64)
+        dp[i, k, j] = eps
+        lp = rig.backward(frames, params_from_corners(torch.tensor(start) + dp, gains, sizes, signs))[0]
+        lm = rig.backward(frames, params_from_corners(torch.tensor(start) - dp, gains, sizes, signs))[0]
+        fd = float((lp - lm)[0]) / (2 * eps)
+        assert abs(fd - float(offs.grad[i, k, j])) <= 1e-5 * max(1.0, abs(fd)), (i, k, j)
+    corners, g, hist = refine(rig, frames, start, gains0, steps=60)
+    assert len(hist) == 60 and rig.calls >= 60 + 7
+    assert hist[-1] < 0.05 * hist[0]
+    np.testing.assert_array_equal(corners[0], start[0])  # camera 0 is the gauge: never moves
+    assert g[0] == gains0[0]
+    err0 = np.abs(start[1:] - true_c[1:]).mean()
+    assert np.abs(corners[1:] - true_c[1:]).mean() < 0.3 * err0
+    assert np.abs(g[1:] - 1.0).mean() < np.abs(gains0[1:] - 1.0).mean()
