@@ -62,3 +62,5 @@ def test_gpu_arm_prints_the_contract_line():
     assert e2e["value"] > 0 and e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
     assert line["gpu_launches"] >= 5 and line["cpu_baseline"]["kind"] == "oracle"
     assert "sm_mhz" in line["clocks"] and "reasons" in line["clocks"]
+    fm = line["frame_ms"]
+    assert fm["frames"] == 5 and 0 < fm["p10"] <= fm["median"] <= fm["p90"]
