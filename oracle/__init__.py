@@ -158,12 +158,22 @@ def _cam_arrays(cams, frames):
     Hs = np.array([c.height for c in cams], dtype=np.int32)
     Ms = np.ascontiguousarray(np.stack([np.asarray(c.H, dtype=np.float64).reshape(9) for c in cams]))
     gains = np.array([float(getattr(c, "gain", 1.0)) for c in cams], dtype=np.float64)
-    frames = [np.ascontiguousarray(f, dtype=np.uint8) for f in frames]
-    for c, f in zip(cams, frames):
-        assert f.shape == (c.height, c.width, 3), (f.shape, c.width, c.height)
+    frames = _frames(frames, Ws, Hs)
     fp = (ctypes.c_void_p * n)(*[f.ctypes.data for f in frames])
     pitches = np.array([f.strides[0] for f in frames], dtype=np.int64)
     return Ws, Hs, Ms, gains, fp, pitches, frames
+
+
+def _frames(frames, widths, heights):
+    """Contiguous uint8 copies of one (H, W, 3) frame per camera; ValueError on a count or shape
+    that does not match the cameras (the C code reads H rows of 3 W bytes from each)."""
+    frames = [np.ascontiguousarray(f, dtype=np.uint8) for f in frames]
+    if len(frames) != len(widths):
+        raise ValueError(f"expected {len(widths)} frames, got {len(frames)}")
+    for k, (f, w, h) in enumerate(zip(frames, widths, heights)):
+        if f.shape != (int(h), int(w), 3):
+            raise ValueError(f"frame {k}: expected shape ({int(h)}, {int(w)}, 3), got {f.shape}")
+    return frames
 
 
 def regions(canvas_w: int, canvas_h: int, levels: int, window=None) -> np.ndarray:
@@ -231,7 +241,7 @@ def warp(cam, frame, canvas_w: int, canvas_h: int, canvas=None):
     """Level 0 of one camera on the whole canvas: (I_i as HcxWcx3, raw feather weight HcxWc);
     ``canvas`` as for forward."""
     lib = _load()
-    frame = np.ascontiguousarray(frame, dtype=np.uint8)
+    frame = _frames([frame], [cam.width], [cam.height])[0]
     M = np.ascontiguousarray(np.asarray(cam.H, dtype=np.float64).reshape(9))
     img = np.empty((canvas_h, canvas_w, 3))
     wr = np.empty((canvas_h, canvas_w))
@@ -255,7 +265,7 @@ def loss_grad(widths, heights, params, frames, window, mask_params=None, grad: b
     Hs = np.asarray(heights, dtype=np.int32)
     p = np.ascontiguousarray(params, dtype=np.float64).reshape(n, 9)
     mp = None if mask_params is None else np.ascontiguousarray(mask_params, dtype=np.float64).reshape(n, 9)
-    frames = [np.ascontiguousarray(f, dtype=np.uint8) for f in frames]
+    frames = _frames(frames, Ws, Hs)
     fp = (ctypes.c_void_p * n)(*[f.ctypes.data for f in frames])
     pitches = np.array([f.strides[0] for f in frames], dtype=np.int64)
     loss = np.zeros(1)
@@ -277,6 +287,8 @@ def lorb(frame, areas, pattern, fast_t: int = 20, harris_t: int = 0, max_points:
     pairs.  Returns dict(xy (n, 2) int32, resp (n,) int64, desc (n, 32) uint8[, resp_map])."""
     lib = _load()
     frame = np.ascontiguousarray(frame, dtype=np.uint8)
+    if frame.ndim != 3 or frame.shape[2] != 3:
+        raise ValueError(f"expected an (H, W, 3) frame, got shape {frame.shape}")
     H, W = frame.shape[:2]
     ar = np.ascontiguousarray(np.asarray(areas, dtype=np.int32).reshape(-1, 4))
     pat = np.ascontiguousarray(np.asarray(pattern, dtype=np.int8).reshape(256, 4))

@@ -650,3 +650,22 @@ def test_full_path_matches_an_independent_numpy_formulation():
         np.tensordot(np.linalg.inv(np.asarray(c.H)), np.stack([xs, ys, np.ones_like(xs)]), 1))).astype(int)
         for c in cams)
     assert (n_cov >= 2).sum() > 50
+
+
+def test_oracle_rejects_frames_that_do_not_match_the_cameras():
+    """The oracle's wrappers refuse frame lists whose count or shapes differ from the cameras (the
+    C code would read past them)."""
+    cams = [Camera(8, 6, np.eye(3)), Camera(8, 6, _T(3, 0))]
+    good = [_rand_frame(6, 8, 1), _rand_frame(6, 8, 2)]
+    oracle.forward(cams, good, 12, 6, 2)
+    with pytest.raises(ValueError, match="expected 2 frames"):
+        oracle.forward(cams, good[:1], 12, 6, 2)
+    with pytest.raises(ValueError, match="frame 1"):
+        oracle.forward(cams, [good[0], good[1][:5]], 12, 6, 2)
+    with pytest.raises(ValueError, match="frame 0"):
+        oracle.warp(cams[0], good[0][:, :7], 12, 6)
+    p = np.array([np.r_[np.eye(3).reshape(9)[:8], 1.0]] * 2)
+    with pytest.raises(ValueError, match="expected 2 frames"):
+        oracle.loss_grad([8, 8], [6, 6], p, good[:1], (0, 0, 12, 6))
+    with pytest.raises(ValueError, match=r"\(H, W, 3\)"):
+        oracle.lorb(good[0][..., 0], [(0, 0, 8, 6)], synth.brief_pattern(0))
