@@ -555,8 +555,21 @@ def main():
                 "share": tot_ms / sum(v[0] for v in kt.values()), "algorithmic_flops_per_launch": flops,
                 "hbm_achieved_gbs_compulsory": cbytes / (ms / 1e3) / 1e9, "hbm_peak_gbs": hbm_peak,
                 "hbm_peak_source": f"{peak_kind} hbm_gbs (copy)"}
+    # the whole step against both roofs: HBM on the compulsory bytes, FP32 ALU on the method's
+    # operation count per step (see STEP_FLOPS_* below) at the clock sampled in the timed region
+    step_flops = info["roi_pixels"] * STEP_FLOPS_PER_CAMERA_PX + cfg.canvas_w * cfg.canvas_h * STEP_FLOPS_PER_CANVAS_PX
+    alu_peak = fp32_peak_tflops(clk.get("sm_mhz"), sms)
+    alu_floor_ms = step_flops / (alu_peak * 1e12) * 1e3
+    hbm_floor_ms = cbytes / (hbm_peak * 1e9) * 1e3
     step_roof = {"achieved": cbytes / (ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                 "frac": cbytes / (ms / 1e3) / 1e9 / hbm_peak, "compulsory_bytes_per_step": cbytes}
+                 "frac": cbytes / (ms / 1e3) / 1e9 / hbm_peak, "compulsory_bytes_per_step": cbytes,
+                 "hbm_floor_ms": hbm_floor_ms,
+                 "algorithmic_flops_per_step": step_flops, "alu_peak_tflops": alu_peak,
+                 "alu_achieved_tflops": step_flops / (ms / 1e3) / 1e12,
+                 "alu_floor_ms": alu_floor_ms, "alu_frac": alu_floor_ms / ms,
+                 "floor_ms": max(alu_floor_ms, hbm_floor_ms), "floor_frac": max(alu_floor_ms, hbm_floor_ms) / ms,
+                 "flops_model": f"{STEP_FLOPS_PER_CAMERA_PX} per planned camera level-0 pixel (warp 40, REDUCE 40, "
+                                f"EXPAND 35, blend 13) + {STEP_FLOPS_PER_CANVAS_PX} per canvas pixel (collapse)"}
 
     plain = None
     if args.path == "fused" and not args.no_plain:
@@ -686,6 +699,10 @@ def main():
 FLOPS_WARP = 44
 FLOPS_REDUCE1 = 30
 FLOPS_BLEND = 50
+# The whole step, as the scope's measurement plan counts it: per planned camera level-0 pixel warp
+# 40 + REDUCE 40 + EXPAND 35 + blend 13 (~130, across all levels), per canvas pixel collapse 35.
+STEP_FLOPS_PER_CAMERA_PX = 130
+STEP_FLOPS_PER_CANVAS_PX = 35
 
 PROFILES = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles")
 KERNEL_SOURCE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1810_03988_gb300", "csrc",

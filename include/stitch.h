@@ -176,9 +176,9 @@ const char* stitch_status_string(stitch_status s);
 
 /*
  * Stitch one frame set with no device allocation at all (the paper has no counterpart; this is
- * a deployment convenience).  Callers that cannot call cudaMalloc (code running inside a CUDA
- * graph capture or replay, real-time loops that cannot afford the allocator's implicit device
- * synchronisation, hosts that hand the library a fixed memory budget) describe the rig in `desc`
+ * a deployment convenience).  Callers that cannot call cudaMalloc (real-time loops that cannot
+ * afford the allocator's implicit device synchronisation, hosts that hand the library a fixed
+ * memory budget, plugins whose host application owns every device allocation) describe the rig in `desc`
  * and get the same result as a STITCH_PATH_PLAIN rig's stitch_frames: the plain-path kernels run
  * with every scratch buffer carved from one file-scope device array of STITCH_STATIC_SCRATCH_BYTES
  * (64 MiB) that each GPU loading the library holds until the process exits.
@@ -186,8 +186,10 @@ const char* stitch_status_string(stitch_status s);
  *            the host stack, so each call also re-validates the geometry
  *   frames, pitches, out, out_pitch, stream   as for stitch_frames, on the CURRENT device
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Every call shares the array
- * and keeps the last call's contents; calls whose kernels overlap on the GPU race on it.  A rig
+ * device current and keeps it; make that first call before any stream capture.  Calls on a device
+ * after cudaDeviceReset are not supported (the kept address belonged to the reset context).  Every
+ * call shares the array and keeps the last call's contents; calls whose kernels overlap on the GPU
+ * (other streams or host threads) race on it.  A rig
  * needing more scratch than the array holds returns STITCH_ETOOLARGE before any GPU work.
  * Status: OK, EINVAL, ETOOLARGE, ECUDA.
  */

@@ -109,6 +109,7 @@ struct D1Cams {
 constexpr int D1_INTERIOR = 1;  // inputs solidly inside the camera, no other camera: weight 1
 constexpr int D1_SOLO_OUT = 2;  // the canvas tile under this tile is SOLO for this camera
 constexpr int D1_G0_OUT = 4;    // the canvas tile under this tile is FULL: write its level-0 samples
+constexpr int D1_NOCLAMP = 8;   // every input maps at least 0.01 px inside the image: no coordinate clamping
 
 // up tile: level-0 origin and the contributing cameras (CamRef range), in camera order.
 struct UpTile {
@@ -116,46 +117,103 @@ struct UpTile {
 };
 
 // ------------------------------------------------------------------------------------------------
+// packed single-precision pairs (f32x2: two IEEE binary32 lanes, each rounded exactly as the
+// scalar operation), used where the path computes on pairs of channels
+
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+#define STITCH_F2_BINOP(name, op)                                                           \
+    __device__ __forceinline__ float2 name(float2 a, float2 b) {                            \
+        float2 d;                                                                           \
+        asm("{\n\t.reg .b64 ra, rb, rd;\n\t"                                                \
+            "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t" op                         \
+            " rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"                                    \
+            : "=f"(d.x), "=f"(d.y)                                                          \
+            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                      \
+        return d;                                                                           \
+    }
+STITCH_F2_BINOP(f2add, "add.rn.f32x2")
+STITCH_F2_BINOP(f2sub, "sub.rn.f32x2")
+STITCH_F2_BINOP(f2mul, "mul.rn.f32x2")
+STITCH_F2_BINOP(f2add_rm, "add.rm.f32x2")  // rounded toward -infinity
+#undef STITCH_F2_BINOP
+
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+// (r, g, b, weight) as two pairs
+struct V4 {
+    float2 a, b;
+};
+__device__ __forceinline__ V4 v4_mul(float2 w, V4 s) { return {f2mul(w, s.a), f2mul(w, s.b)}; }
+__device__ __forceinline__ V4 v4_fma(float2 w, V4 s, V4 acc) { return {f2fma(w, s.a, acc.a), f2fma(w, s.b, acc.b)}; }
+__device__ __forceinline__ V4 v4_of(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+__device__ __forceinline__ float4 f4_of(V4 v) { return make_float4(v.a.x, v.a.y, v.b.x, v.b.y); }
+
+// ------------------------------------------------------------------------------------------------
 // down1
+//
+// One block of 64 threads per tile of 32 x 8 level-1 outputs of one camera, on the global grid.
+// The tile's level-0 virtual region is 67 x 19 samples (columns 2 k0 - 2 .. 2 k0 + 64, rows
+// 2 j0 - 2 .. 2 j0 + 16, folded at the canvas borders).  Thread c takes virtual column c < 64 and
+// sweeps its 19 rows: it warps every sample (S1, S2) and feeds it straight into the vertical
+// REDUCE pass (S3), whose three running sums stay in registers; each finished level-1 row goes to
+// shared memory.  The last three columns are one sample per thread.  The horizontal REDUCE pass
+// then reads the 8 x 67 vertically reduced values and writes G^1.  The source footprint of the
+// tile's samples is staged in shared memory as one 32-bit word per texel (R, G, B bytes), so a
+// bilinear tap is four 32-bit shared loads.
 
-constexpr int D1_TX = 32, D1_TY = 16;                        // level-1 outputs per tile
-constexpr int D1_SX = 2 * D1_TX + 3, D1_SY = 2 * D1_TY + 3;  // level-0 virtual region (67 x 35)
-constexpr int D1_THREADS = 256;
-constexpr int D1_BLOCKS_PER_SM = 3;  // resident blocks per SM (launch bound; registers and shared memory)
-constexpr int D1_SXH = (D1_SX + 1) / 2;  // level-0 samples are stored as even and odd column planes
-// Source footprint capacity in texels.  The footprint is staged as three planes of floats (R, G,
-// B; rows padded to a multiple of 4 texels) and shares its space with the horizontal REDUCE
-// buffer, which is used after the samples are taken.  With it a block needs ~73 KB of shared
-// memory, so three blocks fit on an SM.
-constexpr int D1_FOOT = 3072;
-constexpr int D1_S0_F4 = 2 * D1_SXH * D1_SY;                                    // level-0 planes
-constexpr int D1_SH_F4 = 3 * D1_FOOT / 4 > D1_TX * D1_SY ? 3 * D1_FOOT / 4 : D1_TX * D1_SY;  // footprint / sh
-constexpr int D1_ROW_F4 = (D1_SY + 3) / 4;                                      // per-row offsets
-constexpr size_t D1_SMEM = sizeof(float4) * (D1_S0_F4 + D1_SH_F4 + D1_ROW_F4);
-static_assert(D1_THREADS == 256 && D1_SX == 67, "the staged pass maps 64 columns x 4 row phases");
+constexpr int D1_TX = 32, D1_TY = 8;                         // level-1 outputs per tile
+constexpr int D1_SX = 2 * D1_TX + 3, D1_SY = 2 * D1_TY + 3;  // level-0 virtual region (67 x 19)
+constexpr int D1_THREADS = 64;                               // one thread per virtual column 0..63
+constexpr int D1_XC = D1_SX - D1_THREADS;                    // the last 3 columns: one sample per thread
+constexpr int D1_BLOCKS_PER_SM = 12;                         // resident blocks per SM (shared memory)
+constexpr int D1_NSAMP = D1_SX * D1_SY;                      // level-0 samples of a tile's region
+// a FULL canvas tile's level-0 slot (64 x 32 samples per blended camera), written by the camera's
+// two down1 tiles over it (rows 0..15 and 16..31)
+constexpr int D1_SLOT = (2 * D1_TX) * (4 * D1_TY);
+// Footprint capacity in texels (one 32-bit word each; rows padded to a multiple of 4 texels).
+constexpr int D1_FOOT = 2048;
+// Vertically reduced values: per level-1 row, the even columns at slots 0..33 and the odd columns
+// at slots 36..68 (float4), so that a warp's 128-bit stores of 32 consecutive columns and the
+// horizontal pass's loads of consecutive even (odd) columns are free of bank conflicts.
+constexpr int D1_VODD = 36, D1_VROW = 70;
+constexpr int D1_SM_FOOT = 4 * D1_FOOT;                      // bytes
+constexpr int D1_SM_V = 16 * D1_VROW * D1_TY;
+constexpr int D1_SM_X = 16 * D1_XC * D1_SY;
+constexpr int D1_SM_ROW = 8 * ((D1_SY + 1) & ~1);            // (dy, dy) per row
+constexpr size_t D1_SMEM = D1_SM_FOOT + D1_SM_V + D1_SM_X + D1_SM_ROW;
+static_assert(D1_SX == 67 && D1_THREADS == 64 && D1_XC == 3, "column-per-thread sweep of a 67-column region");
+static_assert(D1_SM_FOOT % 16 == 0 && D1_SM_V % 16 == 0 && D1_SM_X % 16 == 0, "16-byte aligned parts");
 
-// Shared-memory slot of level-0 virtual sample (row r, column c): even and odd columns in separate
-// planes, so the horizontal REDUCE pass (columns 2p .. 2p+4 for output p) reads consecutive slots.
-__device__ __forceinline__ int s0_slot(int r, int c) { return r * (2 * D1_SXH) + (c & 1) * D1_SXH + (c >> 1); }
+__device__ __forceinline__ int d1_vslot(int c) { return (c & 1) * D1_VODD + (c >> 1); }
 
-constexpr int D1_NSAMP = D1_SX * D1_SY;  // level-0 samples of a tile's virtual region
+// REDUCE taps [1, 4, 6, 4, 1] / 16 as pairs
+__device__ __forceinline__ float2 d1_w(int n) { return f2(n == 0 || n == 4 ? 0.0625f : n == 2 ? 0.375f : 0.25f); }
 
 // Normalised feather weights of the level-0 samples of a down1 tile (S2: w_i / sum_j w_j over the
 // cameras whose validity box contains the sample), or -1 for samples outside the camera's pyramid
 // region Omega^0_i.  They depend on the geometry only, so the rig computes them once at creation
 // (the paper's pre-corrected parameters, Algorithm 4, and start-up preallocation, Sec. 4.3.2), one
 // block per tile; down1 then warps only its own camera.
-__global__ void __launch_bounds__(D1_THREADS) k_d1_weights(const CamDev* __restrict__ cams, RigGeom g,
-                                                          const D1Tile* __restrict__ tiles,
-                                                          const D1Cams* __restrict__ tcams,
-                                                          const CamRef* __restrict__ refs, float* __restrict__ d1w) {
+constexpr int D1W_THREADS = 256;
+__global__ void __launch_bounds__(D1W_THREADS) k_d1_weights(const CamDev* __restrict__ cams, RigGeom g,
+                                                           const D1Tile* __restrict__ tiles,
+                                                           const D1Cams* __restrict__ tcams,
+                                                           const CamRef* __restrict__ refs, float* __restrict__ d1w) {
     const D1Tile tl = tiles[blockIdx.x];
     const D1Cams tc = tcams[blockIdx.x];
     if (tl.wtab < 0) return;
     const Rect o0 = cams[tl.cam].Om[0];
     const int vx0 = 2 * tl.k0 - 2, vy0 = 2 * tl.j0 - 2;
     float* out = d1w + (long long)tl.wtab * D1_NSAMP;
-    for (int q = threadIdx.x; q < D1_NSAMP; q += D1_THREADS) {
+    for (int q = threadIdx.x; q < D1_NSAMP; q += D1W_THREADS) {
         const int r = q / D1_SX, c = q % D1_SX;
         const int x = fold101(vx0 + c, g.nx[0]), y = fold101(vy0 + r, g.ny[0]);
         if (!o0.contains(x, y)) {
@@ -193,40 +251,43 @@ __global__ void __launch_bounds__(D1_THREADS) k_d1_weights(const CamDev* __restr
     }
 }
 
-__device__ __forceinline__ void store_u8_tile(const unsigned char* __restrict__ stage, const OutDesc& od, int X0,
-                                              int Y0, int X1, int Y1);
-__device__ __forceinline__ void put_pixel(unsigned char* stage, const OutDesc& od, int dx, int dy, int x, int y,
-                                          float r, float g, float b);
-
-// Copy the footprint [fx0, fx0 + fw) x [fy0, fy0 + fh) of an RGB8 frame into shared memory as
-// three planes of floats (exact integer values) with rows of fw4 = fw rounded up to 4 texels.  A
-// thread takes groups of 4 texels (12 bytes: three aligned 32-bit words, since fx0 is a multiple
-// of 4), issues the loads of all its groups before converting, and writes each plane's 4 values
-// with one 16-byte store.  Frames whose base or pitch is not a multiple of 4 bytes are read byte
-// by byte.
-constexpr int D1_SG = (D1_FOOT / 4 + D1_THREADS - 1) / D1_THREADS;  // groups per thread
-
-__device__ __forceinline__ float byte_f(uint32_t w, uint32_t j) {
-    return __int_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | j)) - 8388608.0f;
+// One output pixel written straight to the canvas (8-bit: round half to even of 255 v).
+__device__ __forceinline__ void put_pixel_direct(const OutDesc& od, int x, int y, float r, float g, float b) {
+    char* row = (char*)od.ptr + (long long)y * od.pitch;
+    if (od.is_float) {
+        float* o = (float*)row + 3 * x;
+        o[0] = r;
+        o[1] = g;
+        o[2] = b;
+    } else {
+        unsigned char* o = (unsigned char*)row + 3 * x;
+        o[0] = quantize_u8(r);
+        o[1] = quantize_u8(g);
+        o[2] = quantize_u8(b);
+    }
 }
 
-__device__ __forceinline__ void stage_footprint(float* __restrict__ foot, const uint8_t* __restrict__ px,
+// Copy the footprint [fx0, fx0 + fw) x [fy0, fy0 + fh) of an RGB8 frame into shared memory, one
+// word per texel (bytes R, G, B, and one unused byte), rows of S = fw rounded up to 4 texels.  A
+// thread takes groups of 4 texels (12 bytes: three aligned 32-bit words, since fx0 is a multiple of
+// 4), issues the loads of all its groups before repacking, and writes the 4 texel words with one
+// 16-byte store.  Frames whose base or pitch is not a multiple of 4 bytes are read byte by byte.
+constexpr int D1_SG = D1_FOOT / 4 / D1_THREADS;  // groups per thread
+static_assert(D1_SG * 4 * D1_THREADS == D1_FOOT, "whole groups per thread");
+
+__device__ __forceinline__ void stage_footprint(uint32_t* __restrict__ foot, const uint8_t* __restrict__ px,
                                                 long long pitch, int W, int fx0, int fy0, int fw, int fh) {
     const int t = threadIdx.x;
-    const int gpr = (fw + 3) >> 2, ng = gpr * fh;  // groups per row = fw4 / 4
+    const int gpr = (fw + 3) >> 2, ng = gpr * fh;  // groups per row = S / 4
     if (((reinterpret_cast<uintptr_t>(px) | (uintptr_t)pitch) & 3) != 0) {
         for (int q = t; q < 4 * ng; q += D1_THREADS) {
             const int rr = q / (4 * gpr), u = q - rr * 4 * gpr;
-            float r = 0.f, g = 0.f, b = 0.f;
+            uint32_t w = 0u;
             if (u < fw) {
                 const uint8_t* src = px + (long long)(fy0 + rr) * pitch + 3 * (fx0 + u);
-                r = u8_to_f(__ldg(src));
-                g = u8_to_f(__ldg(src + 1));
-                b = u8_to_f(__ldg(src + 2));
+                w = (uint32_t)__ldg(src) | ((uint32_t)__ldg(src + 1) << 8) | ((uint32_t)__ldg(src + 2) << 16);
             }
-            foot[q] = r;
-            foot[D1_FOOT + q] = g;
-            foot[2 * D1_FOOT + q] = b;
+            foot[q] = w;
         }
         return;
     }
@@ -257,136 +318,163 @@ __device__ __forceinline__ void stage_footprint(float* __restrict__ foot, const 
     for (int k = 0; k < D1_SG; ++k) {
         const int q = t + k * D1_THREADS;
         if (q < ng) {
-            // texels 4q .. 4q+3 of the padded rows (bytes R G B R | G B R G | B R G B)
-            float4* r4 = reinterpret_cast<float4*>(foot) + q;
-            r4[0] = make_float4(byte_f(w[k][0], 0), byte_f(w[k][0], 3), byte_f(w[k][1], 2), byte_f(w[k][2], 1));
-            r4[D1_FOOT / 4] = make_float4(byte_f(w[k][0], 1), byte_f(w[k][1], 0), byte_f(w[k][1], 3), byte_f(w[k][2], 2));
-            r4[D1_FOOT / 2] = make_float4(byte_f(w[k][0], 2), byte_f(w[k][1], 1), byte_f(w[k][2], 0), byte_f(w[k][2], 3));
+            // bytes R0 G0 B0 R1 | G1 B1 R2 G2 | B2 R3 G3 B3 -> one word per texel
+            reinterpret_cast<uint4*>(foot)[q] =
+                make_uint4(__byte_perm(w[k][0], 0u, 0x0210), __byte_perm(w[k][0], w[k][1], 0x0543),
+                           __byte_perm(w[k][1], w[k][2], 0x0432), __byte_perm(w[k][2], 0u, 0x0321));
         }
     }
 }
 
-// One level-0 sample from the staged footprint (planes R, G, B of D1_FOOT floats, rows of fw4).
-// (nu, nv, den) are the anchored numerators and denominator of the camera's TileMap at the
-// sample, bu = U0 - fx0 and bv = V0 - fy0.  Position, taps and arithmetic are those of map_pos +
-// sample_rgb (CLAMP) or sample_rgb_inside (!CLAMP), so the result is bit-identical whenever the
-// planned footprint holds the taps (the planner bounds |u|, |v| < 1e6 for staged tiles, so
-// map_pos's range clamp has no effect there).  Footprint-local taps are clamped into the
-// footprint: any other position reads a wrong texel of the footprint, never outside it; such
-// positions only feed level-1 samples outside the pyramid region, which are not stored.
-template <bool CLAMP>
-__device__ __forceinline__ float3 foot_sample(const float* __restrict__ foot, int fw, int fw4, int fh, int bu,
-                                              int bv, int fx0, int fy0, int W, int H, float nu, float nv,
-                                              float den, float scale) {
+// 2^23 + byte j of w, as a float (exact)
+__device__ __forceinline__ float d1_bf(uint32_t w, uint32_t j) { return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | j)); }
+
+// Bilinear RGB of four texel words with fractions (fx, fy), times `scale`.  The arithmetic is that
+// of sample_rgb (top = p00 + fx (p01 - p00), bot likewise, value = top + fy (bot - top), then the
+// scale), on exact 2^23-offset values whose differences are the byte differences, so the result
+// is bit-identical.  R and G go as one pair.
+__device__ __forceinline__ void d1_bilerp(uint32_t w00, uint32_t w01, uint32_t w10, uint32_t w11, float fx, float fy,
+                                          float scale, V4& s) {
+    constexpr float K23 = 8388608.0f;
+    const float2 a00 = make_float2(d1_bf(w00, 0), d1_bf(w00, 1)), a01 = make_float2(d1_bf(w01, 0), d1_bf(w01, 1));
+    const float2 a10 = make_float2(d1_bf(w10, 0), d1_bf(w10, 1)), a11 = make_float2(d1_bf(w11, 0), d1_bf(w11, 1));
+    const float2 fxx = f2(fx), fyy = f2(fy);
+    const float2 top = f2fma(fxx, f2sub(a01, a00), f2sub(a00, f2(K23)));
+    const float2 bot = f2fma(fxx, f2sub(a11, a10), f2sub(a10, f2(K23)));
+    s.a = f2mul(f2fma(fyy, f2sub(bot, top), top), f2(scale));
+    const float b00 = d1_bf(w00, 2), b01 = d1_bf(w01, 2), b10 = d1_bf(w10, 2), b11 = d1_bf(w11, 2);
+    const float btop = fmaf(fx, b01 - b00, b00 - K23), bbot = fmaf(fx, b11 - b10, b10 - K23);
+    s.b.x = fmaf(fy, bbot - btop, btop) * scale;
+}
+
+// Per-tile constants of the sweep.
+struct D1Ctx {
+    TileMap tm;
+    const uint32_t* foot;  // staged footprint
+    const float2* rowdy;   // (dy, dy) of every virtual row: canvas row minus the anchor row
+    const float* wt;       // normalised weights of the tile's samples (67 x 19), or null
+    const uint8_t* px;     // frame (paths that read taps from it)
+    long long pitch;
+    int S;                 // footprint row stride (words)
+    int fw, fh, fx0, fy0;  // footprint
+    unsigned ibase;        // index of the top-left tap from the floor constants, see d1_sample
+    int maxidx;            // largest top-left index whose four taps lie in the footprint
+    int W, H;
+    float scale, fU0, fV0;
+};
+
+// Sample modes: staged footprint without clamping, weight 1 (INTERIOR tiles) or from the table;
+// staged with the image clamp of S1 (tiles at the image border); taps read from the frame
+// (footprints too large to stage or reaching behind the camera), weight 1 or from the table.
+enum D1Mode { D1M_INTERIOR = 0, D1M_NOCLAMP = 1, D1M_CLAMP = 2, D1M_G_INTERIOR = 3, D1M_G_TABLE = 4 };
+
+constexpr float D1_FLOOR_M = 12582912.0f;       // 1.5 * 2^23
+constexpr unsigned D1_FLOOR_BITS = 0x4B400000u;  // its bit pattern
+
+// Level-0 sample of virtual row r at the column whose anchored numerators and denominator at the
+// anchor row are (nuc, nvc, dqc): (r, g, b, normalised weight), zero outside Omega^0 (a < 0).
+// Position and taps are those of map_pos + sample_rgb (or sample_rgb_inside), so the staged and
+// the frame-reading modes give bit-identical samples.  The floor of the offsets ru, rv (|ru|, |rv|
+// < 2^22 on staged tiles, whose footprint the planner bounds) comes from one addition rounded
+// toward -infinity: RD(ru + 1.5 2^23) = 1.5 2^23 + floor(ru), whose low bits hold the integer.
+template <int MODE>
+__device__ __forceinline__ V4 d1_sample(const D1Ctx& x, float2 nuv, float dqc, int r, float a) {
+    const float2 dy = x.rowdy[r];
+    const float den = fmaf(x.tm.q2, dy.x, dqc);
+    const float2 n = f2fma(make_float2(x.tm.pu2, x.tm.pv2), dy, nuv);
     const float rden = __fdividef(1.0f, den);
-    const float ru = nu * rden, rv = nv * rden;
-    const float flu = floorf(ru), flv = floorf(rv);
-    float fx = ru - flu, fy = rv - flv;
-    const int lu = bu + (int)flu, lv = bv + (int)flv;  // footprint-local top-left tap
-    int lx, ly, ox, oy;
-    if (CLAMP) {
-        // image clamp of S1: outside [0, W-1) x [0, H-1) the border texel, fraction 0
-        if ((unsigned)(lu + fx0) >= (unsigned)(W - 1)) fx = 0.0f;
-        if ((unsigned)(lv + fy0) >= (unsigned)(H - 1)) fy = 0.0f;
-        lx = min(max(lu, 0), fw - 1);
-        ly = min(max(lv, 0), fh - 1);
-        ox = lx < fw - 1 ? 1 : 0;
-        oy = ly < fh - 1 ? fw4 : 0;
+    V4 s;
+    s.b.y = (MODE == D1M_INTERIOR || MODE == D1M_G_INTERIOR) ? 1.0f : a;
+    if (MODE == D1M_G_INTERIOR || MODE == D1M_G_TABLE) {
+        float ru = n.x * rden, rv = n.y * rden;
+        ru = fminf(fmaxf(ru, -1.0e7f), 1.0e7f);
+        rv = fminf(fmaxf(rv, -1.0e7f), 1.0e7f);
+        const float flu = floorf(ru), flv = floorf(rv);
+        Pos p;
+        p.iu = x.tm.U0 + (int)flu;
+        p.iv = x.tm.V0 + (int)flv;
+        p.fu = ru - flu;
+        p.fv = rv - flv;
+        const float3 v = MODE == D1M_G_INTERIOR ? sample_rgb_inside(x.px, x.pitch, p, x.scale)
+                                                : sample_rgb(x.px, x.pitch, p, x.W, x.H, x.scale);
+        s.a = make_float2(v.x, v.y);
+        s.b.x = v.z;
     } else {
-        lx = min(max(lu, 0), fw - 2);
-        ly = min(max(lv, 0), fh - 2);
-        ox = 1;
-        oy = fw4;
+        const float2 ruv = f2mul(n, f2(rden));
+        const float2 tt = f2add_rm(ruv, f2(D1_FLOOR_M));
+        const float2 f = f2sub(ruv, f2sub(tt, f2(D1_FLOOR_M)));  // fractions in [0, 1)
+        const unsigned tu = __float_as_uint(tt.x), tv = __float_as_uint(tt.y);
+        uint32_t w00, w01, w10, w11;
+        float fx = f.x, fy = f.y;
+        if (MODE != D1M_CLAMP) {
+            // top-left tap (V0 + floor(rv) - fy0) S + (U0 + floor(ru) - fx0), clamped into the footprint
+            const int idx = min(max((int)(tv * (unsigned)x.S + tu + x.ibase), 0), x.maxidx);
+            const uint32_t* p = x.foot + idx;
+            w00 = p[0];
+            w01 = p[1];
+            w10 = p[x.S];
+            w11 = p[x.S + 1];
+        } else {
+            // image clamp of S1: outside [0, W-1) x [0, H-1) the border texel, fraction 0
+            const int lu = (int)(tu - D1_FLOOR_BITS) + (x.tm.U0 - x.fx0), lv = (int)(tv - D1_FLOOR_BITS) + (x.tm.V0 - x.fy0);
+            if ((unsigned)(lu + x.fx0) >= (unsigned)(x.W - 1)) fx = 0.0f;
+            if ((unsigned)(lv + x.fy0) >= (unsigned)(x.H - 1)) fy = 0.0f;
+            const int lx = min(max(lu, 0), x.fw - 1), ly = min(max(lv, 0), x.fh - 1);
+            const int ox = lx < x.fw - 1 ? 1 : 0, oy = ly < x.fh - 1 ? x.S : 0;
+            const uint32_t* p = x.foot + ly * x.S + lx;
+            w00 = p[0];
+            w01 = p[ox];
+            w10 = p[oy];
+            w11 = p[oy + ox];
+        }
+        d1_bilerp(w00, w01, w10, w11, fx, fy, x.scale, s);
     }
-    const float* a = foot + ly * fw4 + lx;
-    float3 o;
-    {
-        const float p00 = a[0], p01 = a[ox], p10 = a[oy], p11 = a[oy + ox];
-        const float top = fmaf(fx, p01 - p00, p00), bot = fmaf(fx, p11 - p10, p10);
-        o.x = fmaf(fy, bot - top, top) * scale;
-    }
-    a += D1_FOOT;
-    {
-        const float p00 = a[0], p01 = a[ox], p10 = a[oy], p11 = a[oy + ox];
-        const float top = fmaf(fx, p01 - p00, p00), bot = fmaf(fx, p11 - p10, p10);
-        o.y = fmaf(fy, bot - top, top) * scale;
-    }
-    a += D1_FOOT;
-    {
-        const float p00 = a[0], p01 = a[ox], p10 = a[oy], p11 = a[oy + ox];
-        const float top = fmaf(fx, p01 - p00, p00), bot = fmaf(fx, p11 - p10, p10);
-        o.z = fmaf(fy, bot - top, top) * scale;
-    }
-    return o;
+    if (MODE != D1M_INTERIOR && MODE != D1M_G_INTERIOR && !(a >= 0.f)) s = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    return s;
 }
 
-// S1 + S2 of a down1 tile from its staged footprint.  Thread t takes virtual column t % 64 at
-// the rows of residue t / 64 mod 4 (D1_RPT rows; the column's map terms are formed once) and,
-// for t < 105, one sample of the last 3 columns.  INTERIOR tiles have weight 1; the others take
-// the normalised weights `a` (loaded by d1_load_weights before the footprint was staged) and take
-// every sample: one outside Omega^0 (a < 0) reads a clamped texel and is then zeroed.
-constexpr int D1_RPT = (D1_SY + 3) / 4;  // rows per thread in the staged pass (9)
-
-__device__ __forceinline__ void d1_load_weights(const float* __restrict__ wt, float a[D1_RPT + 1]) {
-    const int t = threadIdx.x, c = t & 63;
-#pragma unroll
-    for (int k = 0; k < D1_RPT; ++k) {
-        const int r = (t >> 6) + 4 * k;
-        a[k] = r < D1_SY ? __ldg(wt + r * D1_SX + c) : -1.f;
+// Output of a level-0 sample at tile-local canvas position (dx, dy), dy < 16: the SOLO canvas
+// tile's pixel, or the FULL canvas tile's level-0 slot (rows 16 h .. 16 h + 15 for the half h).
+template <typename T>
+__device__ __forceinline__ void d1_out(int flags, const OutDesc& od, T* __restrict__ g0, int X0, int Y0, int nx,
+                                       int ny, int dx, int dy, V4 s) {
+    if (flags & D1_SOLO_OUT) {
+        const int x = X0 + dx, y = Y0 + dy;
+        if (x < nx && y < ny) put_pixel_direct(od, x, y, __saturatef(s.a.x), __saturatef(s.a.y), __saturatef(s.b.x));
     }
-    a[D1_RPT] = t < 3 * D1_SY ? __ldg(wt + (t / 3) * D1_SX + 64 + t % 3) : -1.f;
+    if (flags & D1_G0_OUT) st(g0 + dy * (2 * D1_TX) + dx, f4_of(s));
 }
 
-template <bool INTERIOR>
-__device__ __forceinline__ void d1_staged_samples(float4* __restrict__ s0, const float* __restrict__ foot,
-                                                  const float* __restrict__ rowdy, const float a[D1_RPT + 1],
-                                                  const RigGeom& g, const CamRef& ref, const float4* __restrict__ cols,
-                                                  int vx0, int fx0, int fy0, int fw, int fh, int W, int H, float scale) {
-    const TileMap& tm = ref.tm;
-    // column terms: the anchored homography on the planar canvas, the column table on the
-    // cylindrical one
-    auto colterms = [&](int c, float& nuc, float& nvc, float& dqc) {
-        if (cols) {
-            const float4 cc = cols[c];
-            nuc = cc.x;
-            nvc = cc.y;
-            dqc = cc.z;
-        } else {
-            const float dx = (float)(fold101(vx0 + c, g.nx[0]) - ref.ax);
-            nuc = fmaf(tm.pu1, dx, tm.pu0);
-            nvc = fmaf(tm.pv1, dx, tm.pv0);
-            dqc = fmaf(tm.q1, dx, tm.q0);
+// The sweep of thread c (virtual column c < 64): 19 samples, the vertical REDUCE in registers
+// (output row jj takes rows 2 jj .. 2 jj + 4 in order), level-0 outputs on the fly.  Rows go in
+// pairs (2m, 2m + 1) with two running sums: on entry to pair m, C holds output row m - 2 (taps
+// 0..3 applied) and B row m - 1 (taps 0, 1); row 2m completes C, moves B on by tap 2 into C and
+// starts row m in B; row 2m + 1 adds tap 3 to C and tap 1 to B.
+template <typename T, int MODE>
+__device__ __forceinline__ void d1_sweep(const D1Ctx& x, float4* __restrict__ vres, int c, float2 nuv, float dqc,
+                                         int flags, const OutDesc& od, T* __restrict__ g0, int X0, int Y0, int nx, int ny) {
+    constexpr bool TABLE = MODE != D1M_INTERIOR && MODE != D1M_G_INTERIOR;
+    const bool out = c >= 2 && (flags & (D1_SOLO_OUT | D1_G0_OUT));
+    const V4 zero = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    V4 B = zero, C = zero;
+    float4* vcol = vres + d1_vslot(c);
+    const float* wcol = TABLE ? x.wt + c : nullptr;
+#pragma unroll 1
+    for (int m = 0; m <= D1_TY + 1; ++m) {
+        const int r = 2 * m;
+        {
+            const V4 s = d1_sample<MODE>(x, nuv, dqc, r, TABLE ? __ldg(wcol + r * D1_SX) : 1.0f);
+            if (out && r >= 2 && r < D1_SY - 1) d1_out<T>(flags, od, g0, X0, Y0, nx, ny, c - 2, r - 2, s);
+            if (m >= 2) vcol[(m - 2) * D1_VROW] = f4_of(v4_fma(d1_w(4), s, C));
+            C = v4_fma(d1_w(2), s, B);
+            B = v4_mul(d1_w(0), s);
         }
-    };
-    const int bu = tm.U0 - fx0, bv = tm.V0 - fy0;
-    const int fw4 = (fw + 3) & ~3;
-    const int t = threadIdx.x;
-    auto one = [&](int r, int c, float nuc, float nvc, float dqc, float ak) {
-        const float dy = rowdy[r];
-        const float nu = fmaf(tm.pu2, dy, nuc), nv = fmaf(tm.pv2, dy, nvc), den = fmaf(tm.q2, dy, dqc);
-        if (INTERIOR) {
-            const float3 v = foot_sample<false>(foot, fw, fw4, fh, bu, bv, fx0, fy0, W, H, nu, nv, den, scale);
-            s0[s0_slot(r, c)] = make_float4(v.x, v.y, v.z, 1.f);
-        } else {
-            const float3 v = foot_sample<true>(foot, fw, fw4, fh, bu, bv, fx0, fy0, W, H, nu, nv, den, scale);
-            s0[s0_slot(r, c)] = ak >= 0.f ? make_float4(v.x, v.y, v.z, ak) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r + 1 < D1_SY) {
+            const V4 s = d1_sample<MODE>(x, nuv, dqc, r + 1, TABLE ? __ldg(wcol + (r + 1) * D1_SX) : 1.0f);
+            if (out && m >= 1) d1_out<T>(flags, od, g0, X0, Y0, nx, ny, c - 2, r - 1, s);
+            C = v4_fma(d1_w(3), s, C);
+            B = v4_fma(d1_w(1), s, B);
         }
-    };
-    {
-        const int c = t & 63;
-        float nuc, nvc, dqc;
-        colterms(c, nuc, nvc, dqc);
-#pragma unroll
-        for (int k = 0; k < D1_RPT; ++k) {
-            const int r = (t >> 6) + 4 * k;
-            if (r < D1_SY) one(r, c, nuc, nvc, dqc, INTERIOR ? 1.f : a[k]);
-        }
-    }
-    if (t < 3 * D1_SY) {
-        const int c = 64 + t % 3, r = t / 3;
-        float nuc, nvc, dqc;
-        colterms(c, nuc, nvc, dqc);
-        one(r, c, nuc, nvc, dqc, INTERIOR ? 1.f : a[D1_RPT]);
     }
 }
 
@@ -395,8 +483,10 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
                                            const OutDesc& od, const D1Tile& tl, const CamRef* __restrict__ refs,
                                            const float* __restrict__ d1w, const float4* __restrict__ d1cols,
                                            T* __restrict__ g0buf, float4* smem) {
-    float4* s0 = smem;                        // level 0 (virtual coordinates), see s0_slot
-    float4* sh = smem + D1_S0_F4;             // [D1_SY][D1_TX] horizontally reduced (or the footprint)
+    uint32_t* foot = reinterpret_cast<uint32_t*>(smem);
+    float4* vres = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + D1_SM_FOOT);
+    float4* ext = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + D1_SM_FOOT + D1_SM_V);  // [19][3]
+    float2* rowdy = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem) + D1_SM_FOOT + D1_SM_V + D1_SM_X);
 
     const int i = tl.cam;
     const CamDev& ci = cams[i];
@@ -404,129 +494,134 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
     const int k0 = tl.k0, j0 = tl.j0;              // level-1 tile origin
     const int vx0 = 2 * k0 - 2, vy0 = 2 * j0 - 2;  // level-0 virtual origin
     const int t = threadIdx.x;
-    const float scale = ci.gain * (1.0f / 255.0f);
+    const bool act = t < D1_THREADS;  // a larger block (the batched persistent kernel) idles the rest
+    const CamRef ref = refs[tl.ref];
     const uint8_t* px_i = fp.p[i];
     const long long pitch_i = fp.pitch[i];
 
-    if (tl.pf_fwh != 0) {
+    if (tl.pf_fwh != 0 && act) {
         // L2 prefetch of the staging inputs of the tile one resident wave later: its footprint rows
-        // (8 threads per row, one 128-byte line each, the row's last byte for the tail) and its
-        // weight block
+        // (one 128-byte line per thread and row segment) and its weight block
         const int pc = tl.pf_cw & 0xff, pw = (tl.pf_cw >> 8) - 1;
         const int pfx = tl.pf_fxy & 0xffff, pfy = (int)((unsigned)tl.pf_fxy >> 16);
         const int pfw = tl.pf_fwh & 0xffff, pfh = tl.pf_fwh >> 16;
         const uint8_t* pp = fp.p[pc];
         const long long ppitch = fp.pitch[pc];
-        const int len = 3 * pfw;
-        for (int q = t; q < 8 * pfh; q += D1_THREADS) {
-            const int rr = q >> 3, k = q & 7;
-            if (128 * k < len + 127) prefetch_l2(pp + (long long)(pfy + rr) * ppitch + 3 * pfx + min(128 * k, len - 1));
+        const int len = 3 * pfw, segs = (len + 127) >> 7;
+        for (int q = t; q < segs * pfh; q += D1_THREADS) {
+            const int rr = q / segs, k = q - rr * segs;
+            prefetch_l2(pp + (long long)(pfy + rr) * ppitch + 3 * pfx + min(128 * k, len - 1));
         }
-        if (pw >= 0 && t < (4 * D1_NSAMP + 127) / 128)
-            prefetch_l2(d1w + (long long)pw * D1_NSAMP + min(32 * t, D1_NSAMP - 1));
+        if (pw >= 0)
+            for (int q = t; q < (4 * D1_NSAMP + 127) / 128; q += D1_THREADS)
+                prefetch_l2(d1w + (long long)pw * D1_NSAMP + min(32 * q, D1_NSAMP - 1));
     }
-    const CamRef ref = refs[tl.ref];
-    const int W = ci.W, H = ci.H;
-    const float fU0 = (float)ref.tm.U0, fV0 = (float)ref.tm.V0;
-    const bool interior = tl.flags & D1_INTERIOR;
-    const float* __restrict__ wt = d1w + (long long)max(tl.wtab, 0) * D1_NSAMP;
+
+    D1Ctx x;
+    x.tm = ref.tm;
+    x.rowdy = rowdy;
+    x.wt = tl.wtab >= 0 ? d1w + (long long)tl.wtab * D1_NSAMP : nullptr;
+    x.px = px_i;
+    x.pitch = pitch_i;
+    x.W = ci.W;
+    x.H = ci.H;
+    x.scale = ci.gain * (1.0f / 255.0f);
+    x.fU0 = (float)ref.tm.U0;
+    x.fV0 = (float)ref.tm.V0;
+    x.foot = foot;
+    const bool staged = tl.fwh != 0;
+    x.fx0 = tl.fxy & 0xffff;
+    x.fy0 = (int)((unsigned)tl.fxy >> 16);
+    x.fw = tl.fwh & 0xffff;
+    x.fh = tl.fwh >> 16;
+    x.S = (x.fw + 3) & ~3;
+    // footprint index of the top-left tap from the bit patterns tu, tv of the floor constants:
+    // (tv - B + V0 - fy0) S + (tu - B + U0 - fx0), in arithmetic modulo 2^32
+    x.ibase = (unsigned)(ref.tm.V0 - x.fy0) * (unsigned)x.S + (unsigned)(ref.tm.U0 - x.fx0) -
+              D1_FLOOR_BITS * ((unsigned)x.S + 1u);
+    x.maxidx = x.S * (x.fh - 1) - 2;
+    if (staged && act) stage_footprint(foot, px_i, pitch_i, x.W, x.fx0, x.fy0, x.fw, x.fh);
+    if (t < D1_SY) {
+        const float dy = (float)(fold101(vy0 + t, g.ny[0]) - ref.ay);
+        rowdy[t] = make_float2(dy, dy);
+    }
+    // column terms: the anchored homography on the planar canvas, the column table on the
+    // cylindrical one
     const float4* __restrict__ cols = g.cyl ? d1cols + (long long)tl.coltab * D1_SX : nullptr;
-    // position of virtual sample (r, c) for the paths that read taps from the frame
-    auto pos_of = [&](int r, int c) -> Pos {
-        const int y = fold101(vy0 + r, g.ny[0]);
+    auto colterms = [&](int c, float2& nuv, float& dqc) {
         if (cols) {
             const float4 cc = cols[c];
-            return map_pos_col(ref.tm, fU0, fV0, cc.x, cc.y, cc.z, (float)(y - ref.ay));
+            nuv = make_float2(cc.x, cc.y);
+            dqc = cc.z;
+        } else {
+            const float dx = (float)(fold101(vx0 + c, g.nx[0]) - ref.ax);
+            nuv = make_float2(fmaf(x.tm.pu1, dx, x.tm.pu0), fmaf(x.tm.pv1, dx, x.tm.pv0));
+            dqc = fmaf(x.tm.q1, dx, x.tm.q0);
         }
-        const int x = fold101(vx0 + c, g.nx[0]);
-        return map_pos(ref.tm, fU0, fV0, (float)(x - ref.ax), (float)(y - ref.ay));
     };
-    if (tl.fwh != 0) {
-        // S1 from the source footprint staged in shared memory (the footprint shares its space
-        // with sh, which is written only after the samples are taken)
-        const int fx0 = tl.fxy & 0xffff, fy0 = (int)((unsigned)tl.fxy >> 16), fw = tl.fwh & 0xffff, fh = tl.fwh >> 16;
-        float* foot = reinterpret_cast<float*>(sh);
-        float* rowdy = reinterpret_cast<float*>(smem + D1_S0_F4 + D1_SH_F4);
-        float a[D1_RPT + 1];
-        if (!interior) d1_load_weights(wt, a);  // in flight together with the footprint loads
-        stage_footprint(foot, px_i, pitch_i, W, fx0, fy0, fw, fh);
-        if (t < D1_SY) rowdy[t] = (float)(fold101(vy0 + t, g.ny[0]) - ref.ay);
-        __syncthreads();
-        if (interior) d1_staged_samples<true>(s0, foot, rowdy, a, g, ref, cols, vx0, fx0, fy0, fw, fh, W, H, scale);
-        else d1_staged_samples<false>(s0, foot, rowdy, a, g, ref, cols, vx0, fx0, fy0, fw, fh, W, H, scale);
-        __syncthreads();  // the footprint is dead from here on
-    } else if (interior) {
-        for (int q = t; q < D1_NSAMP; q += D1_THREADS) {
-            const int r = q / D1_SX, c = q % D1_SX;
-            const Pos p = pos_of(r, c);
-            const float3 v = sample_rgb_inside(px_i, pitch_i, p, scale);
-            s0[s0_slot(r, c)] = make_float4(v.x, v.y, v.z, 1.f);
+    const int mode = tl.flags & D1_INTERIOR ? (staged ? D1M_INTERIOR : D1M_G_INTERIOR)
+                                            : (staged ? (tl.flags & D1_NOCLAMP ? D1M_NOCLAMP : D1M_CLAMP) : D1M_G_TABLE);
+    const int flags = tl.flags;
+    T* g0 = (flags & D1_G0_OUT) ? g0buf + (long long)tl.g0 * D1_SLOT + ((j0 / D1_TY) & 1) * (2 * D1_TY) * (2 * D1_TX)
+                                : nullptr;
+    const int X0 = 2 * k0, Y0 = 2 * j0, nx0 = g.nx[0], ny0 = g.ny[0];
+    __syncthreads();
+    if (act) {
+        float2 nuv;
+        float dqc;
+        colterms(t, nuv, dqc);
+        switch (mode) {
+            case D1M_INTERIOR: d1_sweep<T, D1M_INTERIOR>(x, vres, t, nuv, dqc, flags, od, g0, X0, Y0, nx0, ny0); break;
+            case D1M_NOCLAMP: d1_sweep<T, D1M_NOCLAMP>(x, vres, t, nuv, dqc, flags, od, g0, X0, Y0, nx0, ny0); break;
+            case D1M_CLAMP: d1_sweep<T, D1M_CLAMP>(x, vres, t, nuv, dqc, flags, od, g0, X0, Y0, nx0, ny0); break;
+            case D1M_G_INTERIOR: d1_sweep<T, D1M_G_INTERIOR>(x, vres, t, nuv, dqc, flags, od, g0, X0, Y0, nx0, ny0); break;
+            default: d1_sweep<T, D1M_G_TABLE>(x, vres, t, nuv, dqc, flags, od, g0, X0, Y0, nx0, ny0); break;
         }
-    } else {
-        for (int q = t; q < D1_NSAMP; q += D1_THREADS) {
-            const int r = q / D1_SX, c = q % D1_SX;
-            const float a = __ldg(wt + q);
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (a >= 0.f) {
-                const Pos p = pos_of(r, c);
-                const float3 s3 = sample_rgb(px_i, pitch_i, p, W, H, scale);
-                v = make_float4(s3.x, s3.y, s3.z, a);
+        // the last three columns: one sample per thread
+        if (t < D1_XC * D1_SY) {
+            const int r = t / D1_XC, k = t - r * D1_XC, c = D1_THREADS + k;
+            colterms(c, nuv, dqc);
+            const float a = x.wt ? __ldg(x.wt + r * D1_SX + c) : 1.0f;
+            V4 s;
+            switch (mode) {
+                case D1M_INTERIOR: s = d1_sample<D1M_INTERIOR>(x, nuv, dqc, r, a); break;
+                case D1M_NOCLAMP: s = d1_sample<D1M_NOCLAMP>(x, nuv, dqc, r, a); break;
+                case D1M_CLAMP: s = d1_sample<D1M_CLAMP>(x, nuv, dqc, r, a); break;
+                case D1M_G_INTERIOR: s = d1_sample<D1M_G_INTERIOR>(x, nuv, dqc, r, a); break;
+                default: s = d1_sample<D1M_G_TABLE>(x, nuv, dqc, r, a); break;
             }
-            s0[s0_slot(r, c)] = v;
+            ext[t] = f4_of(s);
+            if (r >= 2 && r < D1_SY - 1 && c < D1_SX - 1 && (flags & (D1_SOLO_OUT | D1_G0_OUT)))
+                d1_out<T>(flags, od, g0, X0, Y0, nx0, ny0, c - 2, r - 2, s);
         }
     }
     __syncthreads();
-    if (tl.flags & D1_SOLO_OUT) {
-        // the canvas tile [2 k0, 2 k0 + 64) x [2 j0, 2 j0 + 32) is exclusive to this camera: its
-        // output is the clamped level-0 warp, already in s0 (virtual offset 2)
-        unsigned char* stage = reinterpret_cast<unsigned char*>(sh);
-        const int X0 = 2 * k0, Y0 = 2 * j0;
-        const int X1 = min(X0 + 2 * D1_TX, g.nx[0]), Y1 = min(Y0 + 2 * D1_TY, g.ny[0]);
-        for (int q = t; q < 4 * D1_TX * D1_TY; q += D1_THREADS) {
-            const int dx = q % (2 * D1_TX), dy = q / (2 * D1_TX);
-            if (X0 + dx >= X1 || Y0 + dy >= Y1) continue;
-            const float4 v = s0[s0_slot(dy + 2, dx + 2)];
-            put_pixel(stage, od, dx, dy, X0 + dx, Y0 + dy, __saturatef(v.x), __saturatef(v.y), __saturatef(v.z));
-        }
-        if (!od.is_float) {
-            __syncthreads();
-            store_u8_tile(stage, od, X0, Y0, X1, Y1);
-        }
-        __syncthreads();
-    }
-    if (tl.flags & D1_G0_OUT) {
-        // the FULL canvas tile under this tile blends this camera: its level-0 samples (value and
-        // normalised weight, at virtual offset 2) go to the tile's slot, read by up_full
-        T* dst = g0buf + (long long)tl.g0 * (4 * D1_TX * D1_TY);
-        for (int q = t; q < 4 * D1_TX * D1_TY; q += D1_THREADS) {
-            const int dx = q % (2 * D1_TX), dy = q / (2 * D1_TX);
-            st(dst + q, s0[s0_slot(dy + 2, dx + 2)]);
-        }
-    }
-    // S3 horizontal pass: sh[r][p] = sum_m w(m) s0[r][2p + m]
-    for (int q = t; q < D1_TX * D1_SY; q += D1_THREADS) {
-        const int r = q / D1_TX, p = q - r * D1_TX;
-        const float4* ev = s0 + r * (2 * D1_SXH) + p;  // columns 2p, 2p+2, 2p+4
-        const float4* od_ = ev + D1_SXH;              // columns 2p+1, 2p+3
-        float4 acc = f4fma(c_w5[0], ev[0], make_float4(0.f, 0.f, 0.f, 0.f));
-        acc = f4fma(c_w5[1], od_[0], acc);
-        acc = f4fma(c_w5[2], ev[1], acc);
-        acc = f4fma(c_w5[3], od_[1], acc);
-        acc = f4fma(c_w5[4], ev[2], acc);
-        sh[q] = acc;
-    }
-    __syncthreads();
-    // S3 vertical pass and store of G^1
-    T* dst = reinterpret_cast<T*>(ci.FG[1]);
-    for (int q = t; q < D1_TX * D1_TY; q += D1_THREADS) {
-        const int jj = q / D1_TX, p = q - jj * D1_TX;
-        const int k = k0 + p, j = j0 + jj;
-        // tiles lie on the global grid, so they may start before and end after Omega^1
-        if (!o1.contains(k, j)) continue;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    // vertical REDUCE of the last three columns
+    if (t < D1_XC * D1_TY) {
+        const int jj = t / D1_XC, k = t - jj * D1_XC;
+        V4 acc = v4_mul(d1_w(0), v4_of(ext[(2 * jj) * D1_XC + k]));
 #pragma unroll
-        for (int n = 0; n < 5; ++n) acc = f4fma(c_w5[n], sh[(2 * jj + n) * D1_TX + p], acc);
-        st(dst + (long long)(j - o1.y0) * o1.w() + (k - o1.x0), acc);
+        for (int n = 1; n < 5; ++n) acc = v4_fma(d1_w(n), v4_of(ext[(2 * jj + n) * D1_XC + k]), acc);
+        vres[jj * D1_VROW + d1_vslot(D1_THREADS + k)] = f4_of(acc);
+    }
+    __syncthreads();
+    // S3 horizontal pass and store of G^1: output (p, jj) takes columns 2p .. 2p+4
+    if (act) {
+        T* dst = reinterpret_cast<T*>(ci.FG[1]);
+        const int p = t & 31, kk = k0 + p;
+#pragma unroll
+        for (int q = 0; q < D1_TY / 2; ++q) {
+            const int jj = (t >> 5) + 2 * q, j = j0 + jj;
+            const float4* ev = vres + jj * D1_VROW + p;  // columns 2p, 2p+2, 2p+4
+            const float4* odp = ev + D1_VODD;           // columns 2p+1, 2p+3
+            V4 acc = v4_mul(d1_w(0), v4_of(ev[0]));
+            acc = v4_fma(d1_w(1), v4_of(odp[0]), acc);
+            acc = v4_fma(d1_w(2), v4_of(ev[1]), acc);
+            acc = v4_fma(d1_w(3), v4_of(odp[1]), acc);
+            acc = v4_fma(d1_w(4), v4_of(ev[2]), acc);
+            // tiles lie on the global grid, so they may start before and end after Omega^1
+            if (o1.contains(kk, j)) st(dst + (long long)(j - o1.y0) * o1.w() + (kk - o1.x0), f4_of(acc));
+        }
     }
 }
 
@@ -640,8 +735,38 @@ __global__ void __launch_bounds__(256) k_reduce_t(const CamDev* __restrict__ cam
 // coarse levels
 
 // Polyphase EXPAND of a 2x2 block of fine samples whose coarse 3x3 neighbourhood starts at
-// a[oy][ox] (row stride ld): even-even, odd-even (x odd), even-odd (y odd), odd-odd.
-__device__ __forceinline__ void expand_quad(const float4* __restrict__ a, int ld, int ox, int oy, float3 e[4]) {
+// a[oy][ox] (row stride ld): even-even, odd-even (x odd), even-odd (y odd), odd-odd.  R and G go
+// as one pair, B alone; the fourth channel is not expanded.
+struct V3 {
+    float2 rg;
+    float b;
+};
+__device__ __forceinline__ V3 v3_of(float4 v) { return {make_float2(v.x, v.y), v.z}; }
+__device__ __forceinline__ V3 v3_zero() { return {make_float2(0.f, 0.f), 0.f}; }
+
+__device__ __forceinline__ void expand_quad(const float4* __restrict__ a, int ld, int ox, int oy, V3 e[4]) {
+    const float2 k75 = f2(0.75f), k125 = f2(0.125f), k5 = f2(0.5f);
+    auto even = [&](V3 c0, V3 c1, V3 c2) -> V3 {  // (1, 6, 1) / 8
+        return {f2fma(k75, c1.rg, f2mul(k125, f2add(c0.rg, c2.rg))), fmaf(0.75f, c1.b, 0.125f * (c0.b + c2.b))};
+    };
+    auto odd = [&](V3 c1, V3 c2) -> V3 {  // (4, 4) / 8
+        return {f2mul(k5, f2add(c1.rg, c2.rg)), 0.5f * (c1.b + c2.b)};
+    };
+    V3 he[3], ho[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const V3 c0 = v3_of(a[(oy + r) * ld + ox]), c1 = v3_of(a[(oy + r) * ld + ox + 1]), c2 = v3_of(a[(oy + r) * ld + ox + 2]);
+        he[r] = even(c0, c1, c2);
+        ho[r] = odd(c1, c2);
+    }
+    e[0] = even(he[0], he[1], he[2]);
+    e[1] = even(ho[0], ho[1], ho[2]);
+    e[2] = odd(he[1], he[2]);
+    e[3] = odd(ho[1], ho[2]);
+}
+
+// The same EXPAND channel by channel (the up_full kernel: fewer registers than the pairs).
+__device__ __forceinline__ void expand_quad3(const float4* __restrict__ a, int ld, int ox, int oy, float3 e[4]) {
     float3 he[3], ho[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -693,12 +818,12 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
     }
     const int qx = t % (CT_X / 2), qy = t / (CT_X / 2);
     const bool has_quad = t < CT_QUADS;
-    float3 num[4];
-    float den[4];
+    float2 nrg[4];
+    float nb[4], den[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        num[k] = make_float3(0.f, 0.f, 0.f);
-        den[k] = 0.f;
+        nrg[k] = make_float2(0.f, 0.f);
+        nb[k] = den[k] = 0.f;
     }
     for (int c0 = 0; c0 < tl.count; c0 += CT_NC) {
         const int nc = min(CT_NC, tl.count - c0);
@@ -756,25 +881,22 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
         if (has_quad) {
             for (int ci = 0; ci < nc; ++ci) {
                 const Rect z = cams[camlist[tl.first + c0 + ci]].Z[l];
-                float3 e[4] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f),
-                               make_float3(0.f, 0.f, 0.f)};
+                V3 e[4] = {v3_zero(), v3_zero(), v3_zero(), v3_zero()};
                 if (!top) expand_quad(gc[ci], CC_X, qx + 1, qy + 1, e);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
                     if (!z.contains(x, y)) continue;
                     const float4 gv = gl[ci][(2 * qy + (k >> 1)) * CT_X + 2 * qx + (k & 1)];
-                    num[k].x = fmaf(gv.w, gv.x + e[k].x, num[k].x);
-                    num[k].y = fmaf(gv.w, gv.y + e[k].y, num[k].y);
-                    num[k].z = fmaf(gv.w, gv.z + e[k].z, num[k].z);
+                    nrg[k] = f2fma(f2(gv.w), f2add(make_float2(gv.x, gv.y), e[k].rg), nrg[k]);
+                    nb[k] = fmaf(gv.w, gv.z + e[k].b, nb[k]);
                     den[k] += gv.w;
                 }
             }
         }
     }
     if (!has_quad) return;
-    float3 e[4] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f),
-                   make_float3(0.f, 0.f, 0.f)};
+    V3 e[4] = {v3_zero(), v3_zero(), v3_zero(), v3_zero()};
     bool need = false;
 #pragma unroll
     for (int k = 0; k < 4; ++k) need |= !(den[k] > 1e-12f);
@@ -783,10 +905,11 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
     for (int k = 0; k < 4; ++k) {
         const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
         if (x >= nxl || y >= nyl) continue;
-        float4 r = make_float4(e[k].x, e[k].y, e[k].z, 0.f);
+        float4 r = make_float4(e[k].rg.x, e[k].rg.y, e[k].b, 0.f);
         if (den[k] > 1e-12f) {
             const float rd = __frcp_rn(den[k]);  // one reciprocal, three products (within 1 ulp of division)
-            r = make_float4(num[k].x * rd, num[k].y * rd, num[k].z * rd, 0.f);
+            const float2 q = f2mul(nrg[k], f2(rd));
+            r = make_float4(q.x, q.y, nb[k] * rd, 0.f);
         }
         st(Rl + (long long)y * nxl + x, r);
     }
@@ -805,6 +928,8 @@ __global__ void __launch_bounds__(256, 3) k_coarse_t(const CamDev* __restrict__ 
 // up: levels 1 and 0 of one canvas tile
 
 constexpr int U_TX = 64, U_TY = 32;                     // level-0 pixels per tile
+static_assert(D1_SLOT == U_TX * U_TY && 2 * D1_TX == U_TX && 4 * D1_TY == U_TY,
+              "two down1 tiles over one canvas tile of up");
 constexpr int U_THREADS = 256;
 // virtual regions, origins (X0/2 - 2, Y0/2 - 2) at level 1 and (X0/4 - 2, Y0/4 - 2) at level 2
 constexpr int U1_X = U_TX / 2 + 4, U1_Y = U_TY / 2 + 4;  // 36 x 20
@@ -1048,7 +1173,7 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
         for (int c = 0; c < nc; ++c) {
             float3 e[4] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f),
                            make_float3(0.f, 0.f, 0.f)};
-            if (L >= 3) expand_quad(d2 + c * U2_N, U2_X, qx, qy, e);
+            if (L >= 3) expand_quad3(d2 + c * U2_N, U2_X, qx, qy, e);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (!cz1[c].contains(px[k], py[k])) continue;
@@ -1073,7 +1198,7 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
         }
         if (need_plain && L >= 3) {
             float3 e[4];
-            expand_quad(r2s, U2_X, qx, qy, e);
+            expand_quad3(r2s, U2_X, qx, qy, e);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
                 if (!(den[k] > 1e-12f)) r1[k] = e[k];
@@ -1103,7 +1228,7 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
             const int slot = cr[c].g0;
             if (slot < 0) continue;
             float3 e[4];
-            expand_quad(d1 + c * U1_N, U1_X, qx + 1, qy + 1, e);
+            expand_quad3(d1 + c * U1_N, U1_X, qx + 1, qy + 1, e);
             const T* gq = g0buf + (long long)slot * (U_TX * U_TY) + (2 * qy) * U_TX + 2 * qx;
             float4 gv[4];
 #pragma unroll
@@ -1663,10 +1788,12 @@ stitch_status fused_plan(stitch_rig* r) {
             if (!c.FG[l]) return STITCH_ENOMEM;
         }
         if (L >= 2) {
-            // tiles on the global grid of 32 x 16 level-1 samples, so that a tile's level-0 interior
-            // is exactly one 64 x 32 canvas tile of `up`
+            // tiles on the global grid of 32 x 8 level-1 samples, so that two vertically adjacent
+            // tiles' level-0 interiors are exactly one 64 x 32 canvas tile of `up`; both tiles of
+            // every such pair that meets Omega^1 exist
             const Rect o = c.Om[1];
-            for (int y = (o.y0 / D1_TY) * D1_TY; y < o.y1; y += D1_TY)
+            const int band = 2 * D1_TY;
+            for (int y = (o.y0 / band) * band; y < o.y1 || y % band != 0; y += D1_TY)
                 for (int x = (o.x0 / D1_TX) * D1_TX; x < o.x1; x += D1_TX) {
                     // level-0 bounding box of the tile's inputs
                     const int bx0 = std::max(2 * x - 2, 0), bx1 = std::min(2 * x - 2 + D1_SX, g.nx[0]);
@@ -1686,9 +1813,12 @@ stitch_status fused_plan(stitch_rig* r) {
                         cols.resize(cols.size() + D1_SX);
                         cyl_columns(c, g, refs[t.ref], 2 * x - 2, cols.data() + (size_t)t.coltab * D1_SX);
                     }
-                    // interior: one camera, every input at least 0.01 px inside its image, so the
-                    // weight is 1 and no coordinate needs clamping (FP32 positions err by ~1e-5 px)
-                    if (tc.count == 1 && solidly_inside(c, g, Rect{bx0, bx1, by0, by1}, 0.01)) t.flags |= D1_INTERIOR;
+                    // no clamping: every input at least 0.01 px inside the image (FP32 positions err
+                    // by ~1e-5 px); interior: in addition no other camera, so the weight is 1
+                    if (solidly_inside(c, g, Rect{bx0, bx1, by0, by1}, 0.01)) {
+                        t.flags |= D1_NOCLAMP;
+                        if (tc.count == 1) t.flags |= D1_INTERIOR;
+                    }
                     t.wtab = (t.flags & D1_INTERIOR) ? -1 : fs->n_wtab++;
                     int fx0, fy0, fw, fh;
                     if (d1_footprint(c, g, Rect{bx0, bx1, by0, by1}, fx0, fy0, fw, fh)) {
@@ -1779,8 +1909,10 @@ stitch_status fused_plan(stitch_rig* r) {
                     // output (its level-0 samples are the output here)
                     if (L >= 2) {
                         auto it = d1_index.find(((long long)last_v << 42) | ((long long)(X0 / 2) << 21) | (Y0 / 2));
-                        if (it != d1_index.end()) {
+                        auto it2 = d1_index.find(((long long)last_v << 42) | ((long long)(X0 / 2) << 21) | (Y0 / 2 + D1_TY));
+                        if (it != d1_index.end() && it2 != d1_index.end()) {
                             d1[it->second].flags |= D1_SOLO_OUT;
+                            d1[it2->second].flags |= D1_SOLO_OUT;
                             kind = -1;
                         }
                     }
@@ -1788,22 +1920,27 @@ stitch_status fused_plan(stitch_rig* r) {
                     // FULL: every camera blended at level 0 takes its level-0 samples (value and
                     // normalised weight) from its down1 tile over this canvas tile
                     kind = t.count <= 2 ? UP_FULL2 : UP_FULL4;
-                    size_t d1k[4];
+                    size_t d1k[4][2];
                     for (int k = 0; k < t.count && kind != UP_GENERAL; ++k) {
                         const CamRef& rk = refs[t.first + k];
-                        d1k[k] = SIZE_MAX;
+                        d1k[k][0] = d1k[k][1] = SIZE_MAX;
                         if (!rects_meet(r->hcam[rk.cam].V, X0, X1, Y0, Y1)) continue;
-                        auto it = d1_index.find(((long long)rk.cam << 42) | ((long long)(X0 / 2) << 21) | (Y0 / 2));
-                        if (it == d1_index.end()) kind = UP_GENERAL;
-                        else d1k[k] = it->second;
+                        for (int h = 0; h < 2; ++h) {
+                            auto it = d1_index.find(((long long)rk.cam << 42) | ((long long)(X0 / 2) << 21) | (Y0 / 2 + h * D1_TY));
+                            if (it == d1_index.end()) kind = UP_GENERAL;
+                            else d1k[k][h] = it->second;
+                        }
                     }
                     if (kind != UP_GENERAL)
                         for (int k = 0; k < t.count; ++k) {
-                            if (d1k[k] == SIZE_MAX) continue;
-                            D1Tile& dt = d1[d1k[k]];
-                            dt.g0 = fs->n_g0++;
-                            dt.flags |= D1_G0_OUT;
-                            refs[t.first + k].g0 = dt.g0;
+                            if (d1k[k][0] == SIZE_MAX) continue;
+                            const int slot = fs->n_g0++;
+                            for (int h = 0; h < 2; ++h) {
+                                D1Tile& dt = d1[d1k[k][h]];
+                                dt.g0 = slot;
+                                dt.flags |= D1_G0_OUT;
+                            }
+                            refs[t.first + k].g0 = slot;
                         }
                 } else {
                     kind = UP_GENERAL;
@@ -1817,7 +1954,10 @@ stitch_status fused_plan(stitch_rig* r) {
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device) != cudaSuccess || sms < 1)
             return STITCH_ECUDA;
-        const size_t K = (size_t)D1_BLOCKS_PER_SM * sms;
+        int bpsm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_down1<float4>, D1_THREADS, D1_SMEM) != cudaSuccess)
+            return STITCH_ECUDA;
+        const size_t K = (size_t)std::max(bpsm, 1) * sms;
         for (size_t k = 0; k + K < d1.size(); ++k) {
             const D1Tile& nx = d1[k + K];
             if (nx.fwh == 0) continue;
@@ -1885,7 +2025,7 @@ stitch_status fused_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od
 stitch_status fused_precompute(stitch_rig* r) {
     FusedState* fs = (FusedState*)r->fused;
     if (!fs || fs->n_wtab == 0) return STITCH_OK;
-    k_d1_weights<<<fs->n_d1, D1_THREADS>>>(r->dcam, r->geom, fs->d1_tiles, fs->d1_cams, fs->refs, fs->d1w);
+    k_d1_weights<<<fs->n_d1, D1W_THREADS>>>(r->dcam, r->geom, fs->d1_tiles, fs->d1_cams, fs->refs, fs->d1w);
     STITCH_CUDA_TRY(cudaGetLastError());
     STITCH_CUDA_TRY(cudaDeviceSynchronize());
     return STITCH_OK;
@@ -2096,7 +2236,7 @@ __global__ void __launch_bounds__(U_THREADS) k_batch_general(const BatchRigDev* 
 // Multi-rig stage kernels (the alternative batched schedule): one block per task of one task type,
 // tasks of every rig in one launch, each kernel with its own register and shared-memory budget.
 template <typename T>
-__global__ void __launch_bounds__(D1_THREADS, 3) k_mr_down1(const BatchRigDev* __restrict__ rigs,
+__global__ void __launch_bounds__(D1_THREADS, D1_BLOCKS_PER_SM) k_mr_down1(const BatchRigDev* __restrict__ rigs,
                                                              const BTask* __restrict__ tasks) {
     extern __shared__ float4 smem[];
     const BTask tk = tasks[blockIdx.x];

@@ -1,9 +1,9 @@
 // stitch_frames_static: the plain stitching path for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code that runs inside a CUDA graph being captured
-// or replayed, real-time loops whose latency budget forbids the allocator's implicit device
-// synchronisation, embedded hosts that hand the library a fixed memory budget at start-up, or
-// plugins whose host application owns every allocation.  For them this entry point runs the same
+// Some callers cannot call cudaMalloc at all: real-time loops whose latency budget forbids the
+// allocator's implicit device synchronisation, embedded hosts that hand the library a fixed memory
+// budget at start-up, or plugins whose host application owns every allocation and forbids its
+// plugins to allocate device memory of their own.  For them this entry point runs the same
 // plain-path kernels as a STITCH_PATH_PLAIN rig, but every scratch buffer (the per-camera
 // pyramid and band buffers, the per-level blend buffers and the camera descriptors) is carved out
 // of one file-scope device array of fixed size.  The caller passes the frames and the output
@@ -12,10 +12,13 @@
 // The array is a `static __device__` symbol: every GPU that loads this module holds it until the
 // process exits.  Host code cannot use the symbol's name as a device address, so the first call
 // on each device looks the address up with cudaGetSymbolAddress (with that device current) and
-// caches it.  Calls share the array and keep the last call's contents; nothing in it needs to
-// start at zero, because every kernel writes each scratch element before any kernel reads it.
-// Calls whose kernels overlap on the GPU (different streams, or different host threads on one
-// device) race on the array.
+// caches it; that first call should therefore come before any stream capture.  The cached address
+// belongs to the device's current context: after cudaDeviceReset the module is loaded again and
+// further calls on that device are not supported.  Calls share the array and keep the last call's
+// contents; nothing in it needs to start at zero, because every kernel writes each scratch
+// element before any kernel reads it.  Calls whose kernels overlap on the GPU (different streams,
+// or different host threads on one device) race on the array.
+#include <cmath>
 #include <mutex>
 
 #include "stitch_internal.cuh"
@@ -84,7 +87,9 @@ extern "C" stitch_status stitch_frames_static(const stitch_rig_desc* desc, const
         desc->band_fp16 != 0 || (desc->out_float != 0 && desc->out_float != 1) ||
         (desc->weights != STITCH_WEIGHTS_FEATHER && desc->weights != STITCH_WEIGHTS_SEAM) ||
         (desc->canvas_model != STITCH_CANVAS_PLANAR && desc->canvas_model != STITCH_CANVAS_CYLINDRICAL) ||
-        (desc->canvas_model == STITCH_CANVAS_CYLINDRICAL && !(desc->cylinder[0] > 0.0)))
+        (desc->canvas_model == STITCH_CANVAS_CYLINDRICAL &&
+         !(std::isfinite(desc->cylinder[0]) && desc->cylinder[0] > 0.0 && std::isfinite(desc->cylinder[1]) &&
+           std::isfinite(desc->cylinder[2]))))
         return STITCH_EINVAL;
     if ((long long)desc->canvas_w * desc->canvas_h > (1LL << 31)) return STITCH_EINVAL;
     const long long row = (long long)desc->canvas_w * (desc->out_float ? 12 : 3);

@@ -109,6 +109,13 @@ def test_remaining_entry_points_reject_bad_arguments_without_a_device(lib):
         setattr(desc, field, bad)
         assert lib.stitch_frames_static(ctypes.byref(desc), buf, pit, buf, 64, None) == E, field
     assert lib.stitch_frames_static(None, buf, pit, buf, 64, None) == E
+    # cylindrical canvas: focal length, centre must be finite (and the focal length positive)
+    for k, bad in ((0, float("inf")), (0, float("nan")), (0, -1.0), (1, float("nan")), (2, float("-inf"))):
+        cyl = [1000.0, 50.0, 20.0]
+        cyl[k] = bad
+        desc, keep = stitch.make_desc(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels, canvas=cyl)
+        assert lib.stitch_frames_static(ctypes.byref(desc), buf, pit, buf, 64, None) == E, (k, bad)
+        assert lib.stitch_rig_create(ctypes.byref(desc), 0, ctypes.byref(out)) == E and out.value is None, (k, bad)
     # rig queries and profiling
     a = (ctypes.c_double * 9)()
     vis = ctypes.c_int32()
