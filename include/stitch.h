@@ -333,7 +333,7 @@ stitch_status stitch_match_homography(stitch_matcher* ctx, const int32_t* xy_a, 
                                       int32_t* n_inliers, uint8_t* inlier, void* stream);
 
 /* ------------------------------------------------------------------------------------------ */
-/* Batching: several independent rigs stitched by one persistent launch                        */
+/* Batching: several independent rigs stitched together, replacing per-rig launch sequences      */
 
 typedef struct stitch_batch stitch_batch; /* opaque */
 
@@ -346,16 +346,28 @@ typedef struct stitch_batch stitch_batch; /* opaque */
 stitch_status stitch_batch_create(stitch_rig* const* rigs, int32_t n, stitch_batch** out);
 
 /*
- * Stitch one frame set for every rig of the batch in one persistent launch.
+ * Stitch one frame set for every rig of the batch, with the schedule the batch chose on its first
+ * call (stitch_batch_get_schedule): one persistent launch or the staged launches, replayed from a
+ * CUDA graph, or every rig's own launch sequence on a stream of its own.
  *   frames       host array of n host arrays of DEVICE frame pointers (one per camera)
  *   pitches      host array of n host arrays of row pitches
  *   outs         host array of n DEVICE output canvases; out_pitches their row pitches
- * Device-side waits are bounded; a wait that gives up returns STITCH_ETIMEOUT (read back after
- * the launch, so this call synchronises `stream`).  Status: OK, EINVAL, ECUDA, ETIMEOUT.
+ * The first call times the candidate schedules on these frames and synchronises `stream`; later
+ * calls are asynchronous on `stream` (no host synchronisation).  Device-side waits of the
+ * persistent launch are bounded; a wait that gave up is reported as STITCH_ETIMEOUT by
+ * stitch_batch_sync, or by a later stitch_batch_frames call once the failed call's work has
+ * completed (that later call then launches nothing); the outputs of the failed call are undefined.
+ * Status: OK, EINVAL, ECUDA, ETIMEOUT.
  */
 stitch_status stitch_batch_frames(stitch_batch* batch, const uint8_t* const* const* frames,
                                   const int64_t* const* pitches, void* const* outs, const int64_t* out_pitches,
                                   void* stream);
+
+/*
+ * Wait until the batch's last stitch_batch_frames call has completed on the device and report its
+ * outcome (and that of any earlier call not yet reported).  Status: OK, EINVAL, ECUDA, ETIMEOUT.
+ */
+stitch_status stitch_batch_sync(stitch_batch* batch);
 
 void stitch_batch_destroy(stitch_batch* batch);
 

@@ -40,6 +40,16 @@ stitch_status stitch_batch_frames(stitch_batch* batch, const uint8_t* const* con
     return st;
 }
 
+stitch_status stitch_batch_sync(stitch_batch* batch) {
+    if (!batch) return STITCH_EINVAL;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != batch->device && cudaSetDevice(batch->device) != cudaSuccess) return STITCH_ECUDA;
+    const stitch_status st = fused_batch_status(batch->impl);
+    if (prev >= 0 && prev != batch->device) cudaSetDevice(prev);
+    return st;
+}
+
 void stitch_batch_destroy(stitch_batch* batch) {
     if (!batch) return;
     int prev = -1;

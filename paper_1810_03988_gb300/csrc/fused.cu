@@ -99,6 +99,7 @@ struct D1Tile {
     // the staging inputs of the tile one resident wave later (footprint as fxy/fwh, camera and
     // weight block as cam | (wtab + 1) << 8; pf_fwh = 0: none), prefetched into L2 by this tile
     int pf_fxy, pf_fwh, pf_cw;
+    int wsel;  // weight table the samples take: wtab, or the table of ones for INTERIOR tiles
 };
 
 // Cameras (CamRef range, in camera order) whose validity box meets a down1 tile's level-0 inputs,
@@ -120,30 +121,12 @@ struct UpTile {
 // packed single-precision pairs (f32x2: two IEEE binary32 lanes, each rounded exactly as the
 // scalar operation), used where the path computes on pairs of channels
 
-__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
-#define STITCH_F2_BINOP(name, op)                                                           \
-    __device__ __forceinline__ float2 name(float2 a, float2 b) {                            \
-        float2 d;                                                                           \
-        asm("{\n\t.reg .b64 ra, rb, rd;\n\t"                                                \
-            "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t" op                         \
-            " rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"                                    \
-            : "=f"(d.x), "=f"(d.y)                                                          \
-            : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                      \
-        return d;                                                                           \
-    }
-STITCH_F2_BINOP(f2add, "add.rn.f32x2")
-STITCH_F2_BINOP(f2sub, "sub.rn.f32x2")
-STITCH_F2_BINOP(f2mul, "mul.rn.f32x2")
-STITCH_F2_BINOP(f2add_rm, "add.rm.f32x2")  // rounded toward -infinity
-#undef STITCH_F2_BINOP
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as a + (-1) b: the product is exact, so this is the rounded difference, bit for bit
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2add_rm(float2 a, float2 b) { return __fadd2_rd(a, b); }  // toward -infinity
 
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
@@ -251,21 +234,6 @@ __global__ void __launch_bounds__(D1W_THREADS) k_d1_weights(const CamDev* __rest
     }
 }
 
-// One output pixel written straight to the canvas (8-bit: round half to even of 255 v).
-__device__ __forceinline__ void put_pixel_direct(const OutDesc& od, int x, int y, float r, float g, float b) {
-    char* row = (char*)od.ptr + (long long)y * od.pitch;
-    if (od.is_float) {
-        float* o = (float*)row + 3 * x;
-        o[0] = r;
-        o[1] = g;
-        o[2] = b;
-    } else {
-        unsigned char* o = (unsigned char*)row + 3 * x;
-        o[0] = quantize_u8(r);
-        o[1] = quantize_u8(g);
-        o[2] = quantize_u8(b);
-    }
-}
 
 // Copy the footprint [fx0, fx0 + fw) x [fy0, fy0 + fh) of an RGB8 frame into shared memory, one
 // word per texel (bytes R, G, B, and one unused byte), rows of S = fw rounded up to 4 texels.  A
@@ -276,8 +244,7 @@ constexpr int D1_SG = D1_FOOT / 4 / D1_THREADS;  // groups per thread
 static_assert(D1_SG * 4 * D1_THREADS == D1_FOOT, "whole groups per thread");
 
 __device__ __forceinline__ void stage_footprint(uint32_t* __restrict__ foot, const uint8_t* __restrict__ px,
-                                                long long pitch, int W, int fx0, int fy0, int fw, int fh) {
-    const int t = threadIdx.x;
+                                                long long pitch, int W, int fx0, int fy0, int fw, int fh, int t) {
     const int gpr = (fw + 3) >> 2, ng = gpr * fh;  // groups per row = S / 4
     if (((reinterpret_cast<uintptr_t>(px) | (uintptr_t)pitch) & 3) != 0) {
         for (int q = t; q < 4 * ng; q += D1_THREADS) {
@@ -352,31 +319,31 @@ struct D1Ctx {
     TileMap tm;
     const uint32_t* foot;  // staged footprint
     const float2* rowdy;   // (dy, dy) of every virtual row: canvas row minus the anchor row
-    const float* wt;       // normalised weights of the tile's samples (67 x 19), or null
-    const uint8_t* px;     // frame (paths that read taps from it)
+    const float* wt;       // normalised weights of the tile's samples (67 x 19; all 1 on INTERIOR tiles)
+    const uint8_t* px;     // frame (taps read from it)
     long long pitch;
     int S;                 // footprint row stride (words)
     int fw, fh, fx0, fy0;  // footprint
     unsigned ibase;        // index of the top-left tap from the floor constants, see d1_sample
     int maxidx;            // largest top-left index whose four taps lie in the footprint
     int W, H;
-    float scale, fU0, fV0;
+    float scale;
 };
 
-// Sample modes: staged footprint without clamping, weight 1 (INTERIOR tiles) or from the table;
-// staged with the image clamp of S1 (tiles at the image border); taps read from the frame
-// (footprints too large to stage or reaching behind the camera), weight 1 or from the table.
-enum D1Mode { D1M_INTERIOR = 0, D1M_NOCLAMP = 1, D1M_CLAMP = 2, D1M_G_INTERIOR = 3, D1M_G_TABLE = 4 };
+// Sample modes: the staged footprint without clamping (every input at least 0.01 px inside the
+// image), the staged footprint with the image clamp of S1 (tiles at the image border), taps read
+// from the frame (footprints too large to stage or reaching behind the camera).
+enum D1Mode { D1M_STAGED = 0, D1M_CLAMP = 1, D1M_FRAME = 2 };
 
 constexpr float D1_FLOOR_M = 12582912.0f;       // 1.5 * 2^23
 constexpr unsigned D1_FLOOR_BITS = 0x4B400000u;  // its bit pattern
 
 // Level-0 sample of virtual row r at the column whose anchored numerators and denominator at the
-// anchor row are (nuc, nvc, dqc): (r, g, b, normalised weight), zero outside Omega^0 (a < 0).
-// Position and taps are those of map_pos + sample_rgb (or sample_rgb_inside), so the staged and
-// the frame-reading modes give bit-identical samples.  The floor of the offsets ru, rv (|ru|, |rv|
-// < 2^22 on staged tiles, whose footprint the planner bounds) comes from one addition rounded
-// toward -infinity: RD(ru + 1.5 2^23) = 1.5 2^23 + floor(ru), whose low bits hold the integer.
+// anchor row are (nuv, dqc): (r, g, b, normalised weight a), zero outside Omega^0 (a < 0).
+// Position and taps are those of map_pos + sample_rgb, so the three modes give bit-identical
+// samples.  The floor of the offsets ru, rv (|ru|, |rv| < 2^22 on staged tiles, whose footprint
+// the planner bounds) comes from one addition rounded toward -infinity:
+// RD(ru + 1.5 2^23) = 1.5 2^23 + floor(ru), whose low bits hold the integer.
 template <int MODE>
 __device__ __forceinline__ V4 d1_sample(const D1Ctx& x, float2 nuv, float dqc, int r, float a) {
     const float2 dy = x.rowdy[r];
@@ -384,8 +351,8 @@ __device__ __forceinline__ V4 d1_sample(const D1Ctx& x, float2 nuv, float dqc, i
     const float2 n = f2fma(make_float2(x.tm.pu2, x.tm.pv2), dy, nuv);
     const float rden = __fdividef(1.0f, den);
     V4 s;
-    s.b.y = (MODE == D1M_INTERIOR || MODE == D1M_G_INTERIOR) ? 1.0f : a;
-    if (MODE == D1M_G_INTERIOR || MODE == D1M_G_TABLE) {
+    s.b.y = a;
+    if (MODE == D1M_FRAME) {
         float ru = n.x * rden, rv = n.y * rden;
         ru = fminf(fmaxf(ru, -1.0e7f), 1.0e7f);
         rv = fminf(fmaxf(rv, -1.0e7f), 1.0e7f);
@@ -395,18 +362,17 @@ __device__ __forceinline__ V4 d1_sample(const D1Ctx& x, float2 nuv, float dqc, i
         p.iv = x.tm.V0 + (int)flv;
         p.fu = ru - flu;
         p.fv = rv - flv;
-        const float3 v = MODE == D1M_G_INTERIOR ? sample_rgb_inside(x.px, x.pitch, p, x.scale)
-                                                : sample_rgb(x.px, x.pitch, p, x.W, x.H, x.scale);
+        const float3 v = sample_rgb(x.px, x.pitch, p, x.W, x.H, x.scale);
         s.a = make_float2(v.x, v.y);
         s.b.x = v.z;
     } else {
         const float2 ruv = f2mul(n, f2(rden));
         const float2 tt = f2add_rm(ruv, f2(D1_FLOOR_M));
-        const float2 f = f2sub(ruv, f2sub(tt, f2(D1_FLOOR_M)));  // fractions in [0, 1)
+        const float2 f = f2sub(ruv, f2add(tt, f2(-D1_FLOOR_M)));  // fractions in [0, 1)
         const unsigned tu = __float_as_uint(tt.x), tv = __float_as_uint(tt.y);
         uint32_t w00, w01, w10, w11;
         float fx = f.x, fy = f.y;
-        if (MODE != D1M_CLAMP) {
+        if (MODE == D1M_STAGED) {
             // top-left tap (V0 + floor(rv) - fy0) S + (U0 + floor(ru) - fx0), clamped into the footprint
             const int idx = min(max((int)(tv * (unsigned)x.S + tu + x.ibase), 0), x.maxidx);
             const uint32_t* p = x.foot + idx;
@@ -429,60 +395,90 @@ __device__ __forceinline__ V4 d1_sample(const D1Ctx& x, float2 nuv, float dqc, i
         }
         d1_bilerp(w00, w01, w10, w11, fx, fy, x.scale, s);
     }
-    if (MODE != D1M_INTERIOR && MODE != D1M_G_INTERIOR && !(a >= 0.f)) s = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (!(a >= 0.f)) s = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     return s;
 }
 
-// Output of a level-0 sample at tile-local canvas position (dx, dy), dy < 16: the SOLO canvas
-// tile's pixel, or the FULL canvas tile's level-0 slot (rows 16 h .. 16 h + 15 for the half h).
+// Where a tile's level-0 samples go besides the pyramid: nowhere, the FULL canvas tile's level-0
+// slot, or the SOLO canvas tile's pixels (8-bit or float).  The sweep thread of virtual column c
+// writes the sample of virtual row r at canvas (X0 + c - 2, Y0 + r - 2) for 2 <= r < 18.
+enum D1OutKind { D1O_NONE = 0, D1O_SLOT = 1, D1O_U8 = 2, D1O_F32 = 3, D1O_ANY = 4 };
+
 template <typename T>
-__device__ __forceinline__ void d1_out(int flags, const OutDesc& od, T* __restrict__ g0, int X0, int Y0, int nx,
-                                       int ny, int dx, int dy, V4 s) {
-    if (flags & D1_SOLO_OUT) {
-        const int x = X0 + dx, y = Y0 + dy;
-        if (x < nx && y < ny) put_pixel_direct(od, x, y, __saturatef(s.a.x), __saturatef(s.a.y), __saturatef(s.b.x));
+struct D1Out {
+    char* p;         // the thread's element at r = 2 (slot element, or canvas pixel)
+    long long step;  // bytes from one row to the next
+    int rows;        // rows r - 2 < rows exist (canvas bottom; 0 right of the canvas)
+    int kind;
+};
+
+// OUTK: the output kind fixed at compile time, or D1O_ANY to take o.kind.  Slot rows always exist.
+template <typename T, int OUTK>
+__device__ __forceinline__ void d1_put(const D1Out<T>& o, int dy, V4 s) {
+    const int kind = OUTK == D1O_ANY ? o.kind : OUTK;
+    if (kind == D1O_NONE) return;
+    if (kind != D1O_SLOT && dy >= o.rows) return;
+    char* q = o.p + dy * o.step;
+    if (kind == D1O_SLOT) {
+        st(reinterpret_cast<T*>(q), f4_of(s));
+    } else if (kind == D1O_U8) {
+        unsigned char* b = reinterpret_cast<unsigned char*>(q);
+        b[0] = quantize_u8(__saturatef(s.a.x));
+        b[1] = quantize_u8(__saturatef(s.a.y));
+        b[2] = quantize_u8(__saturatef(s.b.x));
+    } else {
+        float* f = reinterpret_cast<float*>(q);
+        f[0] = __saturatef(s.a.x);
+        f[1] = __saturatef(s.a.y);
+        f[2] = __saturatef(s.b.x);
     }
-    if (flags & D1_G0_OUT) st(g0 + dy * (2 * D1_TX) + dx, f4_of(s));
 }
 
-// The sweep of thread c (virtual column c < 64): 19 samples, the vertical REDUCE in registers
-// (output row jj takes rows 2 jj .. 2 jj + 4 in order), level-0 outputs on the fly.  Rows go in
-// pairs (2m, 2m + 1) with two running sums: on entry to pair m, C holds output row m - 2 (taps
-// 0..3 applied) and B row m - 1 (taps 0, 1); row 2m completes C, moves B on by tap 2 into C and
-// starts row m in B; row 2m + 1 adds tap 3 to C and tap 1 to B.
-template <typename T, int MODE>
-__device__ __forceinline__ void d1_sweep(const D1Ctx& x, float4* __restrict__ vres, int c, float2 nuv, float dqc,
-                                         int flags, const OutDesc& od, T* __restrict__ g0, int X0, int Y0, int nx, int ny) {
-    constexpr bool TABLE = MODE != D1M_INTERIOR && MODE != D1M_G_INTERIOR;
-    const bool out = c >= 2 && (flags & (D1_SOLO_OUT | D1_G0_OUT));
-    const V4 zero = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    V4 B = zero, C = zero;
-    float4* vcol = vres + d1_vslot(c);
-    const float* wcol = TABLE ? x.wt + c : nullptr;
+// The sweep of one thread over the 19 rows of its virtual column c: the vertical REDUCE in
+// registers (output row jj takes rows 2 jj .. 2 jj + 4 in order), level-0 outputs on the fly.  Rows
+// go in pairs (2m, 2m + 1) with two running sums: on entry to pair m, C holds output row m - 2
+// (taps 0..3 applied) and B row m - 1 (taps 0, 1); row 2m completes C (stored from m = 2 on), moves
+// B on by tap 2 into C and starts row m in B; row 2m + 1 adds tap 3 to C and tap 1 to B.
+template <typename T, int MODE, int OUTK, bool ONES>
+__device__ __forceinline__ void d1_sweep(const D1Ctx& x, float4* __restrict__ vcol, const float* __restrict__ wcol,
+                                         float2 nuv, float dqc, const D1Out<T>& o) {
+    V4 B = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, C = B;
+    // weights of INTERIOR tiles are all 1; the others are loaded one row pair ahead
+    float we = ONES ? 1.0f : __ldg(wcol), wo = ONES ? 1.0f : __ldg(wcol + D1_SX);
 #pragma unroll 1
     for (int m = 0; m <= D1_TY + 1; ++m) {
-        const int r = 2 * m;
-        {
-            const V4 s = d1_sample<MODE>(x, nuv, dqc, r, TABLE ? __ldg(wcol + r * D1_SX) : 1.0f);
-            if (out && r >= 2 && r < D1_SY - 1) d1_out<T>(flags, od, g0, X0, Y0, nx, ny, c - 2, r - 2, s);
-            if (m >= 2) vcol[(m - 2) * D1_VROW] = f4_of(v4_fma(d1_w(4), s, C));
-            C = v4_fma(d1_w(2), s, B);
-            B = v4_mul(d1_w(0), s);
+        const bool put = m >= 1 && m <= D1_TY;
+        const float ae = we, ao = wo;
+        if (!ONES && m <= D1_TY) {
+            we = __ldg(wcol + (2 * m + 2) * D1_SX);
+            wo = m < D1_TY ? __ldg(wcol + (2 * m + 3) * D1_SX) : 0.f;
         }
-        if (r + 1 < D1_SY) {
-            const V4 s = d1_sample<MODE>(x, nuv, dqc, r + 1, TABLE ? __ldg(wcol + (r + 1) * D1_SX) : 1.0f);
-            if (out && m >= 1) d1_out<T>(flags, od, g0, X0, Y0, nx, ny, c - 2, r - 1, s);
-            C = v4_fma(d1_w(3), s, C);
-            B = v4_fma(d1_w(1), s, B);
-        }
+        const V4 se = d1_sample<MODE>(x, nuv, dqc, 2 * m, ae);
+        if (put) d1_put<T, OUTK>(o, 2 * m - 2, se);
+        if (m >= 2) vcol[(m - 2) * D1_VROW] = f4_of(v4_fma(d1_w(4), se, C));
+        C = v4_fma(d1_w(2), se, B);
+        B = v4_mul(d1_w(0), se);
+        if (m > D1_TY) break;
+        const V4 so = d1_sample<MODE>(x, nuv, dqc, 2 * m + 1, ao);
+        if (put) d1_put<T, OUTK>(o, 2 * m - 1, so);
+        C = v4_fma(d1_w(3), so, C);
+        B = v4_fma(d1_w(1), so, B);
     }
 }
 
+// Barrier of the threads working on one down1 tile: the whole block (id 0), or a named barrier of
+// the 64 threads of one group when a larger block works on several tiles at once.
+__device__ __forceinline__ void d1_bar(int id) {
+    if (id == 0) __syncthreads();
+    else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(D1_THREADS) : "memory");
+}
+
+// One down1 tile, worked on by the D1_THREADS threads t = 0 .. 63 that share barrier `bar`.
 template <typename T>
 __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
                                            const OutDesc& od, const D1Tile& tl, const CamRef* __restrict__ refs,
                                            const float* __restrict__ d1w, const float4* __restrict__ d1cols,
-                                           T* __restrict__ g0buf, float4* smem) {
+                                           T* __restrict__ g0buf, float4* smem, int t = threadIdx.x, int bar = 0) {
     uint32_t* foot = reinterpret_cast<uint32_t*>(smem);
     float4* vres = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + D1_SM_FOOT);
     float4* ext = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + D1_SM_FOOT + D1_SM_V);  // [19][3]
@@ -493,8 +489,7 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
     const Rect o1 = ci.Om[1];
     const int k0 = tl.k0, j0 = tl.j0;              // level-1 tile origin
     const int vx0 = 2 * k0 - 2, vy0 = 2 * j0 - 2;  // level-0 virtual origin
-    const int t = threadIdx.x;
-    const bool act = t < D1_THREADS;  // a larger block (the batched persistent kernel) idles the rest
+    const bool act = t < D1_THREADS;
     const CamRef ref = refs[tl.ref];
     const uint8_t* px_i = fp.p[i];
     const long long pitch_i = fp.pitch[i];
@@ -520,14 +515,12 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
     D1Ctx x;
     x.tm = ref.tm;
     x.rowdy = rowdy;
-    x.wt = tl.wtab >= 0 ? d1w + (long long)tl.wtab * D1_NSAMP : nullptr;
+    x.wt = d1w + (long long)tl.wsel * D1_NSAMP;
     x.px = px_i;
     x.pitch = pitch_i;
     x.W = ci.W;
     x.H = ci.H;
     x.scale = ci.gain * (1.0f / 255.0f);
-    x.fU0 = (float)ref.tm.U0;
-    x.fV0 = (float)ref.tm.V0;
     x.foot = foot;
     const bool staged = tl.fwh != 0;
     x.fx0 = tl.fxy & 0xffff;
@@ -540,7 +533,7 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
     x.ibase = (unsigned)(ref.tm.V0 - x.fy0) * (unsigned)x.S + (unsigned)(ref.tm.U0 - x.fx0) -
               D1_FLOOR_BITS * ((unsigned)x.S + 1u);
     x.maxidx = x.S * (x.fh - 1) - 2;
-    if (staged && act) stage_footprint(foot, px_i, pitch_i, x.W, x.fx0, x.fy0, x.fw, x.fh);
+    if (staged && act) stage_footprint(foot, px_i, pitch_i, x.W, x.fx0, x.fy0, x.fw, x.fh, t);
     if (t < D1_SY) {
         const float dy = (float)(fold101(vy0 + t, g.ny[0]) - ref.ay);
         rowdy[t] = make_float2(dy, dy);
@@ -559,52 +552,76 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
             dqc = fmaf(x.tm.q1, dx, x.tm.q0);
         }
     };
-    const int mode = tl.flags & D1_INTERIOR ? (staged ? D1M_INTERIOR : D1M_G_INTERIOR)
-                                            : (staged ? (tl.flags & D1_NOCLAMP ? D1M_NOCLAMP : D1M_CLAMP) : D1M_G_TABLE);
+    const int mode = staged ? (tl.flags & D1_NOCLAMP ? D1M_STAGED : D1M_CLAMP) : D1M_FRAME;
     const int flags = tl.flags;
-    T* g0 = (flags & D1_G0_OUT) ? g0buf + (long long)tl.g0 * D1_SLOT + ((j0 / D1_TY) & 1) * (2 * D1_TY) * (2 * D1_TX)
-                                : nullptr;
-    const int X0 = 2 * k0, Y0 = 2 * j0, nx0 = g.nx[0], ny0 = g.ny[0];
-    __syncthreads();
+    const int X0 = 2 * k0, Y0 = 2 * j0;
+    d1_bar(bar);
     if (act) {
+        // sweep thread t takes virtual column t + 2 (the 64 columns of the canvas tile's pixels);
+        // the remaining columns 0, 1 and 66 are one sample per thread
+        const int c = t + 2;
         float2 nuv;
         float dqc;
-        colterms(t, nuv, dqc);
-        switch (mode) {
-            case D1M_INTERIOR: d1_sweep<T, D1M_INTERIOR>(x, vres, t, nuv, dqc, flags, od, g0, X0, Y0, nx0, ny0); break;
-            case D1M_NOCLAMP: d1_sweep<T, D1M_NOCLAMP>(x, vres, t, nuv, dqc, flags, od, g0, X0, Y0, nx0, ny0); break;
-            case D1M_CLAMP: d1_sweep<T, D1M_CLAMP>(x, vres, t, nuv, dqc, flags, od, g0, X0, Y0, nx0, ny0); break;
-            case D1M_G_INTERIOR: d1_sweep<T, D1M_G_INTERIOR>(x, vres, t, nuv, dqc, flags, od, g0, X0, Y0, nx0, ny0); break;
-            default: d1_sweep<T, D1M_G_TABLE>(x, vres, t, nuv, dqc, flags, od, g0, X0, Y0, nx0, ny0); break;
+        colterms(c, nuv, dqc);
+        D1Out<T> o{nullptr, 0, 0, D1O_NONE};
+        if (flags & D1_G0_OUT) {
+            o.kind = D1O_SLOT;
+            o.p = reinterpret_cast<char*>(g0buf + (long long)tl.g0 * D1_SLOT + ((j0 / D1_TY) & 1) * (2 * D1_TY) * (2 * D1_TX) + t);
+            o.step = (long long)sizeof(T) * (2 * D1_TX);
+            o.rows = 2 * D1_TY;
+        } else if (flags & D1_SOLO_OUT) {
+            o.kind = od.is_float ? D1O_F32 : D1O_U8;
+            const int xo = X0 + t;
+            o.p = (char*)od.ptr + (long long)Y0 * od.pitch + (long long)xo * (od.is_float ? 12 : 3);
+            o.step = od.pitch;
+            o.rows = xo < g.nx[0] ? max(0, min(2 * D1_TY, g.ny[0] - Y0)) : 0;
         }
-        // the last three columns: one sample per thread
+        float4* vcol = vres + d1_vslot(c);
+        const float* wcol = x.wt + c;
+        // the staged mode (nearly every tile) has a sweep per output kind; the rare clamping and
+        // frame-reading modes take the kind at run time
+        if (mode == D1M_STAGED && (flags & D1_INTERIOR)) {
+            switch (o.kind) {
+                case D1O_SLOT: d1_sweep<T, D1M_STAGED, D1O_SLOT, true>(x, vcol, wcol, nuv, dqc, o); break;
+                case D1O_U8: d1_sweep<T, D1M_STAGED, D1O_U8, true>(x, vcol, wcol, nuv, dqc, o); break;
+                case D1O_F32: d1_sweep<T, D1M_STAGED, D1O_F32, true>(x, vcol, wcol, nuv, dqc, o); break;
+                default: d1_sweep<T, D1M_STAGED, D1O_NONE, true>(x, vcol, wcol, nuv, dqc, o); break;
+            }
+        } else if (mode == D1M_STAGED) {
+            switch (o.kind) {
+                case D1O_SLOT: d1_sweep<T, D1M_STAGED, D1O_SLOT, false>(x, vcol, wcol, nuv, dqc, o); break;
+                case D1O_U8: d1_sweep<T, D1M_STAGED, D1O_U8, false>(x, vcol, wcol, nuv, dqc, o); break;
+                case D1O_F32: d1_sweep<T, D1M_STAGED, D1O_F32, false>(x, vcol, wcol, nuv, dqc, o); break;
+                default: d1_sweep<T, D1M_STAGED, D1O_NONE, false>(x, vcol, wcol, nuv, dqc, o); break;
+            }
+        } else if (mode == D1M_CLAMP) {
+            d1_sweep<T, D1M_CLAMP, D1O_ANY, false>(x, vcol, wcol, nuv, dqc, o);
+        } else {
+            d1_sweep<T, D1M_FRAME, D1O_ANY, false>(x, vcol, wcol, nuv, dqc, o);
+        }
         if (t < D1_XC * D1_SY) {
-            const int r = t / D1_XC, k = t - r * D1_XC, c = D1_THREADS + k;
-            colterms(c, nuv, dqc);
-            const float a = x.wt ? __ldg(x.wt + r * D1_SX + c) : 1.0f;
+            const int r = t / D1_XC, k = t - r * D1_XC, ce = k < 2 ? k : D1_SX - 1;
+            colterms(ce, nuv, dqc);
+            const float a = __ldg(x.wt + r * D1_SX + ce);
             V4 s;
             switch (mode) {
-                case D1M_INTERIOR: s = d1_sample<D1M_INTERIOR>(x, nuv, dqc, r, a); break;
-                case D1M_NOCLAMP: s = d1_sample<D1M_NOCLAMP>(x, nuv, dqc, r, a); break;
+                case D1M_STAGED: s = d1_sample<D1M_STAGED>(x, nuv, dqc, r, a); break;
                 case D1M_CLAMP: s = d1_sample<D1M_CLAMP>(x, nuv, dqc, r, a); break;
-                case D1M_G_INTERIOR: s = d1_sample<D1M_G_INTERIOR>(x, nuv, dqc, r, a); break;
-                default: s = d1_sample<D1M_G_TABLE>(x, nuv, dqc, r, a); break;
+                default: s = d1_sample<D1M_FRAME>(x, nuv, dqc, r, a); break;
             }
             ext[t] = f4_of(s);
-            if (r >= 2 && r < D1_SY - 1 && c < D1_SX - 1 && (flags & (D1_SOLO_OUT | D1_G0_OUT)))
-                d1_out<T>(flags, od, g0, X0, Y0, nx0, ny0, c - 2, r - 2, s);
         }
     }
-    __syncthreads();
-    // vertical REDUCE of the last three columns
+    d1_bar(bar);
+    // vertical REDUCE of columns 0, 1 and 66
     if (t < D1_XC * D1_TY) {
-        const int jj = t / D1_XC, k = t - jj * D1_XC;
+        const int jj = t / D1_XC, k = t - jj * D1_XC, ce = k < 2 ? k : D1_SX - 1;
         V4 acc = v4_mul(d1_w(0), v4_of(ext[(2 * jj) * D1_XC + k]));
 #pragma unroll
         for (int n = 1; n < 5; ++n) acc = v4_fma(d1_w(n), v4_of(ext[(2 * jj + n) * D1_XC + k]), acc);
-        vres[jj * D1_VROW + d1_vslot(D1_THREADS + k)] = f4_of(acc);
+        vres[jj * D1_VROW + d1_vslot(ce)] = f4_of(acc);
     }
-    __syncthreads();
+    d1_bar(bar);
     // S3 horizontal pass and store of G^1: output (p, jj) takes columns 2p .. 2p+4
     if (act) {
         T* dst = reinterpret_cast<T*>(ci.FG[1]);
@@ -639,68 +656,84 @@ __global__ void __launch_bounds__(D1_THREADS, D1_BLOCKS_PER_SM) k_down1(const Ca
 
 // Tiled separable REDUCE: 32 x 16 outputs of level l+1 from a 67 x 35 input region of level l
 // staged in shared memory with coalesced loads.
-constexpr int RT_X = 32, RT_Y = 16;
-constexpr int RS_X = 2 * RT_X + 3, RS_Y = 2 * RT_Y + 3;
-constexpr int RS_XH = (RS_X + 1) / 2;  // inputs stored as even and odd column planes
-constexpr size_t RT_SMEM = sizeof(float4) * (2 * RS_XH * RS_Y + RT_X * RS_Y);
+// The tile shape is a template parameter (the batched schedule's tuner picks one per batch); the
+// single-rig path uses 32 x 16.
+template <int X, int Y>
+struct RShape {
+    static constexpr int TX = X, TY = Y;                  // outputs
+    static constexpr int SX = 2 * X + 3, SY = 2 * Y + 3;  // staged inputs
+    static constexpr int SXH = (SX + 1) / 2;              // inputs stored as even and odd column planes
+    static constexpr size_t SMEM = sizeof(float4) * (2 * SXH * SY + X * SY);
+};
+using RS32x16 = RShape<32, 16>;
+using RS64x8 = RShape<64, 8>;
+constexpr int RT_X = RS32x16::TX, RT_Y = RS32x16::TY;
+constexpr size_t RT_SMEM = RS32x16::SMEM;
 
 // L2 prefetch of a reduce tile's input rows (the part inside Omega^l; rows that fold at the canvas
 // border are left to the loads), 16 threads per row, one 128-byte line each.
-template <typename T>
+template <typename T, typename RS = RS32x16>
 __device__ __forceinline__ void reduce_prefetch(const CamDev* __restrict__ cams, int l, const Tile& tn) {
     const CamDev& c = cams[tn.cam];
     const Rect of = c.Om[l];
     const int vx0 = 2 * tn.x0 - 2, vy0 = 2 * tn.y0 - 2;
-    const int x0 = max(vx0, of.x0), x1 = min(vx0 + RS_X, of.x1);
+    const int x0 = max(vx0, of.x0), x1 = min(vx0 + RS::SX, of.x1);
     if (x1 <= x0) return;
     const char* base = reinterpret_cast<const char*>(c.FG[l]);
     const int len = (x1 - x0) * (int)sizeof(T);
-    for (int q = threadIdx.x; q < 16 * RS_Y; q += 256) {
+    for (int q = threadIdx.x; q < 16 * RS::SY; q += 256) {
         const int rr = q >> 4, k = q & 15, y = vy0 + rr;
         if (y < of.y0 || y >= of.y1 || 128 * k >= len + 127) continue;
         prefetch_l2(base + ((long long)(y - of.y0) * of.w() + (x0 - of.x0)) * (long long)sizeof(T) + min(128 * k, len - 1));
     }
 }
 
-template <typename T>
+template <typename T, typename RS = RS32x16>
 __device__ __forceinline__ void reduce_tile(const CamDev* __restrict__ cams, const RigGeom& g, int l, const Tile& tl,
                                             float4* smem, const Tile* pf = nullptr) {
-    float4* s0 = smem;  // [RS_Y][2][RS_XH]: even columns, then odd columns, of each row
-    float4* sh = smem + 2 * RS_XH * RS_Y;
+    float4* s0 = smem;  // [SY][2][SXH]: even columns, then odd columns, of each row
+    float4* sh = smem + 2 * RS::SXH * RS::SY;
     const CamDev& c = cams[tl.cam];
     const Rect oc = c.Om[l + 1], of = c.Om[l];
     const int vx0 = 2 * tl.x0 - 2, vy0 = 2 * tl.y0 - 2;
     const T* src = reinterpret_cast<const T*>(c.FG[l]);
     const int nxl = g.nx[l], nyl = g.ny[l];
     {
-        // all loads of a thread in flight before the shared-memory stores
-        constexpr int NL = (RS_X * RS_Y + 255) / 256;
+        // all loads of a thread in flight before the shared-memory stores; a tile whose inputs lie
+        // inside Omega^l (so inside the level: nothing folds) reads them straight
+        constexpr int NL = (RS::SX * RS::SY + 255) / 256;
         float4 v[NL];
+        const bool inside = vx0 >= of.x0 && vx0 + RS::SX <= of.x1 && vy0 >= of.y0 && vy0 + RS::SY <= of.y1;
+        const T* base = src + (long long)(vy0 - of.y0) * of.w() + (vx0 - of.x0);
 #pragma unroll
         for (int k = 0; k < NL; ++k) {
             const int q = threadIdx.x + 256 * k;
             v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (q < RS_X * RS_Y) {
-                const int r = q / RS_X, cc = q - r * RS_X;
-                const int x = fold101(vx0 + cc, nxl), y = fold101(vy0 + r, nyl);
-                if (of.contains(x, y)) v[k] = ld(src + (long long)(y - of.y0) * of.w() + (x - of.x0));
+            if (q < RS::SX * RS::SY) {
+                const int r = q / RS::SX, cc = q - r * RS::SX;
+                if (inside) {
+                    v[k] = ld(base + (long long)r * of.w() + cc);
+                } else {
+                    const int x = fold101(vx0 + cc, nxl), y = fold101(vy0 + r, nyl);
+                    if (of.contains(x, y)) v[k] = ld(src + (long long)(y - of.y0) * of.w() + (x - of.x0));
+                }
             }
         }
 #pragma unroll
         for (int k = 0; k < NL; ++k) {
             const int q = threadIdx.x + 256 * k;
-            if (q < RS_X * RS_Y) {
-                const int r = q / RS_X, cc = q - r * RS_X;
-                s0[r * (2 * RS_XH) + (cc & 1) * RS_XH + (cc >> 1)] = v[k];
+            if (q < RS::SX * RS::SY) {
+                const int r = q / RS::SX, cc = q - r * RS::SX;
+                s0[r * (2 * RS::SXH) + (cc & 1) * RS::SXH + (cc >> 1)] = v[k];
             }
         }
     }
-    if (pf) reduce_prefetch<T>(cams, l, *pf);  // the tile one resident wave later
+    if (pf) reduce_prefetch<T, RS>(cams, l, *pf);  // the tile one resident wave later
     __syncthreads();
-    for (int q = threadIdx.x; q < RT_X * RS_Y; q += 256) {
-        const int r = q / RT_X, p = q - r * RT_X;
-        const float4* ev = s0 + r * (2 * RS_XH) + p;  // columns 2p, 2p+2, 2p+4
-        const float4* od = ev + RS_XH;                // columns 2p+1, 2p+3
+    for (int q = threadIdx.x; q < RS::TX * RS::SY; q += 256) {
+        const int r = q / RS::TX, p = q - r * RS::TX;
+        const float4* ev = s0 + r * (2 * RS::SXH) + p;  // columns 2p, 2p+2, 2p+4
+        const float4* od = ev + RS::SXH;                // columns 2p+1, 2p+3
         float4 acc = f4fma(c_w5[0], ev[0], make_float4(0.f, 0.f, 0.f, 0.f));
         acc = f4fma(c_w5[1], od[0], acc);
         acc = f4fma(c_w5[2], ev[1], acc);
@@ -710,13 +743,13 @@ __device__ __forceinline__ void reduce_tile(const CamDev* __restrict__ cams, con
     }
     __syncthreads();
     T* dst = reinterpret_cast<T*>(c.FG[l + 1]);
-    for (int q = threadIdx.x; q < RT_X * RT_Y; q += 256) {
-        const int jj = q / RT_X, p = q - jj * RT_X;
+    for (int q = threadIdx.x; q < RS::TX * RS::TY; q += 256) {
+        const int jj = q / RS::TX, p = q - jj * RS::TX;
         const int k = tl.x0 + p, j = tl.y0 + jj;
         if (k >= oc.x1 || j >= oc.y1) continue;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int n = 0; n < 5; ++n) acc = f4fma(c_w5[n], sh[(2 * jj + n) * RT_X + p], acc);
+        for (int n = 0; n < 5; ++n) acc = f4fma(c_w5[n], sh[(2 * jj + n) * RS::TX + p], acc);
         st(dst + (long long)(j - oc.y0) * oc.w() + (k - oc.x0), acc);
     }
 }
@@ -785,39 +818,50 @@ __device__ __forceinline__ void expand_quad3(const float4* __restrict__ a, int l
     e[3] = make_float3(0.5f * (ho[1].x + ho[2].x), 0.5f * (ho[1].y + ho[2].y), 0.5f * (ho[1].z + ho[2].z));
 }
 
-// Tiled coarse level: R^l on a 32 x 32 tile of level l (l >= 2), one 2 x 2 quad per thread,
-// cameras in chunks of 2.  Virtual level-(l+1) region: origin (X0/2 - 2, Y0/2 - 2), 20 x 20.
-constexpr int CT_X = 32, CT_Y = 32, CT_NC = 2;
-constexpr int CC_X = CT_X / 2 + 4, CC_Y = CT_Y / 2 + 4;
-constexpr int CC_N = CC_X * CC_Y, CT_N = CT_X * CT_Y;
-constexpr int CT_QUADS = (CT_X / 2) * (CT_Y / 2);  // 256
-constexpr int CT_SMEM_F4 = CC_N + CT_NC * CT_N + CT_NC * CC_N;  // shared memory in float4 units
+// Tiled coarse level: R^l on a tile of level l (l >= 2), one 2 x 2 quad per thread, cameras in
+// chunks of 2.  Virtual level-(l+1) region: origin (X0/2 - 2, Y0/2 - 2), TX/2 + 4 by TY/2 + 4.
+// The tile shape is a template parameter (the batched schedule's tuner picks one per batch); the
+// single-rig path uses 32 x 32.
+constexpr int CT_NC = 2;
+template <int X, int Y>
+struct CShape {
+    static constexpr int TX = X, TY = Y;                   // level-l outputs
+    static constexpr int CX = X / 2 + 4, CY = Y / 2 + 4;   // level-(l+1) virtual region
+    static constexpr int CN = CX * CY, TN = X * Y;
+    static constexpr int QUADS = (X / 2) * (Y / 2);
+    static constexpr int SMEM_F4 = CN + CT_NC * TN + CT_NC * CN;  // shared memory in float4 units
+    static_assert(QUADS == 256, "one 2 x 2 quad per thread of a 256-thread block");
+};
+using CS32x32 = CShape<32, 32>;
+using CS64x16 = CShape<64, 16>;
+constexpr int CT_X = CS32x32::TX, CT_Y = CS32x32::TY;
+constexpr int CT_SMEM_F4 = CS32x32::SMEM_F4;
 
 struct LevelTile {
     int x0, y0, first, count;  // level origin, range of camera indices in the list
 };
 
-template <typename T>
+template <typename T, typename CS = CS32x32>
 __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, const RigGeom& g, int l,
                                             T* __restrict__ Rl, const T* __restrict__ Rc, const LevelTile& tl,
                                             const int* __restrict__ camlist, float4* smem) {
-    float4* rc = smem;                                                   // [CC_N] R^{l+1}
-    float4 (*gl)[CT_N] = reinterpret_cast<float4 (*)[CT_N]>(rc + CC_N);  // [CT_NC][CT_N] G^l per camera
-    float4 (*gc)[CC_N] = reinterpret_cast<float4 (*)[CC_N]>(rc + CC_N + CT_NC * CT_N);  // G^{l+1}, then R - G
+    float4* rc = smem;                                                   // [CS::CN] R^{l+1}
+    float4 (*gl)[CS::TN] = reinterpret_cast<float4 (*)[CS::TN]>(rc + CS::CN);  // [CT_NC][CS::TN] G^l per camera
+    float4 (*gc)[CS::CN] = reinterpret_cast<float4 (*)[CS::CN]>(rc + CS::CN + CT_NC * CS::TN);  // G^{l+1}, then R - G
     const bool top = l == g.levels - 1;
     const int X0 = tl.x0, Y0 = tl.y0;
     const int ax = X0 / 2 - 2, ay = Y0 / 2 - 2;
     const int nxl = g.nx[l], nyl = g.ny[l];
     const int t = threadIdx.x;
     if (!top) {
-        for (int q = t; q < CC_N; q += 256) {
-            const int r = q / CC_X, c = q - r * CC_X;
+        for (int q = t; q < CS::CN; q += 256) {
+            const int r = q / CS::CX, c = q - r * CS::CX;
             const int x = fold101(ax + c, g.nx[l + 1]), y = fold101(ay + r, g.ny[l + 1]);
             rc[q] = ld(Rc + (long long)y * g.nx[l + 1] + x);
         }
     }
-    const int qx = t % (CT_X / 2), qy = t / (CT_X / 2);
-    const bool has_quad = t < CT_QUADS;
+    const int qx = t % (CS::TX / 2), qy = t / (CS::TX / 2);
+    const bool has_quad = t < CS::QUADS;
     float2 nrg[4];
     float nb[4], den[4];
 #pragma unroll
@@ -829,16 +873,16 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
         const int nc = min(CT_NC, tl.count - c0);
         __syncthreads();
         {
-            constexpr int NL = (CT_NC * CT_N + 255) / 256, NC2 = (CT_NC * CC_N + 255) / 256;
+            constexpr int NL = (CT_NC * CS::TN + 255) / 256, NC2 = (CT_NC * CS::CN + 255) / 256;
             float4 v[NL], w[NC2];
 #pragma unroll
             for (int k = 0; k < NL; ++k) {
                 const int q = t + 256 * k;
                 v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (q < nc * CT_N) {
-                    const int ci = q / CT_N, qq = q - ci * CT_N;
+                if (q < nc * CS::TN) {
+                    const int ci = q / CS::TN, qq = q - ci * CS::TN;
                     const CamDev& c = cams[camlist[tl.first + c0 + ci]];
-                    const int x = X0 + qq % CT_X, y = Y0 + qq / CT_X;
+                    const int x = X0 + qq % CS::TX, y = Y0 + qq / CS::TX;
                     const Rect o = c.Om[l];
                     if (o.contains(x, y))
                         v[k] = ld(reinterpret_cast<const T*>(c.FG[l]) + (long long)(y - o.y0) * o.w() + (x - o.x0));
@@ -848,10 +892,10 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
             for (int k = 0; k < NC2; ++k) {
                 const int q = t + 256 * k;
                 w[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (!top && q < nc * CC_N) {
-                    const int ci = q / CC_N, qq = q - ci * CC_N;
+                if (!top && q < nc * CS::CN) {
+                    const int ci = q / CS::CN, qq = q - ci * CS::CN;
                     const CamDev& c = cams[camlist[tl.first + c0 + ci]];
-                    const int r = qq / CC_X, cc = qq - r * CC_X;
+                    const int r = qq / CS::CX, cc = qq - r * CS::CX;
                     const int x = fold101(ax + cc, g.nx[l + 1]), y = fold101(ay + r, g.ny[l + 1]);
                     const Rect o = c.Om[l + 1];
                     if (o.contains(x, y))
@@ -861,18 +905,18 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
 #pragma unroll
             for (int k = 0; k < NL; ++k) {
                 const int q = t + 256 * k;
-                if (q < nc * CT_N) gl[q / CT_N][q % CT_N] = v[k];
+                if (q < nc * CS::TN) gl[q / CS::TN][q % CS::TN] = v[k];
             }
 #pragma unroll
             for (int k = 0; k < NC2; ++k) {
                 const int q = t + 256 * k;
-                if (!top && q < nc * CC_N) gc[q / CC_N][q % CC_N] = w[k];
+                if (!top && q < nc * CS::CN) gc[q / CS::CN][q % CS::CN] = w[k];
             }
         }
         __syncthreads();
         if (!top) {
-            for (int q = t; q < nc * CC_N; q += 256) {
-                const int ci = q / CC_N, qq = q - ci * CC_N;
+            for (int q = t; q < nc * CS::CN; q += 256) {
+                const int ci = q / CS::CN, qq = q - ci * CS::CN;
                 const float4 a = rc[qq], b = gc[ci][qq];
                 gc[ci][qq] = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, 0.f);
             }
@@ -882,12 +926,12 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
             for (int ci = 0; ci < nc; ++ci) {
                 const Rect z = cams[camlist[tl.first + c0 + ci]].Z[l];
                 V3 e[4] = {v3_zero(), v3_zero(), v3_zero(), v3_zero()};
-                if (!top) expand_quad(gc[ci], CC_X, qx + 1, qy + 1, e);
+                if (!top) expand_quad(gc[ci], CS::CX, qx + 1, qy + 1, e);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
                     if (!z.contains(x, y)) continue;
-                    const float4 gv = gl[ci][(2 * qy + (k >> 1)) * CT_X + 2 * qx + (k & 1)];
+                    const float4 gv = gl[ci][(2 * qy + (k >> 1)) * CS::TX + 2 * qx + (k & 1)];
                     nrg[k] = f2fma(f2(gv.w), f2add(make_float2(gv.x, gv.y), e[k].rg), nrg[k]);
                     nb[k] = fmaf(gv.w, gv.z + e[k].b, nb[k]);
                     den[k] += gv.w;
@@ -900,7 +944,7 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
     bool need = false;
 #pragma unroll
     for (int k = 0; k < 4; ++k) need |= !(den[k] > 1e-12f);
-    if (need && !top) expand_quad(rc, CC_X, qx + 1, qy + 1, e);
+    if (need && !top) expand_quad(rc, CS::CX, qx + 1, qy + 1, e);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
@@ -1164,19 +1208,13 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
             num[k] = make_float3(0.f, 0.f, 0.f);
             den[k] = 0.f;
         }
-        int px[4], py[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            px[k] = fold101(a1x + 2 * qx + (k & 1), g.nx[1]);
-            py[k] = fold101(a1y + 2 * qy + (k >> 1), g.ny[1]);
-        }
         for (int c = 0; c < nc; ++c) {
             float3 e[4] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f),
                            make_float3(0.f, 0.f, 0.f)};
             if (L >= 3) expand_quad3(d2 + c * U2_N, U2_X, qx, qy, e);
+            // outside the camera's Z^1 its weight pyramid is exactly 0, so those terms add nothing
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                if (!cz1[c].contains(px[k], py[k])) continue;
                 const float4 gv = d1[c * U1_N + (2 * qy + (k >> 1)) * U1_X + 2 * qx + (k & 1)];
                 num[k].x = fmaf(gv.w, gv.x + e[k].x, num[k].x);
                 num[k].y = fmaf(gv.w, gv.y + e[k].y, num[k].y);
@@ -1212,6 +1250,20 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
         }
     }
     __syncthreads();
+    if (L >= 2 && (a1x + U1_X > g.nx[1] || a1y + U1_Y > g.ny[1])) {
+        // Past the right or bottom border the level-1 region's values are those of the folded
+        // positions.  Delta^1 was evaluated there with EXPAND on the virtual level-2 grid, which
+        // agrees with the folded position's value only where the level's size is odd (the fine and
+        // coarse reflection points then correspond), so copy them from the folded positions.
+        for (int q = t; q < nc * U1_N; q += U_THREADS) {
+            const int ci = q / U1_N, qq = q - ci * U1_N;
+            const int r = qq / U1_X, cc = qq - r * U1_X;
+            if (a1x + cc < g.nx[1] && a1y + r < g.ny[1]) continue;
+            const int sx = fold101(a1x + cc, g.nx[1]) - a1x, sy = fold101(a1y + r, g.ny[1]) - a1y;
+            if (sx >= 0 && sx < U1_X && sy >= 0 && sy < U1_Y) d1[ci * U1_N + qq] = d1[ci * U1_N + sy * U1_X + sx];
+        }
+        __syncthreads();
+    }
     // level 0: R^0 = sum_i a_i (G^0_i + EXPAND(Delta^1_i)) / sum_i a_i on covered pixels, with the
     // level-0 sample G^0_i and normalised weight a_i of every blended camera written by its down1
     // tile (slot g0)
@@ -1233,10 +1285,11 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
             float4 gv[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) gv[k] = ld(gq + (k >> 1) * U_TX + (k & 1));
+            // a camera's weight is 0 (and its sample 0) where it does not cover the pixel: the
+            // terms add nothing there, so no test is needed
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float a = gv[k].w;
-                if (!(a > 0.f)) continue;
                 num[k].x = fmaf(a, gv[k].x + e[k].x, num[k].x);
                 num[k].y = fmaf(a, gv[k].y + e[k].y, num[k].y);
                 num[k].z = fmaf(a, gv[k].z + e[k].z, num[k].z);
@@ -1460,6 +1513,16 @@ __device__ __forceinline__ void up_general_tile(const CamDev* __restrict__ cams,
             r1[q] = v;
         }
         __syncthreads();
+        if (a1x + UG1_X > g.nx[1] || a1y + UG1_Y > g.ny[1]) {
+            // past the right or bottom border, R^1 is that of the folded positions (see up_full_tile)
+            for (int q = t; q < UG1_N; q += U_THREADS) {
+                const int r = q / UG1_X, cc = q - r * UG1_X;
+                if (a1x + cc < g.nx[1] && a1y + r < g.ny[1]) continue;
+                const int sx = fold101(a1x + cc, g.nx[1]) - a1x, sy = fold101(a1y + r, g.ny[1]) - a1y;
+                if (sx >= 0 && sx < UG1_X && sy >= 0 && sy < UG1_Y) r1[q] = r1[sy * UG1_X + sx];
+            }
+            __syncthreads();
+        }
     }
 #pragma unroll
     for (int k = 0; k < UG_PPT; ++k) {
@@ -1705,6 +1768,7 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
                                                              fs->wave_red);
     }
     for (int l = L - 1; l >= 2; --l) {
+        if (fs->n_co[l] == 0) continue;
         prof_mark(r, "fused_coarse", s);
         k_coarse_t<T><<<fs->n_co[l], 256, sizeof(float4) * CT_SMEM_F4, s>>>(r->dcam, g, l, (T*)fs->R[l],
                                                    l + 1 < L ? (const T*)fs->R[l + 1] : nullptr, fs->co_tiles[l],
@@ -1798,7 +1862,7 @@ stitch_status fused_plan(stitch_rig* r) {
                     // level-0 bounding box of the tile's inputs
                     const int bx0 = std::max(2 * x - 2, 0), bx1 = std::min(2 * x - 2 + D1_SX, g.nx[0]);
                     const int by0 = std::max(2 * y - 2, 0), by1 = std::min(2 * y - 2 + D1_SY, g.ny[0]);
-                    D1Tile t{i, x, y, -1, -1, 0, 0, 0, -1, -1, 0, 0, 0};
+                    D1Tile t{i, x, y, -1, -1, 0, 0, 0, -1, -1, 0, 0, 0, -1};
                     D1Cams tc{(int)refs.size(), 0, -1, 0};
                     for (int j = 0; j < g.ncam; ++j) {
                         const CamDev& cj = r->hcam[j];
@@ -1820,6 +1884,7 @@ stitch_status fused_plan(stitch_rig* r) {
                         if (tc.count == 1) t.flags |= D1_INTERIOR;
                     }
                     t.wtab = (t.flags & D1_INTERIOR) ? -1 : fs->n_wtab++;
+                    t.wsel = t.wtab;
                     int fx0, fy0, fw, fh;
                     if (d1_footprint(c, g, Rect{bx0, bx1, by0, by1}, fx0, fy0, fw, fh)) {
                         t.fxy = fx0 | (fy0 << 16);
@@ -1835,24 +1900,6 @@ stitch_status fused_plan(stitch_rig* r) {
             for (int y = o.y0; y < o.y1; y += RT_Y)
                 for (int x = o.x0; x < o.x1; x += RT_X) red[l].push_back({i, x, y, 0});
         }
-    }
-    std::vector<LevelTile> co[MAXL];
-    std::vector<int> camlist;
-    for (int l = 2; l < L; ++l) {
-        fs->R[l] = rig_alloc(r, elem * (size_t)g.nx[l] * g.ny[l]);
-        if (!fs->R[l]) return STITCH_ENOMEM;
-        for (int y = 0; y < g.ny[l]; y += CT_Y)
-            for (int x = 0; x < g.nx[l]; x += CT_X) {
-                LevelTile t{x, y, (int)camlist.size(), 0};
-                for (int j = 0; j < g.ncam; ++j) {
-                    const CamDev& cj = r->hcam[j];
-                    if (!cj.visible || !rects_meet(cj.Z[l], x, std::min(x + CT_X, g.nx[l]), y, std::min(y + CT_Y, g.ny[l])))
-                        continue;
-                    camlist.push_back(j);
-                    ++t.count;
-                }
-                co[l].push_back(t);
-            }
     }
     // classify the canvas tiles of `up`
     std::vector<UpTile> up[UP_KINDS];
@@ -1948,6 +1995,54 @@ stitch_status fused_plan(stitch_rig* r) {
             }
             if (kind >= 0) up[kind].push_back(t);
         }
+    // coarse tiles: R^l (l >= 2) is read only by the FULL and GENERAL canvas tiles (R^2, in a halo
+    // around the tile) and by the coarse tiles of level l - 1 (R^l, in a halo), so a coarse tile is
+    // emitted only where one of those readers needs it (the halos taken with a margin of 2)
+    std::vector<char> need[MAXL];
+    auto mark = [&](int l, int x0, int x1, int y0, int y1) {
+        x0 = std::max(x0, 0);
+        y0 = std::max(y0, 0);
+        x1 = std::min(x1, g.nx[l]);
+        y1 = std::min(y1, g.ny[l]);
+        const int ntx = (g.nx[l] + CT_X - 1) / CT_X;
+        for (int ty = y0 / CT_Y; ty * CT_Y < y1; ++ty)
+            for (int tx = x0 / CT_X; tx * CT_X < x1; ++tx) need[l][(size_t)ty * ntx + tx] = 1;
+    };
+    for (int l = 2; l < L; ++l)
+        need[l].assign((size_t)((g.nx[l] + CT_X - 1) / CT_X) * ((g.ny[l] + CT_Y - 1) / CT_Y), 0);
+    if (L >= 3) {
+        for (int kind : {UP_FULL2, UP_FULL4, UP_GENERAL})
+            for (const UpTile& t : up[kind])
+                mark(2, t.x0 / 4 - 4, t.x0 / 4 + U_TX / 4 + 4, t.y0 / 4 - 4, t.y0 / 4 + U_TY / 4 + 4);
+        for (int l = 2; l + 1 < L; ++l) {
+            const int ntx = (g.nx[l] + CT_X - 1) / CT_X;
+            for (size_t k = 0; k < need[l].size(); ++k)
+                if (need[l][k]) {
+                    const int x = (int)(k % ntx) * CT_X, y = (int)(k / ntx) * CT_Y;
+                    mark(l + 1, x / 2 - 4, x / 2 + CT_X / 2 + 4, y / 2 - 4, y / 2 + CT_Y / 2 + 4);
+                }
+        }
+    }
+    std::vector<LevelTile> co[MAXL];
+    std::vector<int> camlist;
+    for (int l = 2; l < L; ++l) {
+        fs->R[l] = rig_alloc(r, elem * (size_t)g.nx[l] * g.ny[l]);
+        if (!fs->R[l]) return STITCH_ENOMEM;
+        const int ntx = (g.nx[l] + CT_X - 1) / CT_X;
+        for (int y = 0; y < g.ny[l]; y += CT_Y)
+            for (int x = 0; x < g.nx[l]; x += CT_X) {
+                if (!need[l][(size_t)(y / CT_Y) * ntx + x / CT_X]) continue;
+                LevelTile t{x, y, (int)camlist.size(), 0};
+                for (int j = 0; j < g.ncam; ++j) {
+                    const CamDev& cj = r->hcam[j];
+                    if (!cj.visible || !rects_meet(cj.Z[l], x, std::min(x + CT_X, g.nx[l]), y, std::min(y + CT_Y, g.ny[l])))
+                        continue;
+                    camlist.push_back(j);
+                    ++t.count;
+                }
+                co[l].push_back(t);
+            }
+    }
     // L2 prefetch chain: blocks start in index order as resident ones finish, so tile i + K
     // (K = resident blocks of k_down1 on the device) starts about when tile i ends
     {
@@ -1966,6 +2061,9 @@ stitch_status fused_plan(stitch_rig* r) {
             d1[k].pf_cw = nx.cam | ((nx.wtab + 1) << 8);
         }
     }
+    // INTERIOR tiles sample with the table of ones, after the tiles' own tables
+    for (D1Tile& t : d1)
+        if (t.wsel < 0) t.wsel = fs->n_wtab;
     fs->h_d1 = d1;
     for (int l = 0; l < MAXL; ++l) {
         fs->h_red[l] = red[l];
@@ -1981,8 +2079,8 @@ stitch_status fused_plan(stitch_rig* r) {
     st = upload(r, cols, &fs->d1cols);
     if (st != STITCH_OK) return st;
     fs->n_d1 = (int)d1.size();
-    if (fs->n_wtab > 0) {
-        fs->d1w = (float*)rig_alloc(r, sizeof(float) * D1_NSAMP * (size_t)fs->n_wtab);
+    if (fs->n_d1 > 0) {
+        fs->d1w = (float*)rig_alloc(r, sizeof(float) * D1_NSAMP * (size_t)(fs->n_wtab + 1));
         if (!fs->d1w) return STITCH_ENOMEM;
     }
     if (fs->n_g0 > 0) {
@@ -2008,7 +2106,7 @@ stitch_status fused_plan(stitch_rig* r) {
     }
     int kernels = 0;
     if (L >= 2 && fs->n_d1 > 0) kernels += 1;
-    for (int l = 2; l < L; ++l) kernels += (fs->n_red[l] > 0) + 1;
+    for (int l = 2; l < L; ++l) kernels += (fs->n_red[l] > 0) + (fs->n_co[l] > 0);
     for (int k = 0; k < UP_KINDS; ++k) kernels += fs->n_up[k] > 0;
     r->kernels_per_frame = kernels;
     st = fs->fp16 ? set_smem_attrs<half4>() : set_smem_attrs<float4>();
@@ -2024,9 +2122,14 @@ stitch_status fused_frames(stitch_rig* r, const FramePtrs& fp, const OutDesc& od
 
 stitch_status fused_precompute(stitch_rig* r) {
     FusedState* fs = (FusedState*)r->fused;
-    if (!fs || fs->n_wtab == 0) return STITCH_OK;
-    k_d1_weights<<<fs->n_d1, D1W_THREADS>>>(r->dcam, r->geom, fs->d1_tiles, fs->d1_cams, fs->refs, fs->d1w);
-    STITCH_CUDA_TRY(cudaGetLastError());
+    if (!fs || fs->n_d1 == 0) return STITCH_OK;
+    if (fs->n_wtab > 0) {
+        k_d1_weights<<<fs->n_d1, D1W_THREADS>>>(r->dcam, r->geom, fs->d1_tiles, fs->d1_cams, fs->refs, fs->d1w);
+        STITCH_CUDA_TRY(cudaGetLastError());
+    }
+    const std::vector<float> ones(D1_NSAMP, 1.0f);
+    STITCH_CUDA_TRY(cudaMemcpy(fs->d1w + (size_t)fs->n_wtab * D1_NSAMP, ones.data(), sizeof(float) * D1_NSAMP,
+                               cudaMemcpyHostToDevice));
     STITCH_CUDA_TRY(cudaDeviceSynchronize());
     return STITCH_OK;
 }
@@ -2086,7 +2189,9 @@ struct BatchRigDev {
     void* R[MAXL];
 };
 
-// A task carries a copy of its tile record, so a block needs one load to start.
+// A task carries a copy of its tile record, so a block needs one load to start.  A down1 task of
+// the persistent schedule stands for pad0 (<= 4) consecutive tiles from idx on, read from the rig's
+// tile table.
 struct BTask {
     int rig, type, idx, level, stage, pad0, pad1, pad2;
     int tile[14];
@@ -2098,7 +2203,9 @@ __device__ __forceinline__ const TL& task_tile(const BTask& tk) {
 }
 
 constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
-constexpr size_t B_SMEM = cmax(cmax(cmax(D1_SMEM, RT_SMEM), sizeof(float4) * CT_SMEM_F4),
+constexpr int B_D1_GROUPS = B_THREADS / D1_THREADS;  // down1 tiles a persistent block works on at once
+static_assert(B_D1_GROUPS == 4 && D1_SMEM % 16 == 0, "four 64-thread down1 groups per block");
+constexpr size_t B_SMEM = cmax(cmax(cmax(B_D1_GROUPS * D1_SMEM, RT_SMEM), sizeof(float4) * CT_SMEM_F4),
                                cmax(up_full_smem<4>(), (size_t)3 * U_TX * U_TY));
 
 constexpr int B_MAXRIGS = 64;
@@ -2178,9 +2285,15 @@ __global__ void __launch_bounds__(B_THREADS, MINB) k_batch(const BatchRigDev* __
             const BatchRigDev& rg = rigs[tk.rig];
             const T* R2 = rg.g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
             switch (tk.type) {
-                case BT_D1:
-                    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, rg.d1cols, (T*)rg.g0buf, smem);
+                case BT_D1: {
+                    // up to four consecutive down1 tiles of the rig, one per group of 64 threads
+                    const int grp = t / D1_THREADS;
+                    if (grp < tk.pad0)
+                        down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, rg.d1[tk.idx + grp], rg.refs, rg.d1w, rg.d1cols,
+                                      (T*)rg.g0buf, reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + grp * D1_SMEM),
+                                      t % D1_THREADS, 1 + grp);
                     break;
+                }
                 case BT_RED:
                     reduce_tile<T>(rg.cams, rg.g, tk.level - 1, task_tile<Tile>(tk), smem);
                     break;
@@ -2314,6 +2427,8 @@ struct BatchState {
     cudaStream_t rs[B_MAXRIGS] = {};
     cudaEvent_t rdone[B_MAXRIGS] = {};
     cudaEvent_t fork = nullptr;
+    cudaEvent_t last = nullptr;  // recorded after each call's work
+    bool launched = false;
     long long tasks_by_type[8] = {};
 };
 
@@ -2337,6 +2452,7 @@ void b_free(BatchState* b) {
         if (b->rdone[k]) cudaEventDestroy(b->rdone[k]);
     }
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->last) cudaEventDestroy(b->last);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (void* p : b->allocs) cudaFree(p);
@@ -2363,6 +2479,14 @@ stitch_status b_launch(BatchState* b, int order, int variant, int grid, int chun
 }
 
 stitch_status b_prepare(BatchState* b, cudaStream_t s);
+
+// Report a wait that gave up: clear the device status and its host copy, return STITCH_ETIMEOUT.
+stitch_status b_clear_status(BatchState* b) {
+    *b->h_status = 0;
+    STITCH_CUDA_TRY(cudaMemset(b->d_ctl + 1, 0, sizeof(int)));
+    return STITCH_ETIMEOUT;
+}
+
 
 template <typename T>
 stitch_status b_launch_staged(BatchState* b, cudaStream_t s) {
@@ -2419,9 +2543,13 @@ stitch_status b_build_staged_graph(BatchState* b) {
     return STITCH_OK;
 }
 
+// Per call: the rig descriptors, the next-task counter ctl[0] and the abort flag ctl[2] reset, the
+// completion counters cleared.  The status ctl[1] stays set once a wait has given up, until the host
+// has reported it (fused_batch_status), so no call's timeout goes unreported.
 stitch_status b_prepare(BatchState* b, cudaStream_t s) {
     STITCH_CUDA_TRY(cudaMemcpyAsync(b->d_rigs, b->h_rigs, sizeof(BatchRigDev) * b->n, cudaMemcpyHostToDevice, s));
-    STITCH_CUDA_TRY(cudaMemsetAsync(b->d_ctl, 0, 3 * sizeof(int), s));
+    STITCH_CUDA_TRY(cudaMemsetAsync(b->d_ctl, 0, sizeof(int), s));
+    STITCH_CUDA_TRY(cudaMemsetAsync(b->d_ctl + 2, 0, sizeof(int), s));
     STITCH_CUDA_TRY(cudaMemsetAsync(b->d_done, 0, sizeof(int) * b->need.size(), s));
     return STITCH_OK;
 }
@@ -2431,17 +2559,19 @@ stitch_status b_build_graph(BatchState* b) {
     cudaGraph_t g;
     STITCH_CUDA_TRY(cudaGraphCreate(&g, 0));
     b->graph = g;
-    cudaGraphNode_t cp, m1, m2, kb, kg = nullptr, st;
+    cudaGraphNode_t cp, m1, m1b, m2, kb, kg = nullptr, st;
     STITCH_CUDA_TRY(cudaGraphAddMemcpyNode1D(&cp, g, nullptr, 0, b->d_rigs, b->h_rigs, sizeof(BatchRigDev) * b->n,
                                              cudaMemcpyHostToDevice));
     cudaMemsetParams ms{};
     ms.dst = b->d_ctl;
     ms.value = 0;
     ms.elementSize = sizeof(int);
-    ms.width = 3;
+    ms.width = 1;
     ms.height = 1;
     ms.pitch = 0;
     STITCH_CUDA_TRY(cudaGraphAddMemsetNode(&m1, g, nullptr, 0, &ms));
+    ms.dst = b->d_ctl + 2;
+    STITCH_CUDA_TRY(cudaGraphAddMemsetNode(&m1b, g, nullptr, 0, &ms));
     ms.dst = b->d_done;
     ms.width = b->need.size();
     STITCH_CUDA_TRY(cudaGraphAddMemsetNode(&m2, g, nullptr, 0, &ms));
@@ -2454,8 +2584,8 @@ stitch_status b_build_graph(BatchState* b) {
     kp.blockDim = dim3(B_THREADS);
     kp.sharedMemBytes = (unsigned)B_SMEM;
     kp.kernelParams = args;
-    cudaGraphNode_t deps[3] = {cp, m1, m2};
-    STITCH_CUDA_TRY(cudaGraphAddKernelNode(&kb, g, deps, 3, &kp));
+    cudaGraphNode_t deps[4] = {cp, m1, m1b, m2};
+    STITCH_CUDA_TRY(cudaGraphAddKernelNode(&kb, g, deps, 4, &kp));
     cudaLaunchAttributeValue coop{};
     coop.cooperative = 1;
     STITCH_CUDA_TRY(cudaGraphKernelNodeSetAttribute(kb, cudaLaunchAttributeCooperative, &coop));
@@ -2532,7 +2662,7 @@ stitch_status b_tune(BatchState* b, cudaStream_t s) {
                     STITCH_CUDA_TRY(cudaEventSynchronize(e1));
                     int status = 0;
                     STITCH_CUDA_TRY(cudaMemcpy(&status, b->d_ctl + 1, sizeof(int), cudaMemcpyDeviceToHost));
-                    if (status) return STITCH_ETIMEOUT;
+                    if (status) return b_clear_status(b);
                     float ms = 0.f;
                     cudaEventElapsedTime(&ms, e0, e1);
                     if (rep == 1 && ms < best) {
@@ -2613,6 +2743,7 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
         b_free(b);
         return STITCH_ENOMEM;
     }
+    *b->h_status = 0;
     for (int k = 0; k < n; ++k) {
         stitch_rig* r = rigs[k];
         FusedState* fs = (FusedState*)r->fused;
@@ -2672,16 +2803,33 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
             for (int i = 0; i < fs->n_up[UP_GENERAL]; ++i) gtasks.push_back(mk(BT_UPG, i, 0, st));
         }
     }
+    // the persistent schedule takes the down1 tiles four at a time (one per 64-thread group)
+    std::vector<std::vector<std::vector<BTask>>> pstages(n);
+    for (int k = 0; k < n; ++k)
+        for (size_t st = 0; st < stages[k].size(); ++st) {
+            const std::vector<BTask>& v = stages[k][st];
+            pstages[k].emplace_back();
+            if (v.empty() || v[0].type != BT_D1) {
+                pstages[k].back() = v;
+                continue;
+            }
+            for (size_t i = 0; i < v.size(); i += B_D1_GROUPS) {
+                BTask tk = v[i];
+                tk.pad0 = (int)std::min<size_t>(B_D1_GROUPS, v.size() - i);
+                pstages[k].back().push_back(tk);
+            }
+            b->need[(size_t)k * B_MAXSTAGE + st] = (int)pstages[k].back().size();
+        }
     // two orderings: stages ranked from the start, or aligned so that every rig ends together
     int maxs = 0;
-    for (int k = 0; k < n; ++k) maxs = std::max(maxs, (int)stages[k].size());
+    for (int k = 0; k < n; ++k) maxs = std::max(maxs, (int)pstages[k].size());
     std::vector<BTask> ord[2];
     for (int o = 0; o < 2; ++o)
         for (int rank = 0; rank < maxs; ++rank)
             for (int k = 0; k < n; ++k) {
-                const int s = o == 0 ? rank : rank - (maxs - (int)stages[k].size());
-                if (s < 0 || s >= (int)stages[k].size()) continue;
-                ord[o].insert(ord[o].end(), stages[k][s].begin(), stages[k][s].end());
+                const int s = o == 0 ? rank : rank - (maxs - (int)pstages[k].size());
+                if (s < 0 || s >= (int)pstages[k].size()) continue;
+                ord[o].insert(ord[o].end(), pstages[k][s].begin(), pstages[k][s].end());
             }
     b->ntasks = (int)ord[0].size();
     stitch_status st = STITCH_OK;
@@ -2758,6 +2906,11 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
         b->max_bpsm[variant] = bpsm;
     }
     b->grid = b->max_bpsm[1] * b->sms;
+    if (cudaEventCreateWithFlags(&b->last, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        b_free(b);
+        return STITCH_ECUDA;
+    }
     *out = b;
     return STITCH_OK;
 }
@@ -2792,17 +2945,29 @@ stitch_status fused_batch_frames(void* bp, const uint8_t* const* const* frames, 
             if (gs != STITCH_OK) return gs;
         }
     }
+    // a wait that gave up in an earlier call whose work has completed is reported now, before any
+    // further launch; one that has not completed yet is reported by a later call or by
+    // fused_batch_status
+    if (b->launched && cudaEventQuery(b->last) == cudaSuccess && *b->h_status) return b_clear_status(b);
+    cudaGetLastError();  // a cudaErrorNotReady of the query is not an error
     if (b->streams) {
         // the frame and output pointers are kernel arguments here: launched directly, no graph
         const stitch_status st = b->fp16 ? b_launch_streams<half4>(b, s) : b_launch_streams<float4>(b, s);
         if (st != STITCH_OK) return st;
-        STITCH_CUDA_TRY(cudaStreamSynchronize(s));
-        return STITCH_OK;
+    } else {
+        STITCH_CUDA_TRY(cudaGraphLaunch(b->exec, s));
     }
-    *b->h_status = 0;
-    STITCH_CUDA_TRY(cudaGraphLaunch(b->exec, s));
-    STITCH_CUDA_TRY(cudaStreamSynchronize(s));
-    return *b->h_status ? STITCH_ETIMEOUT : STITCH_OK;
+    STITCH_CUDA_TRY(cudaEventRecord(b->last, s));
+    b->launched = true;
+    return STITCH_OK;
+}
+
+stitch_status fused_batch_status(void* bp) {
+    BatchState* b = (BatchState*)bp;
+    if (!b) return STITCH_EINVAL;
+    if (!b->launched) return STITCH_OK;
+    STITCH_CUDA_TRY(cudaEventSynchronize(b->last));
+    return *b->h_status ? b_clear_status(b) : STITCH_OK;
 }
 
 void fused_batch_destroy(void* bp) {

@@ -540,6 +540,7 @@ stitch_status fused_batch_frames(void* b, const uint8_t* const* const* frames, c
 void fused_batch_destroy(void* b);
 stitch_status fused_batch_info(void* b, int32_t* order, int32_t* grid, int64_t* ntasks);
 stitch_status fused_batch_wait_test(void* b, int spin_limit, int rig);
+stitch_status fused_batch_status(void* b);
 
 #define STITCH_CUDA_TRY(expr)                         \
     do {                                              \

@@ -81,6 +81,7 @@ SIGNATURES = {
     "stitch_batch_get_schedule": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                                  ctypes.POINTER(ctypes.c_int64)]),
     "stitch_batch_wait_test": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "stitch_batch_sync": (ctypes.c_int, [_P]),
     "stitch_frames_static": (ctypes.c_int, [ctypes.POINTER(stitch_rig_desc), _P, _P, _P, ctypes.c_int64, _P]),
     "stitch_lorb_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(_P)]),
@@ -251,6 +252,10 @@ def stitch_batch_get_schedule(batch: int) -> dict:
             "chunk": o.value >> 8, "grid": g.value, "tasks": t.value}
 
 
+def stitch_batch_sync(batch: int) -> None:
+    _check(load().stitch_batch_sync(batch), "stitch_batch_sync")
+
+
 def stitch_batch_wait_test(batch: int, spin_limit: int, rig: int) -> None:
     _check(load().stitch_batch_wait_test(batch, spin_limit, rig), "stitch_batch_wait_test")
 
@@ -402,7 +407,9 @@ class Rig:
 
 
 class Batch:
-    """Several rigs (fused path, same device and band storage) stitched by one persistent launch."""
+    """Several rigs (fused path, same device and band storage) stitched together by the schedule
+    the batch picks on its first call.  stitch() is asynchronous after that first call; sync()
+    waits for the last call and raises if a device wait gave up."""
 
     def __init__(self, rigs):
         self.rigs = list(rigs)
@@ -443,6 +450,9 @@ class Batch:
             ops_pitch.append(opitch)
         stitch_batch_frames(self.handle, fps, pts, ops, ops_pitch, _stream_handle(stream))
         return outs
+
+    def sync(self) -> None:
+        stitch_batch_sync(self.handle)
 
     def schedule(self) -> dict:
         return stitch_batch_get_schedule(self.handle)

@@ -65,6 +65,30 @@ def test_backward_matches_oracle_scaled():
         _compare(cfg, rig, p0, signs, frames)
 
 
+def test_backward_entrywise_against_oracle():
+    """Entry by entry: every gradient entry whose pixel-scaled size is at least 1 % of its camera's
+    largest is within 1e-3 of the oracle's value, relative to that entry (scaled rig, perturbed
+    corners and gains, and the true geometry)."""
+    import torch
+    cfg = synth.config_refine(scale=0.25)
+    frames = cfg.frame(0)
+    dev = gpu_util.gpu_frames(frames)
+    rig, p, signs, _, _ = _rig_and_params(cfg, np.random.default_rng(1), 1.0, (0.8, 1.2))
+    _, p0, _, _, _ = _rig_and_params(cfg)
+    s = _px_scale(cfg)
+    with rig:
+        for params in (p, p0):
+            _, grad = rig.backward(dev, torch.tensor(params, device="cuda"))
+            torch.cuda.synchronize()
+            grad = grad.cpu().numpy()
+            _, go = oracle.loss_grad([c.width for c in cfg.cameras], [c.height for c in cfg.cameras], params, frames,
+                                     (0, 0, cfg.canvas_w, cfg.canvas_h), a33=signs)
+            for i in range(len(cfg.cameras)):
+                big = np.abs(go[i] * s) >= 0.01 * np.abs(go[i] * s).max()
+                rel = np.abs(grad[i] - go[i])[big] / np.abs(go[i])[big]
+                assert rel.max() <= 1e-3, (i, rel.max(), grad[i], go[i])
+
+
 def test_backward_matches_oracle_full_size():
     """The 4-camera 1920x1080 refinement rig (canvas 5200x1300), perturbed corners and gains."""
     cfg = synth.config_refine()

@@ -69,6 +69,23 @@ def test_batch_matches_oracle():
         r.close()
 
 
+def test_batch_full_size_matches_oracle_windows():
+    """The full-size 16-rig batch (2-6 cameras of 720p/1080p/4K, 4-6 levels): windows at every
+    rig's seams, corners and random places against the oracle (each window evaluated exactly)."""
+    from paper_1810_03988_gb300 import Batch
+    cfgs = synth.config_batch(16, seed=0)
+    rigs, frames = _rigs_and_frames(cfgs)
+    with Batch(rigs) as b:
+        got = [o.cpu().numpy() for o in b.stitch(frames)]
+    for k, (cfg, g) in enumerate(zip(cfgs, got)):
+        host = cfg.frame(0)
+        for (x0, y0, w, h) in gpu_util.sample_windows(cfg, 6, 48, seed=k)[:10]:
+            ref = oracle.forward(cfg.cameras, host, cfg.canvas_w, cfg.canvas_h, cfg.levels, window=(x0, y0, w, h))
+            gpu_util.compare(g[y0:y0 + h, x0:x0 + w], ref, False)
+    for r in rigs:
+        r.close()
+
+
 def test_batch_fp16_bands():
     from paper_1810_03988_gb300 import Batch
     cfgs = synth.config_batch(4, seed=2, scale=0.125)
@@ -108,8 +125,8 @@ def test_each_schedule_equals_per_rig_launches(mode, forced_schedule):
 
 def test_batch_bounded_wait_times_out_and_recovers(forced_schedule):
     """A stage target that is never reached makes the device wait of the persistent schedule give
-    up: the call returns STITCH_ETIMEOUT, and after restoring the target the same batch stitches
-    correctly."""
+    up: the asynchronous call's outcome, read by sync(), is STITCH_ETIMEOUT, and after restoring the
+    target the same batch stitches correctly."""
     from paper_1810_03988_gb300 import Batch, StitchError, stitch
     forced_schedule("persistent")
     cfgs = synth.config_batch(3, seed=1, scale=0.125)
@@ -120,9 +137,13 @@ def test_batch_bounded_wait_times_out_and_recovers(forced_schedule):
         b.wait_test(2000, 0)
         with pytest.raises(StitchError) as e:
             b.stitch(frames)
+            b.sync()
         assert e.value.status == stitch.STITCH_ETIMEOUT
+        b.sync()  # reported once
         b.wait_test(1 << 22, -1)
-        got = [o.cpu().numpy() for o in b.stitch(frames)]
+        outs = b.stitch(frames)
+        b.sync()
+        got = [o.cpu().numpy() for o in outs]
     for g, r in zip(got, ref):
         assert np.array_equal(g, r)
     for r in rigs:

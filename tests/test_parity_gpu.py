@@ -294,3 +294,32 @@ def test_fp16_bands_8x4k_full_size_windows():
     for (x0, y0, w, h) in gpu_util.sample_windows(cfg, 20, 32):
         ref = oracle.forward(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h, cfg.levels, window=(x0, y0, w, h))
         gpu_util.compare(got[y0:y0 + h, x0:x0 + w], ref, True, tol=gpu_util.TOL_F16)
+
+
+def _max_rig():
+    """32 cameras (the ABI's maximum) in an 8 x 4 grid of overlapping 160 x 120 views with small
+    rotations and a perspective term, on a 1140 x 420 canvas with 12 levels (the maximum: the
+    level sizes run 1140, 570, ..., 2, 1)."""
+    from paper_1810_03988_gb300 import stitch
+    cams, frames = [], []
+    rng = np.random.default_rng(11)
+    for gy in range(4):
+        for gx in range(8):
+            a = rng.uniform(-0.05, 0.05)
+            H = np.array([[np.cos(a), -np.sin(a), 10.0 + gx * 140.0 + rng.uniform(-3, 3)],
+                          [np.sin(a), np.cos(a), 8.0 + gy * 100.0 + rng.uniform(-3, 3)],
+                          [rng.uniform(-2e-5, 2e-5), rng.uniform(-2e-5, 2e-5), 1.0]])
+            cams.append(Camera(160, 120, H))
+            frames.append(_rand(120, 160, 500 + len(frames)))
+    assert len(cams) == stitch.STITCH_MAX_CAMERAS
+    return synth.RigConfig("max", cams, 1140, 420, stitch.STITCH_MAX_LEVELS, 1, None), frames
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_abi_maxima_full_canvas(path):
+    """32 cameras and 12 pyramid levels: every canvas pixel against the oracle, float and uint8."""
+    cfg, frames = _max_rig()
+    ref = oracle.forward(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h, cfg.levels)
+    for out_float in (True, False):
+        got = gpu_util.run_gpu(cfg, frames, path, out_float=out_float)
+        gpu_util.compare(got, ref, out_float)
