@@ -373,16 +373,25 @@ void stitch_batch_destroy(stitch_batch* batch);
 
 /*
  * The schedule the batch runs, chosen on its first stitch_batch_frames call by timing every
- * candidate on the real frames.  Candidates: the cooperative persistent launch (stage ordering x
- * register variant x tasks per dequeue) and the staged schedule (one launch per task type and
- * level over all rigs, no device waits), both replayed from a CUDA graph, and the per-rig streams
- * (every rig's own launch sequence on a stream of its own, launched directly).  The environment
- * variable STITCH_TUNE=off skips timing (persistent defaults), =persistent, =staged or =streams
- * forces one.  *order is 0xF for the staged schedule, 0xE for the per-rig streams; otherwise
- * bits 0-3 are the stage ordering (0 ranks every
- * rig's stages from the start, 1 aligns them so every rig finishes together), bits 4-7 the
- * register variant (0: 2 resident blocks per SM, 1: 3), bits 8+ the tasks a block dequeues at
- * once.  *grid is the number of persistent blocks; *tasks the number of tile tasks per call.
+ * candidate on the real frames.  Candidates:
+ *   - the cooperative persistent launch (stage ordering x register variant x tasks per dequeue),
+ *     replayed from a CUDA graph;
+ *   - the staged schedule (one launch per task type and level over all rigs, no device waits),
+ *     replayed from a CUDA graph, with four tile-shape combinations for its REDUCE launches
+ *     (32 x 16 or 64 x 8 outputs) and coarse-level launches (32 x 32 or 64 x 16);
+ *   - the per-rig streams (every rig's own launch sequence on a stream of its own, launched directly).
+ * Environment: STITCH_TUNE=off skips timing (persistent defaults); =persistent, =staged or =streams
+ * forces that mode (its parameters still timed); =full times even when a cached choice exists.
+ * STITCH_TUNE_CACHE=<path> names a file of JSON lines keyed by the GPU's name and SM count and a hash
+ * of every rig's description: a batch whose key is found takes the stored choice without timing,
+ * and a timed choice is appended to it.
+ * Encoding: bit 24 of *order is set when the choice came from the cache.  Below it, 0xE marks the
+ * per-rig streams; a low nibble of 0xF the staged schedule, with bits 8-11 its tile shapes (bit 8:
+ * 64 x 8 reduce tiles, bit 9: 64 x 16 coarse tiles); otherwise the persistent launch, with bits 0-3
+ * the stage ordering (0 ranks every rig's stages from the start, 1 aligns them so every rig
+ * finishes together), bits 4-7 the register variant (0: 2 resident blocks per SM, 1: 3) and bits
+ * 8-23 the tasks a block dequeues at once.  *grid is the number of persistent blocks; *tasks the
+ * number of tile tasks per call.
  */
 stitch_status stitch_batch_get_schedule(const stitch_batch* batch, int32_t* order, int32_t* grid, int64_t* tasks);
 

@@ -39,6 +39,9 @@
 //          clamped warp of camera c, with no pyramid work;
 //   FULL   up to 2 or 4 contributing cameras, everything in shared memory;
 //   GENERAL more cameras: a slower kernel that streams one camera at a time.
+#include <cstdio>
+#include <cstring>
+#include <string>
 #include <unordered_map>
 
 #include "stitch_internal.cuh"
@@ -1752,6 +1755,70 @@ bool d1_footprint(const CamDev& c, const RigGeom& g, const Rect& q, int& fx0, in
     return true;
 }
 
+// Reduce tiles producing level l >= 2 of every visible camera: tx x ty outputs on its Omega^l.
+void plan_reduce_tiles(const stitch_rig* r, int tx, int ty, std::vector<Tile> red[MAXL]) {
+    const RigGeom& g = r->geom;
+    for (int i = 0; i < g.ncam; ++i) {
+        const CamDev& c = r->hcam[i];
+        if (!c.visible) continue;
+        for (int l = 2; l < g.levels; ++l) {
+            const Rect o = c.Om[l];
+            for (int y = o.y0; y < o.y1; y += ty)
+                for (int x = o.x0; x < o.x1; x += tx) red[l].push_back({i, x, y, 0});
+        }
+    }
+}
+
+// Coarse tiles of tx x ty on levels l >= 2 and their cameras (those whose Z^l meets the tile).
+// R^l is read only by the FULL and GENERAL canvas tiles (R^2, in a halo around the tile) and by the
+// coarse tiles of level l - 1 (R^l, in a halo), so a coarse tile is emitted only where one of those
+// readers needs it (the halos taken with a margin of 2).
+void plan_coarse_tiles(const stitch_rig* r, const std::vector<UpTile>* up, int tx, int ty, std::vector<LevelTile> co[MAXL],
+                       std::vector<int>& camlist) {
+    const RigGeom& g = r->geom;
+    const int L = g.levels;
+    std::vector<char> need[MAXL];
+    auto mark = [&](int l, int x0, int x1, int y0, int y1) {
+        x0 = std::max(x0, 0);
+        y0 = std::max(y0, 0);
+        x1 = std::min(x1, g.nx[l]);
+        y1 = std::min(y1, g.ny[l]);
+        const int ntx = (g.nx[l] + tx - 1) / tx;
+        for (int yy = y0 / ty; yy * ty < y1; ++yy)
+            for (int xx = x0 / tx; xx * tx < x1; ++xx) need[l][(size_t)yy * ntx + xx] = 1;
+    };
+    for (int l = 2; l < L; ++l) need[l].assign((size_t)((g.nx[l] + tx - 1) / tx) * ((g.ny[l] + ty - 1) / ty), 0);
+    if (L >= 3) {
+        for (int kind : {UP_FULL2, UP_FULL4, UP_GENERAL})
+            for (const UpTile& t : up[kind])
+                mark(2, t.x0 / 4 - 4, t.x0 / 4 + U_TX / 4 + 4, t.y0 / 4 - 4, t.y0 / 4 + U_TY / 4 + 4);
+        for (int l = 2; l + 1 < L; ++l) {
+            const int ntx = (g.nx[l] + tx - 1) / tx;
+            for (size_t k = 0; k < need[l].size(); ++k)
+                if (need[l][k]) {
+                    const int x = (int)(k % ntx) * tx, y = (int)(k / ntx) * ty;
+                    mark(l + 1, x / 2 - 4, x / 2 + tx / 2 + 4, y / 2 - 4, y / 2 + ty / 2 + 4);
+                }
+        }
+    }
+    for (int l = 2; l < L; ++l) {
+        const int ntx = (g.nx[l] + tx - 1) / tx;
+        for (int y = 0; y < g.ny[l]; y += ty)
+            for (int x = 0; x < g.nx[l]; x += tx) {
+                if (!need[l][(size_t)(y / ty) * ntx + x / tx]) continue;
+                LevelTile t{x, y, (int)camlist.size(), 0};
+                for (int j = 0; j < g.ncam; ++j) {
+                    const CamDev& cj = r->hcam[j];
+                    if (!cj.visible || !rects_meet(cj.Z[l], x, std::min(x + tx, g.nx[l]), y, std::min(y + ty, g.ny[l])))
+                        continue;
+                    camlist.push_back(j);
+                    ++t.count;
+                }
+                co[l].push_back(t);
+            }
+    }
+}
+
 template <typename T>
 stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, const OutDesc& od, cudaStream_t s) {
     const RigGeom& g = r->geom;
@@ -1895,12 +1962,8 @@ stitch_status fused_plan(stitch_rig* r) {
                     d1c.push_back(tc);
                 }
         }
-        for (int l = 2; l < L; ++l) {
-            const Rect o = c.Om[l];
-            for (int y = o.y0; y < o.y1; y += RT_Y)
-                for (int x = o.x0; x < o.x1; x += RT_X) red[l].push_back({i, x, y, 0});
-        }
     }
+    plan_reduce_tiles(r, RT_X, RT_Y, red);
     // classify the canvas tiles of `up`
     std::vector<UpTile> up[UP_KINDS];
     std::unordered_map<long long, size_t> d1_index;  // (camera, level-1 origin) -> down1 tile
@@ -1995,54 +2058,13 @@ stitch_status fused_plan(stitch_rig* r) {
             }
             if (kind >= 0) up[kind].push_back(t);
         }
-    // coarse tiles: R^l (l >= 2) is read only by the FULL and GENERAL canvas tiles (R^2, in a halo
-    // around the tile) and by the coarse tiles of level l - 1 (R^l, in a halo), so a coarse tile is
-    // emitted only where one of those readers needs it (the halos taken with a margin of 2)
-    std::vector<char> need[MAXL];
-    auto mark = [&](int l, int x0, int x1, int y0, int y1) {
-        x0 = std::max(x0, 0);
-        y0 = std::max(y0, 0);
-        x1 = std::min(x1, g.nx[l]);
-        y1 = std::min(y1, g.ny[l]);
-        const int ntx = (g.nx[l] + CT_X - 1) / CT_X;
-        for (int ty = y0 / CT_Y; ty * CT_Y < y1; ++ty)
-            for (int tx = x0 / CT_X; tx * CT_X < x1; ++tx) need[l][(size_t)ty * ntx + tx] = 1;
-    };
-    for (int l = 2; l < L; ++l)
-        need[l].assign((size_t)((g.nx[l] + CT_X - 1) / CT_X) * ((g.ny[l] + CT_Y - 1) / CT_Y), 0);
-    if (L >= 3) {
-        for (int kind : {UP_FULL2, UP_FULL4, UP_GENERAL})
-            for (const UpTile& t : up[kind])
-                mark(2, t.x0 / 4 - 4, t.x0 / 4 + U_TX / 4 + 4, t.y0 / 4 - 4, t.y0 / 4 + U_TY / 4 + 4);
-        for (int l = 2; l + 1 < L; ++l) {
-            const int ntx = (g.nx[l] + CT_X - 1) / CT_X;
-            for (size_t k = 0; k < need[l].size(); ++k)
-                if (need[l][k]) {
-                    const int x = (int)(k % ntx) * CT_X, y = (int)(k / ntx) * CT_Y;
-                    mark(l + 1, x / 2 - 4, x / 2 + CT_X / 2 + 4, y / 2 - 4, y / 2 + CT_Y / 2 + 4);
-                }
-        }
-    }
     std::vector<LevelTile> co[MAXL];
     std::vector<int> camlist;
     for (int l = 2; l < L; ++l) {
         fs->R[l] = rig_alloc(r, elem * (size_t)g.nx[l] * g.ny[l]);
         if (!fs->R[l]) return STITCH_ENOMEM;
-        const int ntx = (g.nx[l] + CT_X - 1) / CT_X;
-        for (int y = 0; y < g.ny[l]; y += CT_Y)
-            for (int x = 0; x < g.nx[l]; x += CT_X) {
-                if (!need[l][(size_t)(y / CT_Y) * ntx + x / CT_X]) continue;
-                LevelTile t{x, y, (int)camlist.size(), 0};
-                for (int j = 0; j < g.ncam; ++j) {
-                    const CamDev& cj = r->hcam[j];
-                    if (!cj.visible || !rects_meet(cj.Z[l], x, std::min(x + CT_X, g.nx[l]), y, std::min(y + CT_Y, g.ny[l])))
-                        continue;
-                    camlist.push_back(j);
-                    ++t.count;
-                }
-                co[l].push_back(t);
-            }
     }
+    plan_coarse_tiles(r, up, CT_X, CT_Y, co, camlist);
     // L2 prefetch chain: blocks start in index order as resident ones finish, so tile i + K
     // (K = resident blocks of k_down1 on the device) starts about when tile i ends
     {
@@ -2180,7 +2202,8 @@ struct BatchRigDev {
     const D1Tile* d1;
     const Tile* red[MAXL];
     const LevelTile* co[MAXL];
-    const int* camlist;
+    const int* camlist;    // camera lists of the coarse tiles (32 x 32) ...
+    const int* camlist_w;  // ... and of the batch's 64 x 16 coarse tiles
     const CamRef* refs;
     const float* d1w;
     const float4* d1cols;
@@ -2357,22 +2380,23 @@ __global__ void __launch_bounds__(D1_THREADS, D1_BLOCKS_PER_SM) k_mr_down1(const
     down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, rg.d1cols, (T*)rg.g0buf, smem);
 }
 
-template <typename T>
+template <typename T, typename RS>
 __global__ void __launch_bounds__(256) k_mr_reduce(const BatchRigDev* __restrict__ rigs, const BTask* __restrict__ tasks) {
     extern __shared__ float4 smem[];
     const BTask tk = tasks[blockIdx.x];
     const BatchRigDev& rg = rigs[tk.rig];
-    reduce_tile<T>(rg.cams, rg.g, tk.level - 1, task_tile<Tile>(tk), smem);
+    reduce_tile<T, RS>(rg.cams, rg.g, tk.level - 1, task_tile<Tile>(tk), smem);
 }
 
-template <typename T>
+// camlist: the rig's camera list of the coarse tiles of this shape
+template <typename T, typename CS>
 __global__ void __launch_bounds__(256, 3) k_mr_coarse(const BatchRigDev* __restrict__ rigs, const BTask* __restrict__ tasks) {
     extern __shared__ float4 smem[];
     const BTask tk = tasks[blockIdx.x];
     const BatchRigDev& rg = rigs[tk.rig];
-    coarse_tile<T>(rg.cams, rg.g, tk.level, (T*)rg.R[tk.level],
-                   tk.level + 1 < rg.g.levels ? (const T*)rg.R[tk.level + 1] : nullptr, rg.co[tk.level][tk.idx],
-                   rg.camlist, smem);
+    coarse_tile<T, CS>(rg.cams, rg.g, tk.level, (T*)rg.R[tk.level],
+                       tk.level + 1 < rg.g.levels ? (const T*)rg.R[tk.level + 1] : nullptr, task_tile<LevelTile>(tk),
+                       std::is_same<CS, CS32x32>::value ? rg.camlist : rg.camlist_w, smem);
 }
 
 __global__ void __launch_bounds__(U_THREADS) k_mr_up_simple(const BatchRigDev* __restrict__ rigs,
@@ -2399,6 +2423,12 @@ struct StageGroup {
     BTask* d_tasks;
 };
 
+// Tile shapes the staged schedule can take for its REDUCE and coarse launches (the tuner times the
+// four combinations): reduce 32 x 16 or 64 x 8 outputs, coarse 32 x 32 or 64 x 16.
+constexpr int B_SHAPES = 4;
+__host__ __device__ constexpr int b_rs(int shape) { return shape & 1; }
+__host__ __device__ constexpr int b_cs(int shape) { return shape >> 1; }
+
 struct BatchState {
     int device = 0, n = 0;
     bool fp16 = false;
@@ -2421,7 +2451,8 @@ struct BatchState {
     bool tuned = false;
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
-    std::vector<StageGroup> groups;  // staged schedule, in launch order
+    std::vector<StageGroup> groups[B_SHAPES];  // staged schedule per tile-shape combination, in launch order
+    int shape = 0;                             // the combination chosen
     bool staged = false;             // schedule chosen by the tuner: staged launches or persistent
     bool streams = false;            // ... or every rig's own launch sequence on its own stream
     cudaStream_t rs[B_MAXRIGS] = {};
@@ -2429,6 +2460,7 @@ struct BatchState {
     cudaEvent_t fork = nullptr;
     cudaEvent_t last = nullptr;  // recorded after each call's work
     bool launched = false;
+    bool from_cache = false;  // the schedule came from the tuning cache
     long long tasks_by_type[8] = {};
 };
 
@@ -2489,13 +2521,21 @@ stitch_status b_clear_status(BatchState* b) {
 
 
 template <typename T>
-stitch_status b_launch_staged(BatchState* b, cudaStream_t s) {
-    for (const StageGroup& gr : b->groups) {
+stitch_status b_launch_staged(BatchState* b, int shape, cudaStream_t s) {
+    for (const StageGroup& gr : b->groups[shape]) {
         if (!gr.count) continue;
         switch (gr.type) {
             case BT_D1: k_mr_down1<T><<<gr.count, D1_THREADS, D1_SMEM, s>>>(b->d_rigs, gr.d_tasks); break;
-            case BT_RED: k_mr_reduce<T><<<gr.count, 256, RT_SMEM, s>>>(b->d_rigs, gr.d_tasks); break;
-            case BT_CO: k_mr_coarse<T><<<gr.count, 256, sizeof(float4) * CT_SMEM_F4, s>>>(b->d_rigs, gr.d_tasks); break;
+            case BT_RED:
+                if (b_rs(shape)) k_mr_reduce<T, RS64x8><<<gr.count, 256, RS64x8::SMEM, s>>>(b->d_rigs, gr.d_tasks);
+                else k_mr_reduce<T, RS32x16><<<gr.count, 256, RS32x16::SMEM, s>>>(b->d_rigs, gr.d_tasks);
+                break;
+            case BT_CO:
+                if (b_cs(shape))
+                    k_mr_coarse<T, CS64x16><<<gr.count, 256, sizeof(float4) * CS64x16::SMEM_F4, s>>>(b->d_rigs, gr.d_tasks);
+                else
+                    k_mr_coarse<T, CS32x32><<<gr.count, 256, sizeof(float4) * CS32x32::SMEM_F4, s>>>(b->d_rigs, gr.d_tasks);
+                break;
             case BT_UPS: k_mr_up_simple<<<gr.count, U_THREADS, 0, s>>>(b->d_rigs, gr.d_tasks); break;
             case BT_UPF2: k_mr_up_full<T, 2><<<gr.count, U_THREADS, up_full_smem<2>(), s>>>(b->d_rigs, gr.d_tasks); break;
             case BT_UPF4: k_mr_up_full<T, 4><<<gr.count, U_THREADS, up_full_smem<4>(), s>>>(b->d_rigs, gr.d_tasks); break;
@@ -2509,9 +2549,14 @@ stitch_status b_launch_staged(BatchState* b, cudaStream_t s) {
 template <typename T>
 stitch_status b_staged_attrs() {
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
-    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM));
-    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_coarse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(float4) * CT_SMEM_F4)));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce<T, RS32x16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)RS32x16::SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce<T, RS64x8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)RS64x8::SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_coarse<T, CS32x32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float4) * CS32x32::SMEM_F4)));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_coarse<T, CS64x16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float4) * CS64x16::SMEM_F4)));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_up_full<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)up_full_smem<2>()));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_up_full<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2528,7 +2573,7 @@ stitch_status b_build_staged_graph(BatchState* b) {
     stitch_status st = STITCH_OK;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = STITCH_ECUDA;
     if (st == STITCH_OK) st = b_prepare(b, cs);
-    if (st == STITCH_OK) st = b_launch_staged<T>(b, cs);
+    if (st == STITCH_OK) st = b_launch_staged<T>(b, b->shape, cs);
     if (st == STITCH_OK && cudaMemcpyAsync(b->h_status, b->d_ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, cs) != cudaSuccess)
         st = STITCH_ECUDA;
     cudaGraph_t g = nullptr;
@@ -2631,6 +2676,101 @@ stitch_status b_launch_streams(BatchState* b, cudaStream_t s) {
     return STITCH_OK;
 }
 
+// Tuning cache: a file of JSON lines (STITCH_TUNE_CACHE), one object per tuned batch:
+//   {"key": "<GPU name>|<SMs>|<hash of every rig's description>", "mode": "staged", "order": 1,
+//    "variant": 1, "chunk": 4, "shape": 2, "ms": 5.43}
+// A later batch with the same key on the same kind of GPU takes the schedule without timing it;
+// the last line with a key wins.
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+    const unsigned char* c = (const unsigned char*)p;
+    for (size_t k = 0; k < n; ++k) h = (h ^ c[k]) * 1099511628211ull;
+    return h;
+}
+
+std::string b_cache_key(const BatchState* b) {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, b->device) != cudaSuccess) return std::string();
+    uint64_t h = 1469598103934665603ull;
+    const char tag[] = "libstitch batch schedule 2";
+    h = fnv1a(h, tag, sizeof(tag));
+    h = fnv1a(h, &b->n, sizeof(b->n));
+    for (const stitch_rig* r : b->rigs) {
+        const stitch_rig_desc& d = r->desc;
+        const int32_t f[9] = {d.num_cameras, d.canvas_w, d.canvas_h, d.levels, d.band_fp16, d.out_float, d.path,
+                              d.weights, d.canvas_model};
+        h = fnv1a(h, f, sizeof(f));
+        h = fnv1a(h, d.cylinder, sizeof(d.cylinder));
+        for (const stitch_camera& c : r->cams) {
+            h = fnv1a(h, &c.width, sizeof(c.width));
+            h = fnv1a(h, &c.height, sizeof(c.height));
+            h = fnv1a(h, c.H, sizeof(c.H));
+            h = fnv1a(h, &c.gain, sizeof(c.gain));
+        }
+    }
+    std::string name(prop.name);
+    for (char& ch : name)
+        if (ch == '"' || ch == '\\' || ch == '|' || (unsigned char)ch < 32) ch = '_';
+    char buf[96];
+    snprintf(buf, sizeof(buf), "|%d|%016llx", prop.multiProcessorCount, (unsigned long long)h);
+    return name + buf;
+}
+
+// Integer field `name` of a cache line, or `fallback`.
+long cache_field(const std::string& line, const char* name, long fallback) {
+    const std::string pat = std::string("\"") + name + "\": ";
+    const size_t at = line.find(pat);
+    if (at == std::string::npos) return fallback;
+    const char* p = line.c_str() + at + pat.size();
+    if (*p == '"') {
+        ++p;
+        if (!strncmp(p, "persistent", 10)) return 0;
+        if (!strncmp(p, "staged", 6)) return 1;
+        if (!strncmp(p, "streams", 7)) return 2;
+        return fallback;
+    }
+    char* end = nullptr;
+    const long v = strtol(p, &end, 10);
+    return end == p ? fallback : v;
+}
+
+bool b_cache_load(BatchState* b, const char* path, const std::string& key) {
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    std::string line, found;
+    char buf[1024];
+    const std::string kpat = "\"key\": \"" + key + "\"";
+    while (fgets(buf, sizeof(buf), f)) {
+        line = buf;
+        if (line.find(kpat) != std::string::npos) found = line;
+    }
+    fclose(f);
+    if (found.empty()) return false;
+    const long mode = cache_field(found, "mode", -1), order = cache_field(found, "order", -1),
+               variant = cache_field(found, "variant", -1), chunk = cache_field(found, "chunk", -1),
+               shape = cache_field(found, "shape", -1);
+    if (mode < 0 || mode > 2 || order < 0 || order > 1 || variant < 0 || variant > 1 ||
+        (chunk != 1 && chunk != 4 && chunk != 8) || shape < 0 || shape >= B_SHAPES)
+        return false;
+    b->staged = mode == 1;
+    b->streams = mode == 2;
+    b->order = (int)order;
+    b->variant = (int)variant;
+    b->grid = b->max_bpsm[variant] * b->sms;
+    b->chunk = (int)chunk;
+    b->shape = (int)shape;
+    b->from_cache = true;
+    return true;
+}
+
+void b_cache_store(const BatchState* b, const char* path, const std::string& key) {
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "{\"key\": \"%s\", \"mode\": \"%s\", \"order\": %d, \"variant\": %d, \"chunk\": %d, \"shape\": %d, \"ms\": %.4f}\n",
+            key.c_str(), b->streams ? "streams" : b->staged ? "staged" : "persistent", b->order, b->variant, b->chunk,
+            b->shape, b->tuned_ms);
+    fclose(f);
+}
+
 // Time every candidate schedule (stage ordering, register variant with its resident blocks per
 // SM, tasks per dequeue; the staged launches; the per-rig streams) on the real frames and keep the
 // fastest.
@@ -2643,6 +2783,12 @@ stitch_status b_tune(BatchState* b, cudaStream_t s) {
     b->chunk = 4;
     b->staged = false;
     if (mode && strcmp(mode, "off") == 0) return STITCH_OK;
+    // a cached schedule for this batch and GPU (unless STITCH_TUNE forces a mode or a new timing)
+    const char* cache = getenv("STITCH_TUNE_CACHE");
+    const bool use_cache = cache && *cache && (!mode || !*mode || strcmp(mode, "cache") == 0);
+    const bool store_cache = cache && *cache && (use_cache || (mode && strcmp(mode, "full") == 0));
+    const std::string key = cache && *cache ? b_cache_key(b) : std::string();
+    if (use_cache && !key.empty() && b_cache_load(b, cache, key)) return STITCH_OK;
     cudaEvent_t e0, e1;
     STITCH_CUDA_TRY(cudaEventCreate(&e0));
     STITCH_CUDA_TRY(cudaEventCreate(&e1));
@@ -2673,21 +2819,27 @@ stitch_status b_tune(BatchState* b, cudaStream_t s) {
                         b->chunk = chunks[ci];
                     }
                 }
-    // the staged schedule
-    for (int rep = 0; rep < 2; ++rep) {
-        stitch_status st = b_prepare(b, s);
-        if (st != STITCH_OK) return st;
-        cudaEventRecord(e0, s);
-        st = b_launch_staged<T>(b, s);
-        if (st != STITCH_OK) return st;
-        cudaEventRecord(e1, s);
-        STITCH_CUDA_TRY(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep == 1 && ms < best) {
-            best = ms;
-            b->staged = true;
+    // the staged schedule, every tile-shape combination
+    float best_staged = 1e30f;
+    for (int shape = 0; shape < B_SHAPES; ++shape)
+        for (int rep = 0; rep < 2; ++rep) {
+            stitch_status st = b_prepare(b, s);
+            if (st != STITCH_OK) return st;
+            cudaEventRecord(e0, s);
+            st = b_launch_staged<T>(b, shape, s);
+            if (st != STITCH_OK) return st;
+            cudaEventRecord(e1, s);
+            STITCH_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1 && ms < best_staged) {
+                best_staged = ms;
+                b->shape = shape;
+            }
         }
+    if (best_staged < best) {
+        best = best_staged;
+        b->staged = true;
     }
     // the per-rig streams
     for (int rep = 0; rep < 2; ++rep) {
@@ -2710,6 +2862,7 @@ stitch_status b_tune(BatchState* b, cudaStream_t s) {
     }
     if (mode && strcmp(mode, "streams") == 0) b->streams = true;
     b->tuned_ms = best;
+    if (store_cache && !key.empty()) b_cache_store(b, cache, key);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return STITCH_OK;
@@ -2839,10 +2992,40 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
         return st;
     }
     b->ngtasks = (int)gtasks.size();
-    // staged schedule: groups by (type, level) in dependency order
+    // staged schedule: groups by (type, level) in dependency order, for every tile-shape combination;
+    // the 32 x 16 reduce and 32 x 32 coarse tiles are the rigs' own, the 64 x 8 and 64 x 16 ones are
+    // planned here (with their own camera lists)
     {
         int maxL = 0;
         for (int k = 0; k < n; ++k) maxL = std::max(maxL, rigs[k]->geom.levels);
+        std::vector<BTask> wred[MAXL], wco[MAXL];
+        for (int k = 0; k < n; ++k) {
+            stitch_rig* r = rigs[k];
+            FusedState* fs = (FusedState*)r->fused;
+            std::vector<Tile> red[MAXL];
+            std::vector<LevelTile> co[MAXL];
+            std::vector<int> camlist;
+            plan_reduce_tiles(r, RS64x8::TX, RS64x8::TY, red);
+            plan_coarse_tiles(r, fs->h_up, CS64x16::TX, CS64x16::TY, co, camlist);
+            int* d_cl = nullptr;
+            if ((st = b_upload(b, camlist, &d_cl)) != STITCH_OK) {
+                b_free(b);
+                return st;
+            }
+            b->h_rigs[k].camlist_w = d_cl;
+            for (int l = 2; l < MAXL; ++l) {
+                for (size_t i = 0; i < red[l].size(); ++i) {
+                    BTask tk{k, BT_RED, (int)i, l, 0, 0, 0, 0, {}};
+                    memcpy(tk.tile, &red[l][i], sizeof(Tile));
+                    wred[l].push_back(tk);
+                }
+                for (size_t i = 0; i < co[l].size(); ++i) {
+                    BTask tk{k, BT_CO, (int)i, l, 0, 0, 0, 0, {}};
+                    memcpy(tk.tile, &co[l][i], sizeof(LevelTile));
+                    wco[l].push_back(tk);
+                }
+            }
+        }
         std::vector<std::pair<int, int>> order_tl;
         order_tl.push_back({BT_D1, 1});
         for (int l = 2; l < maxL; ++l) order_tl.push_back({BT_RED, l});
@@ -2856,15 +3039,29 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
                 for (const auto& stv : stages[k])
                     for (const BTask& tk : stv)
                         if (tk.type == type && tk.level == level) v.push_back(tk);
-            if (v.empty()) continue;
             StageGroup gr{type, level, (int)v.size(), nullptr};
-            if ((st = b_upload(b, v, &gr.d_tasks)) != STITCH_OK) {
+            if (!v.empty() && (st = b_upload(b, v, &gr.d_tasks)) != STITCH_OK) {
                 b_free(b);
                 return st;
             }
-            b->groups.push_back(gr);
+            StageGroup gw = gr;  // the same group with the batch's wide tiles
+            const std::vector<BTask>* w = type == BT_RED ? &wred[level] : type == BT_CO ? &wco[level] : nullptr;
+            if (w) {
+                gw.count = (int)w->size();
+                gw.d_tasks = nullptr;
+                if (!w->empty() && (st = b_upload(b, *w, &gw.d_tasks)) != STITCH_OK) {
+                    b_free(b);
+                    return st;
+                }
+            }
+            for (int shape = 0; shape < B_SHAPES; ++shape) {
+                const bool wide = (type == BT_RED && b_rs(shape)) || (type == BT_CO && b_cs(shape));
+                const StageGroup& use = wide ? gw : gr;
+                if (use.count) b->groups[shape].push_back(use);
+            }
         }
-        if (!gtasks.empty()) b->groups.push_back({BT_UPG, 0, (int)gtasks.size(), b->d_gtasks});
+        if (!gtasks.empty())
+            for (int shape = 0; shape < B_SHAPES; ++shape) b->groups[shape].push_back({BT_UPG, 0, (int)gtasks.size(), b->d_gtasks});
         const stitch_status as = fp16 ? b_staged_attrs<half4>() : b_staged_attrs<float4>();
         if (as != STITCH_OK) {
             b_free(b);
@@ -2981,7 +3178,9 @@ void fused_batch_destroy(void* bp) {
 stitch_status fused_batch_info(void* bp, int32_t* order, int32_t* grid, int64_t* ntasks) {
     BatchState* b = (BatchState*)bp;
     if (!b) return STITCH_EINVAL;
-    if (order) *order = b->streams ? 0xE : b->staged ? 0xF : (b->order | (b->variant << 4) | (b->chunk << 8));
+    if (order)
+        *order = (b->streams ? 0xE : b->staged ? (0xF | (b->shape << 8)) : (b->order | (b->variant << 4) | (b->chunk << 8))) |
+                 (b->from_cache ? 1 << 24 : 0);
     if (grid) *grid = b->grid;
     if (ntasks) *ntasks = b->ntasks + b->ngtasks;
     return STITCH_OK;

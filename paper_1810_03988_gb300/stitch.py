@@ -244,12 +244,16 @@ def stitch_batch_get_schedule(batch: int) -> dict:
     o, g, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
     _check(load().stitch_batch_get_schedule(batch, ctypes.byref(o), ctypes.byref(g), ctypes.byref(t)),
            "stitch_batch_get_schedule")
-    if o.value == 0xF:
-        return {"mode": "staged", "tasks": t.value}
-    if o.value == 0xE:
-        return {"mode": "streams", "tasks": t.value}
-    return {"mode": "persistent", "order": o.value & 15, "register_variant": (o.value >> 4) & 15,
-            "chunk": o.value >> 8, "grid": g.value, "tasks": t.value}
+    cached = bool(o.value >> 24 & 1)
+    code = o.value & 0xFFFFFF
+    if code & 0xF == 0xF:
+        shape = code >> 8 & 0xF
+        return {"mode": "staged", "reduce_tile": ["32x16", "64x8"][shape & 1],
+                "coarse_tile": ["32x32", "64x16"][shape >> 1], "shape": shape, "tasks": t.value, "cached": cached}
+    if code == 0xE:
+        return {"mode": "streams", "tasks": t.value, "cached": cached}
+    return {"mode": "persistent", "order": code & 15, "register_variant": (code >> 4) & 15, "chunk": code >> 8,
+            "grid": g.value, "tasks": t.value, "cached": cached}
 
 
 def stitch_batch_sync(batch: int) -> None:

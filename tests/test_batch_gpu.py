@@ -164,3 +164,44 @@ def test_batch_rejects_unsupported_mixes():
     assert e.value.status == stitch.STITCH_EUNSUPPORTED
     for r in (a, p, h):
         r.close()
+
+
+def test_tuning_cache_round_trip_and_every_tile_shape(tmp_path, monkeypatch):
+    """STITCH_TUNE_CACHE: the first batch times the candidates and appends its choice; a second batch
+    over the same rigs takes it from the file without timing.  A cache line naming each staged
+    tile-shape combination (reduce 32x16 / 64x8, coarse 32x32 / 64x16) is taken as written, and
+    every combination gives canvases bit-identical to per-rig launches."""
+    import json
+    from paper_1810_03988_gb300 import Batch
+    cache = tmp_path / "tune.jsonl"
+    monkeypatch.setenv("STITCH_TUNE_CACHE", str(cache))
+    monkeypatch.delenv("STITCH_TUNE", raising=False)
+    cfgs = synth.config_batch(5, seed=6, scale=0.25)
+    rigs, frames = _rigs_and_frames(cfgs)
+    ref = _per_rig(rigs, frames)
+    with Batch(rigs) as b:
+        b.stitch(frames)
+        b.sync()
+        first = b.schedule()
+    assert not first["cached"]
+    lines = [json.loads(x) for x in cache.read_text().splitlines()]
+    assert len(lines) == 1 and lines[0]["mode"] == first["mode"]
+    key = lines[0]["key"]
+    with Batch(rigs) as b:
+        got = [o.cpu().numpy() for o in b.stitch(frames)]
+        assert b.schedule()["cached"] and b.schedule()["mode"] == first["mode"]
+    for g, r in zip(got, ref):
+        assert np.array_equal(g, r)
+    for shape in range(4):
+        with open(cache, "a") as f:
+            f.write(json.dumps({"key": key, "mode": "staged", "order": 1, "variant": 1, "chunk": 4, "shape": shape,
+                                "ms": 0.0}) + "\n")
+        with Batch(rigs) as b:
+            outs = b.stitch(frames)
+            b.sync()
+            sch = b.schedule()
+            assert sch["cached"] and sch["mode"] == "staged" and sch["shape"] == shape, sch
+            for o, r in zip(outs, ref):
+                assert np.array_equal(o.cpu().numpy(), r), shape
+    for r in rigs:
+        r.close()
