@@ -219,6 +219,20 @@ typedef struct {
 stitch_status stitch_rig_get_info(const stitch_rig* rig, stitch_rig_info* info);
 
 /*
+ * Debug build only (libstitch_debug.so, compiled with STITCH_DEBUG; the paper has no counterpart):
+ * a memory-safety check standing in for a sanitizer.  That build surrounds every rig allocation
+ * with 256-byte guard bands of a NaN word and compiles index checks into the fused kernels, which
+ * record the first check that fails and skip the access instead of trapping.  This call waits for
+ * the rig's device, then reports the guard words that no longer hold the NaN word
+ * (*damaged_words) and the first failed check as (code << 48 | value) (*failed_check, 0 when none;
+ * reading it resets it).  Codes: 1 a source tap outside the staged footprint, 2 a footprint larger
+ * than the staging capacity, 3 a REDUCE output before its camera's region, 4 a coarse output at a
+ * negative position.
+ * Status: OK, EINVAL, ECUDA; EUNSUPPORTED from the release build.
+ */
+stitch_status stitch_rig_debug_check(stitch_rig* rig, int64_t* damaged_words, int64_t* failed_check);
+
+/*
  * The rig's canvas->camera map of camera `index` as used by every kernel: a[9] receives
  * A = H^-1 / |(H^-1)_33| (row-major, a[8] = +1 or -1); *visible is 0 when the camera's footprint
  * misses the canvas.  The first 8 entries and the camera gain are the stitch_backward params of

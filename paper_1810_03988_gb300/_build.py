@@ -13,6 +13,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libstitch.so")
+# the debug build: guard bands around every rig allocation and index checks in the fused kernels
+DEBUG_LIB = os.path.join(BUILD, "libstitch_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
@@ -34,39 +36,48 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "stitch.h"), __file__]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every csrc/*.cu for sm_103a and link libstitch.so in _build/."""
-    if not force and up_to_date():
+    """Compile every csrc/*.cu for sm_103a and link libstitch.so (release) and libstitch_debug.so
+    (STITCH_DEBUG) in _build/, all translation units of both in parallel."""
+    todo = [(lib, flags) for lib, flags in ((LIB, []), (DEBUG_LIB, ["-DSTITCH_DEBUG"]))
+            if force or not up_to_date(lib)]
+    if not todo:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     exe = nvcc()
     srcs = _sources()
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [exe, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+    def compile_one(job):
+        src, lib, flags = job
+        sub = "debug" if flags else "release"
+        os.makedirs(os.path.join(BUILD, sub), exist_ok=True)
+        obj = os.path.join(BUILD, sub, os.path.basename(src)[:-3] + ".o")
+        cmd = [exe, *ARCH, *NVCC_FLAGS, *flags, "-c", src, "-o", obj]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{res.stderr}")
+            raise RuntimeError(f"nvcc failed on {os.path.basename(src)} ({sub}):\n{res.stderr}")
         if verbose and res.stderr:
             print(res.stderr)
-        return obj
+        return lib, obj
 
-    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = f"{LIB}.{os.getpid()}.tmp"
-    cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError(f"link of libstitch.so failed:\n{res.stderr}")
-    os.replace(tmp, LIB)
+    jobs = [(src, lib, flags) for lib, flags in todo for src in srcs]
+    with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        done = list(ex.map(compile_one, jobs))
+    for lib, _ in todo:
+        objs = [o for l, o in done if l == lib]
+        tmp = f"{lib}.{os.getpid()}.tmp"
+        cmd = [exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"link of {os.path.basename(lib)} failed:\n{res.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

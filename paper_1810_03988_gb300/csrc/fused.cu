@@ -46,6 +46,33 @@
 
 #include "stitch_internal.cuh"
 
+#ifdef STITCH_DEBUG
+// debug build: the first failed index check of this translation unit (code << 48 | value)
+static __device__ unsigned long long g_dcheck;
+__device__ __noinline__ void stitch_dcheck_fail(int code, long long val) {
+    atomicCAS(&g_dcheck, 0ull, ((unsigned long long)code << 48) | ((unsigned long long)val & 0xFFFFFFFFFFFFull));
+}
+#endif
+
+long long fused_debug_take(int device) {
+#ifdef STITCH_DEBUG
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != device) cudaSetDevice(device);
+    unsigned long long v = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_dcheck, sizeof(v)) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_dcheck, &zero, sizeof(zero)) != cudaSuccess) {
+        cudaGetLastError();
+        v = ~0ull;
+    }
+    if (prev >= 0 && prev != device) cudaSetDevice(prev);
+    return (long long)v;
+#else
+    (void)device;
+    return 0;
+#endif
+}
+
 namespace {
 
 // ------------------------------------------------------------------------------------------------
@@ -249,6 +276,7 @@ static_assert(D1_SG * 4 * D1_THREADS == D1_FOOT, "whole groups per thread");
 __device__ __forceinline__ void stage_footprint(uint32_t* __restrict__ foot, const uint8_t* __restrict__ px,
                                                 long long pitch, int W, int fx0, int fy0, int fw, int fh, int t) {
     const int gpr = (fw + 3) >> 2, ng = gpr * fh;  // groups per row = S / 4
+    if (!STITCH_DCHECK(ng <= D1_FOOT / 4, 2, ng)) return;
     if (((reinterpret_cast<uintptr_t>(px) | (uintptr_t)pitch) & 3) != 0) {
         for (int q = t; q < 4 * ng; q += D1_THREADS) {
             const int rr = q / (4 * gpr), u = q - rr * 4 * gpr;
@@ -377,7 +405,10 @@ __device__ __forceinline__ V4 d1_sample(const D1Ctx& x, float2 nuv, float dqc, i
         float fx = f.x, fy = f.y;
         if (MODE == D1M_STAGED) {
             // top-left tap (V0 + floor(rv) - fy0) S + (U0 + floor(ru) - fx0), clamped into the footprint
-            const int idx = min(max((int)(tv * (unsigned)x.S + tu + x.ibase), 0), x.maxidx);
+            // (the planner's footprint holds every tap; the debug build records one that it misses)
+            const int raw = (int)(tv * (unsigned)x.S + tu + x.ibase);
+            (void)STITCH_DCHECK(raw >= 0 && raw <= x.maxidx, 1, raw);
+            const int idx = min(max(raw, 0), x.maxidx);
             const uint32_t* p = x.foot + idx;
             w00 = p[0];
             w01 = p[1];
@@ -750,6 +781,7 @@ __device__ __forceinline__ void reduce_tile(const CamDev* __restrict__ cams, con
         const int jj = q / RS::TX, p = q - jj * RS::TX;
         const int k = tl.x0 + p, j = tl.y0 + jj;
         if (k >= oc.x1 || j >= oc.y1) continue;
+        if (!STITCH_DCHECK(k >= oc.x0 && j >= oc.y0, 3, (long long)k << 24 | j)) continue;
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int n = 0; n < 5; ++n) acc = f4fma(c_w5[n], sh[(2 * jj + n) * RS::TX + p], acc);
@@ -952,6 +984,7 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
     for (int k = 0; k < 4; ++k) {
         const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
         if (x >= nxl || y >= nyl) continue;
+        if (!STITCH_DCHECK(x >= 0 && y >= 0, 4, (long long)x << 24 | y)) continue;
         float4 r = make_float4(e[k].rg.x, e[k].rg.y, e[k].b, 0.f);
         if (den[k] > 1e-12f) {
             const float rd = __frcp_rn(den[k]);  // one reciprocal, three products (within 1 ulp of division)
@@ -1068,9 +1101,9 @@ __global__ void __launch_bounds__(U_THREADS) k_up_simple(const CamDev* __restric
 template <int NC>
 struct UpCams {
     CamRef cr[NC];
-    Rect cv[NC], cz1[NC];
-    int cwh[NC][2];
-    float cscale[NC], cwm[NC], chm[NC];
+    Rect om1[NC], om2[NC];       // the cameras' Omega^1, Omega^2
+    const void* fg1[NC];         // and their G^1, G^2
+    const void* fg2[NC];
 };
 
 // L2 prefetch of an up_full tile's largest inputs: the level-0 slots of its blended cameras
@@ -1111,12 +1144,6 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
     unsigned char* stage = reinterpret_cast<unsigned char*>(r2s + U2_N);
     UpCams<NC>& ucs = *reinterpret_cast<UpCams<NC>*>(stage + 3 * U_TX * U_TY);
     CamRef* cr = ucs.cr;
-    Rect* cv = ucs.cv;
-    Rect* cz1 = ucs.cz1;
-    int (*cwh)[2] = ucs.cwh;
-    float* cscale = ucs.cscale;
-    float* cwm = ucs.cwm;
-    float* chm = ucs.chm;
 
     const int L = g.levels;
     const int nc = min(tl.count, NC);
@@ -1128,14 +1155,12 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
     if (t < nc) {
         cr[t] = refs[tl.first + t];
         const CamDev& c = cams[cr[t].cam];
-        cv[t] = c.V;
-        cz1[t] = L >= 2 ? c.Z[1] : Rect{0, 0, 0, 0};
-        cwh[t][0] = c.W;
-        cwh[t][1] = c.H;
-        cwm[t] = (float)c.W - 0.5f;
-        chm[t] = (float)c.H - 0.5f;
-        cscale[t] = c.gain * (1.0f / 255.0f);
+        ucs.om1[t] = c.Om[1];
+        ucs.om2[t] = c.Om[2];
+        ucs.fg1[t] = c.FG[1];
+        ucs.fg2[t] = c.FG[2];
     }
+    __syncthreads();
     // loads of level 1 and 2 data, all of a thread's loads in flight before the stores
     if (L >= 2) {
         constexpr int NL = (NC * U1_N + U_THREADS - 1) / U_THREADS;
@@ -1146,12 +1171,11 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
             v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (q < nc * U1_N) {
                 const int ci = q / U1_N, qq = q - ci * U1_N;
-                const CamDev& c = cams[refs[tl.first + ci].cam];
                 const int r = qq / U1_X, cc = qq - r * U1_X;
                 const int x = fold101(a1x + cc, g.nx[1]), y = fold101(a1y + r, g.ny[1]);
-                const Rect o1 = c.Om[1];
+                const Rect o1 = ucs.om1[ci];
                 if (o1.contains(x, y))
-                    v[k] = ld(reinterpret_cast<const T*>(c.FG[1]) + (long long)(y - o1.y0) * o1.w() + (x - o1.x0));
+                    v[k] = ld(reinterpret_cast<const T*>(ucs.fg1[ci]) + (long long)(y - o1.y0) * o1.w() + (x - o1.x0));
             }
         }
 #pragma unroll
@@ -1174,10 +1198,9 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
                 if (ci == nc) {
                     v[k] = ld(R2 + (long long)y * g.nx[2] + x);
                 } else {
-                    const CamDev& c = cams[refs[tl.first + ci].cam];
-                    const Rect o2 = c.Om[2];
+                    const Rect o2 = ucs.om2[ci];
                     if (o2.contains(x, y))
-                        v[k] = ld(reinterpret_cast<const T*>(c.FG[2]) + (long long)(y - o2.y0) * o2.w() + (x - o2.x0));
+                        v[k] = ld(reinterpret_cast<const T*>(ucs.fg2[ci]) + (long long)(y - o2.y0) * o2.w() + (x - o2.x0));
                 }
             }
         }
@@ -1618,6 +1641,17 @@ stitch_status upload(stitch_rig* r, const std::vector<V>& v, V** out) {
     return STITCH_OK;
 }
 
+// Canvas positions [lo, hi) that the virtual positions v0 .. v0 + n - 1 fold to on a grid of size m.
+Span folded_span(int v0, int n, int m) {
+    Span s{m, -1};
+    for (int v = v0; v < v0 + n; ++v) {
+        const int f = fold101(v, m);
+        s.lo = std::min(s.lo, f);
+        s.hi = std::max(s.hi, f + 1);
+    }
+    return s;
+}
+
 bool rects_meet(const Rect& a, int x0, int x1, int y0, int y1) {
     return !a.empty() && a.x0 < x1 && a.x1 > x0 && a.y0 < y1 && a.y1 > y0;
 }
@@ -1872,12 +1906,12 @@ template <typename T>
 stitch_status set_smem_attrs() {
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_reduce_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM));
-    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_coarse_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(float4) * CT_SMEM_F4)));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)up_full_smem<2>()));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)up_full_smem<4>()));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_coarse_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float4) * CT_SMEM_F4)));
     return STITCH_OK;
 }
 
@@ -1926,9 +1960,11 @@ stitch_status fused_plan(stitch_rig* r) {
             const int band = 2 * D1_TY;
             for (int y = (o.y0 / band) * band; y < o.y1 || y % band != 0; y += D1_TY)
                 for (int x = (o.x0 / D1_TX) * D1_TX; x < o.x1; x += D1_TX) {
-                    // level-0 bounding box of the tile's inputs
-                    const int bx0 = std::max(2 * x - 2, 0), bx1 = std::min(2 * x - 2 + D1_SX, g.nx[0]);
-                    const int by0 = std::max(2 * y - 2, 0), by1 = std::min(2 * y - 2 + D1_SY, g.ny[0]);
+                    // level-0 bounding box of the tile's inputs: the canvas positions its virtual
+                    // samples fold to (past the right or bottom border they fold back by as much
+                    // as they reach beyond it)
+                    const Span fx = folded_span(2 * x - 2, D1_SX, g.nx[0]), fy = folded_span(2 * y - 2, D1_SY, g.ny[0]);
+                    const int bx0 = fx.lo, bx1 = fx.hi, by0 = fy.lo, by1 = fy.hi;
                     D1Tile t{i, x, y, -1, -1, 0, 0, 0, -1, -1, 0, 0, 0, -1};
                     D1Cams tc{(int)refs.size(), 0, -1, 0};
                     for (int j = 0; j < g.ncam; ++j) {

@@ -216,9 +216,43 @@ bool frames_ok(const stitch_rig* r, const uint8_t* const* frames, const int64_t*
 
 // ------------------------------------------------------------------------------------------------
 
+#ifdef STITCH_DEBUG
+namespace {
+__global__ void k_guard_fill(uint32_t* p, size_t n) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        p[k] = kGuardWord;
+}
+__global__ void k_guard_check(const uint32_t* p, size_t n, unsigned long long* damaged) {
+    unsigned long long bad = 0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        bad += p[k] != kGuardWord;
+    if (bad) atomicAdd(damaged, bad);
+}
+}  // namespace
+#endif
+
+// Device allocation owned by the rig.  The debug build puts a guard band of kGuardBytes before and
+// after it (the allocation rounded up to 16 bytes), filled with a NaN word and checked by
+// stitch_rig_debug_check.
 void* rig_alloc(stitch_rig* r, size_t bytes) {
     void* p = nullptr;
     if (bytes == 0) bytes = 16;
+#ifdef STITCH_DEBUG
+    const size_t body = (bytes + 15) & ~(size_t)15;
+    if (cudaMalloc(&p, body + 2 * kGuardBytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    r->allocs.push_back(p);
+    uint32_t* lo = (uint32_t*)p;
+    uint32_t* hi = (uint32_t*)((char*)p + kGuardBytes + body);
+    for (uint32_t* gp : {lo, hi}) {
+        k_guard_fill<<<1, 64>>>(gp, kGuardBytes / 4);
+        r->guards.push_back({gp, kGuardBytes / 4});
+    }
+    r->scratch_bytes += (long long)bytes;
+    return (char*)p + kGuardBytes;
+#else
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
@@ -226,6 +260,7 @@ void* rig_alloc(stitch_rig* r, size_t bytes) {
     r->allocs.push_back(p);
     r->scratch_bytes += (long long)bytes;
     return p;
+#endif
 }
 
 void prof_mark(stitch_rig* r, const char* name, cudaStream_t s) {
@@ -334,6 +369,30 @@ void stitch_rig_destroy(stitch_rig* r) {
     backward_release(r);
     free_all(r);
     delete r;
+}
+
+stitch_status stitch_rig_debug_check(stitch_rig* r, int64_t* damaged_words, int64_t* failed_check) {
+    if (!r || !damaged_words || !failed_check) return STITCH_EINVAL;
+    *damaged_words = 0;
+    *failed_check = 0;
+#ifdef STITCH_DEBUG
+    DeviceGuard dg(r->device);
+    if (!dg.ok) return STITCH_ECUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return STITCH_ECUDA;
+    unsigned long long* d = nullptr;
+    if (cudaMalloc(&d, sizeof(*d)) != cudaSuccess) return STITCH_ECUDA;
+    unsigned long long h = 0;
+    stitch_status st = cudaMemset(d, 0, sizeof(*d)) == cudaSuccess ? STITCH_OK : STITCH_ECUDA;
+    for (const auto& gd : r->guards)
+        if (st == STITCH_OK) k_guard_check<<<1, 64>>>(gd.first, gd.second, d);
+    if (st == STITCH_OK && cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) st = STITCH_ECUDA;
+    cudaFree(d);
+    *damaged_words = (int64_t)h;
+    *failed_check = fused_debug_take(r->device);
+    return st;
+#else
+    return STITCH_EUNSUPPORTED;
+#endif
 }
 
 stitch_status stitch_rig_get_info(const stitch_rig* r, stitch_rig_info* info) {

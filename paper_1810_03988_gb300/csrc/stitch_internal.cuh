@@ -63,6 +63,24 @@ struct OutDesc {
 };
 
 // ------------------------------------------------------------------------------------------------
+// debug build (STITCH_DEBUG): index checks that record the first failure in a device word of the
+// translation unit and let the caller skip the access (no trap, so the context stays usable), and
+// guard bands around every rig allocation.  Release builds compile the checks to `true`.
+
+#ifdef STITCH_DEBUG
+constexpr bool kStitchDebug = true;
+#define STITCH_DCHECK(cond, code, val) ((cond) ? true : (stitch_dcheck_fail((code), (long long)(val)), false))
+#else
+constexpr bool kStitchDebug = false;
+#define STITCH_DCHECK(cond, code, val) true
+#endif
+
+// Guard band around each rig allocation in the debug build: this many bytes before and after,
+// filled with the quiet-NaN word kGuardWord.
+constexpr size_t kGuardBytes = 256;
+constexpr uint32_t kGuardWord = 0x7FC0DEADu;
+
+// ------------------------------------------------------------------------------------------------
 // small device helpers
 
 // reflect-101 border folding on a grid of n samples: ... 2 1 | 0 1 2 ... n-1 | n-2 n-3 ...
@@ -489,6 +507,7 @@ struct stitch_rig {
     CamDev* dcam = nullptr;
     float4* Bl[MAXL]{};  // plain path: blended band / collapse buffer per level (full level grid)
     std::vector<void*> allocs;
+    std::vector<std::pair<uint32_t*, size_t>> guards;  // debug build: guard bands (words)
     long long scratch_bytes = 0;
     long long roi_pixels = 0;
     int kernels_per_frame = 0;
@@ -541,6 +560,8 @@ void fused_batch_destroy(void* b);
 stitch_status fused_batch_info(void* b, int32_t* order, int32_t* grid, int64_t* ntasks);
 stitch_status fused_batch_wait_test(void* b, int spin_limit, int rig);
 stitch_status fused_batch_status(void* b);
+// debug build: the fused path's first failed index check (code << 48 | value), 0 when none; reset
+long long fused_debug_take(int device);
 
 #define STITCH_CUDA_TRY(expr)                         \
     do {                                              \

@@ -82,6 +82,7 @@ SIGNATURES = {
                                                  ctypes.POINTER(ctypes.c_int64)]),
     "stitch_batch_wait_test": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "stitch_batch_sync": (ctypes.c_int, [_P]),
+    "stitch_rig_debug_check": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "stitch_frames_static": (ctypes.c_int, [ctypes.POINTER(stitch_rig_desc), _P, _P, _P, ctypes.c_int64, _P]),
     "stitch_lorb_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(_P)]),
@@ -110,7 +111,8 @@ def load(build_if_missing: bool = False):
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.LIB
+            # STITCH_LIBRARY selects another build of the library (the debug build)
+            path = os.environ.get("STITCH_LIBRARY") or _build.LIB
             if not os.path.exists(path):
                 if not build_if_missing:
                     raise RuntimeError("libstitch.so is not built: run __graft_entry__.build() (nvcc, sm_103a)")
@@ -402,6 +404,13 @@ class Rig:
                 "tiles": {"zero": i.tiles_zero, "solo": i.tiles_solo, "full2": i.tiles_full2,
                           "full4": i.tiles_full4, "general": i.tiles_general, "down1": i.tiles_down1,
                           "down1_staged": i.tiles_down1_staged, "down1_interior": i.tiles_down1_interior}}
+
+    def debug_check(self) -> dict:
+        """Debug build only: guard words no longer intact and the first failed index check."""
+        dmg, chk = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().stitch_rig_debug_check(self.handle, ctypes.byref(dmg), ctypes.byref(chk)),
+               "stitch_rig_debug_check")
+        return {"damaged_words": dmg.value, "failed_check": chk.value}
 
     def set_profiling(self, enable: bool):
         stitch_rig_set_profiling(self.handle, enable)

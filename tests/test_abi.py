@@ -131,6 +131,7 @@ def test_remaining_entry_points_reject_bad_arguments_without_a_device(lib):
     assert lib.stitch_batch_get_schedule(None, None, None, None) == E
     assert lib.stitch_batch_wait_test(None, 10, 0) == E
     assert lib.stitch_batch_sync(None) == E
+    assert lib.stitch_rig_debug_check(None, None, None) == E
     lib.stitch_batch_destroy(None)
     # L-ORB: sizes below the 37-pixel minimum, point limits, missing outputs
     assert lib.stitch_lorb_create(36, 100, 100, 0, ctypes.byref(out)) == E
