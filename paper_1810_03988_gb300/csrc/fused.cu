@@ -141,6 +141,7 @@ constexpr int D1_INTERIOR = 1;  // inputs solidly inside the camera, no other ca
 constexpr int D1_SOLO_OUT = 2;  // the canvas tile under this tile is SOLO for this camera
 constexpr int D1_G0_OUT = 4;    // the canvas tile under this tile is FULL: write its level-0 samples
 constexpr int D1_NOCLAMP = 8;   // every input maps at least 0.01 px inside the image: no coordinate clamping
+constexpr int D1_G1_OUT = 16;   // some of the tile's level-1 outputs are read: REDUCE and store G^1
 
 // up tile: level-0 origin and the contributing cameras (CamRef range), in camera order.
 struct UpTile {
@@ -633,7 +634,7 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
         } else {
             d1_sweep<T, D1M_FRAME, D1O_ANY, false>(x, vcol, wcol, nuv, dqc, o);
         }
-        if (t < D1_XC * D1_SY) {
+        if (t < D1_XC * D1_SY && (flags & D1_G1_OUT)) {
             const int r = t / D1_XC, k = t - r * D1_XC, ce = k < 2 ? k : D1_SX - 1;
             colterms(ce, nuv, dqc);
             const float a = __ldg(x.wt + r * D1_SX + ce);
@@ -646,6 +647,7 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
             ext[t] = f4_of(s);
         }
     }
+    if (!(flags & D1_G1_OUT)) return;  // no level-1 output of this tile is read
     d1_bar(bar);
     // vertical REDUCE of columns 0, 1 and 66
     if (t < D1_XC * D1_TY) {
@@ -2101,6 +2103,143 @@ stitch_status fused_plan(stitch_rig* r) {
         if (!fs->R[l]) return STITCH_ENOMEM;
     }
     plan_coarse_tiles(r, up, CT_X, CT_Y, co, camlist);
+    // Only part of every camera's Gaussian levels >= 1 is ever read: by the coarse tiles (G^l on the
+    // tile, G^{l+1} on its halo), the FULL and GENERAL canvas tiles (G^1 and G^2 on their halos) and,
+    // through REDUCE, by the needed part of the next level (its 5 x 5 support).  The needed pixels
+    // are marked top-down; REDUCE tiles with no needed output are dropped, down1 tiles store G^1
+    // only where it is needed, and a down1 tile with neither a needed G^1 nor a level-0 output is
+    // dropped.  The rest of the level buffers is never written and never read.
+    if (L >= 2) {
+        std::vector<std::vector<uint8_t>> need[MAXL];  // [level][camera]: a byte per pixel of Omega^l
+        for (int l = 1; l < L; ++l) {
+            need[l].resize(g.ncam);
+            for (int i = 0; i < g.ncam; ++i)
+                if (r->hcam[i].visible) need[l][i].assign((size_t)r->hcam[i].Om[l].area(), 0);
+        }
+        // mark [x0, x1) x [y0, y1) of level l of camera i: the range is taken on the level grid (a
+        // range reaching past a border also covers the positions it folds to), then cut to Omega^l
+        auto fold_range = [](int a0, int a1, int n, int& lo, int& hi) {
+            lo = std::max(a0, 0);
+            hi = std::min(a1, n);
+            if (a0 < 0) hi = std::max(hi, std::min(-a0 + 1, n));
+            if (a1 > n) lo = std::min(lo, std::max(2 * n - 1 - a1, 0));
+        };
+        auto mark = [&](int l, int i, int x0, int x1, int y0, int y1) {
+            const CamDev& c = r->hcam[i];
+            if (!c.visible) return;
+            int ax, bx, ay, by;
+            fold_range(x0, x1, g.nx[l], ax, bx);
+            fold_range(y0, y1, g.ny[l], ay, by);
+            const Rect o = c.Om[l];
+            ax = std::max(ax, o.x0);
+            bx = std::min(bx, o.x1);
+            ay = std::max(ay, o.y0);
+            by = std::min(by, o.y1);
+            for (int y = ay; y < by; ++y)
+                if (bx > ax) memset(need[l][i].data() + (size_t)(y - o.y0) * o.w() + (ax - o.x0), 1, bx - ax);
+        };
+        auto any = [&](int l, int i, int x0, int x1, int y0, int y1) {
+            const Rect o = r->hcam[i].Om[l];
+            x0 = std::max(x0, o.x0);
+            x1 = std::min(x1, o.x1);
+            y0 = std::max(y0, o.y0);
+            y1 = std::min(y1, o.y1);
+            for (int y = y0; y < y1; ++y)
+                if (x1 > x0 && memchr(need[l][i].data() + (size_t)(y - o.y0) * o.w() + (x0 - o.x0), 1, x1 - x0)) return true;
+            return false;
+        };
+        for (int kind : {UP_FULL2, UP_FULL4, UP_GENERAL})
+            for (const UpTile& t : up[kind])
+                for (int k = 0; k < t.count; ++k) {
+                    const int i = refs[t.first + k].cam;
+                    mark(1, i, t.x0 / 2 - 3, t.x0 / 2 + U_TX / 2 + 3, t.y0 / 2 - 3, t.y0 / 2 + U_TY / 2 + 3);
+                    if (L >= 3) mark(2, i, t.x0 / 4 - 3, t.x0 / 4 + U_TX / 4 + 3, t.y0 / 4 - 3, t.y0 / 4 + U_TY / 4 + 3);
+                }
+        // R^l (l >= 2) is needed on the FULL and GENERAL canvas tiles' level-2 halos and, from
+        // level to level, on the EXPAND support of the needed part of the finer level; a coarse
+        // tile computes R^l at a pixel from G^l_i there and from G^{l+1}_i on the support, so G^l_i
+        // is needed wherever R^l is
+        std::vector<uint8_t> needR[MAXL];
+        for (int l = 2; l < L; ++l) needR[l].assign((size_t)g.nx[l] * g.ny[l], 0);
+        auto markR = [&](int l, int x0, int x1, int y0, int y1) {
+            int ax, bx, ay, by;
+            fold_range(x0, x1, g.nx[l], ax, bx);
+            fold_range(y0, y1, g.ny[l], ay, by);
+            for (int y = ay; y < by; ++y)
+                if (bx > ax) memset(needR[l].data() + (size_t)y * g.nx[l] + ax, 1, bx - ax);
+        };
+        if (L >= 3) {
+            for (int kind : {UP_FULL2, UP_FULL4, UP_GENERAL})
+                for (const UpTile& t : up[kind])
+                    markR(2, t.x0 / 4 - 3, t.x0 / 4 + U_TX / 4 + 3, t.y0 / 4 - 3, t.y0 / 4 + U_TY / 4 + 3);
+            for (int l = 2; l + 1 < L; ++l)
+                for (int y = 0; y < g.ny[l]; ++y) {
+                    const uint8_t* row = needR[l].data() + (size_t)y * g.nx[l];
+                    for (int x = 0; x < g.nx[l];) {
+                        if (!row[x]) {
+                            ++x;
+                            continue;
+                        }
+                        int e = x;
+                        while (e < g.nx[l] && row[e]) ++e;
+                        markR(l + 1, x / 2 - 2, (e - 1) / 2 + 3, y / 2 - 2, y / 2 + 3);
+                        x = e;
+                    }
+                }
+            for (int l = 2; l < L; ++l)
+                for (int i = 0; i < g.ncam; ++i) {
+                    const CamDev& c = r->hcam[i];
+                    if (!c.visible) continue;
+                    const Rect o = c.Om[l];
+                    for (int y = o.y0; y < o.y1; ++y) {
+                        const uint8_t* src = needR[l].data() + (size_t)y * g.nx[l] + o.x0;
+                        uint8_t* dst = need[l][i].data() + (size_t)(y - o.y0) * o.w();
+                        for (int x = 0; x < o.w(); ++x) dst[x] |= src[x];
+                    }
+                }
+        }
+        // top-down: the 5 x 5 support of every needed pixel of level l is needed at level l - 1,
+        // row by row over runs of needed pixels
+        for (int l = L - 1; l >= 2; --l)
+            for (int i = 0; i < g.ncam; ++i) {
+                const CamDev& c = r->hcam[i];
+                if (!c.visible) continue;
+                const Rect o = c.Om[l];
+                for (int y = o.y0; y < o.y1; ++y) {
+                    const uint8_t* row = need[l][i].data() + (size_t)(y - o.y0) * o.w();
+                    for (int x = 0; x < o.w();) {
+                        if (!row[x]) {
+                            ++x;
+                            continue;
+                        }
+                        int e = x;
+                        while (e < o.w() && row[e]) ++e;
+                        mark(l - 1, i, 2 * (o.x0 + x) - 2, 2 * (o.x0 + e - 1) + 3, 2 * y - 2, 2 * y + 3);
+                        x = e;
+                    }
+                }
+            }
+        for (int l = 2; l < L; ++l) {
+            std::vector<Tile> keep;
+            for (const Tile& t : red[l])
+                if (any(l, t.cam, t.x0, t.x0 + RT_X, t.y0, t.y0 + RT_Y)) keep.push_back(t);
+            red[l].swap(keep);
+        }
+        // down1: G^1 only where needed; drop tiles without any output (renumbering weight tables)
+        std::vector<D1Tile> kd;
+        std::vector<D1Cams> kc;
+        fs->n_wtab = 0;
+        for (size_t k = 0; k < d1.size(); ++k) {
+            D1Tile t = d1[k];
+            if (any(1, t.cam, t.k0, t.k0 + D1_TX, t.j0, t.j0 + D1_TY)) t.flags |= D1_G1_OUT;
+            if (!(t.flags & (D1_G1_OUT | D1_SOLO_OUT | D1_G0_OUT))) continue;
+            if (t.wtab >= 0) t.wtab = t.wsel = fs->n_wtab++;
+            kd.push_back(t);
+            kc.push_back(d1c[k]);
+        }
+        d1.swap(kd);
+        d1c.swap(kc);
+    }
     // L2 prefetch chain: blocks start in index order as resident ones finish, so tile i + K
     // (K = resident blocks of k_down1 on the device) starts about when tile i ends
     {
@@ -2120,8 +2259,11 @@ stitch_status fused_plan(stitch_rig* r) {
         }
     }
     // INTERIOR tiles sample with the table of ones, after the tiles' own tables
-    for (D1Tile& t : d1)
+    fs->n_staged = 0;
+    for (D1Tile& t : d1) {
         if (t.wsel < 0) t.wsel = fs->n_wtab;
+        fs->n_staged += t.fwh != 0;
+    }
     fs->h_d1 = d1;
     for (int l = 0; l < MAXL; ++l) {
         fs->h_red[l] = red[l];
