@@ -835,26 +835,6 @@ __device__ __forceinline__ void expand_quad(const float4* __restrict__ a, int ld
     e[3] = odd(ho[1], ho[2]);
 }
 
-// The same EXPAND channel by channel (the up_full kernel: fewer registers than the pairs).
-__device__ __forceinline__ void expand_quad3(const float4* __restrict__ a, int ld, int ox, int oy, float3 e[4]) {
-    float3 he[3], ho[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        const float4 c0 = a[(oy + r) * ld + ox], c1 = a[(oy + r) * ld + ox + 1], c2 = a[(oy + r) * ld + ox + 2];
-        he[r] = make_float3(fmaf(0.75f, c1.x, 0.125f * (c0.x + c2.x)), fmaf(0.75f, c1.y, 0.125f * (c0.y + c2.y)),
-                            fmaf(0.75f, c1.z, 0.125f * (c0.z + c2.z)));
-        ho[r] = make_float3(0.5f * (c1.x + c2.x), 0.5f * (c1.y + c2.y), 0.5f * (c1.z + c2.z));
-    }
-    e[0] = make_float3(fmaf(0.75f, he[1].x, 0.125f * (he[0].x + he[2].x)),
-                       fmaf(0.75f, he[1].y, 0.125f * (he[0].y + he[2].y)),
-                       fmaf(0.75f, he[1].z, 0.125f * (he[0].z + he[2].z)));
-    e[1] = make_float3(fmaf(0.75f, ho[1].x, 0.125f * (ho[0].x + ho[2].x)),
-                       fmaf(0.75f, ho[1].y, 0.125f * (ho[0].y + ho[2].y)),
-                       fmaf(0.75f, ho[1].z, 0.125f * (ho[0].z + ho[2].z)));
-    e[2] = make_float3(0.5f * (he[1].x + he[2].x), 0.5f * (he[1].y + he[2].y), 0.5f * (he[1].z + he[2].z));
-    e[3] = make_float3(0.5f * (ho[1].x + ho[2].x), 0.5f * (ho[1].y + ho[2].y), 0.5f * (ho[1].z + ho[2].z));
-}
-
 // Tiled coarse level: R^l on a tile of level l (l >= 2), one 2 x 2 quad per thread, cameras in
 // chunks of 2.  Virtual level-(l+1) region: origin (X0/2 - 2, Y0/2 - 2), TX/2 + 4 by TY/2 + 4.
 // The tile shape is a template parameter (the batched schedule's tuner picks one per batch); the
@@ -1239,7 +1219,13 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
         for (int c = 0; c < nc; ++c) {
             float3 e[4] = {make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f), make_float3(0.f, 0.f, 0.f),
                            make_float3(0.f, 0.f, 0.f)};
-            if (L >= 3) expand_quad3(d2 + c * U2_N, U2_X, qx, qy, e);
+            if (L >= 3) {
+                V3 e2[4];
+                expand_quad(d2 + c * U2_N, U2_X, qx, qy, e2);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) e[k] = make_float3(e2[k].rg.x, e2[k].rg.y, e2[k].b);
+            }
+
             // outside the camera's Z^1 its weight pyramid is exactly 0, so those terms add nothing
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -1263,11 +1249,11 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
             }
         }
         if (need_plain && L >= 3) {
-            float3 e[4];
-            expand_quad3(r2s, U2_X, qx, qy, e);
+            V3 e[4];
+            expand_quad(r2s, U2_X, qx, qy, e);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (!(den[k] > 1e-12f)) r1[k] = e[k];
+                if (!(den[k] > 1e-12f)) r1[k] = make_float3(e[k].rg.x, e[k].rg.y, e[k].b);
         }
         for (int c = 0; c < nc; ++c) {
 #pragma unroll
@@ -1308,7 +1294,12 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
             const int slot = cr[c].g0;
             if (slot < 0) continue;
             float3 e[4];
-            expand_quad3(d1 + c * U1_N, U1_X, qx + 1, qy + 1, e);
+            {
+                V3 e2[4];
+                expand_quad(d1 + c * U1_N, U1_X, qx + 1, qy + 1, e2);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) e[k] = make_float3(e2[k].rg.x, e2[k].rg.y, e2[k].b);
+            }
             const T* gq = g0buf + (long long)slot * (U_TX * U_TY) + (2 * qy) * U_TX + 2 * qx;
             float4 gv[4];
 #pragma unroll
@@ -1345,13 +1336,19 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
     }
 }
 
+// Blocks n .. n + n_simple - 1 take the ZERO (and fallback SOLO) canvas tiles `simple`, so that they
+// need no launch of their own.
 template <typename T, int NC>
 __global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
                                                         OutDesc od, const T* __restrict__ R2,
                                                         const UpTile* __restrict__ tiles,
                                                         const CamRef* __restrict__ refs, const T* __restrict__ g0buf,
-                                                        int n, int wave) {
+                                                        int n, int wave, const UpTile* __restrict__ simple) {
     extern __shared__ float4 usm[];
+    if ((int)blockIdx.x >= n) {
+        up_simple_tile(cams, g, fp, od, simple[blockIdx.x - n], refs, reinterpret_cast<unsigned char*>(usm));
+        return;
+    }
     const int nb = blockIdx.x + wave;  // prefetched: the tile one resident wave later (see k_reduce_t)
     up_full_tile<T, NC>(cams, g, fp, od, R2, tiles[blockIdx.x], refs, g0buf, usm, nb < n ? tiles + nb : nullptr);
 }
@@ -1878,23 +1875,24 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
                                                    fs->camlist);
     }
     const T* R2 = L >= 3 ? (const T*)fs->R[2] : nullptr;
-    if (fs->n_up[UP_SIMPLE]) {
+    // the ZERO canvas tiles ride along with the first up_full launch (or get their own)
+    const int ns = fs->n_up[UP_SIMPLE];
+    if (ns && !fs->n_up[UP_FULL2] && !fs->n_up[UP_FULL4]) {
         prof_mark(r, "fused_up_simple", s);
-        k_up_simple<<<fs->n_up[UP_SIMPLE], U_THREADS, 0, s>>>(r->dcam, g, fp, od, fs->up_tiles[UP_SIMPLE], fs->refs);
+        k_up_simple<<<ns, U_THREADS, 0, s>>>(r->dcam, g, fp, od, fs->up_tiles[UP_SIMPLE], fs->refs);
     }
     if (fs->n_up[UP_FULL2]) {
         prof_mark(r, "fused_up_full", s);
-        k_up_full<T, 2><<<fs->n_up[UP_FULL2], U_THREADS, up_full_smem<2>(), s>>>(r->dcam, g, fp, od, R2,
-                                                                               fs->up_tiles[UP_FULL2], fs->refs,
-                                                                               (const T*)fs->g0buf,
-                                                                               fs->n_up[UP_FULL2], fs->wave_up2);
+        k_up_full<T, 2><<<fs->n_up[UP_FULL2] + ns, U_THREADS, up_full_smem<2>(), s>>>(
+            r->dcam, g, fp, od, R2, fs->up_tiles[UP_FULL2], fs->refs, (const T*)fs->g0buf, fs->n_up[UP_FULL2],
+            fs->wave_up2, fs->up_tiles[UP_SIMPLE]);
     }
     if (fs->n_up[UP_FULL4]) {
+        const int extra = fs->n_up[UP_FULL2] ? 0 : ns;
         prof_mark(r, "fused_up_full4", s);
-        k_up_full<T, 4><<<fs->n_up[UP_FULL4], U_THREADS, up_full_smem<4>(), s>>>(r->dcam, g, fp, od, R2,
-                                                                               fs->up_tiles[UP_FULL4], fs->refs,
-                                                                               (const T*)fs->g0buf,
-                                                                               fs->n_up[UP_FULL4], fs->wave_up4);
+        k_up_full<T, 4><<<fs->n_up[UP_FULL4] + extra, U_THREADS, up_full_smem<4>(), s>>>(
+            r->dcam, g, fp, od, R2, fs->up_tiles[UP_FULL4], fs->refs, (const T*)fs->g0buf, fs->n_up[UP_FULL4],
+            fs->wave_up4, fs->up_tiles[UP_SIMPLE]);
     }
     if (fs->n_up[UP_GENERAL]) {
         prof_mark(r, "fused_up_general", s);
@@ -2308,6 +2306,7 @@ stitch_status fused_plan(stitch_rig* r) {
     if (L >= 2 && fs->n_d1 > 0) kernels += 1;
     for (int l = 2; l < L; ++l) kernels += (fs->n_red[l] > 0) + (fs->n_co[l] > 0);
     for (int k = 0; k < UP_KINDS; ++k) kernels += fs->n_up[k] > 0;
+    if (fs->n_up[UP_SIMPLE] && (fs->n_up[UP_FULL2] || fs->n_up[UP_FULL4])) kernels -= 1;  // rides along
     r->kernels_per_frame = kernels;
     st = fs->fp16 ? set_smem_attrs<half4>() : set_smem_attrs<float4>();
     if (st != STITCH_OK) return st;
