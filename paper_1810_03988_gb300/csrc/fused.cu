@@ -703,8 +703,10 @@ struct RShape {
 };
 using RS32x16 = RShape<32, 16>;
 using RS64x8 = RShape<64, 8>;
-constexpr int RT_X = RS32x16::TX, RT_Y = RS32x16::TY;
-constexpr size_t RT_SMEM = RS32x16::SMEM;
+using RSRig = RS32x16;  // the shape of a rig's own REDUCE tiles (the single-rig path, the persistent batch)
+using RSAlt = RShape<RSRig::TY * 4, RSRig::TY / 2>;  // the batch tuner's other shape (64 x 8)
+constexpr int RT_X = RSRig::TX, RT_Y = RSRig::TY;
+constexpr size_t RT_SMEM = RSRig::SMEM;
 
 // L2 prefetch of a reduce tile's input rows (the part inside Omega^l; rows that fold at the canvas
 // border are left to the loads), 16 threads per row, one 128-byte line each.
@@ -798,7 +800,7 @@ __global__ void __launch_bounds__(256) k_reduce_t(const CamDev* __restrict__ cam
                                                    const Tile* __restrict__ tiles, int n, int wave) {
     extern __shared__ float4 smem[];
     const int nb = blockIdx.x + wave;
-    reduce_tile<T>(cams, g, l, tiles[blockIdx.x], smem, nb < n ? tiles + nb : nullptr);
+    reduce_tile<T, RSRig>(cams, g, l, tiles[blockIdx.x], smem, nb < n ? tiles + nb : nullptr);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -851,8 +853,10 @@ struct CShape {
 };
 using CS32x32 = CShape<32, 32>;
 using CS64x16 = CShape<64, 16>;
-constexpr int CT_X = CS32x32::TX, CT_Y = CS32x32::TY;
-constexpr int CT_SMEM_F4 = CS32x32::SMEM_F4;
+using CSRig = CS32x32;  // the shape of a rig's own coarse tiles (the single-rig path, the persistent batch)
+using CSAlt = CShape<CSRig::TX * 2, CSRig::TY / 2>;  // the batch tuner's other shape (64 x 16)
+constexpr int CT_X = CSRig::TX, CT_Y = CSRig::TY;
+constexpr int CT_SMEM_F4 = CSRig::SMEM_F4;
 
 struct LevelTile {
     int x0, y0, first, count;  // level origin, range of camera indices in the list
@@ -983,7 +987,7 @@ __global__ void __launch_bounds__(256, 3) k_coarse_t(const CamDev* __restrict__ 
                                                    const LevelTile* __restrict__ tiles,
                                                    const int* __restrict__ camlist) {
     extern __shared__ float4 smem[];
-    coarse_tile<T>(cams, g, l, Rl, Rc, tiles[blockIdx.x], camlist, smem);
+    coarse_tile<T, CSRig>(cams, g, l, Rl, Rc, tiles[blockIdx.x], camlist, smem);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -2495,10 +2499,10 @@ __global__ void __launch_bounds__(B_THREADS, MINB) k_batch(const BatchRigDev* __
                     break;
                 }
                 case BT_RED:
-                    reduce_tile<T>(rg.cams, rg.g, tk.level - 1, task_tile<Tile>(tk), smem);
+                    reduce_tile<T, RSRig>(rg.cams, rg.g, tk.level - 1, task_tile<Tile>(tk), smem);
                     break;
                 case BT_CO:
-                    coarse_tile<T>(rg.cams, rg.g, tk.level, (T*)rg.R[tk.level],
+                    coarse_tile<T, CSRig>(rg.cams, rg.g, tk.level, (T*)rg.R[tk.level],
                                    tk.level + 1 < rg.g.levels ? (const T*)rg.R[tk.level + 1] : nullptr,
                                    task_tile<LevelTile>(tk), rg.camlist, smem);
                     break;
@@ -2573,7 +2577,7 @@ __global__ void __launch_bounds__(256, 3) k_mr_coarse(const BatchRigDev* __restr
     const BatchRigDev& rg = rigs[tk.rig];
     coarse_tile<T, CS>(rg.cams, rg.g, tk.level, (T*)rg.R[tk.level],
                        tk.level + 1 < rg.g.levels ? (const T*)rg.R[tk.level + 1] : nullptr, task_tile<LevelTile>(tk),
-                       std::is_same<CS, CS32x32>::value ? rg.camlist : rg.camlist_w, smem);
+                       std::is_same<CS, CSRig>::value ? rg.camlist : rg.camlist_w, smem);
 }
 
 __global__ void __launch_bounds__(U_THREADS) k_mr_up_simple(const BatchRigDev* __restrict__ rigs,
@@ -2704,14 +2708,14 @@ stitch_status b_launch_staged(BatchState* b, int shape, cudaStream_t s) {
         switch (gr.type) {
             case BT_D1: k_mr_down1<T><<<gr.count, D1_THREADS, D1_SMEM, s>>>(b->d_rigs, gr.d_tasks); break;
             case BT_RED:
-                if (b_rs(shape)) k_mr_reduce<T, RS64x8><<<gr.count, 256, RS64x8::SMEM, s>>>(b->d_rigs, gr.d_tasks);
-                else k_mr_reduce<T, RS32x16><<<gr.count, 256, RS32x16::SMEM, s>>>(b->d_rigs, gr.d_tasks);
+                if (b_rs(shape)) k_mr_reduce<T, RSAlt><<<gr.count, 256, RSAlt::SMEM, s>>>(b->d_rigs, gr.d_tasks);
+                else k_mr_reduce<T, RSRig><<<gr.count, 256, RSRig::SMEM, s>>>(b->d_rigs, gr.d_tasks);
                 break;
             case BT_CO:
                 if (b_cs(shape))
-                    k_mr_coarse<T, CS64x16><<<gr.count, 256, sizeof(float4) * CS64x16::SMEM_F4, s>>>(b->d_rigs, gr.d_tasks);
+                    k_mr_coarse<T, CSAlt><<<gr.count, 256, sizeof(float4) * CSAlt::SMEM_F4, s>>>(b->d_rigs, gr.d_tasks);
                 else
-                    k_mr_coarse<T, CS32x32><<<gr.count, 256, sizeof(float4) * CS32x32::SMEM_F4, s>>>(b->d_rigs, gr.d_tasks);
+                    k_mr_coarse<T, CSRig><<<gr.count, 256, sizeof(float4) * CSRig::SMEM_F4, s>>>(b->d_rigs, gr.d_tasks);
                 break;
             case BT_UPS: k_mr_up_simple<<<gr.count, U_THREADS, 0, s>>>(b->d_rigs, gr.d_tasks); break;
             case BT_UPF2: k_mr_up_full<T, 2><<<gr.count, U_THREADS, up_full_smem<2>(), s>>>(b->d_rigs, gr.d_tasks); break;
@@ -2726,14 +2730,14 @@ stitch_status b_launch_staged(BatchState* b, int shape, cudaStream_t s) {
 template <typename T>
 stitch_status b_staged_attrs() {
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
-    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce<T, RS32x16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)RS32x16::SMEM));
-    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce<T, RS64x8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)RS64x8::SMEM));
-    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_coarse<T, CS32x32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(float4) * CS32x32::SMEM_F4)));
-    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_coarse<T, CS64x16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(float4) * CS64x16::SMEM_F4)));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce<T, RSRig>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)RSRig::SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce<T, RSAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)RSAlt::SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_coarse<T, CSRig>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float4) * CSRig::SMEM_F4)));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_coarse<T, CSAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float4) * CSAlt::SMEM_F4)));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_up_full<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)up_full_smem<2>()));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_up_full<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -3182,8 +3186,8 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
             std::vector<Tile> red[MAXL];
             std::vector<LevelTile> co[MAXL];
             std::vector<int> camlist;
-            plan_reduce_tiles(r, RS64x8::TX, RS64x8::TY, red);
-            plan_coarse_tiles(r, fs->h_up, CS64x16::TX, CS64x16::TY, co, camlist);
+            plan_reduce_tiles(r, RSAlt::TX, RSAlt::TY, red);
+            plan_coarse_tiles(r, fs->h_up, CSAlt::TX, CSAlt::TY, co, camlist);
             int* d_cl = nullptr;
             if ((st = b_upload(b, camlist, &d_cl)) != STITCH_OK) {
                 b_free(b);
