@@ -471,9 +471,10 @@ __device__ __forceinline__ void d1_put(const D1Out<T>& o, int dy, V4 s) {
 
 // The sweep of one thread over the 19 rows of its virtual column c: the vertical REDUCE in
 // registers (output row jj takes rows 2 jj .. 2 jj + 4 in order), level-0 outputs on the fly.  Rows
-// go in pairs (2m, 2m + 1) with two running sums: on entry to pair m, C holds output row m - 2
-// (taps 0..3 applied) and B row m - 1 (taps 0, 1); row 2m completes C (stored from m = 2 on), moves
-// B on by tap 2 into C and starts row m in B; row 2m + 1 adds tap 3 to C and tap 1 to B.
+// go in pairs (2m, 2m + 1), m = 0 .. 8, with two running sums: on entry to pair m, C holds output
+// row m - 2 (taps 0..3 applied) and B row m - 1 (taps 0, 1); row 2m completes C (stored from m = 2
+// on), moves B on by tap 2 into C and starts row m in B; row 2m + 1 adds tap 3 to C and tap 1 to B.
+// Row 18 completes output row 7.
 template <typename T, int MODE, int OUTK, bool ONES>
 __device__ __forceinline__ void d1_sweep(const D1Ctx& x, float4* __restrict__ vcol, const float* __restrict__ wcol,
                                          float2 nuv, float dqc, const D1Out<T>& o) {
@@ -481,24 +482,24 @@ __device__ __forceinline__ void d1_sweep(const D1Ctx& x, float4* __restrict__ vc
     // weights of INTERIOR tiles are all 1; the others are loaded one row pair ahead
     float we = ONES ? 1.0f : __ldg(wcol), wo = ONES ? 1.0f : __ldg(wcol + D1_SX);
 #pragma unroll 1
-    for (int m = 0; m <= D1_TY + 1; ++m) {
-        const bool put = m >= 1 && m <= D1_TY;
+    for (int m = 0; m <= D1_TY; ++m) {
         const float ae = we, ao = wo;
-        if (!ONES && m <= D1_TY) {
+        if (!ONES) {
             we = __ldg(wcol + (2 * m + 2) * D1_SX);
-            wo = m < D1_TY ? __ldg(wcol + (2 * m + 3) * D1_SX) : 0.f;
+            wo = __ldg(wcol + min(2 * m + 3, D1_SY - 1) * D1_SX);
         }
         const V4 se = d1_sample<MODE>(x, nuv, dqc, 2 * m, ae);
-        if (put) d1_put<T, OUTK>(o, 2 * m - 2, se);
+        const V4 so = d1_sample<MODE>(x, nuv, dqc, 2 * m + 1, ao);
+        if (m >= 1) d1_put<T, OUTK>(o, 2 * m - 2, se);
         if (m >= 2) vcol[(m - 2) * D1_VROW] = f4_of(v4_fma(d1_w(4), se, C));
         C = v4_fma(d1_w(2), se, B);
         B = v4_mul(d1_w(0), se);
-        if (m > D1_TY) break;
-        const V4 so = d1_sample<MODE>(x, nuv, dqc, 2 * m + 1, ao);
-        if (put) d1_put<T, OUTK>(o, 2 * m - 1, so);
+        if (m >= 1) d1_put<T, OUTK>(o, 2 * m - 1, so);
         C = v4_fma(d1_w(3), so, C);
         B = v4_fma(d1_w(1), so, B);
     }
+    const V4 se = d1_sample<MODE>(x, nuv, dqc, 2 * D1_TY + 2, we);
+    vcol[(D1_TY - 1) * D1_VROW] = f4_of(v4_fma(d1_w(4), se, C));
 }
 
 // Barrier of the threads working on one down1 tile: the whole block (id 0), or a named barrier of
@@ -1294,29 +1295,35 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
             num[k] = make_float3(0.f, 0.f, 0.f);
             den[k] = 0.f;
         }
-        for (int c = 0; c < nc; ++c) {
-            const int slot = cr[c].g0;
-            if (slot < 0) continue;
-            float3 e[4];
-            {
-                V3 e2[4];
-                expand_quad(d1 + c * U1_N, U1_X, qx + 1, qy + 1, e2);
+        // the level-0 samples of every blended camera (FP32 slots of two cameras at most: all their
+        // loads in flight at once), or of one camera after another
+        constexpr int NB = NC <= 2 && std::is_same<T, float4>::value ? NC : 1;
+        for (int c0 = 0; c0 < nc; c0 += NB) {
+            float4 gv[NB][4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) e[k] = make_float3(e2[k].rg.x, e2[k].rg.y, e2[k].b);
+            for (int b = 0; b < NB; ++b) {
+                const int slot = c0 + b < nc ? cr[c0 + b].g0 : -1;
+                const T* gq = g0buf + (long long)max(slot, 0) * (U_TX * U_TY) + (2 * qy) * U_TX + 2 * qx;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    gv[b][k] = slot >= 0 ? ld(gq + (k >> 1) * U_TX + (k & 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            const T* gq = g0buf + (long long)slot * (U_TX * U_TY) + (2 * qy) * U_TX + 2 * qx;
-            float4 gv[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) gv[k] = ld(gq + (k >> 1) * U_TX + (k & 1));
-            // a camera's weight is 0 (and its sample 0) where it does not cover the pixel: the
-            // terms add nothing there, so no test is needed
+            for (int b = 0; b < NB; ++b) {
+                const int c = c0 + b;
+                if (c >= nc || cr[c].g0 < 0) continue;
+                V3 e[4];
+                expand_quad(d1 + c * U1_N, U1_X, qx + 1, qy + 1, e);
+                // a camera's weight is 0 (and its sample 0) where it does not cover the pixel: the
+                // terms add nothing there, so no test is needed
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float a = gv[k].w;
-                num[k].x = fmaf(a, gv[k].x + e[k].x, num[k].x);
-                num[k].y = fmaf(a, gv[k].y + e[k].y, num[k].y);
-                num[k].z = fmaf(a, gv[k].z + e[k].z, num[k].z);
-                den[k] += a;
+                for (int k = 0; k < 4; ++k) {
+                    const float a = gv[b][k].w;
+                    num[k].x = fmaf(a, gv[b][k].x + e[k].rg.x, num[k].x);
+                    num[k].y = fmaf(a, gv[b][k].y + e[k].rg.y, num[k].y);
+                    num[k].z = fmaf(a, gv[b][k].z + e[k].b, num[k].z);
+                    den[k] += a;
+                }
             }
         }
 #pragma unroll
