@@ -192,6 +192,13 @@ constexpr int D1_NSAMP = D1_SX * D1_SY;                      // level-0 samples 
 // a FULL canvas tile's level-0 slot (64 x 32 samples per blended camera), written by the camera's
 // two down1 tiles over it (rows 0..15 and 16..31)
 constexpr int D1_SLOT = (2 * D1_TX) * (4 * D1_TY);
+// A slot element: the sample's R, G, B and normalised weight a as 16-bit codes, R | G << 16 and
+// B | a << 16.  Colours go in steps of 1/256 of an 8-bit level (a bilinear sample of 8-bit texels
+// rounds to within 1/512 of a level), the weight in steps of 1/65535; the blend divides by the sum
+// of the weights, so their codes enter it as they are.  Both band precisions use this format.
+using Slot = uint2;
+constexpr float SLOT_RGB = 256.0f;  // codes per 8-bit level
+constexpr float SLOT_A = 65535.0f;  // codes per unit weight
 // Footprint capacity in texels (one 32-bit word each; rows padded to a multiple of 4 texels).
 constexpr int D1_FOOT = 2048;
 // Vertically reduced values: per level-1 row, the even columns at slots 0..33 and the odd columns
@@ -434,6 +441,26 @@ __device__ __forceinline__ V4 d1_sample(const D1Ctx& x, float2 nuv, float dqc, i
     return s;
 }
 
+// The slot element of a sample whose colours are 8-bit levels times `scale`; enc = SLOT_RGB / scale
+// (0 for scale 0).  Each code is the low half of 2^23 + code, the result of one rounded addition.
+__device__ __forceinline__ Slot slot_encode(V4 s, float enc) {
+    const float2 rg = f2fma(s.a, f2(enc), f2(8388608.0f));
+    const float2 ba = f2fma(s.b, make_float2(enc, SLOT_A), f2(8388608.0f));
+    return make_uint2(__byte_perm(__float_as_uint(rg.x), __float_as_uint(rg.y), 0x5410),
+                      __byte_perm(__float_as_uint(ba.x), __float_as_uint(ba.y), 0x5410));
+}
+
+// (R, G, B) of a slot element in scaled units (dsc = scale / SLOT_RGB) and its weight code.
+__device__ __forceinline__ float4 slot_decode(Slot w, float dsc) {
+    constexpr float K23 = 8388608.0f;
+    const float2 c = make_float2(__uint_as_float(__byte_perm(w.x, 0x4B000000u, 0x7610)),
+                                 __uint_as_float(__byte_perm(w.x, 0x4B000000u, 0x7632)));
+    const float2 rg = f2mul(f2sub(c, f2(K23)), f2(dsc));
+    const float b = (__uint_as_float(__byte_perm(w.y, 0x4B000000u, 0x7610)) - K23) * dsc;
+    const float a = __uint_as_float(__byte_perm(w.y, 0x4B000000u, 0x7632)) - K23;
+    return make_float4(rg.x, rg.y, b, a);
+}
+
 // Where a tile's level-0 samples go besides the pyramid: nowhere, the FULL canvas tile's level-0
 // slot, or the SOLO canvas tile's pixels (8-bit or float).  The sweep thread of virtual column c
 // writes the sample of virtual row r at canvas (X0 + c - 2, Y0 + r - 2) for 2 <= r < 18.
@@ -445,6 +472,7 @@ struct D1Out {
     long long step;  // bytes from one row to the next
     int rows;        // rows r - 2 < rows exist (canvas bottom; 0 right of the canvas)
     int kind;
+    float enc;       // slot codes per scaled unit (slot_encode)
 };
 
 // OUTK: the output kind fixed at compile time, or D1O_ANY to take o.kind.  Slot rows always exist.
@@ -455,7 +483,7 @@ __device__ __forceinline__ void d1_put(const D1Out<T>& o, int dy, V4 s) {
     if (kind != D1O_SLOT && dy >= o.rows) return;
     char* q = o.p + dy * o.step;
     if (kind == D1O_SLOT) {
-        st(reinterpret_cast<T*>(q), f4_of(s));
+        *reinterpret_cast<Slot*>(q) = slot_encode(s, o.enc);
     } else if (kind == D1O_U8) {
         unsigned char* b = reinterpret_cast<unsigned char*>(q);
         b[0] = quantize_u8(__saturatef(s.a.x));
@@ -514,7 +542,7 @@ template <typename T>
 __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
                                            const OutDesc& od, const D1Tile& tl, const CamRef* __restrict__ refs,
                                            const float* __restrict__ d1w, const float4* __restrict__ d1cols,
-                                           T* __restrict__ g0buf, float4* smem, int t = threadIdx.x, int bar = 0) {
+                                           Slot* __restrict__ g0buf, float4* smem, int t = threadIdx.x, int bar = 0) {
     uint32_t* foot = reinterpret_cast<uint32_t*>(smem);
     float4* vres = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + D1_SM_FOOT);
     float4* ext = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + D1_SM_FOOT + D1_SM_V);  // [19][3]
@@ -599,12 +627,13 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
         float2 nuv;
         float dqc;
         colterms(c, nuv, dqc);
-        D1Out<T> o{nullptr, 0, 0, D1O_NONE};
+        D1Out<T> o{nullptr, 0, 0, D1O_NONE, 0.f};
         if (flags & D1_G0_OUT) {
             o.kind = D1O_SLOT;
             o.p = reinterpret_cast<char*>(g0buf + (long long)tl.g0 * D1_SLOT + ((j0 / D1_TY) & 1) * (2 * D1_TY) * (2 * D1_TX) + t);
-            o.step = (long long)sizeof(T) * (2 * D1_TX);
+            o.step = (long long)sizeof(Slot) * (2 * D1_TX);
             o.rows = 2 * D1_TY;
+            o.enc = x.scale != 0.f ? SLOT_RGB / x.scale : 0.f;
         } else if (flags & D1_SOLO_OUT) {
             o.kind = od.is_float ? D1O_F32 : D1O_U8;
             const int xo = X0 + t;
@@ -683,7 +712,7 @@ template <typename T>
 __global__ void __launch_bounds__(D1_THREADS, D1_BLOCKS_PER_SM) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
                                                        OutDesc od, const D1Tile* __restrict__ tiles,
                                                        const CamRef* __restrict__ refs, const float* __restrict__ d1w,
-                                                       const float4* __restrict__ d1cols, T* __restrict__ g0buf) {
+                                                       const float4* __restrict__ d1cols, Slot* __restrict__ g0buf) {
     extern __shared__ float4 smem[];
     down1_tile<T>(cams, g, fp, od, tiles[blockIdx.x], refs, d1w, d1cols, g0buf, smem);
 }
@@ -1091,20 +1120,21 @@ struct UpCams {
     Rect om1[NC], om2[NC];       // the cameras' Omega^1, Omega^2
     const void* fg1[NC];         // and their G^1, G^2
     const void* fg2[NC];
+    float dsc[NC];               // scale / SLOT_RGB: slot codes to scaled units
 };
 
 // L2 prefetch of an up_full tile's largest inputs: the level-0 slots of its blended cameras
 // (one 128-byte line per thread and pass) and their G^1 rows inside Omega^1.
 template <typename T, int NC>
 __device__ __forceinline__ void up_prefetch(const CamDev* __restrict__ cams, const UpTile& tn,
-                                            const CamRef* __restrict__ refs, const T* __restrict__ g0buf) {
+                                            const CamRef* __restrict__ refs, const Slot* __restrict__ g0buf) {
     const int nc = min(tn.count, NC);
     const int a1x = tn.x0 / 2 - 2, a1y = tn.y0 / 2 - 2;
     for (int c = 0; c < nc; ++c) {
         const CamRef& cr = refs[tn.first + c];
         if (cr.g0 >= 0) {
             const char* p = reinterpret_cast<const char*>(g0buf + (long long)cr.g0 * (U_TX * U_TY));
-            for (int q = threadIdx.x; q < (int)(U_TX * U_TY * sizeof(T)) / 128; q += U_THREADS) prefetch_l2(p + 128 * q);
+            for (int q = threadIdx.x; q < (int)(U_TX * U_TY * sizeof(Slot)) / 128; q += U_THREADS) prefetch_l2(p + 128 * q);
         }
         const CamDev& cd = cams[cr.cam];
         const Rect o1 = cd.Om[1];
@@ -1123,7 +1153,7 @@ __device__ __forceinline__ void up_prefetch(const CamDev* __restrict__ cams, con
 template <typename T, int NC>
 __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
                                              const OutDesc& od, const T* __restrict__ R2, const UpTile& tl,
-                                             const CamRef* __restrict__ refs, const T* __restrict__ g0buf,
+                                             const CamRef* __restrict__ refs, const Slot* __restrict__ g0buf,
                                              float4* usm, const UpTile* pf = nullptr) {
     float4* d1 = usm;                // [NC][U1_N]: G^1 of each camera, then R^1 - G^1
     float4* d2 = d1 + NC * U1_N;     // [NC][U2_N]: G^2 of each camera, then R^2 - G^2
@@ -1146,6 +1176,7 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
         ucs.om2[t] = c.Om[2];
         ucs.fg1[t] = c.FG[1];
         ucs.fg2[t] = c.FG[2];
+        ucs.dsc[t] = c.gain * (1.0f / 255.0f) * (1.0f / SLOT_RGB);
     }
     __syncthreads();
     // loads of level 1 and 2 data, all of a thread's loads in flight before the stores
@@ -1295,18 +1326,18 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
             num[k] = make_float3(0.f, 0.f, 0.f);
             den[k] = 0.f;
         }
-        // the level-0 samples of every blended camera (FP32 slots of two cameras at most: all their
-        // loads in flight at once), or of one camera after another
-        constexpr int NB = NC <= 2 && std::is_same<T, float4>::value ? NC : 1;
+        // the level-0 samples of every blended camera (two at a time: all their loads in flight at
+        // once); the weights enter as their slot codes
+        constexpr int NB = NC < 2 ? NC : 2;
         for (int c0 = 0; c0 < nc; c0 += NB) {
-            float4 gv[NB][4];
+            Slot gw[NB][4];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
                 const int slot = c0 + b < nc ? cr[c0 + b].g0 : -1;
-                const T* gq = g0buf + (long long)max(slot, 0) * (U_TX * U_TY) + (2 * qy) * U_TX + 2 * qx;
+                const Slot* gq = g0buf + (long long)max(slot, 0) * (U_TX * U_TY) + (2 * qy) * U_TX + 2 * qx;
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
-                    gv[b][k] = slot >= 0 ? ld(gq + (k >> 1) * U_TX + (k & 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    gw[b][k] = slot >= 0 ? __ldcg(gq + (k >> 1) * U_TX + (k & 1)) : make_uint2(0u, 0u);
             }
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
@@ -1318,11 +1349,11 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
                 // terms add nothing there, so no test is needed
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const float a = gv[b][k].w;
-                    num[k].x = fmaf(a, gv[b][k].x + e[k].rg.x, num[k].x);
-                    num[k].y = fmaf(a, gv[b][k].y + e[k].rg.y, num[k].y);
-                    num[k].z = fmaf(a, gv[b][k].z + e[k].b, num[k].z);
-                    den[k] += a;
+                    const float4 gv = slot_decode(gw[b][k], ucs.dsc[c]);
+                    num[k].x = fmaf(gv.w, gv.x + e[k].rg.x, num[k].x);
+                    num[k].y = fmaf(gv.w, gv.y + e[k].rg.y, num[k].y);
+                    num[k].z = fmaf(gv.w, gv.z + e[k].b, num[k].z);
+                    den[k] += gv.w;
                 }
             }
         }
@@ -1353,7 +1384,7 @@ template <typename T, int NC>
 __global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
                                                         OutDesc od, const T* __restrict__ R2,
                                                         const UpTile* __restrict__ tiles,
-                                                        const CamRef* __restrict__ refs, const T* __restrict__ g0buf,
+                                                        const CamRef* __restrict__ refs, const Slot* __restrict__ g0buf,
                                                         int n, int wave, const UpTile* __restrict__ simple) {
     extern __shared__ float4 usm[];
     if ((int)blockIdx.x >= n) {
@@ -1870,7 +1901,7 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
     if (L >= 2 && fs->n_d1 > 0) {
         prof_mark(r, "fused_down1", s);
         k_down1<T><<<fs->n_d1, D1_THREADS, D1_SMEM, s>>>(r->dcam, g, fp, od, fs->d1_tiles, fs->refs, fs->d1w,
-                                                         fs->d1cols, (T*)fs->g0buf);
+                                                         fs->d1cols, (Slot*)fs->g0buf);
     }
     for (int l = 1; l + 1 < L; ++l) {
         if (fs->n_red[l + 1] == 0) continue;
@@ -1895,14 +1926,14 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
     if (fs->n_up[UP_FULL2]) {
         prof_mark(r, "fused_up_full", s);
         k_up_full<T, 2><<<fs->n_up[UP_FULL2] + ns, U_THREADS, up_full_smem<2>(), s>>>(
-            r->dcam, g, fp, od, R2, fs->up_tiles[UP_FULL2], fs->refs, (const T*)fs->g0buf, fs->n_up[UP_FULL2],
+            r->dcam, g, fp, od, R2, fs->up_tiles[UP_FULL2], fs->refs, (const Slot*)fs->g0buf, fs->n_up[UP_FULL2],
             fs->wave_up2, fs->up_tiles[UP_SIMPLE]);
     }
     if (fs->n_up[UP_FULL4]) {
         const int extra = fs->n_up[UP_FULL2] ? 0 : ns;
         prof_mark(r, "fused_up_full4", s);
         k_up_full<T, 4><<<fs->n_up[UP_FULL4] + extra, U_THREADS, up_full_smem<4>(), s>>>(
-            r->dcam, g, fp, od, R2, fs->up_tiles[UP_FULL4], fs->refs, (const T*)fs->g0buf, fs->n_up[UP_FULL4],
+            r->dcam, g, fp, od, R2, fs->up_tiles[UP_FULL4], fs->refs, (const Slot*)fs->g0buf, fs->n_up[UP_FULL4],
             fs->wave_up4, fs->up_tiles[UP_SIMPLE]);
     }
     if (fs->n_up[UP_GENERAL]) {
@@ -2293,7 +2324,7 @@ stitch_status fused_plan(stitch_rig* r) {
         if (!fs->d1w) return STITCH_ENOMEM;
     }
     if (fs->n_g0 > 0) {
-        fs->g0buf = rig_alloc(r, elem * (size_t)U_TX * U_TY * fs->n_g0);
+        fs->g0buf = rig_alloc(r, sizeof(Slot) * (size_t)U_TX * U_TY * fs->n_g0);
         if (!fs->g0buf) return STITCH_ENOMEM;
     }
     for (int l = 2; l < L; ++l) {
@@ -2501,7 +2532,7 @@ __global__ void __launch_bounds__(B_THREADS, MINB) k_batch(const BatchRigDev* __
                     const int grp = t / D1_THREADS;
                     if (grp < tk.pad0)
                         down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, rg.d1[tk.idx + grp], rg.refs, rg.d1w, rg.d1cols,
-                                      (T*)rg.g0buf, reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + grp * D1_SMEM),
+                                      (Slot*)rg.g0buf, reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + grp * D1_SMEM),
                                       t % D1_THREADS, 1 + grp);
                     break;
                 }
@@ -2518,10 +2549,10 @@ __global__ void __launch_bounds__(B_THREADS, MINB) k_batch(const BatchRigDev* __
                                    reinterpret_cast<unsigned char*>(smem));
                     break;
                 case BT_UPF2:
-                    up_full_tile<T, 2>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, (const T*)rg.g0buf, smem);
+                    up_full_tile<T, 2>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, (const Slot*)rg.g0buf, smem);
                     break;
                 case BT_UPF4:
-                    up_full_tile<T, 4>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, (const T*)rg.g0buf, smem);
+                    up_full_tile<T, 4>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, (const Slot*)rg.g0buf, smem);
                     break;
                 default:
                     break;
@@ -2565,7 +2596,7 @@ __global__ void __launch_bounds__(D1_THREADS, D1_BLOCKS_PER_SM) k_mr_down1(const
     extern __shared__ float4 smem[];
     const BTask tk = tasks[blockIdx.x];
     const BatchRigDev& rg = rigs[tk.rig];
-    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, rg.d1cols, (T*)rg.g0buf, smem);
+    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, rg.d1cols, (Slot*)rg.g0buf, smem);
 }
 
 template <typename T, typename RS>
@@ -2602,7 +2633,7 @@ __global__ void __launch_bounds__(U_THREADS) k_mr_up_full(const BatchRigDev* __r
     const BTask tk = tasks[blockIdx.x];
     const BatchRigDev& rg = rigs[tk.rig];
     const T* R2 = rg.g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
-    up_full_tile<T, NC>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, (const T*)rg.g0buf, usm);
+    up_full_tile<T, NC>(rg.cams, rg.g, rg.fp, rg.od, R2, task_tile<UpTile>(tk), rg.refs, (const Slot*)rg.g0buf, usm);
 }
 
 // A launch of the staged schedule: all tasks of one type and level, over every rig.
