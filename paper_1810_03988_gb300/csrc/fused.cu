@@ -729,7 +729,7 @@ struct RShape {
     static constexpr int TX = X, TY = Y;                  // outputs
     static constexpr int SX = 2 * X + 3, SY = 2 * Y + 3;  // staged inputs
     static constexpr int SXH = (SX + 1) / 2;              // inputs stored as even and odd column planes
-    static constexpr size_t SMEM = sizeof(float4) * (2 * SXH * SY + X * SY);
+    static constexpr size_t SMEM = sizeof(float4) * (2 * SXH * SY + 2 * SXH * Y);
 };
 using RS32x16 = RShape<32, 16>;
 using RS64x8 = RShape<64, 8>;
@@ -741,7 +741,7 @@ constexpr size_t RT_SMEM = RSRig::SMEM;
 // L2 prefetch of a reduce tile's input rows (the part inside Omega^l; rows that fold at the canvas
 // border are left to the loads), 16 threads per row, one 128-byte line each.
 template <typename T, typename RS = RS32x16>
-__device__ __forceinline__ void reduce_prefetch(const CamDev* __restrict__ cams, int l, const Tile& tn) {
+__device__ __forceinline__ void reduce_prefetch(const CamDev* __restrict__ cams, int l, const Tile& tn, int nthreads = 256) {
     const CamDev& c = cams[tn.cam];
     const Rect of = c.Om[l];
     const int vx0 = 2 * tn.x0 - 2, vy0 = 2 * tn.y0 - 2;
@@ -749,8 +749,9 @@ __device__ __forceinline__ void reduce_prefetch(const CamDev* __restrict__ cams,
     if (x1 <= x0) return;
     const char* base = reinterpret_cast<const char*>(c.FG[l]);
     const int len = (x1 - x0) * (int)sizeof(T);
-    for (int q = threadIdx.x; q < 16 * RS::SY; q += 256) {
-        const int rr = q >> 4, k = q & 15, y = vy0 + rr;
+    constexpr int LPR = (RS::SX * (int)sizeof(T) + 127) / 128 + 1;  // 128-byte lines a row may touch
+    for (int q = threadIdx.x; q < LPR * RS::SY; q += nthreads) {
+        const int rr = q / LPR, k = q - rr * LPR, y = vy0 + rr;
         if (y < of.y0 || y >= of.y1 || 128 * k >= len + 127) continue;
         prefetch_l2(base + ((long long)(y - of.y0) * of.w() + (x0 - of.x0)) * (long long)sizeof(T) + min(128 * k, len - 1));
     }
@@ -798,16 +799,16 @@ __device__ __forceinline__ void reduce_tile(const CamDev* __restrict__ cams, con
     }
     if (pf) reduce_prefetch<T, RS>(cams, l, *pf);  // the tile one resident wave later
     __syncthreads();
-    for (int q = threadIdx.x; q < RS::TX * RS::SY; q += 256) {
-        const int r = q / RS::TX, p = q - r * RS::TX;
-        const float4* ev = s0 + r * (2 * RS::SXH) + p;  // columns 2p, 2p+2, 2p+4
-        const float4* od = ev + RS::SXH;                // columns 2p+1, 2p+3
-        float4 acc = f4fma(c_w5[0], ev[0], make_float4(0.f, 0.f, 0.f, 0.f));
-        acc = f4fma(c_w5[1], od[0], acc);
-        acc = f4fma(c_w5[2], ev[1], acc);
-        acc = f4fma(c_w5[3], od[1], acc);
-        acc = f4fma(c_w5[4], ev[2], acc);
-        sh[q] = acc;
+    // vertical pass (rows 2 jj .. 2 jj + 4 of every column, into even and odd column planes), then
+    // horizontal: each output's operations in the order of reduce_col_tile, so both give the same bits
+    for (int q = threadIdx.x; q < RS::SX * RS::TY; q += 256) {
+        const int jj = q / RS::SX, cc = q - jj * RS::SX;
+        const int slot = (cc & 1) * RS::SXH + (cc >> 1);
+        const float4* col = s0 + (2 * jj) * (2 * RS::SXH) + slot;
+        float4 acc = f4fma(c_w5[0], col[0], make_float4(0.f, 0.f, 0.f, 0.f));
+#pragma unroll
+        for (int n = 1; n < 5; ++n) acc = f4fma(c_w5[n], col[n * (2 * RS::SXH)], acc);
+        sh[jj * (2 * RS::SXH) + slot] = acc;
     }
     __syncthreads();
     T* dst = reinterpret_cast<T*>(c.FG[l + 1]);
@@ -816,21 +817,124 @@ __device__ __forceinline__ void reduce_tile(const CamDev* __restrict__ cams, con
         const int k = tl.x0 + p, j = tl.y0 + jj;
         if (k >= oc.x1 || j >= oc.y1) continue;
         if (!STITCH_DCHECK(k >= oc.x0 && j >= oc.y0, 3, (long long)k << 24 | j)) continue;
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int n = 0; n < 5; ++n) acc = f4fma(c_w5[n], sh[(2 * jj + n) * RS::TX + p], acc);
+        const float4* ev = sh + jj * (2 * RS::SXH) + p;  // columns 2p, 2p+2, 2p+4
+        const float4* od = ev + RS::SXH;                 // columns 2p+1, 2p+3
+        float4 acc = f4fma(c_w5[0], ev[0], make_float4(0.f, 0.f, 0.f, 0.f));
+        acc = f4fma(c_w5[1], od[0], acc);
+        acc = f4fma(c_w5[2], ev[1], acc);
+        acc = f4fma(c_w5[3], od[1], acc);
+        acc = f4fma(c_w5[4], ev[2], acc);
         st(dst + (long long)(j - oc.y0) * oc.w() + (k - oc.x0), acc);
     }
 }
 
 // Blocks start in index order as resident ones finish, so block b prefetches into L2 the input of
 // tile b + wave (wave = resident blocks on the device), which starts about when b ends.
+// Column-sweep REDUCE of the single-rig path: 64 x 8 outputs of level l+1 from the 131 x 19 region
+// of level l.  Thread t takes virtual column t + 2 and runs the vertical pass down its 19 rows in
+// registers, with its loads straight from G^l a few rows ahead; the columns 0, 1 and 130 are one
+// element per thread.  The vertically reduced rows go to shared memory (even and odd column
+// planes, 16 banks apart) for the horizontal pass.  Shared memory carries 8 rows instead of the
+// whole input region, and every operation is that of reduce_tile, in the same order.
+using RSCol = RShape<64, 8>;
+constexpr int RC_THREADS = 128;
+constexpr int RC_VODD = 68, RC_VROW = 136;
+constexpr size_t RC_SMEM = sizeof(float4) * (RC_VROW * RSCol::TY + 3 * RSCol::SY);
+static_assert(RSCol::SX == RC_THREADS + 3 && RSCol::SY == 19 && RC_VODD >= RSCol::SXH && RC_VROW >= 2 * RC_VODD,
+              "column per thread over a 131 x 19 region");
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_reduce_t(const CamDev* __restrict__ cams, const __grid_constant__ RigGeom g, int l,
-                                                   const Tile* __restrict__ tiles, int n, int wave) {
+__device__ __forceinline__ void reduce_col_tile(const CamDev* __restrict__ cams, const RigGeom& g, int l, const Tile& tl,
+                                                float4* smem, const Tile* pf) {
+    constexpr int SX = RSCol::SX, SY = RSCol::SY, TX = RSCol::TX, TY = RSCol::TY;
+    float4* vres = smem;                 // [TY][RC_VROW]
+    float4* ext = smem + RC_VROW * TY;   // [SY][3]: columns 0, 1 and SX - 1
+    const CamDev& c = cams[tl.cam];
+    const Rect oc = c.Om[l + 1], of = c.Om[l];
+    const int vx0 = 2 * tl.x0 - 2, vy0 = 2 * tl.y0 - 2;
+    const T* src = reinterpret_cast<const T*>(c.FG[l]);
+    const int nxl = g.nx[l], nyl = g.ny[l];
+    const long long w = of.w();
+    const int t = threadIdx.x;
+    // a tile whose inputs lie inside Omega^l (so inside the level: nothing folds) reads them straight
+    const bool inside = vx0 >= of.x0 && vx0 + SX <= of.x1 && vy0 >= of.y0 && vy0 + SY <= of.y1;
+    auto elem = [&](int r, int x, bool xin) -> float4 {
+        if (inside) return ld(src + (long long)(vy0 + r - of.y0) * w + (x - of.x0));
+        const int y = fold101(vy0 + r, nyl);
+        return xin && y >= of.y0 && y < of.y1 ? ld(src + (long long)(y - of.y0) * w + (x - of.x0))
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto colx = [&](int cc, bool& xin) {
+        const int x = inside ? vx0 + cc : fold101(vx0 + cc, nxl);
+        xin = x >= of.x0 && x < of.x1;
+        return x;
+    };
+    if (t < 3 * SY) {
+        const int r = t / 3, k = t - 3 * r;
+        bool xin;
+        const int x = colx(k < 2 ? k : SX - 1, xin);
+        ext[t] = elem(r, x, xin);
+    }
+    {
+        const int cc = t + 2;
+        bool xin;
+        const int x = colx(cc, xin);
+        float4* vcol = vres + (cc & 1) * RC_VODD + (cc >> 1);
+        constexpr int D = 6;  // rows in flight ahead of the one being reduced
+        float4 row[SY];
+#pragma unroll
+        for (int r = 0; r < D; ++r) row[r] = elem(r, x, xin);
+        V4 B = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, C = B;
+        // rows 2m complete output row m - 2 (stored from m = 2 on) and start row m; rows 2m + 1 add
+        // their taps to rows m - 1 and m
+#pragma unroll
+        for (int r = 0; r < SY; ++r) {
+            if (r + D < SY) row[r + D] = elem(r + D, x, xin);
+            const V4 v = v4_of(row[r]);
+            if ((r & 1) == 0) {
+                if (r >= 4) vcol[(r / 2 - 2) * RC_VROW] = f4_of(v4_fma(d1_w(4), v, C));
+                C = v4_fma(d1_w(2), v, B);
+                B = v4_mul(d1_w(0), v);
+            } else {
+                C = v4_fma(d1_w(3), v, C);
+                B = v4_fma(d1_w(1), v, B);
+            }
+        }
+    }
+    if (pf) reduce_prefetch<T, RSCol>(cams, l, *pf, RC_THREADS);  // the tile one resident wave later
+    __syncthreads();
+    if (t < 3 * TY) {
+        const int jj = t / 3, k = t - 3 * jj, cc = k < 2 ? k : SX - 1;
+        V4 acc = v4_mul(d1_w(0), v4_of(ext[(2 * jj) * 3 + k]));
+#pragma unroll
+        for (int n = 1; n < 5; ++n) acc = v4_fma(d1_w(n), v4_of(ext[(2 * jj + n) * 3 + k]), acc);
+        vres[jj * RC_VROW + (cc & 1) * RC_VODD + (cc >> 1)] = f4_of(acc);
+    }
+    __syncthreads();
+    T* dst = reinterpret_cast<T*>(c.FG[l + 1]);
+    const int p = t % TX, k = tl.x0 + p;
+#pragma unroll
+    for (int q = 0; q < TY * TX / RC_THREADS; ++q) {
+        const int jj = t / TX + q * (RC_THREADS / TX), j = tl.y0 + jj;
+        const float4* ev = vres + jj * RC_VROW + p;  // columns 2p, 2p+2, 2p+4
+        const float4* od = ev + RC_VODD;             // columns 2p+1, 2p+3
+        V4 acc = v4_mul(d1_w(0), v4_of(ev[0]));
+        acc = v4_fma(d1_w(1), v4_of(od[0]), acc);
+        acc = v4_fma(d1_w(2), v4_of(ev[1]), acc);
+        acc = v4_fma(d1_w(3), v4_of(od[1]), acc);
+        acc = v4_fma(d1_w(4), v4_of(ev[2]), acc);
+        if (k >= oc.x1 || j >= oc.y1) continue;
+        if (!STITCH_DCHECK(k >= oc.x0 && j >= oc.y0, 3, (long long)k << 24 | j)) continue;
+        st(dst + (long long)(j - oc.y0) * oc.w() + (k - oc.x0), f4_of(acc));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RC_THREADS, 8) k_reduce_t(const CamDev* __restrict__ cams, const __grid_constant__ RigGeom g,
+                                                           int l, const Tile* __restrict__ tiles, int n, int wave) {
     extern __shared__ float4 smem[];
     const int nb = blockIdx.x + wave;
-    reduce_tile<T, RSRig>(cams, g, l, tiles[blockIdx.x], smem, nb < n ? tiles + nb : nullptr);
+    reduce_col_tile<T>(cams, g, l, tiles[blockIdx.x], smem, nb < n ? tiles + nb : nullptr);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1646,8 +1750,10 @@ enum UpKind { UP_SIMPLE = 0, UP_FULL2 = 1, UP_FULL4 = 2, UP_GENERAL = 3, UP_KIND
 struct FusedState {
     D1Tile* d1_tiles = nullptr;
     int n_d1 = 0;
-    Tile* red_tiles[MAXL] = {};  // tiles producing level l (l >= 2)
+    Tile* red_tiles[MAXL] = {};  // tiles producing level l (l >= 2), RSRig shape (the batched schedules)
     int n_red[MAXL] = {};
+    Tile* rc_tiles[MAXL] = {};   // the same levels in the column-sweep kernel's 64 x 8 tiles (stitch_frames)
+    int n_rc[MAXL] = {};
     LevelTile* co_tiles[MAXL] = {};  // coarse tiles of level l (l >= 2)
     int n_co[MAXL] = {};
     int* camlist = nullptr;
@@ -1904,10 +2010,10 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
                                                          fs->d1cols, (Slot*)fs->g0buf);
     }
     for (int l = 1; l + 1 < L; ++l) {
-        if (fs->n_red[l + 1] == 0) continue;
+        if (fs->n_rc[l + 1] == 0) continue;
         prof_mark(r, "fused_reduce", s);
-        k_reduce_t<T><<<fs->n_red[l + 1], 256, RT_SMEM, s>>>(r->dcam, g, l, fs->red_tiles[l + 1], fs->n_red[l + 1],
-                                                             fs->wave_red);
+        k_reduce_t<T><<<fs->n_rc[l + 1], RC_THREADS, RC_SMEM, s>>>(r->dcam, g, l, fs->rc_tiles[l + 1], fs->n_rc[l + 1],
+                                                                   fs->wave_red);
     }
     for (int l = L - 1; l >= 2; --l) {
         if (fs->n_co[l] == 0) continue;
@@ -1947,7 +2053,7 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
 template <typename T>
 stitch_status set_smem_attrs() {
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
-    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_reduce_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RT_SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_reduce_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC_SMEM));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)up_full_smem<2>()));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1963,7 +2069,7 @@ template <typename T>
 stitch_status set_waves(stitch_rig* r, FusedState* fs) {
     int sms = 0, pr = 0, p2 = 0, p4 = 0;
     STITCH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device));
-    STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pr, k_reduce_t<T>, 256, RT_SMEM));
+    STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pr, k_reduce_t<T>, RC_THREADS, RC_SMEM));
     STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_up_full<T, 2>, U_THREADS, up_full_smem<2>()));
     STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p4, k_up_full<T, 4>, U_THREADS, up_full_smem<4>()));
     fs->wave_red = std::max(pr, 1) * sms;
@@ -2042,6 +2148,8 @@ stitch_status fused_plan(stitch_rig* r) {
         }
     }
     plan_reduce_tiles(r, RT_X, RT_Y, red);
+    std::vector<Tile> redc[MAXL];
+    plan_reduce_tiles(r, RSCol::TX, RSCol::TY, redc);
     // classify the canvas tiles of `up`
     std::vector<UpTile> up[UP_KINDS];
     std::unordered_map<long long, size_t> d1_index;  // (camera, level-1 origin) -> down1 tile
@@ -2260,10 +2368,13 @@ stitch_status fused_plan(stitch_rig* r) {
                 }
             }
         for (int l = 2; l < L; ++l) {
-            std::vector<Tile> keep;
+            std::vector<Tile> keep, keepc;
             for (const Tile& t : red[l])
                 if (any(l, t.cam, t.x0, t.x0 + RT_X, t.y0, t.y0 + RT_Y)) keep.push_back(t);
+            for (const Tile& t : redc[l])
+                if (any(l, t.cam, t.x0, t.x0 + RSCol::TX, t.y0, t.y0 + RSCol::TY)) keepc.push_back(t);
             red[l].swap(keep);
+            redc[l].swap(keepc);
         }
         // down1: G^1 only where needed; drop tiles without any output (renumbering weight tables)
         std::vector<D1Tile> kd;
@@ -2331,6 +2442,9 @@ stitch_status fused_plan(stitch_rig* r) {
         st = upload(r, red[l], &fs->red_tiles[l]);
         if (st != STITCH_OK) return st;
         fs->n_red[l] = (int)red[l].size();
+        st = upload(r, redc[l], &fs->rc_tiles[l]);
+        if (st != STITCH_OK) return st;
+        fs->n_rc[l] = (int)redc[l].size();
     }
     st = upload(r, camlist, &fs->camlist);
     if (st != STITCH_OK) return st;
@@ -2346,7 +2460,7 @@ stitch_status fused_plan(stitch_rig* r) {
     }
     int kernels = 0;
     if (L >= 2 && fs->n_d1 > 0) kernels += 1;
-    for (int l = 2; l < L; ++l) kernels += (fs->n_red[l] > 0) + (fs->n_co[l] > 0);
+    for (int l = 2; l < L; ++l) kernels += (fs->n_rc[l] > 0) + (fs->n_co[l] > 0);
     for (int k = 0; k < UP_KINDS; ++k) kernels += fs->n_up[k] > 0;
     if (fs->n_up[UP_SIMPLE] && (fs->n_up[UP_FULL2] || fs->n_up[UP_FULL4])) kernels -= 1;  // rides along
     r->kernels_per_frame = kernels;
