@@ -982,7 +982,7 @@ struct CShape {
     static constexpr int CX = X / 2 + 4, CY = Y / 2 + 4;   // level-(l+1) virtual region
     static constexpr int CN = CX * CY, TN = X * Y;
     static constexpr int QUADS = (X / 2) * (Y / 2);
-    static constexpr int SMEM_F4 = CN + CT_NC * TN + CT_NC * CN;  // shared memory in float4 units
+    static constexpr int SMEM_F4 = CN + CT_NC * CN;  // shared memory in float4 units
     static_assert(QUADS == 256, "one 2 x 2 quad per thread of a 256-thread block");
 };
 using CS32x32 = CShape<32, 32>;
@@ -1001,8 +1001,7 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
                                             T* __restrict__ Rl, const T* __restrict__ Rc, const LevelTile& tl,
                                             const int* __restrict__ camlist, float4* smem) {
     float4* rc = smem;                                                   // [CS::CN] R^{l+1}
-    float4 (*gl)[CS::TN] = reinterpret_cast<float4 (*)[CS::TN]>(rc + CS::CN);  // [CT_NC][CS::TN] G^l per camera
-    float4 (*gc)[CS::CN] = reinterpret_cast<float4 (*)[CS::CN]>(rc + CS::CN + CT_NC * CS::TN);  // G^{l+1}, then R - G
+    float4 (*gc)[CS::CN] = reinterpret_cast<float4 (*)[CS::CN]>(rc + CS::CN);  // [CT_NC][CS::CN] G^{l+1}, then R - G
     const bool top = l == g.levels - 1;
     const int X0 = tl.x0, Y0 = tl.y0;
     const int ax = X0 / 2 - 2, ay = Y0 / 2 - 2;
@@ -1027,22 +1026,10 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
     for (int c0 = 0; c0 < tl.count; c0 += CT_NC) {
         const int nc = min(CT_NC, tl.count - c0);
         __syncthreads();
+        // the chunk's G^{l+1} regions into shared memory, all loads in flight before the stores
         {
-            constexpr int NL = (CT_NC * CS::TN + 255) / 256, NC2 = (CT_NC * CS::CN + 255) / 256;
-            float4 v[NL], w[NC2];
-#pragma unroll
-            for (int k = 0; k < NL; ++k) {
-                const int q = t + 256 * k;
-                v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (q < nc * CS::TN) {
-                    const int ci = q / CS::TN, qq = q - ci * CS::TN;
-                    const CamDev& c = cams[camlist[tl.first + c0 + ci]];
-                    const int x = X0 + qq % CS::TX, y = Y0 + qq / CS::TX;
-                    const Rect o = c.Om[l];
-                    if (o.contains(x, y))
-                        v[k] = ld(reinterpret_cast<const T*>(c.FG[l]) + (long long)(y - o.y0) * o.w() + (x - o.x0));
-                }
-            }
+            constexpr int NC2 = (CT_NC * CS::CN + 255) / 256;
+            float4 w[NC2];
 #pragma unroll
             for (int k = 0; k < NC2; ++k) {
                 const int q = t + 256 * k;
@@ -1056,11 +1043,6 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
                     if (o.contains(x, y))
                         w[k] = ld(reinterpret_cast<const T*>(c.FG[l + 1]) + (long long)(y - o.y0) * o.w() + (x - o.x0));
                 }
-            }
-#pragma unroll
-            for (int k = 0; k < NL; ++k) {
-                const int q = t + 256 * k;
-                if (q < nc * CS::TN) gl[q / CS::TN][q % CS::TN] = v[k];
             }
 #pragma unroll
             for (int k = 0; k < NC2; ++k) {
@@ -1079,14 +1061,24 @@ __device__ __forceinline__ void coarse_tile(const CamDev* __restrict__ cams, con
         }
         if (has_quad) {
             for (int ci = 0; ci < nc; ++ci) {
-                const Rect z = cams[camlist[tl.first + c0 + ci]].Z[l];
+                // the quad's G^l of the camera: each value is read by this thread only, so it goes
+                // straight into registers (only inside Z^l, where it enters the blend)
+                const CamDev& c = cams[camlist[tl.first + c0 + ci]];
+                const Rect z = c.Z[l], o = c.Om[l];
+                const T* fg = reinterpret_cast<const T*>(c.FG[l]);
+                float4 gq[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
+                    gq[k] = z.contains(x, y) ? ld(fg + (long long)(y - o.y0) * o.w() + (x - o.x0)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 V3 e[4] = {v3_zero(), v3_zero(), v3_zero(), v3_zero()};
                 if (!top) expand_quad(gc[ci], CS::CX, qx + 1, qy + 1, e);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int x = X0 + 2 * qx + (k & 1), y = Y0 + 2 * qy + (k >> 1);
                     if (!z.contains(x, y)) continue;
-                    const float4 gv = gl[ci][(2 * qy + (k >> 1)) * CS::TX + 2 * qx + (k & 1)];
+                    const float4 gv = gq[k];
                     nrg[k] = f2fma(f2(gv.w), f2add(make_float2(gv.x, gv.y), e[k].rg), nrg[k]);
                     nb[k] = fmaf(gv.w, gv.z + e[k].b, nb[k]);
                     den[k] += gv.w;
