@@ -734,7 +734,7 @@ struct RShape {
 using RS32x16 = RShape<32, 16>;
 using RS64x8 = RShape<64, 8>;
 using RSRig = RS32x16;  // the shape of a rig's own REDUCE tiles (the single-rig path, the persistent batch)
-using RSAlt = RShape<RSRig::TY * 4, RSRig::TY / 2>;  // the batch tuner's other shape (64 x 8)
+using RSAlt = RShape<RSRig::TY * 4, RSRig::TY / 2>;  // the batch tuner's other shape (64 x 8, column sweep)
 constexpr int RT_X = RSRig::TX, RT_Y = RSRig::TY;
 constexpr size_t RT_SMEM = RSRig::SMEM;
 
@@ -842,6 +842,7 @@ constexpr int RC_VODD = 68, RC_VROW = 136;
 constexpr size_t RC_SMEM = sizeof(float4) * (RC_VROW * RSCol::TY + 3 * RSCol::SY);
 static_assert(RSCol::SX == RC_THREADS + 3 && RSCol::SY == 19 && RC_VODD >= RSCol::SXH && RC_VROW >= 2 * RC_VODD,
               "column per thread over a 131 x 19 region");
+static_assert(RSAlt::TX == RSCol::TX && RSAlt::TY == RSCol::TY, "the staged schedule's 64 x 8 tiles run the column sweep");
 
 template <typename T>
 __device__ __forceinline__ void reduce_col_tile(const CamDev* __restrict__ cams, const RigGeom& g, int l, const Tile& tl,
@@ -880,7 +881,7 @@ __device__ __forceinline__ void reduce_col_tile(const CamDev* __restrict__ cams,
         bool xin;
         const int x = colx(cc, xin);
         float4* vcol = vres + (cc & 1) * RC_VODD + (cc >> 1);
-        constexpr int D = 6;  // rows in flight ahead of the one being reduced
+        constexpr int D = 10;  // rows in flight ahead of the one being reduced
         float4 row[SY];
 #pragma unroll
         for (int r = 0; r < D; ++r) row[r] = elem(r, x, xin);
@@ -2713,6 +2714,16 @@ __global__ void __launch_bounds__(256) k_mr_reduce(const BatchRigDev* __restrict
     reduce_tile<T, RS>(rg.cams, rg.g, tk.level - 1, task_tile<Tile>(tk), smem);
 }
 
+// The 64 x 8 REDUCE tiles of the staged schedule run the single-rig path's column sweep.
+template <typename T>
+__global__ void __launch_bounds__(RC_THREADS, 8) k_mr_reduce_col(const BatchRigDev* __restrict__ rigs,
+                                                                const BTask* __restrict__ tasks) {
+    extern __shared__ float4 smem[];
+    const BTask tk = tasks[blockIdx.x];
+    const BatchRigDev& rg = rigs[tk.rig];
+    reduce_col_tile<T>(rg.cams, rg.g, tk.level - 1, task_tile<Tile>(tk), smem, nullptr);
+}
+
 // camlist: the rig's camera list of the coarse tiles of this shape
 template <typename T, typename CS>
 __global__ void __launch_bounds__(256, 3) k_mr_coarse(const BatchRigDev* __restrict__ rigs, const BTask* __restrict__ tasks) {
@@ -2852,7 +2863,7 @@ stitch_status b_launch_staged(BatchState* b, int shape, cudaStream_t s) {
         switch (gr.type) {
             case BT_D1: k_mr_down1<T><<<gr.count, D1_THREADS, D1_SMEM, s>>>(b->d_rigs, gr.d_tasks); break;
             case BT_RED:
-                if (b_rs(shape)) k_mr_reduce<T, RSAlt><<<gr.count, 256, RSAlt::SMEM, s>>>(b->d_rigs, gr.d_tasks);
+                if (b_rs(shape)) k_mr_reduce_col<T><<<gr.count, RC_THREADS, RC_SMEM, s>>>(b->d_rigs, gr.d_tasks);
                 else k_mr_reduce<T, RSRig><<<gr.count, 256, RSRig::SMEM, s>>>(b->d_rigs, gr.d_tasks);
                 break;
             case BT_CO:
@@ -2876,8 +2887,8 @@ stitch_status b_staged_attrs() {
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce<T, RSRig>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)RSRig::SMEM));
-    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce<T, RSAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)RSAlt::SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce_col<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)RC_SMEM));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_coarse<T, CSRig>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(sizeof(float4) * CSRig::SMEM_F4)));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_coarse<T, CSAlt>, cudaFuncAttributeMaxDynamicSharedMemorySize,
