@@ -392,7 +392,8 @@ void stitch_batch_destroy(stitch_batch* batch);
  *     replayed from a CUDA graph;
  *   - the staged schedule (one launch per task type and level over all rigs, no device waits),
  *     replayed from a CUDA graph, with four tile-shape combinations for its REDUCE launches
- *     (32 x 16 or 64 x 8 outputs) and coarse-level launches (32 x 32 or 64 x 16);
+ *     (32 x 16 outputs, or the column sweep of stitch_frames on 64 x 8) and coarse-level launches
+ *     (32 x 32 or 64 x 16);
  *   - the per-rig streams (every rig's own launch sequence on a stream of its own, launched directly).
  * Environment: STITCH_TUNE=off skips timing (persistent defaults); =persistent, =staged or =streams
  * forces that mode (its parameters still timed); =full times even when a cached choice exists.
