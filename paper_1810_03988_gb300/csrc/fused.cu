@@ -187,7 +187,7 @@ constexpr int D1_TX = 32, D1_TY = 8;                         // level-1 outputs 
 constexpr int D1_SX = 2 * D1_TX + 3, D1_SY = 2 * D1_TY + 3;  // level-0 virtual region (67 x 19)
 constexpr int D1_THREADS = 64;                               // one thread per virtual column 0..63
 constexpr int D1_XC = D1_SX - D1_THREADS;                    // the last 3 columns: one sample per thread
-constexpr int D1_BLOCKS_PER_SM = 12;                         // resident blocks per SM (shared memory)
+
 constexpr int D1_NSAMP = D1_SX * D1_SY;                      // level-0 samples of a tile's region
 // a FULL canvas tile's level-0 slot (64 x 32 samples per blended camera), written by the camera's
 // two down1 tiles over it (rows 0..15 and 16..31)
@@ -199,19 +199,32 @@ constexpr int D1_SLOT = (2 * D1_TX) * (4 * D1_TY);
 using Slot = uint2;
 constexpr float SLOT_RGB = 256.0f;  // codes per 8-bit level
 constexpr float SLOT_A = 65535.0f;  // codes per unit weight
-// Footprint capacity in texels (one 32-bit word each; rows padded to a multiple of 4 texels).
-constexpr int D1_FOOT = 2048;
+// Footprint capacity in texels (one 32-bit word each; rows padded to a multiple of 4 texels).  The
+// kernel comes in two capacities: 2048 texels with 12 resident blocks per SM, and 1536 with 13.  A
+// rig takes the smaller one when at most 2 % of its staged tiles need more (those then read their
+// taps from the frame): one more block per SM beats that (8 x 4K: 315 of 76 350 tiles).
+constexpr int D1_FOOT = 2048;        // the larger capacity (planning, the batched kernels)
+constexpr int D1_FOOT_SMALL = 1536;
 // Vertically reduced values: per level-1 row, the even columns at slots 0..33 and the odd columns
 // at slots 36..68 (float4), so that a warp's 128-bit stores of 32 consecutive columns and the
 // horizontal pass's loads of consecutive even (odd) columns are free of bank conflicts.
 constexpr int D1_VODD = 36, D1_VROW = 70;
-constexpr int D1_SM_FOOT = 4 * D1_FOOT;                      // bytes
 constexpr int D1_SM_V = 16 * D1_VROW * D1_TY;
 constexpr int D1_SM_X = 16 * D1_XC * D1_SY;
 constexpr int D1_SM_ROW = 8 * ((D1_SY + 1) & ~1);            // (dy, dy) per row
-constexpr size_t D1_SMEM = D1_SM_FOOT + D1_SM_V + D1_SM_X + D1_SM_ROW;
+// shared memory of a block with footprint capacity CAP: footprint, vertically reduced rows, the
+// last three columns' samples, (dy, dy) per row
+template <int CAP>
+struct D1Cap {
+    static constexpr int SM_FOOT = 4 * CAP;
+    static constexpr size_t SMEM = SM_FOOT + D1_SM_V + D1_SM_X + D1_SM_ROW;
+    static constexpr int BLOCKS = CAP > D1_FOOT_SMALL ? 12 : 13;  // resident blocks per SM
+    static constexpr int SG = (CAP / 4 + D1_THREADS - 1) / D1_THREADS;  // staging groups per thread (at most)
+    static_assert(CAP % 16 == 0, "whole groups of 4 texels, 16-byte aligned parts");
+};
+constexpr size_t D1_SMEM = D1Cap<D1_FOOT>::SMEM;  // the larger capacity's
 static_assert(D1_SX == 67 && D1_THREADS == 64 && D1_XC == 3, "column-per-thread sweep of a 67-column region");
-static_assert(D1_SM_FOOT % 16 == 0 && D1_SM_V % 16 == 0 && D1_SM_X % 16 == 0, "16-byte aligned parts");
+static_assert(D1_SM_V % 16 == 0 && D1_SM_X % 16 == 0, "16-byte aligned parts");
 
 __device__ __forceinline__ int d1_vslot(int c) { return (c & 1) * D1_VODD + (c >> 1); }
 
@@ -278,13 +291,12 @@ __global__ void __launch_bounds__(D1W_THREADS) k_d1_weights(const CamDev* __rest
 // thread takes groups of 4 texels (12 bytes: three aligned 32-bit words, since fx0 is a multiple of
 // 4), issues the loads of all its groups before repacking, and writes the 4 texel words with one
 // 16-byte store.  Frames whose base or pitch is not a multiple of 4 bytes are read byte by byte.
-constexpr int D1_SG = D1_FOOT / 4 / D1_THREADS;  // groups per thread
-static_assert(D1_SG * 4 * D1_THREADS == D1_FOOT, "whole groups per thread");
 
+template <int CAP>
 __device__ __forceinline__ void stage_footprint(uint32_t* __restrict__ foot, const uint8_t* __restrict__ px,
                                                 long long pitch, int W, int fx0, int fy0, int fw, int fh, int t) {
     const int gpr = (fw + 3) >> 2, ng = gpr * fh;  // groups per row = S / 4
-    if (!STITCH_DCHECK(ng <= D1_FOOT / 4, 2, ng)) return;
+    if (!STITCH_DCHECK(ng <= CAP / 4, 2, ng)) return;
     if (((reinterpret_cast<uintptr_t>(px) | (uintptr_t)pitch) & 3) != 0) {
         for (int q = t; q < 4 * ng; q += D1_THREADS) {
             const int rr = q / (4 * gpr), u = q - rr * 4 * gpr;
@@ -297,9 +309,10 @@ __device__ __forceinline__ void stage_footprint(uint32_t* __restrict__ foot, con
         }
         return;
     }
-    uint32_t w[D1_SG][3];
+    constexpr int SG = D1Cap<CAP>::SG;
+    uint32_t w[SG][3];
 #pragma unroll
-    for (int k = 0; k < D1_SG; ++k) {
+    for (int k = 0; k < SG; ++k) {
         const int q = t + k * D1_THREADS;
         w[k][0] = w[k][1] = w[k][2] = 0u;
         if (q < ng) {
@@ -321,7 +334,7 @@ __device__ __forceinline__ void stage_footprint(uint32_t* __restrict__ foot, con
         }
     }
 #pragma unroll
-    for (int k = 0; k < D1_SG; ++k) {
+    for (int k = 0; k < SG; ++k) {
         const int q = t + k * D1_THREADS;
         if (q < ng) {
             // bytes R0 G0 B0 R1 | G1 B1 R2 G2 | B2 R3 G3 B3 -> one word per texel
@@ -538,15 +551,16 @@ __device__ __forceinline__ void d1_bar(int id) {
 }
 
 // One down1 tile, worked on by the D1_THREADS threads t = 0 .. 63 that share barrier `bar`.
-template <typename T>
+template <typename T, int CAP = D1_FOOT>
 __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
                                            const OutDesc& od, const D1Tile& tl, const CamRef* __restrict__ refs,
                                            const float* __restrict__ d1w, const float4* __restrict__ d1cols,
                                            Slot* __restrict__ g0buf, float4* smem, int t = threadIdx.x, int bar = 0) {
     uint32_t* foot = reinterpret_cast<uint32_t*>(smem);
-    float4* vres = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + D1_SM_FOOT);
-    float4* ext = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + D1_SM_FOOT + D1_SM_V);  // [19][3]
-    float2* rowdy = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem) + D1_SM_FOOT + D1_SM_V + D1_SM_X);
+    constexpr int SM_FOOT = D1Cap<CAP>::SM_FOOT;
+    float4* vres = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + SM_FOOT);
+    float4* ext = reinterpret_cast<float4*>(reinterpret_cast<char*>(smem) + SM_FOOT + D1_SM_V);  // [19][3]
+    float2* rowdy = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem) + SM_FOOT + D1_SM_V + D1_SM_X);
 
     const int i = tl.cam;
     const CamDev& ci = cams[i];
@@ -597,7 +611,7 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
     x.ibase = (unsigned)(ref.tm.V0 - x.fy0) * (unsigned)x.S + (unsigned)(ref.tm.U0 - x.fx0) -
               D1_FLOOR_BITS * ((unsigned)x.S + 1u);
     x.maxidx = x.S * (x.fh - 1) - 2;
-    if (staged && act) stage_footprint(foot, px_i, pitch_i, x.W, x.fx0, x.fy0, x.fw, x.fh, t);
+    if (staged && act) stage_footprint<CAP>(foot, px_i, pitch_i, x.W, x.fx0, x.fy0, x.fw, x.fh, t);
     if (t < D1_SY) {
         const float dy = (float)(fold101(vy0 + t, g.ny[0]) - ref.ay);
         rowdy[t] = make_float2(dy, dy);
@@ -708,13 +722,16 @@ __device__ __forceinline__ void down1_tile(const CamDev* __restrict__ cams, cons
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(D1_THREADS, D1_BLOCKS_PER_SM) k_down1(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
-                                                       OutDesc od, const D1Tile* __restrict__ tiles,
-                                                       const CamRef* __restrict__ refs, const float* __restrict__ d1w,
-                                                       const float4* __restrict__ d1cols, Slot* __restrict__ g0buf) {
+template <typename T, int CAP>
+__global__ void __launch_bounds__(D1_THREADS, D1Cap<CAP>::BLOCKS) k_down1(const CamDev* __restrict__ cams, RigGeom g,
+                                                                        FramePtrs fp, OutDesc od,
+                                                                        const D1Tile* __restrict__ tiles,
+                                                                        const CamRef* __restrict__ refs,
+                                                                        const float* __restrict__ d1w,
+                                                                        const float4* __restrict__ d1cols,
+                                                                        Slot* __restrict__ g0buf) {
     extern __shared__ float4 smem[];
-    down1_tile<T>(cams, g, fp, od, tiles[blockIdx.x], refs, d1w, d1cols, g0buf, smem);
+    down1_tile<T, CAP>(cams, g, fp, od, tiles[blockIdx.x], refs, d1w, d1cols, g0buf, smem);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1247,7 +1264,8 @@ __device__ __forceinline__ void up_prefetch(const CamDev* __restrict__ cams, con
     }
 }
 
-template <typename T, int NC>
+// NB: blended cameras whose level-0 slot loads are in flight at once (1 or 2)
+template <typename T, int NC, int NB = (NC < 2 ? NC : 2)>
 __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
                                              const OutDesc& od, const T* __restrict__ R2, const UpTile& tl,
                                              const CamRef* __restrict__ refs, const Slot* __restrict__ g0buf,
@@ -1423,9 +1441,9 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
             num[k] = make_float3(0.f, 0.f, 0.f);
             den[k] = 0.f;
         }
-        // the level-0 samples of every blended camera (two at a time: all their loads in flight at
-        // once); the weights enter as their slot codes
-        constexpr int NB = NC < 2 ? NC : 2;
+        // the level-0 samples of every blended camera, NB cameras at a time (all their loads in
+        // flight at once); the weights enter as their slot codes
+
         for (int c0 = 0; c0 < nc; c0 += NB) {
             Slot gw[NB][4];
 #pragma unroll
@@ -1477,6 +1495,21 @@ __device__ __forceinline__ void up_full_tile(const CamDev* __restrict__ cams, co
 
 // Blocks n .. n + n_simple - 1 take the ZERO (and fallback SOLO) canvas tiles `simple`, so that they
 // need no launch of their own.
+template <typename T, int NC, int NB>
+__device__ __forceinline__ void up_full_block(const CamDev* __restrict__ cams, const RigGeom& g, const FramePtrs& fp,
+                                              const OutDesc& od, const T* __restrict__ R2, const UpTile* __restrict__ tiles,
+                                              const CamRef* __restrict__ refs, const Slot* __restrict__ g0buf, int n,
+                                              int wave, const UpTile* __restrict__ simple, float4* usm) {
+    if ((int)blockIdx.x >= n) {
+        up_simple_tile(cams, g, fp, od, simple[blockIdx.x - n], refs, reinterpret_cast<unsigned char*>(usm));
+        return;
+    }
+    const int nb = blockIdx.x + wave;  // prefetched: the tile one resident wave later (see k_reduce_t)
+    up_full_tile<T, NC, NB>(cams, g, fp, od, R2, tiles[blockIdx.x], refs, g0buf, usm, nb < n ? tiles + nb : nullptr);
+}
+// Two occupancies: k_up_full_b4 holds four resident blocks per SM (64 registers, a few spilled in
+// the level-1 phase, one camera's slot loads at a time), for rigs with many waves of canvas tiles;
+// k_up_full three, with two cameras' slot loads in flight, which wins when the launch is a few waves.
 template <typename T, int NC>
 __global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
                                                         OutDesc od, const T* __restrict__ R2,
@@ -1484,12 +1517,17 @@ __global__ void __launch_bounds__(U_THREADS) k_up_full(const CamDev* __restrict_
                                                         const CamRef* __restrict__ refs, const Slot* __restrict__ g0buf,
                                                         int n, int wave, const UpTile* __restrict__ simple) {
     extern __shared__ float4 usm[];
-    if ((int)blockIdx.x >= n) {
-        up_simple_tile(cams, g, fp, od, simple[blockIdx.x - n], refs, reinterpret_cast<unsigned char*>(usm));
-        return;
-    }
-    const int nb = blockIdx.x + wave;  // prefetched: the tile one resident wave later (see k_reduce_t)
-    up_full_tile<T, NC>(cams, g, fp, od, R2, tiles[blockIdx.x], refs, g0buf, usm, nb < n ? tiles + nb : nullptr);
+    up_full_block<T, NC, (NC < 2 ? NC : 2)>(cams, g, fp, od, R2, tiles, refs, g0buf, n, wave, simple, usm);
+}
+template <typename T, int NC>
+__global__ void __launch_bounds__(U_THREADS, 4) k_up_full_b4(const CamDev* __restrict__ cams, RigGeom g, FramePtrs fp,
+                                                              OutDesc od, const T* __restrict__ R2,
+                                                              const UpTile* __restrict__ tiles,
+                                                              const CamRef* __restrict__ refs,
+                                                              const Slot* __restrict__ g0buf, int n, int wave,
+                                                              const UpTile* __restrict__ simple) {
+    extern __shared__ float4 usm[];
+    up_full_block<T, NC, 1>(cams, g, fp, od, R2, tiles, refs, g0buf, n, wave, simple, usm);
 }
 
 template <int NC>
@@ -1757,6 +1795,8 @@ struct FusedState {
     void* g0buf = nullptr;       // level-0 samples of the FULL canvas tiles, one slot per camera
     int n_g0 = 0;
     int n_staged = 0;            // down1 tiles with a staged source footprint
+    bool d1_small = false;       // down1 with the smaller footprint capacity (13 blocks per SM)
+    bool up_four = false;        // up_full with four resident blocks per SM
     int wave_red = 0, wave_up2 = 0, wave_up4 = 0;  // resident blocks on the device (L2 prefetch distance)
     void* R[MAXL] = {};          // R^l on the canvas grid, l >= 2
     CamRef* refs = nullptr;
@@ -1999,8 +2039,12 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
     const int L = g.levels;
     if (L >= 2 && fs->n_d1 > 0) {
         prof_mark(r, "fused_down1", s);
-        k_down1<T><<<fs->n_d1, D1_THREADS, D1_SMEM, s>>>(r->dcam, g, fp, od, fs->d1_tiles, fs->refs, fs->d1w,
-                                                         fs->d1cols, (Slot*)fs->g0buf);
+        if (fs->d1_small)
+            k_down1<T, D1_FOOT_SMALL><<<fs->n_d1, D1_THREADS, D1Cap<D1_FOOT_SMALL>::SMEM, s>>>(
+                r->dcam, g, fp, od, fs->d1_tiles, fs->refs, fs->d1w, fs->d1cols, (Slot*)fs->g0buf);
+        else
+            k_down1<T, D1_FOOT><<<fs->n_d1, D1_THREADS, D1_SMEM, s>>>(r->dcam, g, fp, od, fs->d1_tiles, fs->refs, fs->d1w,
+                                                                     fs->d1cols, (Slot*)fs->g0buf);
     }
     for (int l = 1; l + 1 < L; ++l) {
         if (fs->n_rc[l + 1] == 0) continue;
@@ -2024,14 +2068,16 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
     }
     if (fs->n_up[UP_FULL2]) {
         prof_mark(r, "fused_up_full", s);
-        k_up_full<T, 2><<<fs->n_up[UP_FULL2] + ns, U_THREADS, up_full_smem<2>(), s>>>(
+        auto k = fs->up_four ? k_up_full_b4<T, 2> : k_up_full<T, 2>;
+        k<<<fs->n_up[UP_FULL2] + ns, U_THREADS, up_full_smem<2>(), s>>>(
             r->dcam, g, fp, od, R2, fs->up_tiles[UP_FULL2], fs->refs, (const Slot*)fs->g0buf, fs->n_up[UP_FULL2],
             fs->wave_up2, fs->up_tiles[UP_SIMPLE]);
     }
     if (fs->n_up[UP_FULL4]) {
         const int extra = fs->n_up[UP_FULL2] ? 0 : ns;
         prof_mark(r, "fused_up_full4", s);
-        k_up_full<T, 4><<<fs->n_up[UP_FULL4] + extra, U_THREADS, up_full_smem<4>(), s>>>(
+        auto k = fs->up_four ? k_up_full_b4<T, 4> : k_up_full<T, 4>;
+        k<<<fs->n_up[UP_FULL4] + extra, U_THREADS, up_full_smem<4>(), s>>>(
             r->dcam, g, fp, od, R2, fs->up_tiles[UP_FULL4], fs->refs, (const Slot*)fs->g0buf, fs->n_up[UP_FULL4],
             fs->wave_up4, fs->up_tiles[UP_SIMPLE]);
     }
@@ -2045,11 +2091,17 @@ stitch_status launch_all(stitch_rig* r, FusedState* fs, const FramePtrs& fp, con
 
 template <typename T>
 stitch_status set_smem_attrs() {
-    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_down1<T, D1_FOOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_down1<T, D1_FOOT_SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)D1Cap<D1_FOOT_SMALL>::SMEM));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_reduce_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC_SMEM));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)up_full_smem<2>()));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)up_full_smem<4>()));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full_b4<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)up_full_smem<2>()));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_up_full_b4<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)up_full_smem<4>()));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_coarse_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(sizeof(float4) * CT_SMEM_F4)));
@@ -2063,8 +2115,15 @@ stitch_status set_waves(stitch_rig* r, FusedState* fs) {
     int sms = 0, pr = 0, p2 = 0, p4 = 0;
     STITCH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device));
     STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pr, k_reduce_t<T>, RC_THREADS, RC_SMEM));
-    STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_up_full<T, 2>, U_THREADS, up_full_smem<2>()));
-    STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p4, k_up_full<T, 4>, U_THREADS, up_full_smem<4>()));
+    // four resident up_full blocks per SM when the blended canvas tiles make many waves of them
+    fs->up_four = fs->n_up[UP_FULL2] + fs->n_up[UP_FULL4] >= 8 * 4 * std::max(sms, 1);
+    if (fs->up_four) {
+        STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_up_full_b4<T, 2>, U_THREADS, up_full_smem<2>()));
+        STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p4, k_up_full_b4<T, 4>, U_THREADS, up_full_smem<4>()));
+    } else {
+        STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p2, k_up_full<T, 2>, U_THREADS, up_full_smem<2>()));
+        STITCH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p4, k_up_full<T, 4>, U_THREADS, up_full_smem<4>()));
+    }
     fs->wave_red = std::max(pr, 1) * sms;
     fs->wave_up2 = std::max(p2, 1) * sms;
     fs->wave_up4 = std::max(p4, 1) * sms;
@@ -2384,6 +2443,19 @@ stitch_status fused_plan(stitch_rig* r) {
         d1.swap(kd);
         d1c.swap(kc);
     }
+    // footprint capacity: the smaller one when at most 2 % of the staged tiles need more
+    {
+        int staged = 0, over = 0;
+        for (const D1Tile& t : d1)
+            if (t.fwh != 0) {
+                ++staged;
+                over += ((((t.fwh & 0xffff) + 3) & ~3) * (t.fwh >> 16)) > D1_FOOT_SMALL;
+            }
+        fs->d1_small = (long long)over * 50 <= staged;
+        if (fs->d1_small)
+            for (D1Tile& t : d1)
+                if (t.fwh != 0 && (((t.fwh & 0xffff) + 3) & ~3) * (t.fwh >> 16) > D1_FOOT_SMALL) t.fxy = t.fwh = 0;
+    }
     // L2 prefetch chain: blocks start in index order as resident ones finish, so tile i + K
     // (K = resident blocks of k_down1 on the device) starts about when tile i ends
     {
@@ -2391,8 +2463,11 @@ stitch_status fused_plan(stitch_rig* r) {
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, r->device) != cudaSuccess || sms < 1)
             return STITCH_ECUDA;
         int bpsm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_down1<float4>, D1_THREADS, D1_SMEM) != cudaSuccess)
-            return STITCH_ECUDA;
+        const cudaError_t oe =
+            fs->d1_small ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_down1<float4, D1_FOOT_SMALL>, D1_THREADS,
+                                                                         D1Cap<D1_FOOT_SMALL>::SMEM)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_down1<float4, D1_FOOT>, D1_THREADS, D1_SMEM);
+        if (oe != cudaSuccess) return STITCH_ECUDA;
         const size_t K = (size_t)std::max(bpsm, 1) * sms;
         for (size_t k = 0; k + K < d1.size(); ++k) {
             const D1Tile& nx = d1[k + K];
@@ -2698,7 +2773,7 @@ __global__ void __launch_bounds__(U_THREADS) k_batch_general(const BatchRigDev* 
 // Multi-rig stage kernels (the alternative batched schedule): one block per task of one task type,
 // tasks of every rig in one launch, each kernel with its own register and shared-memory budget.
 template <typename T>
-__global__ void __launch_bounds__(D1_THREADS, D1_BLOCKS_PER_SM) k_mr_down1(const BatchRigDev* __restrict__ rigs,
+__global__ void __launch_bounds__(D1_THREADS, D1Cap<D1_FOOT>::BLOCKS) k_mr_down1(const BatchRigDev* __restrict__ rigs,
                                                              const BTask* __restrict__ tasks) {
     extern __shared__ float4 smem[];
     const BTask tk = tasks[blockIdx.x];

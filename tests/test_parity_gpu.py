@@ -268,11 +268,12 @@ def test_down1_staged_and_unstaged_tiles():
     ref = oracle.forward(cfg.cameras, frames, cfg.canvas_w, cfg.canvas_h, cfg.levels)
     for out_float in (True, False):
         gpu_util.compare(gpu_util.run_gpu(cfg, frames, "fused", out_float), ref, out_float)
-    # every tile of the 8x4K rig is staged
+    # at least 99 % of the 8x4K rig's tiles are staged (it takes the smaller footprint capacity,
+    # whose few larger footprints read from the frame)
     cfg = synth.config_8x4k(frames=1)
     with Rig(cfg.cameras, cfg.canvas_w, cfg.canvas_h, cfg.levels) as rig:
         t = rig.info()["tiles"]
-    assert t["down1_staged"] == t["down1"] and t["down1_interior"] > 0, t
+    assert t["down1_staged"] >= 0.99 * t["down1"] and t["down1_interior"] > 0, t
 
 
 @pytest.mark.parametrize("cfg_name", ["2cam", "4x1080p_scaled", "8x4k_scaled"])
