@@ -2772,13 +2772,13 @@ __global__ void __launch_bounds__(U_THREADS) k_batch_general(const BatchRigDev* 
 
 // Multi-rig stage kernels (the alternative batched schedule): one block per task of one task type,
 // tasks of every rig in one launch, each kernel with its own register and shared-memory budget.
-template <typename T>
-__global__ void __launch_bounds__(D1_THREADS, D1Cap<D1_FOOT>::BLOCKS) k_mr_down1(const BatchRigDev* __restrict__ rigs,
+template <typename T, int CAP>
+__global__ void __launch_bounds__(D1_THREADS, D1Cap<CAP>::BLOCKS) k_mr_down1(const BatchRigDev* __restrict__ rigs,
                                                              const BTask* __restrict__ tasks) {
     extern __shared__ float4 smem[];
     const BTask tk = tasks[blockIdx.x];
     const BatchRigDev& rg = rigs[tk.rig];
-    down1_tile<T>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, rg.d1cols, (Slot*)rg.g0buf, smem);
+    down1_tile<T, CAP>(rg.cams, rg.g, rg.fp, rg.od, task_tile<D1Tile>(tk), rg.refs, rg.d1w, rg.d1cols, (Slot*)rg.g0buf, smem);
 }
 
 template <typename T, typename RS>
@@ -2818,9 +2818,8 @@ __global__ void __launch_bounds__(U_THREADS) k_mr_up_simple(const BatchRigDev* _
     up_simple_tile(rg.cams, rg.g, rg.fp, rg.od, task_tile<UpTile>(tk), rg.refs, stage);
 }
 
-template <typename T, int NC>
-__global__ void __launch_bounds__(U_THREADS) k_mr_up_full(const BatchRigDev* __restrict__ rigs,
-                                                           const BTask* __restrict__ tasks) {
+template <typename T, int NC, int NB>
+__device__ __forceinline__ void mr_up_full_block(const BatchRigDev* __restrict__ rigs, const BTask* __restrict__ tasks) {
     extern __shared__ float4 usm[];
     // the rig's geometry and output descriptor in shared memory: the tile reads them inside its
     // loops, which from the rig record in global memory costs a load each time (1.9 ms against
@@ -2835,7 +2834,18 @@ __global__ void __launch_bounds__(U_THREADS) k_mr_up_full(const BatchRigDev* __r
     }
     __syncthreads();
     const T* R2 = g.levels >= 3 ? (const T*)rg.R[2] : nullptr;
-    up_full_tile<T, NC>(rg.cams, g, rg.fp, od, R2, task_tile<UpTile>(*tp), rg.refs, (const Slot*)rg.g0buf, usm);
+    up_full_tile<T, NC, NB>(rg.cams, g, rg.fp, od, R2, task_tile<UpTile>(*tp), rg.refs, (const Slot*)rg.g0buf, usm);
+}
+// (the two occupancies of k_up_full)
+template <typename T, int NC>
+__global__ void __launch_bounds__(U_THREADS) k_mr_up_full(const BatchRigDev* __restrict__ rigs,
+                                                           const BTask* __restrict__ tasks) {
+    mr_up_full_block<T, NC, (NC < 2 ? NC : 2)>(rigs, tasks);
+}
+template <typename T, int NC>
+__global__ void __launch_bounds__(U_THREADS, 4) k_mr_up_full_b4(const BatchRigDev* __restrict__ rigs,
+                                                                 const BTask* __restrict__ tasks) {
+    mr_up_full_block<T, NC, 1>(rigs, tasks);
 }
 
 // A launch of the staged schedule: all tasks of one type and level, over every rig.
@@ -2875,6 +2885,8 @@ struct BatchState {
     std::vector<StageGroup> groups[B_SHAPES];  // staged schedule per tile-shape combination, in launch order
     int shape = 0;                             // the combination chosen
     bool staged = false;             // schedule chosen by the tuner: staged launches or persistent
+    bool d1_small = false;           // staged down1 launches with the smaller footprint capacity (every rig's)
+    bool up_four = false;            // staged up_full launches at four blocks per SM
     bool streams = false;            // ... or every rig's own launch sequence on its own stream
     cudaStream_t rs[B_MAXRIGS] = {};
     cudaEvent_t rdone[B_MAXRIGS] = {};
@@ -2946,7 +2958,12 @@ stitch_status b_launch_staged(BatchState* b, int shape, cudaStream_t s) {
     for (const StageGroup& gr : b->groups[shape]) {
         if (!gr.count) continue;
         switch (gr.type) {
-            case BT_D1: k_mr_down1<T><<<gr.count, D1_THREADS, D1_SMEM, s>>>(b->d_rigs, gr.d_tasks); break;
+            case BT_D1:
+                if (b->d1_small)
+                    k_mr_down1<T, D1_FOOT_SMALL><<<gr.count, D1_THREADS, D1Cap<D1_FOOT_SMALL>::SMEM, s>>>(b->d_rigs, gr.d_tasks);
+                else
+                    k_mr_down1<T, D1_FOOT><<<gr.count, D1_THREADS, D1_SMEM, s>>>(b->d_rigs, gr.d_tasks);
+                break;
             case BT_RED:
                 if (b_rs(shape)) k_mr_reduce_col<T><<<gr.count, RC_THREADS, RC_SMEM, s>>>(b->d_rigs, gr.d_tasks);
                 else k_mr_reduce<T, RSRig><<<gr.count, 256, RSRig::SMEM, s>>>(b->d_rigs, gr.d_tasks);
@@ -2958,8 +2975,14 @@ stitch_status b_launch_staged(BatchState* b, int shape, cudaStream_t s) {
                     k_mr_coarse<T, CSRig><<<gr.count, 256, sizeof(float4) * CSRig::SMEM_F4, s>>>(b->d_rigs, gr.d_tasks);
                 break;
             case BT_UPS: k_mr_up_simple<<<gr.count, U_THREADS, 0, s>>>(b->d_rigs, gr.d_tasks); break;
-            case BT_UPF2: k_mr_up_full<T, 2><<<gr.count, U_THREADS, up_full_smem<2>(), s>>>(b->d_rigs, gr.d_tasks); break;
-            case BT_UPF4: k_mr_up_full<T, 4><<<gr.count, U_THREADS, up_full_smem<4>(), s>>>(b->d_rigs, gr.d_tasks); break;
+            case BT_UPF2:
+                if (b->up_four) k_mr_up_full_b4<T, 2><<<gr.count, U_THREADS, up_full_smem<2>(), s>>>(b->d_rigs, gr.d_tasks);
+                else k_mr_up_full<T, 2><<<gr.count, U_THREADS, up_full_smem<2>(), s>>>(b->d_rigs, gr.d_tasks);
+                break;
+            case BT_UPF4:
+                if (b->up_four) k_mr_up_full_b4<T, 4><<<gr.count, U_THREADS, up_full_smem<4>(), s>>>(b->d_rigs, gr.d_tasks);
+                else k_mr_up_full<T, 4><<<gr.count, U_THREADS, up_full_smem<4>(), s>>>(b->d_rigs, gr.d_tasks);
+                break;
             case BT_UPG: k_batch_general<T><<<gr.count, U_THREADS, 0, s>>>(b->d_rigs, gr.d_tasks, b->d_ctl); break;
             default: break;
         }
@@ -2969,7 +2992,13 @@ stitch_status b_launch_staged(BatchState* b, int shape, cudaStream_t s) {
 
 template <typename T>
 stitch_status b_staged_attrs() {
-    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_down1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_down1<T, D1_FOOT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)D1_SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_down1<T, D1_FOOT_SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)D1Cap<D1_FOOT_SMALL>::SMEM));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_up_full_b4<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)up_full_smem<2>()));
+    STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_up_full_b4<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)up_full_smem<4>()));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce<T, RSRig>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)RSRig::SMEM));
     STITCH_CUDA_TRY(cudaFuncSetAttribute(k_mr_reduce_col<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -3419,6 +3448,23 @@ stitch_status fused_batch_create(stitch_rig* const* rigs, int n, void** out) {
     {
         int maxL = 0;
         for (int k = 0; k < n; ++k) maxL = std::max(maxL, rigs[k]->geom.levels);
+        // the occupancy variants the rigs' own launches take (down1: the smaller footprint capacity
+        // when every rig takes it; up_full: four blocks per SM for many waves of blended tiles)
+        {
+            long long nfull = 0;
+            b->d1_small = true;
+            for (int k = 0; k < n; ++k) {
+                const FusedState* fs = (const FusedState*)rigs[k]->fused;
+                b->d1_small = b->d1_small && fs->d1_small;
+                nfull += fs->n_up[UP_FULL2] + fs->n_up[UP_FULL4];
+            }
+            int sms = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, rigs[0]->device) != cudaSuccess) {
+                cudaGetLastError();
+                sms = 1;
+            }
+            b->up_four = nfull >= 8LL * 4 * std::max(sms, 1);
+        }
         std::vector<BTask> wred[MAXL], wco[MAXL];
         for (int k = 0; k < n; ++k) {
             stitch_rig* r = rigs[k];
