@@ -391,7 +391,9 @@ constexpr float D1_FLOOR_M = 12582912.0f;       // 1.5 * 2^23
 constexpr unsigned D1_FLOOR_BITS = 0x4B400000u;  // its bit pattern
 
 // Level-0 sample of virtual row r at the column whose anchored numerators and denominator at the
-// anchor row are (nuv, dqc): (r, g, b, normalised weight a), zero outside Omega^0 (a < 0).
+// anchor row are (nuv, dqc): (r, g, b, normalised weight a), weight 0 outside Omega^0 (a < 0).
+// The colour there is whatever the taps give: Omega^0 holds the 5 x 5 support of every stored G^1
+// sample, and a level-0 output of weight 0 adds nothing to a blend, so it is never read.
 // Position and taps are those of map_pos + sample_rgb, so the three modes give bit-identical
 // samples.  The floor of the offsets ru, rv (|ru|, |rv| < 2^22 on staged tiles, whose footprint
 // the planner bounds) comes from one addition rounded toward -infinity:
@@ -403,7 +405,7 @@ __device__ __forceinline__ V4 d1_sample(const D1Ctx& x, float2 nuv, float dqc, i
     const float2 n = f2fma(make_float2(x.tm.pu2, x.tm.pv2), dy, nuv);
     const float rden = __fdividef(1.0f, den);
     V4 s;
-    s.b.y = a;
+    s.b.y = fmaxf(a, 0.0f);
     if (MODE == D1M_FRAME) {
         float ru = n.x * rden, rv = n.y * rden;
         ru = fminf(fmaxf(ru, -1.0e7f), 1.0e7f);
@@ -450,7 +452,6 @@ __device__ __forceinline__ V4 d1_sample(const D1Ctx& x, float2 nuv, float dqc, i
         }
         d1_bilerp(w00, w01, w10, w11, fx, fy, x.scale, s);
     }
-    if (!(a >= 0.f)) s = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     return s;
 }
 
