@@ -523,23 +523,33 @@ __device__ __forceinline__ void d1_sweep(const D1Ctx& x, float4* __restrict__ vc
     V4 B = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, C = B;
     // weights of INTERIOR tiles are all 1; the others are loaded one row pair ahead
     float we = ONES ? 1.0f : __ldg(wcol), wo = ONES ? 1.0f : __ldg(wcol + D1_SX);
+    const float* wp = wcol + 2 * D1_SX;        // weights of row 2m + 2
+    float4* vp = vcol - 2 * D1_VROW;           // vres row of output m - 2
+    D1Out<T> oq = o;
+    oq.p -= 2 * o.step;                        // output row 2m - 2
+    oq.rows += 2;
 #pragma unroll 1
     for (int m = 0; m <= D1_TY; ++m) {
         const float ae = we, ao = wo;
         if (!ONES) {
-            we = __ldg(wcol + (2 * m + 2) * D1_SX);
-            wo = __ldg(wcol + min(2 * m + 3, D1_SY - 1) * D1_SX);
+            we = __ldg(wp);
+            wo = __ldg(m < D1_TY ? wp + D1_SX : wp);
         }
         const V4 se = d1_sample<MODE>(x, nuv, dqc, 2 * m, ae);
         const V4 so = d1_sample<MODE>(x, nuv, dqc, 2 * m + 1, ao);
-        if (m >= 1) d1_put<T, OUTK>(o, 2 * m - 2, se);
-        if (m >= 2) vcol[(m - 2) * D1_VROW] = f4_of(v4_fma(d1_w(4), se, C));
+        if (m >= 1) d1_put<T, OUTK>(oq, 0, se);
+        if (m >= 2) *vp = f4_of(v4_fma(d1_w(4), se, C));
         C = v4_fma(d1_w(2), se, B);
         B = v4_mul(d1_w(0), se);
-        if (m >= 1) d1_put<T, OUTK>(o, 2 * m - 1, so);
+        if (m >= 1) d1_put<T, OUTK>(oq, 1, so);
         C = v4_fma(d1_w(3), so, C);
         B = v4_fma(d1_w(1), so, B);
+        wp += 2 * D1_SX;
+        vp += D1_VROW;
+        oq.p += 2 * o.step;
+        oq.rows -= 2;
     }
+
     const V4 se = d1_sample<MODE>(x, nuv, dqc, 2 * D1_TY + 2, we);
     vcol[(D1_TY - 1) * D1_VROW] = f4_of(v4_fma(d1_w(4), se, C));
 }
