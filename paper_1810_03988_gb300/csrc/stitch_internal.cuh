@@ -413,8 +413,9 @@ __device__ __forceinline__ float3 sample_rgb_inside(const uint8_t* __restrict__ 
 }
 
 __device__ __forceinline__ unsigned char quantize_u8(float v) {
-    // v already clamped to [0, 1]; round half to even
-    return (unsigned char)__float2int_rn(255.0f * v);
+    // v already clamped to [0, 1]: 2^23 + 255 v rounded once to nearest even in the addition of one
+    // fused multiply-add, whose low byte is round-half-even(255 v)
+    return (unsigned char)(__float_as_uint(fmaf(v, 255.0f, 8388608.0f)) & 0xffu);
 }
 
 // ------------------------------------------------------------------------------------------------
